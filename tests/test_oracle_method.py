@@ -1,0 +1,204 @@
+"""Pins for the whole oracle method: Madelung (Eq. st1), Ewald (App. D), periodicity (Eq. 7),
+invariants, energy derivatives and the near-field sum."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import ewald as E
+from oracle import psum_oracle as O
+from paper_1310_4374_gb300 import workloads as W
+
+
+def _eps_M(sys_, phi, madelung):
+    a = sys_.meta["spacing"]
+    return np.abs(sys_.q * phi * a / madelung - 1.0)
+
+
+def test_ewald_reproduces_madelung(madelung):
+    s = W.rock_salt(n=2, p=7, M=200)
+    phi, g = E.ewald(s.x, s.x, s.q, s.d)
+    assert _eps_M(s, phi, madelung).max() < 1e-14
+    assert np.abs(g).max() < 1e-13                      # ions sit at equilibrium
+
+
+@pytest.mark.parametrize("p,M,bound", [(7, 200, 1e-5), (11, 300, 2e-6), (15, 512, 1e-7),
+                                       (34, 2450, 1e-13)])
+def test_method_madelung_2x2x2(p, M, bound, madelung):
+    # Table 1 (Gauss grid: 4.85e-6, 1.17e-7, 7.16e-8 at paper p = 8, 12, 16) and the
+    # high-accuracy run eps_M ~ 6e-14 at paper p = 35 (Sec. 4.1); here p = paper p - 1.
+    s = W.rock_salt(n=2, p=p, M=M)
+    out = O.periodic_sum(s.x, s.q, s.d, p, M)
+    assert _eps_M(s, out["phi"], madelung).max() < bound
+    assert np.abs(out["grad"]).max() < 1e3 * bound
+
+
+def test_method_madelung_rock_salt_8cubed(madelung):
+    s = W.rock_salt(n=8, p=12, M=400)
+    out = O.periodic_sum(s.x, s.q, s.d, s.p, s.M)
+    assert _eps_M(s, out["phi"], madelung).max() < 2e-6
+
+
+def test_error_decays_geometrically_against_ewald():
+    rng = np.random.default_rng(5)
+    N = 40
+    x = rng.uniform(-0.5, 0.5, (N, 3))
+    q = rng.normal(size=N)
+    q -= q.mean()
+    pe, ge = E.ewald(x, x, q, (1, 1, 1))
+    errs = []
+    for p in (8, 12, 16, 24):
+        out = O.periodic_sum(x, q, (1, 1, 1), p, max(200, 2 * (p + 1) ** 2))
+        errs.append((O.relative_l2(out["phi"], pe), O.relative_l2(out["grad"], ge)))
+    # lambda = sqrt(3): a factor lambda^-4 ~ 0.11 per step of 4 in p, until roundoff
+    for (a, ga), (b, gb) in zip(errs[:-1], errs[1:]):
+        assert b < 0.3 * a and gb < 0.3 * ga
+    assert errs[2][0] < 3e-7 and errs[3][0] < 2e-9 and errs[3][1] < 1e-8
+
+
+def test_non_cubic_box_converges_with_wider_near_block():
+    rng = np.random.default_rng(6)
+    d = (1.0, 1.5, 2.0)
+    N = 30
+    x = rng.uniform(-0.5, 0.5, (N, 3)) * d
+    q = rng.normal(size=N)
+    q -= q.mean()
+    pe = E.ewald(x, x, q, d, grad=False)
+    e1 = O.relative_l2(O.periodic_sum(x, q, d, 16, 800, grad=False)["phi"], pe)
+    e2 = O.relative_l2(O.periodic_sum(x, q, d, 16, 800, K=(2, 1, 1), grad=False)["phi"], pe)
+    assert e1 < 2e-3            # lambda_eff = 1.5 / R0 = 1.11 with the 3x3x3 block
+    assert e2 < 1e-5 and e2 < 0.05 * e1
+
+
+@pytest.mark.parametrize("d", [(1.0, 1.0, 1.0), (1.0, 1.0, 2.0)])
+def test_periodicity_on_faces(d):
+    rng = np.random.default_rng(8)
+    N = 24
+    x = rng.uniform(-0.5, 0.5, (N, 3)) * d
+    q = rng.normal(size=N)
+    q -= q.mean()
+    p, M = 20, 900
+    K = (1, 1, 1) if d[2] == 1.0 else (2, 2, 1)
+    pl = O.Plan(d, p, M, K=K)
+    probes, partners = [], []
+    for k in range(3):
+        y = rng.uniform(-0.5, 0.5, (6, 3)) * d
+        y[:, k] = -d[k] / 2
+        yt = y.copy()
+        yt[:, k] += d[k]
+        probes.append(y)
+        partners.append(yt)
+    Y = np.concatenate(probes)
+    Yt = np.concatenate(partners)
+    a = pl.evaluate(x, q, targets=Y)
+    b = pl.evaluate(x, q, targets=Yt)
+    scale = np.sqrt(np.mean(a["phi"] ** 2))
+    assert np.max(np.abs(a["phi"] - b["phi"])) < 1e-6 * scale
+    gscale = np.sqrt(np.mean(a["grad"] ** 2))
+    assert np.max(np.abs(a["grad"] - b["grad"])) < 1e-5 * gscale
+
+
+def _small_system(seed=11, N=30, d=(1.0, 1.0, 1.0)):
+    rng = np.random.default_rng(seed)
+    x = rng.uniform(-0.5, 0.5, (N, 3)) * np.asarray(d)
+    q = rng.normal(size=N)
+    q -= q.mean()
+    return x, q
+
+
+def test_linearity_sign_and_permutation():
+    x, q = _small_system()
+    d, p, M = (1.0, 1.0, 1.0), 12, 400
+    pl = O.Plan(d, p, M)
+    rng = np.random.default_rng(1)
+    q2 = rng.normal(size=q.size)
+    q2 -= q2.mean()
+    a = pl.evaluate(x, q)
+    b = pl.evaluate(x, q2)
+    c = pl.evaluate(x, 2.0 * q - 3.0 * q2)
+    assert np.allclose(c["phi"], 2 * a["phi"] - 3 * b["phi"], rtol=1e-11, atol=1e-11)
+    assert np.allclose(c["grad"], 2 * a["grad"] - 3 * b["grad"], rtol=1e-11, atol=1e-10)
+    n = pl.evaluate(x, -q)
+    assert np.allclose(n["phi"], -a["phi"], rtol=1e-13, atol=1e-13)
+    perm = rng.permutation(q.size)
+    pp = pl.evaluate(x[perm], q[perm])
+    assert np.allclose(pp["phi"], a["phi"][perm], rtol=1e-12, atol=1e-12)
+    assert np.allclose(pp["grad"], a["grad"][perm], rtol=1e-12, atol=1e-11)
+
+
+def test_translation_with_wrap():
+    x, q = _small_system(seed=12, d=(1.0, 1.0, 1.0))
+    d = np.array([1.0, 1.0, 1.0])
+    s = np.array([0.31, -0.22, 0.47])
+    xs = x + s
+    xs -= d * np.floor(xs / d + 0.5)
+    p, M = 22, 1100
+    a = O.periodic_sum(x, q, d, p, M)
+    b = O.periodic_sum(xs, q, d, p, M)
+    assert O.relative_l2(b["phi"], a["phi"]) < 1e-8          # includes the zero-mean constant
+    assert O.relative_l2(b["grad"], a["grad"]) < 1e-8
+
+
+def test_scale_covariance():
+    x, q = _small_system(seed=13, d=(1.0, 1.2, 0.8))
+    d = np.array([1.0, 1.2, 0.8])
+    s = 2.5
+    a = O.periodic_sum(x, q, d, 10, 300)
+    b = O.periodic_sum(s * x, q, s * d, 10, 300)
+    assert np.allclose(b["phi"], a["phi"] / s, rtol=1e-11, atol=1e-12)
+    assert np.allclose(b["grad"], a["grad"] / s ** 2, rtol=1e-10, atol=1e-11)
+
+
+def test_energy_derivatives_match_finite_differences():
+    x, q = _small_system(seed=14, N=12)
+    d, p, M = (1.0, 1.0, 1.0), 20, 900
+    pl = O.Plan(d, p, M)
+    out = pl.evaluate(x, q)
+
+    def energy(xx, qq):
+        return 0.5 * float(np.dot(qq, pl.evaluate(xx, qq, grad=False)["phi"]))
+
+    h = 1e-5
+    for j in (0, 5):
+        for k in range(3):
+            xp, xm = x.copy(), x.copy()
+            xp[j, k] += h
+            xm[j, k] -= h
+            fd = (energy(xp, q) - energy(xm, q)) / (2 * h)
+            assert fd == pytest.approx(q[j] * out["grad"][j, k], rel=1e-6, abs=1e-8)
+    # charge derivative along a neutral direction: dE = phi_a - phi_b
+    qp, qm = q.copy(), q.copy()
+    qp[2] += h
+    qp[7] -= h
+    qm[2] -= h
+    qm[7] += h
+    fd = (energy(x, qp) - energy(x, qm)) / (2 * h)
+    assert fd == pytest.approx(out["phi"][2] - out["phi"][7], rel=1e-6, abs=1e-8)
+
+
+def test_near_sum_reciprocity_and_gradient():
+    rng = np.random.default_rng(15)
+    d = (1.0, 1.3, 0.7)
+    xa = rng.uniform(-0.5, 0.5, (1, 3)) * d
+    xb = rng.uniform(-0.5, 0.5, (1, 3)) * d
+    one = np.ones(1)
+    ab = O.near_sum(xa, xb, one, d, grad=False)[0]
+    ba = O.near_sum(xb, xa, one, d, grad=False)[0]
+    assert ab == pytest.approx(ba, rel=1e-15)
+    # a single pair without images is Coulomb's law
+    r = float(np.linalg.norm(xa - xb))
+    assert O.near_sum(xa, xb, one, d, K=(0, 0, 0), grad=False)[0] == pytest.approx(1 / r, rel=1e-15)
+    # K(0) = 0 for a target on a source, images still count
+    self_ = O.near_sum(xa, xa, one, (1.0, 1.0, 1.0), K=(1, 0, 0), grad=False)[0]
+    assert self_ == pytest.approx(2.0, rel=1e-15)
+    # the gradient is minus the field: central differences of phi
+    y = rng.uniform(-0.5, 0.5, (1, 3)) * d
+    xs = rng.uniform(-0.5, 0.5, (5, 3)) * d
+    qs = rng.normal(size=5)
+    _, g = O.near_sum(y, xs, qs, d)
+    h = 1e-6
+    for k in range(3):
+        e = np.zeros((1, 3))
+        e[0, k] = h
+        fd = (O.near_sum(y + e, xs, qs, d, grad=False)[0] - O.near_sum(y - e, xs, qs, d, grad=False)[0]) / (2 * h)
+        assert g[0, k] == pytest.approx(fd, rel=1e-6, abs=1e-7)
