@@ -1,0 +1,408 @@
+#!/usr/bin/env python3
+"""Benchmark of the periodic Coulomb sum on one GB300 (or N replicas).
+
+One step = one pass of the whole hot path (psum_eval: validation, spatial sort,
+near-field pair sum at the charges and the check points, least-squares fit,
+zero-mean constant, far field, combination) over 100,000 charges in the
+(1, 1.5, 2) box with p = 16 and M = 800, FP32C pair arithmetic.  Inputs are
+resident in device memory; L2 is flushed (a 256 MiB write) before every timed
+step, outside the timed events.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle
+instead, on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "periodic Coulomb pair-interactions/s (pot+force) at 1e-6 rel err, FP32 vs FP64"
+UNIT = "pairs/s"
+N_MAIN, D_MAIN, P_MAIN, M_MAIN, SEED_MAIN = 100_000, (1.0, 1.5, 2.0), 16, 800, 2
+N_FP64 = 20_000            # FP32C-vs-FP64 comparison runs on a 20k-charge system of the same box
+FP32_OPS_PAIR_GRAD = 13    # FP32-pipe instructions per potential+gradient pair (3 sub, 3 r^2, 4 phi/weight, 3 grad)
+FP32_OPS_PAIR_PHI = 7      # potential only (3 sub, 3 r^2, 1 fma)
+
+
+def workload_name(N=N_MAIN):
+    return f"uniform Gaussian charges, N={N}, box d=(1,1.5,2), p=16, M=800, 3x3x3 near images, fp32c"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="psum", choices=["psum", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU budget of the oracle sample")
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = max(float(r[2]) for r in rows if r[2].replace(".", "").isdigit())
+        power = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        loaded = [s for s, p in zip(sm, power)] if sm else []
+        return {"sm_mhz": statistics.median(loaded) if loaded else None, "sm_max_mhz": mx,
+                "samples": len(rows), "power_w_max": max(power) if power else None, "reasons": reasons}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+def near_kernel_traffic(n_pairs_launch):
+    """DRAM traffic per launch of the charge near-field kernel from the committed ncu
+    summary, scaled to this launch, if the kernel source has not changed since."""
+    path = os.path.join(ROOT, "profiles", "near32_traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+        with open(os.path.join(ROOT, "paper_1310_4374_gb300", "csrc", "near.cu"), "rb") as f:
+            h = hashlib.sha256(f.read()).hexdigest()[:16]
+        if rec.get("near_cu_sha256_16") != h:
+            return None
+        return rec["dram_bytes"] * n_pairs_launch / rec["pairs"]
+    except Exception:
+        return None
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def run_psum(args):
+    import numpy as np
+    import torch
+
+    from paper_1310_4374_gb300 import binding as B
+    from paper_1310_4374_gb300 import workloads as W
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    # every rank evaluates its own replica of the system (weak scaling, no exchange)
+    s = W.uniform_gauss(N=N_MAIN, d=D_MAIN, p=P_MAIN, M=M_MAIN, seed=SEED_MAIN + rank)
+    pairs_step = 27 * s.N * (s.N + 2 * s.M)
+    pc = B.PeriodicCoulomb(s.d, s.p, s.M, precision="fp32c")
+    B.psum_profile(pc.plan, True)
+    x = torch.as_tensor(s.x, dtype=torch.float64, device=dev)
+    q = torch.as_tensor(s.q, dtype=torch.float64, device=dev)
+    phi = torch.empty(s.N, dtype=torch.float64, device=dev)
+    grad = torch.empty((s.N, 3), dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        B.psum_eval(pc.plan, x, q, phi, grad, stream=stream)
+
+    for _ in range(max(args.warmup, 0)):
+        step()
+    st = B.psum_sync(pc.plan, stream)
+    if st != B.PSUM_OK:
+        raise B.PsumError(st, "warm-up")
+    torch.cuda.synchronize()
+    barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    launches0 = B.psum_launch_count(pc.plan)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    stage_ms = []
+    torch.cuda.synchronize()
+    barrier()
+    for k in range(args.steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        step()
+        ev[k][1].record(stream)
+        stage_ms.append(B.psum_last_timings(pc.plan, stream))     # waits for the stream
+    torch.cuda.synchronize()
+    barrier()
+    launches = B.psum_launch_count(pc.plan) - launches0
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    st = B.psum_sync(pc.plan, stream)
+    if st != B.PSUM_OK:
+        raise B.PsumError(st, "timed steps")
+    total_ms = sum(step_ms)
+    t_max = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    if dist is not None:
+        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+    total_ms = float(t_max.item())
+    ms_per_step = total_ms / args.steps
+    value = pairs_step * world * args.steps / (total_ms * 1e-3)
+
+    # dominant kernel: the near-field sum at the charges (potential + gradient)
+    near_ms = statistics.mean(t["near_charges"] for t in stage_ms)
+    near_pairs = 27 * s.N * s.N
+    props = torch.cuda.get_device_properties(dev)
+    peaks = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_ops = props.multi_processor_count * 128 * sm_max * 1e6
+    achieved = FP32_OPS_PAIR_GRAD * near_pairs / (near_ms * 1e-3)
+    traffic = near_kernel_traffic(near_pairs)
+    roofline = {"bound": "alu", "kernel": "k_near32<grad>", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
+                "unit": "T FP32-pipe ops/s", "frac": achieved / peak_ops, "traffic": traffic,
+                "peak_source": f"{props.multi_processor_count} SMs x 128 FP32 lanes x {sm_max:.0f} MHz "
+                               "(sm_max_mhz of MEASURED_PEAKS.json)",
+                "ops_per_pair": FP32_OPS_PAIR_GRAD, "pairs_per_launch": near_pairs,
+                "kernel_ms": near_ms}
+    if clk and clk.get("sm_mhz"):
+        roofline["frac_at_observed_clock"] = achieved / (props.multi_processor_count * 128 * clk["sm_mhz"] * 1e6)
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": workload_name(), "N": s.N, "p": s.p, "M": s.M, "box": list(s.d),
+                      "near_images": 27, "pairs_per_step": pairs_step,
+                      "precision": "fp32c: f32 pair arithmetic on group-relative coordinates, two-sum "
+                                   "compensated accumulation; f64 sort keys, fit, mean and far field",
+                      "l2": "flushed before every timed step (256 MiB write, outside the events)",
+                      "parallelism": f"{world} independent replicas" if world > 1 else "single GPU"},
+           "solves_per_s": world * args.steps / (total_ms * 1e-3),
+           "stages_ms": {k: statistics.mean(t[k] for t in stage_ms) for k in stage_ms[0]},
+           "roofline": roofline, "gpu_launches": launches, "clocks": clk}
+
+    if rank == 0 and not args.no_e2e:
+        out["e2e"] = e2e_leg(pc, s, args)
+    if rank == 0 and not args.no_fp64:
+        out["fp64"] = fp64_leg(args)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline_leg(s, phi, grad, args)
+    pc.close()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def e2e_leg(pc, s, args):
+    """The same metric through psum_eval_host: host buffers, copies inside the timed region."""
+    import numpy as np
+    import torch
+
+    from paper_1310_4374_gb300 import binding as B
+
+    x = torch.as_tensor(s.x, dtype=torch.float64).pin_memory()
+    q = torch.as_tensor(s.q, dtype=torch.float64).pin_memory()
+    phi = torch.empty(s.N, dtype=torch.float64).pin_memory()
+    grad = torch.empty((s.N, 3), dtype=torch.float64).pin_memory()
+    stream = torch.cuda.current_stream()
+    B.psum_profile(pc.plan, False)
+    st = B.psum_eval_host(pc.plan, x, q, phi, grad, stream=stream)     # warm-up
+    if st != B.PSUM_OK:
+        raise B.PsumError(st, "e2e warm-up")
+    times = []
+    for _ in range(max(1, min(args.steps, 3))):
+        t0 = time.perf_counter()
+        st = B.psum_eval_host(pc.plan, x, q, phi, grad, stream=stream)
+        times.append(time.perf_counter() - t0)
+        if st != B.PSUM_OK:
+            raise B.PsumError(st, "e2e")
+    B.psum_profile(pc.plan, True)
+    pairs = 27 * s.N * (s.N + 2 * s.M)
+    t = statistics.mean(times)
+    return {"value": pairs / t, "unit": UNIT, "h2d_bytes_per_step": int(x.numel() * 8 + q.numel() * 8),
+            "d2h_bytes_per_step": int(phi.numel() * 8 + grad.numel() * 8), "ms_per_step": t * 1e3,
+            "api": "psum_eval_host (pinned host buffers; copies and final synchronisation timed)"}
+
+
+def fp64_leg(args):
+    """FP64 pair kernel vs FP32C on a 20k-charge system of the same box, p and M."""
+    import torch
+
+    from paper_1310_4374_gb300 import binding as B
+    from paper_1310_4374_gb300 import workloads as W
+
+    s = W.uniform_gauss(N=N_FP64, d=D_MAIN, p=P_MAIN, M=M_MAIN, seed=SEED_MAIN + 100)
+    x = torch.as_tensor(s.x, dtype=torch.float64, device="cuda")
+    q = torch.as_tensor(s.q, dtype=torch.float64, device="cuda")
+    res = {}
+    outs = {}
+    for prec in ("fp64", "fp32c"):
+        pc = B.PeriodicCoulomb(s.d, s.p, s.M, precision=prec)
+        B.psum_profile(pc.plan, True)
+        phi, g = pc(x, q)                       # warm-up
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 2
+        ev0.record()
+        for _ in range(reps):
+            phi, g = pc(x, q, check=False)
+        ev1.record()
+        torch.cuda.synchronize()
+        st = B.psum_sync(pc.plan)
+        if st != B.PSUM_OK:
+            raise B.PsumError(st, "fp64 leg")
+        ms = ev0.elapsed_time(ev1) / reps
+        near_ms = B.psum_last_timings(pc.plan)["near_charges"]
+        pc.close()
+        pairs = 27 * s.N * (s.N + 2 * s.M)
+        res[prec] = {"pairs_per_s": pairs / (ms * 1e-3), "ms_per_step": ms,
+                     "near_charges_pairs_per_s": 27 * s.N * s.N / (near_ms * 1e-3)}
+        outs[prec] = (phi.cpu().numpy(), g.cpu().numpy())
+    import numpy as np
+
+    def rel(a, b):
+        return float(np.sqrt(np.mean((a - b) ** 2)) / np.sqrt(np.mean(b ** 2)))
+    res["workload"] = workload_name(N_FP64).replace("fp32c", "fp64 and fp32c")
+    res["speedup_fp32c_over_fp64"] = res["fp32c"]["pairs_per_s"] / res["fp64"]["pairs_per_s"]
+    res["eps2_fp32c_vs_fp64"] = {"phi": rel(outs["fp32c"][0], outs["fp64"][0]),
+                                 "grad": rel(outs["fp32c"][1], outs["fp64"][1])}
+    return res
+
+
+def cpu_baseline_leg(s, phi_gpu, grad_gpu, args):
+    """The oracle on the host cores on a bounded sample: the 2M check-point rows plus a
+    seeded sample of targets, with the fit, mean and far field; also the GPU's error there."""
+    import numpy as np
+
+    from oracle import psum_oracle as O
+
+    pl = O.Plan(s.d, s.p, s.M)
+    rng = np.random.default_rng(1234)
+    # size the target sample from a short calibration run
+    probe = s.x[:16]
+    t0 = time.perf_counter()
+    O.near_sum(probe, s.x, s.q, s.d, grad=True)
+    rate = 27 * s.N * 16 / (time.perf_counter() - t0)           # pairs/s
+    n_check_pairs = 27 * s.N * 2 * s.M
+    n_t = int(max(16, min(4096, (args.cpu_seconds * rate - n_check_pairs) / (27 * s.N))))
+    sample = np.sort(rng.choice(s.N, size=n_t, replace=False))
+    t0 = time.perf_counter()
+    ref = pl.evaluate(s.x, s.q, targets=s.x[sample])
+    dt = time.perf_counter() - t0
+    pairs = 27 * s.N * (2 * s.M + n_t)
+    phi = phi_gpu.cpu().numpy()[sample]
+    g = grad_gpu.cpu().numpy()[sample]
+    return {"value": pairs / dt, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+            "sample": f"near sums at the {2 * s.M} check points and {n_t} seeded charges of the same "
+                      f"{s.N}-charge system, plus the fit, mean and far field ({pairs:.3e} pairs, {dt:.1f} s)",
+            "gpu_eps2_on_sample": {"phi": O.relative_l2(phi, ref["phi"]), "grad": O.relative_l2(g, ref["grad"])}}
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the oracle as it stands, on the host cores
+# ---------------------------------------------------------------------------
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import numpy as np
+
+    from oracle import psum_oracle as O
+    from paper_1310_4374_gb300 import workloads as W
+
+    s = W.uniform_gauss(N=N_MAIN, d=D_MAIN, p=P_MAIN, M=M_MAIN, seed=SEED_MAIN)
+    pl = O.Plan(s.d, s.p, s.M)
+    rng = np.random.default_rng(4321)
+    n_t = 64
+    pairs = 27 * s.N * (2 * s.M + n_t)
+
+    def step():
+        sample = np.sort(rng.choice(s.N, size=n_t, replace=False))
+        pl.evaluate(s.x, s.q, targets=s.x[sample])
+
+    for _ in range(max(args.warmup, 0)):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = time.perf_counter() - t0
+    value = pairs * args.steps / dt
+    sample = (f"per step: near sums at the {2 * s.M} check points and {n_t} seeded charges of the "
+              f"{s.N}-charge system, plus the fit, mean and far field ({pairs:.3e} pairs)")
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": {"workload": workload_name().replace("fp32c", "CPU oracle f64"),
+                                            "sampled": True},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_psum(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,181 @@
+/*
+ * psum -- periodic Coulomb sums on one GPU by the periodisation method of
+ * Gumerov & Duraiswami, "A method to compute periodic sums" (arXiv 1310.4374).
+ *
+ * For N charges q_i at x_i in the box [-d1/2, d1/2) x [-d2/2, d2/2) x [-d3/2, d3/2)
+ * with sum q_i = 0 (Sec. 1, Eq. 1) the library returns the periodic potential
+ *
+ *     phi(y) = sum_{p} sum_i q_i K(y - x_i + p),  K(r) = 1/|r|, K(0) = 0  (Eq. 2)
+ *
+ * and its gradient at every charge, with the side condition fixed by the paper:
+ * periodicity of phi (Eq. 7) and zero mean over the box (Eqs. pfx2-pfx3 with
+ * phi_mean = 0, the Ewald convention of App. D).  phi is split into
+ *
+ *   phi_near: direct sum over the box and its neighbour images (Eq. 3),
+ *             evaluated at the charges and at 2M check points, and
+ *   phi_far:  C_1 + sum_{t>=2} C_t R_t(y/R0), a regular-solid-harmonic local
+ *             expansion of maximum degree p (Eqs. 1.6-1.8) whose coefficients
+ *             are the least-squares solution of the periodicity conditions at
+ *             M check points on the circumsphere (Eqs. 7-10, algorithms "set"
+ *             and "get" of Sec. 2.3).
+ *
+ * Conventions
+ *   p  is the MAXIMUM DEGREE of the expansion: there are P = (p+1)^2 terms,
+ *      stacked as t = n(n+1) + m (0-based form of Eq. 1.8).  The paper's
+ *      truncation number is p + 1.
+ *   M  is the number of check points (the paper's L).  M >= P - 1 is required
+ *      (Sec. 4.1, rank condition); about 2P to 3P is a good choice.
+ *   All positions, charges and results are float64.  x is row-major N x 3.
+ *
+ * Memory and streams
+ *   Every device pointer is owned by the caller and must stay valid until the
+ *   work queued on `stream` has finished.  `stream` is a cudaStream_t passed
+ *   as void* (NULL = the legacy default stream).  A plan owns its check
+ *   points, its factorisation, the image list and its scratch memory; the
+ *   scratch grows on demand inside psum_eval (a cudaMalloc, which synchronises
+ *   the device) and is then reused, so the first call of a given size should
+ *   not be made inside a stream capture.  A plan may be used by one stream at
+ *   a time.
+ *
+ * Errors
+ *   Every call returns a status code (PSUM_OK = 0).  psum_eval validates its
+ *   arguments on the host and queues the work; conditions only the device can
+ *   see (non-neutral charges, positions outside the box, non-finite results)
+ *   are written to a device status word that psum_sync returns.  After a
+ *   device-side error the outputs are filled with NaN.
+ */
+#ifndef PSUM_H
+#define PSUM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define PSUM_OK              0
+#define PSUM_ERR_ARG         1  /* invalid argument (NULL pointer, p < 1, M < P-1, d <= 0, ...) */
+#define PSUM_ERR_NONNEUTRAL  2  /* |sum q| > 1e-12 sum |q|: Eq. 1 requires a neutral box */
+#define PSUM_ERR_OUT_OF_BOX  3  /* a position outside [-d/2, d/2) or not finite */
+#define PSUM_ERR_RANK        4  /* the fitting matrix A is rank deficient (|R_kk| < 1e-13 |R_11|) */
+#define PSUM_ERR_CUDA        5  /* a CUDA runtime call failed */
+#define PSUM_ERR_TIMEOUT     6  /* a bounded device-side wait gave up */
+#define PSUM_ERR_NOMEM       7  /* host or device allocation failed */
+#define PSUM_ERR_NONFINITE   8  /* a result is not finite (e.g. two charges closer than FP32 resolves) */
+
+/* ---- options ------------------------------------------------------------ */
+#define PSUM_FP64   0  /* near-field pair sum in float64 */
+#define PSUM_FP32C  1  /* pair arithmetic in float32 on tile-relative coordinates,
+                          compensated (two-sum) accumulation, float64 elsewhere */
+
+#define PSUM_MEAN_ZERO 0  /* C_1 makes the box mean of phi zero (Eq. pfx3, phi_mean = 0) */
+#define PSUM_MEAN_NONE 1  /* C_1 = 0 (potential defined up to a constant, Sec. 3) */
+
+typedef struct psum_plan_s *psum_plan_t;
+
+typedef struct psum_opts {
+    double d[3];     /* box edge lengths, > 0 */
+    int p;           /* maximum degree of the local expansion, 1 <= p <= 40 */
+    int M;           /* number of check points, M >= (p+1)^2 - 1 */
+    int precision;   /* PSUM_FP64 or PSUM_FP32C */
+    int mean_mode;   /* PSUM_MEAN_ZERO or PSUM_MEAN_NONE */
+    int K[3];        /* near block: images |i_k| <= K[k] of the box (Eq. 3, Omega_b); 1 = 3x3x3 */
+} psum_opts;
+
+typedef struct psum_info {
+    double d[3];
+    double R0;          /* circumradius (algorithm "set", step 1) */
+    double lambda_eff;  /* distance from the centre to the nearest excluded image box, over R0 */
+    double cond_est;    /* max |R_kk| / min |R_kk| of the pivoted QR of A (a condition estimate) */
+    int rank;           /* numerical rank of A (= P - 1 for a usable plan) */
+    int p, P, M;
+    int K[3];
+    int n_images;       /* (2K1+1)(2K2+1)(2K3+1) */
+    int precision, mean_mode;
+} psum_info;
+
+/* Fill `o` with the defaults: unit cube, p = 8, M = 200, PSUM_FP64,
+   PSUM_MEAN_ZERO, K = (1,1,1). */
+void psum_opts_default(psum_opts *o);
+
+/* Algorithm "set" (Sec. 2.3.1): circumradius R0 (step 1), M check points on the
+ * sphere of radius R0 (step 2; a spherical Fibonacci lattice), their periodic
+ * partners (step 3), the M x (P-1) fitting matrix A_lt = R_t(y_l) - R_t(y~_l)
+ * without the constant column (step 4, Sec. 3), its column-pivoted Householder
+ * QR and pseudo-inverse (step 5, Eq. 10), and the box integrals R_t^(0) by
+ * Gauss-Legendre quadrature (step 6, App. B).  Runs on the host in float64 and
+ * uploads the results to the current CUDA device.
+ * Returns PSUM_ERR_ARG, PSUM_ERR_RANK, PSUM_ERR_NOMEM or PSUM_ERR_CUDA on failure;
+ * *out is set only on success.  psum_plan_create uses FP64 and the defaults. */
+int psum_plan_create(double d1, double d2, double d3, int p, int M, psum_plan_t *out);
+int psum_plan_create_ex(const psum_opts *o, psum_plan_t *out);
+
+/* Algorithm "get" (Sec. 2.3.2) with Y0 = X0 (Remark 1): phi[i] and grad[3i..3i+2]
+ * at every charge.  x (N x 3), q (N), phi (N) and grad (N x 3, may be NULL) are
+ * DEVICE pointers on the plan's device; N >= 1.  Queued on `stream`; returns
+ * after queueing.  Host-side checks give PSUM_ERR_ARG; device-side conditions
+ * are reported by psum_sync. */
+int psum_eval(psum_plan_t plan, int64_t N, const double *x, const double *q,
+              double *phi, double *grad, void *stream);
+
+/* The same with HOST pointers: copies x and q to the device, evaluates, copies
+ * phi and grad back and waits for the stream.  Returns the final status
+ * (including device-side conditions). */
+int psum_eval_host(psum_plan_t plan, int64_t N, const double *x, const double *q,
+                   double *phi, double *grad, void *stream);
+
+/* Wait for `stream`, then return and clear the plan's device status word. */
+int psum_sync(psum_plan_t plan, void *stream);
+
+/* E = 1/2 sum_i q_i phi[i] into the device scalar *E (deterministic reduction).
+ * q and phi are device arrays of length N (phi from psum_eval). */
+int psum_energy(psum_plan_t plan, int64_t N, const double *q, const double *phi, double *E, void *stream);
+
+/* Exact derivatives of the method's energy E = 1/2 sum_i q_i phi(x_i).  The method is
+ * linear in q but its far field is a least-squares fit, so the adjoint of the fit enters:
+ * with w_t = sum_i q_i R_t(x_i/R0) and u = (A^+)^T w,
+ *   psi(x)    = sum_l u_l [G(y~_l - x) - G(y_l - x)]   (G: the near-block image kernel),
+ *   dEdq[i]   = gE (phi_i - phi_far(x_i)/2 + psi(x_i)/2),
+ *   dEdx[3i+k]= gE q_i (grad_i - grad phi_far(x_i)/2 + grad psi(x_i)/2)_k.
+ * x, q, phi, grad (device) must be the inputs and outputs of the LAST psum_eval of this
+ * plan (its coefficients C are used).  gE is a device scalar multiplying the result (the
+ * upstream gradient), or NULL for 1.  dEdq or dEdx may be NULL (not both).  The 27 N^2
+ * pair sum is not repeated: psi is a sum over the 2M check points. */
+int psum_energy_backward(psum_plan_t plan, int64_t N, const double *x, const double *q,
+                         const double *phi, const double *grad, const double *gE,
+                         double *dEdq, double *dEdx, void *stream);
+
+/* Copy the P coefficients C_1..C_P of the last evaluation to host memory
+ * (stacked by Eq. 1.8; C[0] is the constant C_1).  Waits for `stream`. */
+int psum_get_coeffs(psum_plan_t plan, double *C, void *stream);
+
+int psum_plan_info(psum_plan_t plan, psum_info *info);
+
+/* Stage timing.  With profiling enabled, psum_eval records CUDA events on its
+ * stream around each stage; psum_last_timings waits for `stream` and writes the
+ * PSUM_NUM_STAGES durations (milliseconds) of the last evaluation:
+ *   [0] validation, spatial sort and packing
+ *   [1] near-field sum at the charges (potential and gradient)
+ *   [2] near-field sum at the 2M check points (potential)
+ *   [3] reductions, right-hand side, least squares, mean and C_1
+ *   [4] far field, combination and write-back
+ * Returns PSUM_ERR_ARG if profiling is off. */
+#define PSUM_NUM_STAGES 5
+int psum_profile(psum_plan_t plan, int enable);
+int psum_last_timings(psum_plan_t plan, double *ms, void *stream);
+
+/* Number of CUDA kernels this plan has queued since it was created. */
+int psum_launch_count(psum_plan_t plan, int64_t *count);
+
+/* Release the plan and its device memory (waits for the device). NULL is a no-op. */
+void psum_destroy(psum_plan_t plan);
+
+/* Static, NUL-terminated description of a status code. */
+const char *psum_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PSUM_H */

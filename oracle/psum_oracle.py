@@ -377,6 +377,33 @@ class Plan:
         return out
 
 
+def energy_and_gradients(plan: "Plan", x, q, mean: str = "zero"):
+    """E = 1/2 sum_j q_j phi(x_j) of the discrete method and its exact derivatives.
+
+    With phi = phi_near + phi_far, C_{2..P} = A^+ f and f linear in q, the adjoint
+    of the fit gives, for w_t = sum_j q_j R_t(x_j/R0) and u = (A^+)^T w,
+        psi(x) = sum_l u_l [G(y~_l - x) - G(y_l - x)]   (G: the near-block kernel),
+        dE/dq_k = phi_near(x_k) + phi_far(x_k)/2 + psi(x_k)/2,
+        dE/dx_k = q_k [grad phi_near + grad phi_far / 2 + grad psi / 2](x_k).
+    (The C_1 term contributes C_1/2 to dE/dq through sum_j q_j; it vanishes from E.)
+    """
+    x = np.asarray(x, dtype=np.float64).reshape(-1, 3)
+    q = np.asarray(q, dtype=np.float64).reshape(-1)
+    out = plan.evaluate(x, q, mean=mean, parts=True)
+    B = regular_basis(x / plan.R0, plan.p)
+    w = B[1:] @ q                                              # moments, t = 2..P
+    Q, R, piv = plan.factors
+    # A^+ = Pi R^-1 Q^T, so (A^+)^T w = Q R^-T (Pi^T w)
+    u = Q @ scipy.linalg.solve_triangular(R, w[piv], trans="T", lower=False)
+    src = np.concatenate([plan.Yt, plan.Y])
+    c = np.concatenate([u, -u])
+    psi, gpsi = near_sum(x, src, c, plan.d, plan.K, grad=True)
+    E = 0.5 * float(np.dot(q, out["phi"]))
+    dEdq = out["phi_near"] + 0.5 * out["phi_far"] + 0.5 * psi
+    dEdx = q[:, None] * (out["grad_near"] + 0.5 * out["grad_far"] + 0.5 * gpsi)
+    return {"E": E, "dEdq": dEdq, "dEdx": dEdx, "psi": psi, "grad_psi": gpsi, "u": u, "w": w, **out}
+
+
 def periodic_sum(x, q, d, p: int, M: int, targets=None, K=(1, 1, 1), grad: bool = True,
                  mean: str = "zero", parts: bool = False):
     """phi and grad phi of the periodic Coulomb sum at the targets (default: the sources)."""

@@ -1,0 +1,261 @@
+"""Thin Python binding of the C-ABI in ``include/psum.h`` (ctypes).
+
+The functions here carry the C names and only marshal arguments: tensors are
+passed as raw device pointers and the current torch CUDA stream as a
+``cudaStream_t``.  Every step of the computation runs in ``libpsum.so``; if the
+library cannot be built or loaded, ``load()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+from . import build as _build
+
+PSUM_OK = 0
+PSUM_ERR_ARG = 1
+PSUM_ERR_NONNEUTRAL = 2
+PSUM_ERR_OUT_OF_BOX = 3
+PSUM_ERR_RANK = 4
+PSUM_ERR_CUDA = 5
+PSUM_ERR_TIMEOUT = 6
+PSUM_ERR_NOMEM = 7
+PSUM_ERR_NONFINITE = 8
+
+PSUM_FP64 = 0
+PSUM_FP32C = 1
+PSUM_MEAN_ZERO = 0
+PSUM_MEAN_NONE = 1
+PSUM_NUM_STAGES = 5
+STAGE_NAMES = ("prepare", "near_charges", "near_checkpoints", "fit", "far_combine")
+
+PRECISIONS = {"fp64": PSUM_FP64, "fp32c": PSUM_FP32C}
+MEAN_MODES = {"zero": PSUM_MEAN_ZERO, "none": PSUM_MEAN_NONE}
+
+
+class psum_opts(ctypes.Structure):
+    _fields_ = [("d", ctypes.c_double * 3), ("p", ctypes.c_int), ("M", ctypes.c_int),
+                ("precision", ctypes.c_int), ("mean_mode", ctypes.c_int), ("K", ctypes.c_int * 3)]
+
+
+class psum_info(ctypes.Structure):
+    _fields_ = [("d", ctypes.c_double * 3), ("R0", ctypes.c_double), ("lambda_eff", ctypes.c_double),
+                ("cond_est", ctypes.c_double), ("rank", ctypes.c_int), ("p", ctypes.c_int),
+                ("P", ctypes.c_int), ("M", ctypes.c_int), ("K", ctypes.c_int * 3),
+                ("n_images", ctypes.c_int), ("precision", ctypes.c_int), ("mean_mode", ctypes.c_int)]
+
+    def as_dict(self):
+        return {"d": tuple(self.d), "R0": self.R0, "lambda_eff": self.lambda_eff, "cond_est": self.cond_est,
+                "rank": self.rank, "p": self.p, "P": self.P, "M": self.M, "K": tuple(self.K),
+                "n_images": self.n_images, "precision": self.precision, "mean_mode": self.mean_mode}
+
+
+class PsumError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = status
+        super().__init__(f"{what}: {psum_strerror(status)} (status {status})" if what else psum_strerror(status))
+
+
+_lib = None
+_vp = ctypes.c_void_p
+_dp = ctypes.POINTER(ctypes.c_double)
+
+
+def load(build_if_needed: bool = True):
+    """Load libpsum.so (building it first if its sources changed)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = os.environ.get("PSUM_LIB") or (_build.build() if build_if_needed else _build.LIB_PATH)
+    if not os.path.exists(path):
+        raise RuntimeError(f"libpsum.so not found at {path}")
+    lib = ctypes.CDLL(path)
+    lib.psum_opts_default.argtypes = [ctypes.POINTER(psum_opts)]
+    lib.psum_opts_default.restype = None
+    lib.psum_plan_create.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                     ctypes.POINTER(_vp)]
+    lib.psum_plan_create_ex.argtypes = [ctypes.POINTER(psum_opts), ctypes.POINTER(_vp)]
+    lib.psum_eval.argtypes = [_vp, ctypes.c_int64, _vp, _vp, _vp, _vp, _vp]
+    lib.psum_eval_host.argtypes = [_vp, ctypes.c_int64, _vp, _vp, _vp, _vp, _vp]
+    lib.psum_sync.argtypes = [_vp, _vp]
+    lib.psum_get_coeffs.argtypes = [_vp, _dp, _vp]
+    lib.psum_plan_info.argtypes = [_vp, ctypes.POINTER(psum_info)]
+    lib.psum_profile.argtypes = [_vp, ctypes.c_int]
+    lib.psum_last_timings.argtypes = [_vp, _dp, _vp]
+    lib.psum_launch_count.argtypes = [_vp, ctypes.POINTER(ctypes.c_int64)]
+    lib.psum_energy.argtypes = [_vp, ctypes.c_int64, _vp, _vp, _vp, _vp]
+    lib.psum_energy_backward.argtypes = [_vp, ctypes.c_int64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
+    lib.psum_destroy.argtypes = [_vp]
+    lib.psum_destroy.restype = None
+    lib.psum_strerror.argtypes = [ctypes.c_int]
+    lib.psum_strerror.restype = ctypes.c_char_p
+    for name in ("psum_plan_create", "psum_plan_create_ex", "psum_eval", "psum_eval_host", "psum_sync",
+                 "psum_get_coeffs", "psum_plan_info", "psum_profile", "psum_last_timings", "psum_launch_count",
+                 "psum_energy", "psum_energy_backward"):
+        getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def header_functions() -> list:
+    """Names of the functions declared in include/psum.h."""
+    path = os.path.join(_build.INCLUDE, "psum.h")
+    with open(path) as f:
+        text = f.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(psum_[a-z_]+)\s*\(", text)))
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+def _check(status: int, what: str):
+    if status != PSUM_OK:
+        raise PsumError(status, what)
+
+
+def psum_strerror(status: int) -> str:
+    return load().psum_strerror(int(status)).decode()
+
+
+def psum_opts_default() -> psum_opts:
+    o = psum_opts()
+    load().psum_opts_default(ctypes.byref(o))
+    return o
+
+
+def psum_plan_create(d1: float, d2: float, d3: float, p: int, M: int):
+    h = _vp()
+    _check(load().psum_plan_create(float(d1), float(d2), float(d3), int(p), int(M), ctypes.byref(h)),
+           "psum_plan_create")
+    return h
+
+
+def psum_plan_create_ex(d, p: int, M: int, precision="fp64", mean="zero", K=(1, 1, 1)):
+    o = psum_opts_default()
+    for k in range(3):
+        o.d[k] = float(d[k])
+        o.K[k] = int(K[k])
+    o.p, o.M = int(p), int(M)
+    o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    o.mean_mode = MEAN_MODES[mean] if isinstance(mean, str) else int(mean)
+    h = _vp()
+    _check(load().psum_plan_create_ex(ctypes.byref(o), ctypes.byref(h)), "psum_plan_create_ex")
+    return h
+
+
+def psum_eval(plan, x, q, phi, grad=None, stream=None, check: bool = False) -> int:
+    """Queue algorithm "get" on device tensors (float64, contiguous). Returns the launch status."""
+    for t in (x, q, phi) + ((grad,) if grad is not None else ()):
+        if not (t.is_cuda and t.is_contiguous()):
+            raise ValueError("psum_eval takes contiguous CUDA tensors")
+    st = _stream_ptr(stream)
+    s = load().psum_eval(plan, int(q.numel()), x.data_ptr(), q.data_ptr(), phi.data_ptr(),
+                         grad.data_ptr() if grad is not None else None, st)
+    _check(s, "psum_eval")
+    if check:
+        _check(psum_sync(plan, st), "psum_eval (device)")
+    return s
+
+
+def psum_eval_host(plan, x, q, phi, grad=None, stream=None) -> int:
+    """Host arrays (numpy float64, C-contiguous or pinned CPU tensors); copies both ways and waits."""
+    def ptr(a):
+        if a is None:
+            return None
+        if hasattr(a, "data_ptr"):
+            return a.data_ptr()
+        return a.ctypes.data
+    n = int(q.numel() if hasattr(q, "numel") else q.size)
+    s = load().psum_eval_host(plan, n, ptr(x), ptr(q), ptr(phi), ptr(grad), _stream_ptr(stream) if stream is not None else None)
+    return s
+
+
+def psum_sync(plan, stream=None) -> int:
+    return load().psum_sync(plan, _stream_ptr(stream))
+
+
+def psum_get_coeffs(plan, P: int, stream=None):
+    import numpy as np
+    out = np.zeros(P, dtype=np.float64)
+    _check(load().psum_get_coeffs(plan, out.ctypes.data_as(_dp), _stream_ptr(stream)), "psum_get_coeffs")
+    return out
+
+
+def psum_plan_info(plan) -> dict:
+    info = psum_info()
+    _check(load().psum_plan_info(plan, ctypes.byref(info)), "psum_plan_info")
+    return info.as_dict()
+
+
+def psum_profile(plan, enable: bool = True):
+    _check(load().psum_profile(plan, 1 if enable else 0), "psum_profile")
+
+
+def psum_last_timings(plan, stream=None) -> dict:
+    arr = (ctypes.c_double * PSUM_NUM_STAGES)()
+    _check(load().psum_last_timings(plan, arr, _stream_ptr(stream)), "psum_last_timings")
+    return dict(zip(STAGE_NAMES, list(arr)))
+
+
+def psum_energy(plan, q, phi, E, stream=None):
+    """E (a one-element float64 device tensor) = 1/2 sum q phi."""
+    _check(load().psum_energy(plan, int(q.numel()), q.data_ptr(), phi.data_ptr(), E.data_ptr(),
+                              _stream_ptr(stream)), "psum_energy")
+
+
+def psum_energy_backward(plan, x, q, phi, grad, gE=None, dEdq=None, dEdx=None, stream=None):
+    """dE/dq and dE/dx (device tensors) of E = 1/2 q.phi for the last psum_eval of this plan."""
+    def ptr(t):
+        return t.data_ptr() if t is not None else None
+    _check(load().psum_energy_backward(plan, int(q.numel()), x.data_ptr(), q.data_ptr(), phi.data_ptr(),
+                                       grad.data_ptr(), ptr(gE), ptr(dEdq), ptr(dEdx), _stream_ptr(stream)),
+           "psum_energy_backward")
+
+
+def psum_launch_count(plan) -> int:
+    n = ctypes.c_int64()
+    _check(load().psum_launch_count(plan, ctypes.byref(n)), "psum_launch_count")
+    return int(n.value)
+
+
+def psum_destroy(plan):
+    if plan:
+        load().psum_destroy(plan)
+
+
+class PeriodicCoulomb:
+    """A plan plus tensor-returning evaluation (allocation through torch only)."""
+
+    def __init__(self, d, p: int, M: int, precision="fp64", mean="zero", K=(1, 1, 1)):
+        self.plan = psum_plan_create_ex(d, p, M, precision, mean, K)
+        self.info = psum_plan_info(self.plan)
+
+    def __call__(self, x, q, grad: bool = True, stream=None, check: bool = True):
+        import torch
+        N = q.numel()
+        phi = torch.empty(N, dtype=torch.float64, device=x.device)
+        g = torch.empty((N, 3), dtype=torch.float64, device=x.device) if grad else None
+        psum_eval(self.plan, x, q, phi, g, stream=stream, check=check)
+        return phi, g
+
+    def coefficients(self, stream=None):
+        return psum_get_coeffs(self.plan, self.info["P"], stream)
+
+    def close(self):
+        if self.plan:
+            psum_destroy(self.plan)
+            self.plan = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

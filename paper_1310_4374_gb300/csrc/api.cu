@@ -1,0 +1,555 @@
+// C-ABI entry points (include/psum.h) and the device pipeline of algorithm
+// "get" (Sec. 2.3.2), queued on the caller's stream.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "psum_internal.cuh"
+
+namespace psum {
+// near.cu
+cudaError_t launch_near32(bool grad, const float4* src_hi, const float4* src_lo, const double* src_org,
+                          int64_t n_chunks, const float4* tgt_hi, const float4* tgt_lo, const double* tgt_org,
+                          int64_t n_tiles, const double* shifts, int n_img, double* partial,
+                          const NearPlanLaunch& L, cudaStream_t st);
+cudaError_t launch_near64(bool grad, const double4_32a* src, int64_t n_chunks, const double4_32a* tgt, int64_t n_tiles,
+                          const double* shifts, int n_img, double* partial, const NearPlanLaunch& L,
+                          cudaStream_t st);
+cudaError_t launch_near_reduce(const double* partial, int64_t n_valid, int tile_size, int nq,
+                               const NearPlanLaunch& L, double* out_phi, double* out_grad, cudaStream_t st);
+int near32_occupancy_ctas(int n_img);
+int near64_occupancy_ctas();
+// sort.cu
+int sort_blocks(int64_t n);
+cudaError_t launch_morton_sort(const double* x, int64_t n, const double d[3], uint32_t* ka, uint32_t* va,
+                               uint32_t* kb, uint32_t* vb, uint32_t* hist, cudaStream_t st);
+cudaError_t launch_pack32(const double* x, const double* q, const uint32_t* perm, int64_t n, int64_t n_groups,
+                          float4* pk_hi, float4* pk_lo, double* org, cudaStream_t st);
+cudaError_t launch_pack64(const double* x, const double* q, int64_t n, int64_t n_pad, double4_32a* pk, cudaStream_t st);
+// far.cu
+int reduce_blocks(int64_t n, int num_sms);
+cudaError_t launch_validate(const double* x, const double* q, int64_t n, const double d[3], double* partial,
+                            int nblk, int* status, cudaStream_t st);
+cudaError_t launch_box_mean(const double* x, const double* q, int64_t n, const double H[3], double* partial,
+                            int nblk, cudaStream_t st);
+cudaError_t launch_project(const double* pinv, int rows, int M, const double* phi_check, const int* check_pos,
+                           double* f, double* C, cudaStream_t st);
+cudaError_t launch_constant(double* C, const double* Rbox, int P, const double* mean_partial, int nblk,
+                            double inv_V0, int zero_mean, cudaStream_t st);
+cudaError_t launch_far_combine(const double* x, int64_t n, const int* perm, const double* phi_near,
+                               const double* grad_near, const double* C, int p, double inv_R0, const int* status,
+                               double* phi, double* grad, int* status_out, cudaStream_t st);
+// backward.cu
+cudaError_t launch_moments(const double* x, const double* q, int64_t n, const double* C, int p, double inv_R0,
+                           double* far_phi, double* far_grad, double* w_partial, int nblk, double* w,
+                           cudaStream_t st);
+int moments_blocks(int64_t n);
+size_t moments_smem(int p);
+cudaError_t launch_adjoint(const double* pinv, int rows, int M, const double* w, double* u, cudaStream_t st);
+cudaError_t launch_check_sources32(const float4* chk_hi, const int* inv, int64_t n_pts, int M, const double* u,
+                                   float4* out_hi, cudaStream_t st);
+cudaError_t launch_check_sources64(const double4_32a* chk, int64_t n_pts, int M, const double* u,
+                                   double4_32a* out, cudaStream_t st);
+cudaError_t launch_backward_combine(int64_t n, const int* perm, const double* q, const double* phi,
+                                    const double* grad, const double* far_phi, const double* far_grad,
+                                    const double* psi, const double* gpsi, const double* gE, double* dEdq,
+                                    double* dEdx, cudaStream_t st);
+cudaError_t launch_energy(const double* q, const double* phi, int64_t n, double* partial, int nblk, double* E,
+                          cudaStream_t st);
+cudaError_t set_moments_smem(size_t bytes);
+}  // namespace psum
+
+using namespace psum;
+
+struct psum_plan_s {
+    Plan pl;
+    int64_t launches = 0;
+    bool profile = false;
+    cudaEvent_t ev[6] = {};
+};
+
+namespace {
+
+struct Bump {
+    char* base;
+    size_t off = 0;
+    size_t cap;
+    template <class T>
+    T* take(size_t count) {
+        off = (off + 255) & ~(size_t)255;
+        T* p = base ? (T*)(base + off) : nullptr;
+        off += sizeof(T) * std::max<size_t>(count, 1);
+        return p;
+    }
+};
+
+int cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return PSUM_OK;
+    if (e == cudaErrorMemoryAllocation) return PSUM_ERR_NOMEM;
+    return PSUM_ERR_CUDA;
+}
+
+int map_device_status(int s) {
+    if (s & kStatNonNeutral) return PSUM_ERR_NONNEUTRAL;
+    if (s & kStatOutOfBox) return PSUM_ERR_OUT_OF_BOX;
+    if (s & kStatNonFinite) return PSUM_ERR_NONFINITE;
+    if (s & kStatTimeout) return PSUM_ERR_TIMEOUT;
+    return PSUM_OK;
+}
+
+__global__ void k_status_merge(const int* eval_status, int* plan_status) {
+    if (*eval_status) atomicOr(plan_status, *eval_status);
+}
+
+struct Layout {
+    // FP32C
+    uint32_t *ka, *va, *kb, *vb, *hist;
+    float4 *pk32, *pk32lo;
+    double* org;
+    // FP64
+    double4_32a* pk64;
+    // common
+    double *part_n, *part_c, *phi_n, *grad_n, *phi_c, *val_part, *mean_part, *f;
+    int* eval_status;
+    // backward
+    double *far_phi, *far_grad, *w_part, *w, *u, *psi, *gpsi, *part_b;
+    float4* chk_src32;
+    double4_32a* chk_src64;
+    NearPlanLaunch Lb;
+    int nblk_mom;
+    NearPlanLaunch Ln, Lc;
+    int64_t n_tiles, n_chunks, n_pts;
+    int nblk_val, nblk_mean;
+};
+
+// Lay out the scratch buffer for N charges; with base == nullptr only the size is computed.
+// `backward` adds the buffers of the energy derivatives.
+size_t layout(Plan& pl, int64_t N, char* base, Layout& L, bool backward = false) {
+    Bump b{base, 0, 0};
+    const bool fp32 = pl.opt.precision == PSUM_FP32C;
+    const int n_img = pl.n_images;
+    if (fp32) {
+        L.n_tiles = (N + kTile32 - 1) / kTile32;
+        L.n_chunks = (N + kNearChunk - 1) / kNearChunk;
+        const int64_t n_groups = L.n_tiles * kTgt32;
+        L.n_pts = n_groups * kNearChunk;
+        const int64_t gmax = (int64_t)pl.num_sms * near32_occupancy_ctas(n_img);
+        L.Ln = near_partition(L.n_tiles, L.n_chunks, n_img, gmax);
+        L.Lc = near_partition(pl.n_check_tiles, L.n_chunks, n_img, gmax);
+        L.ka = b.take<uint32_t>(N);
+        L.va = b.take<uint32_t>(N);
+        L.kb = b.take<uint32_t>(N);
+        L.vb = b.take<uint32_t>(N);
+        L.hist = b.take<uint32_t>((size_t)256 * sort_blocks(N));
+        L.pk32 = b.take<float4>(2 * (size_t)L.n_pts);
+        L.pk32lo = b.take<float4>(2 * (size_t)L.n_pts);
+        L.org = b.take<double>(4 * (size_t)n_groups);
+        L.pk64 = nullptr;
+        L.part_n = b.take<double>((size_t)L.n_tiles * L.Ln.max_contrib * 4 * kTile32);
+        L.part_c = b.take<double>((size_t)pl.n_check_tiles * L.Lc.max_contrib * kTile32);
+        L.phi_c = b.take<double>((size_t)pl.n_check_tiles * kTile32);
+    } else {
+        L.n_tiles = (N + kTile64 - 1) / kTile64;
+        L.n_chunks = L.n_tiles;
+        L.n_pts = L.n_tiles * kTile64;
+        const int64_t gmax = (int64_t)pl.num_sms * near64_occupancy_ctas();
+        L.Ln = near_partition(L.n_tiles, L.n_chunks, n_img, gmax);
+        L.Lc = near_partition(pl.n_check_tiles, L.n_chunks, n_img, gmax);
+        L.ka = L.va = L.kb = L.vb = L.hist = nullptr;
+        L.pk32 = L.pk32lo = nullptr;
+        L.org = nullptr;
+        L.pk64 = b.take<double4_32a>((size_t)L.n_pts);
+        L.part_n = b.take<double>((size_t)L.n_tiles * L.Ln.max_contrib * 4 * kTile64);
+        L.part_c = b.take<double>((size_t)pl.n_check_tiles * L.Lc.max_contrib * kTile64);
+        L.phi_c = b.take<double>((size_t)pl.n_check_tiles * kTile64);
+    }
+    L.phi_n = b.take<double>((size_t)L.n_pts);
+    L.grad_n = b.take<double>(3 * (size_t)L.n_pts);
+    L.nblk_val = reduce_blocks(N, pl.num_sms);
+    L.nblk_mean = reduce_blocks(N, pl.num_sms);
+    L.val_part = b.take<double>(2 * (size_t)L.nblk_val);
+    L.mean_part = b.take<double>((size_t)L.nblk_mean);
+    L.f = b.take<double>((size_t)pl.opt.M);
+    L.eval_status = b.take<int>(1);
+    L.far_phi = L.far_grad = L.w_part = L.w = L.u = L.psi = L.gpsi = L.part_b = nullptr;
+    L.chk_src32 = nullptr;
+    L.chk_src64 = nullptr;
+    L.nblk_mom = 0;
+    if (backward) {
+        const int n_img = pl.n_images;
+        const int64_t n_chk_chunks = fp32 ? (int64_t)pl.n_check_tiles * kTgt32 : (int64_t)pl.n_check_tiles;
+        const int64_t gmax = (int64_t)pl.num_sms * (fp32 ? near32_occupancy_ctas(n_img) : near64_occupancy_ctas());
+        L.Lb = near_partition(L.n_tiles, n_chk_chunks, n_img, gmax);
+        L.nblk_mom = moments_blocks(N);
+        L.far_phi = b.take<double>((size_t)N);
+        L.far_grad = b.take<double>(3 * (size_t)N);
+        L.w_part = b.take<double>((size_t)L.nblk_mom * pl.P);
+        L.w = b.take<double>((size_t)pl.P);
+        L.u = b.take<double>((size_t)pl.opt.M);
+        L.psi = b.take<double>((size_t)L.n_pts);
+        L.gpsi = b.take<double>(3 * (size_t)L.n_pts);
+        const int tile = fp32 ? kTile32 : kTile64;
+        L.part_b = b.take<double>((size_t)L.n_tiles * L.Lb.max_contrib * 4 * tile);
+        if (fp32)
+            L.chk_src32 = b.take<float4>(2 * (size_t)n_chk_chunks * kNearChunk);
+        else
+            L.chk_src64 = b.take<double4_32a>((size_t)n_chk_chunks * kNearChunk);
+    }
+    return b.off + 256;
+}
+
+class DeviceGuard {
+   public:
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&old_);
+        if (old_ != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (cur != old_) cudaSetDevice(old_);
+    }
+
+   private:
+    int old_ = 0;
+};
+
+#define TRY(expr)                                  \
+    do {                                           \
+        cudaError_t e_ = (expr);                   \
+        if (e_ != cudaSuccess) return cuda_status(e_); \
+    } while (0)
+
+int ensure_scratch(Plan& pl, size_t need) {
+    if (need <= pl.scratch.bytes) return PSUM_OK;
+    cudaFree(pl.scratch.ptr);              // synchronises: no queued kernel still uses the old buffer
+    pl.scratch.ptr = nullptr;
+    pl.scratch.bytes = 0;
+    TRY(cudaMalloc(&pl.scratch.ptr, need));
+    pl.scratch.bytes = need;
+    return PSUM_OK;
+}
+
+int eval_device(psum_plan_s* h, int64_t N, const double* x, const double* q, double* phi, double* grad,
+                cudaStream_t st) {
+    Plan& pl = h->pl;
+    const psum_opts& o = pl.opt;
+    Layout L;
+    int rs = ensure_scratch(pl, layout(pl, N, nullptr, L));
+    if (rs != PSUM_OK) return rs;
+    layout(pl, N, (char*)pl.scratch.ptr, L);
+    const bool fp32 = o.precision == PSUM_FP32C;
+    const int M = o.M, P = pl.P;
+    if (h->profile) TRY(cudaEventRecord(h->ev[0], st));
+    TRY(cudaMemsetAsync(L.eval_status, 0, sizeof(int), st));
+    TRY(launch_validate(x, q, N, o.d, L.val_part, L.nblk_val, L.eval_status, st));
+    h->launches += 2;
+    const int* perm = nullptr;
+    if (fp32) {
+        TRY(launch_morton_sort(x, N, o.d, L.ka, L.va, L.kb, L.vb, L.hist, st));
+        perm = (const int*)L.va;
+        TRY(launch_pack32(x, q, L.va, N, L.n_tiles * kTgt32, L.pk32, L.pk32lo, L.org, st));
+        h->launches += 1 + 4 * 3 + 1;
+    } else {
+        TRY(launch_pack64(x, q, N, L.n_pts, L.pk64, st));
+        h->launches += 1;
+    }
+    if (h->profile) TRY(cudaEventRecord(h->ev[1], st));
+    if (fp32) {
+        TRY(launch_near32(true, L.pk32, L.pk32lo, L.org, L.n_chunks, L.pk32, L.pk32lo, L.org, L.n_tiles,
+                          pl.d_shifts, pl.n_images, L.part_n, L.Ln, st));
+    } else {
+        TRY(launch_near64(true, L.pk64, L.n_chunks, L.pk64, L.n_tiles, pl.d_shifts, pl.n_images, L.part_n, L.Ln, st));
+    }
+    if (h->profile) TRY(cudaEventRecord(h->ev[2], st));
+    if (fp32) {
+        const float4* ct = (const float4*)pl.d_check_tgt;
+        const size_t half = 2 * (size_t)pl.n_check_tiles * kTile32;    // hi parts, then lo parts
+        TRY(launch_near32(false, L.pk32, L.pk32lo, L.org, L.n_chunks, ct, ct + half, pl.d_check_org,
+                          pl.n_check_tiles, pl.d_shifts, pl.n_images, L.part_c, L.Lc, st));
+    } else {
+        TRY(launch_near64(false, L.pk64, L.n_chunks, (const double4_32a*)pl.d_check_tgt, pl.n_check_tiles, pl.d_shifts,
+                          pl.n_images, L.part_c, L.Lc, st));
+    }
+    if (h->profile) TRY(cudaEventRecord(h->ev[3], st));
+    const int tile = fp32 ? kTile32 : kTile64;
+    TRY(launch_near_reduce(L.part_n, N, tile, 4, L.Ln, L.phi_n, L.grad_n, st));
+    TRY(launch_near_reduce(L.part_c, pl.n_check, tile, 1, L.Lc, L.phi_c, nullptr, st));
+    h->launches += 4;   // two near-field kernels, two reductions
+    const bool zero_mean = o.mean_mode == PSUM_MEAN_ZERO;
+    if (zero_mean) {
+        const double H[3] = {0.5 * (2 * o.K[0] + 1) * o.d[0], 0.5 * (2 * o.K[1] + 1) * o.d[1],
+                             0.5 * (2 * o.K[2] + 1) * o.d[2]};
+        TRY(launch_box_mean(x, q, N, H, L.mean_part, L.nblk_mean, st));
+        h->launches += 1;
+    }
+    TRY(launch_project(pl.d_pinv, P - 1, M, L.phi_c, pl.d_check_pos, L.f, pl.d_C, st));
+    TRY(launch_constant(pl.d_C, pl.d_Rbox, P, L.mean_part, L.nblk_mean, 1.0 / (o.d[0] * o.d[1] * o.d[2]),
+                        zero_mean ? 1 : 0, st));
+    if (h->profile) TRY(cudaEventRecord(h->ev[4], st));
+    TRY(launch_far_combine(x, N, perm, L.phi_n, grad ? L.grad_n : nullptr, pl.d_C, o.p, 1.0 / pl.R0,
+                           L.eval_status, phi, grad, L.eval_status, st));
+    k_status_merge<<<1, 1, 0, st>>>(L.eval_status, pl.d_status);
+    TRY(cudaGetLastError());
+    h->launches += 5;   // right-hand side, projection, constant, far field, status merge
+    if (h->profile) TRY(cudaEventRecord(h->ev[5], st));
+    return PSUM_OK;
+}
+
+int backward_device(psum_plan_s* h, int64_t N, const double* x, const double* q, const double* phi,
+                    const double* grad, const double* gE, double* dEdq, double* dEdx, cudaStream_t st) {
+    Plan& pl = h->pl;
+    const psum_opts& o = pl.opt;
+    Layout L;
+    int rs = ensure_scratch(pl, layout(pl, N, nullptr, L, true));
+    if (rs != PSUM_OK) return rs;
+    layout(pl, N, (char*)pl.scratch.ptr, L, true);
+    const bool fp32 = o.precision == PSUM_FP32C;
+    const int M = o.M, P = pl.P;
+    if (moments_smem(o.p) > 48 * 1024) TRY(set_moments_smem(moments_smem(o.p)));
+    const int* perm = nullptr;
+    if (fp32) {
+        TRY(launch_morton_sort(x, N, o.d, L.ka, L.va, L.kb, L.vb, L.hist, st));
+        perm = (const int*)L.va;
+        TRY(launch_pack32(x, q, L.va, N, L.n_tiles * kTgt32, L.pk32, L.pk32lo, L.org, st));
+        h->launches += 1 + 4 * 3 + 1;
+    } else {
+        TRY(launch_pack64(x, q, N, L.n_pts, L.pk64, st));
+        h->launches += 1;
+    }
+    // moments w and the far field at the charges; u = (A^+)^T w
+    TRY(launch_moments(x, q, N, pl.d_C, o.p, 1.0 / pl.R0, L.far_phi, L.far_grad, L.w_part, L.nblk_mom, L.w, st));
+    TRY(launch_adjoint(pl.d_pinv, P - 1, M, L.w, L.u, st));
+    h->launches += 3;
+    // psi and grad psi at the charges: the check points as sources
+    const int tile = fp32 ? kTile32 : kTile64;
+    if (fp32) {
+        const size_t n_chk_pts = (size_t)pl.n_check_tiles * kTile32;
+        const float4* chk = (const float4*)pl.d_check_tgt;
+        TRY(launch_check_sources32(chk, pl.d_check_inv, (int64_t)n_chk_pts, M, L.u, L.chk_src32, st));
+        TRY(launch_near32(true, L.chk_src32, chk + 2 * n_chk_pts, pl.d_check_org, (int64_t)pl.n_check_tiles * kTgt32,
+                          L.pk32, L.pk32lo, L.org, L.n_tiles, pl.d_shifts, pl.n_images, L.part_b, L.Lb, st));
+    } else {
+        const size_t n_chk_pts = (size_t)pl.n_check_tiles * kTile64;
+        TRY(launch_check_sources64((const double4_32a*)pl.d_check_tgt, (int64_t)n_chk_pts, M, L.u, L.chk_src64, st));
+        TRY(launch_near64(true, L.chk_src64, pl.n_check_tiles, L.pk64, L.n_tiles, pl.d_shifts, pl.n_images,
+                          L.part_b, L.Lb, st));
+    }
+    TRY(launch_near_reduce(L.part_b, N, tile, 4, L.Lb, L.psi, L.gpsi, st));
+    TRY(launch_backward_combine(N, perm, q, phi, grad, L.far_phi, L.far_grad, L.psi, L.gpsi, gE, dEdq, dEdx, st));
+    h->launches += 4;
+    return PSUM_OK;
+}
+
+bool valid_opts(const psum_opts* o) {
+    if (!o) return false;
+    for (int k = 0; k < 3; ++k) {
+        if (!(o->d[k] > 0.0) || !std::isfinite(o->d[k])) return false;
+        if (o->K[k] < 0 || o->K[k] > 3) return false;
+    }
+    if (o->p < 1 || o->p > kMaxDegree) return false;
+    const int P = (o->p + 1) * (o->p + 1);
+    if (o->M < P - 1 || o->M > 100000) return false;
+    if (o->precision != PSUM_FP64 && o->precision != PSUM_FP32C) return false;
+    if (o->mean_mode != PSUM_MEAN_ZERO && o->mean_mode != PSUM_MEAN_NONE) return false;
+    return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+void psum_opts_default(psum_opts* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->d[0] = o->d[1] = o->d[2] = 1.0;
+    o->p = 8;
+    o->M = 200;
+    o->precision = PSUM_FP64;
+    o->mean_mode = PSUM_MEAN_ZERO;
+    o->K[0] = o->K[1] = o->K[2] = 1;
+}
+
+int psum_plan_create_ex(const psum_opts* o, psum_plan_t* out) {
+    if (!out || !valid_opts(o)) return PSUM_ERR_ARG;
+    psum_plan_s* h = new (std::nothrow) psum_plan_s();
+    if (!h) return PSUM_ERR_NOMEM;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        delete h;
+        return PSUM_ERR_CUDA;
+    }
+    h->pl.device = dev;
+    cudaDeviceGetAttribute(&h->pl.num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (h->pl.num_sms < 1) h->pl.num_sms = 1;
+    const int st = build_plan(*o, h->pl);
+    if (st != PSUM_OK) {
+        free_plan_device(h->pl);
+        delete h;
+        return st;
+    }
+    for (auto& e : h->ev) cudaEventCreate(&e);
+    *out = h;
+    return PSUM_OK;
+}
+
+int psum_plan_create(double d1, double d2, double d3, int p, int M, psum_plan_t* out) {
+    psum_opts o;
+    psum_opts_default(&o);
+    o.d[0] = d1;
+    o.d[1] = d2;
+    o.d[2] = d3;
+    o.p = p;
+    o.M = M;
+    return psum_plan_create_ex(&o, out);
+}
+
+int psum_eval(psum_plan_t h, int64_t N, const double* x, const double* q, double* phi, double* grad,
+              void* stream) {
+    if (!h || N < 1 || N > (int64_t)1 << 30 || !x || !q || !phi) return PSUM_ERR_ARG;
+    DeviceGuard g(h->pl.device);
+    return eval_device(h, N, x, q, phi, grad, (cudaStream_t)stream);
+}
+
+int psum_sync(psum_plan_t h, void* stream) {
+    if (!h) return PSUM_ERR_ARG;
+    DeviceGuard g(h->pl.device);
+    cudaStream_t st = (cudaStream_t)stream;
+    TRY(cudaMemcpyAsync(h->pl.h_status, h->pl.d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    TRY(cudaMemsetAsync(h->pl.d_status, 0, sizeof(int), st));
+    TRY(cudaStreamSynchronize(st));
+    return map_device_status(*h->pl.h_status);
+}
+
+int psum_eval_host(psum_plan_t h, int64_t N, const double* x, const double* q, double* phi, double* grad,
+                   void* stream) {
+    if (!h || N < 1 || N > (int64_t)1 << 30 || !x || !q || !phi) return PSUM_ERR_ARG;
+    DeviceGuard g(h->pl.device);
+    Plan& pl = h->pl;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t bx = sizeof(double) * 3 * (size_t)N, bq = sizeof(double) * (size_t)N;
+    const size_t need = 2 * bx + 2 * bq + 4 * 256;
+    if (need > pl.dstage.bytes) {
+        cudaFree(pl.dstage.ptr);
+        pl.dstage.ptr = nullptr;
+        pl.dstage.bytes = 0;
+        TRY(cudaMalloc(&pl.dstage.ptr, need));
+        pl.dstage.bytes = need;
+    }
+    Bump b{(char*)pl.dstage.ptr, 0, need};
+    double* dx = b.take<double>(3 * (size_t)N);
+    double* dq = b.take<double>((size_t)N);
+    double* dphi = b.take<double>((size_t)N);
+    double* dgrad = b.take<double>(3 * (size_t)N);
+    TRY(cudaMemcpyAsync(dx, x, bx, cudaMemcpyHostToDevice, st));
+    TRY(cudaMemcpyAsync(dq, q, bq, cudaMemcpyHostToDevice, st));
+    int s = eval_device(h, N, dx, dq, dphi, grad ? dgrad : nullptr, st);
+    if (s != PSUM_OK) return s;
+    TRY(cudaMemcpyAsync(phi, dphi, bq, cudaMemcpyDeviceToHost, st));
+    if (grad) TRY(cudaMemcpyAsync(grad, dgrad, bx, cudaMemcpyDeviceToHost, st));
+    return psum_sync(h, stream);
+}
+
+int psum_energy(psum_plan_t h, int64_t N, const double* q, const double* phi, double* E, void* stream) {
+    if (!h || N < 1 || N > (int64_t)1 << 30 || !q || !phi || !E) return PSUM_ERR_ARG;
+    DeviceGuard g(h->pl.device);
+    Layout L;
+    int rs = ensure_scratch(h->pl, layout(h->pl, N, nullptr, L));
+    if (rs != PSUM_OK) return rs;
+    layout(h->pl, N, (char*)h->pl.scratch.ptr, L);
+    TRY(launch_energy(q, phi, N, L.val_part, L.nblk_val, E, (cudaStream_t)stream));
+    h->launches += 2;
+    return PSUM_OK;
+}
+
+int psum_energy_backward(psum_plan_t h, int64_t N, const double* x, const double* q, const double* phi,
+                         const double* grad, const double* gE, double* dEdq, double* dEdx, void* stream) {
+    if (!h || N < 1 || N > (int64_t)1 << 30 || !x || !q || !phi || !grad || (!dEdq && !dEdx)) return PSUM_ERR_ARG;
+    DeviceGuard g(h->pl.device);
+    return backward_device(h, N, x, q, phi, grad, gE, dEdq, dEdx, (cudaStream_t)stream);
+}
+
+int psum_get_coeffs(psum_plan_t h, double* C, void* stream) {
+    if (!h || !C) return PSUM_ERR_ARG;
+    DeviceGuard g(h->pl.device);
+    cudaStream_t st = (cudaStream_t)stream;
+    TRY(cudaMemcpyAsync(C, h->pl.d_C, sizeof(double) * h->pl.P, cudaMemcpyDeviceToHost, st));
+    TRY(cudaStreamSynchronize(st));
+    return PSUM_OK;
+}
+
+int psum_plan_info(psum_plan_t h, psum_info* info) {
+    if (!h || !info) return PSUM_ERR_ARG;
+    const Plan& pl = h->pl;
+    std::memset(info, 0, sizeof(*info));
+    for (int k = 0; k < 3; ++k) {
+        info->d[k] = pl.opt.d[k];
+        info->K[k] = pl.opt.K[k];
+    }
+    info->R0 = pl.R0;
+    info->lambda_eff = pl.lambda_eff;
+    info->cond_est = pl.cond_est;
+    info->rank = pl.rank;
+    info->p = pl.opt.p;
+    info->P = pl.P;
+    info->M = pl.opt.M;
+    info->n_images = pl.n_images;
+    info->precision = pl.opt.precision;
+    info->mean_mode = pl.opt.mean_mode;
+    return PSUM_OK;
+}
+
+int psum_profile(psum_plan_t h, int enable) {
+    if (!h) return PSUM_ERR_ARG;
+    h->profile = enable != 0;
+    return PSUM_OK;
+}
+
+int psum_last_timings(psum_plan_t h, double* ms, void* stream) {
+    if (!h || !ms) return PSUM_ERR_ARG;
+    if (!h->profile) return PSUM_ERR_ARG;
+    DeviceGuard g(h->pl.device);
+    TRY(cudaStreamSynchronize((cudaStream_t)stream));
+    for (int i = 0; i < PSUM_NUM_STAGES; ++i) {
+        float t = 0.f;
+        TRY(cudaEventElapsedTime(&t, h->ev[i], h->ev[i + 1]));
+        ms[i] = t;
+    }
+    return PSUM_OK;
+}
+
+int psum_launch_count(psum_plan_t h, int64_t* count) {
+    if (!h || !count) return PSUM_ERR_ARG;
+    *count = h->launches;
+    return PSUM_OK;
+}
+
+void psum_destroy(psum_plan_t h) {
+    if (!h) return;
+    {
+        DeviceGuard g(h->pl.device);
+        cudaDeviceSynchronize();
+        for (auto& e : h->ev)
+            if (e) cudaEventDestroy(e);
+        free_plan_device(h->pl);
+    }
+    delete h;
+}
+
+const char* psum_strerror(int s) {
+    switch (s) {
+        case PSUM_OK: return "ok";
+        case PSUM_ERR_ARG: return "invalid argument";
+        case PSUM_ERR_NONNEUTRAL: return "charges do not sum to zero (|sum q| > 1e-12 sum |q|)";
+        case PSUM_ERR_OUT_OF_BOX: return "a position lies outside the box [-d/2, d/2) or is not finite";
+        case PSUM_ERR_RANK: return "the fitting matrix is rank deficient (more check points needed)";
+        case PSUM_ERR_CUDA: return "CUDA runtime error";
+        case PSUM_ERR_TIMEOUT: return "a device-side wait timed out";
+        case PSUM_ERR_NOMEM: return "out of memory";
+        case PSUM_ERR_NONFINITE: return "a result or charge is not finite";
+        default: return "unknown status";
+    }
+}
+
+}  // extern "C"

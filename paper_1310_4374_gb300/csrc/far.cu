@@ -1,0 +1,275 @@
+// Everything in algorithm "get" (Sec. 2.3.2) around the near-field sum:
+//   validation (Eq. 1: neutral box, positions inside it),
+//   the right-hand side f and the least-squares coefficients (steps 4-5, Eqs. 8-10),
+//   the constant C_1 from the zero-mean condition (step 6, Eqs. pfx3-pfx4, App. C),
+//   the far field and its gradient at the charges and the final sum (steps 7-8,
+//   Eqs. 1.6-1.9).
+// All of it runs in float64.
+#include "psum_internal.cuh"
+
+namespace psum {
+
+// ---------------------------------------------------------------------------
+// block reduction of two doubles (fixed order for a fixed block size)
+// ---------------------------------------------------------------------------
+template <int BS>
+__device__ __forceinline__ void block_sum2(double& a, double& b) {
+    __shared__ double sa[BS / 32], sb[BS / 32];
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        b += __shfl_down_sync(0xffffffffu, b, o);
+    }
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) { sa[w] = a; sb[w] = b; }
+    __syncthreads();
+    if (w == 0) {
+        a = l < BS / 32 ? sa[l] : 0.0;
+        b = l < BS / 32 ? sb[l] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) {
+            a += __shfl_down_sync(0xffffffffu, a, o);
+            b += __shfl_down_sync(0xffffffffu, b, o);
+        }
+    }
+}
+
+constexpr int kRedThreads = 256;
+
+// Eq. 1: charges must sum to zero; positions must lie in [-d/2, d/2).
+__global__ void __launch_bounds__(kRedThreads) k_validate(const double* __restrict__ x, const double* __restrict__ q,
+                                                          int64_t n, double d0, double d1, double d2,
+                                                          double* __restrict__ partial, int* __restrict__ status) {
+    double s = 0.0, sa = 0.0;
+    int bad = 0;
+    for (int64_t i = (int64_t)blockIdx.x * kRedThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kRedThreads) {
+        const double a = x[3 * i], b = x[3 * i + 1], c = x[3 * i + 2], qi = q[i];
+        const bool in = (a >= -0.5 * d0) && (a < 0.5 * d0) && (b >= -0.5 * d1) && (b < 0.5 * d1) &&
+                        (c >= -0.5 * d2) && (c < 0.5 * d2);
+        if (!in) bad |= kStatOutOfBox;           // also catches NaN positions
+        if (!(fabs(qi) <= 1.7976931348623157e308)) bad |= kStatNonFinite;
+        s += qi;
+        sa += fabs(qi);
+    }
+    if (bad) atomicOr(status, bad);
+    block_sum2<kRedThreads>(s, sa);
+    if (threadIdx.x == 0) {
+        partial[2 * blockIdx.x] = s;
+        partial[2 * blockIdx.x + 1] = sa;
+    }
+}
+
+__global__ void k_validate_finish(const double* __restrict__ partial, int nblk, int* __restrict__ status) {
+    double s = 0.0, sa = 0.0;
+    for (int b = threadIdx.x; b < nblk; b += 32) { s += partial[2 * b]; sa += partial[2 * b + 1]; }
+    for (int o = 16; o > 0; o >>= 1) {
+        s += __shfl_down_sync(0xffffffffu, s, o);
+        sa += __shfl_down_sync(0xffffffffu, sa, o);
+    }
+    if (threadIdx.x == 0 && !(fabs(s) <= 1e-12 * sa)) atomicOr(status, kStatNonNeutral);
+}
+
+// ---------------------------------------------------------------------------
+// Mean of phi_near over the box (Eq. pfx4).  The near block is the union of the
+// box images, so sum_p Phi_0(x + p) = U(x) / V0 with U(x) = int_B dV(y)/|y - x|
+// over the block B = [-H0,H0] x [-H1,H1] x [-H2,H2].  U is reduced to the faces
+// by the divergence theorem (Eqs. B1-B2), each face integral to its four edges
+// by the divergence theorem in the plane (Eqs. B3-B5), and each edge integral
+// has the primitive (Eqs. B7-B9, in the form derived below)
+//   G(t; z, h) = z ln(t + rho) + h atan(h t / (z rho)) - h atan(t / z),
+//   rho = sqrt(t^2 + z^2 + h^2),
+// where h is the distance from x to the face plane, z the signed distance of
+// the projected point to the edge line (positive inside the face) and t runs
+// along the edge from the foot of the perpendicular.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double edge_primitive(double t, double z, double h) {
+    const double rho = sqrt(t * t + z * z + h * h);
+    const double lg = t >= 0.0 ? log(t + rho) : log((z * z + h * h) / (rho - t));
+    return z * lg + h * atan(h * t / (z * rho)) - h * atan(t / z);
+}
+
+__device__ __forceinline__ double edge_integral(double z, double h, double t0, double t1) {
+    if (z == 0.0) return 0.0;     // the point projects onto the edge line: the integrand vanishes
+    return edge_primitive(t1, z, h) - edge_primitive(t0, z, h);
+}
+
+__device__ double block_potential(const double X[3], const double H[3]) {
+    double U = 0.0;
+    for (int k = 0; k < 3; ++k) {
+        const int k1 = (k + 1) % 3, k2 = (k + 2) % 3;
+        const double a = X[k1], b = X[k2];
+        // face integral L = sum over its four edges (independent of the face's side)
+        const double h_lo = fabs(H[k] + X[k]), h_hi = fabs(H[k] - X[k]);
+        for (int side = 0; side < 2; ++side) {
+            const double s = side ? (H[k] - X[k]) : (H[k] + X[k]);     // n . (y - x) on the face
+            const double h = side ? h_hi : h_lo;
+            if (s == 0.0) continue;
+            double L = 0.0;
+            L += edge_integral(H[k1] - a, h, -H[k2] - b, H[k2] - b);
+            L += edge_integral(H[k1] + a, h, -H[k2] - b, H[k2] - b);
+            L += edge_integral(H[k2] - b, h, -H[k1] - a, H[k1] - a);
+            L += edge_integral(H[k2] + b, h, -H[k1] - a, H[k1] - a);
+            U += 0.5 * s * L;
+        }
+    }
+    return U;
+}
+
+__global__ void __launch_bounds__(kRedThreads) k_box_mean(const double* __restrict__ x, const double* __restrict__ q,
+                                                          int64_t n, double H0, double H1, double H2,
+                                                          double* __restrict__ partial) {
+    const double H[3] = {H0, H1, H2};
+    double s = 0.0, dummy = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * kRedThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kRedThreads) {
+        const double X[3] = {x[3 * i], x[3 * i + 1], x[3 * i + 2]};
+        s += q[i] * block_potential(X, H);
+    }
+    block_sum2<kRedThreads>(s, dummy);
+    if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+// ---------------------------------------------------------------------------
+// Steps 4-5: f_l = phi_near(y~_l) - phi_near(y_l), C_{2..P} = A^+ f.
+// One warp per row of the (P-1) x M pseudo-inverse.
+// ---------------------------------------------------------------------------
+constexpr int kProjThreads = 256;
+
+__global__ void k_rhs(const double* __restrict__ phi_check, const int* __restrict__ check_pos, int M,
+                      double* __restrict__ f) {
+    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l < M) f[l] = phi_check[check_pos[M + l]] - phi_check[check_pos[l]];
+}
+
+__global__ void __launch_bounds__(kProjThreads) k_project(const double* __restrict__ pinv, int rows, int M,
+                                                          const double* __restrict__ f, double* __restrict__ C) {
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int row = blockIdx.x * (kProjThreads / 32) + w;
+    if (row >= rows) return;
+    const double* a = pinv + (int64_t)row * M;
+    double s = 0.0;
+    for (int l = lane; l < M; l += 32) s = fma(a[l], f[l], s);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) C[1 + row] = s;
+}
+
+// Step 6 (Eq. pfx3 with phi_mean = 0): C_1 = -<phi_near> - sum_{t>=2} C_t R_t^(0).
+__global__ void k_constant(double* __restrict__ C, const double* __restrict__ Rbox, int P,
+                           const double* __restrict__ mean_partial, int nblk, double inv_V0, int zero_mean) {
+    double s = 0.0, m = 0.0;
+    if (zero_mean) {
+        for (int t = 1 + threadIdx.x; t < P; t += 32) s = fma(C[t], Rbox[t], s);
+        for (int b = threadIdx.x; b < nblk; b += 32) m += mean_partial[b];
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        s += __shfl_down_sync(0xffffffffu, s, o);
+        m += __shfl_down_sync(0xffffffffu, m, o);
+    }
+    if (threadIdx.x == 0) C[0] = zero_mean ? (-m * inv_V0 - s) : 0.0;
+}
+
+// ---------------------------------------------------------------------------
+// Steps 7-8: phi = phi_near + C_1 + sum_t C_t R_t(x/R0), grad likewise
+// (the gradient of the expansion by differentiating the recurrence), written
+// back to the caller's order.
+// ---------------------------------------------------------------------------
+constexpr int kFarThreads = 128;
+
+__global__ void __launch_bounds__(kFarThreads) k_far_combine(const double* __restrict__ x, int64_t n,
+                                                             const int* __restrict__ perm,
+                                                             const double* __restrict__ phi_near,
+                                                             const double* __restrict__ grad_near,
+                                                             const double* __restrict__ C, int p, double inv_R0,
+                                                             const int* __restrict__ status,
+                                                             double* __restrict__ phi, double* __restrict__ grad,
+                                                             int* __restrict__ status_out) {
+    extern __shared__ double s_C[];
+    const int P = (p + 1) * (p + 1);
+    for (int t = threadIdx.x; t < P; t += kFarThreads) s_C[t] = C[t];
+    __syncthreads();
+    const int64_t s = (int64_t)blockIdx.x * kFarThreads + threadIdx.x;
+    if (s >= n) return;
+    const int64_t i = perm ? (int64_t)perm[s] : s;
+    const bool failed = (*status & (kStatNonNeutral | kStatOutOfBox | kStatNonFinite)) != 0;
+    if (failed) {
+        phi[i] = __longlong_as_double(0x7ff8000000000000ll);
+        if (grad) grad[3 * i] = grad[3 * i + 1] = grad[3 * i + 2] = __longlong_as_double(0x7ff8000000000000ll);
+        return;
+    }
+    const double ux = x[3 * i] * inv_R0, uy = x[3 * i + 1] * inv_R0, uz = x[3 * i + 2] * inv_R0;
+    double f = 0.0, gx = 0.0, gy = 0.0, gz = 0.0;
+    if (grad) {
+        sh_visit<true>(ux, uy, uz, p, [&](int nn, int mm, double v, double vx, double vy, double vz) {
+            const double c = s_C[sh_index(nn, mm)];
+            f = fma(c, v, f);
+            gx = fma(c, vx, gx);
+            gy = fma(c, vy, gy);
+            gz = fma(c, vz, gz);
+        });
+    } else {
+        sh_visit<false>(ux, uy, uz, p, [&](int nn, int mm, double v, double, double, double) {
+            f = fma(s_C[sh_index(nn, mm)], v, f);
+        });
+    }
+    // the t = 1 term of the sum is C_1 R^_0^0 = C_1: included by the visitor
+    const double ph = phi_near[s] + f;
+    phi[i] = ph;
+    bool finite = fabs(ph) <= 1.7976931348623157e308;
+    if (grad) {
+        const double g0 = grad_near[3 * s] + gx * inv_R0;
+        const double g1 = grad_near[3 * s + 1] + gy * inv_R0;
+        const double g2 = grad_near[3 * s + 2] + gz * inv_R0;
+        grad[3 * i] = g0;
+        grad[3 * i + 1] = g1;
+        grad[3 * i + 2] = g2;
+        finite = finite && fabs(g0) <= 1.7976931348623157e308 && fabs(g1) <= 1.7976931348623157e308 &&
+                 fabs(g2) <= 1.7976931348623157e308;
+    }
+    if (!finite) atomicOr(status_out, kStatNonFinite);
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+int reduce_blocks(int64_t n, int num_sms) {
+    int64_t nb = (n + kRedThreads - 1) / kRedThreads;
+    const int64_t cap = 4LL * num_sms;
+    if (nb > cap) nb = cap;
+    return nb < 1 ? 1 : (int)nb;
+}
+
+cudaError_t launch_validate(const double* x, const double* q, int64_t n, const double d[3], double* partial,
+                            int nblk, int* status, cudaStream_t st) {
+    k_validate<<<nblk, kRedThreads, 0, st>>>(x, q, n, d[0], d[1], d[2], partial, status);
+    k_validate_finish<<<1, 32, 0, st>>>(partial, nblk, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_box_mean(const double* x, const double* q, int64_t n, const double H[3], double* partial,
+                            int nblk, cudaStream_t st) {
+    k_box_mean<<<nblk, kRedThreads, 0, st>>>(x, q, n, H[0], H[1], H[2], partial);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_project(const double* pinv, int rows, int M, const double* phi_check, const int* check_pos,
+                           double* f, double* C, cudaStream_t st) {
+    k_rhs<<<(M + 255) / 256, 256, 0, st>>>(phi_check, check_pos, M, f);
+    const int per = kProjThreads / 32;
+    k_project<<<(rows + per - 1) / per, kProjThreads, 0, st>>>(pinv, rows, M, f, C);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_constant(double* C, const double* Rbox, int P, const double* mean_partial, int nblk,
+                            double inv_V0, int zero_mean, cudaStream_t st) {
+    k_constant<<<1, 32, 0, st>>>(C, Rbox, P, mean_partial, nblk, inv_V0, zero_mean);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_far_combine(const double* x, int64_t n, const int* perm, const double* phi_near,
+                               const double* grad_near, const double* C, int p, double inv_R0, const int* status,
+                               double* phi, double* grad, int* status_out, cudaStream_t st) {
+    const int P = (p + 1) * (p + 1);
+    const unsigned nb = (unsigned)((n + kFarThreads - 1) / kFarThreads);
+    k_far_combine<<<nb, kFarThreads, sizeof(double) * P, st>>>(x, n, perm, phi_near, grad_near, C, p, inv_R0,
+                                                               status, phi, grad, status_out);
+    return cudaGetLastError();
+}
+
+}  // namespace psum

@@ -1,0 +1,460 @@
+// Near-field direct image sum (Sec. 2.1, Eq. 3; algorithm "get", steps 1 and 3):
+//
+//   phi_near(y)      = sum_{p in images} sum_i q_i / |y - x_i - p|       (K(0) = 0, Eq. 1)
+//   grad phi_near(y) = sum_{p} sum_i q_i (x_i + p - y) / |y - x_i - p|^3
+//
+// at the N charges (potential and gradient) and at the 2M check points
+// (potential only).  Two kernels share one work decomposition:
+//
+//   * the work unit is (target tile, source chunk, image); the unit space is
+//     split into G contiguous ranges, one per CTA (a stream-K partition), so
+//     every CTA does the same number of units whatever N is;
+//   * a CTA stages a source chunk in shared memory once and applies every
+//     image to it; the image shift is folded into the targets in registers;
+//   * a CTA writes its per-tile partial sums to a slot of a partial buffer,
+//     and a reduction kernel adds the slots in a fixed order.
+//
+// FP32C: coordinates are float32 offsets from a float64 origin per group of
+// 128 consecutive (Morton-sorted) points; the offset between a target group and
+// a source chunk, minus the image vector, is formed in float64 and rounded once,
+// so close pairs keep their relative precision.  Pair arithmetic uses packed
+// f32x2 instructions on two targets at a time and MUFU rsqrt; per-unit float32
+// partial sums are folded into a float32 (hi, lo) pair by Knuth's two-sum.
+//
+// FP64: absolute float64 coordinates; 1/sqrt(r^2) is a float32 MUFU estimate
+// refined by two Newton-Raphson steps y <- y (3 - r^2 y^2)/2 in float64.
+#include "psum_internal.cuh"
+
+namespace psum {
+
+constexpr int kGroup = kNearChunk;             // points per origin group (= chunk size)
+constexpr int kGroupsPerTile32 = kTile32 / kGroup;  // 4
+static_assert(kThreads32 == kGroup, "one target per thread per group");
+static_assert(kGroupsPerTile32 == kTgt32, "targets per thread = groups per tile");
+static_assert(kTile64 == kNearChunk, "FP64 tile = one chunk");
+
+// A unit is "near" when the distance between the target-group origin and the shifted
+// chunk origin is at most kNearFactor times the sum of the two group radii.  Near units
+// form the pair offsets from float-float (hi + lo) coordinates and honour K(0) = 0;
+// far units cannot hold a pair closer than (kNearFactor - 1)(R_T + R_S), where the
+// float32 offsets from the two origins are accurate to a few float32 ulps of the pair
+// distance.
+constexpr double kNearFactor = 1.5;
+
+__device__ __forceinline__ float rsqrt_mufu(float x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Knuth's two-sum: s + err = a + b exactly.
+__device__ __forceinline__ float two_sum(float a, float b, float& err) {
+    const float s = a + b;
+    const float bp = s - a;
+    err = (a - (s - bp)) + (b - bp);
+    return s;
+}
+
+struct Near32Args {
+    const float4* src_hi;    // 2 float4 per source: (x,x,y,y),(z,z,q,q), offsets from the chunk origin
+    const float4* src_lo;    // 2 float4 per source: (xl,xl,yl,yl),(zl,zl,0,0), the float32 rounding remainders
+    const double* src_org;   // 4 per chunk: origin x, y, z and radius
+    const float4* tgt_hi;    // same layouts for the targets (q unused)
+    const float4* tgt_lo;
+    const double* tgt_org;   // 4 per target group (kGroupsPerTile32 groups per tile)
+    const double* shifts;    // n_img x 3 image vectors
+    double* partial;         // [n_tiles][max_contrib][4 or 1][kTile32]
+    int64_t n_tiles, n_chunks, U, G;
+    int n_img, max_contrib;
+};
+
+// Far units: one chunk of sources against the thread's 4 targets (2 packed pairs),
+// plain float32 offsets s - t'.
+template <bool kGrad>
+__device__ __forceinline__ void pair_loop_far(const float4* __restrict__ s_hi, const float2 (&nx)[2],
+                                              const float2 (&ny)[2], const float2 (&nz)[2], float2 (&aphi)[2],
+                                              float2 (&agx)[2], float2 (&agy)[2], float2 (&agz)[2]) {
+#pragma unroll 2
+    for (int s = 0; s < kNearChunk; ++s) {
+        const float4 A = s_hi[2 * s];       // x x y y
+        const float4 B = s_hi[2 * s + 1];   // z z q q
+        const float2 sq = make_float2(B.z, B.w);
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const float2 ex = __fadd2_rn(make_float2(A.x, A.y), nx[j]);
+            const float2 ey = __fadd2_rn(make_float2(A.z, A.w), ny[j]);
+            const float2 ez = __fadd2_rn(make_float2(B.x, B.y), nz[j]);
+            float2 r2 = __fmul2_rn(ex, ex);
+            r2 = __ffma2_rn(ey, ey, r2);
+            r2 = __ffma2_rn(ez, ez, r2);
+            const float2 ri = make_float2(rsqrt_mufu(r2.x), rsqrt_mufu(r2.y));
+            const float2 qr = __fmul2_rn(sq, ri);
+            aphi[j] = __fadd2_rn(aphi[j], qr);
+            if (kGrad) {
+                const float2 w = __fmul2_rn(qr, __fmul2_rn(ri, ri));
+                agx[j] = __ffma2_rn(ex, w, agx[j]);
+                agy[j] = __ffma2_rn(ey, w, agy[j]);
+                agz[j] = __ffma2_rn(ez, w, agz[j]);
+            }
+        }
+    }
+}
+
+// Near units: one packed target pair at a time, offsets from hi + lo coordinates,
+// K(0) = 0 applied.
+template <bool kGrad>
+__device__ __forceinline__ void pair_loop_near(const float4* __restrict__ s_hi, const float4* __restrict__ s_lo,
+                                               float2 nhx, float2 nhy, float2 nhz, float2 nlx, float2 nly,
+                                               float2 nlz, float2& aphi, float2& agx, float2& agy, float2& agz) {
+#pragma unroll 2
+    for (int s = 0; s < kNearChunk; ++s) {
+        const float4 A = s_hi[2 * s];
+        const float4 B = s_hi[2 * s + 1];
+        const float4 C = s_lo[2 * s];
+        const float4 D = s_lo[2 * s + 1];
+        const float2 ex = __fadd2_rn(__fadd2_rn(make_float2(A.x, A.y), nhx), __fadd2_rn(make_float2(C.x, C.y), nlx));
+        const float2 ey = __fadd2_rn(__fadd2_rn(make_float2(A.z, A.w), nhy), __fadd2_rn(make_float2(C.z, C.w), nly));
+        const float2 ez = __fadd2_rn(__fadd2_rn(make_float2(B.x, B.y), nhz), __fadd2_rn(make_float2(D.x, D.y), nlz));
+        float2 r2 = __fmul2_rn(ex, ex);
+        r2 = __ffma2_rn(ey, ey, r2);
+        r2 = __ffma2_rn(ez, ez, r2);
+        float2 ri = make_float2(rsqrt_mufu(r2.x), rsqrt_mufu(r2.y));
+        ri.x = r2.x > 0.f ? ri.x : 0.f;                   // K(0) = 0 (Eq. 1)
+        ri.y = r2.y > 0.f ? ri.y : 0.f;
+        const float2 qr = __fmul2_rn(make_float2(B.z, B.w), ri);
+        aphi = __fadd2_rn(aphi, qr);
+        if (kGrad) {
+            const float2 w = __fmul2_rn(qr, __fmul2_rn(ri, ri));
+            agx = __ffma2_rn(ex, w, agx);
+            agy = __ffma2_rn(ey, w, agy);
+            agz = __ffma2_rn(ez, w, agz);
+        }
+    }
+}
+
+// (hi, lo) += v for a packed pair of accumulators: Knuth's two-sum with the error
+// carried in lo.
+__device__ __forceinline__ void two_sum_acc2(float2& hi, float2& lo, float2 v) {
+    const float2 m1 = make_float2(-1.f, -1.f);
+    const float2 s = __fadd2_rn(hi, v);
+    const float2 bp = __ffma2_rn(m1, hi, s);              // s - hi
+    const float2 t1 = __ffma2_rn(m1, bp, s);              // s - bp
+    const float2 e1 = __ffma2_rn(m1, t1, hi);             // hi - (s - bp)
+    const float2 e2 = __ffma2_rn(m1, bp, v);              // v - bp
+    lo = __fadd2_rn(lo, __fadd2_rn(e1, e2));
+    hi = s;
+}
+
+#ifndef PSUM_NEAR32_MIN_BLOCKS
+#define PSUM_NEAR32_MIN_BLOCKS 6
+#endif
+template <bool kGrad>
+__global__ void __launch_bounds__(kThreads32, PSUM_NEAR32_MIN_BLOCKS) k_near32(Near32Args a) {
+    constexpr int NQ = kGrad ? 4 : 1;
+    __shared__ float4 s_hi[2 * kNearChunk];
+    __shared__ float4 s_lo[2 * kNearChunk];
+    __shared__ float2 s_th[3][2][kThreads32];             // target hi offsets, [coord][pair]
+    __shared__ float2 s_acc[NQ][2][2][kThreads32];        // [quantity][pair][hi, lo]
+    extern __shared__ float s_dyn[];                      // [n_img][kTgt32][6] deltas, then [n_img] flags
+    float* s_delta = s_dyn;
+    int* s_near = (int*)(s_dyn + 6 * kTgt32 * a.n_img);
+
+    const int tid = threadIdx.x;
+    const int64_t g = blockIdx.x;
+    int64_t u = sk_bound(g, a.U, a.G);
+    const int64_t u_end = sk_bound(g + 1, a.U, a.G);
+    const int64_t upt = a.n_chunks * a.n_img;
+    int64_t cur_tile = -1, cur_chunk = -1;
+
+    auto flush = [&](int64_t tile) {
+        const int64_t slot = g - sk_owner(tile * upt, a.U, a.G);
+        double* dst = a.partial + ((tile * a.max_contrib + slot) * NQ) * kTile32;
+#pragma unroll
+        for (int qi = 0; qi < NQ; ++qi)
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const float2 h = s_acc[qi][j][0][tid], l = s_acc[qi][j][1][tid];
+                dst[qi * kTile32 + (2 * j) * kThreads32 + tid] = (double)h.x + (double)l.x;
+                dst[qi * kTile32 + (2 * j + 1) * kThreads32 + tid] = (double)h.y + (double)l.y;
+            }
+    };
+
+    while (u < u_end) {
+        const int64_t tile = u / upt;
+        const int64_t rem = u - tile * upt;
+        const int64_t chunk = rem / a.n_img;
+        const int img = (int)(rem - chunk * a.n_img);
+        if (tile != cur_tile) {
+            if (cur_tile >= 0) flush(cur_tile);
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const int64_t i0 = (tile * kTgt32 + 2 * j) * kGroup + tid;
+                const int64_t i1 = i0 + kGroup;
+                const float4 A0 = a.tgt_hi[2 * i0], B0 = a.tgt_hi[2 * i0 + 1];
+                const float4 A1 = a.tgt_hi[2 * i1], B1 = a.tgt_hi[2 * i1 + 1];
+                s_th[0][j][tid] = make_float2(A0.x, A1.x);
+                s_th[1][j][tid] = make_float2(A0.z, A1.z);
+                s_th[2][j][tid] = make_float2(B0.x, B1.x);
+#pragma unroll
+                for (int qi = 0; qi < NQ; ++qi) {
+                    s_acc[qi][j][0][tid] = make_float2(0.f, 0.f);
+                    s_acc[qi][j][1][tid] = make_float2(0.f, 0.f);
+                }
+            }
+            cur_tile = tile;
+            cur_chunk = -1;
+        }
+        if (chunk != cur_chunk) {
+            __syncthreads();   // every thread is done with the previous chunk, deltas and flags
+            const float4* hsrc = a.src_hi + chunk * (2 * kNearChunk);
+            const float4* lsrc = a.src_lo + chunk * (2 * kNearChunk);
+            for (int i = tid; i < 2 * kNearChunk; i += kThreads32) { s_hi[i] = hsrc[i]; s_lo[i] = lsrc[i]; }
+            const double* so = a.src_org + 4 * chunk;
+            for (int im = tid; im < a.n_img; im += kThreads32) {
+                const double* sh = a.shifts + 3 * im;
+                int nr = 0;
+                for (int k = 0; k < kTgt32; ++k) {
+                    const double* to = a.tgt_org + 4 * (cur_tile * kTgt32 + k);
+                    // offset of the target-group origin from the shifted chunk origin, as hi + lo
+                    const double D0 = (to[0] - so[0]) - sh[0], D1 = (to[1] - so[1]) - sh[1], D2 = (to[2] - so[2]) - sh[2];
+                    float* dl = s_delta + 6 * (im * kTgt32 + k);
+                    dl[0] = (float)D0; dl[1] = (float)D1; dl[2] = (float)D2;
+                    dl[3] = (float)(D0 - (double)dl[0]); dl[4] = (float)(D1 - (double)dl[1]);
+                    dl[5] = (float)(D2 - (double)dl[2]);
+                    const double reach = kNearFactor * (to[3] + so[3]);
+                    if (D0 * D0 + D1 * D1 + D2 * D2 <= reach * reach) nr = 1;
+                }
+                s_near[im] = nr;
+            }
+            __syncthreads();
+            cur_chunk = chunk;
+        }
+        const float* dl = s_delta + 6 * (img * kTgt32);
+        if (s_near[img] != 0) {
+            // t' = t + delta in float-float: hi by rounding, lo = exact remainder + both lo parts
+#pragma unroll 1
+            for (int j = 0; j < 2; ++j) {
+                const float* d0 = dl + 6 * (2 * j);
+                const float* d1 = dl + 6 * (2 * j + 1);
+                // target lo parts are read from global memory: near units are rare
+                const int64_t i0 = (cur_tile * kTgt32 + 2 * j) * kGroup + tid;
+                const int64_t i1 = i0 + kGroup;
+                const float4 C0 = a.tgt_lo[2 * i0], D0 = a.tgt_lo[2 * i0 + 1];
+                const float4 C1 = a.tgt_lo[2 * i1], D1 = a.tgt_lo[2 * i1 + 1];
+                const float2 tls[3] = {make_float2(C0.x, C1.x), make_float2(C0.z, C1.z), make_float2(D0.x, D1.x)};
+                float2 nh[3], nl[3];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const float2 th = s_th[c][j][tid], tl = tls[c];
+                    float e0, e1;
+                    const float h0 = two_sum(th.x, d0[c], e0);
+                    const float h1 = two_sum(th.y, d1[c], e1);
+                    nh[c] = make_float2(-h0, -h1);
+                    nl[c] = make_float2(-(e0 + (tl.x + d0[3 + c])), -(e1 + (tl.y + d1[3 + c])));
+                }
+                float2 aphi = make_float2(0.f, 0.f), agx = aphi, agy = aphi, agz = aphi;
+                pair_loop_near<kGrad>(s_hi, s_lo, nh[0], nh[1], nh[2], nl[0], nl[1], nl[2], aphi, agx, agy, agz);
+                two_sum_acc2(s_acc[0][j][0][tid], s_acc[0][j][1][tid], aphi);
+                if (kGrad) {
+                    two_sum_acc2(s_acc[1 % NQ][j][0][tid], s_acc[1 % NQ][j][1][tid], agx);
+                    two_sum_acc2(s_acc[2 % NQ][j][0][tid], s_acc[2 % NQ][j][1][tid], agy);
+                    two_sum_acc2(s_acc[3 % NQ][j][0][tid], s_acc[3 % NQ][j][1][tid], agz);
+                }
+            }
+        } else {
+            float2 nx[2], ny[2], nz[2];
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const float* d0 = dl + 6 * (2 * j);
+                const float* d1 = dl + 6 * (2 * j + 1);
+                const float2 tx = s_th[0][j][tid], ty = s_th[1][j][tid], tz = s_th[2][j][tid];
+                nx[j] = make_float2(-(tx.x + d0[0]), -(tx.y + d1[0]));
+                ny[j] = make_float2(-(ty.x + d0[1]), -(ty.y + d1[1]));
+                nz[j] = make_float2(-(tz.x + d0[2]), -(tz.y + d1[2]));
+            }
+            float2 aphi[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+            float2 agx[2] = {aphi[0], aphi[0]}, agy[2] = {aphi[0], aphi[0]}, agz[2] = {aphi[0], aphi[0]};
+            pair_loop_far<kGrad>(s_hi, nx, ny, nz, aphi, agx, agy, agz);
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                two_sum_acc2(s_acc[0][j][0][tid], s_acc[0][j][1][tid], aphi[j]);
+                if (kGrad) {
+                    two_sum_acc2(s_acc[1 % NQ][j][0][tid], s_acc[1 % NQ][j][1][tid], agx[j]);
+                    two_sum_acc2(s_acc[2 % NQ][j][0][tid], s_acc[2 % NQ][j][1][tid], agy[j]);
+                    two_sum_acc2(s_acc[3 % NQ][j][0][tid], s_acc[3 % NQ][j][1][tid], agz[j]);
+                }
+            }
+        }
+        ++u;
+    }
+    if (cur_tile >= 0) flush(cur_tile);
+}
+
+// ---------------------------------------------------------------------------
+// FP64 kernel
+// ---------------------------------------------------------------------------
+struct Near64Args {
+    const double4_32a* src;      // (x, y, z, q), absolute
+    const double4_32a* tgt;      // (x, y, z, -)
+    const double* shifts;
+    double* partial;         // [n_tiles][max_contrib][4 or 1][kTile64]
+    int64_t n_tiles, n_chunks, U, G;
+    int n_img, max_contrib;
+};
+
+__device__ __forceinline__ double rsqrt_f64(double r2) {
+    // MUFU estimate (about 23 bits), then two Newton-Raphson steps for 1/sqrt(r2)
+    double y = (double)rsqrt_mufu((float)r2);
+    y = y * fma(-0.5 * r2, y * y, 1.5);
+    y = y * fma(-0.5 * r2, y * y, 1.5);
+    return y;
+}
+
+template <bool kGrad>
+__global__ void __launch_bounds__(kThreads64) k_near64(Near64Args a) {
+    __shared__ double4_32a s_src[kNearChunk];
+    constexpr int NQ = kGrad ? 4 : 1;
+    const int tid = threadIdx.x;
+    const int64_t g = blockIdx.x;
+    int64_t u = sk_bound(g, a.U, a.G);
+    const int64_t u_end = sk_bound(g + 1, a.U, a.G);
+    const int64_t upt = a.n_chunks * a.n_img;
+    double tx = 0, ty = 0, tz = 0;
+    double acc[NQ];
+    int64_t cur_tile = -1, cur_chunk = -1;
+
+    auto flush = [&](int64_t tile) {
+        const int64_t slot = g - sk_owner(tile * upt, a.U, a.G);
+        double* dst = a.partial + ((tile * a.max_contrib + slot) * NQ) * kTile64;
+#pragma unroll
+        for (int qi = 0; qi < NQ; ++qi) dst[qi * kTile64 + tid] = acc[qi];
+    };
+
+    while (u < u_end) {
+        const int64_t tile = u / upt;
+        const int64_t rem = u - tile * upt;
+        const int64_t chunk = rem / a.n_img;
+        const int img = (int)(rem - chunk * a.n_img);
+        if (tile != cur_tile) {
+            if (cur_tile >= 0) flush(cur_tile);
+            const double4_32a t = a.tgt[tile * kTile64 + tid];
+            tx = t.x; ty = t.y; tz = t.z;
+#pragma unroll
+            for (int qi = 0; qi < NQ; ++qi) acc[qi] = 0.0;
+            cur_tile = tile;
+            cur_chunk = -1;
+        }
+        if (chunk != cur_chunk) {
+            __syncthreads();
+            for (int i = tid; i < kNearChunk; i += kThreads64) s_src[i] = a.src[chunk * kNearChunk + i];
+            __syncthreads();
+            cur_chunk = chunk;
+        }
+        // y - x_i - p with the shift folded into the target
+        const double px = tx - a.shifts[3 * img], py = ty - a.shifts[3 * img + 1], pz = tz - a.shifts[3 * img + 2];
+#pragma unroll 4
+        for (int s = 0; s < kNearChunk; ++s) {
+            const double4_32a S = s_src[s];
+            const double ex = S.x - px, ey = S.y - py, ez = S.z - pz;   // x_i + p - y
+            const double r2 = fma(ez, ez, fma(ey, ey, ex * ex));
+            const double ri = r2 > 0.0 ? rsqrt_f64(r2) : 0.0;           // K(0) = 0
+            const double qr = S.w * ri;
+            acc[0] += qr;
+            if (kGrad) {
+                const double w = qr * ri * ri;
+                acc[1 % NQ] = fma(ex, w, acc[1 % NQ]);
+                acc[2 % NQ] = fma(ey, w, acc[2 % NQ]);
+                acc[3 % NQ] = fma(ez, w, acc[3 % NQ]);
+            }
+        }
+        ++u;
+    }
+    if (cur_tile >= 0) flush(cur_tile);
+}
+
+// ---------------------------------------------------------------------------
+// Reduction of the partial slots (fixed order: slot 0, 1, ...).
+// out_phi[i], out_grad[3i..] for packed target index i < n_valid.
+// ---------------------------------------------------------------------------
+__global__ void k_near_reduce(const double* __restrict__ partial, int64_t n_valid, int tile_size, int nq,
+                              int64_t n_chunks, int n_img, int64_t U, int64_t G, int max_contrib,
+                              double* __restrict__ out_phi, double* __restrict__ out_grad) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_valid) return;
+    const int64_t tile = i / tile_size;
+    const int loc = (int)(i - tile * tile_size);
+    const int64_t upt = n_chunks * n_img;
+    const int64_t g0 = sk_owner(tile * upt, U, G);
+    const int64_t g1 = sk_owner((tile + 1) * upt - 1, U, G);
+    double s[4] = {0, 0, 0, 0};
+    for (int64_t sl = 0; sl <= g1 - g0; ++sl) {
+        const double* src = partial + ((tile * max_contrib + sl) * nq) * tile_size + loc;
+        for (int qi = 0; qi < nq; ++qi) s[qi] += src[qi * tile_size];
+    }
+    out_phi[i] = s[0];
+    if (nq == 4 && out_grad) {
+        out_grad[3 * i + 0] = s[1];
+        out_grad[3 * i + 1] = s[2];
+        out_grad[3 * i + 2] = s[3];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Host launchers
+// ---------------------------------------------------------------------------
+size_t near32_dyn_smem(int n_img) { return sizeof(float) * 6 * kTgt32 * n_img + sizeof(int) * n_img; }
+
+cudaError_t launch_near32(bool grad, const float4* src_hi, const float4* src_lo, const double* src_org,
+                          int64_t n_chunks, const float4* tgt_hi, const float4* tgt_lo, const double* tgt_org,
+                          int64_t n_tiles, const double* shifts, int n_img, double* partial,
+                          const NearPlanLaunch& L, cudaStream_t st) {
+    Near32Args a;
+    a.src_hi = src_hi; a.src_lo = src_lo; a.src_org = src_org;
+    a.tgt_hi = tgt_hi; a.tgt_lo = tgt_lo; a.tgt_org = tgt_org; a.shifts = shifts;
+    a.partial = partial; a.n_tiles = n_tiles; a.n_chunks = n_chunks; a.U = L.U; a.G = L.G;
+    a.n_img = n_img; a.max_contrib = L.max_contrib;
+    const size_t smem = near32_dyn_smem(n_img);
+    if (grad)
+        k_near32<true><<<(unsigned)L.G, kThreads32, smem, st>>>(a);
+    else
+        k_near32<false><<<(unsigned)L.G, kThreads32, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_near64(bool grad, const double4_32a* src, int64_t n_chunks, const double4_32a* tgt, int64_t n_tiles,
+                          const double* shifts, int n_img, double* partial, const NearPlanLaunch& L,
+                          cudaStream_t st) {
+    Near64Args a;
+    a.src = src; a.tgt = tgt; a.shifts = shifts; a.partial = partial;
+    a.n_tiles = n_tiles; a.n_chunks = n_chunks; a.U = L.U; a.G = L.G;
+    a.n_img = n_img; a.max_contrib = L.max_contrib;
+    if (grad)
+        k_near64<true><<<(unsigned)L.G, kThreads64, 0, st>>>(a);
+    else
+        k_near64<false><<<(unsigned)L.G, kThreads64, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_near_reduce(const double* partial, int64_t n_valid, int tile_size, int nq,
+                               const NearPlanLaunch& L, double* out_phi, double* out_grad, cudaStream_t st) {
+    if (n_valid <= 0) return cudaSuccess;
+    const int bs = 256;
+    const unsigned nb = (unsigned)((n_valid + bs - 1) / bs);
+    k_near_reduce<<<nb, bs, 0, st>>>(partial, n_valid, tile_size, nq, L.n_chunks, (int)L.n_img, L.U, L.G,
+                                     L.max_contrib, out_phi, out_grad);
+    return cudaGetLastError();
+}
+
+int near32_occupancy_ctas(int n_img) {
+    int nb = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_near32<true>, kThreads32, near32_dyn_smem(n_img));
+    return nb < 1 ? 1 : nb;
+}
+
+int near64_occupancy_ctas() {
+    int nb = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_near64<true>, kThreads64, 0);
+    return nb < 1 ? 1 : nb;
+}
+
+}  // namespace psum

@@ -1,0 +1,347 @@
+// Algorithm "set" (Sec. 2.3.1) on the host in float64, and the upload of its
+// results to the device.
+//
+//   step 1: circumradius R0 = |d|/2
+//   step 2: M check points on the sphere of radius R0 (spherical Fibonacci lattice)
+//   step 3: periodic partners y~_l (one coordinate shifted by one period into S0)
+//   step 4: A_lt = R_t(y_l/R0) - R_t(y~_l/R0), t = 2..P (the constant column is
+//           identically zero and is dropped, Sec. 3)
+//   step 5: column-pivoted Householder QR of A and the pseudo-inverse
+//           A^+ = Pi R^-1 Q^T (Eq. 10), so that "get" needs one matrix-vector product
+//   step 6: box integrals R_t^(0) by tensor Gauss-Legendre quadrature with
+//           floor(p/2)+1 nodes per axis, exact for degree <= p (App. B, Eqs. A1-A2)
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <vector>
+
+#include "psum_internal.cuh"
+
+namespace psum {
+
+static void fibonacci_sphere(int M, double R0, std::vector<double>& Y) {
+    Y.resize(3 * (size_t)M);
+    const double golden = M_PI * (3.0 - std::sqrt(5.0));
+    for (int l = 0; l < M; ++l) {
+        const double z = 1.0 - (2.0 * l + 1.0) / M;
+        const double rho = std::sqrt(std::max(0.0, 1.0 - z * z));
+        const double az = l * golden;
+        Y[3 * l + 0] = R0 * rho * std::cos(az);
+        Y[3 * l + 1] = R0 * rho * std::sin(az);
+        Y[3 * l + 2] = R0 * z;
+    }
+}
+
+// Partner: shift the coordinate with the largest |y_k|/d_k (first on ties) by one
+// period towards the box.
+static void partners(const std::vector<double>& Y, const double d[3], std::vector<double>& Yt) {
+    const size_t M = Y.size() / 3;
+    Yt = Y;
+    for (size_t l = 0; l < M; ++l) {
+        int k = 0;
+        double best = std::fabs(Y[3 * l]) / d[0];
+        for (int c = 1; c < 3; ++c) {
+            const double v = std::fabs(Y[3 * l + c]) / d[c];
+            if (v > best) { best = v; k = c; }
+        }
+        const double y = Y[3 * l + k];
+        Yt[3 * l + k] = y - (y > 0 ? d[k] : (y < 0 ? -d[k] : 0.0));
+    }
+}
+
+static void basis_values(double x, double y, double z, int p, double* out) {
+    sh_visit<false>(x, y, z, p, [&](int n, int m, double v, double, double, double) { out[sh_index(n, m)] = v; });
+}
+
+// Gauss-Legendre nodes and weights on [-1, 1] by Newton's method on P_n.
+static void gauss_legendre(int n, std::vector<double>& t, std::vector<double>& w) {
+    t.assign(n, 0.0);
+    w.assign(n, 0.0);
+    for (int i = 0; i < n; ++i) {
+        double x = std::cos(M_PI * (i + 0.75) / (n + 0.5));
+        double dp = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = x;
+            for (int k = 2; k <= n; ++k) {
+                const double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            if (n == 1) { p1 = x; p0 = 1.0; }
+            dp = n * (x * p1 - p0) / (x * x - 1.0);
+            const double dx = p1 / dp;
+            x -= dx;
+            if (std::fabs(dx) < 1e-16) break;
+        }
+        // recompute the derivative at the converged node
+        double p0 = 1.0, p1 = x;
+        for (int k = 2; k <= n; ++k) {
+            const double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+            p0 = p1;
+            p1 = p2;
+        }
+        if (n == 1) { p1 = x; p0 = 1.0; }
+        dp = n * (x * p1 - p0) / (x * x - 1.0);
+        t[i] = x;
+        w[i] = 2.0 / ((1.0 - x * x) * dp * dp);
+    }
+}
+
+// Householder QR with column pivoting of the M x n matrix A (column-major),
+// then pinv = Pi R^-1 Q1^T (n x M, row-major).  Returns PSUM_ERR_RANK if
+// |R_kk| < 1e-13 |R_11| for some k.
+static int qr_pseudo_inverse(std::vector<double>& A, int M, int n, std::vector<double>& pinv, int& rank,
+                             double& cond_est) {
+    std::vector<int> piv(n);
+    std::iota(piv.begin(), piv.end(), 0);
+    std::vector<double> beta(n, 0.0), rdiag(n, 0.0);
+    auto col = [&](int j) { return A.data() + (size_t)j * M; };
+    for (int k = 0; k < n; ++k) {
+        // pivot: the remaining column of largest norm (recomputed exactly)
+        int jb = k;
+        double nb = -1.0;
+        for (int j = k; j < n; ++j) {
+            const double* c = col(j);
+            double s = 0.0;
+            for (int i = k; i < M; ++i) s += c[i] * c[i];
+            if (s > nb) { nb = s; jb = j; }
+        }
+        if (jb != k) {
+            std::swap_ranges(col(k), col(k) + M, col(jb));
+            std::swap(piv[k], piv[jb]);
+        }
+        double* v = col(k);
+        const double norm = std::sqrt(nb);
+        const double alpha = v[k] > 0 ? -norm : norm;
+        rdiag[k] = alpha;
+        if (norm == 0.0) { beta[k] = 0.0; continue; }
+        v[k] -= alpha;                          // v = x - alpha e1 (stored in place below the diagonal)
+        double vv = 0.0;
+        for (int i = k; i < M; ++i) vv += v[i] * v[i];
+        beta[k] = vv > 0 ? 2.0 / vv : 0.0;
+        for (int j = k + 1; j < n; ++j) {
+            double* c = col(j);
+            double s = 0.0;
+            for (int i = k; i < M; ++i) s += v[i] * c[i];
+            s *= beta[k];
+            for (int i = k; i < M; ++i) c[i] -= s * v[i];
+        }
+    }
+    const double r11 = std::fabs(rdiag[0]);
+    rank = 0;
+    double rmin = r11;
+    for (int k = 0; k < n; ++k) {
+        const double a = std::fabs(rdiag[k]);
+        if (!(a >= 1e-13 * r11) || r11 == 0.0) break;
+        rank = k + 1;
+        rmin = std::min(rmin, a);
+    }
+    cond_est = rmin > 0 ? r11 / rmin : INFINITY;
+    if (rank < n) return PSUM_ERR_RANK;
+    // Q1 (M x n): apply H_0 .. H_{n-1} to [I_n; 0] in reverse order
+    std::vector<double> Q((size_t)M * n, 0.0);      // column-major
+    for (int j = 0; j < n; ++j) Q[(size_t)j * M + j] = 1.0;
+    for (int k = n - 1; k >= 0; --k) {
+        const double* v = col(k);
+        for (int j = 0; j < n; ++j) {
+            double* c = Q.data() + (size_t)j * M;
+            double s = 0.0;
+            for (int i = k; i < M; ++i) s += v[i] * c[i];
+            s *= beta[k];
+            for (int i = k; i < M; ++i) c[i] -= s * v[i];
+        }
+    }
+    // Z = R^-1 Q1^T by back substitution, R upper-triangular: R_kk = rdiag[k],
+    // R_kj (j > k) = A[k][j] after the factorisation.
+    pinv.assign((size_t)n * M, 0.0);
+    std::vector<double> z(n);
+    for (int l = 0; l < M; ++l) {
+        for (int k = n - 1; k >= 0; --k) {
+            double s = Q[(size_t)k * M + l];
+            for (int j = k + 1; j < n; ++j) s -= A[(size_t)j * M + k] * z[j];
+            z[k] = s / rdiag[k];
+        }
+        for (int k = 0; k < n; ++k) pinv[(size_t)piv[k] * M + l] = z[k];
+    }
+    return PSUM_OK;
+}
+
+// Morton order of points inside [-R, R]^3 (host), used to group the check targets.
+static uint64_t morton_host(const double* p, double R) {
+    uint64_t key = 0;
+    uint32_t c[3];
+    for (int k = 0; k < 3; ++k) {
+        double u = (p[k] / (2.0 * R) + 0.5) * 1024.0;
+        int v = (int)std::floor(u);
+        c[k] = (uint32_t)std::min(1023, std::max(0, v));
+    }
+    for (int b = 9; b >= 0; --b)
+        for (int k = 0; k < 3; ++k) key = (key << 1) | ((c[k] >> b) & 1u);
+    return key;
+}
+
+#define PSUM_CUDA_TRY(call)                            \
+    do {                                               \
+        cudaError_t e_ = (call);                       \
+        if (e_ == cudaErrorMemoryAllocation) return PSUM_ERR_NOMEM; \
+        if (e_ != cudaSuccess) return PSUM_ERR_CUDA;   \
+    } while (0)
+
+template <class T>
+static int upload(T** dst, const T* src, size_t count) {
+    PSUM_CUDA_TRY(cudaMalloc((void**)dst, sizeof(T) * std::max<size_t>(count, 1)));
+    if (count) PSUM_CUDA_TRY(cudaMemcpy(*dst, src, sizeof(T) * count, cudaMemcpyHostToDevice));
+    return PSUM_OK;
+}
+
+int build_plan(const psum_opts& o, Plan& pl) {
+    pl.opt = o;
+    const int p = o.p, M = o.M;
+    pl.P = (p + 1) * (p + 1);
+    const double d[3] = {o.d[0], o.d[1], o.d[2]};
+    pl.R0 = 0.5 * std::sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);             // step 1
+    // image vectors of the near block and lambda_eff
+    pl.shifts.clear();
+    pl.self_image = -1;
+    for (int i1 = -o.K[0]; i1 <= o.K[0]; ++i1)
+        for (int i2 = -o.K[1]; i2 <= o.K[1]; ++i2)
+            for (int i3 = -o.K[2]; i3 <= o.K[2]; ++i3) {
+                if (i1 == 0 && i2 == 0 && i3 == 0) pl.self_image = (int)(pl.shifts.size() / 3);
+                pl.shifts.push_back(i1 * d[0]);
+                pl.shifts.push_back(i2 * d[1]);
+                pl.shifts.push_back(i3 * d[2]);
+            }
+    pl.n_images = (int)(pl.shifts.size() / 3);
+    double hmin = 1e300;
+    for (int k = 0; k < 3; ++k) hmin = std::min(hmin, 0.5 * (2 * o.K[k] + 1) * d[k]);
+    pl.lambda_eff = hmin / pl.R0;
+
+    fibonacci_sphere(M, pl.R0, pl.Y);                                                 // step 2
+    partners(pl.Y, d, pl.Yt);                                                         // step 3
+    const int n = pl.P - 1;                                                           // step 4
+    std::vector<double> A((size_t)M * n);
+    {
+        std::vector<double> b1(pl.P), b2(pl.P);
+        const double s = 1.0 / pl.R0;
+        for (int l = 0; l < M; ++l) {
+            basis_values(pl.Y[3 * l] * s, pl.Y[3 * l + 1] * s, pl.Y[3 * l + 2] * s, p, b1.data());
+            basis_values(pl.Yt[3 * l] * s, pl.Yt[3 * l + 1] * s, pl.Yt[3 * l + 2] * s, p, b2.data());
+            for (int t = 1; t < pl.P; ++t) A[(size_t)(t - 1) * M + l] = b1[t] - b2[t];
+        }
+    }
+    int st = qr_pseudo_inverse(A, M, n, pl.pinv, pl.rank, pl.cond_est);               // step 5
+    if (st != PSUM_OK) return st;
+    {                                                                                 // step 6
+        const int nq = p / 2 + 1;
+        std::vector<double> t, w;
+        gauss_legendre(nq, t, w);
+        pl.Rbox.assign(pl.P, 0.0);
+        std::vector<double> b(pl.P);
+        for (int i = 0; i < nq; ++i)
+            for (int j = 0; j < nq; ++j)
+                for (int k = 0; k < nq; ++k) {
+                    basis_values(0.5 * d[0] * t[i] / pl.R0, 0.5 * d[1] * t[j] / pl.R0, 0.5 * d[2] * t[k] / pl.R0,
+                                 p, b.data());
+                    const double ww = w[i] * w[j] * w[k] / 8.0;
+                    for (int q = 0; q < pl.P; ++q) pl.Rbox[q] += ww * b[q];
+                }
+    }
+
+    // ---- check targets: y_0..y_{M-1}, y~_0..y~_{M-1} ----
+    pl.n_check = 2 * M;
+    std::vector<double> pts(3 * (size_t)pl.n_check);
+    std::copy(pl.Y.begin(), pl.Y.end(), pts.begin());
+    std::copy(pl.Yt.begin(), pl.Yt.end(), pts.begin() + 3 * (size_t)M);
+    std::vector<int> pos(pl.n_check);
+    if (o.precision == PSUM_FP32C) {
+        const int tile = kTile32;
+        pl.check_tile = tile;
+        pl.n_check_tiles = (pl.n_check + tile - 1) / tile;
+        const int ngroups = pl.n_check_tiles * kTgt32;
+        std::vector<int> order(pl.n_check);
+        std::iota(order.begin(), order.end(), 0);
+        std::vector<uint64_t> key(pl.n_check);
+        for (int j = 0; j < pl.n_check; ++j) key[j] = morton_host(&pts[3 * (size_t)j], pl.R0);
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return key[a] < key[b]; });
+        // hi parts (2 float4 per point) followed by lo parts (2 float4 per point)
+        const size_t npk = 2 * (size_t)ngroups * kNearChunk;
+        std::vector<float4> pk(2 * npk, make_float4(0.f, 0.f, 0.f, 0.f));
+        for (size_t i = 0; i < npk; ++i) pk[i] = make_float4(1e3f, 1e3f, 1e3f, 1e3f);
+        std::vector<double> org(4 * (size_t)ngroups, 0.0);
+        for (int g = 0; g < ngroups; ++g) {
+            double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+            const int i0 = g * kNearChunk, i1 = std::min(pl.n_check, (g + 1) * kNearChunk);
+            for (int i = i0; i < i1; ++i)
+                for (int c = 0; c < 3; ++c) {
+                    lo[c] = std::min(lo[c], pts[3 * (size_t)order[i] + c]);
+                    hi[c] = std::max(hi[c], pts[3 * (size_t)order[i] + c]);
+                }
+            for (int c = 0; c < 3; ++c) org[4 * g + c] = lo[c] <= hi[c] ? 0.5 * (lo[c] + hi[c]) : 0.0;
+            double r2max = 0.0;
+            for (int i = i0; i < i1; ++i) {
+                const double* q = &pts[3 * (size_t)order[i]];
+                const double r[3] = {q[0] - org[4 * g], q[1] - org[4 * g + 1], q[2] - org[4 * g + 2]};
+                r2max = std::max(r2max, r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+                const float f[3] = {(float)r[0], (float)r[1], (float)r[2]};
+                const float l[3] = {(float)(r[0] - (double)f[0]), (float)(r[1] - (double)f[1]),
+                                    (float)(r[2] - (double)f[2])};
+                pk[2 * (size_t)i] = make_float4(f[0], f[0], f[1], f[1]);
+                pk[2 * (size_t)i + 1] = make_float4(f[2], f[2], 0.f, 0.f);
+                pk[npk + 2 * (size_t)i] = make_float4(l[0], l[0], l[1], l[1]);
+                pk[npk + 2 * (size_t)i + 1] = make_float4(l[2], l[2], 0.f, 0.f);
+                pos[order[i]] = i;
+            }
+            org[4 * g + 3] = std::sqrt(r2max);
+        }
+        std::vector<int> inv((size_t)ngroups * kNearChunk, -1);
+        for (int j = 0; j < pl.n_check; ++j) inv[pos[j]] = j;
+        int s1 = upload((float4**)&pl.d_check_tgt, pk.data(), pk.size());
+        if (s1) return s1;
+        s1 = upload(&pl.d_check_org, org.data(), org.size());
+        if (s1) return s1;
+        s1 = upload(&pl.d_check_inv, inv.data(), inv.size());
+        if (s1) return s1;
+    } else {
+        const int tile = kTile64;
+        pl.check_tile = tile;
+        pl.n_check_tiles = (pl.n_check + tile - 1) / tile;
+        std::vector<double4_32a> pk((size_t)pl.n_check_tiles * tile, make_double4_32a(1e3, 1e3, 1e3, 0.0));
+        for (int j = 0; j < pl.n_check; ++j) {
+            pk[j] = make_double4_32a(pts[3 * (size_t)j], pts[3 * (size_t)j + 1], pts[3 * (size_t)j + 2], 0.0);
+            pos[j] = j;
+        }
+        int s1 = upload((double4_32a**)&pl.d_check_tgt, pk.data(), pk.size());
+        if (s1) return s1;
+    }
+    int s2 = upload(&pl.d_check_pos, pos.data(), pos.size());
+    if (s2) return s2;
+    if ((s2 = upload(&pl.d_pinv, pl.pinv.data(), pl.pinv.size()))) return s2;
+    if ((s2 = upload(&pl.d_Rbox, pl.Rbox.data(), pl.Rbox.size()))) return s2;
+    if ((s2 = upload(&pl.d_shifts, pl.shifts.data(), pl.shifts.size()))) return s2;
+    PSUM_CUDA_TRY(cudaMalloc((void**)&pl.d_C, sizeof(double) * pl.P));
+    PSUM_CUDA_TRY(cudaMemset(pl.d_C, 0, sizeof(double) * pl.P));
+    PSUM_CUDA_TRY(cudaMalloc((void**)&pl.d_status, sizeof(int)));
+    PSUM_CUDA_TRY(cudaMemset(pl.d_status, 0, sizeof(int)));
+    PSUM_CUDA_TRY(cudaMallocHost((void**)&pl.h_status, sizeof(int)));
+    *pl.h_status = 0;
+    return PSUM_OK;
+}
+
+void free_plan_device(Plan& pl) {
+    cudaFree(pl.d_check_pos);
+    cudaFree(pl.d_check_inv);
+    cudaFree(pl.d_check_tgt);
+    cudaFree(pl.d_check_org);
+    cudaFree(pl.d_pinv);
+    cudaFree(pl.d_Rbox);
+    cudaFree(pl.d_shifts);
+    cudaFree(pl.d_C);
+    cudaFree(pl.d_status);
+    if (pl.h_status) cudaFreeHost(pl.h_status);
+    cudaFree(pl.scratch.ptr);
+    cudaFree(pl.dstage.ptr);
+    pl = Plan();
+}
+
+}  // namespace psum

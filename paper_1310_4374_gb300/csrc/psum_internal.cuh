@@ -1,0 +1,206 @@
+// Internal definitions shared by the psum translation units (product code).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cmath>
+#include <vector>
+
+#include "psum.h"
+
+namespace psum {
+
+// ---------------------------------------------------------------------------
+// Tiling of the near-field pair sum.
+//   * a source CHUNK is kNearChunk consecutive (Morton-ordered) sources staged
+//     in shared memory, with one float64 origin;
+//   * a target TILE is kThreads threads x kTgt targets, with one float64 origin;
+//   * a work UNIT is (tile, chunk, image): every target of the tile against
+//     every source of the chunk shifted by one image vector.
+// ---------------------------------------------------------------------------
+constexpr int kNearChunk = 128;           // sources per chunk (both precisions)
+constexpr int kThreads32 = 128;           // threads per CTA, FP32C kernel
+constexpr int kTgt32 = 4;                 // targets per thread, FP32C kernel (2 packed pairs)
+constexpr int kTile32 = kThreads32 * kTgt32;
+constexpr int kThreads64 = 128;           // threads per CTA, FP64 kernel
+constexpr int kTile64 = kThreads64;       // one target per thread
+constexpr int kMaxImages = 343;           // K <= 3 per axis
+constexpr int kMaxDegree = 40;
+
+// device status bits (OR-ed by kernels, mapped to PSUM_ERR_* on the host)
+constexpr int kStatNonNeutral = 1;
+constexpr int kStatOutOfBox = 2;
+constexpr int kStatNonFinite = 4;
+constexpr int kStatTimeout = 8;
+
+// 0-based stacking of Eq. 1.8: t = n(n+1) + m
+__host__ __device__ __forceinline__ int sh_index(int n, int m) { return n * (n + 1) + m; }
+
+// ---------------------------------------------------------------------------
+// Renormalised regular solid harmonics R^_n^m(u) (Eqs. 1.6-1.7), written as a
+// recurrence directly on R^ so that the factorials never appear:
+//   R^_0^0 = 1
+//   R^_m^m   = -(x a + y b) sqrt((2m-1)/(2m)),  R^_m^-m = (y a - x b) sqrt((2m-1)/(2m)),
+//              a = R^_{m-1}^{m-1}, b = R^_{m-1}^{-(m-1)}  (b = 0 for m = 1)
+//   R^_{m+1}^{+-m} = -z sqrt(2m+1) R^_m^{+-m}
+//   R^_n^{+-m} = -[(2n-1) z R^_{n-1} / sqrt((n-m)(n+m))
+//                  + r^2 sqrt((n-m-1)(n+m-1)/((n-m)(n+m))) R^_{n-2}]
+// (Eq. 1.6 with each factor sqrt((n-m)!(n+m)!) of Eq. 1.7 divided out step by step).
+// The visitor is called once per (n, m) with the value and its gradient.
+// ---------------------------------------------------------------------------
+template <bool kGrad, class Visit>
+__host__ __device__ __forceinline__ void sh_visit(double x, double y, double z, int p, Visit&& visit) {
+    const double r2 = x * x + y * y + z * z;
+    // sectoral pair (m, -m) carried along the diagonal, with gradients
+    double a = 1.0, b = 0.0;
+    double ax = 0, ay = 0, az = 0, bx = 0, by = 0, bz = 0;
+    for (int m = 0; m <= p; ++m) {
+        double sp, sm, spx = 0, spy = 0, spz = 0, smx = 0, smy = 0, smz = 0;
+        if (m == 0) {
+            sp = 1.0;
+            sm = 0.0;
+        } else {
+            const double c = sqrt((2.0 * m - 1.0) / (2.0 * m));
+            sp = -(x * a + y * b) * c;
+            sm = (y * a - x * b) * c;
+            if (kGrad) {
+                spx = -(a + x * ax + y * bx) * c;
+                spy = -(x * ay + b + y * by) * c;
+                spz = -(x * az + y * bz) * c;
+                smx = (y * ax - b - x * bx) * c;
+                smy = (a + y * ay - x * by) * c;
+                smz = (y * az - x * bz) * c;
+            }
+        }
+        a = sp; b = sm;
+        if (kGrad) { ax = spx; ay = spy; az = spz; bx = smx; by = smy; bz = smz; }
+        // walk up in n for +m and -m
+        for (int s = 0; s < (m == 0 ? 1 : 2); ++s) {
+            const int mm = s == 0 ? m : -m;
+            double v2 = s == 0 ? sp : sm;            // R^_m^mm
+            double g2x = s == 0 ? spx : smx, g2y = s == 0 ? spy : smy, g2z = s == 0 ? spz : smz;
+            visit(m, mm, v2, g2x, g2y, g2z);
+            if (m + 1 > p) continue;
+            const double c1 = sqrt(2.0 * m + 1.0);
+            double v1 = -z * c1 * v2;                 // R^_{m+1}^mm
+            double g1x = 0, g1y = 0, g1z = 0;
+            if (kGrad) {
+                g1x = -z * c1 * g2x;
+                g1y = -z * c1 * g2y;
+                g1z = -c1 * (v2 + z * g2z);
+            }
+            visit(m + 1, mm, v1, g1x, g1y, g1z);
+            for (int n = m + 2; n <= p; ++n) {
+                const double nm = (double)(n - m) * (double)(n + m);
+                const double e1 = (2.0 * n - 1.0) / sqrt(nm);
+                const double e2 = sqrt((double)(n - m - 1) * (double)(n + m - 1) / nm);
+                const double v = -(e1 * z * v1 + e2 * r2 * v2);
+                double gx = 0, gy = 0, gz = 0;
+                if (kGrad) {
+                    gx = -(e1 * z * g1x + e2 * (2.0 * x * v2 + r2 * g2x));
+                    gy = -(e1 * z * g1y + e2 * (2.0 * y * v2 + r2 * g2y));
+                    gz = -(e1 * (v1 + z * g1z) + e2 * (2.0 * z * v2 + r2 * g2z));
+                }
+                visit(n, mm, v, gx, gy, gz);
+                v2 = v1; v1 = v;
+                if (kGrad) { g2x = g1x; g2y = g1y; g2z = g1z; g1x = gx; g1y = gy; g1z = gz; }
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// The plan (algorithm "set" results, device copies and scratch).
+// ---------------------------------------------------------------------------
+struct DevBuf {
+    void* ptr = nullptr;
+    size_t bytes = 0;
+};
+
+struct Plan {
+    psum_opts opt{};
+    int device = 0;
+    int P = 0;                  // (p+1)^2
+    double R0 = 0;
+    double lambda_eff = 0;
+    double cond_est = 0;
+    int rank = 0;
+    int n_images = 0;
+    std::vector<double> shifts;     // n_images x 3: image vectors (i1 d1, i2 d2, i3 d3)
+    std::vector<double> Y, Yt;      // M x 3 check points and partners
+    std::vector<double> pinv;       // (P-1) x M pseudo-inverse of A (row-major)
+    std::vector<double> Rbox;       // P box integrals R_t^(0)
+    int self_image = 0;             // index of the zero image vector in `shifts`
+
+    // check targets (2M points) as the near kernels consume them
+    int n_check = 0;                // 2M
+    int n_check_tiles = 0;
+    int check_tile = 0;             // targets per check tile
+    int* d_check_pos = nullptr;     // 2M: position of target j (j < M: y_j, else y~_{j-M}) in the packed order
+    int* d_check_inv = nullptr;     // packed position -> j (-1 for padding), FP32C only
+    void* d_check_tgt = nullptr;    // packed check targets (float4 rel coords or double4_32a)
+    double* d_check_org = nullptr;  // tile origins (FP32C), 3 per tile
+
+    double* d_pinv = nullptr;
+    double* d_Rbox = nullptr;
+    double* d_shifts = nullptr;
+    double* d_C = nullptr;          // P coefficients of the last evaluation
+    int* d_status = nullptr;
+    int* h_status = nullptr;        // pinned
+
+    // scratch, grown on demand
+    DevBuf scratch;
+    // pinned host staging and device staging for psum_eval_host
+    DevBuf dstage;
+
+    int num_sms = 0;
+};
+
+// ---------------------------------------------------------------------------
+// Host helpers implemented in plan.cu
+// ---------------------------------------------------------------------------
+int build_plan(const psum_opts& o, Plan& pl);     // algorithm "set" on the host, then upload
+void free_plan_device(Plan& pl);
+
+// ---------------------------------------------------------------------------
+// Stream-K partition of the (tile, chunk, image) unit space over G CTAs.
+// CTA g covers units [bound(g), bound(g+1)), bound(g) = floor(g U / G).
+// ---------------------------------------------------------------------------
+__host__ __device__ __forceinline__ int64_t sk_bound(int64_t g, int64_t U, int64_t G) {
+    return (g * U) / G;
+}
+// the CTA whose range contains unit u
+__host__ __device__ __forceinline__ int64_t sk_owner(int64_t u, int64_t U, int64_t G) {
+    // largest g with floor(g U / G) <= u  <=>  g U < (u + 1) G
+    int64_t g = ((u + 1) * G - 1) / U;
+    if (g > G - 1) g = G - 1;
+    return g;
+}
+
+struct NearPlanLaunch {
+    int64_t n_tiles, n_chunks, n_img;
+    int64_t U, G;
+    int max_contrib;              // partial slots per tile
+};
+
+inline NearPlanLaunch near_partition(int64_t n_tiles, int64_t n_chunks, int n_img, int64_t G_max) {
+    NearPlanLaunch L;
+    L.n_tiles = n_tiles;
+    L.n_chunks = n_chunks;
+    L.n_img = n_img;
+    L.U = n_tiles * n_chunks * n_img;
+    L.G = L.U < G_max ? L.U : G_max;
+    if (L.G < 1) L.G = 1;
+    int mc = 1;
+    const int64_t upt = n_chunks * n_img;
+    for (int64_t t = 0; t < n_tiles; ++t) {
+        const int64_t g0 = sk_owner(t * upt, L.U, L.G);
+        const int64_t g1 = sk_owner((t + 1) * upt - 1, L.U, L.G);
+        if (g1 - g0 + 1 > mc) mc = (int)(g1 - g0 + 1);
+    }
+    L.max_contrib = mc;
+    return L;
+}
+
+}  // namespace psum

@@ -1,0 +1,233 @@
+// Spatial ordering and packing of the sources for the near-field kernels.
+//
+// FP32C needs sources grouped into compact chunks so that float32 offsets from a
+// per-chunk float64 origin keep the precision of close pairs.  The charges are
+// ordered along a Morton (Z-order) curve of a 256^3 grid over the box by a
+// stable least-significant-digit radix sort (8-bit digits), then packed 128 at
+// a time with the midpoint of each chunk's bounding box as its origin.
+#include "psum_internal.cuh"
+
+namespace psum {
+
+constexpr int kSortThreads = 256;
+constexpr int kSortWarps = kSortThreads / 32;
+constexpr int kSortPerThread = 8;
+constexpr int kSortTile = kSortThreads * kSortPerThread;   // 2048 keys per block
+constexpr int kRadix = 256;
+
+__device__ __forceinline__ uint32_t spread_bits8(uint32_t v) {
+    // 8 bits -> every third bit of 24
+    v &= 0xffu;
+    v = (v | (v << 8)) & 0x00f00fu;
+    v = (v | (v << 4)) & 0x0c30c3u;
+    v = (v | (v << 2)) & 0x249249u;
+    return v;
+}
+
+__global__ void k_morton(const double* __restrict__ x, int64_t n, double d0, double d1, double d2,
+                         uint32_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double dd[3] = {d0, d1, d2};
+    uint32_t c[3];
+    for (int k = 0; k < 3; ++k) {
+        double u = (x[3 * i + k] / dd[k] + 0.5) * 256.0;
+        int v = (int)floor(u);
+        v = v < 0 ? 0 : (v > 255 ? 255 : v);      // also maps NaN (validated elsewhere) into range
+        c[k] = (uint32_t)v;
+    }
+    keys[i] = spread_bits8(c[0]) | (spread_bits8(c[1]) << 1) | (spread_bits8(c[2]) << 2);
+    vals[i] = (uint32_t)i;
+}
+
+__global__ void __launch_bounds__(kSortThreads) k_sort_hist(const uint32_t* __restrict__ keys, int64_t n, int shift,
+                                                            uint32_t* __restrict__ hist, int nblk) {
+    __shared__ uint32_t cnt[kRadix];
+    for (int d = threadIdx.x; d < kRadix; d += kSortThreads) cnt[d] = 0;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * kSortTile;
+    for (int k = 0; k < kSortPerThread; ++k) {
+        const int64_t i = base + k * kSortThreads + threadIdx.x;
+        if (i < n) atomicAdd(&cnt[(keys[i] >> shift) & (kRadix - 1)], 1u);
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < kRadix; d += kSortThreads) hist[(int64_t)d * nblk + blockIdx.x] = cnt[d];
+}
+
+// exclusive scan of `total` counts in place, one block of 1024 threads
+__global__ void __launch_bounds__(1024) k_sort_scan(uint32_t* __restrict__ hist, int64_t total) {
+    __shared__ uint32_t s[1024];
+    const int64_t per = (total + 1023) / 1024;
+    const int64_t b = threadIdx.x * per;
+    const int64_t e = b + per < total ? b + per : total;
+    uint32_t sum = 0;
+    for (int64_t i = b; i < e; ++i) sum += hist[i];
+    s[threadIdx.x] = sum;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+        const uint32_t v = threadIdx.x >= o ? s[threadIdx.x - o] : 0u;
+        __syncthreads();
+        s[threadIdx.x] += v;
+        __syncthreads();
+    }
+    uint32_t run = s[threadIdx.x] - sum;
+    for (int64_t i = b; i < e; ++i) {
+        const uint32_t v = hist[i];
+        hist[i] = run;
+        run += v;
+    }
+}
+
+// Stable scatter: warp w of block b owns keys [b*T + w*256, +256) and walks them in
+// order, 32 at a time; equal digits inside a step are ranked by lane.
+__global__ void __launch_bounds__(kSortThreads) k_sort_scatter(const uint32_t* __restrict__ kin,
+                                                               const uint32_t* __restrict__ vin, int64_t n, int shift,
+                                                               const uint32_t* __restrict__ offs, int nblk,
+                                                               uint32_t* __restrict__ kout,
+                                                               uint32_t* __restrict__ vout) {
+    __shared__ uint32_t wcnt[kSortWarps][kRadix];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int i = threadIdx.x; i < kSortWarps * kRadix; i += kSortThreads) (&wcnt[0][0])[i] = 0;
+    __syncthreads();
+    const int64_t wbase = (int64_t)blockIdx.x * kSortTile + w * (kSortPerThread * 32);
+    for (int k = 0; k < kSortPerThread; ++k) {
+        const int64_t i = wbase + k * 32 + lane;
+        if (i < n) atomicAdd(&wcnt[w][(kin[i] >> shift) & (kRadix - 1)], 1u);
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < kRadix; d += kSortThreads) {
+        uint32_t run = offs[(int64_t)d * nblk + blockIdx.x];
+        for (int ww = 0; ww < kSortWarps; ++ww) {
+            const uint32_t c = wcnt[ww][d];
+            wcnt[ww][d] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+    const uint32_t lt = (1u << lane) - 1u;
+    for (int k = 0; k < kSortPerThread; ++k) {
+        const int64_t i = wbase + k * 32 + lane;
+        const bool valid = i < n;
+        const uint32_t key = valid ? kin[i] : 0u;
+        const uint32_t dig = valid ? ((key >> shift) & (kRadix - 1)) : (uint32_t)(kRadix + lane);
+        const uint32_t peers = __match_any_sync(0xffffffffu, dig);
+        const uint32_t rank = __popc(peers & lt);
+        uint32_t pos = 0;
+        if (valid) pos = wcnt[w][dig] + rank;
+        __syncwarp();
+        if (valid && rank == 0) wcnt[w][dig] += __popc(peers);
+        __syncwarp();
+        if (valid) {
+            kout[pos] = key;
+            vout[pos] = vin[i];
+        }
+    }
+}
+
+// One warp per group of kNearChunk sorted positions: the bounding-box midpoint is the
+// float64 origin, stored with the group radius (largest distance of a point from it);
+// each point's offset from the origin is split into a float32 hi part and the float32
+// rounding remainder lo, packed two float4 each: (x,x,y,y),(z,z,q,q) and (xl,xl,yl,yl),(zl,zl,0,0).
+// Padding points (s >= n) get q = 0 and a far-away position.
+__global__ void k_pack32(const double* __restrict__ x, const double* __restrict__ q,
+                         const uint32_t* __restrict__ perm, int64_t n, int64_t n_groups,
+                         float4* __restrict__ pk_hi, float4* __restrict__ pk_lo, double* __restrict__ org) {
+    const int64_t grp = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (grp >= n_groups) return;
+    constexpr int per = kNearChunk / 32;
+    double px[per][3], pq[per];
+    bool ok[per];
+    double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+#pragma unroll
+    for (int k = 0; k < per; ++k) {
+        const int64_t s = grp * kNearChunk + k * 32 + lane;
+        ok[k] = s < n;
+        if (ok[k]) {
+            const int64_t i = perm ? (int64_t)perm[s] : s;
+            for (int c = 0; c < 3; ++c) {
+                px[k][c] = x[3 * i + c];
+                lo[c] = fmin(lo[c], px[k][c]);
+                hi[c] = fmax(hi[c], px[k][c]);
+            }
+            pq[k] = q[i];
+        }
+    }
+    double o[3];
+    for (int c = 0; c < 3; ++c) {
+        for (int off = 16; off > 0; off >>= 1) {
+            lo[c] = fmin(lo[c], __shfl_xor_sync(0xffffffffu, lo[c], off));
+            hi[c] = fmax(hi[c], __shfl_xor_sync(0xffffffffu, hi[c], off));
+        }
+        o[c] = lo[c] <= hi[c] ? 0.5 * (lo[c] + hi[c]) : 0.0;
+    }
+    double r2max = 0.0;
+#pragma unroll
+    for (int k = 0; k < per; ++k) {
+        const int64_t s = grp * kNearChunk + k * 32 + lane;
+        float fx = 1.0e3f, fy = 1.0e3f, fz = 1.0e3f, fq = 0.f, lx = 0.f, ly = 0.f, lz = 0.f;
+        if (ok[k]) {
+            const double rx = px[k][0] - o[0], ry = px[k][1] - o[1], rz = px[k][2] - o[2];
+            r2max = fmax(r2max, rx * rx + ry * ry + rz * rz);
+            fx = (float)rx; fy = (float)ry; fz = (float)rz;
+            lx = (float)(rx - (double)fx); ly = (float)(ry - (double)fy); lz = (float)(rz - (double)fz);
+            fq = (float)pq[k];
+        }
+        pk_hi[2 * s] = make_float4(fx, fx, fy, fy);
+        pk_hi[2 * s + 1] = make_float4(fz, fz, fq, fq);
+        pk_lo[2 * s] = make_float4(lx, lx, ly, ly);
+        pk_lo[2 * s + 1] = make_float4(lz, lz, 0.f, 0.f);
+    }
+    for (int off = 16; off > 0; off >>= 1) r2max = fmax(r2max, __shfl_xor_sync(0xffffffffu, r2max, off));
+    if (lane == 0) {
+        org[4 * grp] = o[0]; org[4 * grp + 1] = o[1]; org[4 * grp + 2] = o[2];
+        org[4 * grp + 3] = sqrt(r2max);
+    }
+}
+
+__global__ void k_pack64(const double* __restrict__ x, const double* __restrict__ q, int64_t n, int64_t n_pad,
+                         double4_32a* __restrict__ pk) {
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n_pad) return;
+    if (s < n)
+        pk[s] = make_double4_32a(x[3 * s], x[3 * s + 1], x[3 * s + 2], q[s]);
+    else
+        pk[s] = make_double4_32a(1.0e3, 1.0e3, 1.0e3, 0.0);
+}
+
+// ---------------------------------------------------------------------------
+int sort_blocks(int64_t n) { return (int)((n + kSortTile - 1) / kSortTile); }
+
+// keys/vals ping-pong in (ka, va) <-> (kb, vb); result in (ka, va) after an even number of passes.
+cudaError_t launch_morton_sort(const double* x, int64_t n, const double d[3], uint32_t* ka, uint32_t* va,
+                               uint32_t* kb, uint32_t* vb, uint32_t* hist, cudaStream_t st) {
+    const int bs = 256;
+    k_morton<<<(unsigned)((n + bs - 1) / bs), bs, 0, st>>>(x, n, d[0], d[1], d[2], ka, va);
+    const int nblk = sort_blocks(n);
+    uint32_t *ki = ka, *vi = va, *ko = kb, *vo = vb;
+    for (int pass = 0; pass < 4; ++pass) {      // 24-bit keys: 3 passes; a 4th (empty digit) keeps the result in (ka, va)
+        const int shift = 8 * pass;
+        k_sort_hist<<<nblk, kSortThreads, 0, st>>>(ki, n, shift, hist, nblk);
+        k_sort_scan<<<1, 1024, 0, st>>>(hist, (int64_t)kRadix * nblk);
+        k_sort_scatter<<<nblk, kSortThreads, 0, st>>>(ki, vi, n, shift, hist, nblk, ko, vo);
+        uint32_t* t = ki; ki = ko; ko = t;
+        t = vi; vi = vo; vo = t;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack32(const double* x, const double* q, const uint32_t* perm, int64_t n, int64_t n_groups,
+                          float4* pk_hi, float4* pk_lo, double* org, cudaStream_t st) {
+    const int warps = 4;
+    k_pack32<<<(unsigned)((n_groups + warps - 1) / warps), 32 * warps, 0, st>>>(x, q, perm, n, n_groups, pk_hi,
+                                                                                  pk_lo, org);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack64(const double* x, const double* q, int64_t n, int64_t n_pad, double4_32a* pk, cudaStream_t st) {
+    const int bs = 256;
+    k_pack64<<<(unsigned)((n_pad + bs - 1) / bs), bs, 0, st>>>(x, q, n, n_pad, pk);
+    return cudaGetLastError();
+}
+
+}  // namespace psum

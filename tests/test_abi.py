@@ -1,0 +1,64 @@
+"""The C-ABI library builds, loads and exports every function its header declares.
+These tests make no compute call and need no GPU."""
+import ctypes
+import subprocess
+
+import pytest
+
+from paper_1310_4374_gb300 import binding as B
+from paper_1310_4374_gb300 import build as _build
+
+
+def test_header_declares_the_boundary():
+    names = B.header_functions()
+    for required in ("psum_plan_create", "psum_plan_create_ex", "psum_eval", "psum_eval_host", "psum_sync",
+                     "psum_get_coeffs", "psum_plan_info", "psum_destroy", "psum_strerror", "psum_opts_default",
+                     "psum_profile", "psum_last_timings"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol():
+    path = _build.build()
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True, check=True).stdout
+    exported = {line.split()[-1] for line in out.splitlines() if line.strip()}
+    missing = [n for n in B.header_functions() if n not in exported]
+    assert not missing, missing
+    lib = B.load()
+    for n in B.header_functions():
+        assert hasattr(lib, n)
+
+
+def test_strerror_and_defaults_without_gpu():
+    assert B.psum_strerror(B.PSUM_OK) == "ok"
+    for s in range(1, 9):
+        assert B.psum_strerror(s) and B.psum_strerror(s) != "unknown status"
+    assert B.psum_strerror(99) == "unknown status"
+    o = B.psum_opts_default()
+    assert tuple(o.d) == (1.0, 1.0, 1.0) and o.p == 8 and o.M == 200 and tuple(o.K) == (1, 1, 1)
+    assert o.precision == B.PSUM_FP64 and o.mean_mode == B.PSUM_MEAN_ZERO
+
+
+@pytest.mark.parametrize("d,p,M,prec,K", [
+    ((1, 1, 1), 0, 200, "fp64", (1, 1, 1)),        # p < 1
+    ((1, 1, 1), 41, 5000, "fp64", (1, 1, 1)),      # p above the supported maximum
+    ((1, 1, 1), 8, 79, "fp64", (1, 1, 1)),         # M < P - 1 (rank condition)
+    ((1, -1, 1), 8, 200, "fp64", (1, 1, 1)),       # d <= 0
+    ((1, 1, float("nan")), 8, 200, "fp64", (1, 1, 1)),
+    ((1, 1, 1), 8, 200, 7, (1, 1, 1)),             # unknown precision
+    ((1, 1, 1), 8, 200, "fp64", (1, 4, 1)),        # K out of range
+])
+def test_invalid_plan_arguments_are_rejected_on_the_host(d, p, M, prec, K):
+    with pytest.raises(B.PsumError) as e:
+        B.psum_plan_create_ex(d, p, M, prec, "zero", K)
+    assert e.value.status == B.PSUM_ERR_ARG
+
+
+def test_null_arguments_are_rejected():
+    lib = B.load()
+    assert lib.psum_plan_create_ex(None, None) == B.PSUM_ERR_ARG
+    assert lib.psum_eval(None, 10, None, None, None, None, None) == B.PSUM_ERR_ARG
+    assert lib.psum_sync(None, None) == B.PSUM_ERR_ARG
+    assert lib.psum_plan_info(None, None) == B.PSUM_ERR_ARG
+    lib.psum_destroy(None)
+    h = ctypes.c_void_p()
+    assert lib.psum_plan_create(1.0, 1.0, 1.0, 8, 10, ctypes.byref(h)) == B.PSUM_ERR_ARG

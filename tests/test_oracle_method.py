@@ -202,3 +202,43 @@ def test_near_sum_reciprocity_and_gradient():
         e[0, k] = h
         fd = (O.near_sum(y + e, xs, qs, d, grad=False)[0] - O.near_sum(y - e, xs, qs, d, grad=False)[0]) / (2 * h)
         assert g[0, k] == pytest.approx(fd, rel=1e-6, abs=1e-7)
+
+
+def test_adjoint_gradients_are_the_exact_derivatives_of_the_discrete_energy():
+    # finite differences of E = 1/2 q.phi of the discrete method (at a low degree, where the
+    # method is far from symmetric) against the adjoint formula
+    rng = np.random.default_rng(16)
+    N = 10
+    d = (1.0, 1.2, 0.9)
+    x = rng.uniform(-0.5, 0.5, (N, 3)) * d
+    q = rng.normal(size=N)
+    q -= q.mean()
+    pl = O.Plan(d, 6, 100)
+    g = O.energy_and_gradients(pl, x, q)
+
+    def energy(xx, qq):
+        return 0.5 * float(np.dot(qq, pl.evaluate(xx, qq, grad=False)["phi"]))
+
+    h = 1e-6
+    for j in (0, 7):
+        for k in range(3):
+            xp, xm = x.copy(), x.copy()
+            xp[j, k] += h
+            xm[j, k] -= h
+            fd = (energy(xp, q) - energy(xm, q)) / (2 * h)
+            assert fd == pytest.approx(g["dEdx"][j, k], rel=2e-7, abs=1e-8)
+    for a, b in ((1, 4), (2, 9)):
+        qp, qm = q.copy(), q.copy()
+        qp[a] += h
+        qp[b] -= h
+        qm[a] -= h
+        qm[b] += h
+        fd = (energy(x, qp) - energy(x, qm)) / (2 * h)
+        assert fd == pytest.approx(g["dEdq"][a] - g["dEdq"][b], rel=2e-7, abs=1e-8)
+    # At a higher degree the method is nearly symmetric: psi is the far field of the
+    # images outside the near block, so it equals phi_far up to a constant (the zero-mean
+    # convention fixes the constant of phi_far) and the truncation error.
+    h14 = O.energy_and_gradients(O.Plan(d, 14, 500), x, q)
+    diff = h14["psi"] - h14["phi_far"]
+    assert np.std(diff) < 1e-5 * np.std(h14["phi_far"])
+    assert np.max(np.abs(h14["grad_psi"] - h14["grad_far"])) < 1e-4 * np.max(np.abs(h14["grad_far"]))
