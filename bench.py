@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU budget of the oracle sample")
+    ap.add_argument("--n", type=int, default=N_MAIN, help="charges (smaller cases are for profiling only)")
     return ap.parse_args()
 
 
@@ -117,9 +118,11 @@ def measured_peaks():
         return {}
 
 
-def near_kernel_traffic(n_pairs_launch):
-    """DRAM traffic per launch of the charge near-field kernel from the committed ncu
-    summary, scaled to this launch, if the kernel source has not changed since."""
+def near_kernel_traffic(n_points):
+    """DRAM bytes per launch of the charge near-field kernel from the committed ncu
+    summary (a smaller case), scaled to this launch by the number of points: the
+    traffic is the compulsory read of the packed sources, which stay in L2.  None if
+    the kernel source has changed since the counters were taken."""
     path = os.path.join(ROOT, "profiles", "near32_traffic.json")
     try:
         with open(path) as f:
@@ -128,7 +131,7 @@ def near_kernel_traffic(n_pairs_launch):
             h = hashlib.sha256(f.read()).hexdigest()[:16]
         if rec.get("near_cu_sha256_16") != h:
             return None
-        return rec["dram_bytes"] * n_pairs_launch / rec["pairs"]
+        return rec["dram_bytes"] * n_points / rec["n_points"]
     except Exception:
         return None
 
@@ -156,7 +159,7 @@ def run_psum(args):
             dist.barrier()
 
     # every rank evaluates its own replica of the system (weak scaling, no exchange)
-    s = W.uniform_gauss(N=N_MAIN, d=D_MAIN, p=P_MAIN, M=M_MAIN, seed=SEED_MAIN + rank)
+    s = W.uniform_gauss(N=args.n, d=D_MAIN, p=P_MAIN, M=M_MAIN, seed=SEED_MAIN + rank)
     pairs_step = 27 * s.N * (s.N + 2 * s.M)
     pc = B.PeriodicCoulomb(s.d, s.p, s.M, precision="fp32c")
     B.psum_profile(pc.plan, True)
@@ -214,7 +217,7 @@ def run_psum(args):
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     peak_ops = props.multi_processor_count * 128 * sm_max * 1e6
     achieved = FP32_OPS_PAIR_GRAD * near_pairs / (near_ms * 1e-3)
-    traffic = near_kernel_traffic(near_pairs)
+    traffic = near_kernel_traffic(s.N)
     roofline = {"bound": "alu", "kernel": "k_near32<grad>", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
                 "unit": "T FP32-pipe ops/s", "frac": achieved / peak_ops, "traffic": traffic,
                 "peak_source": f"{props.multi_processor_count} SMs x 128 FP32 lanes x {sm_max:.0f} MHz "
@@ -227,7 +230,7 @@ def run_psum(args):
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-           "config": {"workload": workload_name(), "N": s.N, "p": s.p, "M": s.M, "box": list(s.d),
+           "config": {"workload": workload_name(s.N), "N": s.N, "p": s.p, "M": s.M, "box": list(s.d),
                       "near_images": 27, "pairs_per_step": pairs_step,
                       "precision": "fp32c: f32 pair arithmetic on group-relative coordinates, two-sum "
                                    "compensated accumulation; f64 sort keys, fit, mean and far field",
@@ -335,12 +338,13 @@ def cpu_baseline_leg(s, phi_gpu, grad_gpu, args):
     pl = O.Plan(s.d, s.p, s.M)
     rng = np.random.default_rng(1234)
     # size the target sample from a short calibration run
-    probe = s.x[:16]
+    n_probe = max(64, 8 * O.num_threads())
+    probe = s.x[:n_probe]
     t0 = time.perf_counter()
     O.near_sum(probe, s.x, s.q, s.d, grad=True)
-    rate = 27 * s.N * 16 / (time.perf_counter() - t0)           # pairs/s
+    rate = 27 * s.N * n_probe / (time.perf_counter() - t0)      # pairs/s on all host cores
     n_check_pairs = 27 * s.N * 2 * s.M
-    n_t = int(max(16, min(4096, (args.cpu_seconds * rate - n_check_pairs) / (27 * s.N))))
+    n_t = int(max(64, min(16384, (args.cpu_seconds * rate - n_check_pairs) / (27 * s.N))))
     sample = np.sort(rng.choice(s.N, size=n_t, replace=False))
     t0 = time.perf_counter()
     ref = pl.evaluate(s.x, s.q, targets=s.x[sample])

@@ -74,30 +74,40 @@ template <bool kGrad>
 __device__ __forceinline__ void pair_loop_far(const float4* __restrict__ s_hi, const float2 (&nx)[2],
                                               const float2 (&ny)[2], const float2 (&nz)[2], float2 (&aphi)[2],
                                               float2 (&agx)[2], float2 (&agy)[2], float2 (&agz)[2]) {
-#pragma unroll 2
-    for (int s = 0; s < kNearChunk; ++s) {
-        const float4 A = s_hi[2 * s];       // x x y y
-        const float4 B = s_hi[2 * s + 1];   // z z q q
-        const float2 sq = make_float2(B.z, B.w);
+    // the potential, whose terms cancel most, goes into two interleaved partial sums
+    float2 bphi[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+#pragma unroll 1
+    for (int s = 0; s < kNearChunk; s += 2) {
 #pragma unroll
-        for (int j = 0; j < 2; ++j) {
-            const float2 ex = __fadd2_rn(make_float2(A.x, A.y), nx[j]);
-            const float2 ey = __fadd2_rn(make_float2(A.z, A.w), ny[j]);
-            const float2 ez = __fadd2_rn(make_float2(B.x, B.y), nz[j]);
-            float2 r2 = __fmul2_rn(ex, ex);
-            r2 = __ffma2_rn(ey, ey, r2);
-            r2 = __ffma2_rn(ez, ez, r2);
-            const float2 ri = make_float2(rsqrt_mufu(r2.x), rsqrt_mufu(r2.y));
-            const float2 qr = __fmul2_rn(sq, ri);
-            aphi[j] = __fadd2_rn(aphi[j], qr);
-            if (kGrad) {
-                const float2 w = __fmul2_rn(qr, __fmul2_rn(ri, ri));
-                agx[j] = __ffma2_rn(ex, w, agx[j]);
-                agy[j] = __ffma2_rn(ey, w, agy[j]);
-                agz[j] = __ffma2_rn(ez, w, agz[j]);
+        for (int h = 0; h < 2; ++h) {
+            const float4 A = s_hi[2 * (s + h)];       // x x y y
+            const float4 B = s_hi[2 * (s + h) + 1];   // z z q q
+            const float2 sq = make_float2(B.z, B.w);
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const float2 ex = __fadd2_rn(make_float2(A.x, A.y), nx[j]);
+                const float2 ey = __fadd2_rn(make_float2(A.z, A.w), ny[j]);
+                const float2 ez = __fadd2_rn(make_float2(B.x, B.y), nz[j]);
+                float2 r2 = __fmul2_rn(ex, ex);
+                r2 = __ffma2_rn(ey, ey, r2);
+                r2 = __ffma2_rn(ez, ez, r2);
+                const float2 ri = make_float2(rsqrt_mufu(r2.x), rsqrt_mufu(r2.y));
+                const float2 qr = __fmul2_rn(sq, ri);
+                if (h == 0)
+                    aphi[j] = __fadd2_rn(aphi[j], qr);
+                else
+                    bphi[j] = __fadd2_rn(bphi[j], qr);
+                if (kGrad) {
+                    const float2 w = __fmul2_rn(qr, __fmul2_rn(ri, ri));
+                    agx[j] = __ffma2_rn(ex, w, agx[j]);
+                    agy[j] = __ffma2_rn(ey, w, agy[j]);
+                    agz[j] = __ffma2_rn(ez, w, agz[j]);
+                }
             }
         }
     }
+    aphi[0] = __fadd2_rn(aphi[0], bphi[0]);
+    aphi[1] = __fadd2_rn(aphi[1], bphi[1]);
 }
 
 // Near units: one packed target pair at a time, offsets from hi + lo coordinates,

@@ -161,6 +161,23 @@ __global__ void k_pack32(const double* __restrict__ x, const double* __restrict_
         }
         o[c] = lo[c] <= hi[c] ? 0.5 * (lo[c] + hi[c]) : 0.0;
     }
+    // float32 charges with the rounding error diffused along the group (in sorted order):
+    // each charge absorbs the error carried so far, so the group's float32 charges sum to
+    // its float64 total up to one rounding; a non-neutral rounding residue would add the
+    // potential of a net charge over all images to every target.
+    float fqk[per];
+    double carry = 0.0;
+    for (int k = 0; k < per; ++k)
+        for (int l = 0; l < 32; ++l) {
+            float v = 0.f;
+            double nc = carry;
+            if (lane == l && ok[k]) {
+                v = (float)(pq[k] - carry);
+                nc = carry + ((double)v - pq[k]);
+                fqk[k] = v;
+            }
+            carry = __shfl_sync(0xffffffffu, nc, l);
+        }
     double r2max = 0.0;
 #pragma unroll
     for (int k = 0; k < per; ++k) {
@@ -171,7 +188,7 @@ __global__ void k_pack32(const double* __restrict__ x, const double* __restrict_
             r2max = fmax(r2max, rx * rx + ry * ry + rz * rz);
             fx = (float)rx; fy = (float)ry; fz = (float)rz;
             lx = (float)(rx - (double)fx); ly = (float)(ry - (double)fy); lz = (float)(rz - (double)fz);
-            fq = (float)pq[k];
+            fq = fqk[k];
         }
         pk_hi[2 * s] = make_float4(fx, fx, fy, fy);
         pk_hi[2 * s + 1] = make_float4(fz, fz, fq, fq);
