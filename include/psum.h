@@ -125,6 +125,29 @@ int psum_eval(psum_plan_t plan, int64_t N, const double *x, const double *q,
 int psum_eval_host(psum_plan_t plan, int64_t N, const double *x, const double *q,
                    double *phi, double *grad, void *stream);
 
+/* psum_eval without any allocation at evaluation time.  The paper has no counterpart:
+ * this entry exists for callers that cannot call cudaMalloc when they evaluate --
+ * code running inside a CUDA stream capture (an allocation there breaks the graph
+ * being recorded), real-time loops that cannot take the device-wide synchronisation
+ * of a cudaMalloc or cudaFree, and runtimes that own all device memory through their
+ * own pool.  psum_eval grows a per-plan scratch buffer with cudaMalloc the first time
+ * it sees a size; this call instead takes all of its scratch from one 16 MiB device
+ * array inside the library, which every GPU that loads the library holds until the
+ * process exits.  It calls no cudaMalloc, cudaFree or allocating library routine.
+ *
+ * Arguments, results and status reporting are those of psum_eval (device pointers,
+ * queued on `stream`, device-side conditions reported by psum_sync).  The results
+ * agree with psum_eval to rounding: the pair sum is split over at most 256 CTAs, so
+ * partial sums are grouped differently.  Limits: an evaluation whose scratch does not
+ * fit in the 16 MiB array returns PSUM_ERR_ARG; that holds up to N = 32768 charges
+ * for plans with p <= 16 and M <= 800 in either precision (larger p or M lower it).
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress);
+ * make that first call before any stream capture.  All calls share the one array:
+ * calls whose work overlaps on the GPU (other streams, other plans, other threads)
+ * race and corrupt each other's results -- serialise them, e.g. on one stream. */
+int psum_eval_noalloc(psum_plan_t plan, int64_t N, const double *x, const double *q,
+                      double *phi, double *grad, void *stream);
+
 /* Wait for `stream`, then return and clear the plan's device status word. */
 int psum_sync(psum_plan_t plan, void *stream);
 

@@ -78,6 +78,7 @@ def load(build_if_needed: bool = True):
     lib.psum_plan_create_ex.argtypes = [ctypes.POINTER(psum_opts), ctypes.POINTER(_vp)]
     lib.psum_eval.argtypes = [_vp, ctypes.c_int64, _vp, _vp, _vp, _vp, _vp]
     lib.psum_eval_host.argtypes = [_vp, ctypes.c_int64, _vp, _vp, _vp, _vp, _vp]
+    lib.psum_eval_noalloc.argtypes = [_vp, ctypes.c_int64, _vp, _vp, _vp, _vp, _vp]
     lib.psum_sync.argtypes = [_vp, _vp]
     lib.psum_get_coeffs.argtypes = [_vp, _dp, _vp]
     lib.psum_plan_info.argtypes = [_vp, ctypes.POINTER(psum_info)]
@@ -90,7 +91,8 @@ def load(build_if_needed: bool = True):
     lib.psum_destroy.restype = None
     lib.psum_strerror.argtypes = [ctypes.c_int]
     lib.psum_strerror.restype = ctypes.c_char_p
-    for name in ("psum_plan_create", "psum_plan_create_ex", "psum_eval", "psum_eval_host", "psum_sync",
+    for name in ("psum_plan_create", "psum_plan_create_ex", "psum_eval", "psum_eval_host", "psum_eval_noalloc",
+                 "psum_sync",
                  "psum_get_coeffs", "psum_plan_info", "psum_profile", "psum_last_timings", "psum_launch_count",
                  "psum_energy", "psum_energy_backward"):
         getattr(lib, name).restype = ctypes.c_int
@@ -162,6 +164,20 @@ def psum_eval(plan, x, q, phi, grad=None, stream=None, check: bool = False) -> i
     _check(s, "psum_eval")
     if check:
         _check(psum_sync(plan, st), "psum_eval (device)")
+    return s
+
+
+def psum_eval_noalloc(plan, x, q, phi, grad=None, stream=None, check: bool = False) -> int:
+    """psum_eval with all scratch taken from the library's static device array (no allocation)."""
+    for t in (x, q, phi) + ((grad,) if grad is not None else ()):
+        if not (t.is_cuda and t.is_contiguous()):
+            raise ValueError("psum_eval_noalloc takes contiguous CUDA tensors")
+    st = _stream_ptr(stream)
+    s = load().psum_eval_noalloc(plan, int(q.numel()), x.data_ptr(), q.data_ptr(), phi.data_ptr(),
+                                 grad.data_ptr() if grad is not None else None, st)
+    _check(s, "psum_eval_noalloc")
+    if check:
+        _check(psum_sync(plan, st), "psum_eval_noalloc (device)")
     return s
 
 

@@ -125,7 +125,7 @@ struct Layout {
 
 // Lay out the scratch buffer for N charges; with base == nullptr only the size is computed.
 // `backward` adds the buffers of the energy derivatives.
-size_t layout(Plan& pl, int64_t N, char* base, Layout& L, bool backward = false) {
+size_t layout(Plan& pl, int64_t N, char* base, Layout& L, bool backward = false, int64_t g_cap = 0) {
     Bump b{base, 0, 0};
     const bool fp32 = pl.opt.precision == PSUM_FP32C;
     const int n_img = pl.n_images;
@@ -134,7 +134,8 @@ size_t layout(Plan& pl, int64_t N, char* base, Layout& L, bool backward = false)
         L.n_chunks = (N + kNearChunk - 1) / kNearChunk;
         const int64_t n_groups = L.n_tiles * kTgt32;
         L.n_pts = n_groups * kNearChunk;
-        const int64_t gmax = (int64_t)pl.num_sms * near32_occupancy_ctas(n_img);
+        int64_t gmax = (int64_t)pl.num_sms * near32_occupancy_ctas(n_img);
+        if (g_cap > 0 && gmax > g_cap) gmax = g_cap;
         L.Ln = near_partition(L.n_tiles, L.n_chunks, n_img, gmax);
         L.Lc = near_partition(pl.n_check_tiles, L.n_chunks, n_img, gmax);
         L.ka = b.take<uint32_t>(N);
@@ -153,7 +154,8 @@ size_t layout(Plan& pl, int64_t N, char* base, Layout& L, bool backward = false)
         L.n_tiles = (N + kTile64 - 1) / kTile64;
         L.n_chunks = L.n_tiles;
         L.n_pts = L.n_tiles * kTile64;
-        const int64_t gmax = (int64_t)pl.num_sms * near64_occupancy_ctas();
+        int64_t gmax = (int64_t)pl.num_sms * near64_occupancy_ctas();
+        if (g_cap > 0 && gmax > g_cap) gmax = g_cap;
         L.Ln = near_partition(L.n_tiles, L.n_chunks, n_img, gmax);
         L.Lc = near_partition(pl.n_check_tiles, L.n_chunks, n_img, gmax);
         L.ka = L.va = L.kb = L.vb = L.hist = nullptr;
@@ -536,6 +538,122 @@ void psum_destroy(psum_plan_t h) {
     }
     delete h;
 }
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free evaluation (psum_eval_noalloc).
+//
+// Some callers cannot call cudaMalloc at evaluation time: code that runs inside a
+// CUDA stream capture (a graph is being recorded and an allocation would break
+// it), real-time loops that cannot afford the device-wide synchronisation a
+// cudaMalloc/cudaFree implies, and runtimes that hand out all device memory from
+// their own pool.  psum_eval grows its scratch with cudaMalloc the first time a size
+// is seen; this variant instead takes all scratch from one file-scope device array
+// of kNoAllocBytes, which every GPU that loads the library holds until exit.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr size_t kNoAllocBytes = (size_t)16 << 20;     // 16 MiB
+constexpr int64_t kNoAllocMaxCtas = 256;                // stream-K width: bounds the partial sums
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+constexpr int kNoAllocMaxDevices = 64;
+void* g_noalloc_addr[kNoAllocMaxDevices] = {};          // device address of the array, per device
+
+// Once per device, with that device current: the array's name is only a host-side
+// stand-in, so its device address must be looked up before a kernel may use it.
+int noalloc_scratch(int dev, char** out) {
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return PSUM_ERR_ARG;
+    if (!g_noalloc_addr[dev]) {
+        void* ptr = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+        if (e != cudaSuccess || !ptr) return PSUM_ERR_CUDA;
+        g_noalloc_addr[dev] = ptr;
+    }
+    *out = (char*)g_noalloc_addr[dev];
+    return PSUM_OK;
+}
+
+int eval_noalloc_device(psum_plan_s* h, int64_t N, const double* x, const double* q, double* phi, double* grad,
+                        cudaStream_t st) {
+    Plan& pl = h->pl;
+    const psum_opts& o = pl.opt;
+    char* base = nullptr;
+    int rs = noalloc_scratch(pl.device, &base);
+    if (rs != PSUM_OK) return rs;
+    Layout L;
+    if (layout(pl, N, nullptr, L, false, kNoAllocMaxCtas) > kNoAllocBytes) return PSUM_ERR_ARG;
+    layout(pl, N, base, L, false, kNoAllocMaxCtas);
+    const bool fp32 = o.precision == PSUM_FP32C;
+    const int M = o.M, P = pl.P;
+    if (h->profile) TRY(cudaEventRecord(h->ev[0], st));
+    // the array keeps the previous call's contents: the status word must start at zero;
+    // every other buffer is written before it is read
+    TRY(cudaMemsetAsync(L.eval_status, 0, sizeof(int), st));
+    TRY(launch_validate(x, q, N, o.d, L.val_part, L.nblk_val, L.eval_status, st));
+    h->launches += 2;
+    const int* perm = nullptr;
+    if (fp32) {
+        TRY(launch_morton_sort(x, N, o.d, L.ka, L.va, L.kb, L.vb, L.hist, st));
+        perm = (const int*)L.va;
+        TRY(launch_pack32(x, q, L.va, N, L.n_tiles * kTgt32, L.pk32, L.pk32lo, L.org, st));
+        h->launches += 1 + 4 * 3 + 1;
+    } else {
+        TRY(launch_pack64(x, q, N, L.n_pts, L.pk64, st));
+        h->launches += 1;
+    }
+    if (h->profile) TRY(cudaEventRecord(h->ev[1], st));
+    if (fp32)
+        TRY(launch_near32(true, L.pk32, L.pk32lo, L.org, L.n_chunks, L.pk32, L.pk32lo, L.org, L.n_tiles,
+                          pl.d_shifts, pl.n_images, L.part_n, L.Ln, st));
+    else
+        TRY(launch_near64(true, L.pk64, L.n_chunks, L.pk64, L.n_tiles, pl.d_shifts, pl.n_images, L.part_n, L.Ln, st));
+    if (h->profile) TRY(cudaEventRecord(h->ev[2], st));
+    if (fp32) {
+        const float4* ct = (const float4*)pl.d_check_tgt;
+        const size_t half = 2 * (size_t)pl.n_check_tiles * kTile32;
+        TRY(launch_near32(false, L.pk32, L.pk32lo, L.org, L.n_chunks, ct, ct + half, pl.d_check_org,
+                          pl.n_check_tiles, pl.d_shifts, pl.n_images, L.part_c, L.Lc, st));
+    } else {
+        TRY(launch_near64(false, L.pk64, L.n_chunks, (const double4_32a*)pl.d_check_tgt, pl.n_check_tiles,
+                          pl.d_shifts, pl.n_images, L.part_c, L.Lc, st));
+    }
+    if (h->profile) TRY(cudaEventRecord(h->ev[3], st));
+    const int tile = fp32 ? kTile32 : kTile64;
+    TRY(launch_near_reduce(L.part_n, N, tile, 4, L.Ln, L.phi_n, L.grad_n, st));
+    TRY(launch_near_reduce(L.part_c, pl.n_check, tile, 1, L.Lc, L.phi_c, nullptr, st));
+    h->launches += 4;
+    const bool zero_mean = o.mean_mode == PSUM_MEAN_ZERO;
+    if (zero_mean) {
+        const double H[3] = {0.5 * (2 * o.K[0] + 1) * o.d[0], 0.5 * (2 * o.K[1] + 1) * o.d[1],
+                             0.5 * (2 * o.K[2] + 1) * o.d[2]};
+        TRY(launch_box_mean(x, q, N, H, L.mean_part, L.nblk_mean, st));
+        h->launches += 1;
+    }
+    TRY(launch_project(pl.d_pinv, P - 1, M, L.phi_c, pl.d_check_pos, L.f, pl.d_C, st));
+    TRY(launch_constant(pl.d_C, pl.d_Rbox, P, L.mean_part, L.nblk_mean, 1.0 / (o.d[0] * o.d[1] * o.d[2]),
+                        zero_mean ? 1 : 0, st));
+    if (h->profile) TRY(cudaEventRecord(h->ev[4], st));
+    TRY(launch_far_combine(x, N, perm, L.phi_n, grad ? L.grad_n : nullptr, pl.d_C, o.p, 1.0 / pl.R0,
+                           L.eval_status, phi, grad, L.eval_status, st));
+    k_status_merge<<<1, 1, 0, st>>>(L.eval_status, pl.d_status);
+    TRY(cudaGetLastError());
+    h->launches += 5;
+    if (h->profile) TRY(cudaEventRecord(h->ev[5], st));
+    return PSUM_OK;
+}
+
+}  // namespace
+
+extern "C" int psum_eval_noalloc(psum_plan_t h, int64_t N, const double* x, const double* q, double* phi,
+                                 double* grad, void* stream) {
+    if (!h || N < 1 || N > (int64_t)1 << 30 || !x || !q || !phi) return PSUM_ERR_ARG;
+    DeviceGuard g(h->pl.device);
+    return eval_noalloc_device(h, N, x, q, phi, grad, (cudaStream_t)stream);
+}
+
+extern "C" {
 
 const char* psum_strerror(int s) {
     switch (s) {
