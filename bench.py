@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-backward", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU budget of the oracle sample")
     ap.add_argument("--n", type=int, default=N_MAIN, help="charges (smaller cases are for profiling only)")
     return ap.parse_args()
@@ -108,6 +110,22 @@ class ClockSampler:
         loaded = [s for s, p in zip(sm, power)] if sm else []
         return {"sm_mhz": statistics.median(loaded) if loaded else None, "sm_max_mhz": mx,
                 "samples": len(rows), "power_w_max": max(power) if power else None, "reasons": reasons}
+
+
+def max_over_ranks(value: float, dist=None, device="cpu") -> float:
+    """The largest value over all ranks (every rank gets it); the value itself without a group."""
+    if dist is None or not dist.is_initialized():
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(pairs_per_rank_step: int, world: int, steps: int, total_ms_max: float) -> float:
+    """Whole-job pairs/s: every rank evaluates its own system (weak scaling), timed by the
+    slowest rank."""
+    return pairs_per_rank_step * world * steps / (total_ms_max * 1e-3)
 
 
 def measured_peaks():
@@ -201,13 +219,9 @@ def run_psum(args):
     st = B.psum_sync(pc.plan, stream)
     if st != B.PSUM_OK:
         raise B.PsumError(st, "timed steps")
-    total_ms = sum(step_ms)
-    t_max = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-    if dist is not None:
-        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
-    total_ms = float(t_max.item())
+    total_ms = max_over_ranks(sum(step_ms), dist, device=dev)
     ms_per_step = total_ms / args.steps
-    value = pairs_step * world * args.steps / (total_ms * 1e-3)
+    value = job_throughput(pairs_step, world, args.steps, total_ms)
 
     # dominant kernel: the near-field sum at the charges (potential + gradient)
     near_ms = statistics.mean(t["near_charges"] for t in stage_ms)
@@ -228,6 +242,7 @@ def run_psum(args):
         roofline["frac_at_observed_clock"] = achieved / (props.multi_processor_count * 128 * clk["sm_mhz"] * 1e6)
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "step_ms": step_ms,
            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": workload_name(s.N), "N": s.N, "p": s.p, "M": s.M, "box": list(s.d),
@@ -244,6 +259,10 @@ def run_psum(args):
         out["e2e"] = e2e_leg(pc, s, args)
     if rank == 0 and not args.no_fp64:
         out["fp64"] = fp64_leg(args)
+    if rank == 0 and not args.no_batch:
+        out["batch"] = batch_leg(args)
+    if rank == 0 and not args.no_backward:
+        out["backward"] = backward_leg(args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline_leg(s, phi, grad, args)
     pc.close()
@@ -326,6 +345,95 @@ def fp64_leg(args):
     res["eps2_fp32c_vs_fp64"] = {"phi": rel(outs["fp32c"][0], outs["fp64"][0]),
                                  "grad": rel(outs["fp32c"][1], outs["fp64"][1])}
     return res
+
+
+def batch_leg(args):
+    """256 independent +-1 systems (N log-uniform in [500, 20000], boxes (1, U[1,2], U[1,2]),
+    p in {8, 12, 16}) in one batched evaluation replayed from a CUDA graph."""
+    import numpy as np
+    import torch
+
+    from paper_1310_4374_gb300 import binding as B
+    from paper_1310_4374_gb300 import workloads as W
+
+    systems = W.config(4)
+    t0 = time.perf_counter()
+    pb = B.PeriodicBatch(systems, precision="fp32c")
+    t_plans = time.perf_counter() - t0
+    try:
+        x = torch.as_tensor(np.concatenate([s.x for s in systems]), dtype=torch.float64, device="cuda")
+        q = torch.as_tensor(np.concatenate([s.q for s in systems]), dtype=torch.float64, device="cuda")
+        phi = torch.empty_like(q)
+        grad = torch.empty_like(x)
+        for _ in range(max(args.warmup, 1)):
+            pb(x, q, phi, grad, use_graph=True)
+        info = B.psum_batch_get_info(pb.batch)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = max(1, min(args.steps, 3))
+        torch.cuda.synchronize()
+        ev0.record()
+        for _ in range(reps):
+            B.psum_batch_eval(pb.batch, x, q, phi, grad, use_graph=True)
+        ev1.record()
+        torch.cuda.synchronize()
+        first, _ = B.psum_batch_sync(pb.batch, pb.B)
+        if first != B.PSUM_OK:
+            raise B.PsumError(first, "batch leg")
+        ms = ev0.elapsed_time(ev1) / reps
+    finally:
+        pb.close()
+    return {"workload": f"{len(systems)} systems, N log-uniform in [500, 20000] (total {info['N_total']}), "
+                        "d = (1, U[1,2], U[1,2]), p in {8,12,16}, +-1 charges, fp32c, CUDA graph",
+            "pairs_per_s": info["pairs"] / (ms * 1e-3), "systems_per_s": len(systems) / (ms * 1e-3),
+            "ms_per_step": ms, "pairs_per_step": info["pairs"], "ctas": info["ctas"],
+            "autotuned_variant": info["variant"], "plan_setup_s": t_plans}
+
+
+def backward_leg(args):
+    """Energy, forces and dE/dq of 100k tight dipoles (200k charges) in the (1, 1, 2) box,
+    p = 16, M = 800, fp32c: forward psum_eval + psum_energy + psum_energy_backward."""
+    import torch
+
+    from paper_1310_4374_gb300 import binding as B
+    from paper_1310_4374_gb300 import workloads as W
+
+    s = W.config(5)
+    pc = B.PeriodicCoulomb(s.d, s.p, s.M, precision="fp32c")
+    try:
+        x = torch.as_tensor(s.x, dtype=torch.float64, device="cuda")
+        q = torch.as_tensor(s.q, dtype=torch.float64, device="cuda")
+        phi = torch.empty_like(q)
+        grad = torch.empty_like(x)
+        E = torch.empty(1, dtype=torch.float64, device="cuda")
+        dEdq = torch.empty_like(q)
+        dEdx = torch.empty_like(x)
+
+        def step():
+            B.psum_eval(pc.plan, x, q, phi, grad)
+            B.psum_energy(pc.plan, q, phi, E)
+            B.psum_energy_backward(pc.plan, x, q, phi, grad, None, dEdq, dEdx)
+
+        step()
+        torch.cuda.synchronize()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        ev[0].record()
+        B.psum_eval(pc.plan, x, q, phi, grad)
+        B.psum_energy(pc.plan, q, phi, E)
+        ev[1].record()
+        B.psum_energy_backward(pc.plan, x, q, phi, grad, None, dEdq, dEdx)
+        ev[2].record()
+        torch.cuda.synchronize()
+        st = B.psum_sync(pc.plan)
+        if st != B.PSUM_OK:
+            raise B.PsumError(st, "backward leg")
+        fwd, bwd = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
+    finally:
+        pc.close()
+    pairs_f = 27 * s.N * (s.N + 2 * s.M)
+    pairs_b = 27 * s.N * 2 * s.M
+    return {"workload": "100k dipole pairs (200k charges, +-0.8, separation 0.01), d = (1,1,2), p = 16, M = 800, fp32c",
+            "forward_ms": fwd, "backward_ms": bwd, "pairs_per_s": (pairs_f + pairs_b) / ((fwd + bwd) * 1e-3),
+            "pairs_forward": pairs_f, "pairs_backward": pairs_b}
 
 
 def cpu_baseline_leg(s, phi_gpu, grad_gpu, args):

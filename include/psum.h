@@ -191,6 +191,48 @@ int psum_last_timings(psum_plan_t plan, double *ms, void *stream);
 /* Number of CUDA kernels this plan has queued since it was created. */
 int psum_launch_count(psum_plan_t plan, int64_t *count);
 
+/* ---- batches of independent systems -------------------------------------- */
+typedef struct psum_batch_s *psum_batch_t;
+
+typedef struct psum_batch_info {
+    int B;               /* systems */
+    int64_t N_total;     /* charges over all systems */
+    int64_t units;       /* (tile, chunk, image) work units of the charge pair sum */
+    int64_t pairs;       /* pair interactions of one evaluation (charges and check points) */
+    int ctas;            /* CTAs of the persistent pair-sum launch */
+    int variant;         /* pair-kernel variant chosen by the autotuner */
+    double tuned_ms;     /* its measured time for one charge pair sum, ms (0 before tuning) */
+} psum_batch_info;
+
+/* B independent periodic systems evaluated together (algorithm "get" for each), with one
+ * persistent stream-K launch for all charge pair sums and one for all check-point pair
+ * sums.  plans[b] fixes system b's box, degree, check points and near block; all plans
+ * must share the precision and the current device (a plan may appear several times).
+ * offsets (host, B+1 entries, offsets[0] = 0, increasing) delimit system b's charges in
+ * the concatenated arrays: rows offsets[b] .. offsets[b+1]-1.  1 <= B <= 256.  All
+ * device memory of the batch is allocated here.  The plans must outlive the batch. */
+int psum_batch_create(const psum_plan_t *plans, int B, const int64_t *offsets, psum_batch_t *out);
+
+/* psum_eval for every system: x (N_total x 3), q, phi, grad (may be NULL) are device
+ * arrays over the concatenated charges.  The first evaluation times the pair-kernel
+ * variants on these inputs and keeps the fastest (cached per batch shape).  With
+ * use_graph != 0 the whole sequence is captured once into a CUDA graph for these
+ * pointers and replayed on `stream` afterwards (a capture for new pointers replaces it). */
+int psum_batch_eval(psum_batch_t batch, const double *x, const double *q, double *phi,
+                    double *grad, int use_graph, void *stream);
+
+/* Wait for `stream`; write the per-system status codes to status (host, B entries, may
+ * be NULL), clear them, and return the first non-zero one. */
+int psum_batch_sync(psum_batch_t batch, int *status, void *stream);
+
+/* System b's P coefficients of the last evaluation (host array), as psum_get_coeffs. */
+int psum_batch_get_coeffs(psum_batch_t batch, int b, double *C, void *stream);
+
+int psum_batch_get_info(psum_batch_t batch, psum_batch_info *info);
+
+/* Release the batch (waits for the device). NULL is a no-op. */
+void psum_batch_destroy(psum_batch_t batch);
+
 /* Release the plan and its device memory (waits for the device). NULL is a no-op. */
 void psum_destroy(psum_plan_t plan);
 

@@ -51,6 +51,15 @@ class psum_info(ctypes.Structure):
                 "n_images": self.n_images, "precision": self.precision, "mean_mode": self.mean_mode}
 
 
+class psum_batch_info(ctypes.Structure):
+    _fields_ = [("B", ctypes.c_int), ("N_total", ctypes.c_int64), ("units", ctypes.c_int64),
+                ("pairs", ctypes.c_int64), ("ctas", ctypes.c_int), ("variant", ctypes.c_int),
+                ("tuned_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class PsumError(RuntimeError):
     def __init__(self, status: int, what: str = ""):
         self.status = status
@@ -87,6 +96,14 @@ def load(build_if_needed: bool = True):
     lib.psum_launch_count.argtypes = [_vp, ctypes.POINTER(ctypes.c_int64)]
     lib.psum_energy.argtypes = [_vp, ctypes.c_int64, _vp, _vp, _vp, _vp]
     lib.psum_energy_backward.argtypes = [_vp, ctypes.c_int64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
+    lib.psum_batch_create.argtypes = [ctypes.POINTER(_vp), ctypes.c_int, ctypes.POINTER(ctypes.c_int64),
+                                      ctypes.POINTER(_vp)]
+    lib.psum_batch_eval.argtypes = [_vp, _vp, _vp, _vp, _vp, ctypes.c_int, _vp]
+    lib.psum_batch_sync.argtypes = [_vp, ctypes.POINTER(ctypes.c_int), _vp]
+    lib.psum_batch_get_coeffs.argtypes = [_vp, ctypes.c_int, _dp, _vp]
+    lib.psum_batch_get_info.argtypes = [_vp, ctypes.POINTER(psum_batch_info)]
+    lib.psum_batch_destroy.argtypes = [_vp]
+    lib.psum_batch_destroy.restype = None
     lib.psum_destroy.argtypes = [_vp]
     lib.psum_destroy.restype = None
     lib.psum_strerror.argtypes = [ctypes.c_int]
@@ -94,7 +111,8 @@ def load(build_if_needed: bool = True):
     for name in ("psum_plan_create", "psum_plan_create_ex", "psum_eval", "psum_eval_host", "psum_eval_noalloc",
                  "psum_sync",
                  "psum_get_coeffs", "psum_plan_info", "psum_profile", "psum_last_timings", "psum_launch_count",
-                 "psum_energy", "psum_energy_backward"):
+                 "psum_energy", "psum_energy_backward", "psum_batch_create", "psum_batch_eval",
+                 "psum_batch_sync", "psum_batch_get_coeffs", "psum_batch_get_info"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -245,6 +263,91 @@ def psum_launch_count(plan) -> int:
 def psum_destroy(plan):
     if plan:
         load().psum_destroy(plan)
+
+
+def psum_batch_create(plans, offsets):
+    arr = (_vp * len(plans))(*[p.value if isinstance(p, _vp) else p for p in plans])
+    off = (ctypes.c_int64 * len(offsets))(*[int(v) for v in offsets])
+    h = _vp()
+    _check(load().psum_batch_create(arr, len(plans), off, ctypes.byref(h)), "psum_batch_create")
+    return h
+
+
+def psum_batch_eval(batch, x, q, phi, grad=None, use_graph: bool = False, stream=None) -> int:
+    for t in (x, q, phi) + ((grad,) if grad is not None else ()):
+        if not (t.is_cuda and t.is_contiguous()):
+            raise ValueError("psum_batch_eval takes contiguous CUDA tensors")
+    s = load().psum_batch_eval(batch, x.data_ptr(), q.data_ptr(), phi.data_ptr(),
+                               grad.data_ptr() if grad is not None else None, 1 if use_graph else 0,
+                               _stream_ptr(stream))
+    _check(s, "psum_batch_eval")
+    return s
+
+
+def psum_batch_sync(batch, B: int, stream=None):
+    """(first status, per-system statuses)."""
+    st = (ctypes.c_int * B)()
+    first = load().psum_batch_sync(batch, st, _stream_ptr(stream))
+    return first, list(st)
+
+
+def psum_batch_get_coeffs(batch, b: int, P: int, stream=None):
+    import numpy as np
+    out = np.zeros(P, dtype=np.float64)
+    _check(load().psum_batch_get_coeffs(batch, int(b), out.ctypes.data_as(_dp), _stream_ptr(stream)),
+           "psum_batch_get_coeffs")
+    return out
+
+
+def psum_batch_get_info(batch) -> dict:
+    info = psum_batch_info()
+    _check(load().psum_batch_get_info(batch, ctypes.byref(info)), "psum_batch_get_info")
+    return info.as_dict()
+
+
+def psum_batch_destroy(batch):
+    if batch:
+        load().psum_batch_destroy(batch)
+
+
+class PeriodicBatch:
+    """Many independent systems (each with its own plan) evaluated together."""
+
+    def __init__(self, systems, precision="fp32c", mean="zero"):
+        self.plans = [psum_plan_create_ex(s.d, s.p, s.M, precision, mean) for s in systems]
+        self.P = [psum_plan_info(p)["P"] for p in self.plans]
+        self.offsets = [0]
+        for s in systems:
+            self.offsets.append(self.offsets[-1] + s.N)
+        self.batch = psum_batch_create(self.plans, self.offsets)
+        self.B = len(systems)
+
+    def __call__(self, x, q, phi=None, grad=None, use_graph=False, stream=None, check=True):
+        import torch
+        N = self.offsets[-1]
+        if phi is None:
+            phi = torch.empty(N, dtype=torch.float64, device=x.device)
+        if grad is None:
+            grad = torch.empty((N, 3), dtype=torch.float64, device=x.device)
+        psum_batch_eval(self.batch, x, q, phi, grad, use_graph, stream)
+        if check:
+            first, _ = psum_batch_sync(self.batch, self.B, stream)
+            _check(first, "psum_batch_eval (device)")
+        return phi, grad
+
+    def close(self):
+        if self.batch:
+            psum_batch_destroy(self.batch)
+            self.batch = None
+        for p in self.plans:
+            psum_destroy(p)
+        self.plans = []
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class PeriodicCoulomb:

@@ -7,67 +7,10 @@
 
 #include "psum_internal.cuh"
 
-namespace psum {
-// near.cu
-cudaError_t launch_near32(bool grad, const float4* src_hi, const float4* src_lo, const double* src_org,
-                          int64_t n_chunks, const float4* tgt_hi, const float4* tgt_lo, const double* tgt_org,
-                          int64_t n_tiles, const double* shifts, int n_img, double* partial,
-                          const NearPlanLaunch& L, cudaStream_t st);
-cudaError_t launch_near64(bool grad, const double4_32a* src, int64_t n_chunks, const double4_32a* tgt, int64_t n_tiles,
-                          const double* shifts, int n_img, double* partial, const NearPlanLaunch& L,
-                          cudaStream_t st);
-cudaError_t launch_near_reduce(const double* partial, int64_t n_valid, int tile_size, int nq,
-                               const NearPlanLaunch& L, double* out_phi, double* out_grad, cudaStream_t st);
-int near32_occupancy_ctas(int n_img);
-int near64_occupancy_ctas();
-// sort.cu
-int sort_blocks(int64_t n);
-cudaError_t launch_morton_sort(const double* x, int64_t n, const double d[3], uint32_t* ka, uint32_t* va,
-                               uint32_t* kb, uint32_t* vb, uint32_t* hist, cudaStream_t st);
-cudaError_t launch_pack32(const double* x, const double* q, const uint32_t* perm, int64_t n, int64_t n_groups,
-                          float4* pk_hi, float4* pk_lo, double* org, cudaStream_t st);
-cudaError_t launch_pack64(const double* x, const double* q, int64_t n, int64_t n_pad, double4_32a* pk, cudaStream_t st);
-// far.cu
-int reduce_blocks(int64_t n, int num_sms);
-cudaError_t launch_validate(const double* x, const double* q, int64_t n, const double d[3], double* partial,
-                            int nblk, int* status, cudaStream_t st);
-cudaError_t launch_box_mean(const double* x, const double* q, int64_t n, const double H[3], double* partial,
-                            int nblk, cudaStream_t st);
-cudaError_t launch_project(const double* pinv, int rows, int M, const double* phi_check, const int* check_pos,
-                           double* f, double* C, cudaStream_t st);
-cudaError_t launch_constant(double* C, const double* Rbox, int P, const double* mean_partial, int nblk,
-                            double inv_V0, int zero_mean, cudaStream_t st);
-cudaError_t launch_far_combine(const double* x, int64_t n, const int* perm, const double* phi_near,
-                               const double* grad_near, const double* C, int p, double inv_R0, const int* status,
-                               double* phi, double* grad, int* status_out, cudaStream_t st);
-// backward.cu
-cudaError_t launch_moments(const double* x, const double* q, int64_t n, const double* C, int p, double inv_R0,
-                           double* far_phi, double* far_grad, double* w_partial, int nblk, double* w,
-                           cudaStream_t st);
-int moments_blocks(int64_t n);
-size_t moments_smem(int p);
-cudaError_t launch_adjoint(const double* pinv, int rows, int M, const double* w, double* u, cudaStream_t st);
-cudaError_t launch_check_sources32(const float4* chk_hi, const int* inv, int64_t n_pts, int M, const double* u,
-                                   float4* out_hi, cudaStream_t st);
-cudaError_t launch_check_sources64(const double4_32a* chk, int64_t n_pts, int M, const double* u,
-                                   double4_32a* out, cudaStream_t st);
-cudaError_t launch_backward_combine(int64_t n, const int* perm, const double* q, const double* phi,
-                                    const double* grad, const double* far_phi, const double* far_grad,
-                                    const double* psi, const double* gpsi, const double* gE, double* dEdq,
-                                    double* dEdx, cudaStream_t st);
-cudaError_t launch_energy(const double* q, const double* phi, int64_t n, double* partial, int nblk, double* E,
-                          cudaStream_t st);
-cudaError_t set_moments_smem(size_t bytes);
-}  // namespace psum
+#include "launch.cuh"
 
 using namespace psum;
 
-struct psum_plan_s {
-    Plan pl;
-    int64_t launches = 0;
-    bool profile = false;
-    cudaEvent_t ev[6] = {};
-};
 
 namespace {
 
@@ -259,20 +202,19 @@ int eval_device(psum_plan_s* h, int64_t N, const double* x, const double* q, dou
     }
     if (h->profile) TRY(cudaEventRecord(h->ev[1], st));
     if (fp32) {
-        TRY(launch_near32(true, L.pk32, L.pk32lo, L.org, L.n_chunks, L.pk32, L.pk32lo, L.org, L.n_tiles,
-                          pl.d_shifts, pl.n_images, L.part_n, L.Ln, st));
+        TRY(launch_near32(true, L.pk32, L.pk32lo, L.org, L.pk32, L.pk32lo, L.org, pl.d_shifts, L.part_n, L.Ln,
+                          st));
     } else {
-        TRY(launch_near64(true, L.pk64, L.n_chunks, L.pk64, L.n_tiles, pl.d_shifts, pl.n_images, L.part_n, L.Ln, st));
+        TRY(launch_near64(true, L.pk64, L.pk64, pl.d_shifts, L.part_n, L.Ln, st));
     }
     if (h->profile) TRY(cudaEventRecord(h->ev[2], st));
     if (fp32) {
         const float4* ct = (const float4*)pl.d_check_tgt;
         const size_t half = 2 * (size_t)pl.n_check_tiles * kTile32;    // hi parts, then lo parts
-        TRY(launch_near32(false, L.pk32, L.pk32lo, L.org, L.n_chunks, ct, ct + half, pl.d_check_org,
-                          pl.n_check_tiles, pl.d_shifts, pl.n_images, L.part_c, L.Lc, st));
+        TRY(launch_near32(false, L.pk32, L.pk32lo, L.org, ct, ct + half, pl.d_check_org, pl.d_shifts, L.part_c,
+                          L.Lc, st));
     } else {
-        TRY(launch_near64(false, L.pk64, L.n_chunks, (const double4_32a*)pl.d_check_tgt, pl.n_check_tiles, pl.d_shifts,
-                          pl.n_images, L.part_c, L.Lc, st));
+        TRY(launch_near64(false, L.pk64, (const double4_32a*)pl.d_check_tgt, pl.d_shifts, L.part_c, L.Lc, st));
     }
     if (h->profile) TRY(cudaEventRecord(h->ev[3], st));
     const int tile = fp32 ? kTile32 : kTile64;
@@ -291,7 +233,8 @@ int eval_device(psum_plan_s* h, int64_t N, const double* x, const double* q, dou
                         zero_mean ? 1 : 0, st));
     if (h->profile) TRY(cudaEventRecord(h->ev[4], st));
     TRY(launch_far_combine(x, N, perm, L.phi_n, grad ? L.grad_n : nullptr, pl.d_C, o.p, 1.0 / pl.R0,
-                           L.eval_status, phi, grad, L.eval_status, st));
+                           pl.d_shtab64, fp32 ? pl.d_shtab32 : nullptr, L.eval_status, phi, grad, L.eval_status,
+                           st));
     k_status_merge<<<1, 1, 0, st>>>(L.eval_status, pl.d_status);
     TRY(cudaGetLastError());
     h->launches += 5;   // right-hand side, projection, constant, far field, status merge
@@ -321,7 +264,8 @@ int backward_device(psum_plan_s* h, int64_t N, const double* x, const double* q,
         h->launches += 1;
     }
     // moments w and the far field at the charges; u = (A^+)^T w
-    TRY(launch_moments(x, q, N, pl.d_C, o.p, 1.0 / pl.R0, L.far_phi, L.far_grad, L.w_part, L.nblk_mom, L.w, st));
+    TRY(launch_moments(x, q, N, pl.d_C, o.p, 1.0 / pl.R0, pl.d_shtab64, L.far_phi, L.far_grad, L.w_part,
+                       L.nblk_mom, L.w, st));
     TRY(launch_adjoint(pl.d_pinv, P - 1, M, L.w, L.u, st));
     h->launches += 3;
     // psi and grad psi at the charges: the check points as sources
@@ -330,13 +274,12 @@ int backward_device(psum_plan_s* h, int64_t N, const double* x, const double* q,
         const size_t n_chk_pts = (size_t)pl.n_check_tiles * kTile32;
         const float4* chk = (const float4*)pl.d_check_tgt;
         TRY(launch_check_sources32(chk, pl.d_check_inv, (int64_t)n_chk_pts, M, L.u, L.chk_src32, st));
-        TRY(launch_near32(true, L.chk_src32, chk + 2 * n_chk_pts, pl.d_check_org, (int64_t)pl.n_check_tiles * kTgt32,
-                          L.pk32, L.pk32lo, L.org, L.n_tiles, pl.d_shifts, pl.n_images, L.part_b, L.Lb, st));
+        TRY(launch_near32(true, L.chk_src32, chk + 2 * n_chk_pts, pl.d_check_org, L.pk32, L.pk32lo, L.org,
+                          pl.d_shifts, L.part_b, L.Lb, st));
     } else {
         const size_t n_chk_pts = (size_t)pl.n_check_tiles * kTile64;
         TRY(launch_check_sources64((const double4_32a*)pl.d_check_tgt, (int64_t)n_chk_pts, M, L.u, L.chk_src64, st));
-        TRY(launch_near64(true, L.chk_src64, pl.n_check_tiles, L.pk64, L.n_tiles, pl.d_shifts, pl.n_images,
-                          L.part_b, L.Lb, st));
+        TRY(launch_near64(true, L.chk_src64, L.pk64, pl.d_shifts, L.part_b, L.Lb, st));
     }
     TRY(launch_near_reduce(L.part_b, N, tile, 4, L.Lb, L.psi, L.gpsi, st));
     TRY(launch_backward_combine(N, perm, q, phi, grad, L.far_phi, L.far_grad, L.psi, L.gpsi, gE, dEdq, dEdx, st));
@@ -605,19 +548,18 @@ int eval_noalloc_device(psum_plan_s* h, int64_t N, const double* x, const double
     }
     if (h->profile) TRY(cudaEventRecord(h->ev[1], st));
     if (fp32)
-        TRY(launch_near32(true, L.pk32, L.pk32lo, L.org, L.n_chunks, L.pk32, L.pk32lo, L.org, L.n_tiles,
-                          pl.d_shifts, pl.n_images, L.part_n, L.Ln, st));
+        TRY(launch_near32(true, L.pk32, L.pk32lo, L.org, L.pk32, L.pk32lo, L.org, pl.d_shifts, L.part_n, L.Ln,
+                          st));
     else
-        TRY(launch_near64(true, L.pk64, L.n_chunks, L.pk64, L.n_tiles, pl.d_shifts, pl.n_images, L.part_n, L.Ln, st));
+        TRY(launch_near64(true, L.pk64, L.pk64, pl.d_shifts, L.part_n, L.Ln, st));
     if (h->profile) TRY(cudaEventRecord(h->ev[2], st));
     if (fp32) {
         const float4* ct = (const float4*)pl.d_check_tgt;
         const size_t half = 2 * (size_t)pl.n_check_tiles * kTile32;
-        TRY(launch_near32(false, L.pk32, L.pk32lo, L.org, L.n_chunks, ct, ct + half, pl.d_check_org,
-                          pl.n_check_tiles, pl.d_shifts, pl.n_images, L.part_c, L.Lc, st));
+        TRY(launch_near32(false, L.pk32, L.pk32lo, L.org, ct, ct + half, pl.d_check_org, pl.d_shifts, L.part_c,
+                          L.Lc, st));
     } else {
-        TRY(launch_near64(false, L.pk64, L.n_chunks, (const double4_32a*)pl.d_check_tgt, pl.n_check_tiles,
-                          pl.d_shifts, pl.n_images, L.part_c, L.Lc, st));
+        TRY(launch_near64(false, L.pk64, (const double4_32a*)pl.d_check_tgt, pl.d_shifts, L.part_c, L.Lc, st));
     }
     if (h->profile) TRY(cudaEventRecord(h->ev[3], st));
     const int tile = fp32 ? kTile32 : kTile64;
@@ -636,7 +578,8 @@ int eval_noalloc_device(psum_plan_s* h, int64_t N, const double* x, const double
                         zero_mean ? 1 : 0, st));
     if (h->profile) TRY(cudaEventRecord(h->ev[4], st));
     TRY(launch_far_combine(x, N, perm, L.phi_n, grad ? L.grad_n : nullptr, pl.d_C, o.p, 1.0 / pl.R0,
-                           L.eval_status, phi, grad, L.eval_status, st));
+                           pl.d_shtab64, fp32 ? pl.d_shtab32 : nullptr, L.eval_status, phi, grad, L.eval_status,
+                           st));
     k_status_merge<<<1, 1, 0, st>>>(L.eval_status, pl.d_status);
     TRY(cudaGetLastError());
     h->launches += 5;

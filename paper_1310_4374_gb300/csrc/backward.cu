@@ -17,15 +17,18 @@ constexpr int kMomThreads = 128;
 // phi_far (with C_1) and grad phi_far at every charge, and per-block partial moments.
 __global__ void __launch_bounds__(kMomThreads) k_moments(const double* __restrict__ x, const double* __restrict__ q,
                                                          int64_t n, const double* __restrict__ C, int p,
-                                                         double inv_R0, double* __restrict__ far_phi,
+                                                         double inv_R0, const double* __restrict__ tab,
+                                                         double* __restrict__ far_phi,
                                                          double* __restrict__ far_grad,
                                                          double* __restrict__ w_partial) {
     extern __shared__ double sm[];
     const int P = (p + 1) * (p + 1);
+    constexpr int W = kMomThreads / 32;
     double* s_C = sm;
     double* s_w = sm + P;                                   // [warps][P]
-    constexpr int W = kMomThreads / 32;
+    double* s_tab = s_w + W * P;
     for (int t = threadIdx.x; t < P; t += kMomThreads) s_C[t] = C[t];
+    for (int t = threadIdx.x; t < sh_tab_size(p); t += kMomThreads) s_tab[t] = tab[t];
     for (int t = threadIdx.x; t < W * P; t += kMomThreads) s_w[t] = 0.0;
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -37,7 +40,7 @@ __global__ void __launch_bounds__(kMomThreads) k_moments(const double* __restric
     const double uz = valid ? x[3 * i + 2] * inv_R0 : 0.0;
     double f = 0.0, gx = 0.0, gy = 0.0, gz = 0.0;
     double* ws = s_w + warp * P;
-    sh_visit<true>(ux, uy, uz, p, [&](int nn, int mm, double v, double vx, double vy, double vz) {
+    sh_visit_tab<true>(ux, uy, uz, p, s_tab, [&](int nn, int mm, double v, double vx, double vy, double vz) {
         const int t = sh_index(nn, mm);
         const double c = s_C[t];
         f = fma(c, v, f);
@@ -149,12 +152,14 @@ __global__ void k_energy_finish(const double* __restrict__ partial, int nblk, do
 }
 
 // ---------------------------------------------------------------------------
+size_t moments_smem(int p);
+
 cudaError_t launch_moments(const double* x, const double* q, int64_t n, const double* C, int p, double inv_R0,
-                           double* far_phi, double* far_grad, double* w_partial, int nblk, double* w,
-                           cudaStream_t st) {
+                           const double* tab, double* far_phi, double* far_grad, double* w_partial, int nblk,
+                           double* w, cudaStream_t st) {
     const int P = (p + 1) * (p + 1);
-    const size_t smem = sizeof(double) * P * (1 + kMomThreads / 32);
-    k_moments<<<nblk, kMomThreads, smem, st>>>(x, q, n, C, p, inv_R0, far_phi, far_grad, w_partial);
+    const size_t smem = moments_smem(p);
+    k_moments<<<nblk, kMomThreads, smem, st>>>(x, q, n, C, p, inv_R0, tab, far_phi, far_grad, w_partial);
     k_moments_reduce<<<(P + 127) / 128, 128, 0, st>>>(w_partial, nblk, P, w);
     return cudaGetLastError();
 }
@@ -165,7 +170,9 @@ cudaError_t set_moments_smem(size_t bytes) {
 
 int moments_blocks(int64_t n) { return (int)((n + kMomThreads - 1) / kMomThreads); }
 
-size_t moments_smem(int p) { return sizeof(double) * (p + 1) * (p + 1) * (1 + kMomThreads / 32); }
+size_t moments_smem(int p) {
+    return sizeof(double) * ((p + 1) * (p + 1) * (1 + kMomThreads / 32) + sh_tab_size(p));
+}
 
 cudaError_t launch_adjoint(const double* pinv, int rows, int M, const double* w, double* u, cudaStream_t st) {
     k_adjoint<<<(M + 127) / 128, 128, 0, st>>>(pinv, rows, M, w, u);

@@ -6,6 +6,7 @@
 //   Eqs. 1.6-1.9).
 // All of it runs in float64.
 #include "psum_internal.cuh"
+#include "mean.cuh"
 
 namespace psum {
 
@@ -67,52 +68,6 @@ __global__ void k_validate_finish(const double* __restrict__ partial, int nblk, 
     if (threadIdx.x == 0 && !(fabs(s) <= 1e-12 * sa)) atomicOr(status, kStatNonNeutral);
 }
 
-// ---------------------------------------------------------------------------
-// Mean of phi_near over the box (Eq. pfx4).  The near block is the union of the
-// box images, so sum_p Phi_0(x + p) = U(x) / V0 with U(x) = int_B dV(y)/|y - x|
-// over the block B = [-H0,H0] x [-H1,H1] x [-H2,H2].  U is reduced to the faces
-// by the divergence theorem (Eqs. B1-B2), each face integral to its four edges
-// by the divergence theorem in the plane (Eqs. B3-B5), and each edge integral
-// has the primitive (Eqs. B7-B9, in the form derived below)
-//   G(t; z, h) = z ln(t + rho) + h atan(h t / (z rho)) - h atan(t / z),
-//   rho = sqrt(t^2 + z^2 + h^2),
-// where h is the distance from x to the face plane, z the signed distance of
-// the projected point to the edge line (positive inside the face) and t runs
-// along the edge from the foot of the perpendicular.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ double edge_primitive(double t, double z, double h) {
-    const double rho = sqrt(t * t + z * z + h * h);
-    const double lg = t >= 0.0 ? log(t + rho) : log((z * z + h * h) / (rho - t));
-    return z * lg + h * atan(h * t / (z * rho)) - h * atan(t / z);
-}
-
-__device__ __forceinline__ double edge_integral(double z, double h, double t0, double t1) {
-    if (z == 0.0) return 0.0;     // the point projects onto the edge line: the integrand vanishes
-    return edge_primitive(t1, z, h) - edge_primitive(t0, z, h);
-}
-
-__device__ double block_potential(const double X[3], const double H[3]) {
-    double U = 0.0;
-    for (int k = 0; k < 3; ++k) {
-        const int k1 = (k + 1) % 3, k2 = (k + 2) % 3;
-        const double a = X[k1], b = X[k2];
-        // face integral L = sum over its four edges (independent of the face's side)
-        const double h_lo = fabs(H[k] + X[k]), h_hi = fabs(H[k] - X[k]);
-        for (int side = 0; side < 2; ++side) {
-            const double s = side ? (H[k] - X[k]) : (H[k] + X[k]);     // n . (y - x) on the face
-            const double h = side ? h_hi : h_lo;
-            if (s == 0.0) continue;
-            double L = 0.0;
-            L += edge_integral(H[k1] - a, h, -H[k2] - b, H[k2] - b);
-            L += edge_integral(H[k1] + a, h, -H[k2] - b, H[k2] - b);
-            L += edge_integral(H[k2] - b, h, -H[k1] - a, H[k1] - a);
-            L += edge_integral(H[k2] + b, h, -H[k1] - a, H[k1] - a);
-            U += 0.5 * s * L;
-        }
-    }
-    return U;
-}
-
 __global__ void __launch_bounds__(kRedThreads) k_box_mean(const double* __restrict__ x, const double* __restrict__ q,
                                                           int64_t n, double H0, double H1, double H2,
                                                           double* __restrict__ partial) {
@@ -172,17 +127,25 @@ __global__ void k_constant(double* __restrict__ C, const double* __restrict__ Rb
 // ---------------------------------------------------------------------------
 constexpr int kFarThreads = 128;
 
+// T = double for FP64 plans; T = float for FP32C plans, whose far field is a smooth,
+// slowly varying part of phi (its float32 evaluation errors sit well below the pair sum's)
+template <class T>
 __global__ void __launch_bounds__(kFarThreads) k_far_combine(const double* __restrict__ x, int64_t n,
                                                              const int* __restrict__ perm,
                                                              const double* __restrict__ phi_near,
                                                              const double* __restrict__ grad_near,
                                                              const double* __restrict__ C, int p, double inv_R0,
+                                                             const T* __restrict__ tab,
                                                              const int* __restrict__ status,
                                                              double* __restrict__ phi, double* __restrict__ grad,
                                                              int* __restrict__ status_out) {
-    extern __shared__ double s_C[];
+    extern __shared__ unsigned char s_raw[];
     const int P = (p + 1) * (p + 1);
-    for (int t = threadIdx.x; t < P; t += kFarThreads) s_C[t] = C[t];
+    const int nt = sh_tab_size(p);
+    T* s_C = (T*)s_raw;
+    T* s_tab = s_C + P;
+    for (int t = threadIdx.x; t < P; t += kFarThreads) s_C[t] = (T)C[t];
+    for (int t = threadIdx.x; t < nt; t += kFarThreads) s_tab[t] = tab[t];
     __syncthreads();
     const int64_t s = (int64_t)blockIdx.x * kFarThreads + threadIdx.x;
     if (s >= n) return;
@@ -193,29 +156,29 @@ __global__ void __launch_bounds__(kFarThreads) k_far_combine(const double* __res
         if (grad) grad[3 * i] = grad[3 * i + 1] = grad[3 * i + 2] = __longlong_as_double(0x7ff8000000000000ll);
         return;
     }
-    const double ux = x[3 * i] * inv_R0, uy = x[3 * i + 1] * inv_R0, uz = x[3 * i + 2] * inv_R0;
-    double f = 0.0, gx = 0.0, gy = 0.0, gz = 0.0;
+    const T ux = (T)(x[3 * i] * inv_R0), uy = (T)(x[3 * i + 1] * inv_R0), uz = (T)(x[3 * i + 2] * inv_R0);
+    T f = 0, gx = 0, gy = 0, gz = 0;
     if (grad) {
-        sh_visit<true>(ux, uy, uz, p, [&](int nn, int mm, double v, double vx, double vy, double vz) {
-            const double c = s_C[sh_index(nn, mm)];
+        sh_visit_tab<true>(ux, uy, uz, p, s_tab, [&](int nn, int mm, T v, T vx, T vy, T vz) {
+            const T c = s_C[sh_index(nn, mm)];
             f = fma(c, v, f);
             gx = fma(c, vx, gx);
             gy = fma(c, vy, gy);
             gz = fma(c, vz, gz);
         });
     } else {
-        sh_visit<false>(ux, uy, uz, p, [&](int nn, int mm, double v, double, double, double) {
+        sh_visit_tab<false>(ux, uy, uz, p, s_tab, [&](int nn, int mm, T v, T, T, T) {
             f = fma(s_C[sh_index(nn, mm)], v, f);
         });
     }
     // the t = 1 term of the sum is C_1 R^_0^0 = C_1: included by the visitor
-    const double ph = phi_near[s] + f;
+    const double ph = phi_near[s] + (double)f;
     phi[i] = ph;
     bool finite = fabs(ph) <= 1.7976931348623157e308;
     if (grad) {
-        const double g0 = grad_near[3 * s] + gx * inv_R0;
-        const double g1 = grad_near[3 * s + 1] + gy * inv_R0;
-        const double g2 = grad_near[3 * s + 2] + gz * inv_R0;
+        const double g0 = grad_near[3 * s] + (double)gx * inv_R0;
+        const double g1 = grad_near[3 * s + 1] + (double)gy * inv_R0;
+        const double g2 = grad_near[3 * s + 2] + (double)gz * inv_R0;
         grad[3 * i] = g0;
         grad[3 * i + 1] = g1;
         grad[3 * i + 2] = g2;
@@ -263,12 +226,20 @@ cudaError_t launch_constant(double* C, const double* Rbox, int P, const double* 
 }
 
 cudaError_t launch_far_combine(const double* x, int64_t n, const int* perm, const double* phi_near,
-                               const double* grad_near, const double* C, int p, double inv_R0, const int* status,
-                               double* phi, double* grad, int* status_out, cudaStream_t st) {
+                               const double* grad_near, const double* C, int p, double inv_R0, const double* tab64,
+                               const float* tab32, const int* status, double* phi, double* grad, int* status_out,
+                               cudaStream_t st) {
     const int P = (p + 1) * (p + 1);
     const unsigned nb = (unsigned)((n + kFarThreads - 1) / kFarThreads);
-    k_far_combine<<<nb, kFarThreads, sizeof(double) * P, st>>>(x, n, perm, phi_near, grad_near, C, p, inv_R0,
-                                                               status, phi, grad, status_out);
+    if (tab32) {
+        const size_t smem = sizeof(float) * (P + sh_tab_size(p));
+        k_far_combine<float><<<nb, kFarThreads, smem, st>>>(x, n, perm, phi_near, grad_near, C, p, inv_R0, tab32,
+                                                            status, phi, grad, status_out);
+    } else {
+        const size_t smem = sizeof(double) * (P + sh_tab_size(p));
+        k_far_combine<double><<<nb, kFarThreads, smem, st>>>(x, n, perm, phi_near, grad_near, C, p, inv_R0, tab64,
+                                                             status, phi, grad, status_out);
+    }
     return cudaGetLastError();
 }
 

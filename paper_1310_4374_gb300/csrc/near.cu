@@ -23,7 +23,7 @@
 //
 // FP64: absolute float64 coordinates; 1/sqrt(r^2) is a float32 MUFU estimate
 // refined by two Newton-Raphson steps y <- y (3 - r^2 y^2)/2 in float64.
-#include "psum_internal.cuh"
+#include "launch.cuh"
 
 namespace psum {
 
@@ -62,11 +62,17 @@ struct Near32Args {
     const float4* tgt_hi;    // same layouts for the targets (q unused)
     const float4* tgt_lo;
     const double* tgt_org;   // 4 per target group (kGroupsPerTile32 groups per tile)
-    const double* shifts;    // n_img x 3 image vectors
-    double* partial;         // [n_tiles][max_contrib][4 or 1][kTile32]
-    int64_t n_tiles, n_chunks, U, G;
-    int n_img, max_contrib;
+    const double* shifts;    // image vectors, 3 per image, systems one after another
+    double* partial;         // [tiles][max_contrib][4 or 1][kTile32]
+    int64_t U, G;
+    int max_contrib, max_img;
+    NearSysTable tab;
 };
+
+#ifndef PSUM_FAR_UNROLL
+#define PSUM_FAR_UNROLL 2
+#endif
+constexpr int kFarUnroll = PSUM_FAR_UNROLL;   // source pairs per unrolled step of the far loop
 
 // Far units: one chunk of sources against the thread's 4 targets (2 packed pairs),
 // plain float32 offsets s - t'.
@@ -76,7 +82,7 @@ __device__ __forceinline__ void pair_loop_far(const float4* __restrict__ s_hi, c
                                               float2 (&agx)[2], float2 (&agy)[2], float2 (&agz)[2]) {
     // the potential, whose terms cancel most, goes into two interleaved partial sums
     float2 bphi[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
-#pragma unroll 1
+#pragma unroll kFarUnroll
     for (int s = 0; s < kNearChunk; s += 2) {
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
@@ -155,29 +161,30 @@ __device__ __forceinline__ void two_sum_acc2(float2& hi, float2& lo, float2 v) {
     hi = s;
 }
 
-#ifndef PSUM_NEAR32_MIN_BLOCKS
-#define PSUM_NEAR32_MIN_BLOCKS 6
-#endif
-template <bool kGrad>
-__global__ void __launch_bounds__(kThreads32, PSUM_NEAR32_MIN_BLOCKS) k_near32(Near32Args a) {
+// Two register budgets of the same kernel: 6 resident CTAs per SM (80 registers) or 5
+// (up to 102).  The batch autotuner times both.
+constexpr int kNear32MinBlocks[2] = {6, 5};
+
+template <bool kGrad, int kMinB>
+__global__ void __launch_bounds__(kThreads32, kMinB) k_near32(Near32Args a) {
     constexpr int NQ = kGrad ? 4 : 1;
     __shared__ float4 s_hi[2 * kNearChunk];
     __shared__ float4 s_lo[2 * kNearChunk];
     __shared__ float2 s_th[3][2][kThreads32];             // target hi offsets, [coord][pair]
     __shared__ float2 s_acc[NQ][2][2][kThreads32];        // [quantity][pair][hi, lo]
-    extern __shared__ float s_dyn[];                      // [n_img][kTgt32][6] deltas, then [n_img] flags
+    extern __shared__ float s_dyn[];                      // [max_img][kTgt32][6] deltas, then [max_img] flags
     float* s_delta = s_dyn;
-    int* s_near = (int*)(s_dyn + 6 * kTgt32 * a.n_img);
+    int* s_near = (int*)(s_dyn + 6 * kTgt32 * a.max_img);
 
     const int tid = threadIdx.x;
     const int64_t g = blockIdx.x;
     int64_t u = sk_bound(g, a.U, a.G);
     const int64_t u_end = sk_bound(g + 1, a.U, a.G);
-    const int64_t upt = a.n_chunks * a.n_img;
-    int64_t cur_tile = -1, cur_chunk = -1;
+    int sb = near_sys_by_unit(a.tab, u);
+    int64_t cur_tile = -1, cur_chunk = -1, cur_first = 0;
 
-    auto flush = [&](int64_t tile) {
-        const int64_t slot = g - sk_owner(tile * upt, a.U, a.G);
+    auto flush = [&](int64_t tile, int64_t first_unit) {
+        const int64_t slot = g - sk_owner(first_unit, a.U, a.G);
         double* dst = a.partial + ((tile * a.max_contrib + slot) * NQ) * kTile32;
 #pragma unroll
         for (int qi = 0; qi < NQ; ++qi)
@@ -190,12 +197,23 @@ __global__ void __launch_bounds__(kThreads32, PSUM_NEAR32_MIN_BLOCKS) k_near32(N
     };
 
     while (u < u_end) {
-        const int64_t tile = u / upt;
-        const int64_t rem = u - tile * upt;
-        const int64_t chunk = rem / a.n_img;
-        const int img = (int)(rem - chunk * a.n_img);
+        // the system descriptor is re-read (parameter or L1) rather than held in registers
+        const NearSys* Sp = a.tab.many ? a.tab.many + sb : &a.tab.one;
+        if (u >= Sp->unit0 + near_sys_units(*Sp)) {
+            ++sb;
+            continue;
+        }
+        const int n_img = Sp->n_img;
+        const int64_t upt = Sp->n_chunks * n_img;
+        const int64_t local = u - Sp->unit0;
+        const int64_t tile_l = local / upt;
+        const int64_t rem = local - tile_l * upt;
+        const int64_t chunk_l = rem / n_img;
+        const int img = (int)(rem - chunk_l * n_img);
+        const int64_t tile = Sp->tile0 + tile_l;
+        const int64_t chunk = Sp->src_chunk0 + chunk_l;
         if (tile != cur_tile) {
-            if (cur_tile >= 0) flush(cur_tile);
+            if (cur_tile >= 0) flush(cur_tile, cur_first);
 #pragma unroll
             for (int j = 0; j < 2; ++j) {
                 const int64_t i0 = (tile * kTgt32 + 2 * j) * kGroup + tid;
@@ -212,6 +230,7 @@ __global__ void __launch_bounds__(kThreads32, PSUM_NEAR32_MIN_BLOCKS) k_near32(N
                 }
             }
             cur_tile = tile;
+            cur_first = Sp->unit0 + tile_l * upt;
             cur_chunk = -1;
         }
         if (chunk != cur_chunk) {
@@ -220,8 +239,9 @@ __global__ void __launch_bounds__(kThreads32, PSUM_NEAR32_MIN_BLOCKS) k_near32(N
             const float4* lsrc = a.src_lo + chunk * (2 * kNearChunk);
             for (int i = tid; i < 2 * kNearChunk; i += kThreads32) { s_hi[i] = hsrc[i]; s_lo[i] = lsrc[i]; }
             const double* so = a.src_org + 4 * chunk;
-            for (int im = tid; im < a.n_img; im += kThreads32) {
-                const double* sh = a.shifts + 3 * im;
+            const int shift0 = Sp->shift0;
+            for (int im = tid; im < n_img; im += kThreads32) {
+                const double* sh = a.shifts + 3 * (shift0 + im);
                 int nr = 0;
                 for (int k = 0; k < kTgt32; ++k) {
                     const double* to = a.tgt_org + 4 * (cur_tile * kTgt32 + k);
@@ -297,7 +317,7 @@ __global__ void __launch_bounds__(kThreads32, PSUM_NEAR32_MIN_BLOCKS) k_near32(N
         }
         ++u;
     }
-    if (cur_tile >= 0) flush(cur_tile);
+    if (cur_tile >= 0) flush(cur_tile, cur_first);
 }
 
 // ---------------------------------------------------------------------------
@@ -307,9 +327,10 @@ struct Near64Args {
     const double4_32a* src;      // (x, y, z, q), absolute
     const double4_32a* tgt;      // (x, y, z, -)
     const double* shifts;
-    double* partial;         // [n_tiles][max_contrib][4 or 1][kTile64]
-    int64_t n_tiles, n_chunks, U, G;
-    int n_img, max_contrib;
+    double* partial;             // [tiles][max_contrib][4 or 1][kTile64]
+    int64_t U, G;
+    int max_contrib;
+    NearSysTable tab;
 };
 
 __device__ __forceinline__ double rsqrt_f64(double r2) {
@@ -328,30 +349,37 @@ __global__ void __launch_bounds__(kThreads64) k_near64(Near64Args a) {
     const int64_t g = blockIdx.x;
     int64_t u = sk_bound(g, a.U, a.G);
     const int64_t u_end = sk_bound(g + 1, a.U, a.G);
-    const int64_t upt = a.n_chunks * a.n_img;
+    int sb = near_sys_by_unit(a.tab, u);
+    NearSys S = near_sys_get(a.tab, sb);
     double tx = 0, ty = 0, tz = 0;
     double acc[NQ];
-    int64_t cur_tile = -1, cur_chunk = -1;
+    int64_t cur_tile = -1, cur_chunk = -1, cur_first = 0;
 
-    auto flush = [&](int64_t tile) {
-        const int64_t slot = g - sk_owner(tile * upt, a.U, a.G);
+    auto flush = [&](int64_t tile, int64_t first_unit) {
+        const int64_t slot = g - sk_owner(first_unit, a.U, a.G);
         double* dst = a.partial + ((tile * a.max_contrib + slot) * NQ) * kTile64;
 #pragma unroll
         for (int qi = 0; qi < NQ; ++qi) dst[qi * kTile64 + tid] = acc[qi];
     };
 
     while (u < u_end) {
-        const int64_t tile = u / upt;
-        const int64_t rem = u - tile * upt;
-        const int64_t chunk = rem / a.n_img;
-        const int img = (int)(rem - chunk * a.n_img);
+        while (u >= S.unit0 + near_sys_units(S)) S = near_sys_get(a.tab, ++sb);
+        const int64_t upt = S.n_chunks * S.n_img;
+        const int64_t local = u - S.unit0;
+        const int64_t tile_l = local / upt;
+        const int64_t rem = local - tile_l * upt;
+        const int64_t chunk_l = rem / S.n_img;
+        const int img = (int)(rem - chunk_l * S.n_img);
+        const int64_t tile = S.tile0 + tile_l;
+        const int64_t chunk = S.src_chunk0 + chunk_l;
         if (tile != cur_tile) {
-            if (cur_tile >= 0) flush(cur_tile);
+            if (cur_tile >= 0) flush(cur_tile, cur_first);
             const double4_32a t = a.tgt[tile * kTile64 + tid];
             tx = t.x; ty = t.y; tz = t.z;
 #pragma unroll
             for (int qi = 0; qi < NQ; ++qi) acc[qi] = 0.0;
             cur_tile = tile;
+            cur_first = S.unit0 + tile_l * upt;
             cur_chunk = -1;
         }
         if (chunk != cur_chunk) {
@@ -361,14 +389,15 @@ __global__ void __launch_bounds__(kThreads64) k_near64(Near64Args a) {
             cur_chunk = chunk;
         }
         // y - x_i - p with the shift folded into the target
-        const double px = tx - a.shifts[3 * img], py = ty - a.shifts[3 * img + 1], pz = tz - a.shifts[3 * img + 2];
+        const double* sh = a.shifts + 3 * (S.shift0 + img);
+        const double px = tx - sh[0], py = ty - sh[1], pz = tz - sh[2];
 #pragma unroll 4
         for (int s = 0; s < kNearChunk; ++s) {
-            const double4_32a S = s_src[s];
-            const double ex = S.x - px, ey = S.y - py, ez = S.z - pz;   // x_i + p - y
+            const double4_32a Q = s_src[s];
+            const double ex = Q.x - px, ey = Q.y - py, ez = Q.z - pz;   // x_i + p - y
             const double r2 = fma(ez, ez, fma(ey, ey, ex * ex));
             const double ri = r2 > 0.0 ? rsqrt_f64(r2) : 0.0;           // K(0) = 0
-            const double qr = S.w * ri;
+            const double qr = Q.w * ri;
             acc[0] += qr;
             if (kGrad) {
                 const double w = qr * ri * ri;
@@ -379,23 +408,25 @@ __global__ void __launch_bounds__(kThreads64) k_near64(Near64Args a) {
         }
         ++u;
     }
-    if (cur_tile >= 0) flush(cur_tile);
+    if (cur_tile >= 0) flush(cur_tile, cur_first);
 }
 
 // ---------------------------------------------------------------------------
-// Reduction of the partial slots (fixed order: slot 0, 1, ...).
-// out_phi[i], out_grad[3i..] for packed target index i < n_valid.
+// Reduction of the partial slots (fixed order: slot 0, 1, ...) for packed target
+// index i < n_valid (tile = i / tile_size is the partial-buffer row).
 // ---------------------------------------------------------------------------
 __global__ void k_near_reduce(const double* __restrict__ partial, int64_t n_valid, int tile_size, int nq,
-                              int64_t n_chunks, int n_img, int64_t U, int64_t G, int max_contrib,
+                              NearSysTable tab, int64_t U, int64_t G, int max_contrib,
                               double* __restrict__ out_phi, double* __restrict__ out_grad) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n_valid) return;
     const int64_t tile = i / tile_size;
     const int loc = (int)(i - tile * tile_size);
-    const int64_t upt = n_chunks * n_img;
-    const int64_t g0 = sk_owner(tile * upt, U, G);
-    const int64_t g1 = sk_owner((tile + 1) * upt - 1, U, G);
+    const NearSys S = near_sys_get(tab, near_sys_by_tile(tab, tile));
+    const int64_t upt = S.n_chunks * S.n_img;
+    const int64_t first = S.unit0 + (tile - S.tile0) * upt;
+    const int64_t g0 = sk_owner(first, U, G);
+    const int64_t g1 = sk_owner(first + upt - 1, U, G);
     double s[4] = {0, 0, 0, 0};
     for (int64_t sl = 0; sl <= g1 - g0; ++sl) {
         const double* src = partial + ((tile * max_contrib + sl) * nq) * tile_size + loc;
@@ -415,29 +446,33 @@ __global__ void k_near_reduce(const double* __restrict__ partial, int64_t n_vali
 size_t near32_dyn_smem(int n_img) { return sizeof(float) * 6 * kTgt32 * n_img + sizeof(int) * n_img; }
 
 cudaError_t launch_near32(bool grad, const float4* src_hi, const float4* src_lo, const double* src_org,
-                          int64_t n_chunks, const float4* tgt_hi, const float4* tgt_lo, const double* tgt_org,
-                          int64_t n_tiles, const double* shifts, int n_img, double* partial,
-                          const NearPlanLaunch& L, cudaStream_t st) {
+                          const float4* tgt_hi, const float4* tgt_lo, const double* tgt_org, const double* shifts,
+                          double* partial, const NearPlanLaunch& L, cudaStream_t st, int variant) {
     Near32Args a;
     a.src_hi = src_hi; a.src_lo = src_lo; a.src_org = src_org;
     a.tgt_hi = tgt_hi; a.tgt_lo = tgt_lo; a.tgt_org = tgt_org; a.shifts = shifts;
-    a.partial = partial; a.n_tiles = n_tiles; a.n_chunks = n_chunks; a.U = L.U; a.G = L.G;
-    a.n_img = n_img; a.max_contrib = L.max_contrib;
-    const size_t smem = near32_dyn_smem(n_img);
-    if (grad)
-        k_near32<true><<<(unsigned)L.G, kThreads32, smem, st>>>(a);
-    else
-        k_near32<false><<<(unsigned)L.G, kThreads32, smem, st>>>(a);
+    a.partial = partial; a.U = L.U; a.G = L.G; a.max_contrib = L.max_contrib; a.max_img = L.max_img;
+    a.tab = L.tab;
+    const size_t smem = near32_dyn_smem(L.max_img);
+    if (variant == 1) {
+        if (grad)
+            k_near32<true, kNear32MinBlocks[1]><<<(unsigned)L.G, kThreads32, smem, st>>>(a);
+        else
+            k_near32<false, kNear32MinBlocks[1]><<<(unsigned)L.G, kThreads32, smem, st>>>(a);
+    } else {
+        if (grad)
+            k_near32<true, kNear32MinBlocks[0]><<<(unsigned)L.G, kThreads32, smem, st>>>(a);
+        else
+            k_near32<false, kNear32MinBlocks[0]><<<(unsigned)L.G, kThreads32, smem, st>>>(a);
+    }
     return cudaGetLastError();
 }
 
-cudaError_t launch_near64(bool grad, const double4_32a* src, int64_t n_chunks, const double4_32a* tgt, int64_t n_tiles,
-                          const double* shifts, int n_img, double* partial, const NearPlanLaunch& L,
-                          cudaStream_t st) {
+cudaError_t launch_near64(bool grad, const double4_32a* src, const double4_32a* tgt, const double* shifts,
+                          double* partial, const NearPlanLaunch& L, cudaStream_t st) {
     Near64Args a;
     a.src = src; a.tgt = tgt; a.shifts = shifts; a.partial = partial;
-    a.n_tiles = n_tiles; a.n_chunks = n_chunks; a.U = L.U; a.G = L.G;
-    a.n_img = n_img; a.max_contrib = L.max_contrib;
+    a.U = L.U; a.G = L.G; a.max_contrib = L.max_contrib; a.tab = L.tab;
     if (grad)
         k_near64<true><<<(unsigned)L.G, kThreads64, 0, st>>>(a);
     else
@@ -450,14 +485,19 @@ cudaError_t launch_near_reduce(const double* partial, int64_t n_valid, int tile_
     if (n_valid <= 0) return cudaSuccess;
     const int bs = 256;
     const unsigned nb = (unsigned)((n_valid + bs - 1) / bs);
-    k_near_reduce<<<nb, bs, 0, st>>>(partial, n_valid, tile_size, nq, L.n_chunks, (int)L.n_img, L.U, L.G,
-                                     L.max_contrib, out_phi, out_grad);
+    k_near_reduce<<<nb, bs, 0, st>>>(partial, n_valid, tile_size, nq, L.tab, L.U, L.G, L.max_contrib, out_phi,
+                                     out_grad);
     return cudaGetLastError();
 }
 
-int near32_occupancy_ctas(int n_img) {
+int near32_occupancy_ctas(int n_img, int variant) {
     int nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_near32<true>, kThreads32, near32_dyn_smem(n_img));
+    if (variant == 1)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_near32<true, kNear32MinBlocks[1]>, kThreads32,
+                                                      near32_dyn_smem(n_img));
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_near32<true, kNear32MinBlocks[0]>, kThreads32,
+                                                      near32_dyn_smem(n_img));
     return nb < 1 ? 1 : nb;
 }
 

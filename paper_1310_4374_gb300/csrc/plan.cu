@@ -319,6 +319,13 @@ int build_plan(const psum_opts& o, Plan& pl) {
     if ((s2 = upload(&pl.d_pinv, pl.pinv.data(), pl.pinv.size()))) return s2;
     if ((s2 = upload(&pl.d_Rbox, pl.Rbox.data(), pl.Rbox.size()))) return s2;
     if ((s2 = upload(&pl.d_shifts, pl.shifts.data(), pl.shifts.size()))) return s2;
+    {
+        std::vector<double> tab(sh_tab_size(p));
+        sh_tab_fill(p, tab.data());
+        std::vector<float> tabf(tab.begin(), tab.end());
+        if ((s2 = upload(&pl.d_shtab64, tab.data(), tab.size()))) return s2;
+        if ((s2 = upload(&pl.d_shtab32, tabf.data(), tabf.size()))) return s2;
+    }
     PSUM_CUDA_TRY(cudaMalloc((void**)&pl.d_C, sizeof(double) * pl.P));
     PSUM_CUDA_TRY(cudaMemset(pl.d_C, 0, sizeof(double) * pl.P));
     PSUM_CUDA_TRY(cudaMalloc((void**)&pl.d_status, sizeof(int)));
@@ -336,6 +343,8 @@ void free_plan_device(Plan& pl) {
     cudaFree(pl.d_pinv);
     cudaFree(pl.d_Rbox);
     cudaFree(pl.d_shifts);
+    cudaFree(pl.d_shtab64);
+    cudaFree(pl.d_shtab32);
     cudaFree(pl.d_C);
     cudaFree(pl.d_status);
     if (pl.h_status) cudaFreeHost(pl.h_status);

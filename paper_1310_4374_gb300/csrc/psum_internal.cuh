@@ -110,6 +110,88 @@ __host__ __device__ __forceinline__ void sh_visit(double x, double y, double z, 
     }
 }
 
+// The same recurrence with its coefficients read from a table, in value type T
+// (double, or float for the FP32C far field).  Table layout for degree p:
+//   [0, p]           c_m  = sqrt((2m-1)/(2m))   (m >= 1; c_0 unused)
+//   [p+1, 2p+1]      c1_m = sqrt(2m+1)
+//   then e1(n,m) = (2n-1)/sqrt((n-m)(n+m)) and e2(n,m) = sqrt((n-m-1)(n+m-1)/((n-m)(n+m)))
+//   for 0 <= m <= n <= p at 2p+2 + 2 (n(n+1)/2 + m) and the entry after it.
+__host__ __device__ __forceinline__ int sh_tab_size(int p) { return 2 * (p + 1) + (p + 1) * (p + 2); }
+
+inline void sh_tab_fill(int p, double* t) {
+    for (int m = 0; m <= p; ++m) {
+        t[m] = m == 0 ? 0.0 : std::sqrt((2.0 * m - 1.0) / (2.0 * m));
+        t[p + 1 + m] = std::sqrt(2.0 * m + 1.0);
+    }
+    for (int n = 0; n <= p; ++n)
+        for (int m = 0; m <= n; ++m) {
+            double* e = t + 2 * (p + 1) + 2 * (n * (n + 1) / 2 + m);
+            const double nm = (double)(n - m) * (double)(n + m);
+            e[0] = nm > 0 ? (2.0 * n - 1.0) / std::sqrt(nm) : 0.0;
+            e[1] = nm > 0 ? std::sqrt((double)(n - m - 1) * (double)(n + m - 1) / nm) : 0.0;
+        }
+}
+
+template <bool kGrad, class T, class Visit>
+__host__ __device__ __forceinline__ void sh_visit_tab(T x, T y, T z, int p, const T* __restrict__ tab,
+                                                      Visit&& visit) {
+    const T r2 = x * x + y * y + z * z;
+    const T* e12 = tab + 2 * (p + 1);
+    T a = T(1), b = T(0);
+    T ax = 0, ay = 0, az = 0, bx = 0, by = 0, bz = 0;
+    for (int m = 0; m <= p; ++m) {
+        T sp, sm, spx = 0, spy = 0, spz = 0, smx = 0, smy = 0, smz = 0;
+        if (m == 0) {
+            sp = T(1);
+            sm = T(0);
+        } else {
+            const T c = tab[m];
+            sp = -(x * a + y * b) * c;
+            sm = (y * a - x * b) * c;
+            if (kGrad) {
+                spx = -(a + x * ax + y * bx) * c;
+                spy = -(x * ay + b + y * by) * c;
+                spz = -(x * az + y * bz) * c;
+                smx = (y * ax - b - x * bx) * c;
+                smy = (a + y * ay - x * by) * c;
+                smz = (y * az - x * bz) * c;
+            }
+        }
+        a = sp; b = sm;
+        if (kGrad) { ax = spx; ay = spy; az = spz; bx = smx; by = smy; bz = smz; }
+        for (int s = 0; s < (m == 0 ? 1 : 2); ++s) {
+            const int mm = s == 0 ? m : -m;
+            T v2 = s == 0 ? sp : sm;
+            T g2x = s == 0 ? spx : smx, g2y = s == 0 ? spy : smy, g2z = s == 0 ? spz : smz;
+            visit(m, mm, v2, g2x, g2y, g2z);
+            if (m + 1 > p) continue;
+            const T c1 = tab[p + 1 + m];
+            T v1 = -z * c1 * v2;
+            T g1x = 0, g1y = 0, g1z = 0;
+            if (kGrad) {
+                g1x = -z * c1 * g2x;
+                g1y = -z * c1 * g2y;
+                g1z = -c1 * (v2 + z * g2z);
+            }
+            visit(m + 1, mm, v1, g1x, g1y, g1z);
+            for (int n = m + 2; n <= p; ++n) {
+                const T* e = e12 + 2 * (n * (n + 1) / 2 + m);
+                const T e1 = e[0], e2 = e[1];
+                const T v = -(e1 * z * v1 + e2 * r2 * v2);
+                T gx = 0, gy = 0, gz = 0;
+                if (kGrad) {
+                    gx = -(e1 * z * g1x + e2 * (T(2) * x * v2 + r2 * g2x));
+                    gy = -(e1 * z * g1y + e2 * (T(2) * y * v2 + r2 * g2y));
+                    gz = -(e1 * (v1 + z * g1z) + e2 * (T(2) * z * v2 + r2 * g2z));
+                }
+                visit(n, mm, v, gx, gy, gz);
+                v2 = v1; v1 = v;
+                if (kGrad) { g2x = g1x; g2y = g1y; g2z = g1z; g1x = gx; g1y = gy; g1z = gz; }
+            }
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // The plan (algorithm "set" results, device copies and scratch).
 // ---------------------------------------------------------------------------
@@ -144,6 +226,8 @@ struct Plan {
 
     double* d_pinv = nullptr;
     double* d_Rbox = nullptr;
+    double* d_shtab64 = nullptr;    // recurrence coefficients (sh_visit_tab), double
+    float* d_shtab32 = nullptr;     // the same in float
     double* d_shifts = nullptr;
     double* d_C = nullptr;          // P coefficients of the last evaluation
     int* d_status = nullptr;
@@ -178,29 +262,108 @@ __host__ __device__ __forceinline__ int64_t sk_owner(int64_t u, int64_t U, int64
     return g;
 }
 
-struct NearPlanLaunch {
-    int64_t n_tiles, n_chunks, n_img;
-    int64_t U, G;
-    int max_contrib;              // partial slots per tile
+// One system of a near-field launch.  Its work units are the global indices
+// [unit0, unit0 + n_tiles * n_chunks * n_img), ordered (tile, chunk, image).
+struct NearSys {
+    int64_t unit0;       // first unit
+    int64_t tile0;       // first tile of the system in the target pack (= its first partial-buffer row)
+    int64_t n_tiles;     // target tiles
+    int64_t n_chunks;    // source chunks
+    int64_t src_chunk0;  // first chunk of the system in the source pack
+    int shift0;          // first image vector of the system in the shift table
+    int n_img;
 };
 
-inline NearPlanLaunch near_partition(int64_t n_tiles, int64_t n_chunks, int n_img, int64_t G_max) {
+// A single system travels by value; a batch passes a device array sorted by unit0.
+struct NearSysTable {
+    NearSys one;
+    const NearSys* many;   // nullptr: the launch has the single system `one`
+    int n;
+};
+
+__host__ __device__ __forceinline__ int64_t near_sys_units(const NearSys& s) {
+    return s.n_tiles * s.n_chunks * s.n_img;
+}
+
+__device__ __forceinline__ NearSys near_sys_get(const NearSysTable& t, int b) {
+    return t.many ? t.many[b] : t.one;
+}
+
+// the system whose unit range contains u (binary search over unit0)
+__device__ __forceinline__ int near_sys_by_unit(const NearSysTable& t, int64_t u) {
+    if (!t.many) return 0;
+    int lo = 0, hi = t.n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (t.many[mid].unit0 <= u) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// the system whose partial-buffer rows contain global tile T
+__device__ __forceinline__ int near_sys_by_tile(const NearSysTable& t, int64_t T) {
+    if (!t.many) return 0;
+    int lo = 0, hi = t.n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (t.many[mid].tile0 <= T) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+struct NearPlanLaunch {
+    int64_t U, G;
+    int max_contrib;              // partial slots per tile
+    int max_img;                  // largest image count of any system (shared-memory sizing)
+    int64_t n_tiles;              // rows of the partial buffer
+    NearSysTable tab;
+};
+
+// Stream-K partition of the systems' units over at most G_max CTAs; the partial
+// buffer needs max_contrib slots per tile.  `dev_tab` is the device copy of `sys`
+// (nullptr when there is one system).
+inline NearPlanLaunch near_partition(const std::vector<NearSys>& sys, int64_t G_max, const NearSys* dev_tab) {
     NearPlanLaunch L;
-    L.n_tiles = n_tiles;
-    L.n_chunks = n_chunks;
-    L.n_img = n_img;
-    L.U = n_tiles * n_chunks * n_img;
+    L.U = 0;
+    L.max_img = 1;
+    L.n_tiles = 0;
+    for (const NearSys& s : sys) {
+        L.U += near_sys_units(s);
+        L.max_img = s.n_img > L.max_img ? s.n_img : L.max_img;
+        L.n_tiles = s.tile0 + s.n_tiles > L.n_tiles ? s.tile0 + s.n_tiles : L.n_tiles;
+    }
     L.G = L.U < G_max ? L.U : G_max;
     if (L.G < 1) L.G = 1;
     int mc = 1;
-    const int64_t upt = n_chunks * n_img;
-    for (int64_t t = 0; t < n_tiles; ++t) {
-        const int64_t g0 = sk_owner(t * upt, L.U, L.G);
-        const int64_t g1 = sk_owner((t + 1) * upt - 1, L.U, L.G);
-        if (g1 - g0 + 1 > mc) mc = (int)(g1 - g0 + 1);
+    for (const NearSys& s : sys) {
+        const int64_t upt = s.n_chunks * s.n_img;
+        for (int64_t t = 0; t < s.n_tiles; ++t) {
+            const int64_t u0 = s.unit0 + t * upt;
+            const int64_t g0 = sk_owner(u0, L.U, L.G);
+            const int64_t g1 = sk_owner(u0 + upt - 1, L.U, L.G);
+            if (g1 - g0 + 1 > mc) mc = (int)(g1 - g0 + 1);
+        }
     }
     L.max_contrib = mc;
+    L.tab.one = sys.empty() ? NearSys{} : sys[0];
+    L.tab.many = sys.size() > 1 ? dev_tab : nullptr;
+    L.tab.n = (int)sys.size();
     return L;
 }
 
+// The single-system case: targets tiles 0..n_tiles-1 against source chunks 0..n_chunks-1.
+inline NearPlanLaunch near_partition(int64_t n_tiles, int64_t n_chunks, int n_img, int64_t G_max) {
+    std::vector<NearSys> one(1);
+    one[0] = NearSys{0, 0, n_tiles, n_chunks, 0, 0, n_img};
+    return near_partition(one, G_max, nullptr);
+}
+
 }  // namespace psum
+
+// The opaque plan handle of the C-ABI.
+struct psum_plan_s {
+    psum::Plan pl;
+    int64_t launches = 0;       // kernels queued so far
+    bool profile = false;
+    cudaEvent_t ev[6] = {};
+};

@@ -129,20 +129,25 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(const uint32_t* _
 // each point's offset from the origin is split into a float32 hi part and the float32
 // rounding remainder lo, packed two float4 each: (x,x,y,y),(z,z,q,q) and (xl,xl,yl,yl),(zl,zl,0,0).
 // Padding points (s >= n) get q = 0 and a far-away position.
+// With a group table (batches) group g covers the sorted positions
+// [grp_start[g], grp_start[g] + grp_count[g]); without one, [128 g, min(128 (g+1), n)).
 __global__ void k_pack32(const double* __restrict__ x, const double* __restrict__ q,
                          const uint32_t* __restrict__ perm, int64_t n, int64_t n_groups,
+                         const int64_t* __restrict__ grp_start, const int* __restrict__ grp_count,
                          float4* __restrict__ pk_hi, float4* __restrict__ pk_lo, double* __restrict__ org) {
     const int64_t grp = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (grp >= n_groups) return;
+    const int64_t s0 = grp_start ? grp_start[grp] : grp * kNearChunk;
+    const int64_t s1 = grp_start ? s0 + grp_count[grp] : (grp + 1) * kNearChunk < n ? (grp + 1) * kNearChunk : n;
     constexpr int per = kNearChunk / 32;
     double px[per][3], pq[per];
     bool ok[per];
     double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
 #pragma unroll
     for (int k = 0; k < per; ++k) {
-        const int64_t s = grp * kNearChunk + k * 32 + lane;
-        ok[k] = s < n;
+        const int64_t s = s0 + k * 32 + lane;
+        ok[k] = s < s1;
         if (ok[k]) {
             const int64_t i = perm ? (int64_t)perm[s] : s;
             for (int c = 0; c < 3; ++c) {
@@ -212,17 +217,39 @@ __global__ void k_pack64(const double* __restrict__ x, const double* __restrict_
         pk[s] = make_double4_32a(1.0e3, 1.0e3, 1.0e3, 0.0);
 }
 
+// batches: packed point s of group g = s / 128 holds charge grp_start[g] + s % 128 if
+// s % 128 < grp_count[g] (caller order inside each system), padding otherwise
+__global__ void k_pack64_groups(const double* __restrict__ x, const double* __restrict__ q, int64_t n_pts,
+                                const int64_t* __restrict__ grp_start, const int* __restrict__ grp_count,
+                                double4_32a* __restrict__ pk) {
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n_pts) return;
+    const int64_t g = s / kNearChunk;
+    const int k = (int)(s - g * kNearChunk);
+    if (k < grp_count[g]) {
+        const int64_t i = grp_start[g] + k;
+        pk[s] = make_double4_32a(x[3 * i], x[3 * i + 1], x[3 * i + 2], q[i]);
+    } else {
+        pk[s] = make_double4_32a(1.0e3, 1.0e3, 1.0e3, 0.0);
+    }
+}
+
+cudaError_t launch_pack64_groups(const double* x, const double* q, int64_t n_pts, const int64_t* grp_start,
+                                 const int* grp_count, double4_32a* pk, cudaStream_t st) {
+    k_pack64_groups<<<(unsigned)((n_pts + 255) / 256), 256, 0, st>>>(x, q, n_pts, grp_start, grp_count, pk);
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------------
 int sort_blocks(int64_t n) { return (int)((n + kSortTile - 1) / kSortTile); }
 
-// keys/vals ping-pong in (ka, va) <-> (kb, vb); result in (ka, va) after an even number of passes.
-cudaError_t launch_morton_sort(const double* x, int64_t n, const double d[3], uint32_t* ka, uint32_t* va,
-                               uint32_t* kb, uint32_t* vb, uint32_t* hist, cudaStream_t st) {
-    const int bs = 256;
-    k_morton<<<(unsigned)((n + bs - 1) / bs), bs, 0, st>>>(x, n, d[0], d[1], d[2], ka, va);
+// Stable LSD radix sort of (key, value) pairs, 8 bits per pass over `passes` passes
+// (an even number, so the result ends in (ka, va)); (kb, vb) and hist are scratch.
+cudaError_t launch_radix_sort(uint32_t* ka, uint32_t* va, uint32_t* kb, uint32_t* vb, uint32_t* hist, int64_t n,
+                              int passes, cudaStream_t st) {
     const int nblk = sort_blocks(n);
     uint32_t *ki = ka, *vi = va, *ko = kb, *vo = vb;
-    for (int pass = 0; pass < 4; ++pass) {      // 24-bit keys: 3 passes; a 4th (empty digit) keeps the result in (ka, va)
+    for (int pass = 0; pass < passes; ++pass) {
         const int shift = 8 * pass;
         k_sort_hist<<<nblk, kSortThreads, 0, st>>>(ki, n, shift, hist, nblk);
         k_sort_scan<<<1, 1024, 0, st>>>(hist, (int64_t)kRadix * nblk);
@@ -233,11 +260,29 @@ cudaError_t launch_morton_sort(const double* x, int64_t n, const double d[3], ui
     return cudaGetLastError();
 }
 
+// keys/vals ping-pong in (ka, va) <-> (kb, vb); result in (ka, va) after an even number of passes.
+cudaError_t launch_morton_sort(const double* x, int64_t n, const double d[3], uint32_t* ka, uint32_t* va,
+                               uint32_t* kb, uint32_t* vb, uint32_t* hist, cudaStream_t st) {
+    const int bs = 256;
+    k_morton<<<(unsigned)((n + bs - 1) / bs), bs, 0, st>>>(x, n, d[0], d[1], d[2], ka, va);
+    // 24-bit keys need 3 passes; a 4th (empty digit) keeps the result in (ka, va)
+    return launch_radix_sort(ka, va, kb, vb, hist, n, 4, st);
+}
+
 cudaError_t launch_pack32(const double* x, const double* q, const uint32_t* perm, int64_t n, int64_t n_groups,
                           float4* pk_hi, float4* pk_lo, double* org, cudaStream_t st) {
     const int warps = 4;
-    k_pack32<<<(unsigned)((n_groups + warps - 1) / warps), 32 * warps, 0, st>>>(x, q, perm, n, n_groups, pk_hi,
-                                                                                  pk_lo, org);
+    k_pack32<<<(unsigned)((n_groups + warps - 1) / warps), 32 * warps, 0, st>>>(x, q, perm, n, n_groups, nullptr,
+                                                                                  nullptr, pk_hi, pk_lo, org);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack32_groups(const double* x, const double* q, const uint32_t* perm, int64_t n_groups,
+                                 const int64_t* grp_start, const int* grp_count, float4* pk_hi, float4* pk_lo,
+                                 double* org, cudaStream_t st) {
+    const int warps = 4;
+    k_pack32<<<(unsigned)((n_groups + warps - 1) / warps), 32 * warps, 0, st>>>(x, q, perm, 0, n_groups, grp_start,
+                                                                                  grp_count, pk_hi, pk_lo, org);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,109 @@
+"""Batched evaluation of many independent systems (one persistent pair-sum launch, CUDA
+graph replay, autotuned kernel variant) against the oracle and the single-system path."""
+import numpy as np
+import pytest
+
+from oracle import psum_oracle as O
+from paper_1310_4374_gb300 import binding as B
+from paper_1310_4374_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-10, "fp32c": 1e-6}
+
+
+def _cat(systems):
+    x = np.concatenate([s.x for s in systems])
+    q = np.concatenate([s.q for s in systems])
+    return (torch.as_tensor(x, dtype=torch.float64, device="cuda"),
+            torch.as_tensor(q, dtype=torch.float64, device="cuda"))
+
+
+_REF = {}
+
+
+def _oracle(s):
+    if s.name not in _REF:
+        _REF[s.name] = O.periodic_sum(s.x, s.q, s.d, s.p, s.M, parts=True)
+    return _REF[s.name]
+
+
+@pytest.mark.parametrize("precision", ["fp32c", "fp64"])
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_batch_matches_oracle_per_system(precision, use_graph):
+    systems = W.config(4, small=True)
+    pb = B.PeriodicBatch(systems, precision=precision)
+    try:
+        x, q = _cat(systems)
+        phi, g = pb(x, q, use_graph=use_graph)
+        phi = phi.cpu().numpy()
+        g = g.cpu().numpy()
+        for b, s in enumerate(systems):
+            sl = slice(pb.offsets[b], pb.offsets[b + 1])
+            ref = _oracle(s)
+            e_phi = O.relative_l2(phi[sl], ref["phi"])
+            e_g = O.relative_l2(g[sl], ref["grad"])
+            assert e_phi < TOL[precision] and e_g < TOL[precision], (b, s.name, e_phi, e_g)
+            C = B.psum_batch_get_coeffs(pb.batch, b, pb.P[b])
+            assert np.max(np.abs(C - ref["C"])) < (1e-9 if precision == "fp64" else 1e-4) * np.abs(ref["C"]).max()
+        info = B.psum_batch_get_info(pb.batch)
+        assert info["B"] == len(systems) and info["variant"] >= 0 and info["ctas"] >= 1
+    finally:
+        pb.close()
+
+
+def test_batch_agrees_with_single_evaluations():
+    systems = W.config(4, small=True)
+    pb = B.PeriodicBatch(systems, precision="fp32c")
+    try:
+        x, q = _cat(systems)
+        phi, g = pb(x, q)
+        for b, s in enumerate(systems):
+            pc = B.PeriodicCoulomb(s.d, s.p, s.M, precision="fp32c")
+            try:
+                p1, g1 = pc(torch.as_tensor(s.x, device="cuda"), torch.as_tensor(s.q, device="cuda"))
+            finally:
+                pc.close()
+            sl = slice(pb.offsets[b], pb.offsets[b + 1])
+            assert O.relative_l2(phi[sl].cpu().numpy(), p1.cpu().numpy()) < 1e-7
+            assert O.relative_l2(g[sl].cpu().numpy(), g1.cpu().numpy()) < 1e-7
+    finally:
+        pb.close()
+
+
+def test_graph_replay_follows_new_inputs_in_the_same_buffers():
+    systems = W.config(4, small=True)
+    pb = B.PeriodicBatch(systems, precision="fp32c")
+    try:
+        x, q = _cat(systems)
+        phi = torch.empty_like(q)
+        g = torch.empty_like(x)
+        pb(x, q, phi, g, use_graph=True)
+        first = phi.clone()
+        pb(x, q, phi, g, use_graph=True)                 # replay
+        assert torch.equal(first, phi)
+        q.mul_(-2.0)                                     # new charges, same buffer
+        pb(x, q, phi, g, use_graph=True)
+        assert torch.allclose(phi, -2.0 * first, rtol=1e-6, atol=1e-9 * float(first.abs().max()))
+        plain_phi, _ = pb(x, q, use_graph=False)
+        assert torch.equal(plain_phi, phi)
+    finally:
+        pb.close()
+
+
+def test_batch_reports_status_per_system():
+    systems = W.config(4, small=True)
+    pb = B.PeriodicBatch(systems, precision="fp32c")
+    try:
+        x, q = _cat(systems)
+        q[pb.offsets[2]] += 0.25                         # system 2 no longer neutral
+        phi = torch.empty_like(q)
+        B.psum_batch_eval(pb.batch, x, q, phi, None)
+        first, st = B.psum_batch_sync(pb.batch, pb.B)
+        assert first == B.PSUM_ERR_NONNEUTRAL
+        assert st[2] == B.PSUM_ERR_NONNEUTRAL and all(v == 0 for k, v in enumerate(st) if k != 2)
+        sl = slice(pb.offsets[2], pb.offsets[3])
+        assert torch.isnan(phi[sl]).all() and torch.isfinite(phi[:pb.offsets[2]]).all()
+    finally:
+        pb.close()
