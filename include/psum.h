@@ -69,6 +69,10 @@ extern "C" {
 #define PSUM_FP32C  1  /* pair arithmetic in float32 on tile-relative coordinates,
                           compensated (two-sum) accumulation, float64 elsewhere */
 
+#define PSUM_POINTS_FIBONACCI 0  /* M check points on a spherical Fibonacci lattice */
+#define PSUM_POINTS_GAUSS     1  /* the Gauss spherical grid of Sec. 2.2: polar angles at the zeros of
+                                    P_{p+1}(cos theta), 2p+1 equispaced azimuths; M = (p+1)(2p+1) */
+
 #define PSUM_MEAN_ZERO 0  /* C_1 makes the box mean of phi zero (Eq. pfx3, phi_mean = 0) */
 #define PSUM_MEAN_NONE 1  /* C_1 = 0 (potential defined up to a constant, Sec. 3) */
 
@@ -81,6 +85,15 @@ typedef struct psum_opts {
     int precision;   /* PSUM_FP64 or PSUM_FP32C */
     int mean_mode;   /* PSUM_MEAN_ZERO or PSUM_MEAN_NONE */
     int K[3];        /* near block: images |i_k| <= K[k] of the box (Eq. 3, Omega_b); 1 = 3x3x3 */
+    int points;      /* PSUM_POINTS_FIBONACCI or PSUM_POINTS_GAUSS (then M must be 0 or (p+1)(2p+1)) */
+    double lambda;   /* 0: the near set is the block of images above.  lambda > 1: the near set
+                        is trimmed to the ball S_b of radius Rb = lambda R0 (algorithm "get",
+                        step 2): a source image x_i + p counts only if |x_i + p| <= Rb, tested
+                        in float64 as ((a*a + b*b) + c*c) <= Rb*Rb without contraction; K is
+                        then ignored and the block is the smallest one that covers the ball,
+                        K_k = ceil(Rb/d_k + 1/2).  Trimmed plans serve psum_eval, psum_eval_host,
+                        psum_eval_noalloc and psum_energy; psum_energy_backward and the batch
+                        API reject them (PSUM_ERR_ARG). */
 } psum_opts;
 
 typedef struct psum_info {
@@ -96,7 +109,7 @@ typedef struct psum_info {
 } psum_info;
 
 /* Fill `o` with the defaults: unit cube, p = 8, M = 200, PSUM_FP64,
-   PSUM_MEAN_ZERO, K = (1,1,1). */
+   PSUM_MEAN_ZERO, K = (1,1,1), PSUM_POINTS_FIBONACCI, lambda = 0. */
 void psum_opts_default(psum_opts *o);
 
 /* Algorithm "set" (Sec. 2.3.1): circumradius R0 (step 1), M check points on the

@@ -15,6 +15,10 @@
  *
  * Plain loops in double precision, one target at a time; targets are spread
  * over OpenMP threads, which does not change the order of any target's sum.
+ *
+ * With Rb > 0 the near set is trimmed to the ball (algorithm "get", step 2): a source
+ * image x_i - p (sources are indexed x_j = x_i - p, Sec. 2.1) is kept only if
+ * |x_i - p| <= Rb.
  */
 #include <math.h>
 #include <stdint.h>
@@ -33,10 +37,23 @@ int oracle_num_threads(void)
 #endif
 }
 
+void oracle_near_sum_ball(int64_t n_targets, const double *y,
+                          int64_t n_sources, const double *x, const double *q,
+                          const double *d, const int32_t *K, double Rb,
+                          double *phi, double *grad);
+
 void oracle_near_sum(int64_t n_targets, const double *y,
                      int64_t n_sources, const double *x, const double *q,
                      const double *d, const int32_t *K,
                      double *phi, double *grad)
+{
+    oracle_near_sum_ball(n_targets, y, n_sources, x, q, d, K, 0.0, phi, grad);
+}
+
+void oracle_near_sum_ball(int64_t n_targets, const double *y,
+                          int64_t n_sources, const double *x, const double *q,
+                          const double *d, const int32_t *K, double Rb,
+                          double *phi, double *grad)
 {
     int64_t j;
 #pragma omp parallel for schedule(dynamic, 8)
@@ -47,6 +64,11 @@ void oracle_near_sum(int64_t n_targets, const double *y,
         for (int i3 = -K[2]; i3 <= K[2]; ++i3) {
             const double p1 = i1 * d[0], p2 = i2 * d[1], p3 = i3 * d[2];
             for (int64_t i = 0; i < n_sources; ++i) {
+                if (Rb > 0.0) {
+                    const double s1 = x[3 * i + 0] - p1, s2 = x[3 * i + 1] - p2, s3 = x[3 * i + 2] - p3;
+                    if (s1 * s1 + s2 * s2 + s3 * s3 > Rb * Rb)
+                        continue;           /* outside the ball S_b: part of the far field */
+                }
                 const double r1 = y[3 * j + 0] - x[3 * i + 0] + p1;
                 const double r2 = y[3 * j + 1] - x[3 * i + 1] + p2;
                 const double r3 = y[3 * j + 2] - x[3 * i + 2] + p3;

@@ -72,6 +72,18 @@ def fibonacci_checkpoints(M: int, R0: float) -> np.ndarray:
     return R0 * np.stack([rho * np.cos(az), rho * np.sin(az), z], axis=1)
 
 
+def gauss_checkpoints(p: int, R0: float) -> np.ndarray:
+    """The Gauss spherical grid of Sec. 2.2 (ii): polar angles at the zeros of the Legendre
+    polynomial P_{p+1}(cos theta), 2p+1 equispaced azimuths (from 0), radius R0.  With the
+    paper's truncation number p' = p + 1 this is its L = 2p'^2 - p' points."""
+    t, _ = np.polynomial.legendre.leggauss(p + 1)
+    theta = np.arccos(t)
+    az = 2.0 * math.pi * np.arange(2 * p + 1) / (2 * p + 1)
+    TH, AZ = np.meshgrid(theta, az, indexing="ij")
+    return R0 * np.stack([np.sin(TH) * np.cos(AZ), np.sin(TH) * np.sin(AZ), np.cos(TH)],
+                         axis=-1).reshape(-1, 3)
+
+
 # ---------------------------------------------------------------------------
 # "set", step 3: periodic partner of every check point (Sec. 2.3.1, Eq. 7).
 # Two coordinates are kept, the coordinate k with the largest |y_k|/d_k is
@@ -267,12 +279,27 @@ def block_potential(x: np.ndarray, lo, hi) -> np.ndarray:
     return U
 
 
-def near_mean(x, q, d, K=(1, 1, 1)) -> float:
-    """<phi_near>_box = sum_i q_i sum_p Phi_0(x_i + p) (Eq. pfx4)."""
+def near_mean(x, q, d, K=(1, 1, 1), Rb: float = 0.0) -> float:
+    """<phi_near>_box = sum_j q_j Phi_0(x_j) over the near set (Eq. pfx4).
+
+    Without trimming the near set is the whole block of boxes, whose union gives
+    U/V0 of the (2K+1)d block.  With the ball S_b of radius Rb (get step 2) every kept
+    source image x_i - p contributes Phi_0(x_i - p) = U_box(x_i - p)/V0."""
     d = np.asarray(d, dtype=np.float64)
-    half = 0.5 * (2 * np.asarray(K) + 1) * d
-    U = block_potential(x, -half, half)
-    return float(np.dot(q, U) / np.prod(d))
+    x = np.atleast_2d(np.asarray(x, dtype=np.float64))
+    if Rb <= 0.0:
+        half = 0.5 * (2 * np.asarray(K) + 1) * d
+        U = block_potential(x, -half, half)
+        return float(np.dot(q, U) / np.prod(d))
+    total = 0.0
+    for i1 in range(-K[0], K[0] + 1):
+        for i2 in range(-K[1], K[1] + 1):
+            for i3 in range(-K[2], K[2] + 1):
+                xs = x - np.array([i1, i2, i3]) * d
+                keep = np.sum(xs * xs, axis=1) <= Rb * Rb
+                if np.any(keep):
+                    total += float(np.dot(q[keep], block_potential(xs[keep], -0.5 * d, 0.5 * d)))
+    return total / float(np.prod(d))
 
 
 # ---------------------------------------------------------------------------
@@ -291,6 +318,9 @@ def _load():
         lib.oracle_near_sum.argtypes = [ctypes.c_int64, dp, ctypes.c_int64, dp, dp, dp,
                                         ctypes.POINTER(ctypes.c_int32), dp, dp]
         lib.oracle_near_sum.restype = None
+        lib.oracle_near_sum_ball.argtypes = [ctypes.c_int64, dp, ctypes.c_int64, dp, dp, dp,
+                                             ctypes.POINTER(ctypes.c_int32), ctypes.c_double, dp, dp]
+        lib.oracle_near_sum_ball.restype = None
         lib.oracle_num_threads.restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -300,7 +330,7 @@ def num_threads() -> int:
     return int(_load().oracle_num_threads())
 
 
-def near_sum(targets, x, q, d, K=(1, 1, 1), grad: bool = True):
+def near_sum(targets, x, q, d, K=(1, 1, 1), grad: bool = True, Rb: float = 0.0):
     lib = _load()
     targets = np.ascontiguousarray(targets, dtype=np.float64).reshape(-1, 3)
     x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, 3)
@@ -310,10 +340,10 @@ def near_sum(targets, x, q, d, K=(1, 1, 1), grad: bool = True):
     phi = np.zeros(targets.shape[0])
     g = np.zeros((targets.shape[0], 3)) if grad else None
     dp = ctypes.POINTER(ctypes.c_double)
-    lib.oracle_near_sum(targets.shape[0], targets.ctypes.data_as(dp), x.shape[0],
-                        x.ctypes.data_as(dp), q.ctypes.data_as(dp), d.ctypes.data_as(dp),
-                        Karr.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
-                        phi.ctypes.data_as(dp), g.ctypes.data_as(dp) if grad else None)
+    lib.oracle_near_sum_ball(targets.shape[0], targets.ctypes.data_as(dp), x.shape[0],
+                             x.ctypes.data_as(dp), q.ctypes.data_as(dp), d.ctypes.data_as(dp),
+                             Karr.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), float(Rb),
+                             phi.ctypes.data_as(dp), g.ctypes.data_as(dp) if grad else None)
     return (phi, g) if grad else phi
 
 
@@ -325,13 +355,25 @@ def near_sum(targets, x, q, d, K=(1, 1, 1), grad: bool = True):
 class Plan:
     """Algorithm "set" (Sec. 2.3.1) for box d, maximum degree p, M check points."""
 
-    def __init__(self, d, p: int, M: int, K=(1, 1, 1), checkpoints=None):
+    def __init__(self, d, p: int, M: int, K=(1, 1, 1), checkpoints=None, lam: float = 0.0):
+        """checkpoints: None (Fibonacci lattice of M points), "gauss" (the Gauss spherical
+        grid; M is then (p+1)(2p+1)) or an explicit (M, 3) array on the sphere of radius R0.
+        lam > 0 trims the near set to the ball of radius Rb = lam R0 (get step 2); the block
+        of images is then the smallest one that covers the ball."""
         self.d = np.asarray(d, dtype=np.float64)
-        self.p, self.M, self.K = int(p), int(M), tuple(int(k) for k in K)
+        self.p, self.K = int(p), tuple(int(k) for k in K)
         self.P = num_terms(p)
         self.R0 = circumradius(self.d)                                   # step 1
-        self.Y = (fibonacci_checkpoints(M, self.R0) if checkpoints is None
-                  else np.asarray(checkpoints, dtype=np.float64))        # step 2
+        self.Rb = float(lam) * self.R0 if lam and lam > 0 else 0.0
+        if self.Rb > 0.0:
+            self.K = tuple(int(math.ceil(self.Rb / dk + 0.5)) for dk in self.d)
+        if checkpoints is None:                                          # step 2
+            self.Y = fibonacci_checkpoints(M, self.R0)
+        elif isinstance(checkpoints, str) and checkpoints == "gauss":
+            self.Y = gauss_checkpoints(self.p, self.R0)
+        else:
+            self.Y = np.asarray(checkpoints, dtype=np.float64)
+        self.M = int(self.Y.shape[0])
         self.Yt = periodic_partners(self.Y, self.d)                      # step 3
         self.A = fit_matrix(self.Y, self.Yt, self.p, self.R0)            # step 4
         self.factors = qr_factor(self.A)                                 # step 5
@@ -339,13 +381,13 @@ class Plan:
 
     def coefficients(self, x, q, mean: str = "zero"):
         """"get" steps 3-6: near sums at the check points, f, C_2..C_P and C_1."""
-        phi_y = near_sum(self.Y, x, q, self.d, self.K, grad=False)
-        phi_yt = near_sum(self.Yt, x, q, self.d, self.K, grad=False)
+        phi_y = near_sum(self.Y, x, q, self.d, self.K, grad=False, Rb=self.Rb)
+        phi_yt = near_sum(self.Yt, x, q, self.d, self.K, grad=False, Rb=self.Rb)
         f = phi_yt - phi_y                                               # step 4
         C = np.zeros(self.P)
         C[1:] = qr_solve(self.factors, f)                                # step 5
         if mean == "zero":                                               # step 6
-            C[0] = -near_mean(x, q, self.d, self.K) - float(np.dot(C[1:], self.Rbox[1:]))
+            C[0] = -near_mean(x, q, self.d, self.K, self.Rb) - float(np.dot(C[1:], self.Rbox[1:]))
         elif mean != "none":
             raise ValueError(mean)
         return C, f
@@ -367,9 +409,9 @@ class Plan:
             targets = x
         C, f = self.coefficients(x, q, mean)
         if grad:
-            phi_n, g_n = near_sum(targets, x, q, self.d, self.K, grad=True)    # step 3
+            phi_n, g_n = near_sum(targets, x, q, self.d, self.K, grad=True, Rb=self.Rb)  # step 3
         else:
-            phi_n, g_n = near_sum(targets, x, q, self.d, self.K, grad=False), None
+            phi_n, g_n = near_sum(targets, x, q, self.d, self.K, grad=False, Rb=self.Rb), None
         phi_f, g_f = self.far_field(C, targets, grad)                         # step 7
         out = {"phi": phi_n + phi_f, "grad": (g_n + g_f) if grad else None}   # step 8
         if parts:
@@ -387,6 +429,10 @@ def energy_and_gradients(plan: "Plan", x, q, mean: str = "zero"):
         dE/dx_k = q_k [grad phi_near + grad phi_far / 2 + grad psi / 2](x_k).
     (The C_1 term contributes C_1/2 to dE/dq through sum_j q_j; it vanishes from E.)
     """
+    if plan.Rb > 0.0:
+        # with the ball the near set moves with each source, and the zero-mean constant
+        # C_1 depends on which images are kept: the derivation above does not cover it
+        raise NotImplementedError("energy derivatives of a ball-trimmed near set")
     x = np.asarray(x, dtype=np.float64).reshape(-1, 3)
     q = np.asarray(q, dtype=np.float64).reshape(-1)
     out = plan.evaluate(x, q, mean=mean, parts=True)
@@ -397,7 +443,7 @@ def energy_and_gradients(plan: "Plan", x, q, mean: str = "zero"):
     u = Q @ scipy.linalg.solve_triangular(R, w[piv], trans="T", lower=False)
     src = np.concatenate([plan.Yt, plan.Y])
     c = np.concatenate([u, -u])
-    psi, gpsi = near_sum(x, src, c, plan.d, plan.K, grad=True)
+    psi, gpsi = near_sum(x, src, c, plan.d, plan.K, grad=True, Rb=plan.Rb)
     E = 0.5 * float(np.dot(q, out["phi"]))
     dEdq = out["phi_near"] + 0.5 * out["phi_far"] + 0.5 * psi
     dEdx = q[:, None] * (out["grad_near"] + 0.5 * out["grad_far"] + 0.5 * gpsi)
@@ -405,9 +451,9 @@ def energy_and_gradients(plan: "Plan", x, q, mean: str = "zero"):
 
 
 def periodic_sum(x, q, d, p: int, M: int, targets=None, K=(1, 1, 1), grad: bool = True,
-                 mean: str = "zero", parts: bool = False):
+                 mean: str = "zero", parts: bool = False, checkpoints=None, lam: float = 0.0):
     """phi and grad phi of the periodic Coulomb sum at the targets (default: the sources)."""
-    return Plan(d, p, M, K).evaluate(x, q, targets, grad=grad, mean=mean, parts=parts)
+    return Plan(d, p, M, K, checkpoints, lam).evaluate(x, q, targets, grad=grad, mean=mean, parts=parts)
 
 
 def energy(x, q, d, p: int, M: int, K=(1, 1, 1)) -> float:

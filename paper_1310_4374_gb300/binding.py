@@ -31,12 +31,14 @@ PSUM_NUM_STAGES = 5
 STAGE_NAMES = ("prepare", "near_charges", "near_checkpoints", "fit", "far_combine")
 
 PRECISIONS = {"fp64": PSUM_FP64, "fp32c": PSUM_FP32C}
+POINTS = {"fibonacci": 0, "gauss": 1}
 MEAN_MODES = {"zero": PSUM_MEAN_ZERO, "none": PSUM_MEAN_NONE}
 
 
 class psum_opts(ctypes.Structure):
     _fields_ = [("d", ctypes.c_double * 3), ("p", ctypes.c_int), ("M", ctypes.c_int),
-                ("precision", ctypes.c_int), ("mean_mode", ctypes.c_int), ("K", ctypes.c_int * 3)]
+                ("precision", ctypes.c_int), ("mean_mode", ctypes.c_int), ("K", ctypes.c_int * 3),
+                ("points", ctypes.c_int), ("lambda_", ctypes.c_double)]
 
 
 class psum_info(ctypes.Structure):
@@ -158,8 +160,11 @@ def psum_plan_create(d1: float, d2: float, d3: float, p: int, M: int):
     return h
 
 
-def psum_plan_create_ex(d, p: int, M: int, precision="fp64", mean="zero", K=(1, 1, 1)):
+def psum_plan_create_ex(d, p: int, M: int, precision="fp64", mean="zero", K=(1, 1, 1), points="fibonacci",
+                        lam: float = 0.0):
     o = psum_opts_default()
+    o.lambda_ = float(lam)
+    o.points = POINTS[points] if isinstance(points, str) else int(points)
     for k in range(3):
         o.d[k] = float(d[k])
         o.K[k] = int(K[k])
@@ -353,8 +358,9 @@ class PeriodicBatch:
 class PeriodicCoulomb:
     """A plan plus tensor-returning evaluation (allocation through torch only)."""
 
-    def __init__(self, d, p: int, M: int, precision="fp64", mean="zero", K=(1, 1, 1)):
-        self.plan = psum_plan_create_ex(d, p, M, precision, mean, K)
+    def __init__(self, d, p: int, M: int, precision="fp64", mean="zero", K=(1, 1, 1), points="fibonacci",
+                 lam: float = 0.0):
+        self.plan = psum_plan_create_ex(d, p, M, precision, mean, K, points, lam)
         self.info = psum_plan_info(self.plan)
 
     def __call__(self, x, q, grad: bool = True, stream=None, check: bool = True):

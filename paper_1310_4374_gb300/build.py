@@ -21,7 +21,10 @@ BUILD_DIR = os.path.join(HERE, "_build")
 LIB_PATH = os.path.join(BUILD_DIR, "libpsum.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
+# host code without floating-point contraction: the plan's float64 arithmetic (R0, the ball
+# radius, check points) rounds the same way on every host architecture
+NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
+              "--expt-relaxed-constexpr",
               "-Xptxas", "-warn-spills", "-I", INCLUDE, "-I", CSRC]
 
 

@@ -50,6 +50,7 @@ struct Layout {
     uint32_t *ka, *va, *kb, *vb, *hist;
     float4 *pk32, *pk32lo;
     double* org;
+    double* xs;          // float64 packed source positions (trimmed plans)
     // FP64
     double4_32a* pk64;
     // common
@@ -77,10 +78,12 @@ size_t layout(Plan& pl, int64_t N, char* base, Layout& L, bool backward = false,
         L.n_chunks = (N + kNearChunk - 1) / kNearChunk;
         const int64_t n_groups = L.n_tiles * kTgt32;
         L.n_pts = n_groups * kNearChunk;
-        int64_t gmax = (int64_t)pl.num_sms * near32_occupancy_ctas(n_img);
+        const bool trimmed = pl.Rb > 0.0;
+        int64_t gmax = (int64_t)pl.num_sms * near32_occupancy_ctas(n_img, 0, trimmed);
         if (g_cap > 0 && gmax > g_cap) gmax = g_cap;
         L.Ln = near_partition(L.n_tiles, L.n_chunks, n_img, gmax);
         L.Lc = near_partition(pl.n_check_tiles, L.n_chunks, n_img, gmax);
+        L.xs = trimmed ? b.take<double>(3 * (size_t)L.n_pts) : nullptr;
         L.ka = b.take<uint32_t>(N);
         L.va = b.take<uint32_t>(N);
         L.kb = b.take<uint32_t>(N);
@@ -104,6 +107,7 @@ size_t layout(Plan& pl, int64_t N, char* base, Layout& L, bool backward = false,
         L.ka = L.va = L.kb = L.vb = L.hist = nullptr;
         L.pk32 = L.pk32lo = nullptr;
         L.org = nullptr;
+        L.xs = nullptr;
         L.pk64 = b.take<double4_32a>((size_t)L.n_pts);
         L.part_n = b.take<double>((size_t)L.n_tiles * L.Ln.max_contrib * 4 * kTile64);
         L.part_c = b.take<double>((size_t)pl.n_check_tiles * L.Lc.max_contrib * kTile64);
@@ -176,17 +180,16 @@ int ensure_scratch(Plan& pl, size_t need) {
     return PSUM_OK;
 }
 
-int eval_device(psum_plan_s* h, int64_t N, const double* x, const double* q, double* phi, double* grad,
-                cudaStream_t st) {
+// Algorithm "get" on the device for the charges (x, q), with the scratch laid out in L;
+// every kernel is queued on `st`.
+int queue_forward(psum_plan_s* h, int64_t N, const double* x, const double* q, double* phi, double* grad,
+                  const Layout& L, cudaStream_t st) {
     Plan& pl = h->pl;
     const psum_opts& o = pl.opt;
-    Layout L;
-    int rs = ensure_scratch(pl, layout(pl, N, nullptr, L));
-    if (rs != PSUM_OK) return rs;
-    layout(pl, N, (char*)pl.scratch.ptr, L);
     const bool fp32 = o.precision == PSUM_FP32C;
     const int M = o.M, P = pl.P;
     if (h->profile) TRY(cudaEventRecord(h->ev[0], st));
+    // the status word must start at zero; every other buffer is written before it is read
     TRY(cudaMemsetAsync(L.eval_status, 0, sizeof(int), st));
     TRY(launch_validate(x, q, N, o.d, L.val_part, L.nblk_val, L.eval_status, st));
     h->launches += 2;
@@ -194,7 +197,7 @@ int eval_device(psum_plan_s* h, int64_t N, const double* x, const double* q, dou
     if (fp32) {
         TRY(launch_morton_sort(x, N, o.d, L.ka, L.va, L.kb, L.vb, L.hist, st));
         perm = (const int*)L.va;
-        TRY(launch_pack32(x, q, L.va, N, L.n_tiles * kTgt32, L.pk32, L.pk32lo, L.org, st));
+        TRY(launch_pack32(x, q, L.va, N, L.n_tiles * kTgt32, L.pk32, L.pk32lo, L.org, st, L.xs));
         h->launches += 1 + 4 * 3 + 1;
     } else {
         TRY(launch_pack64(x, q, N, L.n_pts, L.pk64, st));
@@ -203,18 +206,19 @@ int eval_device(psum_plan_s* h, int64_t N, const double* x, const double* q, dou
     if (h->profile) TRY(cudaEventRecord(h->ev[1], st));
     if (fp32) {
         TRY(launch_near32(true, L.pk32, L.pk32lo, L.org, L.pk32, L.pk32lo, L.org, pl.d_shifts, L.part_n, L.Ln,
-                          st));
+                          st, 0, L.xs, pl.Rb));
     } else {
-        TRY(launch_near64(true, L.pk64, L.pk64, pl.d_shifts, L.part_n, L.Ln, st));
+        TRY(launch_near64(true, L.pk64, L.pk64, pl.d_shifts, L.part_n, L.Ln, st, pl.Rb));
     }
     if (h->profile) TRY(cudaEventRecord(h->ev[2], st));
     if (fp32) {
         const float4* ct = (const float4*)pl.d_check_tgt;
         const size_t half = 2 * (size_t)pl.n_check_tiles * kTile32;    // hi parts, then lo parts
         TRY(launch_near32(false, L.pk32, L.pk32lo, L.org, ct, ct + half, pl.d_check_org, pl.d_shifts, L.part_c,
-                          L.Lc, st));
+                          L.Lc, st, 0, L.xs, pl.Rb));
     } else {
-        TRY(launch_near64(false, L.pk64, (const double4_32a*)pl.d_check_tgt, pl.d_shifts, L.part_c, L.Lc, st));
+        TRY(launch_near64(false, L.pk64, (const double4_32a*)pl.d_check_tgt, pl.d_shifts, L.part_c, L.Lc, st,
+                          pl.Rb));
     }
     if (h->profile) TRY(cudaEventRecord(h->ev[3], st));
     const int tile = fp32 ? kTile32 : kTile64;
@@ -223,9 +227,13 @@ int eval_device(psum_plan_s* h, int64_t N, const double* x, const double* q, dou
     h->launches += 4;   // two near-field kernels, two reductions
     const bool zero_mean = o.mean_mode == PSUM_MEAN_ZERO;
     if (zero_mean) {
-        const double H[3] = {0.5 * (2 * o.K[0] + 1) * o.d[0], 0.5 * (2 * o.K[1] + 1) * o.d[1],
-                             0.5 * (2 * o.K[2] + 1) * o.d[2]};
-        TRY(launch_box_mean(x, q, N, H, L.mean_part, L.nblk_mean, st));
+        if (pl.Rb > 0.0) {
+            TRY(launch_box_mean_ball(x, q, N, o.d, pl.d_shifts, pl.n_images, pl.Rb, L.mean_part, L.nblk_mean, st));
+        } else {
+            const double H[3] = {0.5 * (2 * o.K[0] + 1) * o.d[0], 0.5 * (2 * o.K[1] + 1) * o.d[1],
+                                 0.5 * (2 * o.K[2] + 1) * o.d[2]};
+            TRY(launch_box_mean(x, q, N, H, L.mean_part, L.nblk_mean, st));
+        }
         h->launches += 1;
     }
     TRY(launch_project(pl.d_pinv, P - 1, M, L.phi_c, pl.d_check_pos, L.f, pl.d_C, st));
@@ -240,6 +248,16 @@ int eval_device(psum_plan_s* h, int64_t N, const double* x, const double* q, dou
     h->launches += 5;   // right-hand side, projection, constant, far field, status merge
     if (h->profile) TRY(cudaEventRecord(h->ev[5], st));
     return PSUM_OK;
+}
+
+int eval_device(psum_plan_s* h, int64_t N, const double* x, const double* q, double* phi, double* grad,
+                cudaStream_t st) {
+    Plan& pl = h->pl;
+    Layout L;
+    int rs = ensure_scratch(pl, layout(pl, N, nullptr, L));
+    if (rs != PSUM_OK) return rs;
+    layout(pl, N, (char*)pl.scratch.ptr, L);
+    return queue_forward(h, N, x, q, phi, grad, L, st);
 }
 
 int backward_device(psum_plan_s* h, int64_t N, const double* x, const double* q, const double* phi,
@@ -295,7 +313,20 @@ bool valid_opts(const psum_opts* o) {
     }
     if (o->p < 1 || o->p > kMaxDegree) return false;
     const int P = (o->p + 1) * (o->p + 1);
-    if (o->M < P - 1 || o->M > 100000) return false;
+    if (o->points != PSUM_POINTS_FIBONACCI && o->points != PSUM_POINTS_GAUSS) return false;
+    if (o->points == PSUM_POINTS_GAUSS) {
+        if (o->M != 0 && o->M != (o->p + 1) * (2 * o->p + 1)) return false;
+    } else if (o->M < P - 1 || o->M > 100000) {
+        return false;
+    }
+    if (!(o->lambda == 0.0 || (o->lambda > 1.0 && o->lambda <= 8.0))) return false;
+    if (o->lambda > 0.0) {
+        // the covering block must stay within the image table
+        const double R0 = 0.5 * std::sqrt(o->d[0] * o->d[0] + o->d[1] * o->d[1] + o->d[2] * o->d[2]);
+        int64_t n = 1;
+        for (int k = 0; k < 3; ++k) n *= 2 * (int64_t)std::ceil(o->lambda * R0 / o->d[k] + 0.5) + 1;
+        if (n > 100000) return false;
+    }
     if (o->precision != PSUM_FP64 && o->precision != PSUM_FP32C) return false;
     if (o->mean_mode != PSUM_MEAN_ZERO && o->mean_mode != PSUM_MEAN_NONE) return false;
     return true;
@@ -314,10 +345,14 @@ void psum_opts_default(psum_opts* o) {
     o->precision = PSUM_FP64;
     o->mean_mode = PSUM_MEAN_ZERO;
     o->K[0] = o->K[1] = o->K[2] = 1;
+    o->points = PSUM_POINTS_FIBONACCI;
+    o->lambda = 0.0;
 }
 
 int psum_plan_create_ex(const psum_opts* o, psum_plan_t* out) {
     if (!out || !valid_opts(o)) return PSUM_ERR_ARG;
+    psum_opts oo = *o;
+    if (oo.points == PSUM_POINTS_GAUSS) oo.M = (oo.p + 1) * (2 * oo.p + 1);
     psum_plan_s* h = new (std::nothrow) psum_plan_s();
     if (!h) return PSUM_ERR_NOMEM;
     int dev = 0;
@@ -328,7 +363,7 @@ int psum_plan_create_ex(const psum_opts* o, psum_plan_t* out) {
     h->pl.device = dev;
     cudaDeviceGetAttribute(&h->pl.num_sms, cudaDevAttrMultiProcessorCount, dev);
     if (h->pl.num_sms < 1) h->pl.num_sms = 1;
-    const int st = build_plan(*o, h->pl);
+    const int st = build_plan(oo, h->pl);
     if (st != PSUM_OK) {
         free_plan_device(h->pl);
         delete h;
@@ -411,6 +446,7 @@ int psum_energy(psum_plan_t h, int64_t N, const double* q, const double* phi, do
 int psum_energy_backward(psum_plan_t h, int64_t N, const double* x, const double* q, const double* phi,
                          const double* grad, const double* gE, double* dEdq, double* dEdx, void* stream) {
     if (!h || N < 1 || N > (int64_t)1 << 30 || !x || !q || !phi || !grad || (!dEdq && !dEdx)) return PSUM_ERR_ARG;
+    if (h->pl.Rb > 0.0) return PSUM_ERR_ARG;   // the adjoint assumes the untrimmed near block
     DeviceGuard g(h->pl.device);
     return backward_device(h, N, x, q, phi, grad, gE, dEdq, dEdx, (cudaStream_t)stream);
 }
@@ -521,70 +557,15 @@ int noalloc_scratch(int dev, char** out) {
 int eval_noalloc_device(psum_plan_s* h, int64_t N, const double* x, const double* q, double* phi, double* grad,
                         cudaStream_t st) {
     Plan& pl = h->pl;
-    const psum_opts& o = pl.opt;
     char* base = nullptr;
     int rs = noalloc_scratch(pl.device, &base);
     if (rs != PSUM_OK) return rs;
     Layout L;
     if (layout(pl, N, nullptr, L, false, kNoAllocMaxCtas) > kNoAllocBytes) return PSUM_ERR_ARG;
     layout(pl, N, base, L, false, kNoAllocMaxCtas);
-    const bool fp32 = o.precision == PSUM_FP32C;
-    const int M = o.M, P = pl.P;
-    if (h->profile) TRY(cudaEventRecord(h->ev[0], st));
-    // the array keeps the previous call's contents: the status word must start at zero;
-    // every other buffer is written before it is read
-    TRY(cudaMemsetAsync(L.eval_status, 0, sizeof(int), st));
-    TRY(launch_validate(x, q, N, o.d, L.val_part, L.nblk_val, L.eval_status, st));
-    h->launches += 2;
-    const int* perm = nullptr;
-    if (fp32) {
-        TRY(launch_morton_sort(x, N, o.d, L.ka, L.va, L.kb, L.vb, L.hist, st));
-        perm = (const int*)L.va;
-        TRY(launch_pack32(x, q, L.va, N, L.n_tiles * kTgt32, L.pk32, L.pk32lo, L.org, st));
-        h->launches += 1 + 4 * 3 + 1;
-    } else {
-        TRY(launch_pack64(x, q, N, L.n_pts, L.pk64, st));
-        h->launches += 1;
-    }
-    if (h->profile) TRY(cudaEventRecord(h->ev[1], st));
-    if (fp32)
-        TRY(launch_near32(true, L.pk32, L.pk32lo, L.org, L.pk32, L.pk32lo, L.org, pl.d_shifts, L.part_n, L.Ln,
-                          st));
-    else
-        TRY(launch_near64(true, L.pk64, L.pk64, pl.d_shifts, L.part_n, L.Ln, st));
-    if (h->profile) TRY(cudaEventRecord(h->ev[2], st));
-    if (fp32) {
-        const float4* ct = (const float4*)pl.d_check_tgt;
-        const size_t half = 2 * (size_t)pl.n_check_tiles * kTile32;
-        TRY(launch_near32(false, L.pk32, L.pk32lo, L.org, ct, ct + half, pl.d_check_org, pl.d_shifts, L.part_c,
-                          L.Lc, st));
-    } else {
-        TRY(launch_near64(false, L.pk64, (const double4_32a*)pl.d_check_tgt, pl.d_shifts, L.part_c, L.Lc, st));
-    }
-    if (h->profile) TRY(cudaEventRecord(h->ev[3], st));
-    const int tile = fp32 ? kTile32 : kTile64;
-    TRY(launch_near_reduce(L.part_n, N, tile, 4, L.Ln, L.phi_n, L.grad_n, st));
-    TRY(launch_near_reduce(L.part_c, pl.n_check, tile, 1, L.Lc, L.phi_c, nullptr, st));
-    h->launches += 4;
-    const bool zero_mean = o.mean_mode == PSUM_MEAN_ZERO;
-    if (zero_mean) {
-        const double H[3] = {0.5 * (2 * o.K[0] + 1) * o.d[0], 0.5 * (2 * o.K[1] + 1) * o.d[1],
-                             0.5 * (2 * o.K[2] + 1) * o.d[2]};
-        TRY(launch_box_mean(x, q, N, H, L.mean_part, L.nblk_mean, st));
-        h->launches += 1;
-    }
-    TRY(launch_project(pl.d_pinv, P - 1, M, L.phi_c, pl.d_check_pos, L.f, pl.d_C, st));
-    TRY(launch_constant(pl.d_C, pl.d_Rbox, P, L.mean_part, L.nblk_mean, 1.0 / (o.d[0] * o.d[1] * o.d[2]),
-                        zero_mean ? 1 : 0, st));
-    if (h->profile) TRY(cudaEventRecord(h->ev[4], st));
-    TRY(launch_far_combine(x, N, perm, L.phi_n, grad ? L.grad_n : nullptr, pl.d_C, o.p, 1.0 / pl.R0,
-                           pl.d_shtab64, fp32 ? pl.d_shtab32 : nullptr, L.eval_status, phi, grad, L.eval_status,
-                           st));
-    k_status_merge<<<1, 1, 0, st>>>(L.eval_status, pl.d_status);
-    TRY(cudaGetLastError());
-    h->launches += 5;
-    if (h->profile) TRY(cudaEventRecord(h->ev[5], st));
-    return PSUM_OK;
+    // the array keeps the previous call's contents; the pipeline zeroes the status word
+    // first and writes every other buffer before reading it
+    return queue_forward(h, N, x, q, phi, grad, L, st);
 }
 
 }  // namespace

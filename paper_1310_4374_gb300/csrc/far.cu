@@ -81,6 +81,34 @@ __global__ void __launch_bounds__(kRedThreads) k_box_mean(const double* __restri
     if (threadIdx.x == 0) partial[blockIdx.x] = s;
 }
 
+// With the near set trimmed to the ball S_b (get step 2) every kept source image x + p
+// (|x + p| <= Rb, the same float64 test as the pair kernels) contributes the potential of
+// the single box at x + p.
+__global__ void __launch_bounds__(kRedThreads) k_box_mean_ball(const double* __restrict__ x,
+                                                               const double* __restrict__ q, int64_t n, double H0,
+                                                               double H1, double H2,
+                                                               const double* __restrict__ shifts, int n_img,
+                                                               double Rb, double* __restrict__ partial) {
+    const double H[3] = {H0, H1, H2};
+    double s = 0.0, dummy = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * kRedThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kRedThreads) {
+        double u = 0.0;
+        for (int im = 0; im < n_img; ++im) {
+            const double* p = shifts + 3 * im;
+            const double a = __dadd_rn(x[3 * i], p[0]), b = __dadd_rn(x[3 * i + 1], p[1]),
+                         c = __dadd_rn(x[3 * i + 2], p[2]);
+            const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(a, a), __dmul_rn(b, b)), __dmul_rn(c, c));
+            if (r2 <= __dmul_rn(Rb, Rb)) {
+                const double X[3] = {a, b, c};
+                u += block_potential(X, H);
+            }
+        }
+        s += q[i] * u;
+    }
+    block_sum2<kRedThreads>(s, dummy);
+    if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
 // ---------------------------------------------------------------------------
 // Steps 4-5: f_l = phi_near(y~_l) - phi_near(y_l), C_{2..P} = A^+ f.
 // One warp per row of the (P-1) x M pseudo-inverse.
@@ -208,6 +236,14 @@ cudaError_t launch_validate(const double* x, const double* q, int64_t n, const d
 cudaError_t launch_box_mean(const double* x, const double* q, int64_t n, const double H[3], double* partial,
                             int nblk, cudaStream_t st) {
     k_box_mean<<<nblk, kRedThreads, 0, st>>>(x, q, n, H[0], H[1], H[2], partial);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_box_mean_ball(const double* x, const double* q, int64_t n, const double d[3],
+                                 const double* shifts, int n_img, double Rb, double* partial, int nblk,
+                                 cudaStream_t st) {
+    k_box_mean_ball<<<nblk, kRedThreads, 0, st>>>(x, q, n, 0.5 * d[0], 0.5 * d[1], 0.5 * d[2], shifts, n_img, Rb,
+                                                 partial);
     return cudaGetLastError();
 }
 

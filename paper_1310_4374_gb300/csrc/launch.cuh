@@ -8,12 +8,13 @@ namespace psum {
 // near.cu
 cudaError_t launch_near32(bool grad, const float4* src_hi, const float4* src_lo, const double* src_org,
                           const float4* tgt_hi, const float4* tgt_lo, const double* tgt_org, const double* shifts,
-                          double* partial, const NearPlanLaunch& L, cudaStream_t st, int variant = 0);
+                          double* partial, const NearPlanLaunch& L, cudaStream_t st, int variant = 0,
+                          const double* src_x = nullptr, double Rb = 0.0);
 cudaError_t launch_near64(bool grad, const double4_32a* src, const double4_32a* tgt, const double* shifts,
-                          double* partial, const NearPlanLaunch& L, cudaStream_t st);
+                          double* partial, const NearPlanLaunch& L, cudaStream_t st, double Rb = 0.0);
 cudaError_t launch_near_reduce(const double* partial, int64_t n_valid, int tile_size, int nq,
                                const NearPlanLaunch& L, double* out_phi, double* out_grad, cudaStream_t st);
-int near32_occupancy_ctas(int n_img, int variant = 0);
+int near32_occupancy_ctas(int n_img, int variant = 0, bool trimmed = false);
 constexpr int kNear32Variants = 2;
 int near64_occupancy_ctas();
 // sort.cu
@@ -21,7 +22,7 @@ int sort_blocks(int64_t n);
 cudaError_t launch_morton_sort(const double* x, int64_t n, const double d[3], uint32_t* ka, uint32_t* va,
                                uint32_t* kb, uint32_t* vb, uint32_t* hist, cudaStream_t st);
 cudaError_t launch_pack32(const double* x, const double* q, const uint32_t* perm, int64_t n, int64_t n_groups,
-                          float4* pk_hi, float4* pk_lo, double* org, cudaStream_t st);
+                          float4* pk_hi, float4* pk_lo, double* org, cudaStream_t st, double* xs = nullptr);
 cudaError_t launch_pack64(const double* x, const double* q, int64_t n, int64_t n_pad, double4_32a* pk, cudaStream_t st);
 cudaError_t launch_radix_sort(uint32_t* ka, uint32_t* va, uint32_t* kb, uint32_t* vb, uint32_t* hist, int64_t n,
                               int passes, cudaStream_t st);
@@ -36,6 +37,10 @@ cudaError_t launch_validate(const double* x, const double* q, int64_t n, const d
                             int nblk, int* status, cudaStream_t st);
 cudaError_t launch_box_mean(const double* x, const double* q, int64_t n, const double H[3], double* partial,
                             int nblk, cudaStream_t st);
+// trimmed near set: sum over the kept images x + p (|x + p| <= Rb) of the single box's potential
+cudaError_t launch_box_mean_ball(const double* x, const double* q, int64_t n, const double d[3],
+                                 const double* shifts, int n_img, double Rb, double* partial, int nblk,
+                                 cudaStream_t st);
 cudaError_t launch_project(const double* pinv, int rows, int M, const double* phi_check, const int* check_pos,
                            double* f, double* C, cudaStream_t st);
 cudaError_t launch_constant(double* C, const double* Rbox, int P, const double* mean_partial, int nblk,

@@ -64,10 +64,25 @@ struct Near32Args {
     const double* tgt_org;   // 4 per target group (kGroupsPerTile32 groups per tile)
     const double* shifts;    // image vectors, 3 per image, systems one after another
     double* partial;         // [tiles][max_contrib][4 or 1][kTile32]
+    const double* src_x;     // float64 positions of the packed sources, 3 per point (ball trimming)
+    double Rb;               // > 0: keep a source image x + p only if |x + p| <= Rb (get step 2)
     int64_t U, G;
     int max_contrib, max_img;
     NearSysTable tab;
 };
+
+// unit classes against the ball S_b (flags in shared memory, per image of the staged chunk)
+constexpr int kUnitNear = 1;       // float-float offsets and K(0) = 0
+constexpr int kUnitOutside = 2;    // every source image outside the ball: nothing to add
+constexpr int kUnitStraddle = 4;   // per-source test against the ball
+
+// |x + p|^2 <= Rb^2 with the rounding of a plain left-to-right evaluation (no contraction),
+// the same decision for a source at the boundary as a straightforward float64 evaluation
+__device__ __forceinline__ bool in_ball(double x0, double x1, double x2, const double* p, double Rb) {
+    const double a = __dadd_rn(x0, p[0]), b = __dadd_rn(x1, p[1]), c = __dadd_rn(x2, p[2]);
+    const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(a, a), __dmul_rn(b, b)), __dmul_rn(c, c));
+    return r2 <= __dmul_rn(Rb, Rb);
+}
 
 #ifndef PSUM_FAR_UNROLL
 #define PSUM_FAR_UNROLL 2
@@ -165,16 +180,17 @@ __device__ __forceinline__ void two_sum_acc2(float2& hi, float2& lo, float2 v) {
 // (up to 102).  The batch autotuner times both.
 constexpr int kNear32MinBlocks[2] = {6, 5};
 
-template <bool kGrad, int kMinB>
+template <bool kGrad, int kMinB, bool kTrim>
 __global__ void __launch_bounds__(kThreads32, kMinB) k_near32(Near32Args a) {
     constexpr int NQ = kGrad ? 4 : 1;
     __shared__ float4 s_hi[2 * kNearChunk];
     __shared__ float4 s_lo[2 * kNearChunk];
     __shared__ float2 s_th[3][2][kThreads32];             // target hi offsets, [coord][pair]
     __shared__ float2 s_acc[NQ][2][2][kThreads32];        // [quantity][pair][hi, lo]
-    extern __shared__ float s_dyn[];                      // [max_img][kTgt32][6] deltas, then [max_img] flags
-    float* s_delta = s_dyn;
-    int* s_near = (int*)(s_dyn + 6 * kTgt32 * a.max_img);
+    extern __shared__ float4 s_dyn4[];                    // [max_img][kTgt32][6] deltas, [max_img] flags,
+    float* s_delta = (float*)s_dyn4;                      // then (trimmed plans) a chunk copy with
+    int* s_near = (int*)(s_delta + 6 * kTgt32 * a.max_img);   // masked charges
+    float4* s_hm = s_dyn4 + (6 * kTgt32 * a.max_img + a.max_img + 3) / 4;
 
     const int tid = threadIdx.x;
     const int64_t g = blockIdx.x;
@@ -252,7 +268,16 @@ __global__ void __launch_bounds__(kThreads32, kMinB) k_near32(Near32Args a) {
                     dl[3] = (float)(D0 - (double)dl[0]); dl[4] = (float)(D1 - (double)dl[1]);
                     dl[5] = (float)(D2 - (double)dl[2]);
                     const double reach = kNearFactor * (to[3] + so[3]);
-                    if (D0 * D0 + D1 * D1 + D2 * D2 <= reach * reach) nr = 1;
+                    if (D0 * D0 + D1 * D1 + D2 * D2 <= reach * reach) nr = kUnitNear;
+                }
+                if (kTrim) {
+                    // the chunk's bounding sphere against the ball, with a margin: the exact
+                    // per-source test decides everything near the sphere
+                    const double c0 = so[0] + sh[0], c1 = so[1] + sh[1], c2 = so[2] + sh[2];
+                    const double c2s = c0 * c0 + c1 * c1 + c2 * c2;
+                    const double ro = a.Rb * (1.0 + 1e-12) + so[3], ri = a.Rb * (1.0 - 1e-12) - so[3];
+                    if (c2s > ro * ro) nr = kUnitOutside;
+                    else if (ri < 0.0 || c2s > ri * ri) nr |= kUnitStraddle;
                 }
                 s_near[im] = nr;
             }
@@ -260,7 +285,23 @@ __global__ void __launch_bounds__(kThreads32, kMinB) k_near32(Near32Args a) {
             cur_chunk = chunk;
         }
         const float* dl = s_delta + 6 * (img * kTgt32);
-        if (s_near[img] != 0) {
+        const int cls = s_near[img];
+        if (kTrim && (cls & kUnitOutside)) {
+            ++u;
+            continue;
+        }
+        if (kTrim && (cls & kUnitStraddle)) {
+            // zero, for this image, the charges of the chunk's sources outside the ball; the
+            // originals wait in s_hm and go back after the pair loop
+            __syncthreads();
+            const double* sh = a.shifts + 3 * (Sp->shift0 + img);
+            const double* xp = a.src_x + 3 * (chunk * kNearChunk + tid);
+            const float4 B = s_hi[2 * tid + 1];
+            s_hm[tid] = B;
+            if (!in_ball(xp[0], xp[1], xp[2], sh, a.Rb)) s_hi[2 * tid + 1] = make_float4(B.x, B.y, 0.f, 0.f);
+            __syncthreads();
+        }
+        if (cls & kUnitNear) {
             // t' = t + delta in float-float: hi by rounding, lo = exact remainder + both lo parts
 #pragma unroll 1
             for (int j = 0; j < 2; ++j) {
@@ -315,6 +356,11 @@ __global__ void __launch_bounds__(kThreads32, kMinB) k_near32(Near32Args a) {
                 }
             }
         }
+        if (kTrim && (s_near[img] & kUnitStraddle)) {
+            __syncthreads();
+            s_hi[2 * tid + 1] = s_hm[tid];
+            __syncthreads();
+        }
         ++u;
     }
     if (cur_tile >= 0) flush(cur_tile, cur_first);
@@ -328,6 +374,7 @@ struct Near64Args {
     const double4_32a* tgt;      // (x, y, z, -)
     const double* shifts;
     double* partial;             // [tiles][max_contrib][4 or 1][kTile64]
+    double Rb;                   // > 0: keep a source image x + p only if |x + p| <= Rb (get step 2)
     int64_t U, G;
     int max_contrib;
     NearSysTable tab;
@@ -344,6 +391,7 @@ __device__ __forceinline__ double rsqrt_f64(double r2) {
 template <bool kGrad>
 __global__ void __launch_bounds__(kThreads64) k_near64(Near64Args a) {
     __shared__ double4_32a s_src[kNearChunk];
+    __shared__ double4_32a s_srcm[kNearChunk];        // the chunk with the image's masked charges
     constexpr int NQ = kGrad ? 4 : 1;
     const int tid = threadIdx.x;
     const int64_t g = blockIdx.x;
@@ -391,9 +439,17 @@ __global__ void __launch_bounds__(kThreads64) k_near64(Near64Args a) {
         // y - x_i - p with the shift folded into the target
         const double* sh = a.shifts + 3 * (S.shift0 + img);
         const double px = tx - sh[0], py = ty - sh[1], pz = tz - sh[2];
+        const double4_32a* src = s_src;
+        if (a.Rb > 0.0) {
+            __syncthreads();
+            const double4_32a Q = s_src[tid];
+            s_srcm[tid] = make_double4_32a(Q.x, Q.y, Q.z, in_ball(Q.x, Q.y, Q.z, sh, a.Rb) ? Q.w : 0.0);
+            __syncthreads();
+            src = s_srcm;
+        }
 #pragma unroll 4
         for (int s = 0; s < kNearChunk; ++s) {
-            const double4_32a Q = s_src[s];
+            const double4_32a Q = src[s];
             const double ex = Q.x - px, ey = Q.y - py, ez = Q.z - pz;   // x_i + p - y
             const double r2 = fma(ez, ez, fma(ey, ey, ex * ex));
             const double ri = r2 > 0.0 ? rsqrt_f64(r2) : 0.0;           // K(0) = 0
@@ -443,35 +499,47 @@ __global__ void k_near_reduce(const double* __restrict__ partial, int64_t n_vali
 // ---------------------------------------------------------------------------
 // Host launchers
 // ---------------------------------------------------------------------------
-size_t near32_dyn_smem(int n_img) { return sizeof(float) * 6 * kTgt32 * n_img + sizeof(int) * n_img; }
+size_t near32_dyn_smem(int n_img, bool trimmed) {
+    const size_t head = ((6 * kTgt32 * (size_t)n_img + n_img + 3) / 4) * sizeof(float4);
+    return head + (trimmed ? sizeof(float4) * kNearChunk : 0);
+}
 
 cudaError_t launch_near32(bool grad, const float4* src_hi, const float4* src_lo, const double* src_org,
                           const float4* tgt_hi, const float4* tgt_lo, const double* tgt_org, const double* shifts,
-                          double* partial, const NearPlanLaunch& L, cudaStream_t st, int variant) {
+                          double* partial, const NearPlanLaunch& L, cudaStream_t st, int variant,
+                          const double* src_x, double Rb) {
     Near32Args a;
     a.src_hi = src_hi; a.src_lo = src_lo; a.src_org = src_org;
     a.tgt_hi = tgt_hi; a.tgt_lo = tgt_lo; a.tgt_org = tgt_org; a.shifts = shifts;
     a.partial = partial; a.U = L.U; a.G = L.G; a.max_contrib = L.max_contrib; a.max_img = L.max_img;
     a.tab = L.tab;
-    const size_t smem = near32_dyn_smem(L.max_img);
-    if (variant == 1) {
+    a.src_x = src_x;
+    a.Rb = Rb;
+    const size_t smem = near32_dyn_smem(L.max_img, Rb > 0.0);
+    if (Rb > 0.0) {
+        // trimmed near sets take the larger register budget: the ball tests add live state
         if (grad)
-            k_near32<true, kNear32MinBlocks[1]><<<(unsigned)L.G, kThreads32, smem, st>>>(a);
+            k_near32<true, kNear32MinBlocks[1], true><<<(unsigned)L.G, kThreads32, smem, st>>>(a);
         else
-            k_near32<false, kNear32MinBlocks[1]><<<(unsigned)L.G, kThreads32, smem, st>>>(a);
+            k_near32<false, kNear32MinBlocks[1], true><<<(unsigned)L.G, kThreads32, smem, st>>>(a);
+    } else if (variant == 1) {
+        if (grad)
+            k_near32<true, kNear32MinBlocks[1], false><<<(unsigned)L.G, kThreads32, smem, st>>>(a);
+        else
+            k_near32<false, kNear32MinBlocks[1], false><<<(unsigned)L.G, kThreads32, smem, st>>>(a);
     } else {
         if (grad)
-            k_near32<true, kNear32MinBlocks[0]><<<(unsigned)L.G, kThreads32, smem, st>>>(a);
+            k_near32<true, kNear32MinBlocks[0], false><<<(unsigned)L.G, kThreads32, smem, st>>>(a);
         else
-            k_near32<false, kNear32MinBlocks[0]><<<(unsigned)L.G, kThreads32, smem, st>>>(a);
+            k_near32<false, kNear32MinBlocks[0], false><<<(unsigned)L.G, kThreads32, smem, st>>>(a);
     }
     return cudaGetLastError();
 }
 
 cudaError_t launch_near64(bool grad, const double4_32a* src, const double4_32a* tgt, const double* shifts,
-                          double* partial, const NearPlanLaunch& L, cudaStream_t st) {
+                          double* partial, const NearPlanLaunch& L, cudaStream_t st, double Rb) {
     Near64Args a;
-    a.src = src; a.tgt = tgt; a.shifts = shifts; a.partial = partial;
+    a.src = src; a.tgt = tgt; a.shifts = shifts; a.partial = partial; a.Rb = Rb;
     a.U = L.U; a.G = L.G; a.max_contrib = L.max_contrib; a.tab = L.tab;
     if (grad)
         k_near64<true><<<(unsigned)L.G, kThreads64, 0, st>>>(a);
@@ -490,14 +558,18 @@ cudaError_t launch_near_reduce(const double* partial, int64_t n_valid, int tile_
     return cudaGetLastError();
 }
 
-int near32_occupancy_ctas(int n_img, int variant) {
+int near32_occupancy_ctas(int n_img, int variant, bool trimmed) {
     int nb = 0;
-    if (variant == 1)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_near32<true, kNear32MinBlocks[1]>, kThreads32,
-                                                      near32_dyn_smem(n_img));
+    const size_t smem = near32_dyn_smem(n_img, trimmed);
+    if (trimmed)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_near32<true, kNear32MinBlocks[1], true>, kThreads32,
+                                                      smem);
+    else if (variant == 1)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_near32<true, kNear32MinBlocks[1], false>, kThreads32,
+                                                      smem);
     else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_near32<true, kNear32MinBlocks[0]>, kThreads32,
-                                                      near32_dyn_smem(n_img));
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_near32<true, kNear32MinBlocks[0], false>, kThreads32,
+                                                      smem);
     return nb < 1 ? 1 : nb;
 }
 

@@ -202,22 +202,51 @@ int build_plan(const psum_opts& o, Plan& pl) {
     const double d[3] = {o.d[0], o.d[1], o.d[2]};
     pl.R0 = 0.5 * std::sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);             // step 1
     // image vectors of the near block and lambda_eff
+    pl.Rb = o.lambda > 0.0 ? o.lambda * pl.R0 : 0.0;
+    int K[3] = {o.K[0], o.K[1], o.K[2]};
+    if (pl.Rb > 0.0)   // the smallest block that covers the ball S_b
+        for (int k = 0; k < 3; ++k) pl.opt.K[k] = K[k] = (int)std::ceil(pl.Rb / d[k] + 0.5);
     pl.shifts.clear();
     pl.self_image = -1;
-    for (int i1 = -o.K[0]; i1 <= o.K[0]; ++i1)
-        for (int i2 = -o.K[1]; i2 <= o.K[1]; ++i2)
-            for (int i3 = -o.K[2]; i3 <= o.K[2]; ++i3) {
+    for (int i1 = -K[0]; i1 <= K[0]; ++i1)
+        for (int i2 = -K[1]; i2 <= K[1]; ++i2)
+            for (int i3 = -K[2]; i3 <= K[2]; ++i3) {
+                const double p0 = i1 * d[0], p1 = i2 * d[1], p2 = i3 * d[2];
+                // with the ball, an image box farther than Rb + R0 holds no kept source
+                // (every source lies in the box, within R0 of its centre)
+                if (pl.Rb > 0.0 && std::sqrt(p0 * p0 + p1 * p1 + p2 * p2) > (pl.Rb + pl.R0) * (1.0 + 1e-12))
+                    continue;
                 if (i1 == 0 && i2 == 0 && i3 == 0) pl.self_image = (int)(pl.shifts.size() / 3);
-                pl.shifts.push_back(i1 * d[0]);
-                pl.shifts.push_back(i2 * d[1]);
-                pl.shifts.push_back(i3 * d[2]);
+                pl.shifts.push_back(p0);
+                pl.shifts.push_back(p1);
+                pl.shifts.push_back(p2);
             }
     pl.n_images = (int)(pl.shifts.size() / 3);
+    if (pl.n_images > kMaxImages) return PSUM_ERR_ARG;
     double hmin = 1e300;
-    for (int k = 0; k < 3; ++k) hmin = std::min(hmin, 0.5 * (2 * o.K[k] + 1) * d[k]);
-    pl.lambda_eff = hmin / pl.R0;
+    for (int k = 0; k < 3; ++k) hmin = std::min(hmin, 0.5 * (2 * K[k] + 1) * d[k]);
+    // the ball's radius is the distance to the nearest far-field source
+    pl.lambda_eff = pl.Rb > 0.0 ? o.lambda : hmin / pl.R0;
 
-    fibonacci_sphere(M, pl.R0, pl.Y);                                                 // step 2
+    if (o.points == PSUM_POINTS_GAUSS) {                                              // step 2
+        // Gauss spherical grid (Sec. 2.2): polar angles at the zeros of P_{p+1}(cos theta),
+        // 2p+1 equispaced azimuths starting at 0
+        std::vector<double> t, w;
+        gauss_legendre(p + 1, t, w);
+        pl.Y.resize(3 * (size_t)M);
+        int l = 0;
+        for (int i = 0; i <= p; ++i) {
+            const double st = std::sqrt(std::max(0.0, 1.0 - t[i] * t[i]));
+            for (int j = 0; j < 2 * p + 1; ++j, ++l) {
+                const double az = 2.0 * M_PI * j / (2 * p + 1);
+                pl.Y[3 * l] = pl.R0 * st * std::cos(az);
+                pl.Y[3 * l + 1] = pl.R0 * st * std::sin(az);
+                pl.Y[3 * l + 2] = pl.R0 * t[i];
+            }
+        }
+    } else {
+        fibonacci_sphere(M, pl.R0, pl.Y);
+    }
     partners(pl.Y, d, pl.Yt);                                                         // step 3
     const int n = pl.P - 1;                                                           // step 4
     std::vector<double> A((size_t)M * n);

@@ -25,7 +25,7 @@ constexpr int kTgt32 = 4;                 // targets per thread, FP32C kernel (2
 constexpr int kTile32 = kThreads32 * kTgt32;
 constexpr int kThreads64 = 128;           // threads per CTA, FP64 kernel
 constexpr int kTile64 = kThreads64;       // one target per thread
-constexpr int kMaxImages = 343;           // K <= 3 per axis
+constexpr int kMaxImages = 343;           // K <= 3 per axis; trimmed plans: images kept
 constexpr int kMaxDegree = 40;
 
 // device status bits (OR-ed by kernels, mapped to PSUM_ERR_* on the host)
@@ -206,6 +206,7 @@ struct Plan {
     int P = 0;                  // (p+1)^2
     double R0 = 0;
     double lambda_eff = 0;
+    double Rb = 0;                  // > 0: near set trimmed to the ball of this radius
     double cond_est = 0;
     int rank = 0;
     int n_images = 0;

@@ -134,7 +134,8 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(const uint32_t* _
 __global__ void k_pack32(const double* __restrict__ x, const double* __restrict__ q,
                          const uint32_t* __restrict__ perm, int64_t n, int64_t n_groups,
                          const int64_t* __restrict__ grp_start, const int* __restrict__ grp_count,
-                         float4* __restrict__ pk_hi, float4* __restrict__ pk_lo, double* __restrict__ org) {
+                         float4* __restrict__ pk_hi, float4* __restrict__ pk_lo, double* __restrict__ org,
+                         double* __restrict__ xs) {
     const int64_t grp = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (grp >= n_groups) return;
@@ -199,6 +200,11 @@ __global__ void k_pack32(const double* __restrict__ x, const double* __restrict_
         pk_hi[2 * s + 1] = make_float4(fz, fz, fq, fq);
         pk_lo[2 * s] = make_float4(lx, lx, ly, ly);
         pk_lo[2 * s + 1] = make_float4(lz, lz, 0.f, 0.f);
+        if (xs) {
+            xs[3 * s] = ok[k] ? px[k][0] : 1.0e3;
+            xs[3 * s + 1] = ok[k] ? px[k][1] : 1.0e3;
+            xs[3 * s + 2] = ok[k] ? px[k][2] : 1.0e3;
+        }
     }
     for (int off = 16; off > 0; off >>= 1) r2max = fmax(r2max, __shfl_xor_sync(0xffffffffu, r2max, off));
     if (lane == 0) {
@@ -270,10 +276,10 @@ cudaError_t launch_morton_sort(const double* x, int64_t n, const double d[3], ui
 }
 
 cudaError_t launch_pack32(const double* x, const double* q, const uint32_t* perm, int64_t n, int64_t n_groups,
-                          float4* pk_hi, float4* pk_lo, double* org, cudaStream_t st) {
+                          float4* pk_hi, float4* pk_lo, double* org, cudaStream_t st, double* xs) {
     const int warps = 4;
     k_pack32<<<(unsigned)((n_groups + warps - 1) / warps), 32 * warps, 0, st>>>(x, q, perm, n, n_groups, nullptr,
-                                                                                  nullptr, pk_hi, pk_lo, org);
+                                                                                  nullptr, pk_hi, pk_lo, org, xs);
     return cudaGetLastError();
 }
 
@@ -282,7 +288,8 @@ cudaError_t launch_pack32_groups(const double* x, const double* q, const uint32_
                                  double* org, cudaStream_t st) {
     const int warps = 4;
     k_pack32<<<(unsigned)((n_groups + warps - 1) / warps), 32 * warps, 0, st>>>(x, q, perm, 0, n_groups, grp_start,
-                                                                                  grp_count, pk_hi, pk_lo, org);
+                                                                                  grp_count, pk_hi, pk_lo, org,
+                                                                                  nullptr);
     return cudaGetLastError();
 }
 

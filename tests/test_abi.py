@@ -62,3 +62,20 @@ def test_null_arguments_are_rejected():
     lib.psum_destroy(None)
     h = ctypes.c_void_p()
     assert lib.psum_plan_create(1.0, 1.0, 1.0, 8, 10, ctypes.byref(h)) == B.PSUM_ERR_ARG
+
+
+@pytest.mark.parametrize("lam", [0.5, 1.0, -1.0, 9.0, float("nan")])
+def test_ball_radius_out_of_range_is_rejected(lam):
+    # lambda = Rb/R0 must exceed 1 (the ball holds the box) and stay within the image table
+    with pytest.raises(B.PsumError) as e:
+        B.psum_plan_create_ex((1, 1, 1), 8, 200, lam=lam)
+    assert e.value.status == B.PSUM_ERR_ARG
+
+
+def test_gauss_grid_fixes_the_number_of_check_points():
+    with pytest.raises(B.PsumError) as e:
+        B.psum_plan_create_ex((1, 1, 1), 8, 5, points="gauss")      # M must be 0 or (p+1)(2p+1)
+    assert e.value.status == B.PSUM_ERR_ARG
+    with pytest.raises(B.PsumError) as e:
+        B.psum_plan_create_ex((1, 1, 1), 8, 200, points=7)
+    assert e.value.status == B.PSUM_ERR_ARG

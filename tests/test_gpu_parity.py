@@ -203,3 +203,71 @@ def test_repeat_calls_are_deterministic():
         assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
     finally:
         pc.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32c"])
+def test_gauss_grid_check_points(precision, madelung):
+    # Sec. 2.2 (ii): the Gauss spherical grid; Table 1 prints eps_M = 4.85e-6 for it at
+    # the paper's p = 8 (build p = 7) on the 2x2x2 rock-salt cell
+    s = W.rock_salt(n=2, p=7, M=0)
+    pc = B.PeriodicCoulomb(s.d, 7, 0, precision=precision, points="gauss")
+    try:
+        assert pc.info["M"] == 8 * 15
+        phi, _ = pc(_dev(s.x), _dev(s.q))
+        eps = np.abs(s.q * phi.cpu().numpy() * s.meta["spacing"] / madelung - 1)
+        assert eps.max() == pytest.approx(4.85e-6, rel=0.05)
+    finally:
+        pc.close()
+    s = W.config(1)
+    pc = B.PeriodicCoulomb(s.d, s.p, 0, precision=precision, points="gauss")
+    try:
+        phi, g = pc(_dev(s.x), _dev(s.q))
+    finally:
+        pc.close()
+    ref = O.periodic_sum(s.x, s.q, s.d, s.p, 0, checkpoints="gauss")
+    assert_parity(phi.cpu().numpy(), g.cpu().numpy(), ref, TOL[precision], f"gauss/{precision}")
+
+
+# get step 2 with the ball S_b: the near set keeps a source image x + p only if
+# |x + p| <= Rb = lambda R0.  Both sides take that decision with the same float64
+# arithmetic, so a differing decision would show as a whole charge's potential.
+TRIM = [("uniform_l1.5", lambda: W.uniform_pm1(N=1200, p=12, M=400, seed=7), 1.5, ("fp64", "fp32c")),
+        ("uniform_lsqrt3", lambda: W.config(1, small=True), 3 ** 0.5, ("fp64", "fp32c")),
+        ("ragged_l2.2", lambda: W.uniform_pm1(N=258, p=8, M=200, seed=3), 2.2, ("fp64", "fp32c")),
+        ("rocksalt_lsqrt3", lambda: W.rock_salt(n=8, p=16, M=2 * 17 * 17), 3 ** 0.5, ("fp64",))]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32c"])
+@pytest.mark.parametrize("name,make,lam,precs", TRIM, ids=[t[0] for t in TRIM])
+def test_ball_trimmed_near_set(name, make, lam, precs, precision):
+    if precision not in precs:
+        pytest.skip("perfect lattice: FP64 workload")
+    s = make()
+    pc = B.PeriodicCoulomb(s.d, s.p, s.M, precision=precision, lam=lam)
+    try:
+        info = pc.info
+        phi, g = pc(_dev(s.x), _dev(s.q))
+        phi, g = phi.cpu().numpy(), g.cpu().numpy()
+    finally:
+        pc.close()
+    ref = O.periodic_sum(s.x, s.q, s.d, s.p, s.M, lam=lam, parts=True)
+    pl = O.Plan(s.d, s.p, s.M, lam=lam)
+    assert tuple(info["K"]) == pl.K and info["lambda_eff"] == pytest.approx(lam)
+    assert info["n_images"] < (2 * pl.K[0] + 1) ** 3      # image boxes beyond Rb + R0 dropped
+    assert_parity(phi, g, ref, TOL[precision], f"{name}/{precision}")
+
+
+def test_ball_trimmed_plans_refuse_backward_and_batches():
+    s = W.uniform_pm1(N=200, p=6, M=100, seed=2)
+    pc = B.PeriodicCoulomb(s.d, s.p, s.M, precision="fp32c", lam=1.5)
+    try:
+        x, q = _dev(s.x), _dev(s.q)
+        phi, g = pc(x, q)
+        with pytest.raises(B.PsumError) as e:
+            B.psum_energy_backward(pc.plan, x, q, phi, g, dEdq=torch.empty_like(q))
+        assert e.value.status == B.PSUM_ERR_ARG
+        with pytest.raises(B.PsumError) as e:
+            B.psum_batch_create([pc.plan], [0, s.x.shape[0]])
+        assert e.value.status == B.PSUM_ERR_ARG
+    finally:
+        pc.close()

@@ -242,3 +242,79 @@ def test_adjoint_gradients_are_the_exact_derivatives_of_the_discrete_energy():
     diff = h14["psi"] - h14["phi_far"]
     assert np.std(diff) < 1e-5 * np.std(h14["phi_far"])
     assert np.max(np.abs(h14["grad_psi"] - h14["grad_far"])) < 1e-4 * np.max(np.abs(h14["grad_far"]))
+
+
+def _table1():
+    import os
+    rows = {}
+    with open(os.path.join(os.path.dirname(__file__), "golden", "table1_eps_M.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                a, b = line.split()
+                rows[int(a)] = float(b)
+    return rows
+
+
+def test_gauss_grid_reproduces_table1(madelung):
+    # Table 1, Gauss spherical grid, lambda = sqrt(3): the paper's truncation number p'
+    # is the build's p + 1.  p' = 8 reproduces the printed 4.85e-6; at p' = 12 and 16 the
+    # error is at or below the printed value and falls with p as the lambda^-p bound says.
+    tab = _table1()
+    s = W.rock_salt(n=2, p=7, M=200)
+    eps = {}
+    for pp in (8, 12, 16):
+        out = O.periodic_sum(s.x, s.q, s.d, pp - 1, 0, grad=False, checkpoints="gauss")
+        eps[pp] = _eps_M(s, out["phi"], madelung).max()
+    assert eps[8] == pytest.approx(tab[8], rel=0.05)
+    assert eps[12] < 10 * tab[12] and eps[16] < tab[16]
+    assert eps[16] < 0.1 * eps[12] and eps[12] < 0.5 * eps[8]
+    pl = O.Plan(s.d, 7, 0, checkpoints="gauss")
+    assert pl.M == 2 * 8 * 8 - 8                                      # L = 2p'^2 - p'
+    assert np.allclose(np.linalg.norm(pl.Y, axis=1), pl.R0, rtol=1e-14)
+
+
+def test_ball_trimmed_near_set_converges_to_ewald_and_madelung(madelung):
+    # get step 2: the near set is cut to the ball of radius Rb = lambda R0; the error falls
+    # like lambda^-p (Eqs. errb1-errb4)
+    s = W.rock_salt(n=2, p=7, M=200)
+    e = {}
+    for lam, p in ((1.3, 16), (1.5, 16), (3 ** 0.5, 16), (1.5, 24)):
+        out = O.periodic_sum(s.x, s.q, s.d, p, 2 * (p + 1) ** 2, lam=lam, grad=False)
+        e[(lam, p)] = _eps_M(s, out["phi"], madelung).max()
+    assert e[(3 ** 0.5, 16)] < 3e-7 < e[(1.3, 16)]
+    assert e[(1.5, 24)] < 1e-8 < e[(1.5, 16)]
+    rng = np.random.default_rng(5)
+    N = 40
+    x = rng.uniform(-0.5, 0.5, (N, 3))
+    q = rng.normal(size=N)
+    q -= q.mean()
+    pe, ge = E.ewald(x, x, q, (1, 1, 1))
+    errs = [O.relative_l2(O.periodic_sum(x, q, (1, 1, 1), p, 2 * (p + 1) ** 2, lam=1.5)["grad"], ge)
+            for p in (12, 16, 20)]
+    assert errs[2] < 1e-6 and errs[2] < 0.1 * errs[0]
+    pl = O.Plan((1, 1, 1), 8, 200, lam=1.5)
+    assert pl.K == (2, 2, 2) and pl.Rb == pytest.approx(1.5 * pl.R0)
+
+
+def test_ball_trimmed_adjoint_is_refused():
+    # the adjoint of the fit assumes a fixed near block; trimmed plans have none
+    pl = O.Plan((1, 1, 1), 6, 100, lam=1.5)
+    x = np.array([[0.1, 0.2, 0.3], [-0.2, 0.1, -0.3]])
+    with pytest.raises(NotImplementedError):
+        O.energy_and_gradients(pl, x, np.array([1.0, -1.0]))
+
+
+def test_ball_near_mean_is_the_sum_over_kept_images():
+    # Eq. pfx4 with the ball: every kept source image contributes the single-box mean of
+    # 1/|r|; a ball that holds the whole block reduces to the block's U/V0, and a ball
+    # holding only the box's own images of the sources gives the single-box value
+    rng = np.random.default_rng(11)
+    x = rng.uniform(-0.5, 0.5, (6, 3))
+    q = rng.normal(size=6)
+    full = O.near_mean(x, q, (1, 1, 1), (1, 1, 1))
+    big = O.near_mean(x, q, (1, 1, 1), (1, 1, 1), Rb=10.0)
+    assert big == pytest.approx(full, rel=1e-12)
+    # sources within 0.25 of the centre per axis: |x| <= 0.44 < Rb = 0.5 < 0.56 <= |x - p|
+    xc = rng.uniform(-0.25, 0.25, (6, 3))
+    own = O.near_mean(xc, q, (1, 1, 1), (0, 0, 0))
+    assert O.near_mean(xc, q, (1, 1, 1), (1, 1, 1), Rb=0.5) == pytest.approx(own, rel=1e-12)
