@@ -24,7 +24,10 @@ Readings where the paper is silent (each is listed in the design notes):
     -sign(y_k) d_k (ties go to the lowest k);
   * basis functions are evaluated at y/R0 (same span, better scaling);
   * the near block Omega_b is the (2K+1)^3 block of boxes (default K=1,
-    i.e. the box and its 26 neighbours), with no trimming to the ball;
+    i.e. the box and its 26 neighbours); optionally the ball S_b of radius
+    lambda R0 (get step 2), a source image kept iff |x + p|^2 <= Rb^2;
+  * the RBF basis of Eq. 5 (optional) puts its kernel centres on a spherical
+    Fibonacci lattice on S_b (the paper used Thomson points, not available);
   * rank tolerance of the QR: |R_kk| >= 1e-13 |R_11|;
   * C1 sets the mean of phi over the box to zero (the Ewald convention,
     App. D Eq. e6), and the mean of phi_near uses the closed-form Newtonian
@@ -177,6 +180,35 @@ def regular_basis(u: np.ndarray, p: int, grad: bool = False):
 # "set", step 4: fitting matrix A_lt = R_t(y_l) - R_t(y~_l) (Eq. 8), with the
 # constant function t = 1 removed because its column is zero (Sec. 3).
 # ---------------------------------------------------------------------------
+
+
+# ---------------------------------------------------------------------------
+# The RBF basis of Eq. 5: R_t(y) = K(y - x_t^(s)) = 1/|y - x_t^(s)| with the
+# kernel centres x_t^(s) outside the ball S_b.  Reading: S centres on a spherical
+# Fibonacci lattice of radius Rs (the paper's Thomson points are not available).
+# ---------------------------------------------------------------------------
+
+
+def rbf_centres(S: int, Rs: float) -> np.ndarray:
+    return fibonacci_checkpoints(S, Rs)
+
+
+def rbf_basis(y: np.ndarray, centres: np.ndarray, grad: bool = False):
+    """R_t(y) = 1/|y - x_t| (S, npts) and, with ``grad``, dR_t/dy (S, 3, npts)."""
+    y = np.atleast_2d(np.asarray(y, dtype=np.float64))
+    r = y[None, :, :] - centres[:, None, :]                 # (S, npts, 3)
+    dist = np.sqrt(np.sum(r * r, axis=2))
+    B = 1.0 / dist
+    if not grad:
+        return B
+    G = -(r / dist[:, :, None] ** 3).transpose(0, 2, 1)     # (S, 3, npts)
+    return B, G
+
+
+def fit_matrix_rbf(Y: np.ndarray, Yt: np.ndarray, centres: np.ndarray) -> np.ndarray:
+    """A_lt = R_t(y_l) - R_t(y~_l) for the RBF basis (Eq. 8 with Eq. 5), (M, S).  No
+    constant column arises: the constant C_1 is a separate unknown, fixed by the mean."""
+    return (rbf_basis(Y, centres) - rbf_basis(Yt, centres)).T.copy()
 
 
 def fit_matrix(Y: np.ndarray, Yt: np.ndarray, p: int, R0: float) -> np.ndarray:
@@ -355,18 +387,27 @@ def near_sum(targets, x, q, d, K=(1, 1, 1), grad: bool = True, Rb: float = 0.0):
 class Plan:
     """Algorithm "set" (Sec. 2.3.1) for box d, maximum degree p, M check points."""
 
-    def __init__(self, d, p: int, M: int, K=(1, 1, 1), checkpoints=None, lam: float = 0.0):
+    def __init__(self, d, p: int, M: int, K=(1, 1, 1), checkpoints=None, lam: float = 0.0,
+                 basis: str = "spherical", n_rbf: int = 256, rbf_radius: float = 0.0):
         """checkpoints: None (Fibonacci lattice of M points), "gauss" (the Gauss spherical
         grid; M is then (p+1)(2p+1)) or an explicit (M, 3) array on the sphere of radius R0.
         lam > 0 trims the near set to the ball of radius Rb = lam R0 (get step 2); the block
-        of images is then the smallest one that covers the ball."""
+        of images is then the smallest one that covers the ball.
+        basis "rbf" takes the n_rbf kernel functions of Eq. 5, centred at radius
+        rbf_radius R0 (0: on S_b, i.e. at lambda_eff R0); P is then n_rbf + 1 (C_1 first)."""
         self.d = np.asarray(d, dtype=np.float64)
         self.p, self.K = int(p), tuple(int(k) for k in K)
-        self.P = num_terms(p)
+        self.basis = basis
+        if basis not in ("spherical", "rbf"):
+            raise ValueError(basis)
+        self.P = num_terms(p) if basis == "spherical" else int(n_rbf) + 1
         self.R0 = circumradius(self.d)                                   # step 1
         self.Rb = float(lam) * self.R0 if lam and lam > 0 else 0.0
         if self.Rb > 0.0:
             self.K = tuple(int(math.ceil(self.Rb / dk + 0.5)) for dk in self.d)
+            self.lambda_eff = float(lam)
+        else:   # the largest ball about the centre inside the block
+            self.lambda_eff = float(min(0.5 * (2 * k + 1) * dk for k, dk in zip(self.K, self.d))) / self.R0
         if checkpoints is None:                                          # step 2
             self.Y = fibonacci_checkpoints(M, self.R0)
         elif isinstance(checkpoints, str) and checkpoints == "gauss":
@@ -375,9 +416,20 @@ class Plan:
             self.Y = np.asarray(checkpoints, dtype=np.float64)
         self.M = int(self.Y.shape[0])
         self.Yt = periodic_partners(self.Y, self.d)                      # step 3
-        self.A = fit_matrix(self.Y, self.Yt, self.p, self.R0)            # step 4
-        self.factors = qr_factor(self.A)                                 # step 5
-        self.Rbox = box_integrals(self.d, self.p, self.R0)               # step 6
+        if basis == "spherical":
+            self.A = fit_matrix(self.Y, self.Yt, self.p, self.R0)        # step 4
+            self.factors = qr_factor(self.A)                             # step 5
+            self.Rbox = box_integrals(self.d, self.p, self.R0)           # step 6
+        else:
+            Rs = (rbf_radius if rbf_radius and rbf_radius > 0 else self.lambda_eff) * self.R0
+            self.centres = rbf_centres(int(n_rbf), Rs)
+            self.A = fit_matrix_rbf(self.Y, self.Yt, self.centres)       # step 4
+            self.factors = qr_factor(self.A)                             # step 5
+            # step 6: the box mean of R_t is the single box's Newtonian potential at the
+            # centre over V0 (App. C applies to the RBF far field, end of Sec. 3)
+            self.Rbox = np.empty(self.P)
+            self.Rbox[0] = 1.0
+            self.Rbox[1:] = block_potential(self.centres, -0.5 * self.d, 0.5 * self.d) / float(np.prod(self.d))
 
     def coefficients(self, x, q, mean: str = "zero"):
         """"get" steps 3-6: near sums at the check points, f, C_2..C_P and C_1."""
@@ -395,6 +447,11 @@ class Plan:
     def far_field(self, C, targets, grad: bool = True):
         """"get" step 7: phi_far = sum_t C_t R_t(y/R0) and its gradient (Eqs. 1.8-1.9)."""
         targets = np.asarray(targets, dtype=np.float64).reshape(-1, 3)
+        if self.basis == "rbf":
+            if grad:
+                B, G = rbf_basis(targets, self.centres, grad=True)
+                return C[0] + C[1:] @ B, np.einsum("t,tkn->nk", C[1:], G)
+            return C[0] + C[1:] @ rbf_basis(targets, self.centres), None
         if grad:
             B, G = regular_basis(targets / self.R0, self.p, grad=True)
             return C @ B, np.einsum("t,tkn->nk", C, G) / self.R0
@@ -429,6 +486,8 @@ def energy_and_gradients(plan: "Plan", x, q, mean: str = "zero"):
         dE/dx_k = q_k [grad phi_near + grad phi_far / 2 + grad psi / 2](x_k).
     (The C_1 term contributes C_1/2 to dE/dq through sum_j q_j; it vanishes from E.)
     """
+    if plan.basis != "spherical":
+        raise NotImplementedError("energy derivatives with the RBF basis")
     if plan.Rb > 0.0:
         # with the ball the near set moves with each source, and the zero-mean constant
         # C_1 depends on which images are kept: the derivation above does not cover it
@@ -451,9 +510,11 @@ def energy_and_gradients(plan: "Plan", x, q, mean: str = "zero"):
 
 
 def periodic_sum(x, q, d, p: int, M: int, targets=None, K=(1, 1, 1), grad: bool = True,
-                 mean: str = "zero", parts: bool = False, checkpoints=None, lam: float = 0.0):
+                 mean: str = "zero", parts: bool = False, checkpoints=None, lam: float = 0.0,
+                 basis: str = "spherical", n_rbf: int = 256, rbf_radius: float = 0.0):
     """phi and grad phi of the periodic Coulomb sum at the targets (default: the sources)."""
-    return Plan(d, p, M, K, checkpoints, lam).evaluate(x, q, targets, grad=grad, mean=mean, parts=parts)
+    return Plan(d, p, M, K, checkpoints, lam, basis, n_rbf, rbf_radius).evaluate(
+        x, q, targets, grad=grad, mean=mean, parts=parts)
 
 
 def energy(x, q, d, p: int, M: int, K=(1, 1, 1)) -> float:

@@ -318,3 +318,81 @@ def test_ball_near_mean_is_the_sum_over_kept_images():
     xc = rng.uniform(-0.25, 0.25, (6, 3))
     own = O.near_mean(xc, q, (1, 1, 1), (0, 0, 0))
     assert O.near_mean(xc, q, (1, 1, 1), (1, 1, 1), Rb=0.5) == pytest.approx(own, rel=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# RBF basis (Eq. 5): kernel functions centred outside S_b
+# ---------------------------------------------------------------------------
+
+
+def test_rbf_basis_madelung_matches_the_papers_order(madelung):
+    # Sec. 4.1: 256 RBF centres on S_b, check points of Table 1's last line (Gauss grid,
+    # the paper's p = 16, i.e. build p = 15): the paper prints eps_M ~ 1.32e-7 with Thomson
+    # centres; Fibonacci centres land at the same order, and the error falls with S
+    s = W.rock_salt(n=2, p=15, M=0)
+    eps = {}
+    for S in (128, 256):
+        out = O.periodic_sum(s.x, s.q, s.d, 15, 0, checkpoints="gauss", basis="rbf", n_rbf=S, grad=False)
+        eps[S] = _eps_M(s, out["phi"], madelung).max()
+    assert 1e-8 < eps[256] < 1e-6
+    assert eps[256] < 0.3 * eps[128]
+    pl = O.Plan(s.d, 15, 0, checkpoints="gauss", basis="rbf", n_rbf=256)
+    assert pl.P == 257 and pl.M == 496
+    assert np.allclose(np.linalg.norm(pl.centres, axis=1), 1.5)      # on S_b: lambda_eff R0 = 1.5 d
+
+
+def test_rbf_basis_agrees_with_ewald_and_with_the_spherical_basis():
+    rng = np.random.default_rng(21)
+    N = 40
+    x = rng.uniform(-0.5, 0.5, (N, 3))
+    q = rng.normal(size=N)
+    q -= q.mean()
+    pe, ge = E.ewald(x, x, q, (1, 1, 1))
+    rbf = O.periodic_sum(x, q, (1, 1, 1), 15, 0, checkpoints="gauss", basis="rbf", n_rbf=256, parts=True)
+    sph = O.periodic_sum(x, q, (1, 1, 1), 15, 0, checkpoints="gauss", parts=True)
+    assert O.relative_l2(rbf["phi"], pe) < 1e-6 and O.relative_l2(rbf["grad"], ge) < 3e-6
+    # the two far fields approximate one harmonic function (the images outside the block)
+    far_scale = np.sqrt(np.mean(sph["phi_far"] ** 2))
+    assert np.sqrt(np.mean((rbf["phi_far"] - sph["phi_far"]) ** 2)) < 5e-6 * far_scale
+
+
+def test_rbf_basis_functions_and_box_means():
+    # R_t = 1/|y - x_t|: gradient by central differences, harmonic away from the centre;
+    # the box mean of R_t (the constant's step 6) against a tensor Gauss-Legendre rule
+    c = O.rbf_centres(5, 1.7)
+    assert np.allclose(np.linalg.norm(c, axis=1), 1.7)
+    rng = np.random.default_rng(4)
+    y = rng.uniform(-0.5, 0.5, (7, 3))
+    B, G = O.rbf_basis(y, c, grad=True)
+    h = 1e-5
+    for k in range(3):
+        e = np.zeros(3)
+        e[k] = h
+        fd = (O.rbf_basis(y + e, c) - O.rbf_basis(y - e, c)) / (2 * h)
+        assert np.allclose(G[:, k, :], fd, rtol=1e-8, atol=1e-10)
+    lap = sum(O.rbf_basis(y + s * np.eye(3)[k] * 1e-3, c) for k in range(3) for s in (1, -1)) - 6 * B
+    assert np.max(np.abs(lap)) < 1e-9
+    d = np.array([1.0, 1.2, 0.8])
+    pl = O.Plan(d, 6, 120, basis="rbf", n_rbf=20)
+    t, w = np.polynomial.legendre.leggauss(24)
+    g = np.stack(np.meshgrid(t, t, t, indexing="ij"), axis=-1).reshape(-1, 3) * 0.5 * d
+    wt = np.einsum("i,j,k->ijk", w, w, w).reshape(-1) / 8.0
+    assert np.allclose(pl.Rbox[1:], O.rbf_basis(g, pl.centres) @ wt, rtol=1e-10)
+
+
+def test_rbf_plan_periodicity_and_zero_mean():
+    rng = np.random.default_rng(23)
+    d = (1.0, 1.0, 1.0)
+    x = rng.uniform(-0.5, 0.5, (20, 3))
+    q = rng.normal(size=20)
+    q -= q.mean()
+    pl = O.Plan(d, 15, 0, checkpoints="gauss", basis="rbf", n_rbf=256)
+    y = rng.uniform(-0.5, 0.5, (12, 3))
+    k = np.arange(12) % 3
+    y[np.arange(12), k] = -0.5
+    yt = y.copy()
+    yt[np.arange(12), k] += 1.0
+    a, b = pl.evaluate(x, q, targets=y)["phi"], pl.evaluate(x, q, targets=yt)["phi"]
+    assert np.max(np.abs(a - b)) < 1e-5 * np.sqrt(np.mean(a ** 2))
+    with pytest.raises(NotImplementedError):
+        O.energy_and_gradients(pl, x, q)
