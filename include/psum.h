@@ -73,6 +73,9 @@ extern "C" {
 #define PSUM_POINTS_GAUSS     1  /* the Gauss spherical grid of Sec. 2.2: polar angles at the zeros of
                                     P_{p+1}(cos theta), 2p+1 equispaced azimuths; M = (p+1)(2p+1) */
 
+#define PSUM_BASIS_SPHERICAL 0  /* regular solid harmonics R^_n^m(y/R0), n <= p (Eqs. 1.6-1.8); P = (p+1)^2 */
+#define PSUM_BASIS_RBF       1  /* kernel functions 1/|y - x_t| centred outside S_b (Eq. 5); P = n_rbf + 1 */
+
 #define PSUM_MEAN_ZERO 0  /* C_1 makes the box mean of phi zero (Eq. pfx3, phi_mean = 0) */
 #define PSUM_MEAN_NONE 1  /* C_1 = 0 (potential defined up to a constant, Sec. 3) */
 
@@ -94,6 +97,13 @@ typedef struct psum_opts {
                         K_k = ceil(Rb/d_k + 1/2).  Trimmed plans serve psum_eval, psum_eval_host,
                         psum_eval_noalloc and psum_energy; psum_energy_backward and the batch
                         API reject them (PSUM_ERR_ARG). */
+    int basis;       /* PSUM_BASIS_SPHERICAL or PSUM_BASIS_RBF.  With the RBF basis (Eq. 5) the far
+                        field is C_1 + sum_t C_t / |y - x_t| over n_rbf centres x_t on a spherical
+                        Fibonacci lattice of radius rbf_radius R0; p then only sizes the Gauss grid,
+                        and M >= n_rbf is required.  psum_get_coeffs returns C_1, C_2..C_{n_rbf+1}.
+                        psum_energy_backward and the batch API reject RBF plans (PSUM_ERR_ARG). */
+    int n_rbf;       /* number of RBF centres, 1..4096 (0: 256, the paper's choice) */
+    double rbf_radius;  /* centres at rbf_radius R0, > 1 (0: on S_b, i.e. at lambda_eff R0) */
 } psum_opts;
 
 typedef struct psum_info {
@@ -109,7 +119,8 @@ typedef struct psum_info {
 } psum_info;
 
 /* Fill `o` with the defaults: unit cube, p = 8, M = 200, PSUM_FP64,
-   PSUM_MEAN_ZERO, K = (1,1,1), PSUM_POINTS_FIBONACCI, lambda = 0. */
+   PSUM_MEAN_ZERO, K = (1,1,1), PSUM_POINTS_FIBONACCI, lambda = 0, PSUM_BASIS_SPHERICAL,
+   n_rbf = 256, rbf_radius = 0. */
 void psum_opts_default(psum_opts *o);
 
 /* Algorithm "set" (Sec. 2.3.1): circumradius R0 (step 1), M check points on the

@@ -32,13 +32,15 @@ STAGE_NAMES = ("prepare", "near_charges", "near_checkpoints", "fit", "far_combin
 
 PRECISIONS = {"fp64": PSUM_FP64, "fp32c": PSUM_FP32C}
 POINTS = {"fibonacci": 0, "gauss": 1}
+BASES = {"spherical": 0, "rbf": 1}
 MEAN_MODES = {"zero": PSUM_MEAN_ZERO, "none": PSUM_MEAN_NONE}
 
 
 class psum_opts(ctypes.Structure):
     _fields_ = [("d", ctypes.c_double * 3), ("p", ctypes.c_int), ("M", ctypes.c_int),
                 ("precision", ctypes.c_int), ("mean_mode", ctypes.c_int), ("K", ctypes.c_int * 3),
-                ("points", ctypes.c_int), ("lambda_", ctypes.c_double)]
+                ("points", ctypes.c_int), ("lambda_", ctypes.c_double), ("basis", ctypes.c_int),
+                ("n_rbf", ctypes.c_int), ("rbf_radius", ctypes.c_double)]
 
 
 class psum_info(ctypes.Structure):
@@ -161,9 +163,12 @@ def psum_plan_create(d1: float, d2: float, d3: float, p: int, M: int):
 
 
 def psum_plan_create_ex(d, p: int, M: int, precision="fp64", mean="zero", K=(1, 1, 1), points="fibonacci",
-                        lam: float = 0.0):
+                        lam: float = 0.0, basis="spherical", n_rbf: int = 256, rbf_radius: float = 0.0):
     o = psum_opts_default()
     o.lambda_ = float(lam)
+    o.basis = BASES[basis] if isinstance(basis, str) else int(basis)
+    o.n_rbf = int(n_rbf)
+    o.rbf_radius = float(rbf_radius)
     o.points = POINTS[points] if isinstance(points, str) else int(points)
     for k in range(3):
         o.d[k] = float(d[k])
@@ -359,8 +364,8 @@ class PeriodicCoulomb:
     """A plan plus tensor-returning evaluation (allocation through torch only)."""
 
     def __init__(self, d, p: int, M: int, precision="fp64", mean="zero", K=(1, 1, 1), points="fibonacci",
-                 lam: float = 0.0):
-        self.plan = psum_plan_create_ex(d, p, M, precision, mean, K, points, lam)
+                 lam: float = 0.0, basis="spherical", n_rbf: int = 256, rbf_radius: float = 0.0):
+        self.plan = psum_plan_create_ex(d, p, M, precision, mean, K, points, lam, basis, n_rbf, rbf_radius)
         self.info = psum_plan_info(self.plan)
 
     def __call__(self, x, q, grad: bool = True, stream=None, check: bool = True):

@@ -73,6 +73,9 @@ size_t layout(Plan& pl, int64_t N, char* base, Layout& L, bool backward = false,
     Bump b{base, 0, 0};
     const bool fp32 = pl.opt.precision == PSUM_FP32C;
     const int n_img = pl.n_images;
+    // a capped width (the allocation-free entry) keeps one work item per CTA: the partial
+    // sums grow with the number of items
+    const int ipc = g_cap > 0 ? 1 : kItemsPerCta;
     if (fp32) {
         L.n_tiles = (N + kTile32 - 1) / kTile32;
         L.n_chunks = (N + kNearChunk - 1) / kNearChunk;
@@ -81,8 +84,8 @@ size_t layout(Plan& pl, int64_t N, char* base, Layout& L, bool backward = false,
         const bool trimmed = pl.Rb > 0.0;
         int64_t gmax = (int64_t)pl.num_sms * near32_occupancy_ctas(n_img, 0, trimmed);
         if (g_cap > 0 && gmax > g_cap) gmax = g_cap;
-        L.Ln = near_partition(L.n_tiles, L.n_chunks, n_img, gmax);
-        L.Lc = near_partition(pl.n_check_tiles, L.n_chunks, n_img, gmax);
+        L.Ln = near_partition(L.n_tiles, L.n_chunks, n_img, gmax, ipc);
+        L.Lc = near_partition(pl.n_check_tiles, L.n_chunks, n_img, gmax, ipc);
         L.xs = trimmed ? b.take<double>(3 * (size_t)L.n_pts) : nullptr;
         L.ka = b.take<uint32_t>(N);
         L.va = b.take<uint32_t>(N);
@@ -102,8 +105,8 @@ size_t layout(Plan& pl, int64_t N, char* base, Layout& L, bool backward = false,
         L.n_pts = L.n_tiles * kTile64;
         int64_t gmax = (int64_t)pl.num_sms * near64_occupancy_ctas();
         if (g_cap > 0 && gmax > g_cap) gmax = g_cap;
-        L.Ln = near_partition(L.n_tiles, L.n_chunks, n_img, gmax);
-        L.Lc = near_partition(pl.n_check_tiles, L.n_chunks, n_img, gmax);
+        L.Ln = near_partition(L.n_tiles, L.n_chunks, n_img, gmax, ipc);
+        L.Lc = near_partition(pl.n_check_tiles, L.n_chunks, n_img, gmax, ipc);
         L.ka = L.va = L.kb = L.vb = L.hist = nullptr;
         L.pk32 = L.pk32lo = nullptr;
         L.org = nullptr;
@@ -120,7 +123,11 @@ size_t layout(Plan& pl, int64_t N, char* base, Layout& L, bool backward = false,
     L.val_part = b.take<double>(2 * (size_t)L.nblk_val);
     L.mean_part = b.take<double>((size_t)L.nblk_mean);
     L.f = b.take<double>((size_t)pl.opt.M);
-    L.eval_status = b.take<int>(1);
+    // the status word and the pair launches' work-item counters
+    int* flags = b.take<int>(8);
+    L.eval_status = flags;
+    L.Ln.counter = flags + 1;
+    L.Lc.counter = flags + 2;
     L.far_phi = L.far_grad = L.w_part = L.w = L.u = L.psi = L.gpsi = L.part_b = nullptr;
     L.chk_src32 = nullptr;
     L.chk_src64 = nullptr;
@@ -130,6 +137,7 @@ size_t layout(Plan& pl, int64_t N, char* base, Layout& L, bool backward = false,
         const int64_t n_chk_chunks = fp32 ? (int64_t)pl.n_check_tiles * kTgt32 : (int64_t)pl.n_check_tiles;
         const int64_t gmax = (int64_t)pl.num_sms * (fp32 ? near32_occupancy_ctas(n_img) : near64_occupancy_ctas());
         L.Lb = near_partition(L.n_tiles, n_chk_chunks, n_img, gmax);
+        L.Lb.counter = flags + 3;
         L.nblk_mom = moments_blocks(N);
         L.far_phi = b.take<double>((size_t)N);
         L.far_grad = b.take<double>(3 * (size_t)N);
@@ -240,9 +248,13 @@ int queue_forward(psum_plan_s* h, int64_t N, const double* x, const double* q, d
     TRY(launch_constant(pl.d_C, pl.d_Rbox, P, L.mean_part, L.nblk_mean, 1.0 / (o.d[0] * o.d[1] * o.d[2]),
                         zero_mean ? 1 : 0, st));
     if (h->profile) TRY(cudaEventRecord(h->ev[4], st));
-    TRY(launch_far_combine(x, N, perm, L.phi_n, grad ? L.grad_n : nullptr, pl.d_C, o.p, 1.0 / pl.R0,
-                           pl.d_shtab64, fp32 ? pl.d_shtab32 : nullptr, L.eval_status, phi, grad, L.eval_status,
-                           st));
+    if (o.basis == PSUM_BASIS_RBF)
+        TRY(launch_far_rbf(x, N, perm, L.phi_n, grad ? L.grad_n : nullptr, pl.d_C, pl.d_rbf, pl.P - 1,
+                           L.eval_status, phi, grad, L.eval_status, st));
+    else
+        TRY(launch_far_combine(x, N, perm, L.phi_n, grad ? L.grad_n : nullptr, pl.d_C, o.p, 1.0 / pl.R0,
+                               pl.d_shtab64, fp32 ? pl.d_shtab32 : nullptr, L.eval_status, phi, grad,
+                               L.eval_status, st));
     k_status_merge<<<1, 1, 0, st>>>(L.eval_status, pl.d_status);
     TRY(cudaGetLastError());
     h->launches += 5;   // right-hand side, projection, constant, far field, status merge
@@ -320,6 +332,13 @@ bool valid_opts(const psum_opts* o) {
         return false;
     }
     if (!(o->lambda == 0.0 || (o->lambda > 1.0 && o->lambda <= 8.0))) return false;
+    if (o->basis != PSUM_BASIS_SPHERICAL && o->basis != PSUM_BASIS_RBF) return false;
+    if (o->basis == PSUM_BASIS_RBF) {
+        const int S = o->n_rbf == 0 ? 256 : o->n_rbf;
+        const int Mv = o->points == PSUM_POINTS_GAUSS ? (o->p + 1) * (2 * o->p + 1) : o->M;
+        if (S < 1 || S > 4096 || Mv < S) return false;
+        if (!(o->rbf_radius == 0.0 || (o->rbf_radius > 1.0 && o->rbf_radius <= 100.0))) return false;
+    }
     if (o->lambda > 0.0) {
         // the covering block must stay within the image table
         const double R0 = 0.5 * std::sqrt(o->d[0] * o->d[0] + o->d[1] * o->d[1] + o->d[2] * o->d[2]);
@@ -347,12 +366,16 @@ void psum_opts_default(psum_opts* o) {
     o->K[0] = o->K[1] = o->K[2] = 1;
     o->points = PSUM_POINTS_FIBONACCI;
     o->lambda = 0.0;
+    o->basis = PSUM_BASIS_SPHERICAL;
+    o->n_rbf = 256;
+    o->rbf_radius = 0.0;
 }
 
 int psum_plan_create_ex(const psum_opts* o, psum_plan_t* out) {
     if (!out || !valid_opts(o)) return PSUM_ERR_ARG;
     psum_opts oo = *o;
     if (oo.points == PSUM_POINTS_GAUSS) oo.M = (oo.p + 1) * (2 * oo.p + 1);
+    if (oo.basis == PSUM_BASIS_RBF && oo.n_rbf == 0) oo.n_rbf = 256;
     psum_plan_s* h = new (std::nothrow) psum_plan_s();
     if (!h) return PSUM_ERR_NOMEM;
     int dev = 0;
@@ -447,6 +470,7 @@ int psum_energy_backward(psum_plan_t h, int64_t N, const double* x, const double
                          const double* grad, const double* gE, double* dEdq, double* dEdx, void* stream) {
     if (!h || N < 1 || N > (int64_t)1 << 30 || !x || !q || !phi || !grad || (!dEdq && !dEdx)) return PSUM_ERR_ARG;
     if (h->pl.Rb > 0.0) return PSUM_ERR_ARG;   // the adjoint assumes the untrimmed near block
+    if (h->pl.opt.basis != PSUM_BASIS_SPHERICAL) return PSUM_ERR_ARG;   // and the solid-harmonic moments
     DeviceGuard g(h->pl.device);
     return backward_device(h, N, x, q, phi, grad, gE, dEdq, dEdx, (cudaStream_t)stream);
 }

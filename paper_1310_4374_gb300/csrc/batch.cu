@@ -375,6 +375,9 @@ size_t batch_layout(psum_batch_s* bt, char* base) {
     bt->val_part = b.take<double>(2 * (size_t)bt->n_seg);
     bt->mean_part = b.take<double>(bt->n_seg);
     bt->d_status = b.take<int>(B);
+    int* counters = b.take<int>(2);            // work-item counters of the two pair launches
+    for (int v = 0; v < kNear32Variants; ++v) bt->Ln[v].counter = counters;
+    bt->Lc.counter = counters + 1;
     return b.off + 256;
 }
 
@@ -512,6 +515,7 @@ int psum_batch_create(const psum_plan_t* plans, int B, const int64_t* offsets, p
         if (plans[b]->pl.opt.precision != plans[0]->pl.opt.precision) return PSUM_ERR_ARG;
         if (plans[b]->pl.device != plans[0]->pl.device) return PSUM_ERR_ARG;
         if (plans[b]->pl.Rb > 0.0) return PSUM_ERR_ARG;   // trimmed near sets: single-system path only
+        if (plans[b]->pl.opt.basis != PSUM_BASIS_SPHERICAL) return PSUM_ERR_ARG;
     }
     if (offsets[B] > ((int64_t)1 << 30)) return PSUM_ERR_ARG;
     psum_batch_s* bt = new (std::nothrow) psum_batch_s();
@@ -574,8 +578,10 @@ int psum_batch_create(const psum_plan_t* plans, int B, const int64_t* offsets, p
             grp_count.push_back((int)std::max<int64_t>(0, std::min<int64_t>(kNearChunk, n - g * kNearChunk)));
         }
         const int64_t chk_tiles = pl.n_check_tiles;
-        bt->near_n[b] = NearSys{unit_n, tile_n, n_tiles, n_chunks, pt / kNearChunk, shift0, pl.n_images};
-        bt->near_c[b] = NearSys{unit_c, tile_c, chk_tiles, n_chunks, pt / kNearChunk, shift0, pl.n_images};
+        bt->near_n[b] = NearSys{unit_n, tile_n, n_tiles, n_chunks, pt / kNearChunk, shift0, pl.n_images,
+                                near_chunk_stride(n_chunks)};
+        bt->near_c[b] = NearSys{unit_c, tile_c, chk_tiles, n_chunks, pt / kNearChunk, shift0, pl.n_images,
+                                near_chunk_stride(n_chunks)};
         unit_n += near_sys_units(bt->near_n[b]);
         unit_c += near_sys_units(bt->near_c[b]);
         tile_n += n_tiles;

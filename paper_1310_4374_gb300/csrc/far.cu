@@ -216,9 +216,88 @@ __global__ void __launch_bounds__(kFarThreads) k_far_combine(const double* __res
     if (!finite) atomicOr(status_out, kStatNonFinite);
 }
 
+// Steps 7-8 with the RBF basis of Eq. 5: phi_far(y) = C_1 + sum_t C_{t+1} / |y - x_t| and
+// its gradient, a pair sum of the targets against the n_rbf centres in float64 (the
+// least-squares coefficients of kernel functions cancel strongly: a float32 sum would
+// lose digits to that cancellation).  Centres with their coefficients are staged in
+// shared memory in blocks of kRbfBlock.
+constexpr int kRbfBlock = 256;
+
+template <bool kGrad>
+__global__ void __launch_bounds__(kFarThreads) k_far_rbf(const double* __restrict__ x, int64_t n,
+                                                         const int* __restrict__ perm,
+                                                         const double* __restrict__ phi_near,
+                                                         const double* __restrict__ grad_near,
+                                                         const double* __restrict__ C,
+                                                         const double* __restrict__ centres, int S,
+                                                         const int* __restrict__ status,
+                                                         double* __restrict__ phi, double* __restrict__ grad,
+                                                         int* __restrict__ status_out) {
+    __shared__ double4_32a s_c[kRbfBlock];
+    const int64_t s = (int64_t)blockIdx.x * kFarThreads + threadIdx.x;
+    const bool live = s < n;
+    const int64_t i = live ? (perm ? (int64_t)perm[s] : s) : 0;
+    const double y0 = live ? x[3 * i] : 0.0, y1 = live ? x[3 * i + 1] : 0.0, y2 = live ? x[3 * i + 2] : 0.0;
+    double f = 0.0, gx = 0.0, gy = 0.0, gz = 0.0;
+    for (int t0 = 0; t0 < S; t0 += kRbfBlock) {
+        const int nb = S - t0 < kRbfBlock ? S - t0 : kRbfBlock;
+        __syncthreads();
+        for (int t = threadIdx.x; t < nb; t += kFarThreads) {
+            const double* c = centres + 3 * (size_t)(t0 + t);
+            s_c[t] = make_double4_32a(c[0], c[1], c[2], C[1 + t0 + t]);
+        }
+        __syncthreads();
+        for (int t = 0; t < nb; ++t) {
+            const double4_32a c = s_c[t];
+            const double a = y0 - c.x, b = y1 - c.y, e = y2 - c.z;
+            const double ri = rsqrt(fma(e, e, fma(b, b, a * a)));
+            const double cr = c.w * ri;
+            f += cr;
+            if (kGrad) {
+                const double cr3 = cr * ri * ri;
+                gx = fma(-cr3, a, gx);
+                gy = fma(-cr3, b, gy);
+                gz = fma(-cr3, e, gz);
+            }
+        }
+    }
+    if (!live) return;
+    const bool failed = (*status & (kStatNonNeutral | kStatOutOfBox | kStatNonFinite)) != 0;
+    if (failed) {
+        phi[i] = __longlong_as_double(0x7ff8000000000000ll);
+        if (grad) grad[3 * i] = grad[3 * i + 1] = grad[3 * i + 2] = __longlong_as_double(0x7ff8000000000000ll);
+        return;
+    }
+    const double ph = phi_near[s] + (C[0] + f);
+    phi[i] = ph;
+    bool finite = fabs(ph) <= 1.7976931348623157e308;
+    if (kGrad) {
+        const double g0 = grad_near[3 * s] + gx, g1 = grad_near[3 * s + 1] + gy, g2 = grad_near[3 * s + 2] + gz;
+        grad[3 * i] = g0;
+        grad[3 * i + 1] = g1;
+        grad[3 * i + 2] = g2;
+        finite = finite && fabs(g0) <= 1.7976931348623157e308 && fabs(g1) <= 1.7976931348623157e308 &&
+                 fabs(g2) <= 1.7976931348623157e308;
+    }
+    if (!finite) atomicOr(status_out, kStatNonFinite);
+}
+
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
+cudaError_t launch_far_rbf(const double* x, int64_t n, const int* perm, const double* phi_near,
+                           const double* grad_near, const double* C, const double* centres, int S, const int* status,
+                           double* phi, double* grad, int* status_out, cudaStream_t st) {
+    const unsigned nb = (unsigned)((n + kFarThreads - 1) / kFarThreads);
+    if (grad)
+        k_far_rbf<true><<<nb, kFarThreads, 0, st>>>(x, n, perm, phi_near, grad_near, C, centres, S, status, phi,
+                                                    grad, status_out);
+    else
+        k_far_rbf<false><<<nb, kFarThreads, 0, st>>>(x, n, perm, phi_near, grad_near, C, centres, S, status, phi,
+                                                     grad, status_out);
+    return cudaGetLastError();
+}
+
 int reduce_blocks(int64_t n, int num_sms) {
     int64_t nb = (n + kRedThreads - 1) / kRedThreads;
     const int64_t cap = 4LL * num_sms;

@@ -37,6 +37,10 @@ cudaError_t launch_validate(const double* x, const double* q, int64_t n, const d
                             int nblk, int* status, cudaStream_t st);
 cudaError_t launch_box_mean(const double* x, const double* q, int64_t n, const double H[3], double* partial,
                             int nblk, cudaStream_t st);
+// far field of the RBF basis (Eq. 5): phi = phi_near + C_1 + sum_t C_{t+1} / |y - x_t|, float64
+cudaError_t launch_far_rbf(const double* x, int64_t n, const int* perm, const double* phi_near,
+                           const double* grad_near, const double* C, const double* centres, int S, const int* status,
+                           double* phi, double* grad, int* status_out, cudaStream_t st);
 // trimmed near set: sum over the kept images x + p (|x + p| <= Rb) of the single box's potential
 cudaError_t launch_box_mean_ball(const double* x, const double* q, int64_t n, const double d[3],
                                  const double* shifts, int n_img, double Rb, double* partial, int nblk,

@@ -16,18 +16,18 @@ namespace psum {
 // the projected point to the edge line (positive inside the face) and t runs
 // along the edge from the foot of the perpendicular.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double edge_primitive(double t, double z, double h) {
+__host__ __device__ __forceinline__ double edge_primitive(double t, double z, double h) {
     const double rho = sqrt(t * t + z * z + h * h);
     const double lg = t >= 0.0 ? log(t + rho) : log((z * z + h * h) / (rho - t));
     return z * lg + h * atan(h * t / (z * rho)) - h * atan(t / z);
 }
 
-__device__ __forceinline__ double edge_integral(double z, double h, double t0, double t1) {
+__host__ __device__ __forceinline__ double edge_integral(double z, double h, double t0, double t1) {
     if (z == 0.0) return 0.0;     // the point projects onto the edge line: the integrand vanishes
     return edge_primitive(t1, z, h) - edge_primitive(t0, z, h);
 }
 
-__device__ __forceinline__ double block_potential(const double X[3], const double H[3]) {
+__host__ __device__ __forceinline__ double block_potential(const double X[3], const double H[3]) {
     double U = 0.0;
     for (int k = 0; k < 3; ++k) {
         const int k1 = (k + 1) % 3, k2 = (k + 2) % 3;

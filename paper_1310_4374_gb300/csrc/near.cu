@@ -66,7 +66,8 @@ struct Near32Args {
     double* partial;         // [tiles][max_contrib][4 or 1][kTile32]
     const double* src_x;     // float64 positions of the packed sources, 3 per point (ball trimming)
     double Rb;               // > 0: keep a source image x + p only if |x + p| <= Rb (get step 2)
-    int64_t U, G;
+    int64_t U, W;            // units, work items
+    int* counter;            // next work item
     int max_contrib, max_img;
     NearSysTable tab;
 };
@@ -90,7 +91,34 @@ __device__ __forceinline__ bool in_ball(double x0, double x1, double x2, const d
 constexpr int kFarUnroll = PSUM_FAR_UNROLL;   // source pairs per unrolled step of the far loop
 
 // Far units: one chunk of sources against the thread's 4 targets (2 packed pairs),
-// plain float32 offsets s - t'.
+// plain float32 offsets s - t'.  One source: its potential terms into qr, its field
+// terms added to the gradient sums.
+template <bool kGrad>
+__device__ __forceinline__ void pair_term(const float4* __restrict__ s_hi, int src, const float2 (&nx)[2],
+                                          const float2 (&ny)[2], const float2 (&nz)[2], float2 (&qr)[2],
+                                          float2 (&agx)[2], float2 (&agy)[2], float2 (&agz)[2]) {
+    const float4 A = s_hi[2 * src];       // x x y y
+    const float4 B = s_hi[2 * src + 1];   // z z q q
+    const float2 sq = make_float2(B.z, B.w);
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        const float2 ex = __fadd2_rn(make_float2(A.x, A.y), nx[j]);
+        const float2 ey = __fadd2_rn(make_float2(A.z, A.w), ny[j]);
+        const float2 ez = __fadd2_rn(make_float2(B.x, B.y), nz[j]);
+        float2 r2 = __fmul2_rn(ex, ex);
+        r2 = __ffma2_rn(ey, ey, r2);
+        r2 = __ffma2_rn(ez, ez, r2);
+        const float2 ri = make_float2(rsqrt_mufu(r2.x), rsqrt_mufu(r2.y));
+        qr[j] = __fmul2_rn(sq, ri);
+        if (kGrad) {
+            const float2 w = __fmul2_rn(qr[j], __fmul2_rn(ri, ri));
+            agx[j] = __ffma2_rn(ex, w, agx[j]);
+            agy[j] = __ffma2_rn(ey, w, agy[j]);
+            agz[j] = __ffma2_rn(ez, w, agz[j]);
+        }
+    }
+}
+
 template <bool kGrad>
 __device__ __forceinline__ void pair_loop_far(const float4* __restrict__ s_hi, const float2 (&nx)[2],
                                               const float2 (&ny)[2], const float2 (&nz)[2], float2 (&aphi)[2],
@@ -99,68 +127,17 @@ __device__ __forceinline__ void pair_loop_far(const float4* __restrict__ s_hi, c
     float2 bphi[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
 #pragma unroll kFarUnroll
     for (int s = 0; s < kNearChunk; s += 2) {
+        float2 q0[2], q1[2];
+        pair_term<kGrad>(s_hi, s, nx, ny, nz, q0, agx, agy, agz);
+        pair_term<kGrad>(s_hi, s + 1, nx, ny, nz, q1, agx, agy, agz);
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const float4 A = s_hi[2 * (s + h)];       // x x y y
-            const float4 B = s_hi[2 * (s + h) + 1];   // z z q q
-            const float2 sq = make_float2(B.z, B.w);
-#pragma unroll
-            for (int j = 0; j < 2; ++j) {
-                const float2 ex = __fadd2_rn(make_float2(A.x, A.y), nx[j]);
-                const float2 ey = __fadd2_rn(make_float2(A.z, A.w), ny[j]);
-                const float2 ez = __fadd2_rn(make_float2(B.x, B.y), nz[j]);
-                float2 r2 = __fmul2_rn(ex, ex);
-                r2 = __ffma2_rn(ey, ey, r2);
-                r2 = __ffma2_rn(ez, ez, r2);
-                const float2 ri = make_float2(rsqrt_mufu(r2.x), rsqrt_mufu(r2.y));
-                const float2 qr = __fmul2_rn(sq, ri);
-                if (h == 0)
-                    aphi[j] = __fadd2_rn(aphi[j], qr);
-                else
-                    bphi[j] = __fadd2_rn(bphi[j], qr);
-                if (kGrad) {
-                    const float2 w = __fmul2_rn(qr, __fmul2_rn(ri, ri));
-                    agx[j] = __ffma2_rn(ex, w, agx[j]);
-                    agy[j] = __ffma2_rn(ey, w, agy[j]);
-                    agz[j] = __ffma2_rn(ez, w, agz[j]);
-                }
-            }
+        for (int j = 0; j < 2; ++j) {
+            aphi[j] = __fadd2_rn(aphi[j], q0[j]);
+            bphi[j] = __fadd2_rn(bphi[j], q1[j]);
         }
     }
     aphi[0] = __fadd2_rn(aphi[0], bphi[0]);
     aphi[1] = __fadd2_rn(aphi[1], bphi[1]);
-}
-
-// Near units: one packed target pair at a time, offsets from hi + lo coordinates,
-// K(0) = 0 applied.
-template <bool kGrad>
-__device__ __forceinline__ void pair_loop_near(const float4* __restrict__ s_hi, const float4* __restrict__ s_lo,
-                                               float2 nhx, float2 nhy, float2 nhz, float2 nlx, float2 nly,
-                                               float2 nlz, float2& aphi, float2& agx, float2& agy, float2& agz) {
-#pragma unroll 2
-    for (int s = 0; s < kNearChunk; ++s) {
-        const float4 A = s_hi[2 * s];
-        const float4 B = s_hi[2 * s + 1];
-        const float4 C = s_lo[2 * s];
-        const float4 D = s_lo[2 * s + 1];
-        const float2 ex = __fadd2_rn(__fadd2_rn(make_float2(A.x, A.y), nhx), __fadd2_rn(make_float2(C.x, C.y), nlx));
-        const float2 ey = __fadd2_rn(__fadd2_rn(make_float2(A.z, A.w), nhy), __fadd2_rn(make_float2(C.z, C.w), nly));
-        const float2 ez = __fadd2_rn(__fadd2_rn(make_float2(B.x, B.y), nhz), __fadd2_rn(make_float2(D.x, D.y), nlz));
-        float2 r2 = __fmul2_rn(ex, ex);
-        r2 = __ffma2_rn(ey, ey, r2);
-        r2 = __ffma2_rn(ez, ez, r2);
-        float2 ri = make_float2(rsqrt_mufu(r2.x), rsqrt_mufu(r2.y));
-        ri.x = r2.x > 0.f ? ri.x : 0.f;                   // K(0) = 0 (Eq. 1)
-        ri.y = r2.y > 0.f ? ri.y : 0.f;
-        const float2 qr = __fmul2_rn(make_float2(B.z, B.w), ri);
-        aphi = __fadd2_rn(aphi, qr);
-        if (kGrad) {
-            const float2 w = __fmul2_rn(qr, __fmul2_rn(ri, ri));
-            agx = __ffma2_rn(ex, w, agx);
-            agy = __ffma2_rn(ey, w, agy);
-            agz = __ffma2_rn(ez, w, agz);
-        }
-    }
 }
 
 // (hi, lo) += v for a packed pair of accumulators: Knuth's two-sum with the error
@@ -174,6 +151,51 @@ __device__ __forceinline__ void two_sum_acc2(float2& hi, float2& lo, float2 v) {
     const float2 e2 = __ffma2_rn(m1, bp, v);              // v - bp
     lo = __fadd2_rn(lo, __fadd2_rn(e1, e2));
     hi = s;
+}
+
+// Near units: one packed target pair at a time, offsets from hi + lo coordinates,
+// K(0) = 0 applied.  They hold the closest pairs, whose large terms would dominate the
+// rounding of a plain float32 running sum of the potential: blocks of kNearFold terms are
+// summed in float32 and each block is added with its rounding error carried (two-sum into
+// aphi, aphi_lo).
+constexpr int kNearFold = 4;
+static_assert(kNearChunk % kNearFold == 0, "whole blocks per chunk");
+
+template <bool kGrad>
+__device__ __forceinline__ void pair_loop_near(const float4* __restrict__ s_hi, const float4* __restrict__ s_lo,
+                                               float2 nhx, float2 nhy, float2 nhz, float2 nlx, float2 nly,
+                                               float2 nlz, float2& aphi, float2& aphi_lo, float2& agx, float2& agy,
+                                               float2& agz) {
+#pragma unroll 1
+    for (int s0 = 0; s0 < kNearChunk; s0 += kNearFold) {
+        float2 blk = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int k = 0; k < kNearFold; ++k) {
+            const int s = s0 + k;
+            const float4 A = s_hi[2 * s];
+            const float4 B = s_hi[2 * s + 1];
+            const float4 C = s_lo[2 * s];
+            const float4 D = s_lo[2 * s + 1];
+            const float2 ex = __fadd2_rn(__fadd2_rn(make_float2(A.x, A.y), nhx), __fadd2_rn(make_float2(C.x, C.y), nlx));
+            const float2 ey = __fadd2_rn(__fadd2_rn(make_float2(A.z, A.w), nhy), __fadd2_rn(make_float2(C.z, C.w), nly));
+            const float2 ez = __fadd2_rn(__fadd2_rn(make_float2(B.x, B.y), nhz), __fadd2_rn(make_float2(D.x, D.y), nlz));
+            float2 r2 = __fmul2_rn(ex, ex);
+            r2 = __ffma2_rn(ey, ey, r2);
+            r2 = __ffma2_rn(ez, ez, r2);
+            float2 ri = make_float2(rsqrt_mufu(r2.x), rsqrt_mufu(r2.y));
+            ri.x = r2.x > 0.f ? ri.x : 0.f;                   // K(0) = 0 (Eq. 1)
+            ri.y = r2.y > 0.f ? ri.y : 0.f;
+            const float2 qr = __fmul2_rn(make_float2(B.z, B.w), ri);
+            blk = k == 0 ? qr : __fadd2_rn(blk, qr);
+            if (kGrad) {
+                const float2 w = __fmul2_rn(qr, __fmul2_rn(ri, ri));
+                agx = __ffma2_rn(ex, w, agx);
+                agy = __ffma2_rn(ey, w, agy);
+                agz = __ffma2_rn(ez, w, agz);
+            }
+        }
+        two_sum_acc2(aphi, aphi_lo, blk);
+    }
 }
 
 // Two register budgets of the same kernel: 6 resident CTAs per SM (80 registers) or 5
@@ -192,15 +214,12 @@ __global__ void __launch_bounds__(kThreads32, kMinB) k_near32(Near32Args a) {
     int* s_near = (int*)(s_delta + 6 * kTgt32 * a.max_img);   // masked charges
     float4* s_hm = s_dyn4 + (6 * kTgt32 * a.max_img + a.max_img + 3) / 4;
 
+    __shared__ int s_item;
     const int tid = threadIdx.x;
-    const int64_t g = blockIdx.x;
-    int64_t u = sk_bound(g, a.U, a.G);
-    const int64_t u_end = sk_bound(g + 1, a.U, a.G);
-    int sb = near_sys_by_unit(a.tab, u);
-    int64_t cur_tile = -1, cur_chunk = -1, cur_first = 0;
+    int64_t item = 0;
 
     auto flush = [&](int64_t tile, int64_t first_unit) {
-        const int64_t slot = g - sk_owner(first_unit, a.U, a.G);
+        const int64_t slot = item - sk_owner(first_unit, a.U, a.W);
         double* dst = a.partial + ((tile * a.max_contrib + slot) * NQ) * kTile32;
 #pragma unroll
         for (int qi = 0; qi < NQ; ++qi)
@@ -212,6 +231,16 @@ __global__ void __launch_bounds__(kThreads32, kMinB) k_near32(Near32Args a) {
             }
     };
 
+    for (;;) {
+    if (tid == 0) s_item = atomicAdd(a.counter, 1);
+    __syncthreads();
+    item = s_item;
+    __syncthreads();                     // every thread has the item before s_item changes
+    if (item >= a.W) break;
+    int64_t u = sk_bound(item, a.U, a.W);
+    const int64_t u_end = sk_bound(item + 1, a.U, a.W);
+    int sb = near_sys_by_unit(a.tab, u);
+    int64_t cur_tile = -1, cur_chunk = -1, cur_first = 0;
     while (u < u_end) {
         // the system descriptor is re-read (parameter or L1) rather than held in registers
         const NearSys* Sp = a.tab.many ? a.tab.many + sb : &a.tab.one;
@@ -227,7 +256,7 @@ __global__ void __launch_bounds__(kThreads32, kMinB) k_near32(Near32Args a) {
         const int64_t chunk_l = rem / n_img;
         const int img = (int)(rem - chunk_l * n_img);
         const int64_t tile = Sp->tile0 + tile_l;
-        const int64_t chunk = Sp->src_chunk0 + chunk_l;
+        const int64_t chunk = Sp->src_chunk0 + (chunk_l * Sp->chunk_stride) % Sp->n_chunks;
         if (tile != cur_tile) {
             if (cur_tile >= 0) flush(cur_tile, cur_first);
 #pragma unroll
@@ -323,9 +352,11 @@ __global__ void __launch_bounds__(kThreads32, kMinB) k_near32(Near32Args a) {
                     nh[c] = make_float2(-h0, -h1);
                     nl[c] = make_float2(-(e0 + (tl.x + d0[3 + c])), -(e1 + (tl.y + d1[3 + c])));
                 }
-                float2 aphi = make_float2(0.f, 0.f), agx = aphi, agy = aphi, agz = aphi;
-                pair_loop_near<kGrad>(s_hi, s_lo, nh[0], nh[1], nh[2], nl[0], nl[1], nl[2], aphi, agx, agy, agz);
+                float2 aphi = make_float2(0.f, 0.f), aphi_lo = aphi, agx = aphi, agy = aphi, agz = aphi;
+                pair_loop_near<kGrad>(s_hi, s_lo, nh[0], nh[1], nh[2], nl[0], nl[1], nl[2], aphi, aphi_lo, agx, agy,
+                                      agz);
                 two_sum_acc2(s_acc[0][j][0][tid], s_acc[0][j][1][tid], aphi);
+                s_acc[0][j][1][tid] = __fadd2_rn(s_acc[0][j][1][tid], aphi_lo);
                 if (kGrad) {
                     two_sum_acc2(s_acc[1 % NQ][j][0][tid], s_acc[1 % NQ][j][1][tid], agx);
                     two_sum_acc2(s_acc[2 % NQ][j][0][tid], s_acc[2 % NQ][j][1][tid], agy);
@@ -364,6 +395,7 @@ __global__ void __launch_bounds__(kThreads32, kMinB) k_near32(Near32Args a) {
         ++u;
     }
     if (cur_tile >= 0) flush(cur_tile, cur_first);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -375,7 +407,8 @@ struct Near64Args {
     const double* shifts;
     double* partial;             // [tiles][max_contrib][4 or 1][kTile64]
     double Rb;                   // > 0: keep a source image x + p only if |x + p| <= Rb (get step 2)
-    int64_t U, G;
+    int64_t U, W;                // units, work items
+    int* counter;                // next work item
     int max_contrib;
     NearSysTable tab;
 };
@@ -393,23 +426,30 @@ __global__ void __launch_bounds__(kThreads64) k_near64(Near64Args a) {
     __shared__ double4_32a s_src[kNearChunk];
     __shared__ double4_32a s_srcm[kNearChunk];        // the chunk with the image's masked charges
     constexpr int NQ = kGrad ? 4 : 1;
+    __shared__ int s_item;
     const int tid = threadIdx.x;
-    const int64_t g = blockIdx.x;
-    int64_t u = sk_bound(g, a.U, a.G);
-    const int64_t u_end = sk_bound(g + 1, a.U, a.G);
-    int sb = near_sys_by_unit(a.tab, u);
-    NearSys S = near_sys_get(a.tab, sb);
+    int64_t item = 0;
     double tx = 0, ty = 0, tz = 0;
     double acc[NQ];
-    int64_t cur_tile = -1, cur_chunk = -1, cur_first = 0;
 
     auto flush = [&](int64_t tile, int64_t first_unit) {
-        const int64_t slot = g - sk_owner(first_unit, a.U, a.G);
+        const int64_t slot = item - sk_owner(first_unit, a.U, a.W);
         double* dst = a.partial + ((tile * a.max_contrib + slot) * NQ) * kTile64;
 #pragma unroll
         for (int qi = 0; qi < NQ; ++qi) dst[qi * kTile64 + tid] = acc[qi];
     };
 
+    for (;;) {
+    if (tid == 0) s_item = atomicAdd(a.counter, 1);
+    __syncthreads();
+    item = s_item;
+    __syncthreads();                     // every thread has the item before s_item changes
+    if (item >= a.W) break;
+    int64_t u = sk_bound(item, a.U, a.W);
+    const int64_t u_end = sk_bound(item + 1, a.U, a.W);
+    int sb = near_sys_by_unit(a.tab, u);
+    NearSys S = near_sys_get(a.tab, sb);
+    int64_t cur_tile = -1, cur_chunk = -1, cur_first = 0;
     while (u < u_end) {
         while (u >= S.unit0 + near_sys_units(S)) S = near_sys_get(a.tab, ++sb);
         const int64_t upt = S.n_chunks * S.n_img;
@@ -419,7 +459,7 @@ __global__ void __launch_bounds__(kThreads64) k_near64(Near64Args a) {
         const int64_t chunk_l = rem / S.n_img;
         const int img = (int)(rem - chunk_l * S.n_img);
         const int64_t tile = S.tile0 + tile_l;
-        const int64_t chunk = S.src_chunk0 + chunk_l;
+        const int64_t chunk = S.src_chunk0 + (chunk_l * S.chunk_stride) % S.n_chunks;
         if (tile != cur_tile) {
             if (cur_tile >= 0) flush(cur_tile, cur_first);
             const double4_32a t = a.tgt[tile * kTile64 + tid];
@@ -465,6 +505,7 @@ __global__ void __launch_bounds__(kThreads64) k_near64(Near64Args a) {
         ++u;
     }
     if (cur_tile >= 0) flush(cur_tile, cur_first);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -472,28 +513,36 @@ __global__ void __launch_bounds__(kThreads64) k_near64(Near64Args a) {
 // index i < n_valid (tile = i / tile_size is the partial-buffer row).
 // ---------------------------------------------------------------------------
 __global__ void k_near_reduce(const double* __restrict__ partial, int64_t n_valid, int tile_size, int nq,
-                              NearSysTable tab, int64_t U, int64_t G, int max_contrib,
+                              NearSysTable tab, int64_t U, int64_t W, int max_contrib,
                               double* __restrict__ out_phi, double* __restrict__ out_grad) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n_valid) return;
+    // one thread per (target, quantity); the slots are read four at a time into four
+    // partial sums combined in a fixed order, so the result does not depend on timing
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n_valid * nq) return;
+    const int qi = (int)(k % nq);
+    const int64_t i = k / nq;
     const int64_t tile = i / tile_size;
     const int loc = (int)(i - tile * tile_size);
     const NearSys S = near_sys_get(tab, near_sys_by_tile(tab, tile));
     const int64_t upt = S.n_chunks * S.n_img;
     const int64_t first = S.unit0 + (tile - S.tile0) * upt;
-    const int64_t g0 = sk_owner(first, U, G);
-    const int64_t g1 = sk_owner(first + upt - 1, U, G);
-    double s[4] = {0, 0, 0, 0};
-    for (int64_t sl = 0; sl <= g1 - g0; ++sl) {
-        const double* src = partial + ((tile * max_contrib + sl) * nq) * tile_size + loc;
-        for (int qi = 0; qi < nq; ++qi) s[qi] += src[qi * tile_size];
+    const int n = (int)(sk_owner(first + upt - 1, U, W) - sk_owner(first, U, W) + 1);
+    const double* src = partial + (tile * max_contrib * nq + qi) * (int64_t)tile_size + loc;
+    const int64_t stride = (int64_t)nq * tile_size;
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    int sl = 0;
+    for (; sl + 4 <= n; sl += 4) {
+        s0 += src[(sl + 0) * stride];
+        s1 += src[(sl + 1) * stride];
+        s2 += src[(sl + 2) * stride];
+        s3 += src[(sl + 3) * stride];
     }
-    out_phi[i] = s[0];
-    if (nq == 4 && out_grad) {
-        out_grad[3 * i + 0] = s[1];
-        out_grad[3 * i + 1] = s[2];
-        out_grad[3 * i + 2] = s[3];
-    }
+    for (; sl < n; ++sl) s0 += src[sl * stride];
+    const double v = (s0 + s1) + (s2 + s3);
+    if (qi == 0)
+        out_phi[i] = v;
+    else if (out_grad)
+        out_grad[3 * i + qi - 1] = v;
 }
 
 // ---------------------------------------------------------------------------
@@ -511,11 +560,15 @@ cudaError_t launch_near32(bool grad, const float4* src_hi, const float4* src_lo,
     Near32Args a;
     a.src_hi = src_hi; a.src_lo = src_lo; a.src_org = src_org;
     a.tgt_hi = tgt_hi; a.tgt_lo = tgt_lo; a.tgt_org = tgt_org; a.shifts = shifts;
-    a.partial = partial; a.U = L.U; a.G = L.G; a.max_contrib = L.max_contrib; a.max_img = L.max_img;
+    a.partial = partial; a.U = L.U; a.W = L.W; a.counter = L.counter; a.max_contrib = L.max_contrib;
+    a.max_img = L.max_img;
     a.tab = L.tab;
     a.src_x = src_x;
     a.Rb = Rb;
     const size_t smem = near32_dyn_smem(L.max_img, Rb > 0.0);
+    if (!L.counter) return cudaErrorInvalidValue;
+    const cudaError_t e = cudaMemsetAsync(L.counter, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
     if (Rb > 0.0) {
         // trimmed near sets take the larger register budget: the ball tests add live state
         if (grad)
@@ -540,7 +593,10 @@ cudaError_t launch_near64(bool grad, const double4_32a* src, const double4_32a* 
                           double* partial, const NearPlanLaunch& L, cudaStream_t st, double Rb) {
     Near64Args a;
     a.src = src; a.tgt = tgt; a.shifts = shifts; a.partial = partial; a.Rb = Rb;
-    a.U = L.U; a.G = L.G; a.max_contrib = L.max_contrib; a.tab = L.tab;
+    a.U = L.U; a.W = L.W; a.counter = L.counter; a.max_contrib = L.max_contrib; a.tab = L.tab;
+    if (!L.counter) return cudaErrorInvalidValue;
+    const cudaError_t e = cudaMemsetAsync(L.counter, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
     if (grad)
         k_near64<true><<<(unsigned)L.G, kThreads64, 0, st>>>(a);
     else
@@ -552,8 +608,8 @@ cudaError_t launch_near_reduce(const double* partial, int64_t n_valid, int tile_
                                const NearPlanLaunch& L, double* out_phi, double* out_grad, cudaStream_t st) {
     if (n_valid <= 0) return cudaSuccess;
     const int bs = 256;
-    const unsigned nb = (unsigned)((n_valid + bs - 1) / bs);
-    k_near_reduce<<<nb, bs, 0, st>>>(partial, n_valid, tile_size, nq, L.tab, L.U, L.G, L.max_contrib, out_phi,
+    const unsigned nb = (unsigned)((n_valid * nq + bs - 1) / bs);
+    k_near_reduce<<<nb, bs, 0, st>>>(partial, n_valid, tile_size, nq, L.tab, L.U, L.W, L.max_contrib, out_phi,
                                      out_grad);
     return cudaGetLastError();
 }

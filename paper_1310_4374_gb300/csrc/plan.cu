@@ -17,6 +17,7 @@
 #include <vector>
 
 #include "psum_internal.cuh"
+#include "mean.cuh"
 
 namespace psum {
 
@@ -198,7 +199,8 @@ static int upload(T** dst, const T* src, size_t count) {
 int build_plan(const psum_opts& o, Plan& pl) {
     pl.opt = o;
     const int p = o.p, M = o.M;
-    pl.P = (p + 1) * (p + 1);
+    const bool rbf = o.basis == PSUM_BASIS_RBF;
+    pl.P = rbf ? o.n_rbf + 1 : (p + 1) * (p + 1);
     const double d[3] = {o.d[0], o.d[1], o.d[2]};
     pl.R0 = 0.5 * std::sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);             // step 1
     // image vectors of the near block and lambda_eff
@@ -250,7 +252,18 @@ int build_plan(const psum_opts& o, Plan& pl) {
     partners(pl.Y, d, pl.Yt);                                                         // step 3
     const int n = pl.P - 1;                                                           // step 4
     std::vector<double> A((size_t)M * n);
-    {
+    if (rbf) {
+        // Eq. 5: R_t(y) = 1/|y - x_t| with the centres on a Fibonacci lattice outside S_b
+        const double Rs = (o.rbf_radius > 0.0 ? o.rbf_radius : pl.lambda_eff) * pl.R0;
+        fibonacci_sphere(n, Rs, pl.Xs);
+        auto kern = [&](const double* y, const double* c) {
+            const double a = y[0] - c[0], b = y[1] - c[1], e = y[2] - c[2];
+            return 1.0 / std::sqrt(a * a + b * b + e * e);
+        };
+        for (int t = 0; t < n; ++t)
+            for (int l = 0; l < M; ++l)
+                A[(size_t)t * M + l] = kern(&pl.Y[3 * l], &pl.Xs[3 * t]) - kern(&pl.Yt[3 * l], &pl.Xs[3 * t]);
+    } else {
         std::vector<double> b1(pl.P), b2(pl.P);
         const double s = 1.0 / pl.R0;
         for (int l = 0; l < M; ++l) {
@@ -261,7 +274,14 @@ int build_plan(const psum_opts& o, Plan& pl) {
     }
     int st = qr_pseudo_inverse(A, M, n, pl.pinv, pl.rank, pl.cond_est);               // step 5
     if (st != PSUM_OK) return st;
-    {                                                                                 // step 6
+    if (rbf) {                                                                        // step 6
+        // the box mean of 1/|y - x_t| is the single box's Newtonian potential at x_t over V0
+        // (App. C applies to the RBF far field)
+        pl.Rbox.assign(pl.P, 0.0);
+        pl.Rbox[0] = 1.0;
+        const double H[3] = {0.5 * d[0], 0.5 * d[1], 0.5 * d[2]};
+        for (int t = 0; t < n; ++t) pl.Rbox[t + 1] = block_potential(&pl.Xs[3 * t], H) / (d[0] * d[1] * d[2]);
+    } else {
         const int nq = p / 2 + 1;
         std::vector<double> t, w;
         gauss_legendre(nq, t, w);
@@ -348,6 +368,7 @@ int build_plan(const psum_opts& o, Plan& pl) {
     if ((s2 = upload(&pl.d_pinv, pl.pinv.data(), pl.pinv.size()))) return s2;
     if ((s2 = upload(&pl.d_Rbox, pl.Rbox.data(), pl.Rbox.size()))) return s2;
     if ((s2 = upload(&pl.d_shifts, pl.shifts.data(), pl.shifts.size()))) return s2;
+    if (rbf && (s2 = upload(&pl.d_rbf, pl.Xs.data(), pl.Xs.size()))) return s2;
     {
         std::vector<double> tab(sh_tab_size(p));
         sh_tab_fill(p, tab.data());
@@ -372,6 +393,7 @@ void free_plan_device(Plan& pl) {
     cudaFree(pl.d_pinv);
     cudaFree(pl.d_Rbox);
     cudaFree(pl.d_shifts);
+    cudaFree(pl.d_rbf);
     cudaFree(pl.d_shtab64);
     cudaFree(pl.d_shtab32);
     cudaFree(pl.d_C);

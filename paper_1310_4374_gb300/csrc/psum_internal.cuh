@@ -214,6 +214,7 @@ struct Plan {
     std::vector<double> Y, Yt;      // M x 3 check points and partners
     std::vector<double> pinv;       // (P-1) x M pseudo-inverse of A (row-major)
     std::vector<double> Rbox;       // P box integrals R_t^(0)
+    std::vector<double> Xs;         // RBF basis: n_rbf centres x 3
     int self_image = 0;             // index of the zero image vector in `shifts`
 
     // check targets (2M points) as the near kernels consume them
@@ -230,6 +231,7 @@ struct Plan {
     double* d_shtab64 = nullptr;    // recurrence coefficients (sh_visit_tab), double
     float* d_shtab32 = nullptr;     // the same in float
     double* d_shifts = nullptr;
+    double* d_rbf = nullptr;        // RBF basis: the n_rbf centres, 3 each
     double* d_C = nullptr;          // P coefficients of the last evaluation
     int* d_status = nullptr;
     int* h_status = nullptr;        // pinned
@@ -249,8 +251,8 @@ int build_plan(const psum_opts& o, Plan& pl);     // algorithm "set" on the host
 void free_plan_device(Plan& pl);
 
 // ---------------------------------------------------------------------------
-// Stream-K partition of the (tile, chunk, image) unit space over G CTAs.
-// CTA g covers units [bound(g), bound(g+1)), bound(g) = floor(g U / G).
+// Equal contiguous ranges of the (tile, chunk, image) unit space: range g of G covers units
+// [bound(g), bound(g+1)), bound(g) = floor(g U / G).
 // ---------------------------------------------------------------------------
 __host__ __device__ __forceinline__ int64_t sk_bound(int64_t g, int64_t U, int64_t G) {
     return (g * U) / G;
@@ -273,7 +275,28 @@ struct NearSys {
     int64_t src_chunk0;  // first chunk of the system in the source pack
     int shift0;          // first image vector of the system in the shift table
     int n_img;
+    int64_t chunk_stride;  // a tile visits its chunks in the order (k * chunk_stride) mod n_chunks
 };
+
+// A stride near n / golden ratio, coprime to n: consecutive steps land far apart in the
+// (Morton-ordered) chunk sequence, so the chunks next to a tile -- the costly float-float
+// "near" units -- spread evenly over the CTAs of the stream-K partition instead of
+// piling up in the few whose unit ranges hold the tile's spatial neighbours.
+inline int64_t near_chunk_stride(int64_t n) {
+    if (n <= 2) return 1;
+    int64_t s = (int64_t)(0.6180339887498949 * (double)n);
+    if (s < 1) s = 1;
+    auto gcd = [](int64_t a, int64_t b) {
+        while (b) {
+            const int64_t t = a % b;
+            a = b;
+            b = t;
+        }
+        return a;
+    };
+    while (gcd(s, n) != 1) ++s;
+    return s;
+}
 
 // A single system travels by value; a batch passes a device array sorted by unit0.
 struct NearSysTable {
@@ -312,8 +335,22 @@ __device__ __forceinline__ int near_sys_by_tile(const NearSysTable& t, int64_t T
     return lo;
 }
 
+// The unit space is cut into W equal contiguous work items (fixed ranges, so every tile's
+// partial slots and every summation order are fixed: results are bitwise reproducible);
+// G resident CTAs take items in order from a device counter.  Co-resident CTAs of an SM
+// progress at different rates (measured: 47-130 ms for equal shares of one 130 ms
+// launch), so a static share per CTA left SMs under-occupied for half the launch.  16
+// items per CTA: the tail is at most one small item; the partial sums grow with the
+// item count (16 KiB per item and tile) and their reduction stays under 1 ms at 1e5 charges.
+#ifndef PSUM_ITEMS_PER_CTA
+#define PSUM_ITEMS_PER_CTA 16
+#endif
+constexpr int kItemsPerCta = PSUM_ITEMS_PER_CTA;
+
 struct NearPlanLaunch {
     int64_t U, G;
+    int64_t W;                    // work items
+    int* counter = nullptr;       // device int, zeroed by the launcher before each launch
     int max_contrib;              // partial slots per tile
     int max_img;                  // largest image count of any system (shared-memory sizing)
     int64_t n_tiles;              // rows of the partial buffer
@@ -323,7 +360,8 @@ struct NearPlanLaunch {
 // Stream-K partition of the systems' units over at most G_max CTAs; the partial
 // buffer needs max_contrib slots per tile.  `dev_tab` is the device copy of `sys`
 // (nullptr when there is one system).
-inline NearPlanLaunch near_partition(const std::vector<NearSys>& sys, int64_t G_max, const NearSys* dev_tab) {
+inline NearPlanLaunch near_partition(const std::vector<NearSys>& sys, int64_t G_max, const NearSys* dev_tab,
+                                     int items_per_cta = kItemsPerCta) {
     NearPlanLaunch L;
     L.U = 0;
     L.max_img = 1;
@@ -335,13 +373,15 @@ inline NearPlanLaunch near_partition(const std::vector<NearSys>& sys, int64_t G_
     }
     L.G = L.U < G_max ? L.U : G_max;
     if (L.G < 1) L.G = 1;
+    L.W = L.G * (items_per_cta < 1 ? 1 : items_per_cta);
+    if (L.W > L.U) L.W = L.U < 1 ? 1 : L.U;
     int mc = 1;
     for (const NearSys& s : sys) {
         const int64_t upt = s.n_chunks * s.n_img;
         for (int64_t t = 0; t < s.n_tiles; ++t) {
             const int64_t u0 = s.unit0 + t * upt;
-            const int64_t g0 = sk_owner(u0, L.U, L.G);
-            const int64_t g1 = sk_owner(u0 + upt - 1, L.U, L.G);
+            const int64_t g0 = sk_owner(u0, L.U, L.W);
+            const int64_t g1 = sk_owner(u0 + upt - 1, L.U, L.W);
             if (g1 - g0 + 1 > mc) mc = (int)(g1 - g0 + 1);
         }
     }
@@ -353,10 +393,11 @@ inline NearPlanLaunch near_partition(const std::vector<NearSys>& sys, int64_t G_
 }
 
 // The single-system case: targets tiles 0..n_tiles-1 against source chunks 0..n_chunks-1.
-inline NearPlanLaunch near_partition(int64_t n_tiles, int64_t n_chunks, int n_img, int64_t G_max) {
+inline NearPlanLaunch near_partition(int64_t n_tiles, int64_t n_chunks, int n_img, int64_t G_max,
+                                     int items_per_cta = kItemsPerCta) {
     std::vector<NearSys> one(1);
-    one[0] = NearSys{0, 0, n_tiles, n_chunks, 0, 0, n_img};
-    return near_partition(one, G_max, nullptr);
+    one[0] = NearSys{0, 0, n_tiles, n_chunks, 0, 0, n_img, near_chunk_stride(n_chunks)};
+    return near_partition(one, G_max, nullptr, items_per_cta);
 }
 
 }  // namespace psum

@@ -72,6 +72,17 @@ def test_ball_radius_out_of_range_is_rejected(lam):
     assert e.value.status == B.PSUM_ERR_ARG
 
 
+@pytest.mark.parametrize("kw", [dict(n_rbf=300), dict(n_rbf=-1), dict(n_rbf=5000), dict(rbf_radius=0.9),
+                                dict(rbf_radius=float("inf")), dict(basis=2)])
+def test_rbf_options_out_of_range_are_rejected(kw):
+    # Eq. 5 needs the centres outside the circumsphere, and M >= n_rbf check points
+    args = dict(basis="rbf", n_rbf=100)
+    args.update(kw)
+    with pytest.raises(B.PsumError) as e:
+        B.psum_plan_create_ex((1, 1, 1), 8, 200, **args)
+    assert e.value.status == B.PSUM_ERR_ARG
+
+
 def test_gauss_grid_fixes_the_number_of_check_points():
     with pytest.raises(B.PsumError) as e:
         B.psum_plan_create_ex((1, 1, 1), 8, 5, points="gauss")      # M must be 0 or (p+1)(2p+1)

@@ -271,3 +271,48 @@ def test_ball_trimmed_plans_refuse_backward_and_batches():
         assert e.value.status == B.PSUM_ERR_ARG
     finally:
         pc.close()
+
+
+# The RBF basis of Eq. 5: far field C_1 + sum_t C_t / |y - x_t| with centres on S_b.
+RBF = [("unit_gauss15", lambda: W.uniform_pm1(N=1000, p=15, M=0, seed=9), dict(points="gauss")),
+       ("cfg3_small", lambda: W.config(3, small=True), dict()),
+       ("ragged_r2", lambda: W.uniform_pm1(N=130, p=8, M=300, seed=4), dict(n_rbf=200, rbf_radius=2.0)),
+       ("trimmed_l1.5", lambda: W.uniform_pm1(N=600, p=12, M=400, seed=8), dict(lam=1.5))]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32c"])
+@pytest.mark.parametrize("name,make,kw", RBF, ids=[r[0] for r in RBF])
+def test_rbf_basis(name, make, kw, precision):
+    s = make()
+    gauss = kw.get("points") == "gauss"
+    M = 0 if gauss else s.M
+    n_rbf, radius, lam = kw.get("n_rbf", 256), kw.get("rbf_radius", 0.0), kw.get("lam", 0.0)
+    pc = B.PeriodicCoulomb(s.d, s.p, M, precision=precision, points="gauss" if gauss else "fibonacci", lam=lam,
+                           basis="rbf", n_rbf=n_rbf, rbf_radius=radius)
+    try:
+        assert pc.info["P"] == n_rbf + 1
+        phi, g = pc(_dev(s.x), _dev(s.q))
+        C = pc.coefficients()
+    finally:
+        pc.close()
+    ref = O.periodic_sum(s.x, s.q, s.d, s.p, M, checkpoints="gauss" if gauss else None, lam=lam, basis="rbf",
+                         n_rbf=n_rbf, rbf_radius=radius, parts=True)
+    assert_parity(phi.cpu().numpy(), g.cpu().numpy(), ref, TOL[precision], f"rbf {name}/{precision}")
+    if precision == "fp64":
+        assert np.max(np.abs(C - ref["C"])) < 1e-8 * np.abs(ref["C"]).max()
+
+
+def test_rbf_basis_madelung_on_gpu(madelung):
+    # 256 centres on S_b with the Gauss grid of Table 1's last line (Sec. 4.1)
+    s = W.rock_salt(n=2, p=15, M=0)
+    pc = B.PeriodicCoulomb(s.d, 15, 0, precision="fp64", points="gauss", basis="rbf")
+    try:
+        phi, _ = pc(_dev(s.x), _dev(s.q))
+        with pytest.raises(B.PsumError) as e:
+            B.psum_energy_backward(pc.plan, _dev(s.x), _dev(s.q), phi, torch.empty_like(_dev(s.x)),
+                                   dEdq=torch.empty_like(phi))
+        assert e.value.status == B.PSUM_ERR_ARG
+    finally:
+        pc.close()
+    eps = np.abs(s.q * phi.cpu().numpy() * s.meta["spacing"] / madelung - 1).max()
+    assert 1e-8 < eps < 1e-6
