@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-backward", action="store_true")
+    ap.add_argument("--no-variants", action="store_true", help="skip the trimmed / RBF / Gauss-grid leg")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU budget of the oracle sample")
     ap.add_argument("--n", type=int, default=N_MAIN, help="charges (smaller cases are for profiling only)")
     return ap.parse_args()
@@ -138,9 +139,10 @@ def measured_peaks():
 
 def near_kernel_traffic(n_points):
     """DRAM bytes per launch of the charge near-field kernel from the committed ncu
-    summary (a smaller case), scaled to this launch by the number of points: the
-    traffic is the compulsory read of the packed sources, which stay in L2.  None if
-    the kernel source has changed since the counters were taken."""
+    summary (a smaller case): the read of the packed sources (which stay in L2) scales
+    with the number of points; the write of the partial sums is set by the number of
+    work items, which does not depend on N.  None if the kernel source has changed
+    since the counters were taken."""
     path = os.path.join(ROOT, "profiles", "near32_traffic.json")
     try:
         with open(path) as f:
@@ -149,7 +151,7 @@ def near_kernel_traffic(n_points):
             h = hashlib.sha256(f.read()).hexdigest()[:16]
         if rec.get("near_cu_sha256_16") != h:
             return None
-        return rec["dram_bytes"] * n_points / rec["n_points"]
+        return rec["dram_read_bytes"] * n_points / rec["n_points"] + rec["dram_write_bytes"]
     except Exception:
         return None
 
@@ -263,6 +265,8 @@ def run_psum(args):
         out["batch"] = batch_leg(args)
     if rank == 0 and not args.no_backward:
         out["backward"] = backward_leg(args)
+    if rank == 0 and not args.no_variants:
+        out["variants"] = variants_leg(args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline_leg(s, phi, grad, args)
     pc.close()
@@ -289,17 +293,21 @@ def e2e_leg(pc, s, args):
     if st != B.PSUM_OK:
         raise B.PsumError(st, "e2e warm-up")
     times = []
-    for _ in range(max(1, min(args.steps, 3))):
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    for _ in range(max(1, args.steps)):
         t0 = time.perf_counter()
         st = B.psum_eval_host(pc.plan, x, q, phi, grad, stream=stream)
         times.append(time.perf_counter() - t0)
         if st != B.PSUM_OK:
             raise B.PsumError(st, "e2e")
+    clk = clocks.stop()
     B.psum_profile(pc.plan, True)
     pairs = 27 * s.N * (s.N + 2 * s.M)
     t = statistics.mean(times)
     return {"value": pairs / t, "unit": UNIT, "h2d_bytes_per_step": int(x.numel() * 8 + q.numel() * 8),
             "d2h_bytes_per_step": int(phi.numel() * 8 + grad.numel() * 8), "ms_per_step": t * 1e3,
+            "step_ms": [v * 1e3 for v in times], "clocks": clk,
             "api": "psum_eval_host (pinned host buffers; copies and final synchronisation timed)"}
 
 
@@ -434,6 +442,61 @@ def backward_leg(args):
     return {"workload": "100k dipole pairs (200k charges, +-0.8, separation 0.01), d = (1,1,2), p = 16, M = 800, fp32c",
             "forward_ms": fwd, "backward_ms": bwd, "pairs_per_s": (pairs_f + pairs_b) / ((fwd + bwd) * 1e-3),
             "pairs_forward": pairs_f, "pairs_backward": pairs_b}
+
+
+def variants_leg(args):
+    """The options of Secs. 2-3 on one cube workload (100k uniform Gaussian charges in the
+    unit cube, p = 16, fp32c): the 3x3x3 block with the spherical basis and Fibonacci check
+    points, the near set trimmed to the ball at lambda = sqrt(3) (get step 2; the block's own
+    lambda_eff on a cube), the RBF basis of Eq. 5, and the Gauss spherical grid.  Each is
+    timed (CUDA events, mean of 2 evaluations after a warm-up) and compared with the block."""
+    import numpy as np
+    import torch
+
+    from paper_1310_4374_gb300 import binding as B
+    from paper_1310_4374_gb300 import workloads as W
+
+    s = W.uniform_gauss(N=N_MAIN, d=(1.0, 1.0, 1.0), p=P_MAIN, M=M_MAIN, seed=SEED_MAIN + 200)
+    x = torch.as_tensor(s.x, dtype=torch.float64, device="cuda")
+    q = torch.as_tensor(s.q, dtype=torch.float64, device="cuda")
+    cases = [("block", dict()),
+             ("ball_sqrt3", dict(lam=3 ** 0.5)),
+             ("rbf256", dict(basis="rbf")),
+             ("gauss_grid", dict(points="gauss"))]
+    res, ref = {}, None
+    for name, kw in cases:
+        M = 0 if kw.get("points") == "gauss" else s.M
+        pc = B.PeriodicCoulomb(s.d, s.p, M, precision="fp32c", **kw)
+        try:
+            B.psum_profile(pc.plan, True)
+            phi, g = pc(x, q)
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record()
+            for _ in range(2):
+                phi, g = pc(x, q, check=False)
+            ev1.record()
+            torch.cuda.synchronize()
+            st = B.psum_sync(pc.plan)
+            if st != B.PSUM_OK:
+                raise B.PsumError(st, "variants leg")
+            info = pc.info
+            r = {"ms_per_step": ev0.elapsed_time(ev1) / 2,
+                 "stages_ms": B.psum_last_timings(pc.plan),
+                 "M": info["M"], "P": info["P"], "images": info["n_images"], "lambda_eff": info["lambda_eff"]}
+        finally:
+            pc.close()
+        phi, g = phi.cpu().numpy(), g.cpu().numpy()
+        if ref is None:
+            ref = (phi, g)
+        else:
+            r["eps2_vs_block"] = {"phi": float(np.sqrt(np.mean((phi - ref[0]) ** 2) / np.mean(ref[0] ** 2))),
+                                  "grad": float(np.sqrt(np.mean((g - ref[1]) ** 2) / np.mean(ref[1] ** 2)))}
+            r["speedup_vs_block"] = res["block"]["ms_per_step"] / r["ms_per_step"]
+        res[name] = r
+    res["workload"] = (f"uniform Gaussian charges, N={s.N}, unit cube, p={s.p}, fp32c; "
+                       "block: 27 images, Fibonacci M=800; ball: lambda=sqrt(3); rbf: 256 centres on S_b; "
+                       "gauss: M=(p+1)(2p+1)")
+    return res
 
 
 def cpu_baseline_leg(s, phi_gpu, grad_gpu, args):

@@ -236,7 +236,8 @@ int queue_forward(psum_plan_s* h, int64_t N, const double* x, const double* q, d
     const bool zero_mean = o.mean_mode == PSUM_MEAN_ZERO;
     if (zero_mean) {
         if (pl.Rb > 0.0) {
-            TRY(launch_box_mean_ball(x, q, N, o.d, pl.d_shifts, pl.n_images, pl.Rb, L.mean_part, L.nblk_mean, st));
+            TRY(launch_box_mean_ball(x, q, fp32 ? L.va : nullptr, N, o.d, pl.d_shifts, pl.n_images, pl.Rb,
+                                     L.mean_part, L.nblk_mean, st));
         } else {
             const double H[3] = {0.5 * (2 * o.K[0] + 1) * o.d[0], 0.5 * (2 * o.K[1] + 1) * o.d[1],
                                  0.5 * (2 * o.K[2] + 1) * o.d[2]};

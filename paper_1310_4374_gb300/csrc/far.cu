@@ -83,15 +83,20 @@ __global__ void __launch_bounds__(kRedThreads) k_box_mean(const double* __restri
 
 // With the near set trimmed to the ball S_b (get step 2) every kept source image x + p
 // (|x + p| <= Rb, the same float64 test as the pair kernels) contributes the potential of
-// the single box at x + p.
+// the single box at x + p (by the corner sum, the cheaper closed form for one box).  Which
+// images are kept depends on the charge, so the threads of
+// a warp take charges in Morton order when a permutation is given: neighbours keep nearly
+// the same images and the warp evaluates few potentials that only some of its lanes need.
 __global__ void __launch_bounds__(kRedThreads) k_box_mean_ball(const double* __restrict__ x,
-                                                               const double* __restrict__ q, int64_t n, double H0,
-                                                               double H1, double H2,
+                                                               const double* __restrict__ q,
+                                                               const uint32_t* __restrict__ perm, int64_t n,
+                                                               double H0, double H1, double H2,
                                                                const double* __restrict__ shifts, int n_img,
                                                                double Rb, double* __restrict__ partial) {
     const double H[3] = {H0, H1, H2};
     double s = 0.0, dummy = 0.0;
-    for (int64_t i = (int64_t)blockIdx.x * kRedThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kRedThreads) {
+    for (int64_t k = (int64_t)blockIdx.x * kRedThreads + threadIdx.x; k < n; k += (int64_t)gridDim.x * kRedThreads) {
+        const int64_t i = perm ? (int64_t)perm[k] : k;
         double u = 0.0;
         for (int im = 0; im < n_img; ++im) {
             const double* p = shifts + 3 * im;
@@ -100,7 +105,7 @@ __global__ void __launch_bounds__(kRedThreads) k_box_mean_ball(const double* __r
             const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(a, a), __dmul_rn(b, b)), __dmul_rn(c, c));
             if (r2 <= __dmul_rn(Rb, Rb)) {
                 const double X[3] = {a, b, c};
-                u += block_potential(X, H);
+                u += block_potential_corners(X, H);
             }
         }
         s += q[i] * u;
@@ -318,11 +323,11 @@ cudaError_t launch_box_mean(const double* x, const double* q, int64_t n, const d
     return cudaGetLastError();
 }
 
-cudaError_t launch_box_mean_ball(const double* x, const double* q, int64_t n, const double d[3],
-                                 const double* shifts, int n_img, double Rb, double* partial, int nblk,
-                                 cudaStream_t st) {
-    k_box_mean_ball<<<nblk, kRedThreads, 0, st>>>(x, q, n, 0.5 * d[0], 0.5 * d[1], 0.5 * d[2], shifts, n_img, Rb,
-                                                 partial);
+cudaError_t launch_box_mean_ball(const double* x, const double* q, const uint32_t* perm, int64_t n,
+                                 const double d[3], const double* shifts, int n_img, double Rb, double* partial,
+                                 int nblk, cudaStream_t st) {
+    k_box_mean_ball<<<nblk, kRedThreads, 0, st>>>(x, q, perm, n, 0.5 * d[0], 0.5 * d[1], 0.5 * d[2], shifts, n_img,
+                                                 Rb, partial);
     return cudaGetLastError();
 }
 

@@ -50,4 +50,44 @@ __host__ __device__ __forceinline__ double block_potential(const double X[3], co
 }
 
 
+// The same potential by the corner sum of the classical closed form for a rectangular
+// prism: U(x) = sum over the 8 corners c of s_c F(c - x), s_c = +1 where an even number
+// of coordinates of c take the lower bound, with
+//   F(a, b, c) = ab ln(c + r) + bc ln(a + r) + ca ln(b + r)
+//                - a^2/2 atan(bc/(ar)) - b^2/2 atan(ca/(br)) - c^2/2 atan(ab/(cr)),
+// r = |(a, b, c)|.  It needs 24 logarithms and 24 arctangents where the face/edge route
+// takes 48 and 96; the ball-trimmed mean, which evaluates one single-box potential per
+// kept image and charge, uses it.  Vanishing products drop their term (their limit is 0).
+__host__ __device__ __forceinline__ double log_plus_r(double a, double r, double rest2) {
+    // ln(a + r) with r^2 = a^2 + rest2, without cancellation for a < 0
+    return a >= 0.0 ? log(a + r) : log(rest2 / (r - a));
+}
+
+__host__ __device__ __forceinline__ double prism_corner(double a, double b, double c) {
+    const double a2 = a * a, b2 = b * b, c2 = c * c;
+    const double r = sqrt(a2 + b2 + c2);
+    double f = 0.0;
+    if (a * b != 0.0) f += a * b * log_plus_r(c, r, a2 + b2);
+    if (b * c != 0.0) f += b * c * log_plus_r(a, r, b2 + c2);
+    if (c * a != 0.0) f += c * a * log_plus_r(b, r, c2 + a2);
+    if (a != 0.0 && b * c != 0.0) f -= 0.5 * a2 * atan(b * c / (a * r));
+    if (b != 0.0 && c * a != 0.0) f -= 0.5 * b2 * atan(c * a / (b * r));
+    if (c != 0.0 && a * b != 0.0) f -= 0.5 * c2 * atan(a * b / (c * r));
+    return f;
+}
+
+__host__ __device__ __forceinline__ double block_potential_corners(const double X[3], const double H[3]) {
+    double U = 0.0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const double a = (k & 1) ? H[0] - X[0] : -H[0] - X[0];
+        const double b = (k & 2) ? H[1] - X[1] : -H[1] - X[1];
+        const double c = (k & 4) ? H[2] - X[2] : -H[2] - X[2];
+        const int lower = !(k & 1) + !(k & 2) + !(k & 4);
+        const double f = prism_corner(a, b, c);
+        U += (lower & 1) ? -f : f;
+    }
+    return U;
+}
+
 }  // namespace psum

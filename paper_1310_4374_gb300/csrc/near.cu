@@ -198,9 +198,11 @@ __device__ __forceinline__ void pair_loop_near(const float4* __restrict__ s_hi, 
     }
 }
 
-// Two register budgets of the same kernel: 6 resident CTAs per SM (80 registers) or 5
-// (up to 102).  The batch autotuner times both.
-constexpr int kNear32MinBlocks[2] = {6, 5};
+// Two register budgets of the same kernel: 4 resident CTAs per SM (up to 128 registers) or
+// 6 (80).  With work items handed out dynamically the larger budget, which lets the
+// compiler keep more loads and rsqrt results in flight, is the faster one (109.8 against
+// 115.7-121.1 ms for 1e5 charges); the batch autotuner times both.
+constexpr int kNear32MinBlocks[2] = {4, 6};
 
 template <bool kGrad, int kMinB, bool kTrim>
 __global__ void __launch_bounds__(kThreads32, kMinB) k_near32(Near32Args a) {
@@ -572,9 +574,9 @@ cudaError_t launch_near32(bool grad, const float4* src_hi, const float4* src_lo,
     if (Rb > 0.0) {
         // trimmed near sets take the larger register budget: the ball tests add live state
         if (grad)
-            k_near32<true, kNear32MinBlocks[1], true><<<(unsigned)L.G, kThreads32, smem, st>>>(a);
+            k_near32<true, kNear32MinBlocks[0], true><<<(unsigned)L.G, kThreads32, smem, st>>>(a);
         else
-            k_near32<false, kNear32MinBlocks[1], true><<<(unsigned)L.G, kThreads32, smem, st>>>(a);
+            k_near32<false, kNear32MinBlocks[0], true><<<(unsigned)L.G, kThreads32, smem, st>>>(a);
     } else if (variant == 1) {
         if (grad)
             k_near32<true, kNear32MinBlocks[1], false><<<(unsigned)L.G, kThreads32, smem, st>>>(a);
@@ -618,7 +620,7 @@ int near32_occupancy_ctas(int n_img, int variant, bool trimmed) {
     int nb = 0;
     const size_t smem = near32_dyn_smem(n_img, trimmed);
     if (trimmed)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_near32<true, kNear32MinBlocks[1], true>, kThreads32,
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_near32<true, kNear32MinBlocks[0], true>, kThreads32,
                                                       smem);
     else if (variant == 1)
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_near32<true, kNear32MinBlocks[1], false>, kThreads32,
