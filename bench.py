@@ -312,7 +312,8 @@ def e2e_leg(pc, s, args):
 
 
 def fp64_leg(args):
-    """FP64 pair kernel vs FP32C on a 20k-charge system of the same box, p and M."""
+    """FP64 pair kernel vs float-float (FF) and FP32C on a 20k-charge system of the same box,
+    p and M."""
     import torch
 
     from paper_1310_4374_gb300 import binding as B
@@ -323,7 +324,7 @@ def fp64_leg(args):
     q = torch.as_tensor(s.q, dtype=torch.float64, device="cuda")
     res = {}
     outs = {}
-    for prec in ("fp64", "fp32c"):
+    for prec in ("fp64", "ff", "fp32c"):
         pc = B.PeriodicCoulomb(s.d, s.p, s.M, precision=prec)
         B.psum_profile(pc.plan, True)
         phi, g = pc(x, q)                       # warm-up
@@ -348,10 +349,13 @@ def fp64_leg(args):
 
     def rel(a, b):
         return float(np.sqrt(np.mean((a - b) ** 2)) / np.sqrt(np.mean(b ** 2)))
-    res["workload"] = workload_name(N_FP64).replace("fp32c", "fp64 and fp32c")
+    res["workload"] = workload_name(N_FP64).replace("fp32c", "fp64, ff and fp32c")
     res["speedup_fp32c_over_fp64"] = res["fp32c"]["pairs_per_s"] / res["fp64"]["pairs_per_s"]
+    res["speedup_ff_over_fp64"] = res["ff"]["pairs_per_s"] / res["fp64"]["pairs_per_s"]
     res["eps2_fp32c_vs_fp64"] = {"phi": rel(outs["fp32c"][0], outs["fp64"][0]),
                                  "grad": rel(outs["fp32c"][1], outs["fp64"][1])}
+    res["eps2_ff_vs_fp64"] = {"phi": rel(outs["ff"][0], outs["fp64"][0]),
+                              "grad": rel(outs["ff"][1], outs["fp64"][1])}
     return res
 
 

@@ -68,6 +68,10 @@ extern "C" {
 #define PSUM_FP64   0  /* near-field pair sum in float64 */
 #define PSUM_FP32C  1  /* pair arithmetic in float32 on tile-relative coordinates,
                           compensated (two-sum) accumulation, float64 elsewhere */
+#define PSUM_FF     2  /* pair arithmetic in float-float (a float32 pair carrying about 44 bits)
+                          on the float32 pipe: float64-class results (the float64 tolerance)
+                          without float64 pair arithmetic; float64 elsewhere.  psum_energy_backward
+                          and the batch API reject FF plans (PSUM_ERR_ARG). */
 
 #define PSUM_POINTS_FIBONACCI 0  /* M check points on a spherical Fibonacci lattice */
 #define PSUM_POINTS_GAUSS     1  /* the Gauss spherical grid of Sec. 2.2: polar angles at the zeros of
@@ -85,7 +89,7 @@ typedef struct psum_opts {
     double d[3];     /* box edge lengths, > 0 */
     int p;           /* maximum degree of the local expansion, 1 <= p <= 40 */
     int M;           /* number of check points, M >= (p+1)^2 - 1 */
-    int precision;   /* PSUM_FP64 or PSUM_FP32C */
+    int precision;   /* PSUM_FP64, PSUM_FP32C or PSUM_FF */
     int mean_mode;   /* PSUM_MEAN_ZERO or PSUM_MEAN_NONE */
     int K[3];        /* near block: images |i_k| <= K[k] of the box (Eq. 3, Omega_b); 1 = 3x3x3 */
     int points;      /* PSUM_POINTS_FIBONACCI or PSUM_POINTS_GAUSS (then M must be 0 or (p+1)(2p+1)) */

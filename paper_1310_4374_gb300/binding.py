@@ -30,7 +30,8 @@ PSUM_MEAN_NONE = 1
 PSUM_NUM_STAGES = 5
 STAGE_NAMES = ("prepare", "near_charges", "near_checkpoints", "fit", "far_combine")
 
-PRECISIONS = {"fp64": PSUM_FP64, "fp32c": PSUM_FP32C}
+PSUM_FF = 2
+PRECISIONS = {"fp64": PSUM_FP64, "fp32c": PSUM_FP32C, "ff": PSUM_FF}
 POINTS = {"fibonacci": 0, "gauss": 1}
 BASES = {"spherical": 0, "rbf": 1}
 MEAN_MODES = {"zero": PSUM_MEAN_ZERO, "none": PSUM_MEAN_NONE}

@@ -71,7 +71,7 @@ struct Layout {
 // `backward` adds the buffers of the energy derivatives.
 size_t layout(Plan& pl, int64_t N, char* base, Layout& L, bool backward = false, int64_t g_cap = 0) {
     Bump b{base, 0, 0};
-    const bool fp32 = pl.opt.precision == PSUM_FP32C;
+    const bool fp32 = pl.opt.precision != PSUM_FP64;   // float32 packing (FP32C and FF)
     const int n_img = pl.n_images;
     // a capped width (the allocation-free entry) keeps one work item per CTA: the partial
     // sums grow with the number of items
@@ -82,7 +82,7 @@ size_t layout(Plan& pl, int64_t N, char* base, Layout& L, bool backward = false,
         const int64_t n_groups = L.n_tiles * kTgt32;
         L.n_pts = n_groups * kNearChunk;
         const bool trimmed = pl.Rb > 0.0;
-        int64_t gmax = (int64_t)pl.num_sms * near32_occupancy_ctas(n_img, 0, trimmed);
+        int64_t gmax = (int64_t)pl.num_sms * near32_occupancy_ctas(n_img, 0, trimmed, pl.opt.precision == PSUM_FF);
         if (g_cap > 0 && gmax > g_cap) gmax = g_cap;
         L.Ln = near_partition(L.n_tiles, L.n_chunks, n_img, gmax, ipc);
         L.Lc = near_partition(pl.n_check_tiles, L.n_chunks, n_img, gmax, ipc);
@@ -194,7 +194,8 @@ int queue_forward(psum_plan_s* h, int64_t N, const double* x, const double* q, d
                   const Layout& L, cudaStream_t st) {
     Plan& pl = h->pl;
     const psum_opts& o = pl.opt;
-    const bool fp32 = o.precision == PSUM_FP32C;
+    const bool fp32 = o.precision != PSUM_FP64;       // float32 packing (FP32C and FF)
+    const bool ff = o.precision == PSUM_FF;
     const int M = o.M, P = pl.P;
     if (h->profile) TRY(cudaEventRecord(h->ev[0], st));
     // the status word must start at zero; every other buffer is written before it is read
@@ -214,7 +215,7 @@ int queue_forward(psum_plan_s* h, int64_t N, const double* x, const double* q, d
     if (h->profile) TRY(cudaEventRecord(h->ev[1], st));
     if (fp32) {
         TRY(launch_near32(true, L.pk32, L.pk32lo, L.org, L.pk32, L.pk32lo, L.org, pl.d_shifts, L.part_n, L.Ln,
-                          st, 0, L.xs, pl.Rb));
+                          st, 0, L.xs, pl.Rb, ff));
     } else {
         TRY(launch_near64(true, L.pk64, L.pk64, pl.d_shifts, L.part_n, L.Ln, st, pl.Rb));
     }
@@ -223,7 +224,7 @@ int queue_forward(psum_plan_s* h, int64_t N, const double* x, const double* q, d
         const float4* ct = (const float4*)pl.d_check_tgt;
         const size_t half = 2 * (size_t)pl.n_check_tiles * kTile32;    // hi parts, then lo parts
         TRY(launch_near32(false, L.pk32, L.pk32lo, L.org, ct, ct + half, pl.d_check_org, pl.d_shifts, L.part_c,
-                          L.Lc, st, 0, L.xs, pl.Rb));
+                          L.Lc, st, 0, L.xs, pl.Rb, ff));
     } else {
         TRY(launch_near64(false, L.pk64, (const double4_32a*)pl.d_check_tgt, pl.d_shifts, L.part_c, L.Lc, st,
                           pl.Rb));
@@ -254,8 +255,8 @@ int queue_forward(psum_plan_s* h, int64_t N, const double* x, const double* q, d
                            L.eval_status, phi, grad, L.eval_status, st));
     else
         TRY(launch_far_combine(x, N, perm, L.phi_n, grad ? L.grad_n : nullptr, pl.d_C, o.p, 1.0 / pl.R0,
-                               pl.d_shtab64, fp32 ? pl.d_shtab32 : nullptr, L.eval_status, phi, grad,
-                               L.eval_status, st));
+                               pl.d_shtab64, o.precision == PSUM_FP32C ? pl.d_shtab32 : nullptr, L.eval_status,
+                               phi, grad, L.eval_status, st));
     k_status_merge<<<1, 1, 0, st>>>(L.eval_status, pl.d_status);
     TRY(cudaGetLastError());
     h->launches += 5;   // right-hand side, projection, constant, far field, status merge
@@ -347,7 +348,7 @@ bool valid_opts(const psum_opts* o) {
         for (int k = 0; k < 3; ++k) n *= 2 * (int64_t)std::ceil(o->lambda * R0 / o->d[k] + 0.5) + 1;
         if (n > 100000) return false;
     }
-    if (o->precision != PSUM_FP64 && o->precision != PSUM_FP32C) return false;
+    if (o->precision != PSUM_FP64 && o->precision != PSUM_FP32C && o->precision != PSUM_FF) return false;
     if (o->mean_mode != PSUM_MEAN_ZERO && o->mean_mode != PSUM_MEAN_NONE) return false;
     return true;
 }
@@ -472,6 +473,7 @@ int psum_energy_backward(psum_plan_t h, int64_t N, const double* x, const double
     if (!h || N < 1 || N > (int64_t)1 << 30 || !x || !q || !phi || !grad || (!dEdq && !dEdx)) return PSUM_ERR_ARG;
     if (h->pl.Rb > 0.0) return PSUM_ERR_ARG;   // the adjoint assumes the untrimmed near block
     if (h->pl.opt.basis != PSUM_BASIS_SPHERICAL) return PSUM_ERR_ARG;   // and the solid-harmonic moments
+    if (h->pl.opt.precision == PSUM_FF) return PSUM_ERR_ARG;
     DeviceGuard g(h->pl.device);
     return backward_device(h, N, x, q, phi, grad, gE, dEdq, dEdx, (cudaStream_t)stream);
 }

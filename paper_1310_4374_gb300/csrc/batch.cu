@@ -516,6 +516,7 @@ int psum_batch_create(const psum_plan_t* plans, int B, const int64_t* offsets, p
         if (plans[b]->pl.device != plans[0]->pl.device) return PSUM_ERR_ARG;
         if (plans[b]->pl.Rb > 0.0) return PSUM_ERR_ARG;   // trimmed near sets: single-system path only
         if (plans[b]->pl.opt.basis != PSUM_BASIS_SPHERICAL) return PSUM_ERR_ARG;
+        if (plans[b]->pl.opt.precision == PSUM_FF) return PSUM_ERR_ARG;
     }
     if (offsets[B] > ((int64_t)1 << 30)) return PSUM_ERR_ARG;
     psum_batch_s* bt = new (std::nothrow) psum_batch_s();

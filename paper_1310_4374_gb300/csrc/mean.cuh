@@ -78,7 +78,7 @@ __host__ __device__ __forceinline__ double prism_corner(double a, double b, doub
 
 __host__ __device__ __forceinline__ double block_potential_corners(const double X[3], const double H[3]) {
     double U = 0.0;
-#pragma unroll
+#pragma unroll 1
     for (int k = 0; k < 8; ++k) {
         const double a = (k & 1) ? H[0] - X[0] : -H[0] - X[0];
         const double b = (k & 2) ? H[1] - X[1] : -H[1] - X[1];

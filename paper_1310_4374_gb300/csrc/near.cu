@@ -198,18 +198,125 @@ __device__ __forceinline__ void pair_loop_near(const float4* __restrict__ s_hi, 
     }
 }
 
+// ---------------------------------------------------------------------------
+// Float-float (FF) pair arithmetic: every quantity is an unevaluated sum hi + lo of two
+// float32 values (about 44 significant bits), built from error-free transformations on
+// the float32 pipe -- Knuth's two-sum and the fused-multiply-add product error -- so that
+// float64-class results need no float64 pair arithmetic (a GB300 SM issues 1/64 as many
+// float64 as float32 lane operations).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+
+// s + e = a + b exactly
+__device__ __forceinline__ float2 two_sum2(float2 a, float2 b, float2& e) {
+    const float2 m1 = make_float2(-1.f, -1.f);
+    const float2 s = __fadd2_rn(a, b);
+    const float2 bp = __ffma2_rn(m1, a, s);              // s - a
+    const float2 t1 = __ffma2_rn(m1, bp, s);             // s - bp
+    const float2 e1 = __ffma2_rn(m1, t1, a);             // a - (s - bp)
+    const float2 e2 = __ffma2_rn(m1, bp, b);             // b - bp
+    e = __fadd2_rn(e1, e2);
+    return s;
+}
+
+// (hi, lo) += (vh, vl)
+__device__ __forceinline__ void ff_acc2(float2& hi, float2& lo, float2 vh, float2 vl) {
+    float2 e;
+    hi = two_sum2(hi, vh, e);
+    lo = __fadd2_rn(lo, __fadd2_rn(vl, e));
+}
+
+// (ph, pl) = (ah, al) (bh, bl), dropping al bl
+__device__ __forceinline__ float2 ff_mul2(float2 ah, float2 al, float2 bh, float2 bl, float2& pl) {
+    const float2 ph = __fmul2_rn(ah, bh);
+    float2 e = __ffma2_rn(ah, bh, neg2(ph));             // exact product error
+    e = __ffma2_rn(ah, bl, e);
+    pl = __ffma2_rn(al, bh, e);
+    return ph;
+}
+
+// One chunk against one packed target pair t' (negated: nTh + nTl).  Source offsets
+// s - t' come out of a two-sum of the hi parts plus the lo parts; r^2 is summed with
+// the product errors; 1/r is the MUFU estimate y refined by one Newton step taken in
+// float-float, ri = y - y (r^2 y^2 - 1)/2, which leaves a relative error near
+// (3/2)(2^-22.9)^2 + 2^-46; K(0) = 0 where r^2 is exactly zero.  acc[q] = (hi, lo) of
+// phi and (kGrad) the three field sums.
+template <bool kGrad>
+__device__ __forceinline__ void pair_loop_ff(const float4* __restrict__ s_hi, const float4* __restrict__ s_lo,
+                                             const float2 (&nTh)[3], const float2 (&nTl)[3], float2 (&acc)[4][2]) {
+#pragma unroll 1
+    for (int s = 0; s < kNearChunk; ++s) {
+        const float4 A = s_hi[2 * s], B = s_hi[2 * s + 1], C = s_lo[2 * s], D = s_lo[2 * s + 1];
+        const float2 sh[3] = {make_float2(A.x, A.y), make_float2(A.z, A.w), make_float2(B.x, B.y)};
+        const float2 sl[3] = {make_float2(C.x, C.y), make_float2(C.z, C.w), make_float2(D.x, D.y)};
+        const float2 qh = make_float2(B.z, B.w), ql = make_float2(D.z, D.w);
+        float2 eh[3], el[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            float2 err;
+            eh[c] = two_sum2(sh[c], nTh[c], err);
+            el[c] = __fadd2_rn(__fadd2_rn(sl[c], nTl[c]), err);
+        }
+        // r^2 = sum (eh + el)^2 as r2h + r2l
+        const float2 p0 = __fmul2_rn(eh[0], eh[0]), p1 = __fmul2_rn(eh[1], eh[1]), p2 = __fmul2_rn(eh[2], eh[2]);
+        float2 lo = __ffma2_rn(eh[0], eh[0], neg2(p0));
+        lo = __fadd2_rn(lo, __ffma2_rn(eh[1], eh[1], neg2(p1)));
+        lo = __fadd2_rn(lo, __ffma2_rn(eh[2], eh[2], neg2(p2)));
+        float2 cr = __fmul2_rn(eh[0], el[0]);
+        cr = __ffma2_rn(eh[1], el[1], cr);
+        cr = __ffma2_rn(eh[2], el[2], cr);
+        lo = __ffma2_rn(make_float2(2.f, 2.f), cr, lo);
+        float2 e1, e2;
+        const float2 s1 = two_sum2(p0, p1, e1);
+        const float2 r2h = two_sum2(s1, p2, e2);
+        const float2 r2l = __fadd2_rn(lo, __fadd2_rn(e1, e2));
+        // 1/r
+        const float2 y = make_float2(rsqrt_mufu(r2h.x), rsqrt_mufu(r2h.y));
+        const float2 ah = __fmul2_rn(r2h, y);
+        const float2 ae = __ffma2_rn(r2h, y, neg2(ah));       // r2h y = ah + ae
+        const float2 bh = __fmul2_rn(ah, y);
+        const float2 be = __ffma2_rn(ah, y, neg2(bh));        // ah y = bh + be
+        float2 h = __fadd2_rn(bh, make_float2(-1.f, -1.f));   // exact: bh is within a factor 2 of 1
+        h = __fadd2_rn(h, be);
+        h = __ffma2_rn(ae, y, h);
+        h = __ffma2_rn(__fmul2_rn(r2l, y), y, h);             // h = r^2 y^2 - 1
+        float2 rih = y;
+        float2 ril = __fmul2_rn(__fmul2_rn(make_float2(-0.5f, -0.5f), y), h);
+        if (r2h.x == 0.f) rih.x = ril.x = 0.f;                // K(0) = 0 (Eq. 1)
+        if (r2h.y == 0.f) rih.y = ril.y = 0.f;
+        // q / r
+        float2 Pl;
+        const float2 Ph = ff_mul2(qh, ql, rih, ril, Pl);
+        ff_acc2(acc[0][0], acc[0][1], Ph, Pl);
+        if (kGrad) {
+            // w = q / r^3, field term w (s - t')
+            float2 r2il;
+            const float2 r2ih = ff_mul2(rih, ril, rih, ril, r2il);
+            float2 wl;
+            const float2 wh = ff_mul2(Ph, Pl, r2ih, r2il, wl);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                float2 gl;
+                const float2 gh = ff_mul2(wh, wl, eh[c], el[c], gl);
+                ff_acc2(acc[1 + c][0], acc[1 + c][1], gh, gl);
+            }
+        }
+    }
+}
+
 // Two register budgets of the same kernel: 4 resident CTAs per SM (up to 128 registers) or
 // 6 (80).  With work items handed out dynamically the larger budget, which lets the
 // compiler keep more loads and rsqrt results in flight, is the faster one (109.8 against
 // 115.7-121.1 ms for 1e5 charges); the batch autotuner times both.
 constexpr int kNear32MinBlocks[2] = {4, 6};
 
-template <bool kGrad, int kMinB, bool kTrim>
+template <bool kGrad, int kMinB, bool kTrim, bool kFF>
 __global__ void __launch_bounds__(kThreads32, kMinB) k_near32(Near32Args a) {
     constexpr int NQ = kGrad ? 4 : 1;
     __shared__ float4 s_hi[2 * kNearChunk];
     __shared__ float4 s_lo[2 * kNearChunk];
     __shared__ float2 s_th[3][2][kThreads32];             // target hi offsets, [coord][pair]
+    __shared__ float2 s_tl[kFF ? 3 : 1][2][kThreads32];   // FF: target lo offsets
     __shared__ float2 s_acc[NQ][2][2][kThreads32];        // [quantity][pair][hi, lo]
     extern __shared__ float4 s_dyn4[];                    // [max_img][kTgt32][6] deltas, [max_img] flags,
     float* s_delta = (float*)s_dyn4;                      // then (trimmed plans) a chunk copy with
@@ -270,6 +377,13 @@ __global__ void __launch_bounds__(kThreads32, kMinB) k_near32(Near32Args a) {
                 s_th[0][j][tid] = make_float2(A0.x, A1.x);
                 s_th[1][j][tid] = make_float2(A0.z, A1.z);
                 s_th[2][j][tid] = make_float2(B0.x, B1.x);
+                if (kFF) {
+                    const float4 C0 = a.tgt_lo[2 * i0], D0 = a.tgt_lo[2 * i0 + 1];
+                    const float4 C1 = a.tgt_lo[2 * i1], D1 = a.tgt_lo[2 * i1 + 1];
+                    s_tl[0][j][tid] = make_float2(C0.x, C1.x);
+                    s_tl[kFF ? 1 : 0][j][tid] = make_float2(C0.z, C1.z);
+                    s_tl[kFF ? 2 : 0][j][tid] = make_float2(D0.x, D1.x);
+                }
 #pragma unroll
                 for (int qi = 0; qi < NQ; ++qi) {
                     s_acc[qi][j][0][tid] = make_float2(0.f, 0.f);
@@ -328,11 +442,41 @@ __global__ void __launch_bounds__(kThreads32, kMinB) k_near32(Near32Args a) {
             const double* sh = a.shifts + 3 * (Sp->shift0 + img);
             const double* xp = a.src_x + 3 * (chunk * kNearChunk + tid);
             const float4 B = s_hi[2 * tid + 1];
+            const float4 Dl = s_lo[2 * tid + 1];
             s_hm[tid] = B;
-            if (!in_ball(xp[0], xp[1], xp[2], sh, a.Rb)) s_hi[2 * tid + 1] = make_float4(B.x, B.y, 0.f, 0.f);
+            s_hm[kNearChunk + tid] = Dl;
+            if (!in_ball(xp[0], xp[1], xp[2], sh, a.Rb)) {
+                s_hi[2 * tid + 1] = make_float4(B.x, B.y, 0.f, 0.f);
+                s_lo[2 * tid + 1] = make_float4(Dl.x, Dl.y, 0.f, 0.f);
+            }
             __syncthreads();
         }
-        if (cls & kUnitNear) {
+        if constexpr (kFF) {
+            // every unit in float-float: t' = t + delta as hi + lo
+#pragma unroll 1
+            for (int j = 0; j < 2; ++j) {
+                const float* d0 = dl + 6 * (2 * j);
+                const float* d1 = dl + 6 * (2 * j + 1);
+                float2 nTh[3], nTl[3];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    float2 e;
+                    const float2 th = two_sum2(s_th[c][j][tid], make_float2(d0[c], d1[c]), e);
+                    const float2 tl = __fadd2_rn(__fadd2_rn(s_tl[c][j][tid], make_float2(d0[3 + c], d1[3 + c])), e);
+                    nTh[c] = neg2(th);
+                    nTl[c] = neg2(tl);
+                }
+                float2 acc[4][2];
+#pragma unroll
+                for (int qi = 0; qi < 4; ++qi) acc[qi][0] = acc[qi][1] = make_float2(0.f, 0.f);
+                pair_loop_ff<kGrad>(s_hi, s_lo, nTh, nTl, acc);
+#pragma unroll
+                for (int qi = 0; qi < NQ; ++qi) {
+                    two_sum_acc2(s_acc[qi][j][0][tid], s_acc[qi][j][1][tid], acc[qi][0]);
+                    s_acc[qi][j][1][tid] = __fadd2_rn(s_acc[qi][j][1][tid], acc[qi][1]);
+                }
+            }
+        } else if (cls & kUnitNear) {
             // t' = t + delta in float-float: hi by rounding, lo = exact remainder + both lo parts
 #pragma unroll 1
             for (int j = 0; j < 2; ++j) {
@@ -392,6 +536,7 @@ __global__ void __launch_bounds__(kThreads32, kMinB) k_near32(Near32Args a) {
         if (kTrim && (s_near[img] & kUnitStraddle)) {
             __syncthreads();
             s_hi[2 * tid + 1] = s_hm[tid];
+            s_lo[2 * tid + 1] = s_hm[kNearChunk + tid];
             __syncthreads();
         }
         ++u;
@@ -552,13 +697,13 @@ __global__ void k_near_reduce(const double* __restrict__ partial, int64_t n_vali
 // ---------------------------------------------------------------------------
 size_t near32_dyn_smem(int n_img, bool trimmed) {
     const size_t head = ((6 * kTgt32 * (size_t)n_img + n_img + 3) / 4) * sizeof(float4);
-    return head + (trimmed ? sizeof(float4) * kNearChunk : 0);
+    return head + (trimmed ? sizeof(float4) * 2 * kNearChunk : 0);   // saved charges (hi, lo parts)
 }
 
 cudaError_t launch_near32(bool grad, const float4* src_hi, const float4* src_lo, const double* src_org,
                           const float4* tgt_hi, const float4* tgt_lo, const double* tgt_org, const double* shifts,
                           double* partial, const NearPlanLaunch& L, cudaStream_t st, int variant,
-                          const double* src_x, double Rb) {
+                          const double* src_x, double Rb, bool ff) {
     Near32Args a;
     a.src_hi = src_hi; a.src_lo = src_lo; a.src_org = src_org;
     a.tgt_hi = tgt_hi; a.tgt_lo = tgt_lo; a.tgt_org = tgt_org; a.shifts = shifts;
@@ -571,22 +716,26 @@ cudaError_t launch_near32(bool grad, const float4* src_hi, const float4* src_lo,
     if (!L.counter) return cudaErrorInvalidValue;
     const cudaError_t e = cudaMemsetAsync(L.counter, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
-    if (Rb > 0.0) {
+    constexpr int B0 = kNear32MinBlocks[0], B1 = kNear32MinBlocks[1];
+    const unsigned G = (unsigned)L.G;
+    if (ff) {
+        if (Rb > 0.0) {
+            if (grad) k_near32<true, B0, true, true><<<G, kThreads32, smem, st>>>(a);
+            else k_near32<false, B0, true, true><<<G, kThreads32, smem, st>>>(a);
+        } else {
+            if (grad) k_near32<true, B0, false, true><<<G, kThreads32, smem, st>>>(a);
+            else k_near32<false, B0, false, true><<<G, kThreads32, smem, st>>>(a);
+        }
+    } else if (Rb > 0.0) {
         // trimmed near sets take the larger register budget: the ball tests add live state
-        if (grad)
-            k_near32<true, kNear32MinBlocks[0], true><<<(unsigned)L.G, kThreads32, smem, st>>>(a);
-        else
-            k_near32<false, kNear32MinBlocks[0], true><<<(unsigned)L.G, kThreads32, smem, st>>>(a);
+        if (grad) k_near32<true, B0, true, false><<<G, kThreads32, smem, st>>>(a);
+        else k_near32<false, B0, true, false><<<G, kThreads32, smem, st>>>(a);
     } else if (variant == 1) {
-        if (grad)
-            k_near32<true, kNear32MinBlocks[1], false><<<(unsigned)L.G, kThreads32, smem, st>>>(a);
-        else
-            k_near32<false, kNear32MinBlocks[1], false><<<(unsigned)L.G, kThreads32, smem, st>>>(a);
+        if (grad) k_near32<true, B1, false, false><<<G, kThreads32, smem, st>>>(a);
+        else k_near32<false, B1, false, false><<<G, kThreads32, smem, st>>>(a);
     } else {
-        if (grad)
-            k_near32<true, kNear32MinBlocks[0], false><<<(unsigned)L.G, kThreads32, smem, st>>>(a);
-        else
-            k_near32<false, kNear32MinBlocks[0], false><<<(unsigned)L.G, kThreads32, smem, st>>>(a);
+        if (grad) k_near32<true, B0, false, false><<<G, kThreads32, smem, st>>>(a);
+        else k_near32<false, B0, false, false><<<G, kThreads32, smem, st>>>(a);
     }
     return cudaGetLastError();
 }
@@ -616,18 +765,20 @@ cudaError_t launch_near_reduce(const double* partial, int64_t n_valid, int tile_
     return cudaGetLastError();
 }
 
-int near32_occupancy_ctas(int n_img, int variant, bool trimmed) {
+int near32_occupancy_ctas(int n_img, int variant, bool trimmed, bool ff) {
     int nb = 0;
     const size_t smem = near32_dyn_smem(n_img, trimmed);
-    if (trimmed)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_near32<true, kNear32MinBlocks[0], true>, kThreads32,
-                                                      smem);
+    constexpr int B0 = kNear32MinBlocks[0], B1 = kNear32MinBlocks[1];
+    if (ff && trimmed)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_near32<true, B0, true, true>, kThreads32, smem);
+    else if (ff)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_near32<true, B0, false, true>, kThreads32, smem);
+    else if (trimmed)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_near32<true, B0, true, false>, kThreads32, smem);
     else if (variant == 1)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_near32<true, kNear32MinBlocks[1], false>, kThreads32,
-                                                      smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_near32<true, B1, false, false>, kThreads32, smem);
     else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_near32<true, kNear32MinBlocks[0], false>, kThreads32,
-                                                      smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_near32<true, B0, false, false>, kThreads32, smem);
     return nb < 1 ? 1 : nb;
 }
 

@@ -303,7 +303,7 @@ int build_plan(const psum_opts& o, Plan& pl) {
     std::copy(pl.Y.begin(), pl.Y.end(), pts.begin());
     std::copy(pl.Yt.begin(), pl.Yt.end(), pts.begin() + 3 * (size_t)M);
     std::vector<int> pos(pl.n_check);
-    if (o.precision == PSUM_FP32C) {
+    if (o.precision != PSUM_FP64) {   // FP32C and FF: float32 hi/lo packing
         const int tile = kTile32;
         pl.check_tile = tile;
         pl.n_check_tiles = (pl.n_check + tile - 1) / tile;

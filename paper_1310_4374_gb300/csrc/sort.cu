@@ -127,7 +127,8 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(const uint32_t* _
 // One warp per group of kNearChunk sorted positions: the bounding-box midpoint is the
 // float64 origin, stored with the group radius (largest distance of a point from it);
 // each point's offset from the origin is split into a float32 hi part and the float32
-// rounding remainder lo, packed two float4 each: (x,x,y,y),(z,z,q,q) and (xl,xl,yl,yl),(zl,zl,0,0).
+// rounding remainder lo, packed two float4 each: (x,x,y,y),(z,z,q,q) and (xl,xl,yl,yl),(zl,zl,ql,ql)
+// (ql = q - float(q), read only by the float-float kernels).
 // Padding points (s >= n) get q = 0 and a far-away position.
 // With a group table (batches) group g covers the sorted positions
 // [grp_start[g], grp_start[g] + grp_count[g]); without one, [128 g, min(128 (g+1), n)).
@@ -188,18 +189,19 @@ __global__ void k_pack32(const double* __restrict__ x, const double* __restrict_
 #pragma unroll
     for (int k = 0; k < per; ++k) {
         const int64_t s = grp * kNearChunk + k * 32 + lane;
-        float fx = 1.0e3f, fy = 1.0e3f, fz = 1.0e3f, fq = 0.f, lx = 0.f, ly = 0.f, lz = 0.f;
+        float fx = 1.0e3f, fy = 1.0e3f, fz = 1.0e3f, fq = 0.f, lx = 0.f, ly = 0.f, lz = 0.f, lq = 0.f;
         if (ok[k]) {
             const double rx = px[k][0] - o[0], ry = px[k][1] - o[1], rz = px[k][2] - o[2];
             r2max = fmax(r2max, rx * rx + ry * ry + rz * rz);
             fx = (float)rx; fy = (float)ry; fz = (float)rz;
             lx = (float)(rx - (double)fx); ly = (float)(ry - (double)fy); lz = (float)(rz - (double)fz);
             fq = fqk[k];
+            lq = (float)(pq[k] - (double)fq);     // the charge's float-float remainder (FF pair sums)
         }
         pk_hi[2 * s] = make_float4(fx, fx, fy, fy);
         pk_hi[2 * s + 1] = make_float4(fz, fz, fq, fq);
         pk_lo[2 * s] = make_float4(lx, lx, ly, ly);
-        pk_lo[2 * s + 1] = make_float4(lz, lz, 0.f, 0.f);
+        pk_lo[2 * s + 1] = make_float4(lz, lz, lq, lq);
         if (xs) {
             xs[3 * s] = ok[k] ? px[k][0] : 1.0e3;
             xs[3 * s + 1] = ok[k] ? px[k][1] : 1.0e3;

@@ -45,6 +45,7 @@ def test_strerror_and_defaults_without_gpu():
     ((1, -1, 1), 8, 200, "fp64", (1, 1, 1)),       # d <= 0
     ((1, 1, float("nan")), 8, 200, "fp64", (1, 1, 1)),
     ((1, 1, 1), 8, 200, 7, (1, 1, 1)),             # unknown precision
+    ((1, 1, 1), 8, 200, 3, (1, 1, 1)),
     ((1, 1, 1), 8, 200, "fp64", (1, 4, 1)),        # K out of range
 ])
 def test_invalid_plan_arguments_are_rejected_on_the_host(d, p, M, prec, K):
