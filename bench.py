@@ -394,8 +394,10 @@ def batch_leg(args):
         ms = ev0.elapsed_time(ev1) / reps
     finally:
         pb.close()
+    wide = sum(1 for s in systems if tuple(s.K) != (1, 1, 1))
     return {"workload": f"{len(systems)} systems, N log-uniform in [500, 20000] (total {info['N_total']}), "
-                        "d = (1, U[1,2], U[1,2]), p in {8,12,16}, +-1 charges, fp32c, CUDA graph",
+                        "d = (1, U[1,2], U[1,2]), p in {8,12,16}, +-1 charges, fp32c, CUDA graph; "
+                        f"{wide} flat boxes with a widened near block (K = (2,1,1))",
             "pairs_per_s": info["pairs"] / (ms * 1e-3), "systems_per_s": len(systems) / (ms * 1e-3),
             "ms_per_step": ms, "pairs_per_step": info["pairs"], "ctas": info["ctas"],
             "autotuned_variant": info["variant"], "plan_setup_s": t_plans}

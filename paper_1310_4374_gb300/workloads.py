@@ -37,6 +37,7 @@ class System:
     M: int                 # number of check points
     name: str = ""
     meta: dict = field(default_factory=dict)
+    K: tuple = (1, 1, 1)   # near block: images |i_k| <= K_k of the box (Eq. 3)
 
     @property
     def N(self) -> int:
@@ -138,8 +139,20 @@ def batch(B: int = 256, n_lo: int = 500, n_hi: int = 20000, seed: int = 3) -> li
         x = _clip_into_box(rng.uniform(-0.5, 0.5, size=(N, 3)) * np.asarray(d), d)
         q = np.concatenate([np.ones(N // 2), -np.ones(N // 2)])
         rng.shuffle(q)
-        out.append(System(x, q, d, p, M, name=f"batch{b}_N{N}"))
+        out.append(System(x, q, d, p, M, name=f"batch{b}_N{N}", K=batch_near_block(d)))
     return out
+
+
+def batch_near_block(d) -> tuple:
+    """Configuration rule of the batch workload: the 3x3x3 block, widened along the short
+    axes of flat boxes.  The largest ball about the box centre inside the 3x3x3 block has
+    radius 1.5 min(d); when that is under 1.1 times the circumscribed radius |d|/2 (the
+    truncation error then barely falls with p), K_k = max(1, ceil(1.25 |d|/(2 d_k) - 1/2))
+    makes it at least 1.25 times."""
+    h = 0.5 * math.sqrt(sum(v * v for v in d))
+    if 1.5 * min(d) >= 1.1 * h:
+        return (1, 1, 1)
+    return tuple(max(1, int(math.ceil(1.25 * h / v - 0.5))) for v in d)
 
 
 def config(k: int, small: bool = False):

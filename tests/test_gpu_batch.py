@@ -25,7 +25,7 @@ _REF = {}
 
 def _oracle(s):
     if s.name not in _REF:
-        _REF[s.name] = O.periodic_sum(s.x, s.q, s.d, s.p, s.M, parts=True)
+        _REF[s.name] = O.periodic_sum(s.x, s.q, s.d, s.p, s.M, K=s.K, parts=True)
     return _REF[s.name]
 
 
@@ -60,7 +60,7 @@ def test_batch_agrees_with_single_evaluations():
         x, q = _cat(systems)
         phi, g = pb(x, q)
         for b, s in enumerate(systems):
-            pc = B.PeriodicCoulomb(s.d, s.p, s.M, precision="fp32c")
+            pc = B.PeriodicCoulomb(s.d, s.p, s.M, precision="fp32c", K=s.K)
             try:
                 p1, g1 = pc(torch.as_tensor(s.x, device="cuda"), torch.as_tensor(s.q, device="cuda"))
             finally:
