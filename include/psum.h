@@ -70,8 +70,7 @@ extern "C" {
                           compensated (two-sum) accumulation, float64 elsewhere */
 #define PSUM_FF     2  /* pair arithmetic in float-float (a float32 pair carrying about 44 bits)
                           on the float32 pipe: float64-class results (the float64 tolerance)
-                          without float64 pair arithmetic; float64 elsewhere.  psum_energy_backward
-                          and the batch API reject FF plans (PSUM_ERR_ARG). */
+                          without float64 pair arithmetic; float64 elsewhere. */
 
 #define PSUM_POINTS_FIBONACCI 0  /* M check points on a spherical Fibonacci lattice */
 #define PSUM_POINTS_GAUSS     1  /* the Gauss spherical grid of Sec. 2.2: polar angles at the zeros of

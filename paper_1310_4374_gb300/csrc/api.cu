@@ -59,6 +59,7 @@ struct Layout {
     // backward
     double *far_phi, *far_grad, *w_part, *w, *u, *psi, *gpsi, *part_b;
     float4* chk_src32;
+    float4* chk_src32lo;   // float-float plans: lo parts of the check points as sources
     double4_32a* chk_src64;
     NearPlanLaunch Lb;
     int nblk_mom;
@@ -130,12 +131,15 @@ size_t layout(Plan& pl, int64_t N, char* base, Layout& L, bool backward = false,
     L.Lc.counter = flags + 2;
     L.far_phi = L.far_grad = L.w_part = L.w = L.u = L.psi = L.gpsi = L.part_b = nullptr;
     L.chk_src32 = nullptr;
+    L.chk_src32lo = nullptr;
     L.chk_src64 = nullptr;
     L.nblk_mom = 0;
     if (backward) {
         const int n_img = pl.n_images;
         const int64_t n_chk_chunks = fp32 ? (int64_t)pl.n_check_tiles * kTgt32 : (int64_t)pl.n_check_tiles;
-        const int64_t gmax = (int64_t)pl.num_sms * (fp32 ? near32_occupancy_ctas(n_img) : near64_occupancy_ctas());
+        const int64_t gmax = (int64_t)pl.num_sms *
+                             (fp32 ? near32_occupancy_ctas(n_img, 0, false, pl.opt.precision == PSUM_FF)
+                                   : near64_occupancy_ctas());
         L.Lb = near_partition(L.n_tiles, n_chk_chunks, n_img, gmax);
         L.Lb.counter = flags + 3;
         L.nblk_mom = moments_blocks(N);
@@ -150,6 +154,7 @@ size_t layout(Plan& pl, int64_t N, char* base, Layout& L, bool backward = false,
         L.part_b = b.take<double>((size_t)L.n_tiles * L.Lb.max_contrib * 4 * tile);
         if (fp32)
             L.chk_src32 = b.take<float4>(2 * (size_t)n_chk_chunks * kNearChunk);
+            if (pl.opt.precision == PSUM_FF) L.chk_src32lo = b.take<float4>(2 * (size_t)n_chk_chunks * kNearChunk);
         else
             L.chk_src64 = b.take<double4_32a>((size_t)n_chk_chunks * kNearChunk);
     }
@@ -282,7 +287,8 @@ int backward_device(psum_plan_s* h, int64_t N, const double* x, const double* q,
     int rs = ensure_scratch(pl, layout(pl, N, nullptr, L, true));
     if (rs != PSUM_OK) return rs;
     layout(pl, N, (char*)pl.scratch.ptr, L, true);
-    const bool fp32 = o.precision == PSUM_FP32C;
+    const bool fp32 = o.precision != PSUM_FP64;       // float32 packing (FP32C and FF)
+    const bool ff = o.precision == PSUM_FF;
     const int M = o.M, P = pl.P;
     if (moments_smem(o.p) > 48 * 1024) TRY(set_moments_smem(moments_smem(o.p)));
     const int* perm = nullptr;
@@ -305,9 +311,10 @@ int backward_device(psum_plan_s* h, int64_t N, const double* x, const double* q,
     if (fp32) {
         const size_t n_chk_pts = (size_t)pl.n_check_tiles * kTile32;
         const float4* chk = (const float4*)pl.d_check_tgt;
-        TRY(launch_check_sources32(chk, pl.d_check_inv, (int64_t)n_chk_pts, M, L.u, L.chk_src32, st));
-        TRY(launch_near32(true, L.chk_src32, chk + 2 * n_chk_pts, pl.d_check_org, L.pk32, L.pk32lo, L.org,
-                          pl.d_shifts, L.part_b, L.Lb, st));
+        TRY(launch_check_sources32(chk, chk + 2 * n_chk_pts, pl.d_check_inv, (int64_t)n_chk_pts, M, L.u,
+                                   L.chk_src32, L.chk_src32lo, st));
+        TRY(launch_near32(true, L.chk_src32, ff ? L.chk_src32lo : chk + 2 * n_chk_pts, pl.d_check_org, L.pk32,
+                          L.pk32lo, L.org, pl.d_shifts, L.part_b, L.Lb, st, 0, nullptr, 0.0, ff));
     } else {
         const size_t n_chk_pts = (size_t)pl.n_check_tiles * kTile64;
         TRY(launch_check_sources64((const double4_32a*)pl.d_check_tgt, (int64_t)n_chk_pts, M, L.u, L.chk_src64, st));
@@ -473,7 +480,6 @@ int psum_energy_backward(psum_plan_t h, int64_t N, const double* x, const double
     if (!h || N < 1 || N > (int64_t)1 << 30 || !x || !q || !phi || !grad || (!dEdq && !dEdx)) return PSUM_ERR_ARG;
     if (h->pl.Rb > 0.0) return PSUM_ERR_ARG;   // the adjoint assumes the untrimmed near block
     if (h->pl.opt.basis != PSUM_BASIS_SPHERICAL) return PSUM_ERR_ARG;   // and the solid-harmonic moments
-    if (h->pl.opt.precision == PSUM_FF) return PSUM_ERR_ARG;
     DeviceGuard g(h->pl.device);
     return backward_device(h, N, x, q, phi, grad, gE, dEdq, dEdx, (cudaStream_t)stream);
 }

@@ -84,16 +84,26 @@ __global__ void k_adjoint(const double* __restrict__ pinv, int rows, int M, cons
 }
 
 // Check points as sources: charge -u_l at y_l and +u_l at y~_l (packed positions from the plan).
-__global__ void k_check_sources32(const float4* __restrict__ chk_hi, const int* __restrict__ inv, int64_t n_pts,
-                                  int M, const double* __restrict__ u, float4* __restrict__ out_hi) {
+// The check points as sources of psi, charges -u_l at y_l and u_l at y~_l.  With out_lo
+// (float-float plans) the lo parts are copied too, with the charges' float32 remainders.
+__global__ void k_check_sources32(const float4* __restrict__ chk_hi, const float4* __restrict__ chk_lo,
+                                  const int* __restrict__ inv, int64_t n_pts, int M, const double* __restrict__ u,
+                                  float4* __restrict__ out_hi, float4* __restrict__ out_lo) {
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n_pts) return;
     const int j = inv[s];
-    float c = 0.f;
-    if (j >= 0) c = (float)(j < M ? -u[j] : u[j - M]);
+    double cd = 0.0;
+    if (j >= 0) cd = j < M ? -u[j] : u[j - M];
+    const float c = (float)cd;
     const float4 A = chk_hi[2 * s], B = chk_hi[2 * s + 1];
     out_hi[2 * s] = A;
     out_hi[2 * s + 1] = make_float4(B.x, B.y, c, c);
+    if (out_lo) {
+        const float cl = (float)(cd - (double)c);
+        const float4 C = chk_lo[2 * s], D = chk_lo[2 * s + 1];
+        out_lo[2 * s] = C;
+        out_lo[2 * s + 1] = make_float4(D.x, D.y, cl, cl);
+    }
 }
 
 __global__ void k_check_sources64(const double4_32a* __restrict__ chk, int64_t n_pts, int M,
@@ -179,9 +189,10 @@ cudaError_t launch_adjoint(const double* pinv, int rows, int M, const double* w,
     return cudaGetLastError();
 }
 
-cudaError_t launch_check_sources32(const float4* chk_hi, const int* inv, int64_t n_pts, int M, const double* u,
-                                   float4* out_hi, cudaStream_t st) {
-    k_check_sources32<<<(unsigned)((n_pts + 255) / 256), 256, 0, st>>>(chk_hi, inv, n_pts, M, u, out_hi);
+cudaError_t launch_check_sources32(const float4* chk_hi, const float4* chk_lo, const int* inv, int64_t n_pts, int M,
+                                   const double* u, float4* out_hi, float4* out_lo, cudaStream_t st) {
+    k_check_sources32<<<(unsigned)((n_pts + 255) / 256), 256, 0, st>>>(chk_hi, chk_lo, inv, n_pts, M, u, out_hi,
+                                                                         out_lo);
     return cudaGetLastError();
 }
 

@@ -192,7 +192,7 @@ __global__ void k_bconstant(const BatchDev* __restrict__ sys, const double* __re
 }
 
 // steps 7-8 per segment: phi = phi_near + phi_far, grad likewise, written in caller order
-// (T = float for FP32C batches, double for FP64)
+// (T = float for FP32C batches, double for FP64 and FF)
 template <class T>
 __global__ void __launch_bounds__(kSeg) k_bfar(const double* __restrict__ x, const BatchDev* __restrict__ sys,
                                                const int* __restrict__ seg_sys, const int64_t* __restrict__ seg_start,
@@ -332,7 +332,7 @@ std::map<std::pair<int64_t, int64_t>, int> g_tune_cache;
 
 size_t batch_layout(psum_batch_s* bt, char* base) {
     Bump2 b{base};
-    const bool fp32 = bt->precision == PSUM_FP32C;
+    const bool fp32 = bt->precision != PSUM_FP64;   // float32 packing (FP32C and FF)
     const int B = bt->B;
     bt->d_sys = b.take<BatchDev>(B);
     bt->d_near_n = b.take<NearSys>(B);
@@ -383,7 +383,7 @@ size_t batch_layout(psum_batch_s* bt, char* base) {
 
 int queue_batch(psum_batch_s* bt, const double* x, const double* q, double* phi, double* grad, cudaStream_t st,
                 int variant) {
-    const bool fp32 = bt->precision == PSUM_FP32C;
+    const bool fp32 = bt->precision != PSUM_FP64;   // float32 packing (FP32C and FF)
     const int B = bt->B;
     int64_t nl = 0;
     BTRY(cudaMemsetAsync(bt->d_status, 0, sizeof(int) * B, st));
@@ -399,10 +399,11 @@ int queue_batch(psum_batch_s* bt, const double* x, const double* q, double* phi,
         BTRY(launch_pack32_groups(x, q, perm, bt->n_groups, bt->d_grp_start, bt->d_grp_count, bt->pk_hi, bt->pk_lo,
                                   bt->org, st));
         nl += 1 + 12 + 1;
+        const bool ff = bt->precision == PSUM_FF;
         BTRY(launch_near32(true, bt->pk_hi, bt->pk_lo, bt->org, bt->pk_hi, bt->pk_lo, bt->org, bt->d_shifts,
-                           bt->part_n, bt->Ln[variant], st, variant));
+                           bt->part_n, bt->Ln[variant], st, variant, nullptr, 0.0, ff));
         BTRY(launch_near32(false, bt->pk_hi, bt->pk_lo, bt->org, bt->d_chk_hi, bt->d_chk_lo, bt->d_chk_org,
-                           bt->d_shifts, bt->part_c, bt->Lc, st, 0));
+                           bt->d_shifts, bt->part_c, bt->Lc, st, 0, nullptr, 0.0, ff));
     } else {
         BTRY(launch_pack64_groups(x, q, bt->n_pts, bt->d_grp_start, bt->d_grp_count, bt->pk64, st));
         nl += 1;
@@ -421,7 +422,7 @@ int queue_batch(psum_batch_s* bt, const double* x, const double* q, double* phi,
     k_bconstant<<<B, 32, 0, st>>>(bt->d_sys, bt->mean_part, bt->C);
     int max_tab = 1;
     for (const psum_plan_t p : bt->plans) max_tab = std::max(max_tab, sh_tab_size(p->pl.opt.p));
-    if (fp32)
+    if (bt->precision == PSUM_FP32C)
         k_bfar<float><<<bt->n_seg, kSeg, sizeof(float) * (maxP + max_tab), st>>>(
             x, bt->d_sys, bt->d_seg_sys, bt->d_seg_start, perm, bt->phi_n, grad ? bt->grad_n : nullptr, bt->C,
             bt->d_status, phi, grad);
@@ -516,7 +517,6 @@ int psum_batch_create(const psum_plan_t* plans, int B, const int64_t* offsets, p
         if (plans[b]->pl.device != plans[0]->pl.device) return PSUM_ERR_ARG;
         if (plans[b]->pl.Rb > 0.0) return PSUM_ERR_ARG;   // trimmed near sets: single-system path only
         if (plans[b]->pl.opt.basis != PSUM_BASIS_SPHERICAL) return PSUM_ERR_ARG;
-        if (plans[b]->pl.opt.precision == PSUM_FF) return PSUM_ERR_ARG;
     }
     if (offsets[B] > ((int64_t)1 << 30)) return PSUM_ERR_ARG;
     psum_batch_s* bt = new (std::nothrow) psum_batch_s();
@@ -527,7 +527,8 @@ int psum_batch_create(const psum_plan_t* plans, int B, const int64_t* offsets, p
     bt->precision = plans[0]->pl.opt.precision;
     bt->N = offsets[B];
     DevGuard dg(bt->device);
-    const bool fp32 = bt->precision == PSUM_FP32C;
+    const bool fp32 = bt->precision != PSUM_FP64;   // float32 packing (FP32C and FF)
+    const bool ff = bt->precision == PSUM_FF;
     const int tile = fp32 ? kTile32 : kTile64;
     const int gpt = fp32 ? kTgt32 : 1;                  // groups (= chunks) per tile
     const int num_sms = plans[0]->pl.num_sms;
@@ -606,11 +607,13 @@ int psum_batch_create(const psum_plan_t* plans, int B, const int64_t* offsets, p
     int max_img = 1;
     for (int b = 0; b < B; ++b) max_img = std::max(max_img, plans[b]->pl.n_images);
     for (int v = 0; v < (fp32 ? kNear32Variants : 1); ++v) {
-        const int64_t gmax = (int64_t)num_sms * (fp32 ? near32_occupancy_ctas(max_img, v) : near64_occupancy_ctas());
+        const int64_t gmax = (int64_t)num_sms * (fp32 ? near32_occupancy_ctas(max_img, v, false, ff)
+                                                       : near64_occupancy_ctas());
         bt->Ln[v] = near_partition(bt->near_n, gmax, nullptr);
     }
     {
-        const int64_t gmax = (int64_t)num_sms * (fp32 ? near32_occupancy_ctas(max_img, 0) : near64_occupancy_ctas());
+        const int64_t gmax = (int64_t)num_sms * (fp32 ? near32_occupancy_ctas(max_img, 0, false, ff)
+                                                       : near64_occupancy_ctas());
         bt->Lc = near_partition(bt->near_c, gmax, nullptr);
     }
     int st = PSUM_OK;
@@ -715,7 +718,7 @@ int psum_batch_eval(psum_batch_t bt, const double* x, const double* q, double* p
         for (int k = 0; k < 5; ++k) bt->g_args[k] = args[k];
     }
     BTRY(cudaGraphLaunch(bt->exec, st));
-    bt->launches += 2 + (bt->precision == PSUM_FP32C ? 14 : 1) + 4 + 5;
+    bt->launches += 2 + (bt->precision != PSUM_FP64 ? 14 : 1) + 4 + 5;
     return PSUM_OK;
 }
 

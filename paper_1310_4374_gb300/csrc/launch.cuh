@@ -61,8 +61,8 @@ cudaError_t launch_moments(const double* x, const double* q, int64_t n, const do
 int moments_blocks(int64_t n);
 size_t moments_smem(int p);
 cudaError_t launch_adjoint(const double* pinv, int rows, int M, const double* w, double* u, cudaStream_t st);
-cudaError_t launch_check_sources32(const float4* chk_hi, const int* inv, int64_t n_pts, int M, const double* u,
-                                   float4* out_hi, cudaStream_t st);
+cudaError_t launch_check_sources32(const float4* chk_hi, const float4* chk_lo, const int* inv, int64_t n_pts, int M,
+                                   const double* u, float4* out_hi, float4* out_lo, cudaStream_t st);
 cudaError_t launch_check_sources64(const double4_32a* chk, int64_t n_pts, int M, const double* u,
                                    double4_32a* out, cudaStream_t st);
 cudaError_t launch_backward_combine(int64_t n, const int* perm, const double* q, const double* phi,

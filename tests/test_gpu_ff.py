@@ -98,17 +98,37 @@ def test_ff_with_ball_trimming_and_rbf_basis():
     assert max(_eps(phi, g, ref)) < TOL
 
 
-def test_ff_plans_refuse_backward_and_batches():
-    s = W.uniform_pm1(N=200, p=6, M=100, seed=2)
+def test_ff_backward_matches_the_oracle_adjoint():
+    s = W.config(5, small=True)
+    pl = O.Plan(s.d, s.p, s.M)
+    ref = O.energy_and_gradients(pl, s.x, s.q)
     pc = B.PeriodicCoulomb(s.d, s.p, s.M, precision="ff")
     try:
         x, q = _dev(s.x), _dev(s.q)
         phi, g = pc(x, q)
-        with pytest.raises(B.PsumError) as e:
-            B.psum_energy_backward(pc.plan, x, q, phi, g, dEdq=torch.empty_like(q))
-        assert e.value.status == B.PSUM_ERR_ARG
-        with pytest.raises(B.PsumError) as e:
-            B.psum_batch_create([pc.plan], [0, s.x.shape[0]])
-        assert e.value.status == B.PSUM_ERR_ARG
+        dEdq, dEdx = torch.empty_like(q), torch.empty_like(x)
+        B.psum_energy_backward(pc.plan, x, q, phi, g, dEdq=dEdq, dEdx=dEdx)
+        torch.cuda.synchronize()
     finally:
         pc.close()
+    dq = dEdq.cpu().numpy()
+    # dE/dq is defined up to a constant (the charges sum to zero)
+    assert O.relative_l2(dq - dq.mean(), ref["dEdq"] - ref["dEdq"].mean()) < TOL
+    assert O.relative_l2(dEdx.cpu().numpy(), ref["dEdx"]) < TOL
+
+
+def test_ff_batch_matches_the_oracle():
+    systems = W.config(4, small=True)
+    pb = B.PeriodicBatch(systems, precision="ff")
+    try:
+        x = torch.as_tensor(np.concatenate([s.x for s in systems]), dtype=torch.float64, device="cuda")
+        q = torch.as_tensor(np.concatenate([s.q for s in systems]), dtype=torch.float64, device="cuda")
+        phi, g = pb(x, q, use_graph=True)
+        phi, g = phi.cpu().numpy(), g.cpu().numpy()
+        for b, s in enumerate(systems):
+            sl = slice(pb.offsets[b], pb.offsets[b + 1])
+            ref = O.periodic_sum(s.x, s.q, s.d, s.p, s.M, K=s.K, parts=True)
+            e_phi, e_g = _eps(phi[sl], g[sl], ref)
+            assert e_phi < TOL and e_g < TOL, (s.name, e_phi, e_g)
+    finally:
+        pb.close()
