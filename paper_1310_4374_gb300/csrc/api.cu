@@ -86,7 +86,7 @@ size_t layout(Plan& pl, int64_t N, char* base, Layout& L, bool backward = false,
         int64_t gmax = (int64_t)pl.num_sms * near32_occupancy_ctas(n_img, 0, trimmed, pl.opt.precision == PSUM_FF);
         if (g_cap > 0 && gmax > g_cap) gmax = g_cap;
         L.Ln = near_partition(L.n_tiles, L.n_chunks, n_img, gmax, ipc);
-        L.Lc = near_partition(pl.n_check_tiles, L.n_chunks, n_img, gmax, ipc);
+        L.Lc = near_partition(pl.n_check_tiles, L.n_chunks, n_img, gmax, g_cap > 0 ? 1 : kCheckItemsPerCta);
         L.xs = trimmed ? b.take<double>(3 * (size_t)L.n_pts) : nullptr;
         L.ka = b.take<uint32_t>(N);
         L.va = b.take<uint32_t>(N);
@@ -107,7 +107,7 @@ size_t layout(Plan& pl, int64_t N, char* base, Layout& L, bool backward = false,
         int64_t gmax = (int64_t)pl.num_sms * near64_occupancy_ctas();
         if (g_cap > 0 && gmax > g_cap) gmax = g_cap;
         L.Ln = near_partition(L.n_tiles, L.n_chunks, n_img, gmax, ipc);
-        L.Lc = near_partition(pl.n_check_tiles, L.n_chunks, n_img, gmax, ipc);
+        L.Lc = near_partition(pl.n_check_tiles, L.n_chunks, n_img, gmax, g_cap > 0 ? 1 : kCheckItemsPerCta);
         L.ka = L.va = L.kb = L.vb = L.hist = nullptr;
         L.pk32 = L.pk32lo = nullptr;
         L.org = nullptr;

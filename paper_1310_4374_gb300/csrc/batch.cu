@@ -614,7 +614,7 @@ int psum_batch_create(const psum_plan_t* plans, int B, const int64_t* offsets, p
     {
         const int64_t gmax = (int64_t)num_sms * (fp32 ? near32_occupancy_ctas(max_img, 0, false, ff)
                                                        : near64_occupancy_ctas());
-        bt->Lc = near_partition(bt->near_c, gmax, nullptr);
+        bt->Lc = near_partition(bt->near_c, gmax, nullptr, kCheckItemsPerCta);
     }
     int st = PSUM_OK;
     const size_t bytes = batch_layout(bt, nullptr);
