@@ -146,6 +146,18 @@ int psum_plan_create_ex(const psum_opts *o, psum_plan_t *out);
 int psum_eval(psum_plan_t plan, int64_t N, const double *x, const double *q,
               double *phi, double *grad, void *stream);
 
+/* Algorithm "get" at separate evaluation points (the general problem of Sec. 1: the
+   potential and its gradient at points y of the box due to the N charges; psum_eval is the
+   case Y0 = X0 of Remark 1).
+     x, q      : the charges as in psum_eval (device, caller-owned).
+     y         : T x 3 float64 evaluation points, row-major, device, inside the half-open box.
+     phi, grad : T and T x 3 float64 outputs (grad may be NULL).
+   A point that coincides exactly with a charge drops that pair (K(0) = 0, Eq. 1).  Works
+   with every precision, point scheme, basis and the ball-trimmed near set.  Asynchronous on
+   `stream`; a point outside the box gives PSUM_ERR_OUT_OF_BOX at psum_sync. */
+int psum_eval_points(psum_plan_t plan, int64_t N, const double* x, const double* q, int64_t T,
+                     const double* y, double* phi, double* grad, void* stream);
+
 /* The same with HOST pointers: copies x and q to the device, evaluates, copies
  * phi and grad back and waits for the stream.  Returns the final status
  * (including device-side conditions). */

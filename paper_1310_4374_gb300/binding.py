@@ -91,6 +91,7 @@ def load(build_if_needed: bool = True):
                                      ctypes.POINTER(_vp)]
     lib.psum_plan_create_ex.argtypes = [ctypes.POINTER(psum_opts), ctypes.POINTER(_vp)]
     lib.psum_eval.argtypes = [_vp, ctypes.c_int64, _vp, _vp, _vp, _vp, _vp]
+    lib.psum_eval_points.argtypes = [_vp, ctypes.c_int64, _vp, _vp, ctypes.c_int64, _vp, _vp, _vp, _vp]
     lib.psum_eval_host.argtypes = [_vp, ctypes.c_int64, _vp, _vp, _vp, _vp, _vp]
     lib.psum_eval_noalloc.argtypes = [_vp, ctypes.c_int64, _vp, _vp, _vp, _vp, _vp]
     lib.psum_sync.argtypes = [_vp, _vp]
@@ -116,7 +117,7 @@ def load(build_if_needed: bool = True):
     for name in ("psum_plan_create", "psum_plan_create_ex", "psum_eval", "psum_eval_host", "psum_eval_noalloc",
                  "psum_sync",
                  "psum_get_coeffs", "psum_plan_info", "psum_profile", "psum_last_timings", "psum_launch_count",
-                 "psum_energy", "psum_energy_backward", "psum_batch_create", "psum_batch_eval",
+                 "psum_energy", "psum_energy_backward", "psum_eval_points", "psum_batch_create", "psum_batch_eval",
                  "psum_batch_sync", "psum_batch_get_coeffs", "psum_batch_get_info"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
@@ -193,6 +194,20 @@ def psum_eval(plan, x, q, phi, grad=None, stream=None, check: bool = False) -> i
     _check(s, "psum_eval")
     if check:
         _check(psum_sync(plan, st), "psum_eval (device)")
+    return s
+
+
+def psum_eval_points(plan, x, q, y, phi, grad=None, stream=None, check: bool = False) -> int:
+    """Queue algorithm "get" at separate evaluation points y (device tensors, float64)."""
+    for t in (x, q, y, phi) + ((grad,) if grad is not None else ()):
+        if not (t.is_cuda and t.is_contiguous()):
+            raise ValueError("psum_eval_points takes contiguous CUDA tensors")
+    st = _stream_ptr(stream)
+    s = load().psum_eval_points(plan, int(q.numel()), x.data_ptr(), q.data_ptr(), int(y.shape[0]), y.data_ptr(),
+                                phi.data_ptr(), grad.data_ptr() if grad is not None else None, st)
+    _check(s, "psum_eval_points")
+    if check:
+        _check(psum_sync(plan, st), "psum_eval_points (device)")
     return s
 
 
@@ -369,6 +384,14 @@ class PeriodicCoulomb:
                  lam: float = 0.0, basis="spherical", n_rbf: int = 256, rbf_radius: float = 0.0):
         self.plan = psum_plan_create_ex(d, p, M, precision, mean, K, points, lam, basis, n_rbf, rbf_radius)
         self.info = psum_plan_info(self.plan)
+
+    def at(self, x, q, y, grad: bool = True, stream=None, check: bool = True):
+        """phi (and grad phi) at the evaluation points y due to the charges (x, q)."""
+        import torch
+        phi = torch.empty(y.shape[0], dtype=torch.float64, device=y.device)
+        g = torch.empty((y.shape[0], 3), dtype=torch.float64, device=y.device) if grad else None
+        psum_eval_points(self.plan, x, q, y, phi, g, stream, check)
+        return (phi, g) if grad else phi
 
     def __call__(self, x, q, grad: bool = True, stream=None, check: bool = True):
         import torch

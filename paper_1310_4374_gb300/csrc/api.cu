@@ -64,46 +64,74 @@ struct Layout {
     NearPlanLaunch Lb;
     int nblk_mom;
     NearPlanLaunch Ln, Lc;
-    int64_t n_tiles, n_chunks, n_pts;
+    int64_t n_tiles, n_chunks, n_pts;   // target tiles, source chunks, packed target points
+    int64_t n_src_groups, n_src_pts;    // the charges' pack (groups of 128, FP32C/FF; points, FP64)
     int nblk_val, nblk_mean;
+    // separate evaluation points (psum_eval_points): their sort and pack; null otherwise
+    uint32_t *tka, *tva, *tkb, *tvb, *thist;
+    float4 *tpk32, *tpk32lo;
+    double* torg;
+    double4_32a* tpk64;
 };
 
 // Lay out the scratch buffer for N charges; with base == nullptr only the size is computed.
-// `backward` adds the buffers of the energy derivatives.
-size_t layout(Plan& pl, int64_t N, char* base, Layout& L, bool backward = false, int64_t g_cap = 0) {
+// `backward` adds the buffers of the energy derivatives; T >= 0 adds T separate evaluation
+// points (their sort and pack), T < 0 evaluates at the charges.
+size_t layout(Plan& pl, int64_t N, char* base, Layout& L, bool backward = false, int64_t g_cap = 0,
+              int64_t T = -1) {
     Bump b{base, 0, 0};
+    const bool sep = T >= 0;
+    const int64_t NT = sep ? T : N;            // evaluation points
     const bool fp32 = pl.opt.precision != PSUM_FP64;   // float32 packing (FP32C and FF)
     const int n_img = pl.n_images;
     // a capped width (the allocation-free entry) keeps one work item per CTA: the partial
     // sums grow with the number of items
     const int ipc = g_cap > 0 ? 1 : kItemsPerCta;
+    L.tka = L.tva = L.tkb = L.tvb = L.thist = nullptr;
+    L.tpk32 = L.tpk32lo = nullptr;
+    L.torg = nullptr;
+    L.tpk64 = nullptr;
     if (fp32) {
-        L.n_tiles = (N + kTile32 - 1) / kTile32;
+        L.n_tiles = (NT + kTile32 - 1) / kTile32;
         L.n_chunks = (N + kNearChunk - 1) / kNearChunk;
         const int64_t n_groups = L.n_tiles * kTgt32;
         L.n_pts = n_groups * kNearChunk;
+        L.n_src_groups = sep ? L.n_chunks : n_groups;
+        L.n_src_pts = L.n_src_groups * kNearChunk;
         const bool trimmed = pl.Rb > 0.0;
         int64_t gmax = (int64_t)pl.num_sms * near32_occupancy_ctas(n_img, 0, trimmed, pl.opt.precision == PSUM_FF);
         if (g_cap > 0 && gmax > g_cap) gmax = g_cap;
         L.Ln = near_partition(L.n_tiles, L.n_chunks, n_img, gmax, ipc);
         L.Lc = near_partition(pl.n_check_tiles, L.n_chunks, n_img, gmax, g_cap > 0 ? 1 : kCheckItemsPerCta);
-        L.xs = trimmed ? b.take<double>(3 * (size_t)L.n_pts) : nullptr;
+        L.xs = trimmed ? b.take<double>(3 * (size_t)L.n_src_pts) : nullptr;
         L.ka = b.take<uint32_t>(N);
         L.va = b.take<uint32_t>(N);
         L.kb = b.take<uint32_t>(N);
         L.vb = b.take<uint32_t>(N);
         L.hist = b.take<uint32_t>((size_t)256 * sort_blocks(N));
-        L.pk32 = b.take<float4>(2 * (size_t)L.n_pts);
-        L.pk32lo = b.take<float4>(2 * (size_t)L.n_pts);
-        L.org = b.take<double>(4 * (size_t)n_groups);
+        L.pk32 = b.take<float4>(2 * (size_t)L.n_src_pts);
+        L.pk32lo = b.take<float4>(2 * (size_t)L.n_src_pts);
+        L.org = b.take<double>(4 * (size_t)L.n_src_groups);
         L.pk64 = nullptr;
+        if (sep) {
+            L.tka = b.take<uint32_t>(T);
+            L.tva = b.take<uint32_t>(T);
+            L.tkb = b.take<uint32_t>(T);
+            L.tvb = b.take<uint32_t>(T);
+            L.thist = b.take<uint32_t>((size_t)256 * sort_blocks(T));
+            L.tpk32 = b.take<float4>(2 * (size_t)L.n_pts);
+            L.tpk32lo = b.take<float4>(2 * (size_t)L.n_pts);
+            L.torg = b.take<double>(4 * (size_t)n_groups);
+        }
         L.part_n = b.take<double>((size_t)L.n_tiles * L.Ln.max_contrib * 4 * kTile32);
         L.part_c = b.take<double>((size_t)pl.n_check_tiles * L.Lc.max_contrib * kTile32);
         L.phi_c = b.take<double>((size_t)pl.n_check_tiles * kTile32);
     } else {
-        L.n_tiles = (N + kTile64 - 1) / kTile64;
-        L.n_chunks = L.n_tiles;
+        L.n_tiles = (NT + kTile64 - 1) / kTile64;
+        L.n_chunks = (N + kTile64 - 1) / kTile64;
         L.n_pts = L.n_tiles * kTile64;
+        L.n_src_groups = L.n_chunks;
+        L.n_src_pts = L.n_chunks * kTile64;
         int64_t gmax = (int64_t)pl.num_sms * near64_occupancy_ctas();
         if (g_cap > 0 && gmax > g_cap) gmax = g_cap;
         L.Ln = near_partition(L.n_tiles, L.n_chunks, n_img, gmax, ipc);
@@ -112,7 +140,8 @@ size_t layout(Plan& pl, int64_t N, char* base, Layout& L, bool backward = false,
         L.pk32 = L.pk32lo = nullptr;
         L.org = nullptr;
         L.xs = nullptr;
-        L.pk64 = b.take<double4_32a>((size_t)L.n_pts);
+        L.pk64 = b.take<double4_32a>((size_t)L.n_src_pts);
+        if (sep) L.tpk64 = b.take<double4_32a>((size_t)L.n_pts);
         L.part_n = b.take<double>((size_t)L.n_tiles * L.Ln.max_contrib * 4 * kTile64);
         L.part_c = b.take<double>((size_t)pl.n_check_tiles * L.Lc.max_contrib * kTile64);
         L.phi_c = b.take<double>((size_t)pl.n_check_tiles * kTile64);
@@ -196,7 +225,8 @@ int ensure_scratch(Plan& pl, size_t need) {
 // Algorithm "get" on the device for the charges (x, q), with the scratch laid out in L;
 // every kernel is queued on `st`.
 int queue_forward(psum_plan_s* h, int64_t N, const double* x, const double* q, double* phi, double* grad,
-                  const Layout& L, cudaStream_t st) {
+                  const Layout& L, cudaStream_t st, int64_t T = -1, const double* y = nullptr) {
+    const bool sep = y != nullptr;
     Plan& pl = h->pl;
     const psum_opts& o = pl.opt;
     const bool fp32 = o.precision != PSUM_FP64;       // float32 packing (FP32C and FF)
@@ -211,18 +241,38 @@ int queue_forward(psum_plan_s* h, int64_t N, const double* x, const double* q, d
     if (fp32) {
         TRY(launch_morton_sort(x, N, o.d, L.ka, L.va, L.kb, L.vb, L.hist, st));
         perm = (const int*)L.va;
-        TRY(launch_pack32(x, q, L.va, N, L.n_tiles * kTgt32, L.pk32, L.pk32lo, L.org, st, L.xs));
+        TRY(launch_pack32(x, q, L.va, N, L.n_src_groups, L.pk32, L.pk32lo, L.org, st, L.xs));
         h->launches += 1 + 4 * 3 + 1;
     } else {
-        TRY(launch_pack64(x, q, N, L.n_pts, L.pk64, st));
+        TRY(launch_pack64(x, q, N, L.n_src_pts, L.pk64, st));
         h->launches += 1;
     }
+    // separate evaluation points: validated, sorted and packed like the charges, without charges
+    const double* ex = sep ? y : x;              // evaluation points, caller order
+    const int* eperm = perm;
+    if (sep) {
+        TRY(launch_validate_points(y, T, o.d, L.nblk_val, L.eval_status, st));
+        h->launches += 1;
+        if (fp32) {
+            TRY(launch_morton_sort(y, T, o.d, L.tka, L.tva, L.tkb, L.tvb, L.thist, st));
+            eperm = (const int*)L.tva;
+            TRY(launch_pack32(y, nullptr, L.tva, T, L.n_tiles * kTgt32, L.tpk32, L.tpk32lo, L.torg, st));
+            h->launches += 1 + 4 * 3 + 1;
+        } else {
+            TRY(launch_pack64(y, nullptr, T, L.n_pts, L.tpk64, st));
+            h->launches += 1;
+        }
+    }
+    const float4* thi = sep ? L.tpk32 : L.pk32;
+    const float4* tlo = sep ? L.tpk32lo : L.pk32lo;
+    const double* tor = sep ? L.torg : L.org;
+    const double4_32a* t64 = sep ? L.tpk64 : L.pk64;
     if (h->profile) TRY(cudaEventRecord(h->ev[1], st));
     if (fp32) {
-        TRY(launch_near32(true, L.pk32, L.pk32lo, L.org, L.pk32, L.pk32lo, L.org, pl.d_shifts, L.part_n, L.Ln,
-                          st, 0, L.xs, pl.Rb, ff));
+        TRY(launch_near32(true, L.pk32, L.pk32lo, L.org, thi, tlo, tor, pl.d_shifts, L.part_n, L.Ln, st, 0, L.xs,
+                          pl.Rb, ff));
     } else {
-        TRY(launch_near64(true, L.pk64, L.pk64, pl.d_shifts, L.part_n, L.Ln, st, pl.Rb));
+        TRY(launch_near64(true, L.pk64, t64, pl.d_shifts, L.part_n, L.Ln, st, pl.Rb));
     }
     if (h->profile) TRY(cudaEventRecord(h->ev[2], st));
     if (fp32) {
@@ -236,7 +286,7 @@ int queue_forward(psum_plan_s* h, int64_t N, const double* x, const double* q, d
     }
     if (h->profile) TRY(cudaEventRecord(h->ev[3], st));
     const int tile = fp32 ? kTile32 : kTile64;
-    TRY(launch_near_reduce(L.part_n, N, tile, 4, L.Ln, L.phi_n, L.grad_n, st));
+    TRY(launch_near_reduce(L.part_n, sep ? T : N, tile, 4, L.Ln, L.phi_n, L.grad_n, st));
     TRY(launch_near_reduce(L.part_c, pl.n_check, tile, 1, L.Lc, L.phi_c, nullptr, st));
     h->launches += 4;   // two near-field kernels, two reductions
     const bool zero_mean = o.mean_mode == PSUM_MEAN_ZERO;
@@ -255,11 +305,12 @@ int queue_forward(psum_plan_s* h, int64_t N, const double* x, const double* q, d
     TRY(launch_constant(pl.d_C, pl.d_Rbox, P, L.mean_part, L.nblk_mean, 1.0 / (o.d[0] * o.d[1] * o.d[2]),
                         zero_mean ? 1 : 0, st));
     if (h->profile) TRY(cudaEventRecord(h->ev[4], st));
+    const int64_t NE = sep ? T : N;
     if (o.basis == PSUM_BASIS_RBF)
-        TRY(launch_far_rbf(x, N, perm, L.phi_n, grad ? L.grad_n : nullptr, pl.d_C, pl.d_rbf, pl.P - 1,
+        TRY(launch_far_rbf(ex, NE, eperm, L.phi_n, grad ? L.grad_n : nullptr, pl.d_C, pl.d_rbf, pl.P - 1,
                            L.eval_status, phi, grad, L.eval_status, st));
     else
-        TRY(launch_far_combine(x, N, perm, L.phi_n, grad ? L.grad_n : nullptr, pl.d_C, o.p, 1.0 / pl.R0,
+        TRY(launch_far_combine(ex, NE, eperm, L.phi_n, grad ? L.grad_n : nullptr, pl.d_C, o.p, 1.0 / pl.R0,
                                pl.d_shtab64, o.precision == PSUM_FP32C ? pl.d_shtab32 : nullptr, L.eval_status,
                                phi, grad, L.eval_status, st));
     k_status_merge<<<1, 1, 0, st>>>(L.eval_status, pl.d_status);
@@ -279,6 +330,16 @@ int eval_device(psum_plan_s* h, int64_t N, const double* x, const double* q, dou
     return queue_forward(h, N, x, q, phi, grad, L, st);
 }
 
+int eval_points_device(psum_plan_s* h, int64_t N, const double* x, const double* q, int64_t T, const double* y,
+                       double* phi, double* grad, cudaStream_t st) {
+    Plan& pl = h->pl;
+    Layout L;
+    int rs = ensure_scratch(pl, layout(pl, N, nullptr, L, false, 0, T));
+    if (rs != PSUM_OK) return rs;
+    layout(pl, N, (char*)pl.scratch.ptr, L, false, 0, T);
+    return queue_forward(h, N, x, q, phi, grad, L, st, T, y);
+}
+
 int backward_device(psum_plan_s* h, int64_t N, const double* x, const double* q, const double* phi,
                     const double* grad, const double* gE, double* dEdq, double* dEdx, cudaStream_t st) {
     Plan& pl = h->pl;
@@ -295,10 +356,10 @@ int backward_device(psum_plan_s* h, int64_t N, const double* x, const double* q,
     if (fp32) {
         TRY(launch_morton_sort(x, N, o.d, L.ka, L.va, L.kb, L.vb, L.hist, st));
         perm = (const int*)L.va;
-        TRY(launch_pack32(x, q, L.va, N, L.n_tiles * kTgt32, L.pk32, L.pk32lo, L.org, st));
+        TRY(launch_pack32(x, q, L.va, N, L.n_src_groups, L.pk32, L.pk32lo, L.org, st));
         h->launches += 1 + 4 * 3 + 1;
     } else {
-        TRY(launch_pack64(x, q, N, L.n_pts, L.pk64, st));
+        TRY(launch_pack64(x, q, N, L.n_src_pts, L.pk64, st));
         h->launches += 1;
     }
     // moments w and the far field at the charges; u = (A^+)^T w
@@ -422,6 +483,14 @@ int psum_eval(psum_plan_t h, int64_t N, const double* x, const double* q, double
     if (!h || N < 1 || N > (int64_t)1 << 30 || !x || !q || !phi) return PSUM_ERR_ARG;
     DeviceGuard g(h->pl.device);
     return eval_device(h, N, x, q, phi, grad, (cudaStream_t)stream);
+}
+
+int psum_eval_points(psum_plan_t h, int64_t N, const double* x, const double* q, int64_t T, const double* y,
+                     double* phi, double* grad, void* stream) {
+    if (!h || N < 1 || N > (int64_t)1 << 30 || T < 1 || T > (int64_t)1 << 30 || !x || !q || !y || !phi)
+        return PSUM_ERR_ARG;
+    DeviceGuard g(h->pl.device);
+    return eval_points_device(h, N, x, q, T, y, phi, grad, (cudaStream_t)stream);
 }
 
 int psum_sync(psum_plan_t h, void* stream) {

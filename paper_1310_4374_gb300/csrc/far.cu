@@ -58,6 +58,19 @@ __global__ void __launch_bounds__(kRedThreads) k_validate(const double* __restri
     }
 }
 
+// Evaluation points: inside the half-open box and finite, like the charges.
+__global__ void __launch_bounds__(kRedThreads) k_validate_points(const double* __restrict__ y, int64_t n, double d0,
+                                                                 double d1, double d2, int* __restrict__ status) {
+    int bad = 0;
+    for (int64_t i = (int64_t)blockIdx.x * kRedThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kRedThreads) {
+        const double a = y[3 * i], b = y[3 * i + 1], c = y[3 * i + 2];
+        const bool in = (a >= -0.5 * d0) && (a < 0.5 * d0) && (b >= -0.5 * d1) && (b < 0.5 * d1) &&
+                        (c >= -0.5 * d2) && (c < 0.5 * d2);
+        if (!in) bad |= kStatOutOfBox;
+    }
+    if (bad) atomicOr(status, bad);
+}
+
 __global__ void k_validate_finish(const double* __restrict__ partial, int nblk, int* __restrict__ status) {
     double s = 0.0, sa = 0.0;
     for (int b = threadIdx.x; b < nblk; b += 32) { s += partial[2 * b]; sa += partial[2 * b + 1]; }
@@ -308,6 +321,12 @@ int reduce_blocks(int64_t n, int num_sms) {
     const int64_t cap = 4LL * num_sms;
     if (nb > cap) nb = cap;
     return nb < 1 ? 1 : (int)nb;
+}
+
+cudaError_t launch_validate_points(const double* y, int64_t n, const double d[3], int nblk, int* status,
+                                   cudaStream_t st) {
+    k_validate_points<<<nblk, kRedThreads, 0, st>>>(y, n, d[0], d[1], d[2], status);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_validate(const double* x, const double* q, int64_t n, const double d[3], double* partial,

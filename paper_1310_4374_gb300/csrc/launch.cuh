@@ -33,6 +33,8 @@ cudaError_t launch_pack64_groups(const double* x, const double* q, int64_t n_pts
                                  const int* grp_count, double4_32a* pk, cudaStream_t st);
 // far.cu
 int reduce_blocks(int64_t n, int num_sms);
+cudaError_t launch_validate_points(const double* y, int64_t n, const double d[3], int nblk, int* status,
+                                   cudaStream_t st);
 cudaError_t launch_validate(const double* x, const double* q, int64_t n, const double d[3], double* partial,
                             int nblk, int* status, cudaStream_t st);
 cudaError_t launch_box_mean(const double* x, const double* q, int64_t n, const double H[3], double* partial,

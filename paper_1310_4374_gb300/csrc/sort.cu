@@ -157,7 +157,7 @@ __global__ void k_pack32(const double* __restrict__ x, const double* __restrict_
                 lo[c] = fmin(lo[c], px[k][c]);
                 hi[c] = fmax(hi[c], px[k][c]);
             }
-            pq[k] = q[i];
+            pq[k] = q ? q[i] : 0.0;               // no charges: a pack of evaluation points
         }
     }
     double o[3];
@@ -220,7 +220,7 @@ __global__ void k_pack64(const double* __restrict__ x, const double* __restrict_
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n_pad) return;
     if (s < n)
-        pk[s] = make_double4_32a(x[3 * s], x[3 * s + 1], x[3 * s + 2], q[s]);
+        pk[s] = make_double4_32a(x[3 * s], x[3 * s + 1], x[3 * s + 2], q ? q[s] : 0.0);
     else
         pk[s] = make_double4_32a(1.0e3, 1.0e3, 1.0e3, 0.0);
 }
