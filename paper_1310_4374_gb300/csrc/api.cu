@@ -158,6 +158,8 @@ size_t layout(Plan& pl, int64_t N, char* base, Layout& L, bool backward = false,
     L.eval_status = flags;
     L.Ln.counter = flags + 1;
     L.Lc.counter = flags + 2;
+    L.Ln.status = L.Lc.status = flags;
+    L.Ln.n_status = L.Lc.n_status = 1;
     L.far_phi = L.far_grad = L.w_part = L.w = L.u = L.psi = L.gpsi = L.part_b = nullptr;
     L.chk_src32 = nullptr;
     L.chk_src32lo = nullptr;
@@ -171,6 +173,8 @@ size_t layout(Plan& pl, int64_t N, char* base, Layout& L, bool backward = false,
                                    : near64_occupancy_ctas());
         L.Lb = near_partition(L.n_tiles, n_chk_chunks, n_img, gmax);
         L.Lb.counter = flags + 3;
+        L.Lb.status = flags;
+        L.Lb.n_status = 1;
         L.nblk_mom = moments_blocks(N);
         L.far_phi = b.take<double>((size_t)N);
         L.far_grad = b.take<double>(3 * (size_t)N);
@@ -352,6 +356,7 @@ int backward_device(psum_plan_s* h, int64_t N, const double* x, const double* q,
     const bool ff = o.precision == PSUM_FF;
     const int M = o.M, P = pl.P;
     if (moments_smem(o.p) > 48 * 1024) TRY(set_moments_smem(moments_smem(o.p)));
+    TRY(cudaMemsetAsync(L.eval_status, 0, sizeof(int), st));
     const int* perm = nullptr;
     if (fp32) {
         TRY(launch_morton_sort(x, N, o.d, L.ka, L.va, L.kb, L.vb, L.hist, st));
@@ -383,7 +388,9 @@ int backward_device(psum_plan_s* h, int64_t N, const double* x, const double* q,
     }
     TRY(launch_near_reduce(L.part_b, N, tile, 4, L.Lb, L.psi, L.gpsi, st));
     TRY(launch_backward_combine(N, perm, q, phi, grad, L.far_phi, L.far_grad, L.psi, L.gpsi, gE, dEdq, dEdx, st));
-    h->launches += 4;
+    k_status_merge<<<1, 1, 0, st>>>(L.eval_status, pl.d_status);
+    TRY(cudaGetLastError());
+    h->launches += 5;
     return PSUM_OK;
 }
 

@@ -215,7 +215,7 @@ __global__ void __launch_bounds__(kSeg) k_bfar(const double* __restrict__ x, con
     if (s >= S.n0 + S.n) return;
     const int64_t i = perm ? (int64_t)perm[s] : s;
     const int64_t pk = S.pt0 + (s - S.n0);
-    if (status[b] & (kStatNonNeutral | kStatOutOfBox | kStatNonFinite)) {
+    if (status[b] & (kStatNonNeutral | kStatOutOfBox | kStatNonFinite | kStatTimeout)) {
         phi[i] = __longlong_as_double(0x7ff8000000000000ll);
         if (grad) grad[3 * i] = grad[3 * i + 1] = grad[3 * i + 2] = __longlong_as_double(0x7ff8000000000000ll);
         return;
@@ -378,6 +378,12 @@ size_t batch_layout(psum_batch_s* bt, char* base) {
     int* counters = b.take<int>(2);            // work-item counters of the two pair launches
     for (int v = 0; v < kNear32Variants; ++v) bt->Ln[v].counter = counters;
     bt->Lc.counter = counters + 1;
+    for (int v = 0; v < kNear32Variants; ++v) {
+        bt->Ln[v].status = bt->d_status;
+        bt->Ln[v].n_status = B;
+    }
+    bt->Lc.status = bt->d_status;
+    bt->Lc.n_status = B;
     return b.off + 256;
 }
 

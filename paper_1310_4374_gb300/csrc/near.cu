@@ -68,9 +68,52 @@ struct Near32Args {
     double Rb;               // > 0: keep a source image x + p only if |x + p| <= Rb (get step 2)
     int64_t U, W;            // units, work items
     int* counter;            // next work item
+    int* status;             // error words (kStatTimeout when a chunk copy never lands)
+    int n_status;
     int max_contrib, max_img;
     NearSysTable tab;
 };
+
+// ---------------------------------------------------------------------------
+// Chunk staging by the bulk-copy (TMA) engine: one thread arms an mbarrier with the byte
+// count and issues two cp.async.bulk copies (hi and lo parts, 4 KiB each) from global to
+// shared memory; the CTA computes the chunk's image offsets meanwhile, and the same thread
+// waits for the barrier's phase with an iteration limit.
+// ---------------------------------------------------------------------------
+constexpr int kChunkBytes = 2 * kNearChunk * (int)sizeof(float4);   // one of the two parts
+constexpr long long kCopySpinLimit = 1LL << 22;   // polls; a copy lands in about a microsecond
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, int count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, int bytes) {
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}"
+                 ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, int bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
+}
+// true once the barrier has completed the phase with the given parity; false after the limit
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long long limit) {
+    for (long long it = 0; it < limit; ++it) {
+        uint32_t done;
+        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}"
+                     : "=r"(done) : "r"(smem_u32(bar)), "r"(parity) : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
 
 // unit classes against the ball S_b (flags in shared memory, per image of the staged chunk)
 constexpr int kUnitNear = 1;       // float-float offsets and K(0) = 0
@@ -324,8 +367,18 @@ __global__ void __launch_bounds__(kThreads32, kMinB) k_near32(Near32Args a) {
     float4* s_hm = s_dyn4 + (6 * kTgt32 * a.max_img + a.max_img + 3) / 4;
 
     __shared__ int s_item;
+    __shared__ int s_fail;
+    __shared__ __align__(8) uint64_t s_bar;
     const int tid = threadIdx.x;
     int64_t item = 0;
+    uint32_t phase = 0;
+    if (tid == 0) {
+        mbar_init(&s_bar, 1);
+        fence_mbar_init();
+        fence_proxy_async_smem();
+        s_fail = 0;
+    }
+    __syncthreads();
 
     auto flush = [&](int64_t tile, int64_t first_unit) {
         const int64_t slot = item - sk_owner(first_unit, a.U, a.W);
@@ -396,9 +449,13 @@ __global__ void __launch_bounds__(kThreads32, kMinB) k_near32(Near32Args a) {
         }
         if (chunk != cur_chunk) {
             __syncthreads();   // every thread is done with the previous chunk, deltas and flags
-            const float4* hsrc = a.src_hi + chunk * (2 * kNearChunk);
-            const float4* lsrc = a.src_lo + chunk * (2 * kNearChunk);
-            for (int i = tid; i < 2 * kNearChunk; i += kThreads32) { s_hi[i] = hsrc[i]; s_lo[i] = lsrc[i]; }
+            if (tid == 0) {
+                // order this CTA's earlier shared-memory accesses before the copy engine's writes
+                fence_proxy_async_smem();
+                mbar_expect_tx(&s_bar, 2 * kChunkBytes);
+                bulk_g2s(s_hi, a.src_hi + chunk * (2 * kNearChunk), kChunkBytes, &s_bar);
+                bulk_g2s(s_lo, a.src_lo + chunk * (2 * kNearChunk), kChunkBytes, &s_bar);
+            }
             const double* so = a.src_org + 4 * chunk;
             const int shift0 = Sp->shift0;
             for (int im = tid; im < n_img; im += kThreads32) {
@@ -426,7 +483,17 @@ __global__ void __launch_bounds__(kThreads32, kMinB) k_near32(Near32Args a) {
                 }
                 s_near[im] = nr;
             }
+            if (tid == 0 && !mbar_wait(&s_bar, phase, kCopySpinLimit)) s_fail = 1;
+            phase ^= 1u;
             __syncthreads();
+            if (s_fail) {
+                // the copy never completed: report it, give it one more bounded wait, leave
+                if (tid == 0) {
+                    for (int k = 0; k < a.n_status; ++k) atomicOr(a.status + k, kStatTimeout);
+                    mbar_wait(&s_bar, phase ^ 1u, kCopySpinLimit);
+                }
+                return;
+            }
             cur_chunk = chunk;
         }
         const float* dl = s_delta + 6 * (img * kTgt32);
@@ -705,6 +772,9 @@ cudaError_t launch_near32(bool grad, const float4* src_hi, const float4* src_lo,
                           double* partial, const NearPlanLaunch& L, cudaStream_t st, int variant,
                           const double* src_x, double Rb, bool ff) {
     Near32Args a;
+    a.status = L.status;
+    a.n_status = L.n_status;
+    if (!L.status || L.n_status < 1) return cudaErrorInvalidValue;
     a.src_hi = src_hi; a.src_lo = src_lo; a.src_org = src_org;
     a.tgt_hi = tgt_hi; a.tgt_lo = tgt_lo; a.tgt_org = tgt_org; a.shifts = shifts;
     a.partial = partial; a.U = L.U; a.W = L.W; a.counter = L.counter; a.max_contrib = L.max_contrib;

@@ -357,6 +357,8 @@ struct NearPlanLaunch {
     int64_t U, G;
     int64_t W;                    // work items
     int* counter = nullptr;       // device int, zeroed by the launcher before each launch
+    int* status = nullptr;        // device error words the pair kernel may flag (kStatTimeout)
+    int n_status = 0;
     int max_contrib;              // partial slots per tile
     int max_img;                  // largest image count of any system (shared-memory sizing)
     int64_t n_tiles;              // rows of the partial buffer
