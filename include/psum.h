@@ -272,6 +272,14 @@ int psum_batch_get_info(psum_batch_t batch, psum_batch_info *info);
 /* Release the batch (waits for the device). NULL is a no-op. */
 void psum_batch_destroy(psum_batch_t batch);
 
+/* Test hook of the failure path (the paper has no counterpart).  While enabled, the charge
+   pair kernel of this plan (float32 packing: PSUM_FP32C and PSUM_FF) arms its chunk-copy
+   barrier for 16 bytes more than the copies bring, so each wait runs out after a short
+   iteration limit: the kernel flags the evaluation, which then reports PSUM_ERR_TIMEOUT at
+   psum_sync and writes NaN, and the CUDA context stays usable.  Off by default; returns
+   PSUM_ERR_ARG for a NULL plan. */
+int psum_debug_inject_timeout(psum_plan_t plan, int enable);
+
 /* Release the plan and its device memory (waits for the device). NULL is a no-op. */
 void psum_destroy(psum_plan_t plan);
 

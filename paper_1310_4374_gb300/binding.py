@@ -91,6 +91,7 @@ def load(build_if_needed: bool = True):
                                      ctypes.POINTER(_vp)]
     lib.psum_plan_create_ex.argtypes = [ctypes.POINTER(psum_opts), ctypes.POINTER(_vp)]
     lib.psum_eval.argtypes = [_vp, ctypes.c_int64, _vp, _vp, _vp, _vp, _vp]
+    lib.psum_debug_inject_timeout.argtypes = [_vp, ctypes.c_int]
     lib.psum_eval_points.argtypes = [_vp, ctypes.c_int64, _vp, _vp, ctypes.c_int64, _vp, _vp, _vp, _vp]
     lib.psum_eval_host.argtypes = [_vp, ctypes.c_int64, _vp, _vp, _vp, _vp, _vp]
     lib.psum_eval_noalloc.argtypes = [_vp, ctypes.c_int64, _vp, _vp, _vp, _vp, _vp]
@@ -117,7 +118,7 @@ def load(build_if_needed: bool = True):
     for name in ("psum_plan_create", "psum_plan_create_ex", "psum_eval", "psum_eval_host", "psum_eval_noalloc",
                  "psum_sync",
                  "psum_get_coeffs", "psum_plan_info", "psum_profile", "psum_last_timings", "psum_launch_count",
-                 "psum_energy", "psum_energy_backward", "psum_eval_points", "psum_batch_create", "psum_batch_eval",
+                 "psum_energy", "psum_energy_backward", "psum_eval_points", "psum_debug_inject_timeout", "psum_batch_create", "psum_batch_eval",
                  "psum_batch_sync", "psum_batch_get_coeffs", "psum_batch_get_info"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
@@ -209,6 +210,10 @@ def psum_eval_points(plan, x, q, y, phi, grad=None, stream=None, check: bool = F
     if check:
         _check(psum_sync(plan, st), "psum_eval_points (device)")
     return s
+
+
+def psum_debug_inject_timeout(plan, enable: bool) -> None:
+    _check(load().psum_debug_inject_timeout(plan, 1 if enable else 0), "psum_debug_inject_timeout")
 
 
 def psum_eval_noalloc(plan, x, q, phi, grad=None, stream=None, check: bool = False) -> int:

@@ -273,7 +273,9 @@ int queue_forward(psum_plan_s* h, int64_t N, const double* x, const double* q, d
     const double4_32a* t64 = sep ? L.tpk64 : L.pk64;
     if (h->profile) TRY(cudaEventRecord(h->ev[1], st));
     if (fp32) {
-        TRY(launch_near32(true, L.pk32, L.pk32lo, L.org, thi, tlo, tor, pl.d_shifts, L.part_n, L.Ln, st, 0, L.xs,
+        NearPlanLaunch Ln = L.Ln;
+        Ln.inject = h->inject_timeout ? 1 : 0;
+        TRY(launch_near32(true, L.pk32, L.pk32lo, L.org, thi, tlo, tor, pl.d_shifts, L.part_n, Ln, st, 0, L.xs,
                           pl.Rb, ff));
     } else {
         TRY(launch_near64(true, L.pk64, t64, pl.d_shifts, L.part_n, L.Ln, st, pl.Rb));
@@ -587,6 +589,12 @@ int psum_plan_info(psum_plan_t h, psum_info* info) {
     info->n_images = pl.n_images;
     info->precision = pl.opt.precision;
     info->mean_mode = pl.opt.mean_mode;
+    return PSUM_OK;
+}
+
+int psum_debug_inject_timeout(psum_plan_t h, int enable) {
+    if (!h) return PSUM_ERR_ARG;
+    h->inject_timeout = enable != 0;
     return PSUM_OK;
 }
 

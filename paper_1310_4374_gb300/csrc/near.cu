@@ -70,6 +70,7 @@ struct Near32Args {
     int* counter;            // next work item
     int* status;             // error words (kStatTimeout when a chunk copy never lands)
     int n_status;
+    int inject;              // test hook: expect 16 bytes more than the copies bring
     int max_contrib, max_img;
     NearSysTable tab;
 };
@@ -452,7 +453,7 @@ __global__ void __launch_bounds__(kThreads32, kMinB) k_near32(Near32Args a) {
             if (tid == 0) {
                 // order this CTA's earlier shared-memory accesses before the copy engine's writes
                 fence_proxy_async_smem();
-                mbar_expect_tx(&s_bar, 2 * kChunkBytes);
+                mbar_expect_tx(&s_bar, 2 * kChunkBytes + (a.inject ? 16 : 0));
                 bulk_g2s(s_hi, a.src_hi + chunk * (2 * kNearChunk), kChunkBytes, &s_bar);
                 bulk_g2s(s_lo, a.src_lo + chunk * (2 * kNearChunk), kChunkBytes, &s_bar);
             }
@@ -483,14 +484,15 @@ __global__ void __launch_bounds__(kThreads32, kMinB) k_near32(Near32Args a) {
                 }
                 s_near[im] = nr;
             }
-            if (tid == 0 && !mbar_wait(&s_bar, phase, kCopySpinLimit)) s_fail = 1;
+            const long long limit = a.inject ? (1LL << 12) : kCopySpinLimit;
+            if (tid == 0 && !mbar_wait(&s_bar, phase, limit)) s_fail = 1;
             phase ^= 1u;
             __syncthreads();
             if (s_fail) {
                 // the copy never completed: report it, give it one more bounded wait, leave
                 if (tid == 0) {
                     for (int k = 0; k < a.n_status; ++k) atomicOr(a.status + k, kStatTimeout);
-                    mbar_wait(&s_bar, phase ^ 1u, kCopySpinLimit);
+                    mbar_wait(&s_bar, phase ^ 1u, limit);
                 }
                 return;
             }
@@ -774,6 +776,7 @@ cudaError_t launch_near32(bool grad, const float4* src_hi, const float4* src_lo,
     Near32Args a;
     a.status = L.status;
     a.n_status = L.n_status;
+    a.inject = L.inject;
     if (!L.status || L.n_status < 1) return cudaErrorInvalidValue;
     a.src_hi = src_hi; a.src_lo = src_lo; a.src_org = src_org;
     a.tgt_hi = tgt_hi; a.tgt_lo = tgt_lo; a.tgt_org = tgt_org; a.shifts = shifts;

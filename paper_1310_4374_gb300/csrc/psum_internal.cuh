@@ -359,6 +359,7 @@ struct NearPlanLaunch {
     int* counter = nullptr;       // device int, zeroed by the launcher before each launch
     int* status = nullptr;        // device error words the pair kernel may flag (kStatTimeout)
     int n_status = 0;
+    int inject = 0;               // test hook: arm the chunk-copy barrier for bytes that never come
     int max_contrib;              // partial slots per tile
     int max_img;                  // largest image count of any system (shared-memory sizing)
     int64_t n_tiles;              // rows of the partial buffer
@@ -415,5 +416,6 @@ struct psum_plan_s {
     psum::Plan pl;
     int64_t launches = 0;       // kernels queued so far
     bool profile = false;
+    bool inject_timeout = false;  // test hook: the charge pair kernel's copy waits run out
     cudaEvent_t ev[6] = {};
 };
