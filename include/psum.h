@@ -176,7 +176,7 @@ int psum_eval_host(psum_plan_t plan, int64_t N, const double *x, const double *q
  *
  * Arguments, results and status reporting are those of psum_eval (device pointers,
  * queued on `stream`, device-side conditions reported by psum_sync).  The results
- * agree with psum_eval to rounding: the pair sum is split over at most 256 CTAs, so
+ * agree with psum_eval to rounding: the pair sum is split into at most 256 work items, so
  * partial sums are grouped differently.  Limits: an evaluation whose scratch does not
  * fit in the 16 MiB array returns PSUM_ERR_ARG; that holds up to N = 32768 charges
  * for plans with p <= 16 and M <= 800 in either precision (larger p or M lower it).
@@ -244,7 +244,7 @@ typedef struct psum_batch_info {
 } psum_batch_info;
 
 /* B independent periodic systems evaluated together (algorithm "get" for each), with one
- * persistent stream-K launch for all charge pair sums and one for all check-point pair
+ * persistent launch (fixed work items, taken dynamically) for all charge pair sums and one for all check-point pair
  * sums.  plans[b] fixes system b's box, degree, check points and near block; all plans
  * must share the precision and the current device (a plan may appear several times).
  * offsets (host, B+1 entries, offsets[0] = 0, increasing) delimit system b's charges in

@@ -651,7 +651,7 @@ void psum_destroy(psum_plan_t h) {
 namespace {
 
 constexpr size_t kNoAllocBytes = (size_t)16 << 20;     // 16 MiB
-constexpr int64_t kNoAllocMaxCtas = 256;                // stream-K width: bounds the partial sums
+constexpr int64_t kNoAllocMaxCtas = 256;                // CTAs (one work item each): bounds the partial sums
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
 constexpr int kNoAllocMaxDevices = 64;

@@ -1,8 +1,8 @@
 // Many independent periodic systems in one evaluation (psum_batch_*).
 //
 // Each system b has its own plan (box, degree, check points, near block) and a slice
-// of the concatenated charges.  The charge pair sums of all systems form one stream-K
-// unit space and run as ONE persistent launch (the per-system table of the near
+// of the concatenated charges.  The charge pair sums of all systems form one unit space
+// (cut into work items) and run as ONE persistent launch (the per-system table of the near
 // kernels), and likewise the check-point pair sums; sorting, packing, validation, the
 // least-squares fits, the means and the far fields run as one launch each, with a
 // system descriptor per segment, group or block.  The whole sequence can be captured
@@ -608,7 +608,7 @@ int psum_batch_create(const psum_plan_t* plans, int B, const int64_t* offsets, p
     bt->n_seg = (int)seg_sys.size();
     bt->units = unit_n;
 
-    // schedules: one stream-K partition per pair-kernel variant for the charges, one for the
+    // schedules: one work-item partition per pair-kernel variant for the charges, one for the
     // check points; the device tables they point to are filled below
     int max_img = 1;
     for (int b = 0; b < B; ++b) max_img = std::max(max_img, plans[b]->pl.n_images);

@@ -3,16 +3,18 @@
 //   phi_near(y)      = sum_{p in images} sum_i q_i / |y - x_i - p|       (K(0) = 0, Eq. 1)
 //   grad phi_near(y) = sum_{p} sum_i q_i (x_i + p - y) / |y - x_i - p|^3
 //
-// at the N charges (potential and gradient) and at the 2M check points
-// (potential only).  Two kernels share one work decomposition:
+// at the N charges (potential and gradient), at the 2M check points (potential
+// only) or at separate evaluation points.  The kernels share one work decomposition:
 //
-//   * the work unit is (target tile, source chunk, image); the unit space is
-//     split into G contiguous ranges, one per CTA (a stream-K partition), so
-//     every CTA does the same number of units whatever N is;
-//   * a CTA stages a source chunk in shared memory once and applies every
-//     image to it; the image shift is folded into the targets in registers;
-//   * a CTA writes its per-tile partial sums to a slot of a partial buffer,
-//     and a reduction kernel adds the slots in a fixed order.
+//   * the work unit is (target tile, source chunk, image); the unit space is cut
+//     into W equal contiguous work items (fixed, so every tile's partial-sum slots
+//     and every summation order are fixed), which the resident CTAs take in order
+//     from a device counter;
+//   * a CTA stages a source chunk in shared memory once (bulk copies on an
+//     mbarrier) and applies every image to it; the image shift is folded into the
+//     targets in registers;
+//   * a CTA writes each item's per-tile partial sums to the item's slot of a
+//     partial buffer, and a reduction kernel adds the slots in a fixed order.
 //
 // FP32C: coordinates are float32 offsets from a float64 origin per group of
 // 128 consecutive (Morton-sorted) points; the offset between a target group and
@@ -20,6 +22,9 @@
 // so close pairs keep their relative precision.  Pair arithmetic uses packed
 // f32x2 instructions on two targets at a time and MUFU rsqrt; per-unit float32
 // partial sums are folded into a float32 (hi, lo) pair by Knuth's two-sum.
+//
+// FF: the same data in float-float arithmetic (hi + lo pairs) for float64-class
+// results on the float32 pipe.
 //
 // FP64: absolute float64 coordinates; 1/sqrt(r^2) is a float32 MUFU estimate
 // refined by two Newton-Raphson steps y <- y (3 - r^2 y^2)/2 in float64.

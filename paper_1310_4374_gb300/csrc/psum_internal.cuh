@@ -280,7 +280,7 @@ struct NearSys {
 
 // A stride near n / golden ratio, coprime to n: consecutive steps land far apart in the
 // (Morton-ordered) chunk sequence, so the chunks next to a tile -- the costly float-float
-// "near" units -- spread evenly over the CTAs of the stream-K partition instead of
+// "near" units -- spread evenly over the work items instead of
 // piling up in the few whose unit ranges hold the tile's spatial neighbours.
 inline int64_t near_chunk_stride(int64_t n) {
     if (n <= 2) return 1;
@@ -366,7 +366,7 @@ struct NearPlanLaunch {
     NearSysTable tab;
 };
 
-// Stream-K partition of the systems' units over at most G_max CTAs; the partial
+// Partition of the systems' units into work items for at most G_max resident CTAs; the partial
 // buffer needs max_contrib slots per tile.  `dev_tab` is the device copy of `sys`
 // (nullptr when there is one system).
 inline NearPlanLaunch near_partition(const std::vector<NearSys>& sys, int64_t G_max, const NearSys* dev_tab,
