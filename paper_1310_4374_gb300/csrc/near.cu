@@ -171,11 +171,12 @@ __device__ __forceinline__ void pair_term(const float4* __restrict__ s_hi, int s
 template <bool kGrad>
 __device__ __forceinline__ void pair_loop_far(const float4* __restrict__ s_hi, const float2 (&nx)[2],
                                               const float2 (&ny)[2], const float2 (&nz)[2], float2 (&aphi)[2],
-                                              float2 (&agx)[2], float2 (&agy)[2], float2 (&agz)[2]) {
+                                              float2 (&agx)[2], float2 (&agy)[2], float2 (&agz)[2],
+                                              int n = kNearChunk) {
     // the potential, whose terms cancel most, goes into two interleaved partial sums
     float2 bphi[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
 #pragma unroll kFarUnroll
-    for (int s = 0; s < kNearChunk; s += 2) {
+    for (int s = 0; s < n; s += 2) {
         float2 q0[2], q1[2];
         pair_term<kGrad>(s_hi, s, nx, ny, nz, q0, agx, agy, agz);
         pair_term<kGrad>(s_hi, s + 1, nx, ny, nz, q1, agx, agy, agz);
@@ -214,9 +215,9 @@ template <bool kGrad>
 __device__ __forceinline__ void pair_loop_near(const float4* __restrict__ s_hi, const float4* __restrict__ s_lo,
                                                float2 nhx, float2 nhy, float2 nhz, float2 nlx, float2 nly,
                                                float2 nlz, float2& aphi, float2& aphi_lo, float2& agx, float2& agy,
-                                               float2& agz) {
+                                               float2& agz, int n = kNearChunk) {
 #pragma unroll 1
-    for (int s0 = 0; s0 < kNearChunk; s0 += kNearFold) {
+    for (int s0 = 0; s0 < n; s0 += kNearFold) {
         float2 blk = make_float2(0.f, 0.f);
 #pragma unroll
         for (int k = 0; k < kNearFold; ++k) {
@@ -292,9 +293,10 @@ __device__ __forceinline__ float2 ff_mul2(float2 ah, float2 al, float2 bh, float
 // phi and (kGrad) the three field sums.
 template <bool kGrad>
 __device__ __forceinline__ void pair_loop_ff(const float4* __restrict__ s_hi, const float4* __restrict__ s_lo,
-                                             const float2 (&nTh)[3], const float2 (&nTl)[3], float2 (&acc)[4][2]) {
+                                             const float2 (&nTh)[3], const float2 (&nTl)[3], float2 (&acc)[4][2],
+                                             int n = kNearChunk) {
 #pragma unroll 1
-    for (int s = 0; s < kNearChunk; ++s) {
+    for (int s = 0; s < n; ++s) {
         const float4 A = s_hi[2 * s], B = s_hi[2 * s + 1], C = s_lo[2 * s], D = s_lo[2 * s + 1];
         const float2 sh[3] = {make_float2(A.x, A.y), make_float2(A.z, A.w), make_float2(B.x, B.y)};
         const float2 sl[3] = {make_float2(C.x, C.y), make_float2(C.z, C.w), make_float2(D.x, D.y)};
@@ -368,12 +370,13 @@ __global__ void __launch_bounds__(kThreads32, kMinB) k_near32(Near32Args a) {
     __shared__ float2 s_tl[kFF ? 3 : 1][2][kThreads32];   // FF: target lo offsets
     __shared__ float2 s_acc[NQ][2][2][kThreads32];        // [quantity][pair][hi, lo]
     extern __shared__ float4 s_dyn4[];                    // [max_img][kTgt32][6] deltas, [max_img] flags,
-    float* s_delta = (float*)s_dyn4;                      // then (trimmed plans) a chunk copy with
-    int* s_near = (int*)(s_delta + 6 * kTgt32 * a.max_img);   // masked charges
+    float* s_delta = (float*)s_dyn4;                      // then (trimmed plans) the compacted
+    int* s_near = (int*)(s_delta + 6 * kTgt32 * a.max_img);   // sources of a straddling unit
     float4* s_hm = s_dyn4 + (6 * kTgt32 * a.max_img + a.max_img + 3) / 4;
 
     __shared__ int s_item;
     __shared__ int s_fail;
+    __shared__ int s_wcnt[kThreads32 / 32];
     __shared__ __align__(8) uint64_t s_bar;
     const int tid = threadIdx.x;
     int64_t item = 0;
@@ -509,21 +512,45 @@ __global__ void __launch_bounds__(kThreads32, kMinB) k_near32(Near32Args a) {
             ++u;
             continue;
         }
+        // sources the unit's pair loops run over: the staged chunk, or for a unit that
+        // straddles the ball its sources inside the ball, compacted (padded to whole blocks
+        // of 4 with far-away zero charges)
+        const float4* uhi = s_hi;
+        const float4* ulo = s_lo;
+        int un = kNearChunk;
         if (kTrim && (cls & kUnitStraddle)) {
-            // zero, for this image, the charges of the chunk's sources outside the ball; the
-            // originals wait in s_hm and go back after the pair loop
-            __syncthreads();
+            __syncthreads();                 // the previous unit is done with the compacted copy
             const double* sh = a.shifts + 3 * (Sp->shift0 + img);
             const double* xp = a.src_x + 3 * (chunk * kNearChunk + tid);
-            const float4 B = s_hi[2 * tid + 1];
-            const float4 Dl = s_lo[2 * tid + 1];
-            s_hm[tid] = B;
-            s_hm[kNearChunk + tid] = Dl;
-            if (!in_ball(xp[0], xp[1], xp[2], sh, a.Rb)) {
-                s_hi[2 * tid + 1] = make_float4(B.x, B.y, 0.f, 0.f);
-                s_lo[2 * tid + 1] = make_float4(Dl.x, Dl.y, 0.f, 0.f);
+            const bool keep = in_ball(xp[0], xp[1], xp[2], sh, a.Rb);
+            const unsigned m = __ballot_sync(0xffffffffu, keep);
+            const int lane = tid & 31, warp = tid >> 5;
+            if (lane == 0) s_wcnt[warp] = __popc(m);
+            __syncthreads();
+            int base = 0, total = 0;
+#pragma unroll
+            for (int w = 0; w < kThreads32 / 32; ++w) {
+                base += w < warp ? s_wcnt[w] : 0;
+                total += s_wcnt[w];
+            }
+            const int pos = base + __popc(m & ((1u << lane) - 1u));
+            if (keep) {
+                s_hm[2 * pos] = s_hi[2 * tid];
+                s_hm[2 * pos + 1] = s_hi[2 * tid + 1];
+                s_hm[2 * kNearChunk + 2 * pos] = s_lo[2 * tid];
+                s_hm[2 * kNearChunk + 2 * pos + 1] = s_lo[2 * tid + 1];
+            }
+            const int padded = (total + kNearFold - 1) / kNearFold * kNearFold;
+            if (tid >= total && tid < padded) {
+                s_hm[2 * tid] = make_float4(1.0e3f, 1.0e3f, 1.0e3f, 1.0e3f);
+                s_hm[2 * tid + 1] = make_float4(1.0e3f, 1.0e3f, 0.f, 0.f);
+                s_hm[2 * kNearChunk + 2 * tid] = make_float4(0.f, 0.f, 0.f, 0.f);
+                s_hm[2 * kNearChunk + 2 * tid + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
             }
             __syncthreads();
+            uhi = s_hm;
+            ulo = s_hm + 2 * kNearChunk;
+            un = padded;
         }
         if constexpr (kFF) {
             // every unit in float-float: t' = t + delta as hi + lo
@@ -543,7 +570,7 @@ __global__ void __launch_bounds__(kThreads32, kMinB) k_near32(Near32Args a) {
                 float2 acc[4][2];
 #pragma unroll
                 for (int qi = 0; qi < 4; ++qi) acc[qi][0] = acc[qi][1] = make_float2(0.f, 0.f);
-                pair_loop_ff<kGrad>(s_hi, s_lo, nTh, nTl, acc);
+                pair_loop_ff<kGrad>(uhi, ulo, nTh, nTl, acc, un);
 #pragma unroll
                 for (int qi = 0; qi < NQ; ++qi) {
                     two_sum_acc2(s_acc[qi][j][0][tid], s_acc[qi][j][1][tid], acc[qi][0]);
@@ -573,8 +600,8 @@ __global__ void __launch_bounds__(kThreads32, kMinB) k_near32(Near32Args a) {
                     nl[c] = make_float2(-(e0 + (tl.x + d0[3 + c])), -(e1 + (tl.y + d1[3 + c])));
                 }
                 float2 aphi = make_float2(0.f, 0.f), aphi_lo = aphi, agx = aphi, agy = aphi, agz = aphi;
-                pair_loop_near<kGrad>(s_hi, s_lo, nh[0], nh[1], nh[2], nl[0], nl[1], nl[2], aphi, aphi_lo, agx, agy,
-                                      agz);
+                pair_loop_near<kGrad>(uhi, ulo, nh[0], nh[1], nh[2], nl[0], nl[1], nl[2], aphi, aphi_lo, agx, agy,
+                                      agz, un);
                 two_sum_acc2(s_acc[0][j][0][tid], s_acc[0][j][1][tid], aphi);
                 s_acc[0][j][1][tid] = __fadd2_rn(s_acc[0][j][1][tid], aphi_lo);
                 if (kGrad) {
@@ -596,7 +623,7 @@ __global__ void __launch_bounds__(kThreads32, kMinB) k_near32(Near32Args a) {
             }
             float2 aphi[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
             float2 agx[2] = {aphi[0], aphi[0]}, agy[2] = {aphi[0], aphi[0]}, agz[2] = {aphi[0], aphi[0]};
-            pair_loop_far<kGrad>(s_hi, nx, ny, nz, aphi, agx, agy, agz);
+            pair_loop_far<kGrad>(uhi, nx, ny, nz, aphi, agx, agy, agz, un);
 #pragma unroll
             for (int j = 0; j < 2; ++j) {
                 two_sum_acc2(s_acc[0][j][0][tid], s_acc[0][j][1][tid], aphi[j]);
@@ -606,12 +633,6 @@ __global__ void __launch_bounds__(kThreads32, kMinB) k_near32(Near32Args a) {
                     two_sum_acc2(s_acc[3 % NQ][j][0][tid], s_acc[3 % NQ][j][1][tid], agz[j]);
                 }
             }
-        }
-        if (kTrim && (s_near[img] & kUnitStraddle)) {
-            __syncthreads();
-            s_hi[2 * tid + 1] = s_hm[tid];
-            s_lo[2 * tid + 1] = s_hm[kNearChunk + tid];
-            __syncthreads();
         }
         ++u;
     }
@@ -771,7 +792,7 @@ __global__ void k_near_reduce(const double* __restrict__ partial, int64_t n_vali
 // ---------------------------------------------------------------------------
 size_t near32_dyn_smem(int n_img, bool trimmed) {
     const size_t head = ((6 * kTgt32 * (size_t)n_img + n_img + 3) / 4) * sizeof(float4);
-    return head + (trimmed ? sizeof(float4) * 2 * kNearChunk : 0);   // saved charges (hi, lo parts)
+    return head + (trimmed ? sizeof(float4) * 4 * kNearChunk : 0);   // compacted sources (hi, lo parts)
 }
 
 cudaError_t launch_near32(bool grad, const float4* src_hi, const float4* src_lo, const double* src_org,
