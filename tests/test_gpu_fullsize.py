@@ -1,0 +1,92 @@
+"""The benchmark's full-size workloads on the GPU, checked where the oracle can follow:
+sampled outputs of the 200k-charge dipole system (forward and the exact adjoint), and the
+full 256-system batch against single-system evaluations and, for its smallest systems,
+against the oracle."""
+import numpy as np
+import pytest
+
+from oracle import psum_oracle as O
+from paper_1310_4374_gb300 import binding as B
+from paper_1310_4374_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+# The float32 path's error grows with the number of terms a target sums: each of the
+# 27 x 200k terms carries a rounding of a few float32 ulps of its own size, so the error of
+# the sum is about eps sqrt(sum of squared terms), here ~2e-4 against a potential of rms ~100
+# (dominated by each charge's partner at 0.01).  Measured against the float-float path:
+# epsilon_2(phi) 6.8e-7, 1.1e-6 and 1.9e-6 for 2e4, 6e4 and 2e5 charges, while the field
+# stays at 2.1-2.6e-7.  The float-float path holds the float64 tolerance at full size.
+TOL = {"fp32c": {"phi": 3e-6, "grad": 1e-6, "adj": 3e-6}, "ff": {"phi": 1e-10, "grad": 1e-10, "adj": 1e-9}}
+
+
+@pytest.mark.parametrize("precision", ["fp32c", "ff"])
+def test_dipole_system_forward_and_adjoint_on_sampled_charges(precision):
+    s = W.config(5)                                   # 100k tight dipoles, 200k charges
+    tol = TOL[precision]
+    pc = B.PeriodicCoulomb(s.d, s.p, s.M, precision=precision)
+    try:
+        x, q = _dev(s.x), _dev(s.q)
+        phi, g = pc(x, q)
+        dEdq, dEdx = torch.empty_like(q), torch.empty_like(x)
+        B.psum_energy_backward(pc.plan, x, q, phi, g, None, dEdq, dEdx)
+        torch.cuda.synchronize()
+    finally:
+        pc.close()
+    rng = np.random.default_rng(5)
+    k = np.sort(rng.choice(s.N, size=64, replace=False))
+    pl = O.Plan(s.d, s.p, s.M)
+    ref = pl.evaluate(s.x, s.q, targets=s.x[k], parts=True)
+    phi_s, g_s = phi.cpu().numpy()[k], g.cpu().numpy()[k]
+    assert O.relative_l2(phi_s, ref["phi"]) < tol["phi"]
+    assert O.relative_l2(g_s, ref["grad"]) < tol["grad"]
+    # the exact adjoint at the sampled charges: psi from the check points with u = (A^+)^T w
+    w = O.regular_basis(s.x / pl.R0, pl.p)[1:] @ s.q
+    Q, R, piv = pl.factors
+    import scipy.linalg
+    u = Q @ scipy.linalg.solve_triangular(R, w[piv], trans="T", lower=False)
+    psi, gpsi = O.near_sum(s.x[k], np.concatenate([pl.Yt, pl.Y]), np.concatenate([u, -u]), pl.d, pl.K)
+    dq_ref = ref["phi_near"] + 0.5 * ref["phi_far"] + 0.5 * psi
+    dx_ref = s.q[k, None] * (ref["grad_near"] + 0.5 * ref["grad_far"] + 0.5 * gpsi)
+    dq = dEdq.cpu().numpy()[k]
+    # dE/dq is defined up to a constant (the charges sum to zero): compare differences
+    assert O.relative_l2(dq - dq.mean(), dq_ref - dq_ref.mean()) < tol["adj"]
+    assert O.relative_l2(dEdx.cpu().numpy()[k], dx_ref) < tol["adj"]
+
+
+def test_full_batch_against_single_evaluations_and_the_oracle():
+    systems = W.config(4)                             # 256 systems, 1.42M charges
+    pb = B.PeriodicBatch(systems, precision="fp32c")
+    try:
+        x = _dev(np.concatenate([s.x for s in systems]))
+        q = _dev(np.concatenate([s.q for s in systems]))
+        phi, g = pb(x, q, use_graph=True)
+        phi, g = phi.cpu().numpy(), g.cpu().numpy()
+        offsets = list(pb.offsets)
+    finally:
+        pb.close()
+    rng = np.random.default_rng(8)
+    for b in rng.choice(len(systems), size=6, replace=False):
+        s = systems[b]
+        pc = B.PeriodicCoulomb(s.d, s.p, s.M, precision="fp32c", K=s.K)
+        try:
+            p1, g1 = pc(_dev(s.x), _dev(s.q))
+        finally:
+            pc.close()
+        sl = slice(offsets[b], offsets[b + 1])
+        assert O.relative_l2(phi[sl], p1.cpu().numpy()) < 1e-7, s.name
+        assert O.relative_l2(g[sl], g1.cpu().numpy()) < 1e-7, s.name
+    small = sorted(range(len(systems)), key=lambda b: systems[b].N)[:2]
+    small.append(next(b for b in range(len(systems)) if tuple(systems[b].K) != (1, 1, 1)))
+    for b in small:
+        s = systems[b]
+        ref = O.periodic_sum(s.x, s.q, s.d, s.p, s.M, K=s.K)
+        sl = slice(offsets[b], offsets[b + 1])
+        assert O.relative_l2(phi[sl], ref["phi"]) < 1e-6, s.name
+        assert O.relative_l2(g[sl], ref["grad"]) < 1e-6, s.name
