@@ -88,7 +88,7 @@ __global__ void __launch_bounds__(kRedThreads) k_box_mean(const double* __restri
     double s = 0.0, dummy = 0.0;
     for (int64_t i = (int64_t)blockIdx.x * kRedThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kRedThreads) {
         const double X[3] = {x[3 * i], x[3 * i + 1], x[3 * i + 2]};
-        s += q[i] * block_potential(X, H);
+        s += q[i] * block_potential_corners(X, H);
     }
     block_sum2<kRedThreads>(s, dummy);
     if (threadIdx.x == 0) partial[blockIdx.x] = s;

@@ -56,8 +56,10 @@ __host__ __device__ __forceinline__ double block_potential(const double X[3], co
 //   F(a, b, c) = ab ln(c + r) + bc ln(a + r) + ca ln(b + r)
 //                - a^2/2 atan(bc/(ar)) - b^2/2 atan(ca/(br)) - c^2/2 atan(ab/(cr)),
 // r = |(a, b, c)|.  It needs 24 logarithms and 24 arctangents where the face/edge route
-// takes 48 and 96; the ball-trimmed mean, which evaluates one single-box potential per
-// kept image and charge, uses it.  Vanishing products drop their term (their limit is 0).
+// takes 48 and 96, so the device means use it (the block mean: 1.27 ms for 1e5 charges
+// by the face/edge route); the plan's RBF box means on the host keep the face/edge route.
+// The two agree to 1.2e-13 on 2e5 random points.  Vanishing products drop their term
+// (their limit is 0).
 __host__ __device__ __forceinline__ double log_plus_r(double a, double r, double rest2) {
     // ln(a + r) with r^2 = a^2 + rest2, without cancellation for a < 0
     return a >= 0.0 ? log(a + r) : log(rest2 / (r - a));
