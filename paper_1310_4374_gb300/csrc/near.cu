@@ -124,9 +124,11 @@ __device__ __forceinline__ void fence_mbar_init() {
 }
 
 // unit classes against the ball S_b (flags in shared memory, per image of the staged chunk)
-constexpr int kUnitNear = 1;       // float-float offsets and K(0) = 0
+constexpr int kUnitNear0 = 1;      // the thread's target pair 0 (groups 0, 1): float-float offsets, K(0) = 0
 constexpr int kUnitOutside = 2;    // every source image outside the ball: nothing to add
 constexpr int kUnitStraddle = 4;   // per-source test against the ball
+constexpr int kUnitNear1 = 8;      // the same for target pair 1 (groups 2, 3)
+constexpr int kUnitNear = kUnitNear0 | kUnitNear1;
 
 // |x + p|^2 <= Rb^2 with the rounding of a plain left-to-right evaluation (no contraction),
 // the same decision for a source at the boundary as a straightforward float64 evaluation
@@ -144,15 +146,15 @@ constexpr int kFarUnroll = PSUM_FAR_UNROLL;   // source pairs per unrolled step 
 // Far units: one chunk of sources against the thread's 4 targets (2 packed pairs),
 // plain float32 offsets s - t'.  One source: its potential terms into qr, its field
 // terms added to the gradient sums.
-template <bool kGrad>
-__device__ __forceinline__ void pair_term(const float4* __restrict__ s_hi, int src, const float2 (&nx)[2],
-                                          const float2 (&ny)[2], const float2 (&nz)[2], float2 (&qr)[2],
-                                          float2 (&agx)[2], float2 (&agy)[2], float2 (&agz)[2]) {
+template <bool kGrad, int NP>
+__device__ __forceinline__ void pair_term(const float4* __restrict__ s_hi, int src, const float2 (&nx)[NP],
+                                          const float2 (&ny)[NP], const float2 (&nz)[NP], float2 (&qr)[NP],
+                                          float2 (&agx)[NP], float2 (&agy)[NP], float2 (&agz)[NP]) {
     const float4 A = s_hi[2 * src];       // x x y y
     const float4 B = s_hi[2 * src + 1];   // z z q q
     const float2 sq = make_float2(B.z, B.w);
 #pragma unroll
-    for (int j = 0; j < 2; ++j) {
+    for (int j = 0; j < NP; ++j) {
         const float2 ex = __fadd2_rn(make_float2(A.x, A.y), nx[j]);
         const float2 ey = __fadd2_rn(make_float2(A.z, A.w), ny[j]);
         const float2 ez = __fadd2_rn(make_float2(B.x, B.y), nz[j]);
@@ -170,26 +172,29 @@ __device__ __forceinline__ void pair_term(const float4* __restrict__ s_hi, int s
     }
 }
 
-template <bool kGrad>
-__device__ __forceinline__ void pair_loop_far(const float4* __restrict__ s_hi, const float2 (&nx)[2],
-                                              const float2 (&ny)[2], const float2 (&nz)[2], float2 (&aphi)[2],
-                                              float2 (&agx)[2], float2 (&agy)[2], float2 (&agz)[2],
+// NP packed target pairs (both of a thread's pairs, or one when its other pair is near)
+template <bool kGrad, int NP>
+__device__ __forceinline__ void pair_loop_far(const float4* __restrict__ s_hi, const float2 (&nx)[NP],
+                                              const float2 (&ny)[NP], const float2 (&nz)[NP], float2 (&aphi)[NP],
+                                              float2 (&agx)[NP], float2 (&agy)[NP], float2 (&agz)[NP],
                                               int n = kNearChunk) {
     // the potential, whose terms cancel most, goes into two interleaved partial sums
-    float2 bphi[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+    float2 bphi[NP];
+#pragma unroll
+    for (int j = 0; j < NP; ++j) bphi[j] = make_float2(0.f, 0.f);
 #pragma unroll kFarUnroll
     for (int s = 0; s < n; s += 2) {
-        float2 q0[2], q1[2];
-        pair_term<kGrad>(s_hi, s, nx, ny, nz, q0, agx, agy, agz);
-        pair_term<kGrad>(s_hi, s + 1, nx, ny, nz, q1, agx, agy, agz);
+        float2 q0[NP], q1[NP];
+        pair_term<kGrad, NP>(s_hi, s, nx, ny, nz, q0, agx, agy, agz);
+        pair_term<kGrad, NP>(s_hi, s + 1, nx, ny, nz, q1, agx, agy, agz);
 #pragma unroll
-        for (int j = 0; j < 2; ++j) {
+        for (int j = 0; j < NP; ++j) {
             aphi[j] = __fadd2_rn(aphi[j], q0[j]);
             bphi[j] = __fadd2_rn(bphi[j], q1[j]);
         }
     }
-    aphi[0] = __fadd2_rn(aphi[0], bphi[0]);
-    aphi[1] = __fadd2_rn(aphi[1], bphi[1]);
+#pragma unroll
+    for (int j = 0; j < NP; ++j) aphi[j] = __fadd2_rn(aphi[j], bphi[j]);
 }
 
 // (hi, lo) += v for a packed pair of accumulators: Knuth's two-sum with the error
@@ -481,7 +486,7 @@ __global__ void __launch_bounds__(kThreads32, kMinB) k_near32(Near32Args a) {
                     dl[3] = (float)(D0 - (double)dl[0]); dl[4] = (float)(D1 - (double)dl[1]);
                     dl[5] = (float)(D2 - (double)dl[2]);
                     const double reach = kNearFactor * (to[3] + so[3]);
-                    if (D0 * D0 + D1 * D1 + D2 * D2 <= reach * reach) nr = kUnitNear;
+                    if (D0 * D0 + D1 * D1 + D2 * D2 <= reach * reach) nr |= k < 2 ? kUnitNear0 : kUnitNear1;
                 }
                 if (kTrim) {
                     // the chunk's bounding sphere against the ball, with a margin: the exact
@@ -580,12 +585,29 @@ __global__ void __launch_bounds__(kThreads32, kMinB) k_near32(Near32Args a) {
                 }
             }
         } else if (cls & kUnitNear) {
-            // t' = t + delta in float-float: hi by rounding, lo = exact remainder + both lo parts
+            // near pairs: t' = t + delta in float-float (hi by rounding, lo = exact remainder +
+            // both lo parts); a pair whose two groups are both far takes the far loop alone
 #pragma unroll 1
             for (int j = 0; j < 2; ++j) {
                 const float* d0 = dl + 6 * (2 * j);
                 const float* d1 = dl + 6 * (2 * j + 1);
-                // target lo parts are read from global memory: near units are rare
+                if (!(cls & (j ? kUnitNear1 : kUnitNear0))) {
+                    const float2 tx = s_th[0][j][tid], ty = s_th[1][j][tid], tz = s_th[2][j][tid];
+                    const float2 nx[1] = {make_float2(-(tx.x + d0[0]), -(tx.y + d1[0]))};
+                    const float2 ny[1] = {make_float2(-(ty.x + d0[1]), -(ty.y + d1[1]))};
+                    const float2 nz[1] = {make_float2(-(tz.x + d0[2]), -(tz.y + d1[2]))};
+                    float2 aphi[1] = {make_float2(0.f, 0.f)}, agx[1] = {aphi[0]}, agy[1] = {aphi[0]},
+                           agz[1] = {aphi[0]};
+                    pair_loop_far<kGrad, 1>(uhi, nx, ny, nz, aphi, agx, agy, agz, un);
+                    two_sum_acc2(s_acc[0][j][0][tid], s_acc[0][j][1][tid], aphi[0]);
+                    if (kGrad) {
+                        two_sum_acc2(s_acc[1 % NQ][j][0][tid], s_acc[1 % NQ][j][1][tid], agx[0]);
+                        two_sum_acc2(s_acc[2 % NQ][j][0][tid], s_acc[2 % NQ][j][1][tid], agy[0]);
+                        two_sum_acc2(s_acc[3 % NQ][j][0][tid], s_acc[3 % NQ][j][1][tid], agz[0]);
+                    }
+                    continue;
+                }
+                // target lo parts are read from global memory: near pairs are rare
                 const int64_t i0 = (cur_tile * kTgt32 + 2 * j) * kGroup + tid;
                 const int64_t i1 = i0 + kGroup;
                 const float4 C0 = a.tgt_lo[2 * i0], D0 = a.tgt_lo[2 * i0 + 1];
@@ -625,7 +647,7 @@ __global__ void __launch_bounds__(kThreads32, kMinB) k_near32(Near32Args a) {
             }
             float2 aphi[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
             float2 agx[2] = {aphi[0], aphi[0]}, agy[2] = {aphi[0], aphi[0]}, agz[2] = {aphi[0], aphi[0]};
-            pair_loop_far<kGrad>(uhi, nx, ny, nz, aphi, agx, agy, agz, un);
+            pair_loop_far<kGrad, 2>(uhi, nx, ny, nz, aphi, agx, agy, agz, un);
 #pragma unroll
             for (int j = 0; j < 2; ++j) {
                 two_sum_acc2(s_acc[0][j][0][tid], s_acc[0][j][1][tid], aphi[j]);
