@@ -146,6 +146,16 @@ int psum_plan_create_ex(const psum_opts *o, psum_plan_t *out);
 int psum_eval(psum_plan_t plan, int64_t N, const double *x, const double *q,
               double *phi, double *grad, void *stream);
 
+/* psum_eval through a CUDA graph: the first call for a given (N, x, q, phi, grad) captures
+   the whole evaluation (about 25 kernels and memsets) on an internal stream and later calls
+   with the same arguments replay it on `stream`, which removes the per-kernel launch cost
+   (it dominates below ~5000 charges).  The inputs may change between replays in the same
+   buffers.  Results, status reporting (psum_sync) and asynchrony are those of psum_eval;
+   psum_profile timings are not recorded by replays.  The first call of a size allocates
+   scratch, so it must not be made inside a stream capture of the caller. */
+int psum_eval_graph(psum_plan_t plan, int64_t N, const double* x, const double* q, double* phi,
+                    double* grad, void* stream);
+
 /* Algorithm "get" at separate evaluation points (the general problem of Sec. 1: the
    potential and its gradient at points y of the box due to the N charges; psum_eval is the
    case Y0 = X0 of Remark 1).

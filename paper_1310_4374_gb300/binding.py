@@ -92,6 +92,7 @@ def load(build_if_needed: bool = True):
     lib.psum_plan_create_ex.argtypes = [ctypes.POINTER(psum_opts), ctypes.POINTER(_vp)]
     lib.psum_eval.argtypes = [_vp, ctypes.c_int64, _vp, _vp, _vp, _vp, _vp]
     lib.psum_debug_inject_timeout.argtypes = [_vp, ctypes.c_int]
+    lib.psum_eval_graph.argtypes = [_vp, ctypes.c_int64, _vp, _vp, _vp, _vp, _vp]
     lib.psum_eval_points.argtypes = [_vp, ctypes.c_int64, _vp, _vp, ctypes.c_int64, _vp, _vp, _vp, _vp]
     lib.psum_eval_host.argtypes = [_vp, ctypes.c_int64, _vp, _vp, _vp, _vp, _vp]
     lib.psum_eval_noalloc.argtypes = [_vp, ctypes.c_int64, _vp, _vp, _vp, _vp, _vp]
@@ -118,7 +119,7 @@ def load(build_if_needed: bool = True):
     for name in ("psum_plan_create", "psum_plan_create_ex", "psum_eval", "psum_eval_host", "psum_eval_noalloc",
                  "psum_sync",
                  "psum_get_coeffs", "psum_plan_info", "psum_profile", "psum_last_timings", "psum_launch_count",
-                 "psum_energy", "psum_energy_backward", "psum_eval_points", "psum_debug_inject_timeout", "psum_batch_create", "psum_batch_eval",
+                 "psum_energy", "psum_energy_backward", "psum_eval_points", "psum_debug_inject_timeout", "psum_eval_graph", "psum_batch_create", "psum_batch_eval",
                  "psum_batch_sync", "psum_batch_get_coeffs", "psum_batch_get_info"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
@@ -195,6 +196,20 @@ def psum_eval(plan, x, q, phi, grad=None, stream=None, check: bool = False) -> i
     _check(s, "psum_eval")
     if check:
         _check(psum_sync(plan, st), "psum_eval (device)")
+    return s
+
+
+def psum_eval_graph(plan, x, q, phi, grad=None, stream=None, check: bool = False) -> int:
+    """psum_eval replayed from a CUDA graph captured on first use for these tensors."""
+    for t in (x, q, phi) + ((grad,) if grad is not None else ()):
+        if not (t.is_cuda and t.is_contiguous()):
+            raise ValueError("psum_eval_graph takes contiguous CUDA tensors")
+    st = _stream_ptr(stream)
+    s = load().psum_eval_graph(plan, int(q.numel()), x.data_ptr(), q.data_ptr(), phi.data_ptr(),
+                               grad.data_ptr() if grad is not None else None, st)
+    _check(s, "psum_eval_graph")
+    if check:
+        _check(psum_sync(plan, st), "psum_eval_graph (device)")
     return s
 
 

@@ -149,7 +149,7 @@ size_t layout(Plan& pl, int64_t N, char* base, Layout& L, bool backward = false,
     L.phi_n = b.take<double>((size_t)L.n_pts);
     L.grad_n = b.take<double>(3 * (size_t)L.n_pts);
     L.nblk_val = reduce_blocks(N, pl.num_sms);
-    L.nblk_mean = reduce_blocks(N, pl.num_sms);
+    L.nblk_mean = mean_blocks(N, pl.num_sms);
     L.val_part = b.take<double>(2 * (size_t)L.nblk_val);
     L.mean_part = b.take<double>((size_t)L.nblk_mean);
     L.f = b.take<double>((size_t)pl.opt.M);
@@ -246,7 +246,7 @@ int queue_forward(psum_plan_s* h, int64_t N, const double* x, const double* q, d
         TRY(launch_morton_sort(x, N, o.d, L.ka, L.va, L.kb, L.vb, L.hist, st));
         perm = (const int*)L.va;
         TRY(launch_pack32(x, q, L.va, N, L.n_src_groups, L.pk32, L.pk32lo, L.org, st, L.xs));
-        h->launches += 1 + 4 * 3 + 1;
+        h->launches += morton_sort_launches(N) + 1;
     } else {
         TRY(launch_pack64(x, q, N, L.n_src_pts, L.pk64, st));
         h->launches += 1;
@@ -261,7 +261,7 @@ int queue_forward(psum_plan_s* h, int64_t N, const double* x, const double* q, d
             TRY(launch_morton_sort(y, T, o.d, L.tka, L.tva, L.tkb, L.tvb, L.thist, st));
             eperm = (const int*)L.tva;
             TRY(launch_pack32(y, nullptr, L.tva, T, L.n_tiles * kTgt32, L.tpk32, L.tpk32lo, L.torg, st));
-            h->launches += 1 + 4 * 3 + 1;
+            h->launches += morton_sort_launches(T) + 1;
         } else {
             TRY(launch_pack64(y, nullptr, T, L.n_pts, L.tpk64, st));
             h->launches += 1;
@@ -364,7 +364,7 @@ int backward_device(psum_plan_s* h, int64_t N, const double* x, const double* q,
         TRY(launch_morton_sort(x, N, o.d, L.ka, L.va, L.kb, L.vb, L.hist, st));
         perm = (const int*)L.va;
         TRY(launch_pack32(x, q, L.va, N, L.n_src_groups, L.pk32, L.pk32lo, L.org, st));
-        h->launches += 1 + 4 * 3 + 1;
+        h->launches += morton_sort_launches(N) + 1;
     } else {
         TRY(launch_pack64(x, q, N, L.n_src_pts, L.pk64, st));
         h->launches += 1;
@@ -492,6 +492,55 @@ int psum_eval(psum_plan_t h, int64_t N, const double* x, const double* q, double
     if (!h || N < 1 || N > (int64_t)1 << 30 || !x || !q || !phi) return PSUM_ERR_ARG;
     DeviceGuard g(h->pl.device);
     return eval_device(h, N, x, q, phi, grad, (cudaStream_t)stream);
+}
+
+int psum_eval_graph(psum_plan_t h, int64_t N, const double* x, const double* q, double* phi, double* grad,
+                    void* stream) {
+    if (!h || N < 1 || N > (int64_t)1 << 30 || !x || !q || !phi) return PSUM_ERR_ARG;
+    DeviceGuard g(h->pl.device);
+    Plan& pl = h->pl;
+    cudaStream_t st = (cudaStream_t)stream;
+    Layout L;
+    int rs = ensure_scratch(pl, layout(pl, N, nullptr, L));     // outside any capture
+    if (rs != PSUM_OK) return rs;
+    const void* key[6] = {x, q, phi, grad, pl.scratch.ptr, (const void*)(intptr_t)h->inject_timeout};
+    bool same = h->gexec != nullptr && h->gN == N;
+    for (int k = 0; k < 6 && same; ++k) same = h->gkey[k] == key[k];
+    if (!same) {
+        if (h->gexec) {
+            cudaGraphExecDestroy(h->gexec);
+            h->gexec = nullptr;
+        }
+        if (!h->cap) TRY(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking));
+        layout(pl, N, (char*)pl.scratch.ptr, L);
+        const bool prof = h->profile;
+        h->profile = false;                       // no timing events inside the graph
+        const int64_t before = h->launches;
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) {
+            h->profile = prof;
+            return cuda_status(e);
+        }
+        const int s = queue_forward(h, N, x, q, phi, grad, L, h->cap);
+        e = cudaStreamEndCapture(h->cap, &graph);
+        h->profile = prof;
+        h->glaunches = h->launches - before;
+        h->launches = before;                     // capturing queues nothing on the device
+        if (s != PSUM_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return s;
+        }
+        TRY(e);
+        e = cudaGraphInstantiate(&h->gexec, graph, 0);
+        cudaGraphDestroy(graph);
+        TRY(e);
+        for (int k = 0; k < 6; ++k) h->gkey[k] = key[k];
+        h->gN = N;
+    }
+    TRY(cudaGraphLaunch(h->gexec, st));
+    h->launches += h->glaunches;
+    return PSUM_OK;
 }
 
 int psum_eval_points(psum_plan_t h, int64_t N, const double* x, const double* q, int64_t T, const double* y,
@@ -630,6 +679,8 @@ void psum_destroy(psum_plan_t h) {
         cudaDeviceSynchronize();
         for (auto& e : h->ev)
             if (e) cudaEventDestroy(e);
+        if (h->gexec) cudaGraphExecDestroy(h->gexec);
+        if (h->cap) cudaStreamDestroy(h->cap);
         free_plan_device(h->pl);
     }
     delete h;

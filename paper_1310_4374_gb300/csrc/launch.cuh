@@ -19,6 +19,7 @@ constexpr int kNear32Variants = 2;
 int near64_occupancy_ctas();
 // sort.cu
 int sort_blocks(int64_t n);
+int morton_sort_launches(int64_t n);   // kernels launch_morton_sort queues for n points
 cudaError_t launch_morton_sort(const double* x, int64_t n, const double d[3], uint32_t* ka, uint32_t* va,
                                uint32_t* kb, uint32_t* vb, uint32_t* hist, cudaStream_t st);
 cudaError_t launch_pack32(const double* x, const double* q, const uint32_t* perm, int64_t n, int64_t n_groups,
@@ -37,6 +38,7 @@ cudaError_t launch_validate_points(const double* y, int64_t n, const double d[3]
                                    cudaStream_t st);
 cudaError_t launch_validate(const double* x, const double* q, int64_t n, const double d[3], double* partial,
                             int nblk, int* status, cudaStream_t st);
+int mean_blocks(int64_t n, int num_sms);   // grid of launch_box_mean for n charges
 cudaError_t launch_box_mean(const double* x, const double* q, int64_t n, const double H[3], double* partial,
                             int nblk, cudaStream_t st);
 // far field of the RBF basis (Eq. 5): phi = phi_near + C_1 + sum_t C_{t+1} / |y - x_t|, float64

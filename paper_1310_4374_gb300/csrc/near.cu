@@ -778,16 +778,23 @@ __global__ void __launch_bounds__(kThreads64) k_near64(Near64Args a) {
 // Reduction of the partial slots (fixed order: slot 0, 1, ...) for packed target
 // index i < n_valid (tile = i / tile_size is the partial-buffer row).
 // ---------------------------------------------------------------------------
-__global__ void k_near_reduce(const double* __restrict__ partial, int64_t n_valid, int tile_size, int nq,
-                              NearSysTable tab, int64_t U, int64_t W, int max_contrib,
-                              double* __restrict__ out_phi, double* __restrict__ out_grad) {
-    // one thread per (target, quantity); the slots are read four at a time into four
-    // partial sums combined in a fixed order, so the result does not depend on timing
-    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= n_valid * nq) return;
-    const int qi = (int)(k % nq);
-    const int64_t i = k / nq;
-    const int64_t tile = i / tile_size;
+// A block sums the slots of 32 consecutive targets (one per lane) and one quantity: its 8
+// warps take every 8th slot, and the 8 warp sums are added in a fixed order in shared
+// memory, so the result does not depend on timing.  Tiles never mix within a block (the
+// tile sizes are multiples of 32).
+constexpr int kReduceWarps = 8;
+
+__global__ void __launch_bounds__(32 * kReduceWarps) k_near_reduce(const double* __restrict__ partial,
+                                                                   int64_t n_valid, int tile_size, int nq,
+                                                                   NearSysTable tab, int64_t U, int64_t W,
+                                                                   int max_contrib, double* __restrict__ out_phi,
+                                                                   double* __restrict__ out_grad) {
+    __shared__ double s_part[kReduceWarps][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int qi = blockIdx.y;
+    const int64_t i0 = (int64_t)blockIdx.x * 32;
+    const int64_t i = i0 + lane;
+    const int64_t tile = i0 / tile_size;
     const int loc = (int)(i - tile * tile_size);
     const NearSys S = near_sys_get(tab, near_sys_by_tile(tab, tile));
     const int64_t upt = S.n_chunks * S.n_img;
@@ -795,20 +802,20 @@ __global__ void k_near_reduce(const double* __restrict__ partial, int64_t n_vali
     const int n = (int)(sk_owner(first + upt - 1, U, W) - sk_owner(first, U, W) + 1);
     const double* src = partial + (tile * max_contrib * nq + qi) * (int64_t)tile_size + loc;
     const int64_t stride = (int64_t)nq * tile_size;
-    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-    int sl = 0;
-    for (; sl + 4 <= n; sl += 4) {
-        s0 += src[(sl + 0) * stride];
-        s1 += src[(sl + 1) * stride];
-        s2 += src[(sl + 2) * stride];
-        s3 += src[(sl + 3) * stride];
+    double acc = 0.0;
+    if (i < n_valid)
+        for (int sl = warp; sl < n; sl += kReduceWarps) acc += src[sl * stride];
+    s_part[warp][lane] = acc;
+    __syncthreads();
+    if (warp == 0 && i < n_valid) {
+        double v = s_part[0][lane];
+#pragma unroll
+        for (int w = 1; w < kReduceWarps; ++w) v += s_part[w][lane];
+        if (qi == 0)
+            out_phi[i] = v;
+        else if (out_grad)
+            out_grad[3 * i + qi - 1] = v;
     }
-    for (; sl < n; ++sl) s0 += src[sl * stride];
-    const double v = (s0 + s1) + (s2 + s3);
-    if (qi == 0)
-        out_phi[i] = v;
-    else if (out_grad)
-        out_grad[3 * i + qi - 1] = v;
 }
 
 // ---------------------------------------------------------------------------
@@ -881,9 +888,8 @@ cudaError_t launch_near64(bool grad, const double4_32a* src, const double4_32a* 
 cudaError_t launch_near_reduce(const double* partial, int64_t n_valid, int tile_size, int nq,
                                const NearPlanLaunch& L, double* out_phi, double* out_grad, cudaStream_t st) {
     if (n_valid <= 0) return cudaSuccess;
-    const int bs = 256;
-    const unsigned nb = (unsigned)((n_valid * nq + bs - 1) / bs);
-    k_near_reduce<<<nb, bs, 0, st>>>(partial, n_valid, tile_size, nq, L.tab, L.U, L.W, L.max_contrib, out_phi,
+    const dim3 grid((unsigned)((n_valid + 31) / 32), (unsigned)nq);
+    k_near_reduce<<<grid, 32 * kReduceWarps, 0, st>>>(partial, n_valid, tile_size, nq, L.tab, L.U, L.W, L.max_contrib, out_phi,
                                      out_grad);
     return cudaGetLastError();
 }

@@ -352,6 +352,7 @@ constexpr int kItemsPerCta = PSUM_ITEMS_PER_CTA;
 #define PSUM_CHECK_ITEMS_PER_CTA 2
 #endif
 constexpr int kCheckItemsPerCta = PSUM_CHECK_ITEMS_PER_CTA;
+constexpr int64_t kMinUnitsPerItem = 32;
 
 struct NearPlanLaunch {
     int64_t U, G;
@@ -382,7 +383,12 @@ inline NearPlanLaunch near_partition(const std::vector<NearSys>& sys, int64_t G_
     }
     L.G = L.U < G_max ? L.U : G_max;
     if (L.G < 1) L.G = 1;
+    // up to items_per_cta items per CTA, but items of at least kMinUnitsPerItem units where
+    // the launch is small (every item adds a partial-sum slot to each tile it touches), and
+    // at least one item per CTA
     L.W = L.G * (items_per_cta < 1 ? 1 : items_per_cta);
+    if (L.W > L.U / kMinUnitsPerItem) L.W = L.U / kMinUnitsPerItem;
+    if (L.W < L.G) L.W = L.G;
     if (L.W > L.U) L.W = L.U < 1 ? 1 : L.U;
     int mc = 1;
     for (const NearSys& s : sys) {
@@ -418,4 +424,11 @@ struct psum_plan_s {
     bool profile = false;
     bool inject_timeout = false;  // test hook: the charge pair kernel's copy waits run out
     cudaEvent_t ev[6] = {};
+    // psum_eval_graph: one evaluation captured into a CUDA graph, replayed while the
+    // arguments and the scratch buffer stay the same
+    cudaStream_t cap = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    const void* gkey[6] = {};
+    int64_t gN = 0;
+    int64_t glaunches = 0;        // kernels one replay runs
 };

@@ -132,7 +132,9 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(const uint32_t* _
 // Padding points (s >= n) get q = 0 and a far-away position.
 // With a group table (batches) group g covers the sorted positions
 // [grp_start[g], grp_start[g] + grp_count[g]); without one, [128 g, min(128 (g+1), n)).
-__global__ void k_pack32(const double* __restrict__ x, const double* __restrict__ q,
+constexpr int kPackWarps = 4;   // warps (groups) per block of k_pack32
+
+__global__ void __launch_bounds__(32 * kPackWarps) k_pack32(const double* __restrict__ x, const double* __restrict__ q,
                          const uint32_t* __restrict__ perm, int64_t n, int64_t n_groups,
                          const int64_t* __restrict__ grp_start, const int* __restrict__ grp_count,
                          float4* __restrict__ pk_hi, float4* __restrict__ pk_lo, double* __restrict__ org,
@@ -172,19 +174,28 @@ __global__ void k_pack32(const double* __restrict__ x, const double* __restrict_
     // each charge absorbs the error carried so far, so the group's float32 charges sum to
     // its float64 total up to one rounding; a non-neutral rounding residue would add the
     // potential of a net charge over all images to every target.
-    float fqk[per];
-    double carry = 0.0;
-    for (int k = 0; k < per; ++k)
-        for (int l = 0; l < 32; ++l) {
-            float v = 0.f;
-            double nc = carry;
-            if (lane == l && ok[k]) {
-                v = (float)(pq[k] - carry);
-                nc = carry + ((double)v - pq[k]);
-                fqk[k] = v;
-            }
-            carry = __shfl_sync(0xffffffffu, nc, l);
+    // The recurrence is sequential: one lane runs it over the group's charges, staged in
+    // shared memory (a chain of float64 operations, no shuffles).
+    __shared__ double s_q[kPackWarps][kNearChunk];
+    __shared__ float s_f[kPackWarps][kNearChunk];
+    const int w = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < per; ++k) s_q[w][k * 32 + lane] = ok[k] ? pq[k] : 0.0;
+    __syncwarp();
+    if (lane == 0) {
+        const int cnt = (int)(s1 - s0);
+        double carry = 0.0;
+        for (int m = 0; m < cnt; ++m) {
+            const double qm = s_q[w][m];
+            const float v = (float)(qm - carry);
+            carry += (double)v - qm;
+            s_f[w][m] = v;
         }
+    }
+    __syncwarp();
+    float fqk[per];
+#pragma unroll
+    for (int k = 0; k < per; ++k) fqk[k] = s_f[w][k * 32 + lane];
     double r2max = 0.0;
 #pragma unroll
     for (int k = 0; k < per; ++k) {
@@ -251,8 +262,9 @@ cudaError_t launch_pack64_groups(const double* x, const double* q, int64_t n_pts
 // ---------------------------------------------------------------------------
 int sort_blocks(int64_t n) { return (int)((n + kSortTile - 1) / kSortTile); }
 
-// Stable LSD radix sort of (key, value) pairs, 8 bits per pass over `passes` passes
-// (an even number, so the result ends in (ka, va)); (kb, vb) and hist are scratch.
+// Stable LSD radix sort of (key, value) pairs, 8 bits per pass over `passes` passes,
+// ping-ponging (ka, va) -> (kb, vb) -> ...: the result ends in (ka, va) after an even
+// number of passes and in (kb, vb) after an odd one; hist is scratch.
 cudaError_t launch_radix_sort(uint32_t* ka, uint32_t* va, uint32_t* kb, uint32_t* vb, uint32_t* hist, int64_t n,
                               int passes, cudaStream_t st) {
     const int nblk = sort_blocks(n);
@@ -268,18 +280,61 @@ cudaError_t launch_radix_sort(uint32_t* ka, uint32_t* va, uint32_t* kb, uint32_t
     return cudaGetLastError();
 }
 
-// keys/vals ping-pong in (ka, va) <-> (kb, vb); result in (ka, va) after an even number of passes.
+// Small inputs in one block: the (key, index) pairs as 64-bit words in shared memory, a
+// bitonic sort, the same order as the stable radix sort (ties broken by the index), in one
+// launch instead of nine.
+constexpr int kSmallSort = 4096;
+constexpr int kSmallSortThreads = 1024;
+
+__global__ void __launch_bounds__(kSmallSortThreads) k_sort_small(const uint32_t* __restrict__ kin,
+                                                                  const uint32_t* __restrict__ vin, int n,
+                                                                  uint32_t* __restrict__ kout,
+                                                                  uint32_t* __restrict__ vout) {
+    __shared__ unsigned long long w[kSmallSort];
+    int m = 1;
+    while (m < n) m <<= 1;
+    for (int i = threadIdx.x; i < m; i += kSmallSortThreads)
+        w[i] = i < n ? ((unsigned long long)kin[i] << 32) | vin[i] : ~0ull;
+    __syncthreads();
+    for (int k = 2; k <= m; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < m; i += kSmallSortThreads) {
+                const int p = i ^ j;
+                if (p > i) {
+                    const unsigned long long a = w[i], b = w[p];
+                    const bool up = (i & k) == 0;
+                    if ((a > b) == up) {
+                        w[i] = b;
+                        w[p] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    for (int i = threadIdx.x; i < n; i += kSmallSortThreads) {
+        kout[i] = (uint32_t)(w[i] >> 32);
+        vout[i] = (uint32_t)(w[i] & 0xffffffffu);
+    }
+}
+
+int morton_sort_launches(int64_t n) { return n <= kSmallSort ? 2 : 1 + 3 * 3; }
+
+// Morton order of the points: 24-bit keys, written to (kb, vb) and sorted (3 radix passes,
+// or one block for small inputs) so that the sorted keys and the permutation end in (ka, va).
 cudaError_t launch_morton_sort(const double* x, int64_t n, const double d[3], uint32_t* ka, uint32_t* va,
                                uint32_t* kb, uint32_t* vb, uint32_t* hist, cudaStream_t st) {
     const int bs = 256;
-    k_morton<<<(unsigned)((n + bs - 1) / bs), bs, 0, st>>>(x, n, d[0], d[1], d[2], ka, va);
-    // 24-bit keys need 3 passes; a 4th (empty digit) keeps the result in (ka, va)
-    return launch_radix_sort(ka, va, kb, vb, hist, n, 4, st);
+    k_morton<<<(unsigned)((n + bs - 1) / bs), bs, 0, st>>>(x, n, d[0], d[1], d[2], kb, vb);
+    if (n <= kSmallSort) {
+        k_sort_small<<<1, kSmallSortThreads, 0, st>>>(kb, vb, (int)n, ka, va);
+        return cudaGetLastError();
+    }
+    return launch_radix_sort(kb, vb, ka, va, hist, n, 3, st);
 }
 
 cudaError_t launch_pack32(const double* x, const double* q, const uint32_t* perm, int64_t n, int64_t n_groups,
                           float4* pk_hi, float4* pk_lo, double* org, cudaStream_t st, double* xs) {
-    const int warps = 4;
+    const int warps = kPackWarps;
     k_pack32<<<(unsigned)((n_groups + warps - 1) / warps), 32 * warps, 0, st>>>(x, q, perm, n, n_groups, nullptr,
                                                                                   nullptr, pk_hi, pk_lo, org, xs);
     return cudaGetLastError();
@@ -288,7 +343,7 @@ cudaError_t launch_pack32(const double* x, const double* q, const uint32_t* perm
 cudaError_t launch_pack32_groups(const double* x, const double* q, const uint32_t* perm, int64_t n_groups,
                                  const int64_t* grp_start, const int* grp_count, float4* pk_hi, float4* pk_lo,
                                  double* org, cudaStream_t st) {
-    const int warps = 4;
+    const int warps = kPackWarps;
     k_pack32<<<(unsigned)((n_groups + warps - 1) / warps), 32 * warps, 0, st>>>(x, q, perm, 0, n_groups, grp_start,
                                                                                   grp_count, pk_hi, pk_lo, org,
                                                                                   nullptr);
