@@ -680,11 +680,13 @@ struct Near64Args {
 };
 
 __device__ __forceinline__ double rsqrt_f64(double r2) {
-    // MUFU estimate (about 23 bits), then two Newton-Raphson steps for 1/sqrt(r2)
-    double y = (double)rsqrt_mufu((float)r2);
-    y = y * fma(-0.5 * r2, y * y, 1.5);
-    y = y * fma(-0.5 * r2, y * y, 1.5);
-    return y;
+    // MUFU estimate y0 (relative error below 2^-22), then one third-order correction:
+    // with e = 1 - r2 y0^2, 1/sqrt(r2) = y0 (1 - e)^(-1/2) = y0 (1 + e/2 + 3e^2/8 + O(e^3)),
+    // whose truncation (5/16)|e|^3 < 1e-20 is below float64 rounding; 5 float64 operations
+    // where two Newton-Raphson steps take 7
+    const double y = (double)rsqrt_mufu((float)r2);
+    const double e = fma(-r2, y * y, 1.0);
+    return fma(y * e, fma(0.375, e, 0.5), y);
 }
 
 template <bool kGrad>
