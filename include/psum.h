@@ -79,6 +79,16 @@ extern "C" {
 #define PSUM_BASIS_SPHERICAL 0  /* regular solid harmonics R^_n^m(y/R0), n <= p (Eqs. 1.6-1.8); P = (p+1)^2 */
 #define PSUM_BASIS_RBF       1  /* kernel functions 1/|y - x_t| centred outside S_b (Eq. 5); P = n_rbf + 1 */
 
+/* pair kernel of the near sum at the charges (psum_opts.pair_kernel) */
+#define PSUM_PAIRS_AUTO       0  /* symmetric where it applies and the system has at least 16 tiles of 512
+                                    charges, one-sided otherwise */
+#define PSUM_PAIRS_ONE_SIDED  1  /* every (target, source, image) term computed on its own */
+#define PSUM_PAIRS_SYMMETRIC  2  /* where it applies, at any size: the pair (i, j, p) and its mirror
+                                    (j, i, -p) share one offset and one 1/r (FP32C plans without ball
+                                    trimming, potential and field at the charges, psum_eval,
+                                    psum_eval_host, psum_eval_graph and psum_energy; one-sided
+                                    elsewhere).  Same sums, different rounding order. */
+
 #define PSUM_MEAN_ZERO 0  /* C_1 makes the box mean of phi zero (Eq. pfx3, phi_mean = 0) */
 #define PSUM_MEAN_NONE 1  /* C_1 = 0 (potential defined up to a constant, Sec. 3) */
 
@@ -107,6 +117,7 @@ typedef struct psum_opts {
                         psum_energy_backward and the batch API reject RBF plans (PSUM_ERR_ARG). */
     int n_rbf;       /* number of RBF centres, 1..4096 (0: 256, the paper's choice) */
     double rbf_radius;  /* centres at rbf_radius R0, > 1 (0: on S_b, i.e. at lambda_eff R0) */
+    int pair_kernel;    /* PSUM_PAIRS_AUTO, PSUM_PAIRS_ONE_SIDED or PSUM_PAIRS_SYMMETRIC */
 } psum_opts;
 
 typedef struct psum_info {
@@ -123,7 +134,7 @@ typedef struct psum_info {
 
 /* Fill `o` with the defaults: unit cube, p = 8, M = 200, PSUM_FP64,
    PSUM_MEAN_ZERO, K = (1,1,1), PSUM_POINTS_FIBONACCI, lambda = 0, PSUM_BASIS_SPHERICAL,
-   n_rbf = 256, rbf_radius = 0. */
+   n_rbf = 256, rbf_radius = 0, PSUM_PAIRS_AUTO. */
 void psum_opts_default(psum_opts *o);
 
 /* Algorithm "set" (Sec. 2.3.1): circumradius R0 (step 1), M check points on the

@@ -34,6 +34,7 @@ PSUM_FF = 2
 PRECISIONS = {"fp64": PSUM_FP64, "fp32c": PSUM_FP32C, "ff": PSUM_FF}
 POINTS = {"fibonacci": 0, "gauss": 1}
 BASES = {"spherical": 0, "rbf": 1}
+PAIR_KERNELS = {"auto": 0, "one-sided": 1, "symmetric": 2}
 MEAN_MODES = {"zero": PSUM_MEAN_ZERO, "none": PSUM_MEAN_NONE}
 
 
@@ -41,7 +42,7 @@ class psum_opts(ctypes.Structure):
     _fields_ = [("d", ctypes.c_double * 3), ("p", ctypes.c_int), ("M", ctypes.c_int),
                 ("precision", ctypes.c_int), ("mean_mode", ctypes.c_int), ("K", ctypes.c_int * 3),
                 ("points", ctypes.c_int), ("lambda_", ctypes.c_double), ("basis", ctypes.c_int),
-                ("n_rbf", ctypes.c_int), ("rbf_radius", ctypes.c_double)]
+                ("n_rbf", ctypes.c_int), ("rbf_radius", ctypes.c_double), ("pair_kernel", ctypes.c_int)]
 
 
 class psum_info(ctypes.Structure):
@@ -167,8 +168,10 @@ def psum_plan_create(d1: float, d2: float, d3: float, p: int, M: int):
 
 
 def psum_plan_create_ex(d, p: int, M: int, precision="fp64", mean="zero", K=(1, 1, 1), points="fibonacci",
-                        lam: float = 0.0, basis="spherical", n_rbf: int = 256, rbf_radius: float = 0.0):
+                        lam: float = 0.0, basis="spherical", n_rbf: int = 256, rbf_radius: float = 0.0,
+                        pairs="auto"):
     o = psum_opts_default()
+    o.pair_kernel = PAIR_KERNELS[pairs] if isinstance(pairs, str) else int(pairs)
     o.lambda_ = float(lam)
     o.basis = BASES[basis] if isinstance(basis, str) else int(basis)
     o.n_rbf = int(n_rbf)
@@ -401,8 +404,9 @@ class PeriodicCoulomb:
     """A plan plus tensor-returning evaluation (allocation through torch only)."""
 
     def __init__(self, d, p: int, M: int, precision="fp64", mean="zero", K=(1, 1, 1), points="fibonacci",
-                 lam: float = 0.0, basis="spherical", n_rbf: int = 256, rbf_radius: float = 0.0):
-        self.plan = psum_plan_create_ex(d, p, M, precision, mean, K, points, lam, basis, n_rbf, rbf_radius)
+                 lam: float = 0.0, basis="spherical", n_rbf: int = 256, rbf_radius: float = 0.0, pairs="auto"):
+        self.plan = psum_plan_create_ex(d, p, M, precision, mean, K, points, lam, basis, n_rbf, rbf_radius,
+                                        pairs)
         self.info = psum_plan_info(self.plan)
 
     def at(self, x, q, y, grad: bool = True, stream=None, check: bool = True):

@@ -64,6 +64,8 @@ struct Layout {
     NearPlanLaunch Lb;
     int nblk_mom;
     NearPlanLaunch Ln, Lc;
+    bool sym;              // the charge pair sums by the symmetric kernel (partition S)
+    NearSymLaunch S;
     int64_t n_tiles, n_chunks, n_pts;   // target tiles, source chunks, packed target points
     int64_t n_src_groups, n_src_pts;    // the charges' pack (groups of 128, FP32C/FF; points, FP64)
     int nblk_val, nblk_mean;
@@ -103,6 +105,19 @@ size_t layout(Plan& pl, int64_t N, char* base, Layout& L, bool backward = false,
         if (g_cap > 0 && gmax > g_cap) gmax = g_cap;
         L.Ln = near_partition(L.n_tiles, L.n_chunks, n_img, gmax, ipc);
         L.Lc = near_partition(pl.n_check_tiles, L.n_chunks, n_img, gmax, g_cap > 0 ? 1 : kCheckItemsPerCta);
+        // the symmetric kernel: FP32C charges, block image set, a normal (growing) scratch
+        L.sym = false;
+        const int pk = pl.opt.pair_kernel;
+        if (pl.opt.precision == PSUM_FP32C && !sep && !trimmed && g_cap == 0 && pk != PSUM_PAIRS_ONE_SIDED &&
+            (pk == PSUM_PAIRS_SYMMETRIC || L.n_tiles >= kSymMinTiles)) {
+            // image groups sized for the occupancy of the smallest group (the largest dynamic
+            // shared memory), then the partition for that group size
+            const int64_t gs = (int64_t)pl.num_sms * near32s_occupancy_ctas(n_img);
+            L.S = sym_partition(L.n_tiles, L.n_chunks, n_img, gs);
+            L.S.G = (int64_t)pl.num_sms * near32s_occupancy_ctas(L.S.img_per_g);
+            if (L.S.G > L.S.W) L.S.G = L.S.W;
+            L.sym = L.S.partial_doubles() * sizeof(double) <= kSymMaxPartialBytes;
+        }
         L.xs = trimmed ? b.take<double>(3 * (size_t)L.n_src_pts) : nullptr;
         L.ka = b.take<uint32_t>(N);
         L.va = b.take<uint32_t>(N);
@@ -123,10 +138,11 @@ size_t layout(Plan& pl, int64_t N, char* base, Layout& L, bool backward = false,
             L.tpk32lo = b.take<float4>(2 * (size_t)L.n_pts);
             L.torg = b.take<double>(4 * (size_t)n_groups);
         }
-        L.part_n = b.take<double>((size_t)L.n_tiles * L.Ln.max_contrib * 4 * kTile32);
+        L.part_n = b.take<double>(L.sym ? L.S.partial_doubles() : (size_t)L.n_tiles * L.Ln.max_contrib * 4 * kTile32);
         L.part_c = b.take<double>((size_t)pl.n_check_tiles * L.Lc.max_contrib * kTile32);
         L.phi_c = b.take<double>((size_t)pl.n_check_tiles * kTile32);
     } else {
+        L.sym = false;
         L.n_tiles = (NT + kTile64 - 1) / kTile64;
         L.n_chunks = (N + kTile64 - 1) / kTile64;
         L.n_pts = L.n_tiles * kTile64;
@@ -160,6 +176,9 @@ size_t layout(Plan& pl, int64_t N, char* base, Layout& L, bool backward = false,
     L.Lc.counter = flags + 2;
     L.Ln.status = L.Lc.status = flags;
     L.Ln.n_status = L.Lc.n_status = 1;
+    L.S.counter = flags + 1;
+    L.S.status = flags;
+    L.S.n_status = 1;
     L.far_phi = L.far_grad = L.w_part = L.w = L.u = L.psi = L.gpsi = L.part_b = nullptr;
     L.chk_src32 = nullptr;
     L.chk_src32lo = nullptr;
@@ -272,7 +291,11 @@ int queue_forward(psum_plan_s* h, int64_t N, const double* x, const double* q, d
     const double* tor = sep ? L.torg : L.org;
     const double4_32a* t64 = sep ? L.tpk64 : L.pk64;
     if (h->profile) TRY(cudaEventRecord(h->ev[1], st));
-    if (fp32) {
+    if (L.sym) {
+        NearSymLaunch S = L.S;
+        S.inject = h->inject_timeout ? 1 : 0;
+        TRY(launch_near32s(L.pk32, L.pk32lo, L.org, pl.d_shifts, L.part_n, S, st));
+    } else if (fp32) {
         NearPlanLaunch Ln = L.Ln;
         Ln.inject = h->inject_timeout ? 1 : 0;
         TRY(launch_near32(true, L.pk32, L.pk32lo, L.org, thi, tlo, tor, pl.d_shifts, L.part_n, Ln, st, 0, L.xs,
@@ -292,7 +315,10 @@ int queue_forward(psum_plan_s* h, int64_t N, const double* x, const double* q, d
     }
     if (h->profile) TRY(cudaEventRecord(h->ev[3], st));
     const int tile = fp32 ? kTile32 : kTile64;
-    TRY(launch_near_reduce(L.part_n, sep ? T : N, tile, 4, L.Ln, L.phi_n, L.grad_n, st));
+    if (L.sym)
+        TRY(launch_sym_reduce(L.part_n, N, L.S.n_tiles * L.S.n_g, L.phi_n, L.grad_n, st));
+    else
+        TRY(launch_near_reduce(L.part_n, sep ? T : N, tile, 4, L.Ln, L.phi_n, L.grad_n, st));
     TRY(launch_near_reduce(L.part_c, pl.n_check, tile, 1, L.Lc, L.phi_c, nullptr, st));
     h->launches += 4;   // two near-field kernels, two reductions
     const bool zero_mean = o.mean_mode == PSUM_MEAN_ZERO;
@@ -426,6 +452,9 @@ bool valid_opts(const psum_opts* o) {
         if (n > 100000) return false;
     }
     if (o->precision != PSUM_FP64 && o->precision != PSUM_FP32C && o->precision != PSUM_FF) return false;
+    if (o->pair_kernel != PSUM_PAIRS_AUTO && o->pair_kernel != PSUM_PAIRS_ONE_SIDED &&
+        o->pair_kernel != PSUM_PAIRS_SYMMETRIC)
+        return false;
     if (o->mean_mode != PSUM_MEAN_ZERO && o->mean_mode != PSUM_MEAN_NONE) return false;
     return true;
 }
@@ -448,6 +477,7 @@ void psum_opts_default(psum_opts* o) {
     o->basis = PSUM_BASIS_SPHERICAL;
     o->n_rbf = 256;
     o->rbf_radius = 0.0;
+    o->pair_kernel = PSUM_PAIRS_AUTO;
 }
 
 int psum_plan_create_ex(const psum_opts* o, psum_plan_t* out) {

@@ -665,6 +665,435 @@ __global__ void __launch_bounds__(kThreads32, kMinB) k_near32(Near32Args a) {
 }
 
 // ---------------------------------------------------------------------------
+// Symmetric charge kernel (FP32C, potential and field at the charges, block image sets).
+// With the charges as both targets and sources, the pair (i, j, p) and its mirror
+// (j, i, -p) are one distance apart: one offset, one rsqrt and one 1/r^2 serve the
+// target's sum (the action, q_j / r) and the source's (the reaction, q_i / r, field
+// with the opposite sign).  The image set {p} of a block is symmetric, so the pairs
+// of tiles (a, b), a < b, each taken once with every image, cover the whole sum; a
+// tile against itself (a = b) runs the one-sided units above.
+//
+//   * the work item is (tile pair (a, b), group of images); items are taken from a
+//     device counter; the action on tile a goes to partial slot (a, b, g), the reaction
+//     on tile b to slot (b, a, g), so every slot has one writer and the reduction adds
+//     a tile's n_tiles * n_g slots in a fixed order;
+//   * per source chunk of tile b and image, a warp's 32 lanes (4 targets each) visit the
+//     chunk in 4 rounds of 32 sources: at step k lane l takes source (l + k) mod 32 of
+//     the round and adds the targets' terms to that source's reaction sums, which then
+//     move one lane down (a shuffle), so after 32 steps lane l holds the reaction of
+//     source l over the warp's 128 targets; the 4 warps keep private compensated (hi,
+//     lo) sums per source, combined in a fixed order when the chunk is done;
+//   * near pairs (as in the one-sided units) take float-float offsets, K(0) = 0 and
+//     blocks of 4 terms with compensated sums, on both sides.
+// ---------------------------------------------------------------------------
+struct Near32SymArgs {
+    const float4* pk_hi;     // the charges' pack: 2 float4 per point, (x,x,y,y),(z,z,q,q) offsets
+    const float4* pk_lo;     // their float32 rounding remainders
+    const double* org;       // 4 per group of 128 points: origin x, y, z and radius
+    const double* shifts;    // image vectors, 3 per image
+    double* partial;         // [n_tiles][n_tiles * n_g][4][kTile32]
+    int64_t n_tiles, n_chunks;
+    int n_img, n_g, img_per_g;
+    int64_t W;               // items: n_tiles (n_tiles + 1) / 2 * n_g
+    int* counter;
+    int* status;
+    int n_status;
+    int inject;              // test hook: expect 16 bytes more than the copies bring
+};
+
+// compensated float32 (hi, lo) += v
+__device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float v) {
+    float e;
+    hi = two_sum(hi, v, e);
+    lo += e;
+}
+
+// One far step: the lane's 2 packed target pairs against source si of the staged chunk.
+// Action terms go to the pair accumulators, the reaction (summed over the 4 targets) to
+// (rp, rx, ry, rz); the field reaction is accumulated with the action's sign convention
+// (x_s + p - t) and negated when it is stored.
+__device__ __forceinline__ void sym_far_step(const float4* __restrict__ s_hi, int si, const float2 (&nx)[2],
+                                             const float2 (&ny)[2], const float2 (&nz)[2], const float2 (&tq)[2],
+                                             float2 (&aphi)[2], float2 (&agx)[2], float2 (&agy)[2],
+                                             float2 (&agz)[2], float& rp, float& rx, float& ry, float& rz) {
+    const float4 A = s_hi[2 * si];       // x x y y
+    const float4 B = s_hi[2 * si + 1];   // z z q q
+    const float2 sq = make_float2(B.z, B.w);
+    float2 bp, bx, by, bz;
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        const float2 ex = __fadd2_rn(make_float2(A.x, A.y), nx[j]);
+        const float2 ey = __fadd2_rn(make_float2(A.z, A.w), ny[j]);
+        const float2 ez = __fadd2_rn(make_float2(B.x, B.y), nz[j]);
+        float2 r2 = __fmul2_rn(ex, ex);
+        r2 = __ffma2_rn(ey, ey, r2);
+        r2 = __ffma2_rn(ez, ez, r2);
+        const float2 ri = make_float2(rsqrt_mufu(r2.x), rsqrt_mufu(r2.y));
+        const float2 ri2 = __fmul2_rn(ri, ri);
+        const float2 qa = __fmul2_rn(sq, ri);
+        aphi[j] = __fadd2_rn(aphi[j], qa);
+        const float2 wa = __fmul2_rn(qa, ri2);
+        agx[j] = __ffma2_rn(ex, wa, agx[j]);
+        agy[j] = __ffma2_rn(ey, wa, agy[j]);
+        agz[j] = __ffma2_rn(ez, wa, agz[j]);
+        const float2 qb = __fmul2_rn(tq[j], ri);
+        const float2 wb = __fmul2_rn(qb, ri2);
+        if (j == 0) {
+            bp = qb;
+            bx = __fmul2_rn(ex, wb);
+            by = __fmul2_rn(ey, wb);
+            bz = __fmul2_rn(ez, wb);
+        } else {
+            bp = __fadd2_rn(bp, qb);
+            bx = __ffma2_rn(ex, wb, bx);
+            by = __ffma2_rn(ey, wb, by);
+            bz = __ffma2_rn(ez, wb, bz);
+        }
+    }
+    rp += bp.x + bp.y;
+    rx += bx.x + bx.y;
+    ry += by.x + by.y;
+    rz += bz.x + bz.y;
+}
+
+// One near step: float-float offsets (hi + lo of both sides), K(0) = 0; the action's
+// potential terms go to blk (a block of 4 steps), the reaction's potential (a block of
+// the 4 targets' terms) into the compensated (rp, rpl).
+__device__ __forceinline__ void sym_near_step(const float4* __restrict__ s_hi, const float4* __restrict__ s_lo,
+                                              int si, const float2 (&nh)[2][3], const float2 (&nl)[2][3],
+                                              const float2 (&tq)[2], float2 (&blk)[2], bool first,
+                                              float2 (&agx)[2], float2 (&agy)[2], float2 (&agz)[2], float& rp,
+                                              float& rpl, float& rx, float& ry, float& rz) {
+    const float4 A = s_hi[2 * si], B = s_hi[2 * si + 1];
+    const float4 C = s_lo[2 * si], D = s_lo[2 * si + 1];
+    const float2 sq = make_float2(B.z, B.w);
+    float2 bp, bx, by, bz;
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        const float2 ex = __fadd2_rn(__fadd2_rn(make_float2(A.x, A.y), nh[j][0]), __fadd2_rn(make_float2(C.x, C.y), nl[j][0]));
+        const float2 ey = __fadd2_rn(__fadd2_rn(make_float2(A.z, A.w), nh[j][1]), __fadd2_rn(make_float2(C.z, C.w), nl[j][1]));
+        const float2 ez = __fadd2_rn(__fadd2_rn(make_float2(B.x, B.y), nh[j][2]), __fadd2_rn(make_float2(D.x, D.y), nl[j][2]));
+        float2 r2 = __fmul2_rn(ex, ex);
+        r2 = __ffma2_rn(ey, ey, r2);
+        r2 = __ffma2_rn(ez, ez, r2);
+        float2 ri = make_float2(rsqrt_mufu(r2.x), rsqrt_mufu(r2.y));
+        ri.x = r2.x > 0.f ? ri.x : 0.f;                   // K(0) = 0 (Eq. 1)
+        ri.y = r2.y > 0.f ? ri.y : 0.f;
+        const float2 ri2 = __fmul2_rn(ri, ri);
+        const float2 qa = __fmul2_rn(sq, ri);
+        blk[j] = first ? qa : __fadd2_rn(blk[j], qa);
+        const float2 wa = __fmul2_rn(qa, ri2);
+        agx[j] = __ffma2_rn(ex, wa, agx[j]);
+        agy[j] = __ffma2_rn(ey, wa, agy[j]);
+        agz[j] = __ffma2_rn(ez, wa, agz[j]);
+        const float2 qb = __fmul2_rn(tq[j], ri);
+        const float2 wb = __fmul2_rn(qb, ri2);
+        if (j == 0) {
+            bp = qb;
+            bx = __fmul2_rn(ex, wb);
+            by = __fmul2_rn(ey, wb);
+            bz = __fmul2_rn(ez, wb);
+        } else {
+            bp = __fadd2_rn(bp, qb);
+            bx = __ffma2_rn(ex, wb, bx);
+            by = __ffma2_rn(ey, wb, by);
+            bz = __ffma2_rn(ez, wb, bz);
+        }
+    }
+    two_sum_acc(rp, rpl, bp.x + bp.y);
+    rx += bx.x + bx.y;
+    ry += by.x + by.y;
+    rz += bz.x + bz.y;
+}
+
+template <int kMinB>
+__global__ void __launch_bounds__(kThreads32, kMinB) k_near32s(Near32SymArgs a) {
+    constexpr int kWarps = kThreads32 / 32;
+    __shared__ float4 s_hi[2 * kNearChunk];
+    __shared__ float4 s_lo[2 * kNearChunk];
+    __shared__ float2 s_th[3][2][kThreads32];             // target offsets of tile a, [coord][pair]
+    __shared__ float2 s_tq[2][kThreads32];                // target charges, [pair]
+    __shared__ float2 s_acc[4][2][2][kThreads32];         // action sums [quantity][pair][hi, lo]
+    extern __shared__ float4 s_dyn4[];
+    // reaction sums [warp][quantity][hi, lo][source], then [img_per_g][kTgt32][6] deltas and
+    // [img_per_g] unit classes
+    auto s_re = reinterpret_cast<float (*)[4][2][kNearChunk]>(s_dyn4);
+    float* s_delta = (float*)s_dyn4 + kWarps * 4 * 2 * kNearChunk;
+    int* s_near = (int*)(s_delta + 6 * kTgt32 * a.img_per_g);
+    __shared__ int s_item;
+    __shared__ int s_fail;
+    __shared__ __align__(8) uint64_t s_bar;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int up = (lane + 1) & 31;
+    uint32_t phase = 0;
+    if (tid == 0) {
+        mbar_init(&s_bar, 1);
+        fence_mbar_init();
+        fence_proxy_async_smem();
+        s_fail = 0;
+    }
+    __syncthreads();
+    const int64_t n_slots = a.n_tiles * a.n_g;
+
+    for (;;) {
+    if (tid == 0) s_item = atomicAdd(a.counter, 1);
+    __syncthreads();
+    const int64_t item = s_item;
+    __syncthreads();                     // every thread has the item before s_item changes
+    if (item >= a.W) break;
+    const int64_t pair = item / a.n_g;
+    const int gi = (int)(item - pair * a.n_g);
+    // pair = tb (tb + 1) / 2 + ta, ta <= tb
+    int64_t tb = (int64_t)((sqrt(8.0 * (double)pair + 1.0) - 1.0) * 0.5);
+    while (tb > 0 && tb * (tb + 1) / 2 > pair) --tb;
+    while ((tb + 1) * (tb + 2) / 2 <= pair) ++tb;
+    const int64_t ta = pair - tb * (tb + 1) / 2;
+    const bool diag = ta == tb;
+    const int im0 = gi * a.img_per_g;
+    const int nimg = min(a.img_per_g, a.n_img - im0);
+    // targets of tile ta; zero the action sums
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        const int64_t i0 = (ta * kTgt32 + 2 * j) * kGroup + tid;
+        const int64_t i1 = i0 + kGroup;
+        const float4 A0 = a.pk_hi[2 * i0], B0 = a.pk_hi[2 * i0 + 1];
+        const float4 A1 = a.pk_hi[2 * i1], B1 = a.pk_hi[2 * i1 + 1];
+        s_th[0][j][tid] = make_float2(A0.x, A1.x);
+        s_th[1][j][tid] = make_float2(A0.z, A1.z);
+        s_th[2][j][tid] = make_float2(B0.x, B1.x);
+        s_tq[j][tid] = make_float2(B0.z, B1.z);
+#pragma unroll
+        for (int qi = 0; qi < 4; ++qi) s_acc[qi][j][0][tid] = s_acc[qi][j][1][tid] = make_float2(0.f, 0.f);
+    }
+    const int64_t c0 = tb * kTgt32;
+    const int64_t c1 = c0 + kTgt32 < a.n_chunks ? c0 + kTgt32 : a.n_chunks;
+    for (int64_t chunk = c0; chunk < c1; ++chunk) {
+        __syncthreads();   // every thread is done with the previous chunk, deltas, classes and reactions
+        // this warp's reaction sums for the chunk start at zero (private to the warp until the
+        // combination below)
+#pragma unroll
+        for (int qi = 0; qi < 4; ++qi)
+#pragma unroll
+            for (int k = 0; k < kNearChunk / 32; ++k) s_re[warp][qi][0][32 * k + lane] = s_re[warp][qi][1][32 * k + lane] = 0.f;
+        if (tid == 0) {
+            fence_proxy_async_smem();
+            mbar_expect_tx(&s_bar, 2 * kChunkBytes + (a.inject ? 16 : 0));
+            bulk_g2s(s_hi, a.pk_hi + chunk * (2 * kNearChunk), kChunkBytes, &s_bar);
+            bulk_g2s(s_lo, a.pk_lo + chunk * (2 * kNearChunk), kChunkBytes, &s_bar);
+        }
+        const double* so = a.org + 4 * chunk;
+        for (int im = tid; im < nimg; im += kThreads32) {
+            const double* sh = a.shifts + 3 * (im0 + im);
+            int nr = 0;
+            for (int k = 0; k < kTgt32; ++k) {
+                const double* to = a.org + 4 * (ta * kTgt32 + k);
+                const double D0 = (to[0] - so[0]) - sh[0], D1 = (to[1] - so[1]) - sh[1], D2 = (to[2] - so[2]) - sh[2];
+                float* dl = s_delta + 6 * (im * kTgt32 + k);
+                dl[0] = (float)D0; dl[1] = (float)D1; dl[2] = (float)D2;
+                dl[3] = (float)(D0 - (double)dl[0]); dl[4] = (float)(D1 - (double)dl[1]);
+                dl[5] = (float)(D2 - (double)dl[2]);
+                const double reach = kNearFactor * (to[3] + so[3]);
+                if (D0 * D0 + D1 * D1 + D2 * D2 <= reach * reach) nr |= k < 2 ? kUnitNear0 : kUnitNear1;
+            }
+            s_near[im] = nr;
+        }
+        const long long limit = a.inject ? (1LL << 12) : kCopySpinLimit;
+        if (tid == 0 && !mbar_wait(&s_bar, phase, limit)) s_fail = 1;
+        phase ^= 1u;
+        __syncthreads();
+        if (s_fail) {
+            if (tid == 0) {
+                for (int k = 0; k < a.n_status; ++k) atomicOr(a.status + k, kStatTimeout);
+                mbar_wait(&s_bar, phase ^ 1u, limit);
+            }
+            return;
+        }
+        for (int im = 0; im < nimg; ++im) {
+            const float* dl = s_delta + 6 * (im * kTgt32);
+            const int cls = s_near[im];
+            if (diag) {
+                // a tile against its own chunks: the one-sided units
+#pragma unroll 1
+                for (int j = 0; j < 2; ++j) {
+                    const float* d0 = dl + 6 * (2 * j);
+                    const float* d1 = dl + 6 * (2 * j + 1);
+                    const float2 tx = s_th[0][j][tid], ty = s_th[1][j][tid], tz = s_th[2][j][tid];
+                    if (!(cls & (j ? kUnitNear1 : kUnitNear0))) {
+                        const float2 nx[1] = {make_float2(-(tx.x + d0[0]), -(tx.y + d1[0]))};
+                        const float2 ny[1] = {make_float2(-(ty.x + d0[1]), -(ty.y + d1[1]))};
+                        const float2 nz[1] = {make_float2(-(tz.x + d0[2]), -(tz.y + d1[2]))};
+                        float2 aphi[1] = {make_float2(0.f, 0.f)}, agx[1] = {aphi[0]}, agy[1] = {aphi[0]},
+                               agz[1] = {aphi[0]};
+                        pair_loop_far<true, 1>(s_hi, nx, ny, nz, aphi, agx, agy, agz);
+                        two_sum_acc2(s_acc[0][j][0][tid], s_acc[0][j][1][tid], aphi[0]);
+                        two_sum_acc2(s_acc[1][j][0][tid], s_acc[1][j][1][tid], agx[0]);
+                        two_sum_acc2(s_acc[2][j][0][tid], s_acc[2][j][1][tid], agy[0]);
+                        two_sum_acc2(s_acc[3][j][0][tid], s_acc[3][j][1][tid], agz[0]);
+                        continue;
+                    }
+                    const int64_t i0 = (ta * kTgt32 + 2 * j) * kGroup + tid;
+                    const int64_t i1 = i0 + kGroup;
+                    const float4 C0 = a.pk_lo[2 * i0], D0 = a.pk_lo[2 * i0 + 1];
+                    const float4 C1 = a.pk_lo[2 * i1], D1 = a.pk_lo[2 * i1 + 1];
+                    const float2 tls[3] = {make_float2(C0.x, C1.x), make_float2(C0.z, C1.z), make_float2(D0.x, D1.x)};
+                    const float2 ths[3] = {tx, ty, tz};
+                    float2 nh[3], nl[3];
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        float e0, e1;
+                        const float h0 = two_sum(ths[c].x, d0[c], e0);
+                        const float h1 = two_sum(ths[c].y, d1[c], e1);
+                        nh[c] = make_float2(-h0, -h1);
+                        nl[c] = make_float2(-(e0 + (tls[c].x + d0[3 + c])), -(e1 + (tls[c].y + d1[3 + c])));
+                    }
+                    float2 aphi = make_float2(0.f, 0.f), aphi_lo = aphi, agx = aphi, agy = aphi, agz = aphi;
+                    pair_loop_near<true>(s_hi, s_lo, nh[0], nh[1], nh[2], nl[0], nl[1], nl[2], aphi, aphi_lo, agx,
+                                         agy, agz);
+                    two_sum_acc2(s_acc[0][j][0][tid], s_acc[0][j][1][tid], aphi);
+                    s_acc[0][j][1][tid] = __fadd2_rn(s_acc[0][j][1][tid], aphi_lo);
+                    two_sum_acc2(s_acc[1][j][0][tid], s_acc[1][j][1][tid], agx);
+                    two_sum_acc2(s_acc[2][j][0][tid], s_acc[2][j][1][tid], agy);
+                    two_sum_acc2(s_acc[3][j][0][tid], s_acc[3][j][1][tid], agz);
+                }
+                continue;
+            }
+            const float2 tq[2] = {s_tq[0][tid], s_tq[1][tid]};
+            float2 agx[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)}, agy[2] = {agx[0], agx[0]},
+                   agz[2] = {agx[0], agx[0]};
+            float2 aphi[2] = {agx[0], agx[0]}, aphi2[2] = {agx[0], agx[0]};   // far: two interleaved sums; near: hi, lo
+            if (!(cls & kUnitNear)) {
+                float2 nx[2], ny[2], nz[2];
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    const float* d0 = dl + 6 * (2 * j);
+                    const float* d1 = dl + 6 * (2 * j + 1);
+                    const float2 tx = s_th[0][j][tid], ty = s_th[1][j][tid], tz = s_th[2][j][tid];
+                    nx[j] = make_float2(-(tx.x + d0[0]), -(tx.y + d1[0]));
+                    ny[j] = make_float2(-(ty.x + d0[1]), -(ty.y + d1[1]));
+                    nz[j] = make_float2(-(tz.x + d0[2]), -(tz.y + d1[2]));
+                }
+#pragma unroll 1
+                for (int g = 0; g < kNearChunk / 32; ++g) {
+                    float rp = 0.f, rx = 0.f, ry = 0.f, rz = 0.f;
+#pragma unroll 4
+                    for (int k = 0; k < 32; k += 2) {
+                        sym_far_step(s_hi, 32 * g + ((lane + k) & 31), nx, ny, nz, tq, aphi, agx, agy, agz, rp, rx,
+                                     ry, rz);
+                        rp = __shfl_sync(0xffffffffu, rp, up);
+                        rx = __shfl_sync(0xffffffffu, rx, up);
+                        ry = __shfl_sync(0xffffffffu, ry, up);
+                        rz = __shfl_sync(0xffffffffu, rz, up);
+                        sym_far_step(s_hi, 32 * g + ((lane + k + 1) & 31), nx, ny, nz, tq, aphi2, agx, agy, agz, rp,
+                                     rx, ry, rz);
+                        rp = __shfl_sync(0xffffffffu, rp, up);
+                        rx = __shfl_sync(0xffffffffu, rx, up);
+                        ry = __shfl_sync(0xffffffffu, ry, up);
+                        rz = __shfl_sync(0xffffffffu, rz, up);
+                    }
+                    // the lane holds the reaction of source 32 g + lane
+                    const int s = 32 * g + lane;
+                    two_sum_acc(s_re[warp][0][0][s], s_re[warp][0][1][s], rp);
+                    two_sum_acc(s_re[warp][1][0][s], s_re[warp][1][1][s], rx);
+                    two_sum_acc(s_re[warp][2][0][s], s_re[warp][2][1][s], ry);
+                    two_sum_acc(s_re[warp][3][0][s], s_re[warp][3][1][s], rz);
+                }
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    two_sum_acc2(s_acc[0][j][0][tid], s_acc[0][j][1][tid], __fadd2_rn(aphi[j], aphi2[j]));
+                    two_sum_acc2(s_acc[1][j][0][tid], s_acc[1][j][1][tid], agx[j]);
+                    two_sum_acc2(s_acc[2][j][0][tid], s_acc[2][j][1][tid], agy[j]);
+                    two_sum_acc2(s_acc[3][j][0][tid], s_acc[3][j][1][tid], agz[j]);
+                }
+            } else {
+                // near pairs present: every pair of the unit in float-float offsets
+                float2 nh[2][3], nl[2][3];
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    const float* d0 = dl + 6 * (2 * j);
+                    const float* d1 = dl + 6 * (2 * j + 1);
+                    const int64_t i0 = (ta * kTgt32 + 2 * j) * kGroup + tid;
+                    const int64_t i1 = i0 + kGroup;
+                    const float4 C0 = a.pk_lo[2 * i0], D0 = a.pk_lo[2 * i0 + 1];
+                    const float4 C1 = a.pk_lo[2 * i1], D1 = a.pk_lo[2 * i1 + 1];
+                    const float2 tls[3] = {make_float2(C0.x, C1.x), make_float2(C0.z, C1.z), make_float2(D0.x, D1.x)};
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        const float2 th = s_th[c][j][tid];
+                        float e0, e1;
+                        const float h0 = two_sum(th.x, d0[c], e0);
+                        const float h1 = two_sum(th.y, d1[c], e1);
+                        nh[j][c] = make_float2(-h0, -h1);
+                        nl[j][c] = make_float2(-(e0 + (tls[c].x + d0[3 + c])), -(e1 + (tls[c].y + d1[3 + c])));
+                    }
+                }
+#pragma unroll 1
+                for (int g = 0; g < kNearChunk / 32; ++g) {
+                    float rp = 0.f, rpl = 0.f, rx = 0.f, ry = 0.f, rz = 0.f;
+#pragma unroll 1
+                    for (int k0 = 0; k0 < 32; k0 += kNearFold) {
+                        float2 blk[2];
+#pragma unroll
+                        for (int k = 0; k < kNearFold; ++k) {
+                            sym_near_step(s_hi, s_lo, 32 * g + ((lane + k0 + k) & 31), nh, nl, tq, blk, k == 0, agx,
+                                          agy, agz, rp, rpl, rx, ry, rz);
+                            rp = __shfl_sync(0xffffffffu, rp, up);
+                            rpl = __shfl_sync(0xffffffffu, rpl, up);
+                            rx = __shfl_sync(0xffffffffu, rx, up);
+                            ry = __shfl_sync(0xffffffffu, ry, up);
+                            rz = __shfl_sync(0xffffffffu, rz, up);
+                        }
+#pragma unroll
+                        for (int j = 0; j < 2; ++j) two_sum_acc2(aphi[j], aphi2[j], blk[j]);
+                    }
+                    const int s = 32 * g + lane;
+                    two_sum_acc(s_re[warp][0][0][s], s_re[warp][0][1][s], rp);
+                    s_re[warp][0][1][s] += rpl;
+                    two_sum_acc(s_re[warp][1][0][s], s_re[warp][1][1][s], rx);
+                    two_sum_acc(s_re[warp][2][0][s], s_re[warp][2][1][s], ry);
+                    two_sum_acc(s_re[warp][3][0][s], s_re[warp][3][1][s], rz);
+                }
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    two_sum_acc2(s_acc[0][j][0][tid], s_acc[0][j][1][tid], aphi[j]);
+                    s_acc[0][j][1][tid] = __fadd2_rn(s_acc[0][j][1][tid], aphi2[j]);
+                    two_sum_acc2(s_acc[1][j][0][tid], s_acc[1][j][1][tid], agx[j]);
+                    two_sum_acc2(s_acc[2][j][0][tid], s_acc[2][j][1][tid], agy[j]);
+                    two_sum_acc2(s_acc[3][j][0][tid], s_acc[3][j][1][tid], agz[j]);
+                }
+            }
+        }
+        if (!diag) {
+            // the chunk's reaction: the warps' sums in a fixed order, into slot (tb, ta, gi) at
+            // the chunk's positions in tile tb (the field with the reaction's sign)
+            __syncthreads();
+            double* dst = a.partial + ((tb * n_slots + ta * a.n_g + gi) * 4) * kTile32 + (chunk - c0) * kNearChunk;
+            for (int s = tid; s < kNearChunk; s += kThreads32) {
+#pragma unroll
+                for (int qi = 0; qi < 4; ++qi) {
+                    double v = 0.0;
+#pragma unroll
+                    for (int w = 0; w < kWarps; ++w) v += (double)s_re[w][qi][0][s] + (double)s_re[w][qi][1][s];
+                    dst[qi * kTile32 + s] = qi == 0 ? v : -v;
+                }
+            }
+        }
+    }
+    // the action on tile ta: slot (ta, tb, gi)
+    {
+        double* dst = a.partial + ((ta * n_slots + tb * a.n_g + gi) * 4) * kTile32;
+#pragma unroll
+        for (int qi = 0; qi < 4; ++qi)
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const float2 h = s_acc[qi][j][0][tid], l = s_acc[qi][j][1][tid];
+                dst[qi * kTile32 + (2 * j) * kThreads32 + tid] = (double)h.x + (double)l.x;
+                dst[qi * kTile32 + (2 * j + 1) * kThreads32 + tid] = (double)h.y + (double)l.y;
+            }
+    }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // FP64 kernel
 // ---------------------------------------------------------------------------
 struct Near64Args {
@@ -820,6 +1249,36 @@ __global__ void __launch_bounds__(32 * kReduceWarps) k_near_reduce(const double*
     }
 }
 
+// Reduction of the symmetric kernel's slots: target i (packed order, i < n_valid) of tile
+// t adds slots 0 .. n_slots - 1 of row t; a block takes 32 consecutive targets and one
+// quantity, its 8 warps every 8th slot, combined in a fixed order.
+__global__ void __launch_bounds__(32 * kReduceWarps) k_sym_reduce(const double* __restrict__ partial, int64_t n_valid,
+                                                                 int64_t n_slots, double* __restrict__ out_phi,
+                                                                 double* __restrict__ out_grad) {
+    __shared__ double s_part[kReduceWarps][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int qi = blockIdx.y;
+    const int64_t i0 = (int64_t)blockIdx.x * 32;
+    const int64_t i = i0 + lane;
+    const int64_t tile = i0 / kTile32;
+    const int loc = (int)(i - tile * kTile32);
+    double acc = 0.0;
+    if (i < n_valid)
+        for (int64_t s = warp; s < n_slots; s += kReduceWarps)
+            acc += partial[((tile * n_slots + s) * 4 + qi) * kTile32 + loc];
+    s_part[warp][lane] = acc;
+    __syncthreads();
+    if (warp == 0 && i < n_valid) {
+        double v = s_part[0][lane];
+#pragma unroll
+        for (int w = 1; w < kReduceWarps; ++w) v += s_part[w][lane];
+        if (qi == 0)
+            out_phi[i] = v;
+        else if (out_grad)
+            out_grad[3 * i + qi - 1] = v;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Host launchers
 // ---------------------------------------------------------------------------
@@ -869,6 +1328,53 @@ cudaError_t launch_near32(bool grad, const float4* src_hi, const float4* src_lo,
         if (grad) k_near32<true, B0, false, false><<<G, kThreads32, smem, st>>>(a);
         else k_near32<false, B0, false, false><<<G, kThreads32, smem, st>>>(a);
     }
+    return cudaGetLastError();
+}
+
+constexpr int kNear32sMinBlocks = 4;
+
+size_t near32s_dyn_smem(int img_per_g) {
+    const size_t reaction = (size_t)(kThreads32 / 32) * 4 * 2 * kNearChunk * sizeof(float);
+    return reaction + ((6 * kTgt32 * (size_t)img_per_g + img_per_g + 3) / 4) * sizeof(float4);
+}
+
+// the kernel's static and dynamic shared memory together pass the 48 KiB default: allow the
+// largest dynamic size any image group needs
+cudaError_t near32s_allow_smem() {
+    return cudaFuncSetAttribute(k_near32s<kNear32sMinBlocks>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)near32s_dyn_smem(kMaxImages));
+}
+
+cudaError_t launch_near32s(const float4* pk_hi, const float4* pk_lo, const double* org, const double* shifts,
+                           double* partial, const NearSymLaunch& S, cudaStream_t st) {
+    if (!S.counter || !S.status || S.n_status < 1 || S.img_per_g < 1) return cudaErrorInvalidValue;
+    if (S.W <= 0) return cudaSuccess;
+    const cudaError_t ea = near32s_allow_smem();
+    if (ea != cudaSuccess) return ea;
+    Near32SymArgs a;
+    a.pk_hi = pk_hi; a.pk_lo = pk_lo; a.org = org; a.shifts = shifts; a.partial = partial;
+    a.n_tiles = S.n_tiles; a.n_chunks = S.n_chunks;
+    a.n_img = S.n_img; a.n_g = S.n_g; a.img_per_g = S.img_per_g;
+    a.W = S.W; a.counter = S.counter; a.status = S.status; a.n_status = S.n_status; a.inject = S.inject;
+    const cudaError_t e = cudaMemsetAsync(S.counter, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    k_near32s<kNear32sMinBlocks><<<(unsigned)S.G, kThreads32, near32s_dyn_smem(S.img_per_g), st>>>(a);
+    return cudaGetLastError();
+}
+
+int near32s_occupancy_ctas(int img_per_g) {
+    int nb = 0;
+    near32s_allow_smem();
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_near32s<kNear32sMinBlocks>, kThreads32,
+                                                  near32s_dyn_smem(img_per_g));
+    return nb < 1 ? 1 : nb;
+}
+
+cudaError_t launch_sym_reduce(const double* partial, int64_t n_valid, int64_t n_slots, double* out_phi,
+                              double* out_grad, cudaStream_t st) {
+    if (n_valid <= 0) return cudaSuccess;
+    const dim3 grid((unsigned)((n_valid + 31) / 32), 4u);
+    k_sym_reduce<<<grid, 32 * kReduceWarps, 0, st>>>(partial, n_valid, n_slots, out_phi, out_grad);
     return cudaGetLastError();
 }
 

@@ -367,6 +367,41 @@ struct NearPlanLaunch {
     NearSysTable tab;
 };
 
+// The symmetric charge kernel (one system, FP32C, block image set): work items are (tile
+// pair (a <= b), group of images); the partial buffer holds n_tiles x (n_tiles n_g) slots.
+struct NearSymLaunch {
+    int64_t n_tiles = 0, n_chunks = 0;
+    int n_img = 0, n_g = 0, img_per_g = 0;
+    int64_t W = 0, G = 0;          // work items, resident CTAs
+    int* counter = nullptr;
+    int* status = nullptr;
+    int n_status = 0;
+    int inject = 0;
+    size_t partial_doubles() const { return (size_t)n_tiles * (size_t)n_tiles * (size_t)n_g * 4 * kTile32; }
+};
+
+// Image groups: the fewest (1, 3, 9, ... up to one image per group) that give at least
+// kSymItemsPerCta items per resident CTA, so that the last items finish close together.
+constexpr int kSymItemsPerCta = 8;
+constexpr int64_t kSymMinTiles = 16;                          // automatic choice: at least 16 tiles
+constexpr size_t kSymMaxPartialBytes = (size_t)8 << 30;       // and a partial buffer of at most 8 GiB
+inline NearSymLaunch sym_partition(int64_t n_tiles, int64_t n_chunks, int n_img, int64_t G) {
+    NearSymLaunch S;
+    S.n_tiles = n_tiles;
+    S.n_chunks = n_chunks;
+    S.n_img = n_img;
+    S.G = G;
+    const int64_t pairs = n_tiles * (n_tiles + 1) / 2;
+    int ng = 1;
+    while (ng < n_img && pairs * ng < kSymItemsPerCta * G) ng *= 3;
+    if (ng > n_img) ng = n_img;
+    S.img_per_g = (n_img + ng - 1) / ng;
+    S.n_g = (n_img + S.img_per_g - 1) / S.img_per_g;
+    S.W = pairs * S.n_g;
+    if (S.G > S.W) S.G = S.W;
+    return S;
+}
+
 // Partition of the systems' units into work items for at most G_max resident CTAs; the partial
 // buffer needs max_contrib slots per tile.  `dev_tab` is the device copy of `sys`
 // (nullptr when there is one system).

@@ -11,10 +11,10 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("precision", ["fp32c", "ff"])
-def test_copy_wait_that_runs_out_is_reported_and_the_context_survives(precision):
+@pytest.mark.parametrize("precision,pairs", [("fp32c", "one-sided"), ("fp32c", "symmetric"), ("ff", "auto")])
+def test_copy_wait_that_runs_out_is_reported_and_the_context_survives(precision, pairs):
     s = W.config(1, small=True)
-    pc = B.PeriodicCoulomb(s.d, s.p, s.M, precision=precision)
+    pc = B.PeriodicCoulomb(s.d, s.p, s.M, precision=precision, pairs=pairs)
     try:
         x = torch.as_tensor(s.x, dtype=torch.float64, device="cuda")
         q = torch.as_tensor(s.q, dtype=torch.float64, device="cuda")

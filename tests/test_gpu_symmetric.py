@@ -1,0 +1,85 @@
+"""GPU parity of the symmetric charge kernel (PSUM_PAIRS_SYMMETRIC).
+
+The pair (i, j, p) and its mirror (j, i, -p) are one distance apart, so the kernel forms
+one offset and one 1/r for both and adds the source's terms (the reaction) as well as the
+target's; the tiles' pairs (a < b) each run once with every image of the block, a tile
+against itself runs one-sided.  It computes the same sums as the one-sided kernel in a
+different rounding order, so both are held to the FP32C bound (relative L2 error 1e-6,
+Eq. st2) against the FP64 oracle, and to each other.  The cases cover one to five tiles of
+512 charges, a last tile with a single charge, partly filled chunks, close dipole pairs
+(the float-float near units on both sides of a pair), a wider near block and every image
+grouping of the work items.
+"""
+import numpy as np
+import pytest
+
+from oracle import psum_oracle as O
+from paper_1310_4374_gb300 import binding as B
+from paper_1310_4374_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-6
+
+
+def _dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+def _run(s, pairs, K=(1, 1, 1)):
+    pc = B.PeriodicCoulomb(s.d, s.p, s.M, precision="fp32c", K=K, pairs=pairs)
+    try:
+        phi, g = pc(_dev(s.x), _dev(s.q))
+        return phi.cpu().numpy(), g.cpu().numpy()
+    finally:
+        pc.close()
+
+
+def _eps(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+CASES = [
+    ("one_tile_402", lambda: W.config(1, small=True), (1, 1, 1)),
+    ("two_tiles_513", lambda: W.uniform_gauss(N=513, d=(1.0, 1.5, 2.0), p=8, M=200, seed=5), (1, 1, 1)),
+    ("three_tiles_1300", lambda: W.uniform_gauss(N=1300, d=(1.0, 1.5, 2.0), p=12, M=400, seed=6), (1, 1, 1)),
+    ("cfg3_small_3001", lambda: W.config(3, small=True), (1, 1, 1)),
+    ("dipoles_2400", lambda: W.dipole_pairs(n_pairs=1200, d=(1.0, 1.0, 2.0), p=12, M=400, seed=7), (1, 1, 1)),
+    ("wide_block_1100", lambda: W.uniform_gauss(N=1100, d=(2.0, 1.0, 1.0), p=8, M=200, seed=8), (2, 1, 1)),
+]
+
+
+@pytest.mark.parametrize("name,make,K", CASES, ids=[c[0] for c in CASES])
+def test_symmetric_kernel_against_oracle_and_one_sided(name, make, K):
+    s = make()
+    phi_s, g_s = _run(s, "symmetric", K)
+    phi_o, g_o = _run(s, "one-sided", K)
+    ref = O.Plan(s.d, s.p, s.M, K=K).evaluate(s.x, s.q, mean="zero", parts=True)
+    for phi, g, what in ((phi_s, g_s, "symmetric"), (phi_o, g_o, "one-sided")):
+        e_phi, e_g = _eps(phi, ref["phi"]), _eps(g, ref["grad"])
+        assert e_phi < TOL and e_g < TOL, f"{name}/{what}: eps2 phi {e_phi:.3e}, grad {e_g:.3e}"
+    assert _eps(phi_s, phi_o) < TOL and _eps(g_s, g_o) < TOL
+
+
+def test_symmetric_kernel_is_deterministic():
+    s = W.uniform_gauss(N=2900, d=(1.0, 1.5, 2.0), p=8, M=200, seed=9)
+    pc = B.PeriodicCoulomb(s.d, s.p, s.M, precision="fp32c", pairs="symmetric")
+    try:
+        x, q = _dev(s.x), _dev(s.q)
+        phi0, g0 = pc(x, q)
+        for _ in range(3):
+            phi, g = pc(x, q)
+            assert torch.equal(phi, phi0) and torch.equal(g, g0)
+    finally:
+        pc.close()
+
+
+def test_automatic_choice_matches_the_forced_kernels():
+    # 16 tiles or more take the symmetric kernel automatically
+    s = W.uniform_gauss(N=16 * 512 + 77, d=(1.0, 1.5, 2.0), p=8, M=200, seed=10)
+    phi_a, g_a = _run(s, "auto")
+    phi_s, g_s = _run(s, "symmetric")
+    phi_o, g_o = _run(s, "one-sided")
+    assert np.array_equal(phi_a, phi_s) and np.array_equal(g_a, g_s)
+    assert _eps(phi_s, phi_o) < TOL and _eps(g_s, g_o) < TOL
