@@ -31,7 +31,12 @@ METRIC = "periodic Coulomb pair-interactions/s (pot+force) at 1e-6 rel err, FP32
 UNIT = "pairs/s"
 N_MAIN, D_MAIN, P_MAIN, M_MAIN, SEED_MAIN = 100_000, (1.0, 1.5, 2.0), 16, 800, 2
 N_FP64 = 20_000            # FP32C-vs-FP64 comparison runs on a 20k-charge system of the same box
-FP32_OPS_PAIR_GRAD = 13    # FP32-pipe instructions per potential+gradient pair (3 sub, 3 r^2, 4 phi/weight, 3 grad)
+FP32_OPS_PAIR_GRAD = 13    # FP32-pipe lane operations per potential+gradient pair, one-sided kernel
+                           # (3 sub, 3 r^2, 4 phi/weight, 3 grad)
+# symmetric kernel: per step a lane pairs its 4 targets with one source (8 ordered pairs,
+# both directions) in 37 packed f32x2 operations (74 lane operations: 3 sub, 3 r^2, 1 1/r^2,
+# 6 action and 5-6 reaction operations per target pair) and folds the reaction in 8 adds
+FP32_OPS_PAIR_SYM = 82 / 8
 FP32_OPS_PAIR_PHI = 7      # potential only (3 sub, 3 r^2, 1 fma)
 
 
@@ -53,6 +58,8 @@ def parse():
     ap.add_argument("--no-variants", action="store_true", help="skip the trimmed / RBF / Gauss-grid leg")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU budget of the oracle sample")
     ap.add_argument("--n", type=int, default=N_MAIN, help="charges (smaller cases are for profiling only)")
+    ap.add_argument("--pairs", default="auto", choices=["auto", "one-sided", "symmetric"],
+                    help="pair kernel of the charge sums (auto: symmetric from 16 tiles of 512 charges)")
     return ap.parse_args()
 
 
@@ -137,21 +144,27 @@ def measured_peaks():
         return {}
 
 
-def near_kernel_traffic(n_points):
+def near_kernel_traffic(n_points, kernel, image_groups):
     """DRAM bytes per launch of the charge near-field kernel from the committed ncu
-    summary (a smaller case): the read of the packed sources (which stay in L2) scales
-    with the number of points; the write of the partial sums is set by the number of
-    work items, which does not depend on N.  None if the kernel source has changed
-    since the counters were taken."""
+    summary of a smaller case: the read of the packed sources (which stay in L2) scales
+    with the number of points; the write of the partial sums scales with the number of
+    partial slots (symmetric kernel: tiles^2 x image groups, 16 KiB each).  None if the
+    record is for the other kernel or the kernel source has changed since the counters
+    were taken."""
     path = os.path.join(ROOT, "profiles", "near32_traffic.json")
     try:
         with open(path) as f:
             rec = json.load(f)
         with open(os.path.join(ROOT, "paper_1310_4374_gb300", "csrc", "near.cu"), "rb") as f:
             h = hashlib.sha256(f.read()).hexdigest()[:16]
-        if rec.get("near_cu_sha256_16") != h:
+        if rec.get("near_cu_sha256_16") != h or rec.get("pair_kernel") != kernel:
             return None
-        return rec["dram_read_bytes"] * n_points / rec["n_points"] + rec["dram_write_bytes"]
+        read = rec["dram_read_bytes"] * n_points / rec["n_points"]
+        if kernel == "symmetric":
+            tiles = (n_points + 511) // 512
+            slots, slots_rec = tiles * tiles * image_groups, rec["n_tiles"] ** 2 * rec["image_groups"]
+            return read + rec["dram_write_bytes"] * slots / slots_rec
+        return read + rec["dram_write_bytes"]
     except Exception:
         return None
 
@@ -181,7 +194,8 @@ def run_psum(args):
     # every rank evaluates its own replica of the system (weak scaling, no exchange)
     s = W.uniform_gauss(N=args.n, d=D_MAIN, p=P_MAIN, M=M_MAIN, seed=SEED_MAIN + rank)
     pairs_step = 27 * s.N * (s.N + 2 * s.M)
-    pc = B.PeriodicCoulomb(s.d, s.p, s.M, precision="fp32c")
+    pc = B.PeriodicCoulomb(s.d, s.p, s.M, precision="fp32c", pairs=args.pairs)
+    pair_kernel, image_groups = B.psum_pair_kernel(pc.plan, s.N)
     B.psum_profile(pc.plan, True)
     x = torch.as_tensor(s.x, dtype=torch.float64, device=dev)
     q = torch.as_tensor(s.q, dtype=torch.float64, device=dev)
@@ -232,14 +246,22 @@ def run_psum(args):
     peaks = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     peak_ops = props.multi_processor_count * 128 * sm_max * 1e6
-    achieved = FP32_OPS_PAIR_GRAD * near_pairs / (near_ms * 1e-3)
-    traffic = near_kernel_traffic(s.N)
-    roofline = {"bound": "alu", "kernel": "k_near32<grad>", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
+    sym = pair_kernel == "symmetric"
+    ops_pair = FP32_OPS_PAIR_SYM if sym else FP32_OPS_PAIR_GRAD
+    achieved = ops_pair * near_pairs / (near_ms * 1e-3)
+    traffic = near_kernel_traffic(s.N, pair_kernel, image_groups)
+    roofline = {"bound": "alu", "kernel": "k_near32s (symmetric pairs)" if sym else "k_near32<grad>",
+                "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
                 "unit": "T FP32-pipe ops/s", "frac": achieved / peak_ops, "traffic": traffic,
                 "peak_source": f"{props.multi_processor_count} SMs x 128 FP32 lanes x {sm_max:.0f} MHz "
                                "(sm_max_mhz of MEASURED_PEAKS.json)",
-                "ops_per_pair": FP32_OPS_PAIR_GRAD, "pairs_per_launch": near_pairs,
+                "ops_per_pair": ops_pair, "pairs_per_launch": near_pairs,
                 "kernel_ms": near_ms}
+    if sym:
+        # the same pair rate against the roof of the one-sided formulation (13 operations
+        # for each ordered pair): how far the shared offsets and 1/r carry past it
+        roofline["frac_of_one_sided_roof"] = FP32_OPS_PAIR_GRAD * near_pairs / (near_ms * 1e-3) / peak_ops
+        roofline["image_groups"] = image_groups
     if clk and clk.get("sm_mhz"):
         roofline["frac_at_observed_clock"] = achieved / (props.multi_processor_count * 128 * clk["sm_mhz"] * 1e6)
 
@@ -252,6 +274,8 @@ def run_psum(args):
                       "precision": "fp32c: f32 pair arithmetic on group-relative coordinates, two-sum "
                                    "compensated accumulation; f64 sort keys, fit, mean and far field",
                       "l2": "flushed before every timed step (256 MiB write, outside the events)",
+                      "pair_kernel": pair_kernel + (" (each mirror pair (i,j,p)/(j,i,-p) shares one offset "
+                                                    "and one 1/r)" if sym else ""),
                       "parallelism": f"{world} independent replicas" if world > 1 else "single GPU"},
            "solves_per_s": world * args.steps / (total_ms * 1e-3),
            "stages_ms": {k: statistics.mean(t[k] for t in stage_ms) for k in stage_ms[0]},

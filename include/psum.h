@@ -235,6 +235,12 @@ int psum_get_coeffs(psum_plan_t plan, double *C, void *stream);
 
 int psum_plan_info(psum_plan_t plan, psum_info *info);
 
+/* The pair kernel psum_eval runs for N charges on this plan, after the automatic choice:
+ * *kernel = PSUM_PAIRS_ONE_SIDED or PSUM_PAIRS_SYMMETRIC; *image_groups (may be NULL) = the
+ * symmetric kernel's image groups per tile pair (work items = tile pairs x groups), else 0.
+ * Host only; PSUM_ERR_ARG for a null plan or kernel pointer or N < 0. */
+int psum_pair_kernel(psum_plan_t plan, int64_t N, int *kernel, int *image_groups);
+
 /* Stage timing.  With profiling enabled, psum_eval records CUDA events on its
  * stream around each stage; psum_last_timings waits for `stream` and writes the
  * PSUM_NUM_STAGES durations (milliseconds) of the last evaluation:

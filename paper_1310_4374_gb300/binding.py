@@ -100,6 +100,7 @@ def load(build_if_needed: bool = True):
     lib.psum_sync.argtypes = [_vp, _vp]
     lib.psum_get_coeffs.argtypes = [_vp, _dp, _vp]
     lib.psum_plan_info.argtypes = [_vp, ctypes.POINTER(psum_info)]
+    lib.psum_pair_kernel.argtypes = [_vp, ctypes.c_int64, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
     lib.psum_profile.argtypes = [_vp, ctypes.c_int]
     lib.psum_last_timings.argtypes = [_vp, _dp, _vp]
     lib.psum_launch_count.argtypes = [_vp, ctypes.POINTER(ctypes.c_int64)]
@@ -119,7 +120,7 @@ def load(build_if_needed: bool = True):
     lib.psum_strerror.restype = ctypes.c_char_p
     for name in ("psum_plan_create", "psum_plan_create_ex", "psum_eval", "psum_eval_host", "psum_eval_noalloc",
                  "psum_sync",
-                 "psum_get_coeffs", "psum_plan_info", "psum_profile", "psum_last_timings", "psum_launch_count",
+                 "psum_get_coeffs", "psum_plan_info", "psum_pair_kernel", "psum_profile", "psum_last_timings", "psum_launch_count",
                  "psum_energy", "psum_energy_backward", "psum_eval_points", "psum_debug_inject_timeout", "psum_eval_graph", "psum_batch_create", "psum_batch_eval",
                  "psum_batch_sync", "psum_batch_get_coeffs", "psum_batch_get_info"):
         getattr(lib, name).restype = ctypes.c_int
@@ -276,6 +277,13 @@ def psum_plan_info(plan) -> dict:
     info = psum_info()
     _check(load().psum_plan_info(plan, ctypes.byref(info)), "psum_plan_info")
     return info.as_dict()
+
+
+def psum_pair_kernel(plan, N: int):
+    """(kernel, image_groups) psum_eval uses for N charges: kernel is "one-sided" or "symmetric"."""
+    k, g = ctypes.c_int(0), ctypes.c_int(0)
+    _check(load().psum_pair_kernel(plan, int(N), ctypes.byref(k), ctypes.byref(g)), "psum_pair_kernel")
+    return ("symmetric" if k.value == 2 else "one-sided"), g.value
 
 
 def psum_profile(plan, enable: bool = True):

@@ -671,6 +671,16 @@ int psum_plan_info(psum_plan_t h, psum_info* info) {
     return PSUM_OK;
 }
 
+int psum_pair_kernel(psum_plan_t h, int64_t N, int* kernel, int* image_groups) {
+    if (!h || !kernel || N < 0) return PSUM_ERR_ARG;
+    DeviceGuard g(h->pl.device);
+    Layout L{};
+    layout(h->pl, N, nullptr, L);
+    *kernel = L.sym ? PSUM_PAIRS_SYMMETRIC : PSUM_PAIRS_ONE_SIDED;
+    if (image_groups) *image_groups = L.sym ? L.S.n_g : 0;
+    return PSUM_OK;
+}
+
 int psum_debug_inject_timeout(psum_plan_t h, int enable) {
     if (!h) return PSUM_ERR_ARG;
     h->inject_timeout = enable != 0;

@@ -975,7 +975,7 @@ __global__ void __launch_bounds__(kThreads32, kMinB) k_near32s(Near32SymArgs a) 
 #pragma unroll 1
                 for (int g = 0; g < kNearChunk / 32; ++g) {
                     float rp = 0.f, rx = 0.f, ry = 0.f, rz = 0.f;
-#pragma unroll 4
+#pragma unroll 1
                     for (int k = 0; k < 32; k += 2) {
                         sym_far_step(s_hi, 32 * g + ((lane + k) & 31), nx, ny, nz, tq, aphi, agx, agy, agz, rp, rx,
                                      ry, rz);

@@ -382,7 +382,10 @@ struct NearSymLaunch {
 
 // Image groups: the fewest (1, 3, 9, ... up to one image per group) that give at least
 // kSymItemsPerCta items per resident CTA, so that the last items finish close together.
-constexpr int kSymItemsPerCta = 8;
+#ifndef PSUM_SYM_ITEMS_PER_CTA
+#define PSUM_SYM_ITEMS_PER_CTA 8
+#endif
+constexpr int kSymItemsPerCta = PSUM_SYM_ITEMS_PER_CTA;
 constexpr int64_t kSymMinTiles = 16;                          // automatic choice: at least 16 tiles
 constexpr size_t kSymMaxPartialBytes = (size_t)8 << 30;       // and a partial buffer of at most 8 GiB
 inline NearSymLaunch sym_partition(int64_t n_tiles, int64_t n_chunks, int n_img, int64_t G) {
