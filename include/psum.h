@@ -266,8 +266,10 @@ typedef struct psum_batch_info {
     int64_t units;       /* (tile, chunk, image) work units of the charge pair sum */
     int64_t pairs;       /* pair interactions of one evaluation (charges and check points) */
     int ctas;            /* CTAs of the persistent pair-sum launch */
-    int variant;         /* pair-kernel variant chosen by the autotuner */
-    double tuned_ms;     /* its measured time for one charge pair sum, ms (0 before tuning) */
+    int variant;         /* pair-kernel variant chosen by the autotuner: 0 and 1 the one-sided
+                            kernel at 4 and 6 CTAs per SM, 2 the symmetric kernel (FP32C) */
+    double tuned_ms;     /* its measured time for one charge pair sum and its reduction, ms
+                            (0 before tuning) */
 } psum_batch_info;
 
 /* B independent periodic systems evaluated together (algorithm "get" for each), with one

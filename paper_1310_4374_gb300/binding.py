@@ -370,8 +370,8 @@ def psum_batch_destroy(batch):
 class PeriodicBatch:
     """Many independent systems (each with its own plan) evaluated together."""
 
-    def __init__(self, systems, precision="fp32c", mean="zero"):
-        self.plans = [psum_plan_create_ex(s.d, s.p, s.M, precision, mean, getattr(s, "K", (1, 1, 1)))
+    def __init__(self, systems, precision="fp32c", mean="zero", pairs="auto"):
+        self.plans = [psum_plan_create_ex(s.d, s.p, s.M, precision, mean, getattr(s, "K", (1, 1, 1)), pairs=pairs)
                       for s in systems]
         self.P = [psum_plan_info(p)["P"] for p in self.plans]
         self.offsets = [0]

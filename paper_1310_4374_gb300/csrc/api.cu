@@ -110,13 +110,18 @@ size_t layout(Plan& pl, int64_t N, char* base, Layout& L, bool backward = false,
         const int pk = pl.opt.pair_kernel;
         if (pl.opt.precision == PSUM_FP32C && !sep && !trimmed && g_cap == 0 && pk != PSUM_PAIRS_ONE_SIDED &&
             (pk == PSUM_PAIRS_SYMMETRIC || L.n_tiles >= kSymMinTiles)) {
-            // image groups sized for the occupancy of the smallest group (the largest dynamic
-            // shared memory), then the partition for that group size
-            const int64_t gs = (int64_t)pl.num_sms * near32s_occupancy_ctas(n_img);
-            L.S = sym_partition(L.n_tiles, L.n_chunks, n_img, gs);
-            L.S.G = (int64_t)pl.num_sms * near32s_occupancy_ctas(L.S.img_per_g);
+            // image groups sized for the occupancy of the largest group (the largest dynamic
+            // shared memory), then the launch width for the chosen group size
+            std::vector<SymSys> one(1);
+            one[0].tile0 = 0;
+            one[0].n_tiles = L.n_tiles;
+            one[0].n_chunks = L.n_chunks;
+            one[0].shift0 = 0;
+            one[0].n_img = n_img;
+            L.S = sym_partition(one, (int64_t)pl.num_sms * near32s_occupancy_ctas(n_img));
+            L.S.G = (int64_t)pl.num_sms * near32s_occupancy_ctas(L.S.max_ipg);
             if (L.S.G > L.S.W) L.S.G = L.S.W;
-            L.sym = L.S.partial_doubles() * sizeof(double) <= kSymMaxPartialBytes;
+            L.sym = L.S.doubles * sizeof(double) <= kSymMaxPartialBytes;
         }
         L.xs = trimmed ? b.take<double>(3 * (size_t)L.n_src_pts) : nullptr;
         L.ka = b.take<uint32_t>(N);
@@ -138,7 +143,7 @@ size_t layout(Plan& pl, int64_t N, char* base, Layout& L, bool backward = false,
             L.tpk32lo = b.take<float4>(2 * (size_t)L.n_pts);
             L.torg = b.take<double>(4 * (size_t)n_groups);
         }
-        L.part_n = b.take<double>(L.sym ? L.S.partial_doubles() : (size_t)L.n_tiles * L.Ln.max_contrib * 4 * kTile32);
+        L.part_n = b.take<double>(L.sym ? L.S.doubles : (size_t)L.n_tiles * L.Ln.max_contrib * 4 * kTile32);
         L.part_c = b.take<double>((size_t)pl.n_check_tiles * L.Lc.max_contrib * kTile32);
         L.phi_c = b.take<double>((size_t)pl.n_check_tiles * kTile32);
     } else {
@@ -316,7 +321,7 @@ int queue_forward(psum_plan_s* h, int64_t N, const double* x, const double* q, d
     if (h->profile) TRY(cudaEventRecord(h->ev[3], st));
     const int tile = fp32 ? kTile32 : kTile64;
     if (L.sym)
-        TRY(launch_sym_reduce(L.part_n, N, L.S.n_tiles * L.S.n_g, L.phi_n, L.grad_n, st));
+        TRY(launch_sym_reduce(L.part_n, N, L.S, L.phi_n, L.grad_n, st));
     else
         TRY(launch_near_reduce(L.part_n, sep ? T : N, tile, 4, L.Ln, L.phi_n, L.grad_n, st));
     TRY(launch_near_reduce(L.part_c, pl.n_check, tile, 1, L.Lc, L.phi_c, nullptr, st));
@@ -677,7 +682,7 @@ int psum_pair_kernel(psum_plan_t h, int64_t N, int* kernel, int* image_groups) {
     Layout L{};
     layout(h->pl, N, nullptr, L);
     *kernel = L.sym ? PSUM_PAIRS_SYMMETRIC : PSUM_PAIRS_ONE_SIDED;
-    if (image_groups) *image_groups = L.sym ? L.S.n_g : 0;
+    if (image_groups) *image_groups = L.sym ? L.S.tab.one.n_g : 0;
     return PSUM_OK;
 }
 

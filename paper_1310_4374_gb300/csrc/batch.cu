@@ -288,8 +288,14 @@ struct psum_batch_s {
     double *f = nullptr, *C = nullptr, *val_part = nullptr, *mean_part = nullptr;
     int* d_status = nullptr;
     int* h_status = nullptr;
-    // schedule
+    // schedule: variants 0 .. kNear32Variants - 1 are the one-sided charge kernel's register
+    // budgets, variant kVariantSym the symmetric kernel (FP32C, partials within the cap)
     NearPlanLaunch Ln[kNear32Variants], Lc;
+    std::vector<SymSys> sym_sys;
+    SymSys* d_sym_sys = nullptr;
+    NearSymLaunch Ls;
+    bool sym_ok = false;
+    double* part_s = nullptr;
     int variant = -1;
     double tuned_ms = 0.0;
     int64_t units = 0, pairs = 0;
@@ -326,6 +332,8 @@ int cuda_st(cudaError_t e) {
         if (e_ != cudaSuccess) return cuda_st(e_);   \
     } while (0)
 
+constexpr int kVariantSym = kNear32Variants;
+
 // process-wide cache of autotuner decisions, keyed by the batch shape
 std::mutex g_tune_mu;
 std::map<std::pair<int64_t, int64_t>, int> g_tune_cache;
@@ -337,6 +345,7 @@ size_t batch_layout(psum_batch_s* bt, char* base) {
     bt->d_sys = b.take<BatchDev>(B);
     bt->d_near_n = b.take<NearSys>(B);
     bt->d_near_c = b.take<NearSys>(B);
+    bt->d_sym_sys = b.take<SymSys>(B);
     bt->d_seg_sys = b.take<int>(bt->n_seg);
     bt->d_seg_start = b.take<int64_t>(bt->n_seg);
     bt->d_grp_start = b.take<int64_t>(bt->n_groups);
@@ -365,6 +374,7 @@ size_t batch_layout(psum_batch_s* bt, char* base) {
     for (int v = 0; v < (fp32 ? kNear32Variants : 1); ++v) mc_n = std::max(mc_n, bt->Ln[v].max_contrib);
     bt->part_n = b.take<double>((size_t)bt->Ln[0].n_tiles * mc_n * 4 * tile);
     bt->part_c = b.take<double>((size_t)bt->Lc.n_tiles * bt->Lc.max_contrib * tile);
+    bt->part_s = bt->sym_ok ? b.take<double>(bt->Ls.doubles) : nullptr;
     bt->phi_n = b.take<double>(bt->n_pts);
     bt->grad_n = b.take<double>(3 * (size_t)bt->n_pts);
     bt->phi_c = b.take<double>(bt->n_chk_pts);
@@ -377,11 +387,14 @@ size_t batch_layout(psum_batch_s* bt, char* base) {
     bt->d_status = b.take<int>(B);
     int* counters = b.take<int>(2);            // work-item counters of the two pair launches
     for (int v = 0; v < kNear32Variants; ++v) bt->Ln[v].counter = counters;
+    bt->Ls.counter = counters;
     bt->Lc.counter = counters + 1;
     for (int v = 0; v < kNear32Variants; ++v) {
         bt->Ln[v].status = bt->d_status;
         bt->Ln[v].n_status = B;
     }
+    bt->Ls.status = bt->d_status;
+    bt->Ls.n_status = B;
     bt->Lc.status = bt->d_status;
     bt->Lc.n_status = B;
     return b.off + 256;
@@ -406,8 +419,11 @@ int queue_batch(psum_batch_s* bt, const double* x, const double* q, double* phi,
                                   bt->org, st));
         nl += 1 + 12 + 1;
         const bool ff = bt->precision == PSUM_FF;
-        BTRY(launch_near32(true, bt->pk_hi, bt->pk_lo, bt->org, bt->pk_hi, bt->pk_lo, bt->org, bt->d_shifts,
-                           bt->part_n, bt->Ln[variant], st, variant, nullptr, 0.0, ff));
+        if (variant == kVariantSym)
+            BTRY(launch_near32s(bt->pk_hi, bt->pk_lo, bt->org, bt->d_shifts, bt->part_s, bt->Ls, st));
+        else
+            BTRY(launch_near32(true, bt->pk_hi, bt->pk_lo, bt->org, bt->pk_hi, bt->pk_lo, bt->org, bt->d_shifts,
+                               bt->part_n, bt->Ln[variant], st, variant, nullptr, 0.0, ff));
         BTRY(launch_near32(false, bt->pk_hi, bt->pk_lo, bt->org, bt->d_chk_hi, bt->d_chk_lo, bt->d_chk_org,
                            bt->d_shifts, bt->part_c, bt->Lc, st, 0, nullptr, 0.0, ff));
     } else {
@@ -417,7 +433,11 @@ int queue_batch(psum_batch_s* bt, const double* x, const double* q, double* phi,
         BTRY(launch_near64(false, bt->pk64, bt->d_chk64, bt->d_shifts, bt->part_c, bt->Lc, st));
     }
     const int tile = fp32 ? kTile32 : kTile64;
-    BTRY(launch_near_reduce(bt->part_n, bt->n_pts, tile, 4, bt->Ln[fp32 ? variant : 0], bt->phi_n, bt->grad_n, st));
+    if (variant == kVariantSym)
+        BTRY(launch_sym_reduce(bt->part_s, bt->n_pts, bt->Ls, bt->phi_n, bt->grad_n, st));
+    else
+        BTRY(launch_near_reduce(bt->part_n, bt->n_pts, tile, 4, bt->Ln[fp32 ? variant : 0], bt->phi_n, bt->grad_n,
+                                st));
     BTRY(launch_near_reduce(bt->part_c, bt->n_chk_pts, tile, 1, bt->Lc, bt->phi_c, nullptr, st));
     nl += 4;
     int maxM = 1, maxP = 1;
@@ -444,7 +464,20 @@ int queue_batch(psum_batch_s* bt, const double* x, const double* q, double* phi,
 
 // time the charge pair-sum variants on the current (packed) inputs and keep the fastest
 int autotune(psum_batch_s* bt, cudaStream_t st) {
-    const std::pair<int64_t, int64_t> key(bt->units, (int64_t)bt->precision * 1000 + bt->B);
+    // the plans' pair_kernel options: all PSUM_PAIRS_SYMMETRIC forces the symmetric kernel,
+    // any PSUM_PAIRS_ONE_SIDED excludes it
+    bool all_sym = true, any_one = false;
+    for (const psum_plan_t p : bt->plans) {
+        all_sym = all_sym && p->pl.opt.pair_kernel == PSUM_PAIRS_SYMMETRIC;
+        any_one = any_one || p->pl.opt.pair_kernel == PSUM_PAIRS_ONE_SIDED;
+    }
+    const bool allow_sym = bt->sym_ok && !any_one;
+    if (allow_sym && all_sym) {
+        bt->variant = kVariantSym;
+        return PSUM_OK;
+    }
+    const std::pair<int64_t, int64_t> key(bt->units,
+                                          (int64_t)bt->precision * 1000 + bt->B + (allow_sym ? 1000000 : 0));
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tune_cache.find(key);
@@ -462,18 +495,27 @@ int autotune(psum_batch_s* bt, cudaStream_t st) {
     BTRY(cudaEventCreate(&e1));
     double best = 1e300;
     int best_v = 0;
-    for (int v = 0; v < kNear32Variants; ++v) {
+    // each variant's charge pair kernel and its reduction (the symmetric kernel's reduction
+    // reads more slots)
+    for (int v = 0; v <= kVariantSym; ++v) {
+        if (v == kVariantSym && !allow_sym) break;
         float ms = 0.f, tot = 0.f;
         for (int rep = 0; rep < 3; ++rep) {
             BTRY(cudaEventRecord(e0, st));
-            BTRY(launch_near32(true, bt->pk_hi, bt->pk_lo, bt->org, bt->pk_hi, bt->pk_lo, bt->org, bt->d_shifts,
-                               bt->part_n, bt->Ln[v], st, v));
+            if (v == kVariantSym) {
+                BTRY(launch_near32s(bt->pk_hi, bt->pk_lo, bt->org, bt->d_shifts, bt->part_s, bt->Ls, st));
+                BTRY(launch_sym_reduce(bt->part_s, bt->n_pts, bt->Ls, bt->phi_n, bt->grad_n, st));
+            } else {
+                BTRY(launch_near32(true, bt->pk_hi, bt->pk_lo, bt->org, bt->pk_hi, bt->pk_lo, bt->org, bt->d_shifts,
+                                   bt->part_n, bt->Ln[v], st, v));
+                BTRY(launch_near_reduce(bt->part_n, bt->n_pts, kTile32, 4, bt->Ln[v], bt->phi_n, bt->grad_n, st));
+            }
             BTRY(cudaEventRecord(e1, st));
             BTRY(cudaEventSynchronize(e1));
             BTRY(cudaEventElapsedTime(&ms, e0, e1));
             if (rep > 0) tot += ms;          // the first launch of each variant warms up
         }
-        bt->launches += 3;
+        bt->launches += 6;
         if (tot / 2 < best) {
             best = tot / 2;
             best_v = v;
@@ -548,6 +590,7 @@ int psum_batch_create(const psum_plan_t* plans, int B, const int64_t* offsets, p
     bt->sys.resize(B);
     bt->near_n.resize(B);
     bt->near_c.resize(B);
+    bt->sym_sys.resize(B);
     for (int b = 0; b < B; ++b) {
         const Plan& pl = plans[b]->pl;
         const int64_t n = offsets[b + 1] - offsets[b];
@@ -590,6 +633,13 @@ int psum_batch_create(const psum_plan_t* plans, int B, const int64_t* offsets, p
                                 near_chunk_stride(n_chunks)};
         bt->near_c[b] = NearSys{unit_c, tile_c, chk_tiles, n_chunks, pt / kNearChunk, shift0, pl.n_images,
                                 near_chunk_stride(n_chunks)};
+        SymSys ss{};
+        ss.tile0 = tile_n;
+        ss.n_tiles = n_tiles;
+        ss.n_chunks = n_chunks;
+        ss.shift0 = shift0;
+        ss.n_img = pl.n_images;
+        bt->sym_sys[b] = ss;
         unit_n += near_sys_units(bt->near_n[b]);
         unit_c += near_sys_units(bt->near_c[b]);
         tile_n += n_tiles;
@@ -622,6 +672,11 @@ int psum_batch_create(const psum_plan_t* plans, int B, const int64_t* offsets, p
                                                        : near64_occupancy_ctas());
         bt->Lc = near_partition(bt->near_c, gmax, nullptr, kCheckItemsPerCta);
     }
+    if (bt->precision == PSUM_FP32C) {
+        bt->Ls = sym_partition(bt->sym_sys, (int64_t)num_sms * near32s_occupancy_ctas(max_img));
+        bt->Ls.G = std::min<int64_t>((int64_t)num_sms * near32s_occupancy_ctas(bt->Ls.max_ipg), bt->Ls.W);
+        bt->sym_ok = bt->Ls.W > 0 && bt->Ls.doubles * sizeof(double) <= kSymMaxPartialBytes;
+    }
     int st = PSUM_OK;
     const size_t bytes = batch_layout(bt, nullptr);
     cudaError_t e = cudaMalloc(&bt->mem, bytes);
@@ -633,6 +688,7 @@ int psum_batch_create(const psum_plan_t* plans, int B, const int64_t* offsets, p
     if (B > 1) {
         for (int v = 0; v < kNear32Variants; ++v) bt->Ln[v].tab.many = bt->d_near_n;
         bt->Lc.tab.many = bt->d_near_c;
+        bt->Ls.tab.many = bt->d_sym_sys;
     }
     // ---- upload tables and concatenate the plans' check targets and image vectors ----
     auto up = [&](void* dst, const void* src, size_t n) -> int {
@@ -642,6 +698,7 @@ int psum_batch_create(const psum_plan_t* plans, int B, const int64_t* offsets, p
     if ((st = up(bt->d_sys, bt->sys.data(), sizeof(BatchDev) * B)) ||
         (st = up(bt->d_near_n, bt->near_n.data(), sizeof(NearSys) * B)) ||
         (st = up(bt->d_near_c, bt->near_c.data(), sizeof(NearSys) * B)) ||
+        (st = up(bt->d_sym_sys, bt->sym_sys.data(), sizeof(SymSys) * B)) ||
         (st = up(bt->d_seg_sys, seg_sys.data(), sizeof(int) * seg_sys.size())) ||
         (st = up(bt->d_seg_start, seg_start.data(), sizeof(int64_t) * seg_start.size())) ||
         (st = up(bt->d_grp_start, grp_start.data(), sizeof(int64_t) * grp_start.size())) ||
@@ -691,12 +748,13 @@ int psum_batch_eval(psum_batch_t bt, const double* x, const double* q, double* p
     DevGuard dg(bt->device);
     cudaStream_t st = (cudaStream_t)stream;
     if (bt->variant < 0) {
-        // first evaluation: run it plainly, then time the variants on its packed inputs
+        // first evaluation: run it plainly, then time the variants on its packed inputs; the
+        // outputs come from the chosen variant (the symmetric kernel rounds differently)
         int s = queue_batch(bt, x, q, phi, grad, st, 0);
         if (s != PSUM_OK) return s;
         s = autotune(bt, st);
         if (s != PSUM_OK) return s;
-        if (!use_graph) return PSUM_OK;
+        if (!use_graph && bt->variant == 0) return PSUM_OK;
     }
     if (!use_graph) return queue_batch(bt, x, q, phi, grad, st, bt->variant);
     const void* args[5] = {x, q, phi, grad, stream};
@@ -766,7 +824,7 @@ int psum_batch_get_info(psum_batch_t bt, psum_batch_info* info) {
     info->units = bt->units;
     info->pairs = bt->pairs;
     const int v = bt->variant < 0 ? 0 : bt->variant;
-    info->ctas = (int)bt->Ln[v].G;
+    info->ctas = (int)(v == kVariantSym ? bt->Ls.G : bt->Ln[v].G);
     info->variant = bt->variant;
     info->tuned_ms = bt->tuned_ms;
     return PSUM_OK;

@@ -17,7 +17,7 @@ cudaError_t launch_near_reduce(const double* partial, int64_t n_valid, int tile_
 int near32_occupancy_ctas(int n_img, int variant = 0, bool trimmed = false, bool ff = false);
 cudaError_t launch_near32s(const float4* pk_hi, const float4* pk_lo, const double* org, const double* shifts,
                            double* partial, const NearSymLaunch& S, cudaStream_t st);
-cudaError_t launch_sym_reduce(const double* partial, int64_t n_valid, int64_t n_slots, double* out_phi,
+cudaError_t launch_sym_reduce(const double* partial, int64_t n_valid, const NearSymLaunch& S, double* out_phi,
                               double* out_grad, cudaStream_t st);
 int near32s_occupancy_ctas(int img_per_g);
 constexpr int kNear32Variants = 2;

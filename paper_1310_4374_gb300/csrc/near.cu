@@ -690,11 +690,11 @@ struct Near32SymArgs {
     const float4* pk_hi;     // the charges' pack: 2 float4 per point, (x,x,y,y),(z,z,q,q) offsets
     const float4* pk_lo;     // their float32 rounding remainders
     const double* org;       // 4 per group of 128 points: origin x, y, z and radius
-    const double* shifts;    // image vectors, 3 per image
-    double* partial;         // [n_tiles][n_tiles * n_g][4][kTile32]
-    int64_t n_tiles, n_chunks;
-    int n_img, n_g, img_per_g;
-    int64_t W;               // items: n_tiles (n_tiles + 1) / 2 * n_g
+    const double* shifts;    // image vectors, 3 per image, systems one after another
+    double* partial;         // per system [n_tiles][n_tiles * n_g][4][kTile32] from part0
+    SymSysTable tab;
+    int64_t W;               // work items of all systems
+    int max_ipg;             // largest images per group (shared-memory layout)
     int* counter;
     int* status;
     int n_status;
@@ -819,7 +819,7 @@ __global__ void __launch_bounds__(kThreads32, kMinB) k_near32s(Near32SymArgs a) 
     // [img_per_g] unit classes
     auto s_re = reinterpret_cast<float (*)[4][2][kNearChunk]>(s_dyn4);
     float* s_delta = (float*)s_dyn4 + kWarps * 4 * 2 * kNearChunk;
-    int* s_near = (int*)(s_delta + 6 * kTgt32 * a.img_per_g);
+    int* s_near = (int*)(s_delta + 6 * kTgt32 * a.max_ipg);
     __shared__ int s_item;
     __shared__ int s_fail;
     __shared__ __align__(8) uint64_t s_bar;
@@ -833,7 +833,6 @@ __global__ void __launch_bounds__(kThreads32, kMinB) k_near32s(Near32SymArgs a) 
         s_fail = 0;
     }
     __syncthreads();
-    const int64_t n_slots = a.n_tiles * a.n_g;
 
     for (;;) {
     if (tid == 0) s_item = atomicAdd(a.counter, 1);
@@ -841,20 +840,24 @@ __global__ void __launch_bounds__(kThreads32, kMinB) k_near32s(Near32SymArgs a) 
     const int64_t item = s_item;
     __syncthreads();                     // every thread has the item before s_item changes
     if (item >= a.W) break;
-    const int64_t pair = item / a.n_g;
-    const int gi = (int)(item - pair * a.n_g);
-    // pair = tb (tb + 1) / 2 + ta, ta <= tb
+    const SymSys S = a.tab.many ? a.tab.many[sym_sys_by_item(a.tab, item)] : a.tab.one;
+    const int64_t local = item - S.item0;
+    const int64_t pair = local / S.n_g;
+    const int gi = (int)(local - pair * S.n_g);
+    // pair = tb (tb + 1) / 2 + ta, ta <= tb (tiles of the system)
     int64_t tb = (int64_t)((sqrt(8.0 * (double)pair + 1.0) - 1.0) * 0.5);
     while (tb > 0 && tb * (tb + 1) / 2 > pair) --tb;
     while ((tb + 1) * (tb + 2) / 2 <= pair) ++tb;
     const int64_t ta = pair - tb * (tb + 1) / 2;
     const bool diag = ta == tb;
-    const int im0 = gi * a.img_per_g;
-    const int nimg = min(a.img_per_g, a.n_img - im0);
+    const int64_t TA = S.tile0 + ta;     // global tiles
+    const int64_t n_slots = S.n_tiles * S.n_g;
+    const int im0 = gi * S.img_per_g;
+    const int nimg = min(S.img_per_g, S.n_img - im0);
     // targets of tile ta; zero the action sums
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
-        const int64_t i0 = (ta * kTgt32 + 2 * j) * kGroup + tid;
+        const int64_t i0 = (TA * kTgt32 + 2 * j) * kGroup + tid;
         const int64_t i1 = i0 + kGroup;
         const float4 A0 = a.pk_hi[2 * i0], B0 = a.pk_hi[2 * i0 + 1];
         const float4 A1 = a.pk_hi[2 * i1], B1 = a.pk_hi[2 * i1 + 1];
@@ -865,8 +868,9 @@ __global__ void __launch_bounds__(kThreads32, kMinB) k_near32s(Near32SymArgs a) 
 #pragma unroll
         for (int qi = 0; qi < 4; ++qi) s_acc[qi][j][0][tid] = s_acc[qi][j][1][tid] = make_float2(0.f, 0.f);
     }
-    const int64_t c0 = tb * kTgt32;
-    const int64_t c1 = c0 + kTgt32 < a.n_chunks ? c0 + kTgt32 : a.n_chunks;
+    // the source chunks of tile tb (global group indices)
+    const int64_t c0 = (S.tile0 + tb) * kTgt32;
+    const int64_t c1 = c0 + (tb * kTgt32 + kTgt32 < S.n_chunks ? kTgt32 : S.n_chunks - tb * kTgt32);
     for (int64_t chunk = c0; chunk < c1; ++chunk) {
         __syncthreads();   // every thread is done with the previous chunk, deltas, classes and reactions
         // this warp's reaction sums for the chunk start at zero (private to the warp until the
@@ -883,10 +887,10 @@ __global__ void __launch_bounds__(kThreads32, kMinB) k_near32s(Near32SymArgs a) 
         }
         const double* so = a.org + 4 * chunk;
         for (int im = tid; im < nimg; im += kThreads32) {
-            const double* sh = a.shifts + 3 * (im0 + im);
+            const double* sh = a.shifts + 3 * (S.shift0 + im0 + im);
             int nr = 0;
             for (int k = 0; k < kTgt32; ++k) {
-                const double* to = a.org + 4 * (ta * kTgt32 + k);
+                const double* to = a.org + 4 * (TA * kTgt32 + k);
                 const double D0 = (to[0] - so[0]) - sh[0], D1 = (to[1] - so[1]) - sh[1], D2 = (to[2] - so[2]) - sh[2];
                 float* dl = s_delta + 6 * (im * kTgt32 + k);
                 dl[0] = (float)D0; dl[1] = (float)D1; dl[2] = (float)D2;
@@ -931,7 +935,7 @@ __global__ void __launch_bounds__(kThreads32, kMinB) k_near32s(Near32SymArgs a) 
                         two_sum_acc2(s_acc[3][j][0][tid], s_acc[3][j][1][tid], agz[0]);
                         continue;
                     }
-                    const int64_t i0 = (ta * kTgt32 + 2 * j) * kGroup + tid;
+                    const int64_t i0 = (TA * kTgt32 + 2 * j) * kGroup + tid;
                     const int64_t i1 = i0 + kGroup;
                     const float4 C0 = a.pk_lo[2 * i0], D0 = a.pk_lo[2 * i0 + 1];
                     const float4 C1 = a.pk_lo[2 * i1], D1 = a.pk_lo[2 * i1 + 1];
@@ -1011,7 +1015,7 @@ __global__ void __launch_bounds__(kThreads32, kMinB) k_near32s(Near32SymArgs a) 
                 for (int j = 0; j < 2; ++j) {
                     const float* d0 = dl + 6 * (2 * j);
                     const float* d1 = dl + 6 * (2 * j + 1);
-                    const int64_t i0 = (ta * kTgt32 + 2 * j) * kGroup + tid;
+                    const int64_t i0 = (TA * kTgt32 + 2 * j) * kGroup + tid;
                     const int64_t i1 = i0 + kGroup;
                     const float4 C0 = a.pk_lo[2 * i0], D0 = a.pk_lo[2 * i0 + 1];
                     const float4 C1 = a.pk_lo[2 * i1], D1 = a.pk_lo[2 * i1 + 1];
@@ -1066,7 +1070,8 @@ __global__ void __launch_bounds__(kThreads32, kMinB) k_near32s(Near32SymArgs a) 
             // the chunk's reaction: the warps' sums in a fixed order, into slot (tb, ta, gi) at
             // the chunk's positions in tile tb (the field with the reaction's sign)
             __syncthreads();
-            double* dst = a.partial + ((tb * n_slots + ta * a.n_g + gi) * 4) * kTile32 + (chunk - c0) * kNearChunk;
+            double* dst = a.partial + S.part0 + ((tb * n_slots + ta * S.n_g + gi) * 4) * kTile32 +
+                          (chunk - c0) * kNearChunk;
             for (int s = tid; s < kNearChunk; s += kThreads32) {
 #pragma unroll
                 for (int qi = 0; qi < 4; ++qi) {
@@ -1078,9 +1083,18 @@ __global__ void __launch_bounds__(kThreads32, kMinB) k_near32s(Near32SymArgs a) 
             }
         }
     }
+    // positions of tile tb past its last chunk (padding) get zero reactions, so that every
+    // slot is defined
+    if (!diag)
+        for (int64_t c = c1; c < c0 + kTgt32; ++c) {
+            double* dst = a.partial + S.part0 + ((tb * n_slots + ta * S.n_g + gi) * 4) * kTile32 + (c - c0) * kNearChunk;
+            for (int s = tid; s < kNearChunk; s += kThreads32)
+#pragma unroll
+                for (int qi = 0; qi < 4; ++qi) dst[qi * kTile32 + s] = 0.0;
+        }
     // the action on tile ta: slot (ta, tb, gi)
     {
-        double* dst = a.partial + ((ta * n_slots + tb * a.n_g + gi) * 4) * kTile32;
+        double* dst = a.partial + S.part0 + ((ta * n_slots + tb * S.n_g + gi) * 4) * kTile32;
 #pragma unroll
         for (int qi = 0; qi < 4; ++qi)
 #pragma unroll
@@ -1249,23 +1263,32 @@ __global__ void __launch_bounds__(32 * kReduceWarps) k_near_reduce(const double*
     }
 }
 
-// Reduction of the symmetric kernel's slots: target i (packed order, i < n_valid) of tile
-// t adds slots 0 .. n_slots - 1 of row t; a block takes 32 consecutive targets and one
-// quantity, its 8 warps every 8th slot, combined in a fixed order.
+// Reduction of the symmetric kernel's slots: target i (packed order, i < n_valid) in tile t
+// of its system adds that system's slots 0 .. n_tiles n_g - 1 of row t; a block takes 32
+// consecutive targets (one tile) and one quantity, its 8 warps every 8th slot, combined in a
+// fixed order.
 __global__ void __launch_bounds__(32 * kReduceWarps) k_sym_reduce(const double* __restrict__ partial, int64_t n_valid,
-                                                                 int64_t n_slots, double* __restrict__ out_phi,
+                                                                 SymSysTable tab, double* __restrict__ out_phi,
                                                                  double* __restrict__ out_grad) {
     __shared__ double s_part[kReduceWarps][32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int qi = blockIdx.y;
     const int64_t i0 = (int64_t)blockIdx.x * 32;
     const int64_t i = i0 + lane;
-    const int64_t tile = i0 / kTile32;
-    const int loc = (int)(i - tile * kTile32);
+    const int64_t T = i0 / kTile32;
+    int64_t tile0 = tab.one.tile0, n_slots = tab.one.n_tiles * tab.one.n_g, part0 = tab.one.part0;
+    if (tab.many) {
+        const SymSys& S = tab.many[sym_sys_by_tile(tab, T)];
+        tile0 = S.tile0;
+        n_slots = S.n_tiles * S.n_g;
+        part0 = S.part0;
+    }
+    const int64_t tile = T - tile0;
+    const int loc = (int)(i - T * kTile32);
+    const double* base = partial + part0 + (tile * n_slots * 4 + qi) * kTile32 + loc;
     double acc = 0.0;
     if (i < n_valid)
-        for (int64_t s = warp; s < n_slots; s += kReduceWarps)
-            acc += partial[((tile * n_slots + s) * 4 + qi) * kTile32 + loc];
+        for (int64_t s = warp; s < n_slots; s += kReduceWarps) acc += base[s * 4 * kTile32];
     s_part[warp][lane] = acc;
     __syncthreads();
     if (warp == 0 && i < n_valid) {
@@ -1347,18 +1370,17 @@ cudaError_t near32s_allow_smem() {
 
 cudaError_t launch_near32s(const float4* pk_hi, const float4* pk_lo, const double* org, const double* shifts,
                            double* partial, const NearSymLaunch& S, cudaStream_t st) {
-    if (!S.counter || !S.status || S.n_status < 1 || S.img_per_g < 1) return cudaErrorInvalidValue;
+    if (!S.counter || !S.status || S.n_status < 1 || S.max_ipg < 1) return cudaErrorInvalidValue;
     if (S.W <= 0) return cudaSuccess;
     const cudaError_t ea = near32s_allow_smem();
     if (ea != cudaSuccess) return ea;
     Near32SymArgs a;
     a.pk_hi = pk_hi; a.pk_lo = pk_lo; a.org = org; a.shifts = shifts; a.partial = partial;
-    a.n_tiles = S.n_tiles; a.n_chunks = S.n_chunks;
-    a.n_img = S.n_img; a.n_g = S.n_g; a.img_per_g = S.img_per_g;
-    a.W = S.W; a.counter = S.counter; a.status = S.status; a.n_status = S.n_status; a.inject = S.inject;
+    a.tab = S.tab; a.W = S.W; a.max_ipg = S.max_ipg;
+    a.counter = S.counter; a.status = S.status; a.n_status = S.n_status; a.inject = S.inject;
     const cudaError_t e = cudaMemsetAsync(S.counter, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
-    k_near32s<kNear32sMinBlocks><<<(unsigned)S.G, kThreads32, near32s_dyn_smem(S.img_per_g), st>>>(a);
+    k_near32s<kNear32sMinBlocks><<<(unsigned)S.G, kThreads32, near32s_dyn_smem(S.max_ipg), st>>>(a);
     return cudaGetLastError();
 }
 
@@ -1370,11 +1392,11 @@ int near32s_occupancy_ctas(int img_per_g) {
     return nb < 1 ? 1 : nb;
 }
 
-cudaError_t launch_sym_reduce(const double* partial, int64_t n_valid, int64_t n_slots, double* out_phi,
+cudaError_t launch_sym_reduce(const double* partial, int64_t n_valid, const NearSymLaunch& S, double* out_phi,
                               double* out_grad, cudaStream_t st) {
     if (n_valid <= 0) return cudaSuccess;
     const dim3 grid((unsigned)((n_valid + 31) / 32), 4u);
-    k_sym_reduce<<<grid, 32 * kReduceWarps, 0, st>>>(partial, n_valid, n_slots, out_phi, out_grad);
+    k_sym_reduce<<<grid, 32 * kReduceWarps, 0, st>>>(partial, n_valid, S.tab, out_phi, out_grad);
     return cudaGetLastError();
 }
 

@@ -367,42 +367,103 @@ struct NearPlanLaunch {
     NearSysTable tab;
 };
 
-// The symmetric charge kernel (one system, FP32C, block image set): work items are (tile
-// pair (a <= b), group of images); the partial buffer holds n_tiles x (n_tiles n_g) slots.
+// The symmetric charge kernel (FP32C, block image sets): work items are (system, tile pair
+// (a <= b), group of images); a system's partial block holds n_tiles x (n_tiles n_g) slots of
+// 4 x kTile32 doubles.  The targets are the system's charges, packed in whole tiles from
+// global tile tile0 (groups 4 tile0 ..); its source chunks are the first n_chunks groups.
+struct SymSys {
+    int64_t item0;            // first work item
+    int64_t tile0;            // first (global) tile
+    int64_t n_tiles, n_chunks;
+    int64_t part0;            // first double of the system's partial block
+    int shift0, n_img;        // image vectors shift0 .. shift0 + n_img - 1
+    int n_g, img_per_g;       // image groups per tile pair and images per group
+};
+struct SymSysTable {
+    SymSys one;
+    const SymSys* many;       // nullptr: the launch has the single system `one`
+    int n;
+};
+
+__host__ __device__ __forceinline__ int64_t sym_sys_items(const SymSys& s) {
+    return s.n_tiles * (s.n_tiles + 1) / 2 * s.n_g;
+}
+__host__ __device__ __forceinline__ size_t sym_sys_doubles(const SymSys& s) {
+    return (size_t)s.n_tiles * (size_t)s.n_tiles * (size_t)s.n_g * 4 * kTile32;
+}
+
 struct NearSymLaunch {
-    int64_t n_tiles = 0, n_chunks = 0;
-    int n_img = 0, n_g = 0, img_per_g = 0;
+    SymSysTable tab{};
     int64_t W = 0, G = 0;          // work items, resident CTAs
+    int max_ipg = 0;               // largest images per group (shared-memory sizing)
+    size_t doubles = 0;            // partial buffer
     int* counter = nullptr;
     int* status = nullptr;
     int n_status = 0;
     int inject = 0;
-    size_t partial_doubles() const { return (size_t)n_tiles * (size_t)n_tiles * (size_t)n_g * 4 * kTile32; }
 };
 
 // Image groups: the fewest (1, 3, 9, ... up to one image per group) that give at least
-// kSymItemsPerCta items per resident CTA, so that the last items finish close together.
+// kSymItemsPerCta items per resident CTA over all systems, so that the last items finish
+// close together.
 #ifndef PSUM_SYM_ITEMS_PER_CTA
 #define PSUM_SYM_ITEMS_PER_CTA 8
 #endif
 constexpr int kSymItemsPerCta = PSUM_SYM_ITEMS_PER_CTA;
 constexpr int64_t kSymMinTiles = 16;                          // automatic choice: at least 16 tiles
 constexpr size_t kSymMaxPartialBytes = (size_t)8 << 30;       // and a partial buffer of at most 8 GiB
-inline NearSymLaunch sym_partition(int64_t n_tiles, int64_t n_chunks, int n_img, int64_t G) {
+
+// `sys` holds tile0, n_tiles, n_chunks, shift0 and n_img of every system; the rest is filled
+// here.  G is the number of resident CTAs.
+inline NearSymLaunch sym_partition(std::vector<SymSys>& sys, int64_t G) {
     NearSymLaunch S;
-    S.n_tiles = n_tiles;
-    S.n_chunks = n_chunks;
-    S.n_img = n_img;
-    S.G = G;
-    const int64_t pairs = n_tiles * (n_tiles + 1) / 2;
+    int64_t pairs = 0;
+    int max_img = 1;
+    for (const SymSys& s : sys) {
+        pairs += s.n_tiles * (s.n_tiles + 1) / 2;
+        max_img = s.n_img > max_img ? s.n_img : max_img;
+    }
     int ng = 1;
-    while (ng < n_img && pairs * ng < kSymItemsPerCta * G) ng *= 3;
-    if (ng > n_img) ng = n_img;
-    S.img_per_g = (n_img + ng - 1) / ng;
-    S.n_g = (n_img + S.img_per_g - 1) / S.img_per_g;
-    S.W = pairs * S.n_g;
-    if (S.G > S.W) S.G = S.W;
+    while (ng < max_img && pairs * ng < kSymItemsPerCta * G) ng *= 3;
+    int64_t item = 0;
+    size_t part = 0;
+    for (SymSys& s : sys) {
+        const int g = ng < s.n_img ? ng : s.n_img;
+        s.img_per_g = (s.n_img + g - 1) / g;
+        s.n_g = (s.n_img + s.img_per_g - 1) / s.img_per_g;
+        s.item0 = item;
+        s.part0 = (int64_t)part;
+        item += sym_sys_items(s);
+        part += sym_sys_doubles(s);
+        S.max_ipg = s.img_per_g > S.max_ipg ? s.img_per_g : S.max_ipg;
+    }
+    S.W = item;
+    S.doubles = part;
+    S.G = G < S.W ? G : S.W;
+    S.tab.one = sys.empty() ? SymSys{} : sys[0];
+    S.tab.many = nullptr;
+    S.tab.n = (int)sys.size();
     return S;
+}
+
+__device__ __forceinline__ int sym_sys_by_item(const SymSysTable& t, int64_t item) {
+    if (!t.many) return 0;
+    int lo = 0, hi = t.n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (t.many[mid].item0 <= item) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ int sym_sys_by_tile(const SymSysTable& t, int64_t T) {
+    if (!t.many) return 0;
+    int lo = 0, hi = t.n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (t.many[mid].tile0 <= T) lo = mid; else hi = mid - 1;
+    }
+    return lo;
 }
 
 // Partition of the systems' units into work items for at most G_max resident CTAs; the partial

@@ -53,14 +53,19 @@ def test_batch_matches_oracle_per_system(precision, use_graph):
         pb.close()
 
 
-def test_batch_agrees_with_single_evaluations():
+@pytest.mark.parametrize("pairs", ["one-sided", "symmetric"])
+def test_batch_agrees_with_single_evaluations(pairs):
+    # the plans' pair_kernel option steers the autotuner: symmetric plans force the
+    # symmetric kernel, one-sided plans exclude it
     systems = W.config(4, small=True)
-    pb = B.PeriodicBatch(systems, precision="fp32c")
+    pb = B.PeriodicBatch(systems, precision="fp32c", pairs=pairs)
     try:
         x, q = _cat(systems)
         phi, g = pb(x, q)
+        v = B.psum_batch_get_info(pb.batch)["variant"]
+        assert (v == 2) if pairs == "symmetric" else (v in (0, 1))
         for b, s in enumerate(systems):
-            pc = B.PeriodicCoulomb(s.d, s.p, s.M, precision="fp32c", K=s.K)
+            pc = B.PeriodicCoulomb(s.d, s.p, s.M, precision="fp32c", K=s.K, pairs=pairs)
             try:
                 p1, g1 = pc(torch.as_tensor(s.x, device="cuda"), torch.as_tensor(s.q, device="cuda"))
             finally:
