@@ -38,6 +38,8 @@ FP32_OPS_PAIR_GRAD = 13    # FP32-pipe lane operations per potential+gradient pa
 # 6 action and 5-6 reaction operations per target pair) and folds the reaction in 8 adds
 FP32_OPS_PAIR_SYM = 82 / 8
 FP32_OPS_PAIR_PHI = 7      # potential only (3 sub, 3 r^2, 1 fma)
+FP64_OPS_PAIR = 19         # float64 kernel, one-sided
+FP64_OPS_PAIR_SYM = 12     # float64 kernel, symmetric
 
 
 def workload_name(N=N_MAIN):
@@ -364,10 +366,24 @@ def fp64_leg(args):
             raise B.PsumError(st, "fp64 leg")
         ms = ev0.elapsed_time(ev1) / reps
         near_ms = B.psum_last_timings(pc.plan)["near_charges"]
+        kernel = B.psum_pair_kernel(pc.plan, s.N)[0]
         pc.close()
         pairs = 27 * s.N * (s.N + 2 * s.M)
+        near_rate = 27 * s.N * s.N / (near_ms * 1e-3)
         res[prec] = {"pairs_per_s": pairs / (ms * 1e-3), "ms_per_step": ms,
-                     "near_charges_pairs_per_s": 27 * s.N * s.N / (near_ms * 1e-3)}
+                     "near_charges_pairs_per_s": near_rate, "pair_kernel": kernel}
+        if prec == "fp64":
+            # float64 lane operations per ordered pair: one-sided 3 offset, 3 r^2, 5 rsqrt
+            # refinement, 1 q/r, 1 sum, 2 weight, 3 field; symmetric per mirror pair 3 + 3 + 5
+            # + 1 (1/r^2) shared and 6 per direction, 24 for two ordered pairs
+            ops = FP64_OPS_PAIR_SYM if kernel == "symmetric" else FP64_OPS_PAIR
+            props = torch.cuda.get_device_properties(x.device)
+            peak = props.multi_processor_count * 2 * float(measured_peaks().get("sm_max_mhz", 2070.0)) * 1e6
+            res[prec]["roofline"] = {"bound": "alu", "kernel": "k_near64s" if kernel == "symmetric" else "k_near64",
+                                     "ops_per_pair": ops, "achieved": ops * near_rate / 1e12, "peak": peak / 1e12,
+                                     "unit": "T FP64-pipe ops/s", "frac": ops * near_rate / peak,
+                                     "peak_source": "SMs x 2 FP64 lanes x sm_max_mhz (nominal 1.25 TFLOP/s FP64; "
+                                                    "1.90 DFMA/clk/SM measured)"}
         outs[prec] = (phi.cpu().numpy(), g.cpu().numpy())
     import numpy as np
 

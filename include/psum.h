@@ -80,14 +80,14 @@ extern "C" {
 #define PSUM_BASIS_RBF       1  /* kernel functions 1/|y - x_t| centred outside S_b (Eq. 5); P = n_rbf + 1 */
 
 /* pair kernel of the near sum at the charges (psum_opts.pair_kernel) */
-#define PSUM_PAIRS_AUTO       0  /* symmetric where it applies and the system has at least 16 tiles of 512
-                                    charges, one-sided otherwise */
+#define PSUM_PAIRS_AUTO       0  /* symmetric where it applies and the system has at least 8192 charges
+                                    (FP32C: 16 tiles of 512, FP64: 64 tiles of 128), one-sided otherwise */
 #define PSUM_PAIRS_ONE_SIDED  1  /* every (target, source, image) term computed on its own */
 #define PSUM_PAIRS_SYMMETRIC  2  /* where it applies, at any size: the pair (i, j, p) and its mirror
-                                    (j, i, -p) share one offset and one 1/r (FP32C plans without ball
-                                    trimming, potential and field at the charges, psum_eval,
-                                    psum_eval_host, psum_eval_graph and psum_energy; one-sided
-                                    elsewhere).  Same sums, different rounding order. */
+                                    (j, i, -p) share one offset and one 1/r (FP32C and FP64 plans without
+                                    ball trimming, potential and field at the charges, psum_eval,
+                                    psum_eval_host, psum_eval_graph and psum_energy, and FP32C batches;
+                                    one-sided elsewhere).  Same sums, different rounding order. */
 
 #define PSUM_MEAN_ZERO 0  /* C_1 makes the box mean of phi zero (Eq. pfx3, phi_mean = 0) */
 #define PSUM_MEAN_NONE 1  /* C_1 = 0 (potential defined up to a constant, Sec. 3) */

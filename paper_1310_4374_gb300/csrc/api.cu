@@ -147,7 +147,6 @@ size_t layout(Plan& pl, int64_t N, char* base, Layout& L, bool backward = false,
         L.part_c = b.take<double>((size_t)pl.n_check_tiles * L.Lc.max_contrib * kTile32);
         L.phi_c = b.take<double>((size_t)pl.n_check_tiles * kTile32);
     } else {
-        L.sym = false;
         L.n_tiles = (NT + kTile64 - 1) / kTile64;
         L.n_chunks = (N + kTile64 - 1) / kTile64;
         L.n_pts = L.n_tiles * kTile64;
@@ -157,13 +156,27 @@ size_t layout(Plan& pl, int64_t N, char* base, Layout& L, bool backward = false,
         if (g_cap > 0 && gmax > g_cap) gmax = g_cap;
         L.Ln = near_partition(L.n_tiles, L.n_chunks, n_img, gmax, ipc);
         L.Lc = near_partition(pl.n_check_tiles, L.n_chunks, n_img, gmax, g_cap > 0 ? 1 : kCheckItemsPerCta);
+        // the symmetric float64 kernel: charges, block image set, a normal (growing) scratch
+        L.sym = false;
+        const int pk = pl.opt.pair_kernel;
+        if (!sep && !(pl.Rb > 0.0) && g_cap == 0 && pk != PSUM_PAIRS_ONE_SIDED &&
+            (pk == PSUM_PAIRS_SYMMETRIC || L.n_tiles >= kSymMinTiles64)) {
+            std::vector<SymSys> one(1);
+            one[0].tile0 = 0;
+            one[0].n_tiles = L.n_tiles;
+            one[0].n_chunks = L.n_chunks;
+            one[0].shift0 = 0;
+            one[0].n_img = n_img;
+            L.S = sym_partition(one, (int64_t)pl.num_sms * near64s_occupancy_ctas(), kTile64);
+            L.sym = L.S.doubles * sizeof(double) <= kSymMaxPartialBytes;
+        }
         L.ka = L.va = L.kb = L.vb = L.hist = nullptr;
         L.pk32 = L.pk32lo = nullptr;
         L.org = nullptr;
         L.xs = nullptr;
         L.pk64 = b.take<double4_32a>((size_t)L.n_src_pts);
         if (sep) L.tpk64 = b.take<double4_32a>((size_t)L.n_pts);
-        L.part_n = b.take<double>((size_t)L.n_tiles * L.Ln.max_contrib * 4 * kTile64);
+        L.part_n = b.take<double>(L.sym ? L.S.doubles : (size_t)L.n_tiles * L.Ln.max_contrib * 4 * kTile64);
         L.part_c = b.take<double>((size_t)pl.n_check_tiles * L.Lc.max_contrib * kTile64);
         L.phi_c = b.take<double>((size_t)pl.n_check_tiles * kTile64);
     }
@@ -296,10 +309,12 @@ int queue_forward(psum_plan_s* h, int64_t N, const double* x, const double* q, d
     const double* tor = sep ? L.torg : L.org;
     const double4_32a* t64 = sep ? L.tpk64 : L.pk64;
     if (h->profile) TRY(cudaEventRecord(h->ev[1], st));
-    if (L.sym) {
+    if (L.sym && fp32) {
         NearSymLaunch S = L.S;
         S.inject = h->inject_timeout ? 1 : 0;
         TRY(launch_near32s(L.pk32, L.pk32lo, L.org, pl.d_shifts, L.part_n, S, st));
+    } else if (L.sym) {
+        TRY(launch_near64s(L.pk64, pl.d_shifts, L.part_n, L.S, st));
     } else if (fp32) {
         NearPlanLaunch Ln = L.Ln;
         Ln.inject = h->inject_timeout ? 1 : 0;
@@ -321,7 +336,7 @@ int queue_forward(psum_plan_s* h, int64_t N, const double* x, const double* q, d
     if (h->profile) TRY(cudaEventRecord(h->ev[3], st));
     const int tile = fp32 ? kTile32 : kTile64;
     if (L.sym)
-        TRY(launch_sym_reduce(L.part_n, N, L.S, L.phi_n, L.grad_n, st));
+        TRY(launch_sym_reduce(L.part_n, N, L.S, L.phi_n, L.grad_n, st, !fp32));
     else
         TRY(launch_near_reduce(L.part_n, sep ? T : N, tile, 4, L.Ln, L.phi_n, L.grad_n, st));
     TRY(launch_near_reduce(L.part_c, pl.n_check, tile, 1, L.Lc, L.phi_c, nullptr, st));

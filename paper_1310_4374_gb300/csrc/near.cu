@@ -1220,6 +1220,130 @@ __global__ void __launch_bounds__(kThreads64) k_near64(Near64Args a) {
 }
 
 // ---------------------------------------------------------------------------
+// Symmetric float64 charge kernel: the float64 counterpart of k_near32s.  A tile of 128
+// charges (one per thread) is also a source chunk; items are (tile pair (a <= b), image
+// group); per image a warp visits the 128 sources of tile b in 4 rotations of 32, adding
+// the action q_s / r to its targets and passing each source's reaction sums one lane down
+// per step (float64 shuffles); every warp keeps its own float64 reaction sums per source,
+// added in a fixed order when the item is done.  A tile against itself runs one-sided.
+// ---------------------------------------------------------------------------
+struct Near64SymArgs {
+    const double4_32a* pk;   // charges (x, y, z, q), absolute, padded with far-away zero charges
+    const double* shifts;
+    double* partial;         // per system [n_tiles][n_tiles * n_g][4][kTile64] from part0
+    SymSysTable tab;
+    int64_t W;
+    int* counter;
+};
+
+template <int kMinB>
+__global__ void __launch_bounds__(kThreads64, kMinB) k_near64s(Near64SymArgs a) {
+    constexpr int kWarps = kThreads64 / 32;
+    __shared__ double4_32a s_src[kNearChunk];
+    __shared__ double s_re[kWarps][4][kNearChunk];   // reaction sums [warp][quantity][source]
+    __shared__ int s_item;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int up = (lane + 1) & 31;
+    for (;;) {
+    if (tid == 0) s_item = atomicAdd(a.counter, 1);
+    __syncthreads();
+    const int64_t item = s_item;
+    __syncthreads();                     // every thread has the item (and is done with the last one)
+    if (item >= a.W) break;
+    const SymSys S = a.tab.many ? a.tab.many[sym_sys_by_item(a.tab, item)] : a.tab.one;
+    const int64_t local = item - S.item0;
+    const int64_t pair = local / S.n_g;
+    const int gi = (int)(local - pair * S.n_g);
+    int64_t tb = (int64_t)((sqrt(8.0 * (double)pair + 1.0) - 1.0) * 0.5);
+    while (tb > 0 && tb * (tb + 1) / 2 > pair) --tb;
+    while ((tb + 1) * (tb + 2) / 2 <= pair) ++tb;
+    const int64_t ta = pair - tb * (tb + 1) / 2;
+    const bool diag = ta == tb;
+    const int64_t n_slots = S.n_tiles * S.n_g;
+    const int im0 = gi * S.img_per_g;
+    const int nimg = min(S.img_per_g, S.n_img - im0);
+    const double4_32a t = a.pk[(S.tile0 + ta) * kTile64 + tid];
+    s_src[tid] = a.pk[(S.tile0 + tb) * kTile64 + tid];
+#pragma unroll
+    for (int qi = 0; qi < 4; ++qi)
+#pragma unroll
+        for (int k = 0; k < kNearChunk / 32; ++k) s_re[warp][qi][32 * k + lane] = 0.0;
+    __syncthreads();
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int im = 0; im < nimg; ++im) {
+        // y - x_i - p with the shift folded into the target
+        const double* sh = a.shifts + 3 * (S.shift0 + im0 + im);
+        const double px = t.x - sh[0], py = t.y - sh[1], pz = t.z - sh[2];
+        if (diag) {
+#pragma unroll 4
+            for (int s = 0; s < kNearChunk; ++s) {
+                const double4_32a Q = s_src[s];
+                const double ex = Q.x - px, ey = Q.y - py, ez = Q.z - pz;
+                const double r2 = fma(ez, ez, fma(ey, ey, ex * ex));
+                const double ri = r2 > 0.0 ? rsqrt_f64(r2) : 0.0;      // K(0) = 0
+                const double qr = Q.w * ri;
+                acc[0] += qr;
+                const double w = qr * ri * ri;
+                acc[1] = fma(ex, w, acc[1]);
+                acc[2] = fma(ey, w, acc[2]);
+                acc[3] = fma(ez, w, acc[3]);
+            }
+            continue;
+        }
+#pragma unroll 1
+        for (int g = 0; g < kNearChunk / 32; ++g) {
+            double rp = 0.0, rx = 0.0, ry = 0.0, rz = 0.0;
+#pragma unroll 2
+            for (int k = 0; k < 32; ++k) {
+                const double4_32a Q = s_src[32 * g + ((lane + k) & 31)];
+                const double ex = Q.x - px, ey = Q.y - py, ez = Q.z - pz;   // x_s + p - y
+                const double r2 = fma(ez, ez, fma(ey, ey, ex * ex));
+                const double ri = r2 > 0.0 ? rsqrt_f64(r2) : 0.0;
+                const double ri2 = ri * ri;
+                const double qa = Q.w * ri;              // action
+                acc[0] += qa;
+                const double wa = qa * ri2;
+                acc[1] = fma(ex, wa, acc[1]);
+                acc[2] = fma(ey, wa, acc[2]);
+                acc[3] = fma(ez, wa, acc[3]);
+                const double qb = t.w * ri;              // reaction (field sign folded later)
+                rp += qb;
+                const double wb = qb * ri2;
+                rx = fma(ex, wb, rx);
+                ry = fma(ey, wb, ry);
+                rz = fma(ez, wb, rz);
+                rp = __shfl_sync(0xffffffffu, rp, up);
+                rx = __shfl_sync(0xffffffffu, rx, up);
+                ry = __shfl_sync(0xffffffffu, ry, up);
+                rz = __shfl_sync(0xffffffffu, rz, up);
+            }
+            const int s = 32 * g + lane;                 // the lane holds source s's reaction
+            s_re[warp][0][s] += rp;
+            s_re[warp][1][s] += rx;
+            s_re[warp][2][s] += ry;
+            s_re[warp][3][s] += rz;
+        }
+    }
+    {
+        double* dst = a.partial + S.part0 + ((ta * n_slots + tb * S.n_g + gi) * 4) * kTile64 + tid;
+#pragma unroll
+        for (int qi = 0; qi < 4; ++qi) dst[qi * kTile64] = acc[qi];
+    }
+    if (!diag) {
+        __syncthreads();
+        double* dst = a.partial + S.part0 + ((tb * n_slots + ta * S.n_g + gi) * 4) * kTile64 + tid;
+#pragma unroll
+        for (int qi = 0; qi < 4; ++qi) {
+            double v = 0.0;
+#pragma unroll
+            for (int w = 0; w < kWarps; ++w) v += s_re[w][qi][tid];
+            dst[qi * kTile64] = qi == 0 ? v : -v;
+        }
+    }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Reduction of the partial slots (fixed order: slot 0, 1, ...) for packed target
 // index i < n_valid (tile = i / tile_size is the partial-buffer row).
 // ---------------------------------------------------------------------------
@@ -1267,6 +1391,7 @@ __global__ void __launch_bounds__(32 * kReduceWarps) k_near_reduce(const double*
 // of its system adds that system's slots 0 .. n_tiles n_g - 1 of row t; a block takes 32
 // consecutive targets (one tile) and one quantity, its 8 warps every 8th slot, combined in a
 // fixed order.
+template <int kTile>
 __global__ void __launch_bounds__(32 * kReduceWarps) k_sym_reduce(const double* __restrict__ partial, int64_t n_valid,
                                                                  SymSysTable tab, double* __restrict__ out_phi,
                                                                  double* __restrict__ out_grad) {
@@ -1275,7 +1400,7 @@ __global__ void __launch_bounds__(32 * kReduceWarps) k_sym_reduce(const double* 
     const int qi = blockIdx.y;
     const int64_t i0 = (int64_t)blockIdx.x * 32;
     const int64_t i = i0 + lane;
-    const int64_t T = i0 / kTile32;
+    const int64_t T = i0 / kTile;
     int64_t tile0 = tab.one.tile0, n_slots = tab.one.n_tiles * tab.one.n_g, part0 = tab.one.part0;
     if (tab.many) {
         const SymSys& S = tab.many[sym_sys_by_tile(tab, T)];
@@ -1284,11 +1409,11 @@ __global__ void __launch_bounds__(32 * kReduceWarps) k_sym_reduce(const double* 
         part0 = S.part0;
     }
     const int64_t tile = T - tile0;
-    const int loc = (int)(i - T * kTile32);
-    const double* base = partial + part0 + (tile * n_slots * 4 + qi) * kTile32 + loc;
+    const int loc = (int)(i - T * kTile);
+    const double* base = partial + part0 + (tile * n_slots * 4 + qi) * kTile + loc;
     double acc = 0.0;
     if (i < n_valid)
-        for (int64_t s = warp; s < n_slots; s += kReduceWarps) acc += base[s * 4 * kTile32];
+        for (int64_t s = warp; s < n_slots; s += kReduceWarps) acc += base[s * 4 * kTile];
     s_part[warp][lane] = acc;
     __syncthreads();
     if (warp == 0 && i < n_valid) {
@@ -1393,11 +1518,34 @@ int near32s_occupancy_ctas(int img_per_g) {
 }
 
 cudaError_t launch_sym_reduce(const double* partial, int64_t n_valid, const NearSymLaunch& S, double* out_phi,
-                              double* out_grad, cudaStream_t st) {
+                              double* out_grad, cudaStream_t st, bool fp64) {
     if (n_valid <= 0) return cudaSuccess;
     const dim3 grid((unsigned)((n_valid + 31) / 32), 4u);
-    k_sym_reduce<<<grid, 32 * kReduceWarps, 0, st>>>(partial, n_valid, S.tab, out_phi, out_grad);
+    if (fp64)
+        k_sym_reduce<kTile64><<<grid, 32 * kReduceWarps, 0, st>>>(partial, n_valid, S.tab, out_phi, out_grad);
+    else
+        k_sym_reduce<kTile32><<<grid, 32 * kReduceWarps, 0, st>>>(partial, n_valid, S.tab, out_phi, out_grad);
     return cudaGetLastError();
+}
+
+constexpr int kNear64sMinBlocks = 4;
+
+cudaError_t launch_near64s(const double4_32a* pk, const double* shifts, double* partial, const NearSymLaunch& S,
+                           cudaStream_t st) {
+    if (!S.counter) return cudaErrorInvalidValue;
+    if (S.W <= 0) return cudaSuccess;
+    Near64SymArgs a;
+    a.pk = pk; a.shifts = shifts; a.partial = partial; a.tab = S.tab; a.W = S.W; a.counter = S.counter;
+    const cudaError_t e = cudaMemsetAsync(S.counter, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    k_near64s<kNear64sMinBlocks><<<(unsigned)S.G, kThreads64, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+int near64s_occupancy_ctas() {
+    int nb = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_near64s<kNear64sMinBlocks>, kThreads64, 0);
+    return nb < 1 ? 1 : nb;
 }
 
 cudaError_t launch_near64(bool grad, const double4_32a* src, const double4_32a* tgt, const double* shifts,

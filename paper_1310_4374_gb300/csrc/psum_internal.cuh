@@ -388,8 +388,8 @@ struct SymSysTable {
 __host__ __device__ __forceinline__ int64_t sym_sys_items(const SymSys& s) {
     return s.n_tiles * (s.n_tiles + 1) / 2 * s.n_g;
 }
-__host__ __device__ __forceinline__ size_t sym_sys_doubles(const SymSys& s) {
-    return (size_t)s.n_tiles * (size_t)s.n_tiles * (size_t)s.n_g * 4 * kTile32;
+__host__ __device__ __forceinline__ size_t sym_sys_doubles(const SymSys& s, int tile) {
+    return (size_t)s.n_tiles * (size_t)s.n_tiles * (size_t)s.n_g * 4 * (size_t)tile;
 }
 
 struct NearSymLaunch {
@@ -411,11 +411,12 @@ struct NearSymLaunch {
 #endif
 constexpr int kSymItemsPerCta = PSUM_SYM_ITEMS_PER_CTA;
 constexpr int64_t kSymMinTiles = 16;                          // automatic choice: at least 16 tiles
+constexpr int64_t kSymMinTiles64 = 64;                        // (float64: 64 tiles of 128)
 constexpr size_t kSymMaxPartialBytes = (size_t)8 << 30;       // and a partial buffer of at most 8 GiB
 
 // `sys` holds tile0, n_tiles, n_chunks, shift0 and n_img of every system; the rest is filled
 // here.  G is the number of resident CTAs.
-inline NearSymLaunch sym_partition(std::vector<SymSys>& sys, int64_t G) {
+inline NearSymLaunch sym_partition(std::vector<SymSys>& sys, int64_t G, int tile = kTile32) {
     NearSymLaunch S;
     int64_t pairs = 0;
     int max_img = 1;
@@ -434,7 +435,7 @@ inline NearSymLaunch sym_partition(std::vector<SymSys>& sys, int64_t G) {
         s.item0 = item;
         s.part0 = (int64_t)part;
         item += sym_sys_items(s);
-        part += sym_sys_doubles(s);
+        part += sym_sys_doubles(s, tile);
         S.max_ipg = s.img_per_g > S.max_ipg ? s.img_per_g : S.max_ipg;
     }
     S.W = item;

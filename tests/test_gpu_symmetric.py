@@ -1,11 +1,11 @@
 """GPU parity of the symmetric charge kernel (PSUM_PAIRS_SYMMETRIC).
 
-The pair (i, j, p) and its mirror (j, i, -p) are one distance apart, so the kernel forms
-one offset and one 1/r for both and adds the source's terms (the reaction) as well as the
+The pair (i, j, p) and its mirror (j, i, -p) are one distance apart, so the kernels form
+one offset and one 1/r for both and add the source's terms (the reaction) as well as the
 target's; the tiles' pairs (a < b) each run once with every image of the block, a tile
-against itself runs one-sided.  It computes the same sums as the one-sided kernel in a
-different rounding order, so both are held to the FP32C bound (relative L2 error 1e-6,
-Eq. st2) against the FP64 oracle, and to each other.  The cases cover one to five tiles of
+against itself runs one-sided.  They compute the same sums as the one-sided kernels in a
+different rounding order, so both are held to the path's bound (relative L2 error, Eq. st2:
+1e-6 FP32C, 1e-10 FP64) against the FP64 oracle, and to each other (1e-6, 1e-12).  The cases cover one to five tiles of
 512 charges, a last tile with a single charge, partly filled chunks, close dipole pairs
 (the float-float near units on both sides of a pair), a wider near block and every image
 grouping of the work items.
@@ -20,15 +20,16 @@ from paper_1310_4374_gb300 import workloads as W
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-TOL = 1e-6
+TOL = {"fp32c": 1e-6, "fp64": 1e-10}
+TOL_BETWEEN = {"fp32c": 1e-6, "fp64": 1e-12}     # symmetric against one-sided
 
 
 def _dev(a):
     return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
 
 
-def _run(s, pairs, K=(1, 1, 1)):
-    pc = B.PeriodicCoulomb(s.d, s.p, s.M, precision="fp32c", K=K, pairs=pairs)
+def _run(s, pairs, K=(1, 1, 1), precision="fp32c"):
+    pc = B.PeriodicCoulomb(s.d, s.p, s.M, precision=precision, K=K, pairs=pairs)
     try:
         phi, g = pc(_dev(s.x), _dev(s.q))
         return phi.cpu().numpy(), g.cpu().numpy()
@@ -50,16 +51,24 @@ CASES = [
 ]
 
 
+_REF = {}
+
+
+@pytest.mark.parametrize("precision", ["fp32c", "fp64"])
 @pytest.mark.parametrize("name,make,K", CASES, ids=[c[0] for c in CASES])
-def test_symmetric_kernel_against_oracle_and_one_sided(name, make, K):
+def test_symmetric_kernel_against_oracle_and_one_sided(name, make, K, precision):
     s = make()
-    phi_s, g_s = _run(s, "symmetric", K)
-    phi_o, g_o = _run(s, "one-sided", K)
-    ref = O.Plan(s.d, s.p, s.M, K=K).evaluate(s.x, s.q, mean="zero", parts=True)
+    phi_s, g_s = _run(s, "symmetric", K, precision)
+    phi_o, g_o = _run(s, "one-sided", K, precision)
+    if name not in _REF:
+        _REF[name] = O.Plan(s.d, s.p, s.M, K=K).evaluate(s.x, s.q, mean="zero", parts=True)
+    ref = _REF[name]
+    tol = TOL[precision]
     for phi, g, what in ((phi_s, g_s, "symmetric"), (phi_o, g_o, "one-sided")):
         e_phi, e_g = _eps(phi, ref["phi"]), _eps(g, ref["grad"])
-        assert e_phi < TOL and e_g < TOL, f"{name}/{what}: eps2 phi {e_phi:.3e}, grad {e_g:.3e}"
-    assert _eps(phi_s, phi_o) < TOL and _eps(g_s, g_o) < TOL
+        assert e_phi < tol and e_g < tol, f"{name}/{precision}/{what}: eps2 phi {e_phi:.3e}, grad {e_g:.3e}"
+    tb = TOL_BETWEEN[precision]
+    assert _eps(phi_s, phi_o) < tb and _eps(g_s, g_o) < tb
 
 
 def test_symmetric_kernel_is_deterministic():
@@ -75,11 +84,19 @@ def test_symmetric_kernel_is_deterministic():
         pc.close()
 
 
-def test_automatic_choice_matches_the_forced_kernels():
-    # 16 tiles or more take the symmetric kernel automatically
+@pytest.mark.parametrize("precision", ["fp32c", "fp64"])
+def test_automatic_choice_matches_the_forced_kernels(precision):
+    # 16 tiles of 512 charges or more take the symmetric kernel automatically (FP64: 64 of 128)
     s = W.uniform_gauss(N=16 * 512 + 77, d=(1.0, 1.5, 2.0), p=8, M=200, seed=10)
-    phi_a, g_a = _run(s, "auto")
-    phi_s, g_s = _run(s, "symmetric")
-    phi_o, g_o = _run(s, "one-sided")
+    pc = B.PeriodicCoulomb(s.d, s.p, s.M, precision=precision)
+    try:
+        assert B.psum_pair_kernel(pc.plan, s.N)[0] == "symmetric"
+        assert B.psum_pair_kernel(pc.plan, 1000)[0] == "one-sided"
+    finally:
+        pc.close()
+    phi_a, g_a = _run(s, "auto", precision=precision)
+    phi_s, g_s = _run(s, "symmetric", precision=precision)
+    phi_o, g_o = _run(s, "one-sided", precision=precision)
     assert np.array_equal(phi_a, phi_s) and np.array_equal(g_a, g_s)
-    assert _eps(phi_s, phi_o) < TOL and _eps(g_s, g_o) < TOL
+    tb = TOL_BETWEEN[precision]
+    assert _eps(phi_s, phi_o) < tb and _eps(g_s, g_o) < tb
