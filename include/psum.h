@@ -84,8 +84,8 @@ extern "C" {
                                     (FP32C: 16 tiles of 512, FP64: 64 tiles of 128), one-sided otherwise */
 #define PSUM_PAIRS_ONE_SIDED  1  /* every (target, source, image) term computed on its own */
 #define PSUM_PAIRS_SYMMETRIC  2  /* where it applies, at any size: the pair (i, j, p) and its mirror
-                                    (j, i, -p) share one offset and one 1/r (FP32C and FP64 plans without
-                                    ball trimming, potential and field at the charges, psum_eval,
+                                    (j, i, -p) share one offset and one 1/r (FP32C, FF and FP64 plans
+                                    without ball trimming, potential and field at the charges, psum_eval,
                                     psum_eval_host, psum_eval_graph and psum_energy, and FP32C batches;
                                     one-sided elsewhere).  Same sums, different rounding order. */
 

@@ -108,7 +108,8 @@ size_t layout(Plan& pl, int64_t N, char* base, Layout& L, bool backward = false,
         // the symmetric kernel: FP32C charges, block image set, a normal (growing) scratch
         L.sym = false;
         const int pk = pl.opt.pair_kernel;
-        if (pl.opt.precision == PSUM_FP32C && !sep && !trimmed && g_cap == 0 && pk != PSUM_PAIRS_ONE_SIDED &&
+        const bool ffp = pl.opt.precision == PSUM_FF;
+        if (!sep && !trimmed && g_cap == 0 && pk != PSUM_PAIRS_ONE_SIDED &&
             (pk == PSUM_PAIRS_SYMMETRIC || L.n_tiles >= kSymMinTiles)) {
             // image groups sized for the occupancy of the largest group (the largest dynamic
             // shared memory), then the launch width for the chosen group size
@@ -118,8 +119,8 @@ size_t layout(Plan& pl, int64_t N, char* base, Layout& L, bool backward = false,
             one[0].n_chunks = L.n_chunks;
             one[0].shift0 = 0;
             one[0].n_img = n_img;
-            L.S = sym_partition(one, (int64_t)pl.num_sms * near32s_occupancy_ctas(n_img));
-            L.S.G = (int64_t)pl.num_sms * near32s_occupancy_ctas(L.S.max_ipg);
+            L.S = sym_partition(one, (int64_t)pl.num_sms * near32s_occupancy_ctas(n_img, ffp));
+            L.S.G = (int64_t)pl.num_sms * near32s_occupancy_ctas(L.S.max_ipg, ffp);
             if (L.S.G > L.S.W) L.S.G = L.S.W;
             L.sym = L.S.doubles * sizeof(double) <= kSymMaxPartialBytes;
         }
@@ -312,7 +313,7 @@ int queue_forward(psum_plan_s* h, int64_t N, const double* x, const double* q, d
     if (L.sym && fp32) {
         NearSymLaunch S = L.S;
         S.inject = h->inject_timeout ? 1 : 0;
-        TRY(launch_near32s(L.pk32, L.pk32lo, L.org, pl.d_shifts, L.part_n, S, st));
+        TRY(launch_near32s(L.pk32, L.pk32lo, L.org, pl.d_shifts, L.part_n, S, st, ff));
     } else if (L.sym) {
         TRY(launch_near64s(L.pk64, pl.d_shifts, L.part_n, L.S, st));
     } else if (fp32) {

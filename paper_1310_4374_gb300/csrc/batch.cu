@@ -673,8 +673,8 @@ int psum_batch_create(const psum_plan_t* plans, int B, const int64_t* offsets, p
         bt->Lc = near_partition(bt->near_c, gmax, nullptr, kCheckItemsPerCta);
     }
     if (bt->precision == PSUM_FP32C) {
-        bt->Ls = sym_partition(bt->sym_sys, (int64_t)num_sms * near32s_occupancy_ctas(max_img));
-        bt->Ls.G = std::min<int64_t>((int64_t)num_sms * near32s_occupancy_ctas(bt->Ls.max_ipg), bt->Ls.W);
+        bt->Ls = sym_partition(bt->sym_sys, (int64_t)num_sms * near32s_occupancy_ctas(max_img, false));
+        bt->Ls.G = std::min<int64_t>((int64_t)num_sms * near32s_occupancy_ctas(bt->Ls.max_ipg, false), bt->Ls.W);
         bt->sym_ok = bt->Ls.W > 0 && bt->Ls.doubles * sizeof(double) <= kSymMaxPartialBytes;
     }
     int st = PSUM_OK;

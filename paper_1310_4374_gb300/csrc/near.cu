@@ -806,13 +806,91 @@ __device__ __forceinline__ void sym_near_step(const float4* __restrict__ s_hi, c
     rz += bz.x + bz.y;
 }
 
-template <int kMinB>
+// One float-float step: the lane's packed target pair (negated offsets nTh + nTl, charges
+// tqh + tql) against source si, both directions in float-float arithmetic (the one-sided
+// loop's offsets, r^2 and Newton-refined 1/r, computed once).  The action goes to acc
+// (hi, lo per quantity); the reaction, summed over the 2 targets, to the compensated scalar
+// sums r[q] = (hi, lo).
+__device__ __forceinline__ void sym_ff_step(const float4* __restrict__ s_hi, const float4* __restrict__ s_lo,
+                                            int si, const float2 (&nTh)[3], const float2 (&nTl)[3], float2 tqh,
+                                            float2 tql, float2 (&acc)[4][2], float (&r)[4][2]) {
+    const float4 A = s_hi[2 * si], B = s_hi[2 * si + 1], C = s_lo[2 * si], D = s_lo[2 * si + 1];
+    const float2 sh[3] = {make_float2(A.x, A.y), make_float2(A.z, A.w), make_float2(B.x, B.y)};
+    const float2 sl[3] = {make_float2(C.x, C.y), make_float2(C.z, C.w), make_float2(D.x, D.y)};
+    const float2 qh = make_float2(B.z, B.w), ql = make_float2(D.z, D.w);
+    float2 eh[3], el[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        float2 err;
+        eh[c] = two_sum2(sh[c], nTh[c], err);
+        el[c] = __fadd2_rn(__fadd2_rn(sl[c], nTl[c]), err);
+    }
+    const float2 p0 = __fmul2_rn(eh[0], eh[0]), p1 = __fmul2_rn(eh[1], eh[1]), p2 = __fmul2_rn(eh[2], eh[2]);
+    float2 lo = __ffma2_rn(eh[0], eh[0], neg2(p0));
+    lo = __fadd2_rn(lo, __ffma2_rn(eh[1], eh[1], neg2(p1)));
+    lo = __fadd2_rn(lo, __ffma2_rn(eh[2], eh[2], neg2(p2)));
+    float2 cr = __fmul2_rn(eh[0], el[0]);
+    cr = __ffma2_rn(eh[1], el[1], cr);
+    cr = __ffma2_rn(eh[2], el[2], cr);
+    lo = __ffma2_rn(make_float2(2.f, 2.f), cr, lo);
+    float2 e1, e2;
+    const float2 s1 = two_sum2(p0, p1, e1);
+    const float2 r2h = two_sum2(s1, p2, e2);
+    const float2 r2l = __fadd2_rn(lo, __fadd2_rn(e1, e2));
+    const float2 y = make_float2(rsqrt_mufu(r2h.x), rsqrt_mufu(r2h.y));
+    const float2 ah = __fmul2_rn(r2h, y);
+    const float2 ae = __ffma2_rn(r2h, y, neg2(ah));
+    const float2 bh = __fmul2_rn(ah, y);
+    const float2 be = __ffma2_rn(ah, y, neg2(bh));
+    float2 h = __fadd2_rn(bh, make_float2(-1.f, -1.f));
+    h = __fadd2_rn(h, be);
+    h = __ffma2_rn(ae, y, h);
+    h = __ffma2_rn(__fmul2_rn(r2l, y), y, h);
+    float2 rih = y;
+    float2 ril = __fmul2_rn(__fmul2_rn(make_float2(-0.5f, -0.5f), y), h);
+    if (r2h.x == 0.f) rih.x = ril.x = 0.f;                // K(0) = 0 (Eq. 1)
+    if (r2h.y == 0.f) rih.y = ril.y = 0.f;
+    float2 r2il;
+    const float2 r2ih = ff_mul2(rih, ril, rih, ril, r2il);
+    // action: q_s / r and q_s (s - t') / r^3
+    float2 Pl;
+    const float2 Ph = ff_mul2(qh, ql, rih, ril, Pl);
+    ff_acc2(acc[0][0], acc[0][1], Ph, Pl);
+    float2 wl;
+    const float2 wh = ff_mul2(Ph, Pl, r2ih, r2il, wl);
+    // reaction: q_t / r and q_t (s - t') / r^3, the 2 targets' terms added in float-float
+    float2 Rl;
+    const float2 Rh = ff_mul2(tqh, tql, rih, ril, Rl);
+    float2 vl;
+    const float2 vh = ff_mul2(Rh, Rl, r2ih, r2il, vl);
+    float e;
+    float t = two_sum(Rh.x, Rh.y, e);
+    float u = (Rl.x + Rl.y) + e;
+    r[0][0] = two_sum(r[0][0], t, e);
+    r[0][1] += u + e;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        float2 gl;
+        const float2 gh = ff_mul2(wh, wl, eh[c], el[c], gl);
+        ff_acc2(acc[1 + c][0], acc[1 + c][1], gh, gl);
+        float2 kl;
+        const float2 kh = ff_mul2(vh, vl, eh[c], el[c], kl);
+        t = two_sum(kh.x, kh.y, e);
+        u = (kl.x + kl.y) + e;
+        r[1 + c][0] = two_sum(r[1 + c][0], t, e);
+        r[1 + c][1] += u + e;
+    }
+}
+
+template <int kMinB, bool kFF>
 __global__ void __launch_bounds__(kThreads32, kMinB) k_near32s(Near32SymArgs a) {
     constexpr int kWarps = kThreads32 / 32;
     __shared__ float4 s_hi[2 * kNearChunk];
     __shared__ float4 s_lo[2 * kNearChunk];
     __shared__ float2 s_th[3][2][kThreads32];             // target offsets of tile a, [coord][pair]
     __shared__ float2 s_tq[2][kThreads32];                // target charges, [pair]
+    __shared__ float2 s_tl[kFF ? 3 : 1][2][kThreads32];   // FF: target lo offsets
+    __shared__ float2 s_tql[kFF ? 2 : 1][kThreads32];     // FF: target charge lo parts
     __shared__ float2 s_acc[4][2][2][kThreads32];         // action sums [quantity][pair][hi, lo]
     extern __shared__ float4 s_dyn4[];
     // reaction sums [warp][quantity][hi, lo][source], then [img_per_g][kTgt32][6] deltas and
@@ -865,6 +943,14 @@ __global__ void __launch_bounds__(kThreads32, kMinB) k_near32s(Near32SymArgs a) 
         s_th[1][j][tid] = make_float2(A0.z, A1.z);
         s_th[2][j][tid] = make_float2(B0.x, B1.x);
         s_tq[j][tid] = make_float2(B0.z, B1.z);
+        if (kFF) {
+            const float4 C0 = a.pk_lo[2 * i0], D0 = a.pk_lo[2 * i0 + 1];
+            const float4 C1 = a.pk_lo[2 * i1], D1 = a.pk_lo[2 * i1 + 1];
+            s_tl[0][j][tid] = make_float2(C0.x, C1.x);
+            s_tl[kFF ? 1 : 0][j][tid] = make_float2(C0.z, C1.z);
+            s_tl[kFF ? 2 : 0][j][tid] = make_float2(D0.x, D1.x);
+            s_tql[kFF ? j : 0][tid] = make_float2(D0.z, D1.z);
+        }
 #pragma unroll
         for (int qi = 0; qi < 4; ++qi) s_acc[qi][j][0][tid] = s_acc[qi][j][1][tid] = make_float2(0.f, 0.f);
     }
@@ -915,6 +1001,56 @@ __global__ void __launch_bounds__(kThreads32, kMinB) k_near32s(Near32SymArgs a) 
         for (int im = 0; im < nimg; ++im) {
             const float* dl = s_delta + 6 * (im * kTgt32);
             const int cls = s_near[im];
+            if constexpr (kFF) {
+                // every unit in float-float: t' = t + delta as hi + lo, one packed pair at a time
+#pragma unroll 1
+                for (int j = 0; j < 2; ++j) {
+                    const float* d0 = dl + 6 * (2 * j);
+                    const float* d1 = dl + 6 * (2 * j + 1);
+                    float2 nTh[3], nTl[3];
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        float2 e;
+                        const float2 th = two_sum2(s_th[c][j][tid], make_float2(d0[c], d1[c]), e);
+                        const float2 tl = __fadd2_rn(__fadd2_rn(s_tl[c][j][tid], make_float2(d0[3 + c], d1[3 + c])), e);
+                        nTh[c] = neg2(th);
+                        nTl[c] = neg2(tl);
+                    }
+                    float2 acc[4][2];
+#pragma unroll
+                    for (int qi = 0; qi < 4; ++qi) acc[qi][0] = acc[qi][1] = make_float2(0.f, 0.f);
+                    if (diag) {
+                        pair_loop_ff<true>(s_hi, s_lo, nTh, nTl, acc);
+                    } else {
+                        const float2 tqh = s_tq[j][tid], tql = s_tql[kFF ? j : 0][tid];
+#pragma unroll 1
+                        for (int g = 0; g < kNearChunk / 32; ++g) {
+                            float r[4][2] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+#pragma unroll 1
+                            for (int k = 0; k < 32; ++k) {
+                                sym_ff_step(s_hi, s_lo, 32 * g + ((lane + k) & 31), nTh, nTl, tqh, tql, acc, r);
+#pragma unroll
+                                for (int qi = 0; qi < 4; ++qi) {
+                                    r[qi][0] = __shfl_sync(0xffffffffu, r[qi][0], up);
+                                    r[qi][1] = __shfl_sync(0xffffffffu, r[qi][1], up);
+                                }
+                            }
+                            const int s = 32 * g + lane;
+#pragma unroll
+                            for (int qi = 0; qi < 4; ++qi) {
+                                two_sum_acc(s_re[warp][qi][0][s], s_re[warp][qi][1][s], r[qi][0]);
+                                s_re[warp][qi][1][s] += r[qi][1];
+                            }
+                        }
+                    }
+#pragma unroll
+                    for (int qi = 0; qi < 4; ++qi) {
+                        two_sum_acc2(s_acc[qi][j][0][tid], s_acc[qi][j][1][tid], acc[qi][0]);
+                        s_acc[qi][j][1][tid] = __fadd2_rn(s_acc[qi][j][1][tid], acc[qi][1]);
+                    }
+                }
+                continue;
+            }
             if (diag) {
                 // a tile against its own chunks: the one-sided units
 #pragma unroll 1
@@ -1489,12 +1625,16 @@ size_t near32s_dyn_smem(int img_per_g) {
 // the kernel's static and dynamic shared memory together pass the 48 KiB default: allow the
 // largest dynamic size any image group needs
 cudaError_t near32s_allow_smem() {
-    return cudaFuncSetAttribute(k_near32s<kNear32sMinBlocks>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    const cudaError_t e = cudaFuncSetAttribute(k_near32s<kNear32sMinBlocks, false>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)near32s_dyn_smem(kMaxImages));
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_near32s<kNear32sMinBlocks, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)near32s_dyn_smem(kMaxImages));
 }
 
 cudaError_t launch_near32s(const float4* pk_hi, const float4* pk_lo, const double* org, const double* shifts,
-                           double* partial, const NearSymLaunch& S, cudaStream_t st) {
+                           double* partial, const NearSymLaunch& S, cudaStream_t st, bool ff) {
     if (!S.counter || !S.status || S.n_status < 1 || S.max_ipg < 1) return cudaErrorInvalidValue;
     if (S.W <= 0) return cudaSuccess;
     const cudaError_t ea = near32s_allow_smem();
@@ -1505,15 +1645,22 @@ cudaError_t launch_near32s(const float4* pk_hi, const float4* pk_lo, const doubl
     a.counter = S.counter; a.status = S.status; a.n_status = S.n_status; a.inject = S.inject;
     const cudaError_t e = cudaMemsetAsync(S.counter, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
-    k_near32s<kNear32sMinBlocks><<<(unsigned)S.G, kThreads32, near32s_dyn_smem(S.max_ipg), st>>>(a);
+    if (ff)
+        k_near32s<kNear32sMinBlocks, true><<<(unsigned)S.G, kThreads32, near32s_dyn_smem(S.max_ipg), st>>>(a);
+    else
+        k_near32s<kNear32sMinBlocks, false><<<(unsigned)S.G, kThreads32, near32s_dyn_smem(S.max_ipg), st>>>(a);
     return cudaGetLastError();
 }
 
-int near32s_occupancy_ctas(int img_per_g) {
+int near32s_occupancy_ctas(int img_per_g, bool ff) {
     int nb = 0;
     near32s_allow_smem();
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_near32s<kNear32sMinBlocks>, kThreads32,
-                                                  near32s_dyn_smem(img_per_g));
+    if (ff)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_near32s<kNear32sMinBlocks, true>, kThreads32,
+                                                      near32s_dyn_smem(img_per_g));
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_near32s<kNear32sMinBlocks, false>, kThreads32,
+                                                      near32s_dyn_smem(img_per_g));
     return nb < 1 ? 1 : nb;
 }
 

@@ -5,7 +5,8 @@ one offset and one 1/r for both and add the source's terms (the reaction) as wel
 target's; the tiles' pairs (a < b) each run once with every image of the block, a tile
 against itself runs one-sided.  They compute the same sums as the one-sided kernels in a
 different rounding order, so both are held to the path's bound (relative L2 error, Eq. st2:
-1e-6 FP32C, 1e-10 FP64) against the FP64 oracle, and to each other (1e-6, 1e-12).  The cases cover one to five tiles of
+1e-6 FP32C, 1e-10 FP64 and float-float) against the FP64 oracle, and to each other (1e-6, 1e-12,
+1e-11).  The cases cover one to five tiles of
 512 charges, a last tile with a single charge, partly filled chunks, close dipole pairs
 (the float-float near units on both sides of a pair), a wider near block and every image
 grouping of the work items.
@@ -20,8 +21,8 @@ from paper_1310_4374_gb300 import workloads as W
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp32c": 1e-6, "fp64": 1e-10}
-TOL_BETWEEN = {"fp32c": 1e-6, "fp64": 1e-12}     # symmetric against one-sided
+TOL = {"fp32c": 1e-6, "fp64": 1e-10, "ff": 1e-10}
+TOL_BETWEEN = {"fp32c": 1e-6, "fp64": 1e-12, "ff": 1e-11}     # symmetric against one-sided
 
 
 def _dev(a):
@@ -54,7 +55,7 @@ CASES = [
 _REF = {}
 
 
-@pytest.mark.parametrize("precision", ["fp32c", "fp64"])
+@pytest.mark.parametrize("precision", ["fp32c", "fp64", "ff"])
 @pytest.mark.parametrize("name,make,K", CASES, ids=[c[0] for c in CASES])
 def test_symmetric_kernel_against_oracle_and_one_sided(name, make, K, precision):
     s = make()
@@ -84,7 +85,7 @@ def test_symmetric_kernel_is_deterministic():
         pc.close()
 
 
-@pytest.mark.parametrize("precision", ["fp32c", "fp64"])
+@pytest.mark.parametrize("precision", ["fp32c", "fp64", "ff"])
 def test_automatic_choice_matches_the_forced_kernels(precision):
     # 16 tiles of 512 charges or more take the symmetric kernel automatically (FP64: 64 of 128)
     s = W.uniform_gauss(N=16 * 512 + 77, d=(1.0, 1.5, 2.0), p=8, M=200, seed=10)
