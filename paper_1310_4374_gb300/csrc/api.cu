@@ -110,7 +110,7 @@ size_t layout(Plan& pl, int64_t N, char* base, Layout& L, bool backward = false,
         const int pk = pl.opt.pair_kernel;
         const bool ffp = pl.opt.precision == PSUM_FF;
         if (!sep && !trimmed && g_cap == 0 && pk != PSUM_PAIRS_ONE_SIDED &&
-            (pk == PSUM_PAIRS_SYMMETRIC || L.n_tiles >= kSymMinTiles)) {
+            (pk == PSUM_PAIRS_SYMMETRIC || L.n_tiles >= (ffp ? kSymMinTilesFF : kSymMinTiles))) {
             // image groups sized for the occupancy of the largest group (the largest dynamic
             // shared memory), then the launch width for the chosen group size
             std::vector<SymSys> one(1);

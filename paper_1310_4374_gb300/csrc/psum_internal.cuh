@@ -410,8 +410,12 @@ struct NearSymLaunch {
 #define PSUM_SYM_ITEMS_PER_CTA 8
 #endif
 constexpr int kSymItemsPerCta = PSUM_SYM_ITEMS_PER_CTA;
-constexpr int64_t kSymMinTiles = 16;                          // automatic choice: at least 16 tiles
-constexpr int64_t kSymMinTiles64 = 64;                        // (float64: 64 tiles of 128)
+// automatic choice (measured crossovers against the one-sided kernels): FP32C from 16 tiles of
+// 512 charges (6000 charges even), float-float from 6 (3000 even), float64 at every size (1.64x
+// at 1000 charges)
+constexpr int64_t kSymMinTiles = 16;
+constexpr int64_t kSymMinTilesFF = 6;
+constexpr int64_t kSymMinTiles64 = 1;
 constexpr size_t kSymMaxPartialBytes = (size_t)8 << 30;       // and a partial buffer of at most 8 GiB
 
 // `sys` holds tile0, n_tiles, n_chunks, shift0 and n_img of every system; the rest is filled
