@@ -27,7 +27,11 @@
 // results on the float32 pipe.
 //
 // FP64: absolute float64 coordinates; 1/sqrt(r^2) is a float32 MUFU estimate
-// refined by two Newton-Raphson steps y <- y (3 - r^2 y^2)/2 in float64.
+// refined by one third-order step in float64.
+//
+// The charge sums (targets = sources) also have symmetric kernels, k_near32s (FP32C, FF)
+// and k_near64s (FP64), which take each pair of tiles once with every image and add both
+// the target's and the source's terms of a pair; see their own notes below.
 #include "launch.cuh"
 
 namespace psum {
@@ -665,7 +669,8 @@ __global__ void __launch_bounds__(kThreads32, kMinB) k_near32(Near32Args a) {
 }
 
 // ---------------------------------------------------------------------------
-// Symmetric charge kernel (FP32C, potential and field at the charges, block image sets).
+// Symmetric charge kernel (FP32C and float-float, potential and field at the charges,
+// block image sets, one or many systems).
 // With the charges as both targets and sources, the pair (i, j, p) and its mirror
 // (j, i, -p) are one distance apart: one offset, one rsqrt and one 1/r^2 serve the
 // target's sum (the action, q_j / r) and the source's (the reaction, q_i / r, field
@@ -684,7 +689,11 @@ __global__ void __launch_bounds__(kThreads32, kMinB) k_near32(Near32Args a) {
 //     source l over the warp's 128 targets; the 4 warps keep private compensated (hi,
 //     lo) sums per source, combined in a fixed order when the chunk is done;
 //   * near pairs (as in the one-sided units) take float-float offsets, K(0) = 0 and
-//     blocks of 4 terms with compensated sums, on both sides.
+//     blocks of 4 terms with compensated sums, on both sides;
+//   * kFF: every pair in float-float arithmetic (the one-sided float-float loop's offsets,
+//     r^2 and 1/r, shared), one packed target pair per rotation pass.
+// Work items of several systems (batches) follow one another; a system's table entry
+// gives its first item, tiles, chunks, images and partial block.
 // ---------------------------------------------------------------------------
 struct Near32SymArgs {
     const float4* pk_hi;     // the charges' pack: 2 float4 per point, (x,x,y,y),(z,z,q,q) offsets

@@ -13,10 +13,11 @@ def _dev(a):
     return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
 
 
-@pytest.mark.parametrize("precision", ["fp32c", "fp64", "ff"])
-def test_graph_replay_equals_psum_eval_and_follows_new_inputs(precision):
+@pytest.mark.parametrize("precision,pairs", [("fp32c", "one-sided"), ("fp32c", "symmetric"), ("fp64", "one-sided"),
+                                            ("fp64", "symmetric"), ("ff", "one-sided"), ("ff", "symmetric")])
+def test_graph_replay_equals_psum_eval_and_follows_new_inputs(precision, pairs):
     s = W.config(1, small=True)
-    pc = B.PeriodicCoulomb(s.d, s.p, s.M, precision=precision)
+    pc = B.PeriodicCoulomb(s.d, s.p, s.M, precision=precision, pairs=pairs)
     try:
         x, q = _dev(s.x), _dev(s.q)
         ref_phi, ref_g = pc(x, q)
