@@ -21,8 +21,8 @@ def _dev(a):
     return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
 
 
-def run_gpu(sys_, precision, K=(1, 1, 1), mean="zero"):
-    pc = B.PeriodicCoulomb(sys_.d, sys_.p, sys_.M, precision=precision, K=K, mean=mean)
+def run_gpu(sys_, precision, K=(1, 1, 1), mean="zero", pairs="auto"):
+    pc = B.PeriodicCoulomb(sys_.d, sys_.p, sys_.M, precision=precision, K=K, mean=mean, pairs=pairs)
     try:
         phi, g = pc(_dev(sys_.x), _dev(sys_.q))
         C = pc.coefficients()
@@ -110,17 +110,18 @@ def test_madelung_on_gpu(precision, madelung):
     assert eps.max() < (2e-6 if precision == "fp64" else 2e-5)
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32c"])
+@pytest.mark.parametrize("precision,pairs", [("fp64", "one-sided"), ("fp64", "symmetric"), ("fp32c", "one-sided"),
+                                            ("fp32c", "symmetric")])
 @pytest.mark.parametrize("N", [2, 3, 127, 128, 129, 511, 513, 1025])
-def test_ragged_sizes(N, precision):
+def test_ragged_sizes(N, precision, pairs):
     rng = np.random.default_rng(N)
     x = rng.uniform(-0.5, 0.5, (N, 3))
     q = rng.normal(size=N)
     q -= q.mean()
     s = W.System(x, q, (1.0, 1.0, 1.0), 6, 120, name=f"ragged{N}")
-    phi, g, _, _ = run_gpu(s, precision)
+    phi, g, _, _ = run_gpu(s, precision, pairs=pairs)
     ref = run_oracle(s)
-    assert_parity(phi, g, ref, TOL[precision], f"N={N}")
+    assert_parity(phi, g, ref, TOL[precision], f"N={N}/{pairs}")
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32c"])
