@@ -33,10 +33,11 @@ N_MAIN, D_MAIN, P_MAIN, M_MAIN, SEED_MAIN = 100_000, (1.0, 1.5, 2.0), 16, 800, 2
 N_FP64 = 20_000            # FP32C-vs-FP64 comparison runs on a 20k-charge system of the same box
 FP32_OPS_PAIR_GRAD = 13    # FP32-pipe lane operations per potential+gradient pair, one-sided kernel
                            # (3 sub, 3 r^2, 4 phi/weight, 3 grad)
-# symmetric kernel: per step a lane pairs its 4 targets with one source (8 ordered pairs,
-# both directions) in 37 packed f32x2 operations (74 lane operations: 3 sub, 3 r^2, 1 1/r^2,
-# 6 action and 5-6 reaction operations per target pair) and folds the reaction in 8 adds
-FP32_OPS_PAIR_SYM = 82 / 8
+# symmetric kernel: per step a lane pairs its 4 targets with two sources (16 ordered pairs,
+# both directions) in 76 packed f32x2 operations (152 lane operations: per target 3 sub,
+# 3 r^2, 1 1/r^2, 6 action and 5-6 reaction operations, and the block of 4 targets' potential
+# reactions added to the running sum)
+FP32_OPS_PAIR_SYM = 152 / 16
 FP32_OPS_PAIR_PHI = 7      # potential only (3 sub, 3 r^2, 1 fma)
 FP64_OPS_PAIR = 19         # float64 kernel, one-sided
 FP64_OPS_PAIR_SYM = 12     # float64 kernel, symmetric

@@ -683,11 +683,14 @@ __global__ void __launch_bounds__(kThreads32, kMinB) k_near32(Near32Args a) {
 //     on tile b to slot (b, a, g), so every slot has one writer and the reduction adds
 //     a tile's n_tiles * n_g slots in a fixed order;
 //   * per source chunk of tile b and image, a warp's 32 lanes (4 targets each) visit the
-//     chunk in 4 rounds of 32 sources: at step k lane l takes source (l + k) mod 32 of
-//     the round and adds the targets' terms to that source's reaction sums, which then
-//     move one lane down (a shuffle), so after 32 steps lane l holds the reaction of
-//     source l over the warp's 128 targets; the 4 warps keep private compensated (hi,
-//     lo) sums per source, combined in a fixed order when the chunk is done;
+//     chunk in 2 rounds of 32 source pairs (the chunk re-laid in shared memory as pairs,
+//     (x0,x1,y0,y1),(z0,z1,q0,q1), so that one packed operation serves both sources of
+//     a pair for one target): at step k lane l takes pair (l + k) mod 32 of the round and
+//     adds its targets' terms to the pair's reaction sums, which then move one lane down
+//     (shuffles), so after 32 steps lane l holds the reactions of pair l over the warp's
+//     128 targets; the 4 warps keep private compensated (hi, lo) sums per source,
+//     combined in a fixed order when the chunk is done (near units keep one source per
+//     step in the original layout);
 //   * near pairs (as in the one-sided units) take float-float offsets, K(0) = 0 and
 //     blocks of 4 terms with compensated sums, on both sides;
 //   * kFF: every pair in float-float arithmetic (the one-sided float-float loop's offsets,
@@ -763,6 +766,44 @@ __device__ __forceinline__ void sym_far_step(const float4* __restrict__ s_hi, in
     rx += bx.x + bx.y;
     ry += by.x + by.y;
     rz += bz.x + bz.y;
+}
+
+// One far step over a pair of sources (s0, s1) in the pair layout A = (x0, x1, y0, y1),
+// B = (z0, z1, q0, q1): the lane's 4 targets (duplicated coordinates, negated offsets) each
+// take both sources in one packed operation; the action sums keep the two sources in their
+// two halves (folded once per unit), the reaction sums keep the two sources apart, so no
+// per-step fold is needed.
+__device__ __forceinline__ void sym_far_step_pair(float4 A, float4 B, const float2 (&nx)[4], const float2 (&ny)[4],
+                                                  const float2 (&nz)[4], const float2 (&tq)[4], float2 (&aphi)[4],
+                                                  float2 (&agx)[4], float2 (&agy)[4], float2 (&agz)[4],
+                                                  float2& rp, float2& rx, float2& ry, float2& rz) {
+    const float2 sx = make_float2(A.x, A.y), sy = make_float2(A.z, A.w), sz = make_float2(B.x, B.y);
+    const float2 sq = make_float2(B.z, B.w);
+    float2 bp;                 // the 4 targets' potential reactions, summed before the running sum
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float2 ex = __fadd2_rn(sx, nx[i]);
+        const float2 ey = __fadd2_rn(sy, ny[i]);
+        const float2 ez = __fadd2_rn(sz, nz[i]);
+        float2 r2 = __fmul2_rn(ex, ex);
+        r2 = __ffma2_rn(ey, ey, r2);
+        r2 = __ffma2_rn(ez, ez, r2);
+        const float2 ri = make_float2(rsqrt_mufu(r2.x), rsqrt_mufu(r2.y));
+        const float2 ri2 = __fmul2_rn(ri, ri);
+        const float2 qa = __fmul2_rn(sq, ri);
+        aphi[i] = __fadd2_rn(aphi[i], qa);
+        const float2 wa = __fmul2_rn(qa, ri2);
+        agx[i] = __ffma2_rn(ex, wa, agx[i]);
+        agy[i] = __ffma2_rn(ey, wa, agy[i]);
+        agz[i] = __ffma2_rn(ez, wa, agz[i]);
+        const float2 qb = __fmul2_rn(tq[i], ri);
+        bp = i == 0 ? qb : __fadd2_rn(bp, qb);
+        const float2 wb = __fmul2_rn(qb, ri2);
+        rx = __ffma2_rn(ex, wb, rx);
+        ry = __ffma2_rn(ey, wb, ry);
+        rz = __ffma2_rn(ez, wb, rz);
+    }
+    rp = __fadd2_rn(rp, bp);
 }
 
 // One near step: float-float offsets (hi + lo of both sides), K(0) = 0; the action's
@@ -901,6 +942,7 @@ __global__ void __launch_bounds__(kThreads32, kMinB) k_near32s(Near32SymArgs a) 
     __shared__ float2 s_tl[kFF ? 3 : 1][2][kThreads32];   // FF: target lo offsets
     __shared__ float2 s_tql[kFF ? 2 : 1][kThreads32];     // FF: target charge lo parts
     __shared__ float2 s_acc[4][2][2][kThreads32];         // action sums [quantity][pair][hi, lo]
+    __shared__ float4 s_sp[kFF ? 1 : kNearChunk];         // the chunk as source pairs (x0,x1,y0,y1),(z0,z1,q0,q1)
     extern __shared__ float4 s_dyn4[];
     // reaction sums [warp][quantity][hi, lo][source], then [img_per_g][kTgt32][6] deltas and
     // [img_per_g] unit classes
@@ -1007,6 +1049,13 @@ __global__ void __launch_bounds__(kThreads32, kMinB) k_near32s(Near32SymArgs a) 
             }
             return;
         }
+        if (!kFF && !diag) {
+            // the chunk again as source pairs for the far rotation
+            const int P = tid >> 1, h = tid & 1;
+            const float4 U = s_hi[2 * (2 * P) + h], V = s_hi[2 * (2 * P + 1) + h];
+            s_sp[tid] = make_float4(U.x, V.x, U.z, V.z);
+            __syncthreads();
+        }
         for (int im = 0; im < nimg; ++im) {
             const float* dl = s_delta + 6 * (im * kTgt32);
             const int cls = s_near[im];
@@ -1111,47 +1160,64 @@ __global__ void __launch_bounds__(kThreads32, kMinB) k_near32s(Near32SymArgs a) 
                    agz[2] = {agx[0], agx[0]};
             float2 aphi[2] = {agx[0], agx[0]}, aphi2[2] = {agx[0], agx[0]};   // far: two interleaved sums; near: hi, lo
             if (!(cls & kUnitNear)) {
-                float2 nx[2], ny[2], nz[2];
+                // targets as 4 scalars (duplicated into both halves), sources two at a time
+                float2 nx[4], ny[4], nz[4], tq4[4];
+                float2 ph[4], gx[4], gy[4], gz[4];
 #pragma unroll
                 for (int j = 0; j < 2; ++j) {
                     const float* d0 = dl + 6 * (2 * j);
                     const float* d1 = dl + 6 * (2 * j + 1);
                     const float2 tx = s_th[0][j][tid], ty = s_th[1][j][tid], tz = s_th[2][j][tid];
-                    nx[j] = make_float2(-(tx.x + d0[0]), -(tx.y + d1[0]));
-                    ny[j] = make_float2(-(ty.x + d0[1]), -(ty.y + d1[1]));
-                    nz[j] = make_float2(-(tz.x + d0[2]), -(tz.y + d1[2]));
+                    const float a0 = -(tx.x + d0[0]), a1 = -(tx.y + d1[0]);
+                    const float b0 = -(ty.x + d0[1]), b1 = -(ty.y + d1[1]);
+                    const float c0 = -(tz.x + d0[2]), c1 = -(tz.y + d1[2]);
+                    nx[2 * j] = make_float2(a0, a0); nx[2 * j + 1] = make_float2(a1, a1);
+                    ny[2 * j] = make_float2(b0, b0); ny[2 * j + 1] = make_float2(b1, b1);
+                    nz[2 * j] = make_float2(c0, c0); nz[2 * j + 1] = make_float2(c1, c1);
+                    tq4[2 * j] = make_float2(tq[j].x, tq[j].x);
+                    tq4[2 * j + 1] = make_float2(tq[j].y, tq[j].y);
                 }
+#pragma unroll
+                for (int i2 = 0; i2 < 4; ++i2) ph[i2] = gx[i2] = gy[i2] = gz[i2] = make_float2(0.f, 0.f);
 #pragma unroll 1
-                for (int g = 0; g < kNearChunk / 32; ++g) {
-                    float rp = 0.f, rx = 0.f, ry = 0.f, rz = 0.f;
+                for (int g = 0; g < kNearChunk / 64; ++g) {
+                    float2 rp = make_float2(0.f, 0.f), rx = rp, ry = rp, rz = rp;
 #pragma unroll 1
-                    for (int k = 0; k < 32; k += 2) {
-                        sym_far_step(s_hi, 32 * g + ((lane + k) & 31), nx, ny, nz, tq, aphi, agx, agy, agz, rp, rx,
-                                     ry, rz);
-                        rp = __shfl_sync(0xffffffffu, rp, up);
-                        rx = __shfl_sync(0xffffffffu, rx, up);
-                        ry = __shfl_sync(0xffffffffu, ry, up);
-                        rz = __shfl_sync(0xffffffffu, rz, up);
-                        sym_far_step(s_hi, 32 * g + ((lane + k + 1) & 31), nx, ny, nz, tq, aphi2, agx, agy, agz, rp,
-                                     rx, ry, rz);
-                        rp = __shfl_sync(0xffffffffu, rp, up);
-                        rx = __shfl_sync(0xffffffffu, rx, up);
-                        ry = __shfl_sync(0xffffffffu, ry, up);
-                        rz = __shfl_sync(0xffffffffu, rz, up);
+                    for (int k = 0; k < 32; ++k) {
+                        const int P = 32 * g + ((lane + k) & 31);
+                        sym_far_step_pair(s_sp[2 * P], s_sp[2 * P + 1], nx, ny, nz, tq4, ph, gx, gy, gz, rp, rx, ry,
+                                          rz);
+                        rp.x = __shfl_sync(0xffffffffu, rp.x, up);
+                        rp.y = __shfl_sync(0xffffffffu, rp.y, up);
+                        rx.x = __shfl_sync(0xffffffffu, rx.x, up);
+                        rx.y = __shfl_sync(0xffffffffu, rx.y, up);
+                        ry.x = __shfl_sync(0xffffffffu, ry.x, up);
+                        ry.y = __shfl_sync(0xffffffffu, ry.y, up);
+                        rz.x = __shfl_sync(0xffffffffu, rz.x, up);
+                        rz.y = __shfl_sync(0xffffffffu, rz.y, up);
                     }
-                    // the lane holds the reaction of source 32 g + lane
-                    const int s = 32 * g + lane;
-                    two_sum_acc(s_re[warp][0][0][s], s_re[warp][0][1][s], rp);
-                    two_sum_acc(s_re[warp][1][0][s], s_re[warp][1][1][s], rx);
-                    two_sum_acc(s_re[warp][2][0][s], s_re[warp][2][1][s], ry);
-                    two_sum_acc(s_re[warp][3][0][s], s_re[warp][3][1][s], rz);
+                    // the lane holds the reactions of sources 2 P and 2 P + 1, P = 32 g + lane
+                    const int s = 2 * (32 * g + lane);
+                    two_sum_acc(s_re[warp][0][0][s], s_re[warp][0][1][s], rp.x);
+                    two_sum_acc(s_re[warp][0][0][s + 1], s_re[warp][0][1][s + 1], rp.y);
+                    two_sum_acc(s_re[warp][1][0][s], s_re[warp][1][1][s], rx.x);
+                    two_sum_acc(s_re[warp][1][0][s + 1], s_re[warp][1][1][s + 1], rx.y);
+                    two_sum_acc(s_re[warp][2][0][s], s_re[warp][2][1][s], ry.x);
+                    two_sum_acc(s_re[warp][2][0][s + 1], s_re[warp][2][1][s + 1], ry.y);
+                    two_sum_acc(s_re[warp][3][0][s], s_re[warp][3][1][s], rz.x);
+                    two_sum_acc(s_re[warp][3][0][s + 1], s_re[warp][3][1][s + 1], rz.y);
                 }
 #pragma unroll
                 for (int j = 0; j < 2; ++j) {
-                    two_sum_acc2(s_acc[0][j][0][tid], s_acc[0][j][1][tid], __fadd2_rn(aphi[j], aphi2[j]));
-                    two_sum_acc2(s_acc[1][j][0][tid], s_acc[1][j][1][tid], agx[j]);
-                    two_sum_acc2(s_acc[2][j][0][tid], s_acc[2][j][1][tid], agy[j]);
-                    two_sum_acc2(s_acc[3][j][0][tid], s_acc[3][j][1][tid], agz[j]);
+                    // the two sources' halves of each target's sums, folded once per unit
+                    two_sum_acc2(s_acc[0][j][0][tid], s_acc[0][j][1][tid],
+                                 make_float2(ph[2 * j].x + ph[2 * j].y, ph[2 * j + 1].x + ph[2 * j + 1].y));
+                    two_sum_acc2(s_acc[1][j][0][tid], s_acc[1][j][1][tid],
+                                 make_float2(gx[2 * j].x + gx[2 * j].y, gx[2 * j + 1].x + gx[2 * j + 1].y));
+                    two_sum_acc2(s_acc[2][j][0][tid], s_acc[2][j][1][tid],
+                                 make_float2(gy[2 * j].x + gy[2 * j].y, gy[2 * j + 1].x + gy[2 * j + 1].y));
+                    two_sum_acc2(s_acc[3][j][0][tid], s_acc[3][j][1][tid],
+                                 make_float2(gz[2 * j].x + gz[2 * j].y, gz[2 * j + 1].x + gz[2 * j + 1].y));
                 }
             } else {
                 // near pairs present: every pair of the unit in float-float offsets
