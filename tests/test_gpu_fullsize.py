@@ -1,7 +1,8 @@
 """The benchmark's full-size workloads on the GPU, checked where the oracle can follow:
-sampled outputs of the 200k-charge dipole system (forward and the exact adjoint), and the
-full 256-system batch against single-system evaluations and, for its smallest systems,
-against the oracle."""
+sampled outputs of the 200k-charge dipole system (forward and the exact adjoint), the full
+256-system batch against single-system evaluations and, for its smallest systems, against
+the oracle, and the symmetric float64 and float-float kernels at 50k charges on sampled
+targets."""
 import numpy as np
 import pytest
 
@@ -93,3 +94,22 @@ def test_full_batch_against_single_evaluations_and_the_oracle():
         sl = slice(offsets[b], offsets[b + 1])
         assert O.relative_l2(phi[sl], ref["phi"]) < 1e-6, s.name
         assert O.relative_l2(g[sl], ref["grad"]) < 1e-6, s.name
+
+
+@pytest.mark.parametrize("precision", ["fp64", "ff"])
+def test_symmetric_float64_class_kernels_at_50k_charges_on_sampled_targets(precision):
+    # the symmetric float64 and float-float kernels over 98 tiles of 512 (391 of 128), every
+    # image in one group, against the oracle on 64 sampled charges (FP64 tolerance)
+    s = W.uniform_gauss(N=50_000, d=(1.0, 1.5, 2.0), p=16, M=800, seed=21)
+    pc = B.PeriodicCoulomb(s.d, s.p, s.M, precision=precision)
+    try:
+        assert B.psum_pair_kernel(pc.plan, s.N)[0] == "symmetric"
+        phi, g = pc(_dev(s.x), _dev(s.q))
+        phi, g = phi.cpu().numpy(), g.cpu().numpy()
+    finally:
+        pc.close()
+    rng = np.random.default_rng(21)
+    k = np.sort(rng.choice(s.N, size=64, replace=False))
+    ref = O.Plan(s.d, s.p, s.M).evaluate(s.x, s.q, targets=s.x[k], parts=True)
+    assert O.relative_l2(phi[k], ref["phi"]) < 1e-10
+    assert O.relative_l2(g[k], ref["grad"]) < 1e-10
