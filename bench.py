@@ -148,11 +148,14 @@ def measured_peaks():
 
 
 def near_code_hash():
-    """First 16 hex digits of the SHA-256 of near.cu's code: comments removed and
-    whitespace collapsed, so that a comment edit keeps the recorded counters valid."""
+    """First 16 hex digits of the SHA-256 of the symmetric charge kernel's code
+    (near_common.cuh and near_sym.cu): comments removed and whitespace collapsed, so that
+    a comment edit keeps the recorded counters valid."""
     import re
-    with open(os.path.join(ROOT, "paper_1310_4374_gb300", "csrc", "near.cu")) as f:
-        src = f.read()
+    src = ""
+    for name in ("near_common.cuh", "near_sym.cu"):
+        with open(os.path.join(ROOT, "paper_1310_4374_gb300", "csrc", name)) as f:
+            src += f.read() + "\n"
     src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
     src = re.sub(r"//[^\n]*", " ", src)
     return hashlib.sha256(" ".join(src.split()).encode()).hexdigest()[:16]
@@ -169,7 +172,7 @@ def near_kernel_traffic(n_points, kernel, image_groups):
     try:
         with open(path) as f:
             rec = json.load(f)
-        if rec.get("near_cu_code_sha256_16") != near_code_hash() or rec.get("pair_kernel") != kernel:
+        if rec.get("near_code_sha256_16") != near_code_hash() or rec.get("pair_kernel") != kernel:
             return None
         read = rec["dram_read_bytes"] * n_points / rec["n_points"]
         if kernel == "symmetric":
