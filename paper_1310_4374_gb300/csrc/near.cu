@@ -31,7 +31,7 @@
 //
 // The charge sums (targets = sources) also have symmetric kernels, k_near32s (FP32C, FF)
 // and k_near64s (FP64), which take each pair of tiles once with every image and add both
-// the target's and the source's terms of a pair; see their own notes below.
+// the target's and the source's terms of a pair (near_sym.cu).
 #include "near_common.cuh"
 
 namespace psum {

@@ -15,7 +15,7 @@ namespace psum {
 // target's sum (the action, q_j / r) and the source's (the reaction, q_i / r, field
 // with the opposite sign).  The image set {p} of a block is symmetric, so the pairs
 // of tiles (a, b), a < b, each taken once with every image, cover the whole sum; a
-// tile against itself (a = b) runs the one-sided units above.
+// tile against itself (a = b) runs the one-sided pair loops (near_common.cuh).
 //
 //   * the work item is (tile pair (a, b), group of images); items are taken from a
 //     device counter; the action on tile a goes to partial slot (a, b, g), the reaction
