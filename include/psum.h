@@ -80,7 +80,7 @@ extern "C" {
 #define PSUM_BASIS_RBF       1  /* kernel functions 1/|y - x_t| centred outside S_b (Eq. 5); P = n_rbf + 1 */
 
 /* pair kernel of the near sum at the charges (psum_opts.pair_kernel) */
-#define PSUM_PAIRS_AUTO       0  /* symmetric where it applies: FP32C from 16 tiles of 512 charges (7681
+#define PSUM_PAIRS_AUTO       0  /* symmetric where it applies: FP32C from 12 tiles of 512 charges (5633
                                     charges), FF from 6 tiles (2561), FP64 at every size; one-sided
                                     otherwise */
 #define PSUM_PAIRS_ONE_SIDED  1  /* every (target, source, image) term computed on its own */

@@ -445,7 +445,7 @@ __global__ void __launch_bounds__(kThreads64) k_near64(Near64Args a) {
             const double4_32a Q = src[s];
             const double ex = Q.x - px, ey = Q.y - py, ez = Q.z - pz;   // x_i + p - y
             const double r2 = fma(ez, ez, fma(ey, ey, ex * ex));
-            const double ri = r2 > 0.0 ? rsqrt_f64(r2) : 0.0;           // K(0) = 0
+            const double ri = rsqrt_f64_k0(r2);           // K(0) = 0
             const double qr = Q.w * ri;
             acc[0] += qr;
             if (kGrad) {

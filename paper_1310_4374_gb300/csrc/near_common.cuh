@@ -320,14 +320,20 @@ __device__ __forceinline__ void pair_loop_ff(const float4* __restrict__ s_hi, co
     }
 }
 
-__device__ __forceinline__ double rsqrt_f64(double r2) {
-    // MUFU estimate y0 (relative error below 2^-22), then one third-order correction:
-    // with e = 1 - r2 y0^2, 1/sqrt(r2) = y0 (1 - e)^(-1/2) = y0 (1 + e/2 + 3e^2/8 + O(e^3)),
-    // whose truncation (5/16)|e|^3 < 1e-20 is below float64 rounding; 5 float64 operations
-    // where two Newton-Raphson steps take 7
-    const double y = (double)rsqrt_mufu((float)r2);
+// 1/sqrt(r2), or 0 for r2 = 0 (K(0) = 0, Eq. 1), in float64.  MUFU estimate y0 (relative
+// error below 2^-22), then one third-order correction: with e = 1 - r2 y0^2,
+// 1/sqrt(r2) = y0 (1 - e)^(-1/2) = y0 (1 + e/2 + 3e^2/8 + O(e^3)), whose truncation
+// (5/16)|e|^3 < 1e-20 is below float64 rounding; 5 float64 operations where two
+// Newton-Raphson steps take 7.  The zero test is taken on the float32 copy that feeds the
+// MUFU estimate (a float32 compare and selects instead of a float64 compare on the slow
+// float64 pipe); a nonzero r2 whose float32 copy flushes to zero would need two distinct
+// charges within 1e-19 of each other.
+__device__ __forceinline__ double rsqrt_f64_k0(double r2) {
+    const float r2f = (float)r2;
+    const double y = (double)rsqrt_mufu(r2f);
     const double e = fma(-r2, y * y, 1.0);
-    return fma(y * e, fma(0.375, e, 0.5), y);
+    const double ri = fma(y * e, fma(0.375, e, 0.5), y);
+    return r2f > 0.f ? ri : 0.0;
 }
 
 // warps of the reduction kernels (fixed-order combination of the partial slots)

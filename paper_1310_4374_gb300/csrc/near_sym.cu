@@ -670,7 +670,7 @@ __global__ void __launch_bounds__(kThreads64, kMinB) k_near64s(Near64SymArgs a) 
                 const double4_32a Q = s_src[s];
                 const double ex = Q.x - px, ey = Q.y - py, ez = Q.z - pz;
                 const double r2 = fma(ez, ez, fma(ey, ey, ex * ex));
-                const double ri = r2 > 0.0 ? rsqrt_f64(r2) : 0.0;      // K(0) = 0
+                const double ri = rsqrt_f64_k0(r2);      // K(0) = 0
                 const double qr = Q.w * ri;
                 acc[0] += qr;
                 const double w = qr * ri * ri;
@@ -688,7 +688,7 @@ __global__ void __launch_bounds__(kThreads64, kMinB) k_near64s(Near64SymArgs a) 
                 const double4_32a Q = s_src[32 * g + ((lane + k) & 31)];
                 const double ex = Q.x - px, ey = Q.y - py, ez = Q.z - pz;   // x_s + p - y
                 const double r2 = fma(ez, ez, fma(ey, ey, ex * ex));
-                const double ri = r2 > 0.0 ? rsqrt_f64(r2) : 0.0;
+                const double ri = rsqrt_f64_k0(r2);
                 const double ri2 = ri * ri;
                 const double qa = Q.w * ri;              // action
                 acc[0] += qa;

@@ -410,10 +410,10 @@ struct NearSymLaunch {
 #define PSUM_SYM_ITEMS_PER_CTA 8
 #endif
 constexpr int kSymItemsPerCta = PSUM_SYM_ITEMS_PER_CTA;
-// automatic choice (measured crossovers against the one-sided kernels): FP32C from 16 tiles of
-// 512 charges (6000 charges even), float-float from 6 (3000 even), float64 at every size (1.64x
+// automatic choice (measured crossovers against the one-sided kernels): FP32C from 12 tiles of
+// 512 charges (5500 charges even), float-float from 6 (3000 even), float64 at every size (1.64x
 // at 1000 charges)
-constexpr int64_t kSymMinTiles = 16;
+constexpr int64_t kSymMinTiles = 12;
 constexpr int64_t kSymMinTilesFF = 6;
 constexpr int64_t kSymMinTiles64 = 1;
 constexpr size_t kSymMaxPartialBytes = (size_t)8 << 30;       // and a partial buffer of at most 8 GiB

@@ -87,13 +87,13 @@ def test_symmetric_kernel_is_deterministic():
 
 @pytest.mark.parametrize("precision", ["fp32c", "fp64", "ff"])
 def test_automatic_choice_matches_the_forced_kernels(precision):
-    # FP32C takes the symmetric kernel automatically from 16 tiles of 512 charges, FF from 6,
+    # FP32C takes the symmetric kernel automatically from 12 tiles of 512 charges, FF from 6,
     # FP64 at every size
     s = W.uniform_gauss(N=16 * 512 + 77, d=(1.0, 1.5, 2.0), p=8, M=200, seed=10)
     pc = B.PeriodicCoulomb(s.d, s.p, s.M, precision=precision)
     try:
         assert B.psum_pair_kernel(pc.plan, s.N)[0] == "symmetric"
-        small = {"fp32c": (15 * 512, "one-sided"), "ff": (5 * 512, "one-sided"), "fp64": (1000, "symmetric")}
+        small = {"fp32c": (11 * 512, "one-sided"), "ff": (5 * 512, "one-sided"), "fp64": (1000, "symmetric")}
         n, kernel = small[precision]
         assert B.psum_pair_kernel(pc.plan, n)[0] == kernel
         if precision == "ff":
