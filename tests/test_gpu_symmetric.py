@@ -7,9 +7,9 @@ against itself runs one-sided.  They compute the same sums as the one-sided kern
 different rounding order, so both are held to the path's bound (relative L2 error, Eq. st2:
 1e-6 FP32C, 1e-10 FP64 and float-float) against the FP64 oracle, and to each other (1e-6, 1e-12,
 1e-11).  The cases cover one to five tiles of
-512 charges, a last tile with a single charge, partly filled chunks, close dipole pairs
-(the float-float near units on both sides of a pair), a wider near block and every image
-grouping of the work items.
+512 charges, a last tile with a single charge, partly filled chunks, a tight cluster (every
+unit near), close dipole pairs (the float-float near units on both sides of a pair), a wider
+near block and every image grouping of the work items.
 """
 import numpy as np
 import pytest
@@ -42,7 +42,19 @@ def _eps(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
+def _clustered(N=2000, seed=11):
+    # every charge within 0.06 of one point: all tile pairs are near units (float-float
+    # offsets and compensated sums on both sides of every pair)
+    rng = np.random.default_rng(seed)
+    x = 0.06 * rng.normal(size=(N, 3)) / 3.0
+    x = np.clip(x, -0.49, 0.49)
+    q = rng.normal(size=N)
+    q -= q.mean()
+    return W.System(x, q, (1.0, 1.0, 1.0), 8, 200, name=f"clustered_{N}")
+
+
 CASES = [
+    ("clustered_2000", lambda: _clustered(), (1, 1, 1)),
     ("one_tile_402", lambda: W.config(1, small=True), (1, 1, 1)),
     ("two_tiles_513", lambda: W.uniform_gauss(N=513, d=(1.0, 1.5, 2.0), p=8, M=200, seed=5), (1, 1, 1)),
     ("three_tiles_1300", lambda: W.uniform_gauss(N=1300, d=(1.0, 1.5, 2.0), p=12, M=400, seed=6), (1, 1, 1)),
