@@ -324,13 +324,21 @@ __device__ __forceinline__ void pair_loop_ff(const float4* __restrict__ s_hi, co
 // error below 2^-22), then one third-order correction: with e = 1 - r2 y0^2,
 // 1/sqrt(r2) = y0 (1 - e)^(-1/2) = y0 (1 + e/2 + 3e^2/8 + O(e^3)), whose truncation
 // (5/16)|e|^3 < 1e-20 is below float64 rounding; 5 float64 operations where two
-// Newton-Raphson steps take 7.  The zero test is taken on the float32 copy that feeds the
-// MUFU estimate (a float32 compare and selects instead of a float64 compare on the slow
-// float64 pipe); a nonzero r2 whose float32 copy flushes to zero would need two distinct
-// charges within 1e-19 of each other.
+// Newton-Raphson steps take 7.  The conversions between float64 and float32 around the
+// MUFU estimate are done on the bit patterns with integer operations (the float64 pipe, which
+// bounds this kernel, also runs the conversion instructions): the float32 copy of r2 keeps
+// the top 23 mantissa bits (truncated, relative error below 2^-23, so |e| < 2^-21 and the
+// correction's truncation stays below 1e-19), the estimate is widened exactly.  The zero test
+// is taken on that float32 copy (a float32 compare and selects instead of a float64 compare);
+// r2 below 2^-126 counts as zero, which would need two distinct charges within 1e-19 of each
+// other.
 __device__ __forceinline__ double rsqrt_f64_k0(double r2) {
-    const float r2f = (float)r2;
-    const double y = (double)rsqrt_mufu(r2f);
+    // float32 bits: the float64 exponent rebiased (1023 -> 127) and the mantissa cut to 23 bits
+    const long long t = (__double_as_longlong(r2) >> 29) - (896LL << 23);
+    const float r2f = __int_as_float(t > 0 ? (int)t : 0);
+    const float yf = rsqrt_mufu(r2f);
+    // float64 bits of the (positive, normal) estimate: exponent rebiased, mantissa widened
+    const double y = __longlong_as_double(((long long)__float_as_int(yf) << 29) + (896LL << 52));
     const double e = fma(-r2, y * y, 1.0);
     const double ri = fma(y * e, fma(0.375, e, 0.5), y);
     return r2f > 0.f ? ri : 0.0;
