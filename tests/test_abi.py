@@ -36,6 +36,7 @@ def test_strerror_and_defaults_without_gpu():
     o = B.psum_opts_default()
     assert tuple(o.d) == (1.0, 1.0, 1.0) and o.p == 8 and o.M == 200 and tuple(o.K) == (1, 1, 1)
     assert o.precision == B.PSUM_FP64 and o.mean_mode == B.PSUM_MEAN_ZERO
+    assert o.pair_kernel == B.PAIR_KERNELS["auto"] == 0
 
 
 @pytest.mark.parametrize("d,p,M,prec,K", [
@@ -60,6 +61,8 @@ def test_null_arguments_are_rejected():
     assert lib.psum_eval(None, 10, None, None, None, None, None) == B.PSUM_ERR_ARG
     assert lib.psum_sync(None, None) == B.PSUM_ERR_ARG
     assert lib.psum_plan_info(None, None) == B.PSUM_ERR_ARG
+    k = ctypes.c_int(-1)
+    assert lib.psum_pair_kernel(None, 10, ctypes.byref(k), None) == B.PSUM_ERR_ARG
     lib.psum_destroy(None)
     h = ctypes.c_void_p()
     assert lib.psum_plan_create(1.0, 1.0, 1.0, 8, 10, ctypes.byref(h)) == B.PSUM_ERR_ARG
@@ -91,3 +94,13 @@ def test_gauss_grid_fixes_the_number_of_check_points():
     with pytest.raises(B.PsumError) as e:
         B.psum_plan_create_ex((1, 1, 1), 8, 200, points=7)
     assert e.value.status == B.PSUM_ERR_ARG
+
+
+@pytest.mark.parametrize("pair_kernel", [-1, 3, 99])
+def test_unknown_pair_kernel_is_rejected(pair_kernel):
+    # checked on the host before any device call
+    o = B.psum_opts_default()
+    o.p, o.M = 8, 200
+    o.pair_kernel = pair_kernel
+    h = ctypes.c_void_p()
+    assert B.load().psum_plan_create_ex(ctypes.byref(o), ctypes.byref(h)) == B.PSUM_ERR_ARG
