@@ -62,7 +62,9 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU budget of the oracle sample")
     ap.add_argument("--n", type=int, default=N_MAIN, help="charges (smaller cases are for profiling only)")
     ap.add_argument("--pairs", default="auto", choices=["auto", "one-sided", "symmetric"],
-                    help="pair kernel of the charge sums (auto: symmetric from 16 tiles of 512 charges)")
+                    help="pair kernel of the charge sums (auto: symmetric from 12 tiles of 512 charges)")
+    ap.add_argument("--checks", default="auto", choices=["auto", "points", "layers"],
+                    help="form of the check-point sums (auto: the two image layers at the M points)")
     return ap.parse_args()
 
 
@@ -209,8 +211,12 @@ def run_psum(args):
     # every rank evaluates its own replica of the system (weak scaling, no exchange)
     s = W.uniform_gauss(N=args.n, d=D_MAIN, p=P_MAIN, M=M_MAIN, seed=SEED_MAIN + rank)
     pairs_step = 27 * s.N * (s.N + 2 * s.M)
-    pc = B.PeriodicCoulomb(s.d, s.p, s.M, precision="fp32c", pairs=args.pairs)
+    pc = B.PeriodicCoulomb(s.d, s.p, s.M, precision="fp32c", pairs=args.pairs, checks=args.checks)
     pair_kernel, image_groups = B.psum_pair_kernel(pc.plan, s.N)
+    check_form = B.psum_check_form(pc.plan)
+    # interactions the kernels evaluate: the charge sums, and the check sums as 27 images at
+    # the 2M points, or as the two 9-image layers at the M points (same right-hand side)
+    pairs_evaluated = 27 * s.N * s.N + (18 * s.N * s.M if check_form == "layers" else 27 * s.N * 2 * s.M)
     B.psum_profile(pc.plan, True)
     x = torch.as_tensor(s.x, dtype=torch.float64, device=dev)
     q = torch.as_tensor(s.q, dtype=torch.float64, device=dev)
@@ -286,6 +292,10 @@ def run_psum(args):
            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": workload_name(s.N), "N": s.N, "p": s.p, "M": s.M, "box": list(s.d),
                       "near_images": 27, "pairs_per_step": pairs_step,
+                      "check_form": check_form + (" (phi_near(y~) - phi_near(y) as the image layer beyond "
+                                                  "the partner's face minus the opposite layer, 18 images at "
+                                                  "the M points)" if check_form == "layers" else ""),
+                      "pairs_evaluated_per_step": pairs_evaluated,
                       "precision": "fp32c: f32 pair arithmetic on group-relative coordinates, two-sum "
                                    "compensated accumulation; f64 sort keys, fit, mean and far field",
                       "l2": "flushed before every timed step (256 MiB write, outside the events)",

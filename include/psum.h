@@ -12,7 +12,8 @@
  * phi_mean = 0, the Ewald convention of App. D).  phi is split into
  *
  *   phi_near: direct sum over the box and its neighbour images (Eq. 3),
- *             evaluated at the charges and at 2M check points, and
+ *             evaluated at the charges and at the M check points and their
+ *             partners (or as the partners' two-layer difference, PSUM_CHECKS_*), and
  *   phi_far:  C_1 + sum_{t>=2} C_t R_t(y/R0), a regular-solid-harmonic local
  *             expansion of maximum degree p (Eqs. 1.6-1.8) whose coefficients
  *             are the least-squares solution of the periodicity conditions at
@@ -90,6 +91,18 @@ extern "C" {
                                     psum_eval_host, psum_eval_graph and psum_energy, and FP32C batches;
                                     one-sided elsewhere).  Same sums, different rounding order. */
 
+/* form of the right-hand side f_l = phi_near(y~_l) - phi_near(y_l) (psum_opts.check_form).
+ * The partner y~_l = y_l - s d_k e_k (s = +-1) sees the near block shifted by one period
+ * along k, so the two block sums differ by two image layers only:
+ *   f_l = sum_i q_i [ sum_{i_k = s (K_k + 1)} K(y_l - x_i - p) - sum_{i_k = -s K_k} K(y_l - x_i - p) ]
+ * (the other two image indices over their block ranges): 2 (2K_a+1)(2K_b+1) images at M
+ * points instead of (2K_1+1)(2K_2+1)(2K_3+1) images at 2M points (18 x M against 27 x 2M for
+ * the 3x3x3 block). */
+#define PSUM_CHECKS_AUTO    0  /* layers where they apply (FP32C and FF plans without ball trimming,
+                                  single systems), points otherwise */
+#define PSUM_CHECKS_POINTS  1  /* phi_near at y_l and at y~_l, differenced in float64 */
+#define PSUM_CHECKS_LAYERS  2  /* the two-layer form; PSUM_ERR_ARG for FP64 and ball-trimmed plans */
+
 #define PSUM_MEAN_ZERO 0  /* C_1 makes the box mean of phi zero (Eq. pfx3, phi_mean = 0) */
 #define PSUM_MEAN_NONE 1  /* C_1 = 0 (potential defined up to a constant, Sec. 3) */
 
@@ -119,6 +132,7 @@ typedef struct psum_opts {
     int n_rbf;       /* number of RBF centres, 1..4096 (0: 256, the paper's choice) */
     double rbf_radius;  /* centres at rbf_radius R0, > 1 (0: on S_b, i.e. at lambda_eff R0) */
     int pair_kernel;    /* PSUM_PAIRS_AUTO, PSUM_PAIRS_ONE_SIDED or PSUM_PAIRS_SYMMETRIC */
+    int check_form;     /* PSUM_CHECKS_AUTO, PSUM_CHECKS_POINTS or PSUM_CHECKS_LAYERS */
 } psum_opts;
 
 typedef struct psum_info {
@@ -135,7 +149,7 @@ typedef struct psum_info {
 
 /* Fill `o` with the defaults: unit cube, p = 8, M = 200, PSUM_FP64,
    PSUM_MEAN_ZERO, K = (1,1,1), PSUM_POINTS_FIBONACCI, lambda = 0, PSUM_BASIS_SPHERICAL,
-   n_rbf = 256, rbf_radius = 0, PSUM_PAIRS_AUTO. */
+   n_rbf = 256, rbf_radius = 0, PSUM_PAIRS_AUTO, PSUM_CHECKS_AUTO. */
 void psum_opts_default(psum_opts *o);
 
 /* Algorithm "set" (Sec. 2.3.1): circumradius R0 (step 1), M check points on the
@@ -242,12 +256,17 @@ int psum_plan_info(psum_plan_t plan, psum_info *info);
  * Host only; PSUM_ERR_ARG for a null plan or kernel pointer or N < 0. */
 int psum_pair_kernel(psum_plan_t plan, int64_t N, int *kernel, int *image_groups);
 
+/* The form of the check-point sums psum_eval runs on this plan, after the automatic choice:
+ * *form = PSUM_CHECKS_POINTS or PSUM_CHECKS_LAYERS.  Host only; PSUM_ERR_ARG for a null plan
+ * or form pointer. */
+int psum_check_form(psum_plan_t plan, int *form);
+
 /* Stage timing.  With profiling enabled, psum_eval records CUDA events on its
  * stream around each stage; psum_last_timings waits for `stream` and writes the
  * PSUM_NUM_STAGES durations (milliseconds) of the last evaluation:
  *   [0] validation, spatial sort and packing
  *   [1] near-field sum at the charges (potential and gradient)
- *   [2] near-field sum at the 2M check points (potential)
+ *   [2] near-field sum at the check points (potential, or its two-layer difference)
  *   [3] reductions, right-hand side, least squares, mean and C_1
  *   [4] far field, combination and write-back
  * Returns PSUM_ERR_ARG if profiling is off. */

@@ -35,6 +35,7 @@ PRECISIONS = {"fp64": PSUM_FP64, "fp32c": PSUM_FP32C, "ff": PSUM_FF}
 POINTS = {"fibonacci": 0, "gauss": 1}
 BASES = {"spherical": 0, "rbf": 1}
 PAIR_KERNELS = {"auto": 0, "one-sided": 1, "symmetric": 2}
+CHECK_FORMS = {"auto": 0, "points": 1, "layers": 2}
 MEAN_MODES = {"zero": PSUM_MEAN_ZERO, "none": PSUM_MEAN_NONE}
 
 
@@ -42,7 +43,8 @@ class psum_opts(ctypes.Structure):
     _fields_ = [("d", ctypes.c_double * 3), ("p", ctypes.c_int), ("M", ctypes.c_int),
                 ("precision", ctypes.c_int), ("mean_mode", ctypes.c_int), ("K", ctypes.c_int * 3),
                 ("points", ctypes.c_int), ("lambda_", ctypes.c_double), ("basis", ctypes.c_int),
-                ("n_rbf", ctypes.c_int), ("rbf_radius", ctypes.c_double), ("pair_kernel", ctypes.c_int)]
+                ("n_rbf", ctypes.c_int), ("rbf_radius", ctypes.c_double), ("pair_kernel", ctypes.c_int),
+                ("check_form", ctypes.c_int)]
 
 
 class psum_info(ctypes.Structure):
@@ -101,6 +103,7 @@ def load(build_if_needed: bool = True):
     lib.psum_get_coeffs.argtypes = [_vp, _dp, _vp]
     lib.psum_plan_info.argtypes = [_vp, ctypes.POINTER(psum_info)]
     lib.psum_pair_kernel.argtypes = [_vp, ctypes.c_int64, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+    lib.psum_check_form.argtypes = [_vp, ctypes.POINTER(ctypes.c_int)]
     lib.psum_profile.argtypes = [_vp, ctypes.c_int]
     lib.psum_last_timings.argtypes = [_vp, _dp, _vp]
     lib.psum_launch_count.argtypes = [_vp, ctypes.POINTER(ctypes.c_int64)]
@@ -120,7 +123,7 @@ def load(build_if_needed: bool = True):
     lib.psum_strerror.restype = ctypes.c_char_p
     for name in ("psum_plan_create", "psum_plan_create_ex", "psum_eval", "psum_eval_host", "psum_eval_noalloc",
                  "psum_sync",
-                 "psum_get_coeffs", "psum_plan_info", "psum_pair_kernel", "psum_profile", "psum_last_timings", "psum_launch_count",
+                 "psum_get_coeffs", "psum_plan_info", "psum_pair_kernel", "psum_check_form", "psum_profile", "psum_last_timings", "psum_launch_count",
                  "psum_energy", "psum_energy_backward", "psum_eval_points", "psum_debug_inject_timeout", "psum_eval_graph", "psum_batch_create", "psum_batch_eval",
                  "psum_batch_sync", "psum_batch_get_coeffs", "psum_batch_get_info"):
         getattr(lib, name).restype = ctypes.c_int
@@ -170,9 +173,10 @@ def psum_plan_create(d1: float, d2: float, d3: float, p: int, M: int):
 
 def psum_plan_create_ex(d, p: int, M: int, precision="fp64", mean="zero", K=(1, 1, 1), points="fibonacci",
                         lam: float = 0.0, basis="spherical", n_rbf: int = 256, rbf_radius: float = 0.0,
-                        pairs="auto"):
+                        pairs="auto", checks="auto"):
     o = psum_opts_default()
     o.pair_kernel = PAIR_KERNELS[pairs] if isinstance(pairs, str) else int(pairs)
+    o.check_form = CHECK_FORMS[checks] if isinstance(checks, str) else int(checks)
     o.lambda_ = float(lam)
     o.basis = BASES[basis] if isinstance(basis, str) else int(basis)
     o.n_rbf = int(n_rbf)
@@ -284,6 +288,13 @@ def psum_pair_kernel(plan, N: int):
     k, g = ctypes.c_int(0), ctypes.c_int(0)
     _check(load().psum_pair_kernel(plan, int(N), ctypes.byref(k), ctypes.byref(g)), "psum_pair_kernel")
     return ("symmetric" if k.value == 2 else "one-sided"), g.value
+
+
+def psum_check_form(plan) -> str:
+    """The form of the check-point sums psum_eval runs: "points" or "layers"."""
+    f = ctypes.c_int(0)
+    _check(load().psum_check_form(plan, ctypes.byref(f)), "psum_check_form")
+    return "layers" if f.value == 2 else "points"
 
 
 def psum_profile(plan, enable: bool = True):
@@ -412,9 +423,10 @@ class PeriodicCoulomb:
     """A plan plus tensor-returning evaluation (allocation through torch only)."""
 
     def __init__(self, d, p: int, M: int, precision="fp64", mean="zero", K=(1, 1, 1), points="fibonacci",
-                 lam: float = 0.0, basis="spherical", n_rbf: int = 256, rbf_radius: float = 0.0, pairs="auto"):
+                 lam: float = 0.0, basis="spherical", n_rbf: int = 256, rbf_radius: float = 0.0, pairs="auto",
+                 checks="auto"):
         self.plan = psum_plan_create_ex(d, p, M, precision, mean, K, points, lam, basis, n_rbf, rbf_radius,
-                                        pairs)
+                                        pairs, checks)
         self.info = psum_plan_info(self.plan)
 
     def at(self, x, q, y, grad: bool = True, stream=None, check: bool = True):

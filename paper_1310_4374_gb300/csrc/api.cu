@@ -104,7 +104,12 @@ size_t layout(Plan& pl, int64_t N, char* base, Layout& L, bool backward = false,
         int64_t gmax = (int64_t)pl.num_sms * near32_occupancy_ctas(n_img, 0, trimmed, pl.opt.precision == PSUM_FF);
         if (g_cap > 0 && gmax > g_cap) gmax = g_cap;
         L.Ln = near_partition(L.n_tiles, L.n_chunks, n_img, gmax, ipc);
-        L.Lc = near_partition(pl.n_check_tiles, L.n_chunks, n_img, gmax, g_cap > 0 ? 1 : kCheckItemsPerCta);
+        // check sums: the 2M points with the block's images, or the M points with their
+        // class's two image layers
+        const bool layers = pl.lc_tiles > 0;
+        const int64_t c_tiles = layers ? pl.lc_tiles : pl.n_check_tiles;
+        L.Lc = near_partition(c_tiles, L.n_chunks, layers ? pl.lc_img : n_img, gmax,
+                              g_cap > 0 ? 1 : kCheckItemsPerCta);
         // the symmetric kernel: FP32C charges, block image set, a normal (growing) scratch
         L.sym = false;
         const int pk = pl.opt.pair_kernel;
@@ -145,8 +150,8 @@ size_t layout(Plan& pl, int64_t N, char* base, Layout& L, bool backward = false,
             L.torg = b.take<double>(4 * (size_t)n_groups);
         }
         L.part_n = b.take<double>(L.sym ? L.S.doubles : (size_t)L.n_tiles * L.Ln.max_contrib * 4 * kTile32);
-        L.part_c = b.take<double>((size_t)pl.n_check_tiles * L.Lc.max_contrib * kTile32);
-        L.phi_c = b.take<double>((size_t)pl.n_check_tiles * kTile32);
+        L.part_c = b.take<double>((size_t)c_tiles * L.Lc.max_contrib * kTile32);
+        L.phi_c = b.take<double>((size_t)c_tiles * kTile32);
     } else {
         L.n_tiles = (NT + kTile64 - 1) / kTile64;
         L.n_chunks = (N + kTile64 - 1) / kTile64;
@@ -223,11 +228,12 @@ size_t layout(Plan& pl, int64_t N, char* base, Layout& L, bool backward = false,
         L.gpsi = b.take<double>(3 * (size_t)L.n_pts);
         const int tile = fp32 ? kTile32 : kTile64;
         L.part_b = b.take<double>((size_t)L.n_tiles * L.Lb.max_contrib * 4 * tile);
-        if (fp32)
+        if (fp32) {
             L.chk_src32 = b.take<float4>(2 * (size_t)n_chk_chunks * kNearChunk);
             if (pl.opt.precision == PSUM_FF) L.chk_src32lo = b.take<float4>(2 * (size_t)n_chk_chunks * kNearChunk);
-        else
+        } else {
             L.chk_src64 = b.take<double4_32a>((size_t)n_chk_chunks * kNearChunk);
+        }
     }
     return b.off + 256;
 }
@@ -325,7 +331,13 @@ int queue_forward(psum_plan_s* h, int64_t N, const double* x, const double* q, d
         TRY(launch_near64(true, L.pk64, t64, pl.d_shifts, L.part_n, L.Ln, st, pl.Rb));
     }
     if (h->profile) TRY(cudaEventRecord(h->ev[2], st));
-    if (fp32) {
+    const bool layers = fp32 && pl.lc_tiles > 0;
+    if (layers) {
+        const float4* ct = (const float4*)pl.d_lc_tgt;
+        const size_t half = 2 * (size_t)pl.lc_tiles * kTile32;         // hi parts, then lo parts
+        TRY(launch_near32(false, L.pk32, L.pk32lo, L.org, ct, ct + half, pl.d_lc_org, pl.d_lc_shifts, L.part_c,
+                          L.Lc, st, 0, nullptr, 0.0, ff, pl.d_lc_cls, pl.d_lc_w));
+    } else if (fp32) {
         const float4* ct = (const float4*)pl.d_check_tgt;
         const size_t half = 2 * (size_t)pl.n_check_tiles * kTile32;    // hi parts, then lo parts
         TRY(launch_near32(false, L.pk32, L.pk32lo, L.org, ct, ct + half, pl.d_check_org, pl.d_shifts, L.part_c,
@@ -340,7 +352,8 @@ int queue_forward(psum_plan_s* h, int64_t N, const double* x, const double* q, d
         TRY(launch_sym_reduce(L.part_n, N, L.S, L.phi_n, L.grad_n, st, !fp32));
     else
         TRY(launch_near_reduce(L.part_n, sep ? T : N, tile, 4, L.Ln, L.phi_n, L.grad_n, st));
-    TRY(launch_near_reduce(L.part_c, pl.n_check, tile, 1, L.Lc, L.phi_c, nullptr, st));
+    TRY(launch_near_reduce(L.part_c, layers ? (int64_t)pl.lc_tiles * kTile32 : pl.n_check, tile, 1, L.Lc, L.phi_c,
+                           nullptr, st));
     h->launches += 4;   // two near-field kernels, two reductions
     const bool zero_mean = o.mean_mode == PSUM_MEAN_ZERO;
     if (zero_mean) {
@@ -354,7 +367,8 @@ int queue_forward(psum_plan_s* h, int64_t N, const double* x, const double* q, d
         }
         h->launches += 1;
     }
-    TRY(launch_project(pl.d_pinv, P - 1, M, L.phi_c, pl.d_check_pos, L.f, pl.d_C, st));
+    TRY(launch_project(pl.d_pinv, P - 1, M, L.phi_c, layers ? pl.d_lc_pos : pl.d_check_pos, L.f, pl.d_C, st,
+                       layers));
     TRY(launch_constant(pl.d_C, pl.d_Rbox, P, L.mean_part, L.nblk_mean, 1.0 / (o.d[0] * o.d[1] * o.d[2]),
                         zero_mean ? 1 : 0, st));
     if (h->profile) TRY(cudaEventRecord(h->ev[4], st));
@@ -476,6 +490,10 @@ bool valid_opts(const psum_opts* o) {
     if (o->pair_kernel != PSUM_PAIRS_AUTO && o->pair_kernel != PSUM_PAIRS_ONE_SIDED &&
         o->pair_kernel != PSUM_PAIRS_SYMMETRIC)
         return false;
+    if (o->check_form != PSUM_CHECKS_AUTO && o->check_form != PSUM_CHECKS_POINTS &&
+        o->check_form != PSUM_CHECKS_LAYERS)
+        return false;
+    if (o->check_form == PSUM_CHECKS_LAYERS && (o->precision == PSUM_FP64 || o->lambda > 0.0)) return false;
     if (o->mean_mode != PSUM_MEAN_ZERO && o->mean_mode != PSUM_MEAN_NONE) return false;
     return true;
 }
@@ -499,6 +517,7 @@ void psum_opts_default(psum_opts* o) {
     o->n_rbf = 256;
     o->rbf_radius = 0.0;
     o->pair_kernel = PSUM_PAIRS_AUTO;
+    o->check_form = PSUM_CHECKS_AUTO;
 }
 
 int psum_plan_create_ex(const psum_opts* o, psum_plan_t* out) {
@@ -699,6 +718,12 @@ int psum_pair_kernel(psum_plan_t h, int64_t N, int* kernel, int* image_groups) {
     layout(h->pl, N, nullptr, L);
     *kernel = L.sym ? PSUM_PAIRS_SYMMETRIC : PSUM_PAIRS_ONE_SIDED;
     if (image_groups) *image_groups = L.sym ? L.S.tab.one.n_g : 0;
+    return PSUM_OK;
+}
+
+int psum_check_form(psum_plan_t h, int* form) {
+    if (!h || !form) return PSUM_ERR_ARG;
+    *form = h->pl.lc_tiles > 0 ? PSUM_CHECKS_LAYERS : PSUM_CHECKS_POINTS;
     return PSUM_OK;
 }
 

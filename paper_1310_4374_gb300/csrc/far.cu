@@ -145,10 +145,12 @@ __global__ void __launch_bounds__(kRedThreads) k_box_mean_ball(const double* __r
 // ---------------------------------------------------------------------------
 constexpr int kProjThreads = 256;
 
+// f_l = phi_near(y~_l) - phi_near(y_l); with `layers` the check sums already hold the
+// difference (the two image layers at y_l), at packed position check_pos[l].
 __global__ void k_rhs(const double* __restrict__ phi_check, const int* __restrict__ check_pos, int M,
-                      double* __restrict__ f) {
+                      int layers, double* __restrict__ f) {
     const int l = blockIdx.x * blockDim.x + threadIdx.x;
-    if (l < M) f[l] = phi_check[check_pos[M + l]] - phi_check[check_pos[l]];
+    if (l < M) f[l] = layers ? phi_check[check_pos[l]] : phi_check[check_pos[M + l]] - phi_check[check_pos[l]];
 }
 
 __global__ void __launch_bounds__(kProjThreads) k_project(const double* __restrict__ pinv, int rows, int M,
@@ -370,8 +372,8 @@ cudaError_t launch_box_mean_ball(const double* x, const double* q, const uint32_
 }
 
 cudaError_t launch_project(const double* pinv, int rows, int M, const double* phi_check, const int* check_pos,
-                           double* f, double* C, cudaStream_t st) {
-    k_rhs<<<(M + 255) / 256, 256, 0, st>>>(phi_check, check_pos, M, f);
+                           double* f, double* C, cudaStream_t st, bool layers) {
+    k_rhs<<<(M + 255) / 256, 256, 0, st>>>(phi_check, check_pos, M, layers ? 1 : 0, f);
     const int per = kProjThreads / 32;
     k_project<<<(rows + per - 1) / per, kProjThreads, 0, st>>>(pinv, rows, M, f, C);
     return cudaGetLastError();

@@ -9,7 +9,8 @@ namespace psum {
 cudaError_t launch_near32(bool grad, const float4* src_hi, const float4* src_lo, const double* src_org,
                           const float4* tgt_hi, const float4* tgt_lo, const double* tgt_org, const double* shifts,
                           double* partial, const NearPlanLaunch& L, cudaStream_t st, int variant = 0,
-                          const double* src_x = nullptr, double Rb = 0.0, bool ff = false);
+                          const double* src_x = nullptr, double Rb = 0.0, bool ff = false,
+                          const int* tgt_cls = nullptr, const float* img_w = nullptr);
 cudaError_t launch_near64(bool grad, const double4_32a* src, const double4_32a* tgt, const double* shifts,
                           double* partial, const NearPlanLaunch& L, cudaStream_t st, double Rb = 0.0);
 cudaError_t launch_near_reduce(const double* partial, int64_t n_valid, int tile_size, int nq,
@@ -58,7 +59,7 @@ cudaError_t launch_box_mean_ball(const double* x, const double* q, const uint32_
                                  const double d[3], const double* shifts, int n_img, double Rb, double* partial,
                                  int nblk, cudaStream_t st);
 cudaError_t launch_project(const double* pinv, int rows, int M, const double* phi_check, const int* check_pos,
-                           double* f, double* C, cudaStream_t st);
+                           double* f, double* C, cudaStream_t st, bool layers = false);
 cudaError_t launch_constant(double* C, const double* Rbox, int P, const double* mean_partial, int nblk,
                             double inv_V0, int zero_mean, cudaStream_t st);
 // tab32 != nullptr: the far field in float (FP32C plans), else in double with tab64

@@ -54,6 +54,11 @@ struct Near32Args {
     int inject;              // test hook: expect 16 bytes more than the copies bring
     int max_contrib, max_img;
     NearSysTable tab;
+    // two-layer check sums (potential only): the class of each target group; the image
+    // vector of (class c, image j) is shifts[shift0 + c n_img + j] and its weight
+    // img_w[shift0 + c n_img + j].  Null: one image list, weight 1.
+    const int* tgt_cls;
+    const float* img_w;
 };
 
 // Two register budgets of the same kernel: 4 resident CTAs per SM (up to 128 registers) or
@@ -71,9 +76,11 @@ __global__ void __launch_bounds__(kThreads32, kMinB) k_near32(Near32Args a) {
     __shared__ float2 s_tl[kFF ? 3 : 1][2][kThreads32];   // FF: target lo offsets
     __shared__ float2 s_acc[NQ][2][2][kThreads32];        // [quantity][pair][hi, lo]
     extern __shared__ float4 s_dyn4[];                    // [max_img][kTgt32][6] deltas, [max_img] flags,
-    float* s_delta = (float*)s_dyn4;                      // then (trimmed plans) the compacted
-    int* s_near = (int*)(s_delta + 6 * kTgt32 * a.max_img);   // sources of a straddling unit
-    float4* s_hm = s_dyn4 + (6 * kTgt32 * a.max_img + a.max_img + 3) / 4;
+    float* s_delta = (float*)s_dyn4;                      // potential only: [max_img][kTgt32] weights,
+    int* s_near = (int*)(s_delta + 6 * kTgt32 * a.max_img);   // then (trimmed plans) the compacted
+    float* s_w = (float*)(s_near + a.max_img);            // sources of a straddling unit
+    constexpr int kWts = kGrad ? 0 : kTgt32;
+    float4* s_hm = s_dyn4 + (6 * kTgt32 * a.max_img + a.max_img + kWts * a.max_img + 3) / 4;
 
     __shared__ int s_item;
     __shared__ int s_fail;
@@ -171,10 +178,23 @@ __global__ void __launch_bounds__(kThreads32, kMinB) k_near32(Near32Args a) {
             for (int im = tid; im < n_img; im += kThreads32) {
                 const double* sh = a.shifts + 3 * (shift0 + im);
                 int nr = 0;
+                bool weighted = false;
                 for (int k = 0; k < kTgt32; ++k) {
                     const double* to = a.tgt_org + 4 * (cur_tile * kTgt32 + k);
+                    const double* shk = sh;
+                    if constexpr (!kGrad) {
+                        float wk = 1.f;
+                        if (a.tgt_cls) {   // the group's own layer image and its weight
+                            const int e = shift0 + a.tgt_cls[cur_tile * kTgt32 + k] * n_img + im;
+                            shk = a.shifts + 3 * e;
+                            wk = a.img_w[e];
+                        }
+                        s_w[im * kTgt32 + k] = wk;
+                        weighted = weighted || wk != 0.f;
+                    }
                     // offset of the target-group origin from the shifted chunk origin, as hi + lo
-                    const double D0 = (to[0] - so[0]) - sh[0], D1 = (to[1] - so[1]) - sh[1], D2 = (to[2] - so[2]) - sh[2];
+                    const double D0 = (to[0] - so[0]) - shk[0], D1 = (to[1] - so[1]) - shk[1],
+                                 D2 = (to[2] - so[2]) - shk[2];
                     float* dl = s_delta + 6 * (im * kTgt32 + k);
                     dl[0] = (float)D0; dl[1] = (float)D1; dl[2] = (float)D2;
                     dl[3] = (float)(D0 - (double)dl[0]); dl[4] = (float)(D1 - (double)dl[1]);
@@ -191,6 +211,7 @@ __global__ void __launch_bounds__(kThreads32, kMinB) k_near32(Near32Args a) {
                     if (c2s > ro * ro) nr = kUnitOutside;
                     else if (ri < 0.0 || c2s > ri * ri) nr |= kUnitStraddle;
                 }
+                if (!kGrad && !weighted) nr = kUnitOutside;   // padding image of every group: skip
                 s_near[im] = nr;
             }
             const long long limit = a.inject ? (1LL << 12) : kCopySpinLimit;
@@ -209,10 +230,15 @@ __global__ void __launch_bounds__(kThreads32, kMinB) k_near32(Near32Args a) {
         }
         const float* dl = s_delta + 6 * (img * kTgt32);
         const int cls = s_near[img];
-        if (kTrim && (cls & kUnitOutside)) {
+        if ((kTrim || !kGrad) && (cls & kUnitOutside)) {
             ++u;
             continue;
         }
+        // potential only: the weight of each target group for this image (1, or +-1 and 0
+        // for the two-layer check sums); multiplying by it is exact
+        auto wpair = [&](int j) {
+            return make_float2(s_w[img * kTgt32 + 2 * j], s_w[img * kTgt32 + 2 * j + 1]);
+        };
         // sources the unit's pair loops run over: the staged chunk, or for a unit that
         // straddles the ball its sources inside the ball, compacted (padded to whole blocks
         // of 4 with far-away zero charges)
@@ -272,6 +298,10 @@ __global__ void __launch_bounds__(kThreads32, kMinB) k_near32(Near32Args a) {
 #pragma unroll
                 for (int qi = 0; qi < 4; ++qi) acc[qi][0] = acc[qi][1] = make_float2(0.f, 0.f);
                 pair_loop_ff<kGrad>(uhi, ulo, nTh, nTl, acc, un);
+                if constexpr (!kGrad) {
+                    acc[0][0] = __fmul2_rn(acc[0][0], wpair(j));
+                    acc[0][1] = __fmul2_rn(acc[0][1], wpair(j));
+                }
 #pragma unroll
                 for (int qi = 0; qi < NQ; ++qi) {
                     two_sum_acc2(s_acc[qi][j][0][tid], s_acc[qi][j][1][tid], acc[qi][0]);
@@ -293,6 +323,7 @@ __global__ void __launch_bounds__(kThreads32, kMinB) k_near32(Near32Args a) {
                     float2 aphi[1] = {make_float2(0.f, 0.f)}, agx[1] = {aphi[0]}, agy[1] = {aphi[0]},
                            agz[1] = {aphi[0]};
                     pair_loop_far<kGrad, 1>(uhi, nx, ny, nz, aphi, agx, agy, agz, un);
+                    if constexpr (!kGrad) aphi[0] = __fmul2_rn(aphi[0], wpair(j));
                     two_sum_acc2(s_acc[0][j][0][tid], s_acc[0][j][1][tid], aphi[0]);
                     if (kGrad) {
                         two_sum_acc2(s_acc[1 % NQ][j][0][tid], s_acc[1 % NQ][j][1][tid], agx[0]);
@@ -320,6 +351,10 @@ __global__ void __launch_bounds__(kThreads32, kMinB) k_near32(Near32Args a) {
                 float2 aphi = make_float2(0.f, 0.f), aphi_lo = aphi, agx = aphi, agy = aphi, agz = aphi;
                 pair_loop_near<kGrad>(uhi, ulo, nh[0], nh[1], nh[2], nl[0], nl[1], nl[2], aphi, aphi_lo, agx, agy,
                                       agz, un);
+                if constexpr (!kGrad) {
+                    aphi = __fmul2_rn(aphi, wpair(j));
+                    aphi_lo = __fmul2_rn(aphi_lo, wpair(j));
+                }
                 two_sum_acc2(s_acc[0][j][0][tid], s_acc[0][j][1][tid], aphi);
                 s_acc[0][j][1][tid] = __fadd2_rn(s_acc[0][j][1][tid], aphi_lo);
                 if (kGrad) {
@@ -344,6 +379,7 @@ __global__ void __launch_bounds__(kThreads32, kMinB) k_near32(Near32Args a) {
             pair_loop_far<kGrad, 2>(uhi, nx, ny, nz, aphi, agx, agy, agz, un);
 #pragma unroll
             for (int j = 0; j < 2; ++j) {
+                if constexpr (!kGrad) aphi[j] = __fmul2_rn(aphi[j], wpair(j));
                 two_sum_acc2(s_acc[0][j][0][tid], s_acc[0][j][1][tid], aphi[j]);
                 if (kGrad) {
                     two_sum_acc2(s_acc[1 % NQ][j][0][tid], s_acc[1 % NQ][j][1][tid], agx[j]);
@@ -507,15 +543,16 @@ __global__ void __launch_bounds__(32 * kReduceWarps) k_near_reduce(const double*
 // ---------------------------------------------------------------------------
 // Host launchers
 // ---------------------------------------------------------------------------
-size_t near32_dyn_smem(int n_img, bool trimmed) {
-    const size_t head = ((6 * kTgt32 * (size_t)n_img + n_img + 3) / 4) * sizeof(float4);
+size_t near32_dyn_smem(int n_img, bool trimmed, bool grad) {
+    const size_t head = ((6 * kTgt32 * (size_t)n_img + n_img + (grad ? 0 : kTgt32 * (size_t)n_img) + 3) / 4) *
+                        sizeof(float4);
     return head + (trimmed ? sizeof(float4) * 4 * kNearChunk : 0);   // compacted sources (hi, lo parts)
 }
 
 cudaError_t launch_near32(bool grad, const float4* src_hi, const float4* src_lo, const double* src_org,
                           const float4* tgt_hi, const float4* tgt_lo, const double* tgt_org, const double* shifts,
                           double* partial, const NearPlanLaunch& L, cudaStream_t st, int variant,
-                          const double* src_x, double Rb, bool ff) {
+                          const double* src_x, double Rb, bool ff, const int* tgt_cls, const float* img_w) {
     Near32Args a;
     a.status = L.status;
     a.n_status = L.n_status;
@@ -528,7 +565,10 @@ cudaError_t launch_near32(bool grad, const float4* src_hi, const float4* src_lo,
     a.tab = L.tab;
     a.src_x = src_x;
     a.Rb = Rb;
-    const size_t smem = near32_dyn_smem(L.max_img, Rb > 0.0);
+    if ((tgt_cls != nullptr) != (img_w != nullptr) || (tgt_cls && (grad || Rb > 0.0))) return cudaErrorInvalidValue;
+    a.tgt_cls = tgt_cls;
+    a.img_w = img_w;
+    const size_t smem = near32_dyn_smem(L.max_img, Rb > 0.0, grad);
     if (!L.counter) return cudaErrorInvalidValue;
     const cudaError_t e = cudaMemsetAsync(L.counter, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
@@ -582,7 +622,7 @@ cudaError_t launch_near_reduce(const double* partial, int64_t n_valid, int tile_
 
 int near32_occupancy_ctas(int n_img, int variant, bool trimmed, bool ff) {
     int nb = 0;
-    const size_t smem = near32_dyn_smem(n_img, trimmed);
+    const size_t smem = near32_dyn_smem(n_img, trimmed, true);
     constexpr int B0 = kNear32MinBlocks[0], B1 = kNear32MinBlocks[1];
     if (ff && trimmed)
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_near32<true, B0, true, true>, kThreads32, smem);

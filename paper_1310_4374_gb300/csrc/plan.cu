@@ -196,6 +196,134 @@ static int upload(T** dst, const T* src, size_t count) {
     return PSUM_OK;
 }
 
+// Packs points for the float32 pair kernels: slot i of the pack holds point slot_pt[i]
+// (-1: padding far outside the box, never read back), 2 float4 of hi parts per slot
+// followed by the same of lo parts, each an offset from its group's float64 origin (the
+// centre of the group's bounding box; 4 doubles per group with the radius about it).
+static void pack_groups32(const std::vector<double>& pts, const std::vector<int>& slot_pt, int ngroups,
+                          std::vector<float4>& pk, std::vector<double>& org) {
+    const size_t npk = 2 * (size_t)ngroups * kNearChunk;
+    pk.assign(2 * npk, make_float4(0.f, 0.f, 0.f, 0.f));
+    for (size_t i = 0; i < npk; ++i) pk[i] = make_float4(1e3f, 1e3f, 1e3f, 1e3f);
+    org.assign(4 * (size_t)ngroups, 0.0);
+    for (int g = 0; g < ngroups; ++g) {
+        double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+        const int i0 = g * kNearChunk, i1 = (g + 1) * kNearChunk;
+        for (int i = i0; i < i1; ++i) {
+            if (slot_pt[i] < 0) continue;
+            for (int c = 0; c < 3; ++c) {
+                lo[c] = std::min(lo[c], pts[3 * (size_t)slot_pt[i] + c]);
+                hi[c] = std::max(hi[c], pts[3 * (size_t)slot_pt[i] + c]);
+            }
+        }
+        for (int c = 0; c < 3; ++c) org[4 * g + c] = lo[c] <= hi[c] ? 0.5 * (lo[c] + hi[c]) : 0.0;
+        double r2max = 0.0;
+        for (int i = i0; i < i1; ++i) {
+            if (slot_pt[i] < 0) continue;
+            const double* q = &pts[3 * (size_t)slot_pt[i]];
+            const double r[3] = {q[0] - org[4 * g], q[1] - org[4 * g + 1], q[2] - org[4 * g + 2]};
+            r2max = std::max(r2max, r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+            const float f[3] = {(float)r[0], (float)r[1], (float)r[2]};
+            const float l[3] = {(float)(r[0] - (double)f[0]), (float)(r[1] - (double)f[1]),
+                                (float)(r[2] - (double)f[2])};
+            pk[2 * (size_t)i] = make_float4(f[0], f[0], f[1], f[1]);
+            pk[2 * (size_t)i + 1] = make_float4(f[2], f[2], 0.f, 0.f);
+            pk[npk + 2 * (size_t)i] = make_float4(l[0], l[0], l[1], l[1]);
+            pk[npk + 2 * (size_t)i + 1] = make_float4(l[2], l[2], 0.f, 0.f);
+        }
+        org[4 * g + 3] = std::sqrt(r2max);
+    }
+}
+
+// The two-layer form of the right-hand side (float32 plans without ball trimming).  The
+// partner of y_l is y~_l = y_l - s d_k e_k, so the near block seen from y~_l is the block
+// seen from y_l shifted by one period along k: phi_near(y~_l) - phi_near(y_l) is the sum
+// over the image layer i_k = s (K_k + 1) minus the sum over the layer i_k = -s K_k (Eq. 3
+// at both points; algorithm "get", step 3).  Class c = 2k + (s < 0) fixes the two layers;
+// images j < Lmax of a class are its upper layer (weight +1), j >= Lmax its lower layer
+// (weight -1), and a class whose layers are smaller than the largest, Lmax, is padded with
+// weight-0 entries.
+static int build_check_layers(Plan& pl, const double d[3]) {
+    const int M = pl.opt.M;
+    const int* K = pl.opt.K;
+    int Lsize[3], Lmax = 0;
+    for (int k = 0; k < 3; ++k) {
+        Lsize[k] = (2 * K[(k + 1) % 3] + 1) * (2 * K[(k + 2) % 3] + 1);
+        Lmax = std::max(Lmax, Lsize[k]);
+    }
+    const int n_img = 2 * Lmax;
+    std::vector<double> sh(6 * (size_t)n_img * 3, 0.0);
+    std::vector<float> w(6 * (size_t)n_img, 0.f);
+    for (int c = 0; c < 6; ++c) {
+        const int k = c / 2, s = (c & 1) ? -1 : 1;
+        const int a = (k + 1) % 3, b = (k + 2) % 3;
+        for (int side = 0; side < 2; ++side) {
+            const int ik = side == 0 ? s * (K[k] + 1) : -s * K[k];
+            int j = 0;
+            for (int ia = -K[a]; ia <= K[a]; ++ia)
+                for (int ib = -K[b]; ib <= K[b]; ++ib, ++j) {
+                    double* v = &sh[3 * ((size_t)c * n_img + side * Lmax + j)];
+                    v[k] = ik * d[k];
+                    v[a] = ia * d[a];
+                    v[b] = ib * d[b];
+                    w[(size_t)c * n_img + side * Lmax + j] = side == 0 ? 1.f : -1.f;
+                }
+            for (; j < Lmax; ++j) {   // padding: any finite far image, weight 0
+                double* v = &sh[3 * ((size_t)c * n_img + side * Lmax + j)];
+                v[k] = ik * d[k];
+            }
+        }
+    }
+    // class of each check point from its partner
+    std::vector<int> cls(M);
+    for (int l = 0; l < M; ++l) {
+        int c = -1;
+        for (int k = 0; k < 3; ++k) {
+            const double dy = pl.Y[3 * (size_t)l + k] - pl.Yt[3 * (size_t)l + k];
+            if (dy != 0.0) c = 2 * k + (dy < 0.0 ? 1 : 0);
+        }
+        if (c < 0) return PSUM_ERR_ARG;     // a partner equal to its point cannot occur on the sphere
+        cls[l] = c;
+    }
+    // class by class, Morton order within a class, each class in whole groups
+    std::vector<int> order(M);
+    std::iota(order.begin(), order.end(), 0);
+    std::vector<uint64_t> key(M);
+    for (int l = 0; l < M; ++l) key[l] = morton_host(&pl.Y[3 * (size_t)l], pl.R0);
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+        return cls[x] != cls[y] ? cls[x] < cls[y] : key[x] < key[y];
+    });
+    std::vector<int> slot, gcls;
+    for (size_t i = 0; i < order.size();) {
+        const int c = cls[order[i]];
+        size_t e = i;
+        while (e < order.size() && cls[order[e]] == c) ++e;
+        for (size_t t = i; t < e; ++t) slot.push_back(order[t]);
+        while (slot.size() % kNearChunk) slot.push_back(-1);
+        while (gcls.size() < slot.size() / kNearChunk) gcls.push_back(c);
+        i = e;
+    }
+    while (slot.size() % kTile32) slot.push_back(-1);
+    while (gcls.size() < slot.size() / kNearChunk) gcls.push_back(0);
+    const int ngroups = (int)gcls.size();
+    std::vector<float4> pk;
+    std::vector<double> org;
+    pack_groups32(pl.Y, slot, ngroups, pk, org);
+    std::vector<int> pos(M);
+    for (size_t i = 0; i < slot.size(); ++i)
+        if (slot[i] >= 0) pos[slot[i]] = (int)i;
+    int s1;
+    if ((s1 = upload((float4**)&pl.d_lc_tgt, pk.data(), pk.size()))) return s1;
+    if ((s1 = upload(&pl.d_lc_org, org.data(), org.size()))) return s1;
+    if ((s1 = upload(&pl.d_lc_pos, pos.data(), pos.size()))) return s1;
+    if ((s1 = upload(&pl.d_lc_cls, gcls.data(), gcls.size()))) return s1;
+    if ((s1 = upload(&pl.d_lc_shifts, sh.data(), sh.size()))) return s1;
+    if ((s1 = upload(&pl.d_lc_w, w.data(), w.size()))) return s1;
+    pl.lc_tiles = ngroups / kTgt32;
+    pl.lc_img = n_img;
+    return PSUM_OK;
+}
+
 int build_plan(const psum_opts& o, Plan& pl) {
     pl.opt = o;
     const int p = o.p, M = o.M;
@@ -313,36 +441,12 @@ int build_plan(const psum_opts& o, Plan& pl) {
         std::vector<uint64_t> key(pl.n_check);
         for (int j = 0; j < pl.n_check; ++j) key[j] = morton_host(&pts[3 * (size_t)j], pl.R0);
         std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return key[a] < key[b]; });
-        // hi parts (2 float4 per point) followed by lo parts (2 float4 per point)
-        const size_t npk = 2 * (size_t)ngroups * kNearChunk;
-        std::vector<float4> pk(2 * npk, make_float4(0.f, 0.f, 0.f, 0.f));
-        for (size_t i = 0; i < npk; ++i) pk[i] = make_float4(1e3f, 1e3f, 1e3f, 1e3f);
-        std::vector<double> org(4 * (size_t)ngroups, 0.0);
-        for (int g = 0; g < ngroups; ++g) {
-            double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
-            const int i0 = g * kNearChunk, i1 = std::min(pl.n_check, (g + 1) * kNearChunk);
-            for (int i = i0; i < i1; ++i)
-                for (int c = 0; c < 3; ++c) {
-                    lo[c] = std::min(lo[c], pts[3 * (size_t)order[i] + c]);
-                    hi[c] = std::max(hi[c], pts[3 * (size_t)order[i] + c]);
-                }
-            for (int c = 0; c < 3; ++c) org[4 * g + c] = lo[c] <= hi[c] ? 0.5 * (lo[c] + hi[c]) : 0.0;
-            double r2max = 0.0;
-            for (int i = i0; i < i1; ++i) {
-                const double* q = &pts[3 * (size_t)order[i]];
-                const double r[3] = {q[0] - org[4 * g], q[1] - org[4 * g + 1], q[2] - org[4 * g + 2]};
-                r2max = std::max(r2max, r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
-                const float f[3] = {(float)r[0], (float)r[1], (float)r[2]};
-                const float l[3] = {(float)(r[0] - (double)f[0]), (float)(r[1] - (double)f[1]),
-                                    (float)(r[2] - (double)f[2])};
-                pk[2 * (size_t)i] = make_float4(f[0], f[0], f[1], f[1]);
-                pk[2 * (size_t)i + 1] = make_float4(f[2], f[2], 0.f, 0.f);
-                pk[npk + 2 * (size_t)i] = make_float4(l[0], l[0], l[1], l[1]);
-                pk[npk + 2 * (size_t)i + 1] = make_float4(l[2], l[2], 0.f, 0.f);
-                pos[order[i]] = i;
-            }
-            org[4 * g + 3] = std::sqrt(r2max);
-        }
+        order.resize((size_t)ngroups * kNearChunk, -1);
+        std::vector<float4> pk;
+        std::vector<double> org;
+        pack_groups32(pts, order, ngroups, pk, org);
+        for (size_t i = 0; i < order.size(); ++i)
+            if (order[i] >= 0) pos[order[i]] = (int)i;
         std::vector<int> inv((size_t)ngroups * kNearChunk, -1);
         for (int j = 0; j < pl.n_check; ++j) inv[pos[j]] = j;
         int s1 = upload((float4**)&pl.d_check_tgt, pk.data(), pk.size());
@@ -365,6 +469,11 @@ int build_plan(const psum_opts& o, Plan& pl) {
     }
     int s2 = upload(&pl.d_check_pos, pos.data(), pos.size());
     if (s2) return s2;
+    pl.lc_tiles = 0;
+    pl.lc_img = 0;
+    if (o.precision != PSUM_FP64 && !(pl.Rb > 0.0) && o.check_form != PSUM_CHECKS_POINTS &&
+        (s2 = build_check_layers(pl, d)))
+        return s2;
     if ((s2 = upload(&pl.d_pinv, pl.pinv.data(), pl.pinv.size()))) return s2;
     if ((s2 = upload(&pl.d_Rbox, pl.Rbox.data(), pl.Rbox.size()))) return s2;
     if ((s2 = upload(&pl.d_shifts, pl.shifts.data(), pl.shifts.size()))) return s2;
@@ -390,6 +499,12 @@ void free_plan_device(Plan& pl) {
     cudaFree(pl.d_check_inv);
     cudaFree(pl.d_check_tgt);
     cudaFree(pl.d_check_org);
+    cudaFree(pl.d_lc_tgt);
+    cudaFree(pl.d_lc_org);
+    cudaFree(pl.d_lc_pos);
+    cudaFree(pl.d_lc_cls);
+    cudaFree(pl.d_lc_shifts);
+    cudaFree(pl.d_lc_w);
     cudaFree(pl.d_pinv);
     cudaFree(pl.d_Rbox);
     cudaFree(pl.d_shifts);

@@ -226,6 +226,19 @@ struct Plan {
     void* d_check_tgt = nullptr;    // packed check targets (float4 rel coords or double4_32a)
     double* d_check_org = nullptr;  // tile origins (FP32C), 3 per tile
 
+    // the right-hand side as two image layers at the M check points (PSUM_CHECKS_LAYERS):
+    // f_l = sum over the layer i_k = s(K_k + 1) minus the layer i_k = -s K_k, where the
+    // partner is y~_l = y_l - s d_k e_k.  Points of one class c = 2k + (s < 0) share their
+    // image list, so they are packed class by class in whole groups of kGroup points.
+    int lc_tiles = 0;               // target tiles (0: the plan evaluates the 2M points)
+    int lc_img = 0;                 // images per class: 2 x the largest layer (zero-weight padding)
+    void* d_lc_tgt = nullptr;       // packed points, hi parts then lo parts (FP32C/FF layout)
+    double* d_lc_org = nullptr;     // 4 per group: origin and radius
+    int* d_lc_pos = nullptr;        // M: packed position of y_l
+    int* d_lc_cls = nullptr;        // class of each group
+    double* d_lc_shifts = nullptr;  // [6][lc_img][3] image vectors of each class's layers
+    float* d_lc_w = nullptr;        // [6][lc_img] weights: +1 (upper layer), -1 (lower), 0 (padding)
+
     double* d_pinv = nullptr;
     double* d_Rbox = nullptr;
     double* d_shtab64 = nullptr;    // recurrence coefficients (sh_visit_tab), double

@@ -37,6 +37,7 @@ def test_strerror_and_defaults_without_gpu():
     assert tuple(o.d) == (1.0, 1.0, 1.0) and o.p == 8 and o.M == 200 and tuple(o.K) == (1, 1, 1)
     assert o.precision == B.PSUM_FP64 and o.mean_mode == B.PSUM_MEAN_ZERO
     assert o.pair_kernel == B.PAIR_KERNELS["auto"] == 0
+    assert o.check_form == B.CHECK_FORMS["auto"] == 0
 
 
 @pytest.mark.parametrize("d,p,M,prec,K", [
@@ -63,6 +64,7 @@ def test_null_arguments_are_rejected():
     assert lib.psum_plan_info(None, None) == B.PSUM_ERR_ARG
     k = ctypes.c_int(-1)
     assert lib.psum_pair_kernel(None, 10, ctypes.byref(k), None) == B.PSUM_ERR_ARG
+    assert lib.psum_check_form(None, ctypes.byref(k)) == B.PSUM_ERR_ARG
     lib.psum_destroy(None)
     h = ctypes.c_void_p()
     assert lib.psum_plan_create(1.0, 1.0, 1.0, 8, 10, ctypes.byref(h)) == B.PSUM_ERR_ARG
@@ -102,5 +104,19 @@ def test_unknown_pair_kernel_is_rejected(pair_kernel):
     o = B.psum_opts_default()
     o.p, o.M = 8, 200
     o.pair_kernel = pair_kernel
+    h = ctypes.c_void_p()
+    assert B.load().psum_plan_create_ex(ctypes.byref(o), ctypes.byref(h)) == B.PSUM_ERR_ARG
+
+
+@pytest.mark.parametrize("check_form,prec,lam", [(-1, "fp32c", 0.0), (3, "fp32c", 0.0),
+                                                 (2, "fp64", 0.0),       # layers: float32 plans only
+                                                 (2, "fp32c", 1.5)])     # and block (untrimmed) near sets
+def test_invalid_check_form_is_rejected(check_form, prec, lam):
+    # checked on the host before any device call
+    o = B.psum_opts_default()
+    o.p, o.M = 8, 200
+    o.precision = B.PRECISIONS[prec]
+    o.lambda_ = lam
+    o.check_form = check_form
     h = ctypes.c_void_p()
     assert B.load().psum_plan_create_ex(ctypes.byref(o), ctypes.byref(h)) == B.PSUM_ERR_ARG

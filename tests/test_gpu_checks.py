@@ -1,0 +1,110 @@
+"""The right-hand side of the fit in its two-layer form (float32 plans): the partner
+y~_l = y_l - s d_k e_k sees the near block shifted by one period along k, so
+phi_near(y~_l) - phi_near(y_l) is the image layer i_k = s(K_k + 1) minus the layer
+i_k = -s K_k, summed at y_l alone (algorithm "get", step 3; Eq. 3).  The GPU path with
+each form against the FP64 oracle, and the two forms against each other.
+
+Tolerances (relative L2 error over all charges): FP32C 1e-6, FF 1e-10.
+"""
+import numpy as np
+import pytest
+
+from oracle import psum_oracle as O
+from paper_1310_4374_gb300 import binding as B
+from paper_1310_4374_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp32c": 1e-6, "ff": 1e-10}
+# the two forms round differently; their coefficients agree to the float32 pair sums'
+# accuracy amplified by the pseudo-inverse (FP32C), or to float64 accuracy (FF)
+C_TOL = {"fp32c": 1e-4, "ff": 1e-9}
+
+
+def _dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+# (name, system, plan keywords): class sizes from a handful of points (one partly filled
+# group per class, empty groups in the last tile) to several groups per class; an
+# anisotropic block whose layers differ in size (zero-weight padding images); the Gauss grid;
+# the RBF basis; no mean condition
+CASES = [
+    ("uniform_pm1_402_M200", lambda: W.uniform_pm1(N=402, p=8, M=200, seed=4), {}),
+    ("gauss_3001_p16_M800", lambda: W.uniform_gauss(N=3001, d=(1.0, 1.5, 2.0), p=16, M=800, seed=5), {}),
+    ("aniso_K121", lambda: W.uniform_gauss(N=1500, d=(1.0, 1.0, 2.0), p=10, M=300, seed=6), {"K": (1, 2, 1)}),
+    ("gauss_grid_p12", lambda: W.uniform_gauss(N=2000, d=(1.0, 1.5, 2.0), p=12, M=325, seed=7),
+     {"points": "gauss"}),
+    ("small_M40", lambda: W.uniform_gauss(N=130, d=(1.0, 1.0, 1.0), p=4, M=40, seed=8), {}),
+    ("mean_none", lambda: W.uniform_gauss(N=900, d=(2.0, 1.0, 1.5), p=8, M=200, seed=9), {"mean": "none"}),
+    ("rbf_64", lambda: W.uniform_gauss(N=700, d=(1.0, 1.0, 1.0), p=8, M=200, seed=10),
+     {"basis": "rbf", "n_rbf": 64}),
+]
+
+
+def _oracle(s, kw):
+    pl = O.Plan(s.d, s.p, s.M, K=kw.get("K", (1, 1, 1)),
+                checkpoints="gauss" if kw.get("points") == "gauss" else None,
+                basis=kw.get("basis", "spherical"), n_rbf=kw.get("n_rbf", 256))
+    return pl.evaluate(s.x, s.q, mean=kw.get("mean", "zero"))
+
+
+def _gpu(s, precision, checks, kw):
+    M = 0 if kw.get("points") == "gauss" else s.M
+    pc = B.PeriodicCoulomb(s.d, s.p, M, precision=precision, checks=checks, **kw)
+    try:
+        form = B.psum_check_form(pc.plan)
+        phi, g = pc(_dev(s.x), _dev(s.q))
+        return phi.cpu().numpy(), g.cpu().numpy(), np.asarray(pc.coefficients()), form
+    finally:
+        pc.close()
+
+
+@pytest.mark.parametrize("precision", ["fp32c", "ff"])
+@pytest.mark.parametrize("name,make,kw", CASES, ids=[c[0] for c in CASES])
+def test_layers_against_oracle_and_points(name, make, kw, precision):
+    s = make()
+    ref = _oracle(s, kw)
+    phi_l, g_l, C_l, form_l = _gpu(s, precision, "layers", kw)
+    phi_p, g_p, C_p, form_p = _gpu(s, precision, "points", kw)
+    assert (form_l, form_p) == ("layers", "points")
+    tol = TOL[precision]
+    for phi, g, what in ((phi_l, g_l, "layers"), (phi_p, g_p, "points")):
+        e_phi = O.relative_l2(phi, ref["phi"])
+        e_g = O.relative_l2(g, ref["grad"])
+        assert e_phi < tol and e_g < tol, f"{what}: eps2 phi {e_phi:.3e}, grad {e_g:.3e}"
+    e_C = np.linalg.norm(C_l - C_p) / np.linalg.norm(C_p)
+    assert e_C < C_TOL[precision], f"coefficients of the two forms differ by {e_C:.3e}"
+
+
+def test_automatic_check_form():
+    s = W.uniform_gauss(N=300, d=(1.0, 1.5, 2.0), p=8, M=200, seed=1)
+    expect = [({"precision": "fp32c"}, "layers"), ({"precision": "ff"}, "layers"),
+              ({"precision": "fp64"}, "points"), ({"precision": "fp32c", "checks": "points"}, "points"),
+              ({"precision": "fp32c", "lam": 1.5}, "points")]
+    for kw, form in expect:
+        pc = B.PeriodicCoulomb(s.d, s.p, s.M, **kw)
+        try:
+            assert B.psum_check_form(pc.plan) == form, kw
+        finally:
+            pc.close()
+
+
+def test_layers_deterministic_and_graph_replay():
+    # fixed work items and reduction order: repeated evaluations and a graph replay of the
+    # layered plan give identical bits
+    s = W.uniform_gauss(N=2500, d=(1.0, 1.5, 2.0), p=12, M=400, seed=11)
+    pc = B.PeriodicCoulomb(s.d, s.p, s.M, precision="fp32c")
+    try:
+        x, q = _dev(s.x), _dev(s.q)
+        a = pc(x, q)[0].cpu().numpy()
+        b = pc(x, q)[0].cpu().numpy()
+        phi = torch.empty(len(s.q), dtype=torch.float64, device="cuda")
+        g = torch.empty((len(s.q), 3), dtype=torch.float64, device="cuda")
+        B.psum_eval_graph(pc.plan, x, q, phi, g)
+        B.psum_eval_graph(pc.plan, x, q, phi, g)
+        c = phi.cpu().numpy()
+        assert np.array_equal(a, b) and np.array_equal(a, c)
+    finally:
+        pc.close()

@@ -430,3 +430,40 @@ def test_brute_force_over_expanding_cubes_of_cells():
     assert err_g < 1e-6 and err_dphi < 3e-6
     # and the extrapolation is what closes the gap: the raw L = 24 sum is far coarser
     assert np.abs(g2 - ref["grad"]).max() / gs > 5 * err_g
+
+
+@pytest.mark.parametrize("d,K", [((1.0, 1.0, 1.0), (1, 1, 1)), ((1.0, 1.5, 2.0), (1, 1, 1)),
+                                 ((1.0, 1.0, 2.0), (1, 2, 1)), ((2.0, 1.0, 1.0), (2, 1, 1))])
+def test_partner_difference_is_two_image_layers(d, K):
+    # The right-hand side of the fit, phi_near(y~) - phi_near(y) with y~ = y - s d_k e_k
+    # (algorithm "get", step 3; Eq. 3 at both points), equals the sum over the image layer
+    # i_k = s (K_k + 1) minus the sum over the layer i_k = -s K_k: the partner's block is
+    # the block shifted by one period along k.  The float32 plans evaluate it in this
+    # form; here both sides are plain float64 direct sums.
+    rng = np.random.default_rng(17)
+    d = np.asarray(d)
+    N = 25
+    x = rng.uniform(-0.5, 0.5, (N, 3)) * d
+    q = rng.normal(size=N)
+    q -= q.mean()
+    R0 = O.circumradius(d)
+    Y = O.fibonacci_checkpoints(60, R0)
+    Yt = O.periodic_partners(Y, d)
+    f_points = O.near_sum(Yt, x, q, d, K, grad=False) - O.near_sum(Y, x, q, d, K, grad=False)
+    f_layers = np.zeros(len(Y))
+    seen = set()
+    for l in range(len(Y)):
+        k = int(np.flatnonzero(Y[l] != Yt[l])[0])
+        s = 1 if Y[l, k] > Yt[l, k] else -1
+        seen.add((k, s))
+        a, b = (k + 1) % 3, (k + 2) % 3
+        for side, ik in ((1.0, s * (K[k] + 1)), (-1.0, -s * K[k])):
+            for ia in range(-K[a], K[a] + 1):
+                for ib in range(-K[b], K[b] + 1):
+                    p = np.zeros(3)
+                    p[k], p[a], p[b] = ik * d[k], ia * d[a], ib * d[b]
+                    f_layers[l] += side * O.near_sum(Y[l:l + 1], x + p, q, d, (0, 0, 0), grad=False)[0]
+    assert len(seen) >= 4                       # the points cover several faces and both signs
+    assert np.abs(f_layers - f_points).max() < 1e-12 * np.abs(f_points).max()
+    # a dropped layer or a wrong sign is far outside that bound
+    assert np.abs(f_points).max() > 1e-3
