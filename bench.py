@@ -436,8 +436,9 @@ def batch_leg(args):
 
     systems = W.config(4)
     t0 = time.perf_counter()
-    pb = B.PeriodicBatch(systems, precision="fp32c")
+    pb = B.PeriodicBatch(systems, precision="fp32c", checks=args.checks)
     t_plans = time.perf_counter() - t0
+    check_forms = sorted({B.psum_check_form(p) for p in pb.plans})
     try:
         x = torch.as_tensor(np.concatenate([s.x for s in systems]), dtype=torch.float64, device="cuda")
         q = torch.as_tensor(np.concatenate([s.q for s in systems]), dtype=torch.float64, device="cuda")
@@ -466,7 +467,7 @@ def batch_leg(args):
                         f"{wide} flat boxes with a widened near block (K = (2,1,1))",
             "pairs_per_s": info["pairs"] / (ms * 1e-3), "systems_per_s": len(systems) / (ms * 1e-3),
             "ms_per_step": ms, "pairs_per_step": info["pairs"], "ctas": info["ctas"],
-            "autotuned_variant": info["variant"], "plan_setup_s": t_plans}
+            "autotuned_variant": info["variant"], "plan_setup_s": t_plans, "check_form": "/".join(check_forms)}
 
 
 def backward_leg(args):

@@ -296,6 +296,8 @@ typedef struct psum_batch_info {
  * persistent launch (fixed work items, taken dynamically) for all charge pair sums and one for all check-point pair
  * sums.  plans[b] fixes system b's box, degree, check points and near block; all plans
  * must share the precision and the current device (a plan may appear several times).
+ * Each system's check sums take its plan's form (psum_check_form): float32 plans in the
+ * two-layer form evaluate it in the batch too.
  * offsets (host, B+1 entries, offsets[0] = 0, increasing) delimit system b's charges in
  * the concatenated arrays: rows offsets[b] .. offsets[b+1]-1.  1 <= B <= 256.  All
  * device memory of the batch is allocated here.  The plans must outlive the batch. */

@@ -381,9 +381,12 @@ def psum_batch_destroy(batch):
 class PeriodicBatch:
     """Many independent systems (each with its own plan) evaluated together."""
 
-    def __init__(self, systems, precision="fp32c", mean="zero", pairs="auto"):
-        self.plans = [psum_plan_create_ex(s.d, s.p, s.M, precision, mean, getattr(s, "K", (1, 1, 1)), pairs=pairs)
-                      for s in systems]
+    def __init__(self, systems, precision="fp32c", mean="zero", pairs="auto", checks="auto"):
+        """checks: one check-sum form for every plan, or a list with one per system."""
+        forms = checks if isinstance(checks, (list, tuple)) else [checks] * len(systems)
+        self.plans = [psum_plan_create_ex(s.d, s.p, s.M, precision, mean, getattr(s, "K", (1, 1, 1)), pairs=pairs,
+                                          checks=c)
+                      for s, c in zip(systems, forms)]
         self.P = [psum_plan_info(p)["P"] for p in self.plans]
         self.offsets = [0]
         for s in systems:

@@ -31,10 +31,11 @@ struct BatchDev {
     int64_t C0;               // first coefficient
     const double* pinv;       // (P-1) x M
     const double* Rbox;       // P
-    const int* check_pos;     // 2M positions relative to chk_pt0
+    const int* check_pos;     // 2M positions relative to chk_pt0, or M with `layers`
     const double* tab64;      // recurrence coefficients of the system's degree
     const float* tab32;
     int p, P, M, zero_mean;
+    int layers;               // the check sums are the two-layer differences at the M points
     int seg0, nseg;
     double d[3], H[3];
     double inv_V0, inv_R0;
@@ -124,14 +125,15 @@ __global__ void __launch_bounds__(kSeg) k_bmorton(const double* __restrict__ x, 
     vals[i] = (uint32_t)i;
 }
 
-// step 4: f_l = phi_near(y~_l) - phi_near(y_l), for every system (grid.y = system)
+// step 4: f_l = phi_near(y~_l) - phi_near(y_l), for every system (grid.y = system); a
+// system with two-layer check sums has the difference at y_l's position already
 __global__ void k_brhs(const BatchDev* __restrict__ sys, const double* __restrict__ phi_check,
                        double* __restrict__ f) {
     const BatchDev& S = sys[blockIdx.y];
     const int l = blockIdx.x * blockDim.x + threadIdx.x;
     if (l >= S.M) return;
     const double* pc = phi_check + S.chk_pt0;
-    f[S.f0 + l] = pc[S.check_pos[S.M + l]] - pc[S.check_pos[l]];
+    f[S.f0 + l] = S.layers ? pc[S.check_pos[l]] : pc[S.check_pos[S.M + l]] - pc[S.check_pos[l]];
 }
 
 // step 5: C_{2..P} = A^+ f, one warp per row (grid.y = system)
@@ -279,6 +281,13 @@ struct psum_batch_s {
     double* d_shifts = nullptr;
     float4 *d_chk_hi = nullptr, *d_chk_lo = nullptr;
     double* d_chk_org = nullptr;
+    // float32 batches: the check sums' image tables, per system either its block images
+    // (weight 1, every group class 0) or its plan's two-layer tables (6 classes), and the
+    // class of each packed check group
+    int* d_chk_cls = nullptr;
+    double* d_cshifts = nullptr;
+    float* d_cw = nullptr;
+    size_t n_centries = 0;
     double4_32a* d_chk64 = nullptr;
     uint32_t *ka = nullptr, *va = nullptr, *kb = nullptr, *vb = nullptr, *hist = nullptr;
     float4 *pk_hi = nullptr, *pk_lo = nullptr;
@@ -354,6 +363,9 @@ size_t batch_layout(psum_batch_s* bt, char* base) {
     for (const psum_plan_t p : bt->plans) n_shift += 3 * (size_t)p->pl.n_images;
     bt->d_shifts = b.take<double>(n_shift);
     if (fp32) {
+        bt->d_chk_cls = b.take<int>((size_t)(bt->n_chk_pts / kNearChunk));
+        bt->d_cshifts = b.take<double>(3 * bt->n_centries);
+        bt->d_cw = b.take<float>(bt->n_centries);
         bt->d_chk_hi = b.take<float4>(2 * (size_t)bt->n_chk_pts);
         bt->d_chk_lo = b.take<float4>(2 * (size_t)bt->n_chk_pts);
         bt->d_chk_org = b.take<double>(4 * (size_t)(bt->n_chk_pts / kNearChunk));
@@ -425,7 +437,7 @@ int queue_batch(psum_batch_s* bt, const double* x, const double* q, double* phi,
             BTRY(launch_near32(true, bt->pk_hi, bt->pk_lo, bt->org, bt->pk_hi, bt->pk_lo, bt->org, bt->d_shifts,
                                bt->part_n, bt->Ln[variant], st, variant, nullptr, 0.0, ff));
         BTRY(launch_near32(false, bt->pk_hi, bt->pk_lo, bt->org, bt->d_chk_hi, bt->d_chk_lo, bt->d_chk_org,
-                           bt->d_shifts, bt->part_c, bt->Lc, st, 0, nullptr, 0.0, ff));
+                           bt->d_cshifts, bt->part_c, bt->Lc, st, 0, nullptr, 0.0, ff, bt->d_chk_cls, bt->d_cw));
     } else {
         BTRY(launch_pack64_groups(x, q, bt->n_pts, bt->d_grp_start, bt->d_grp_count, bt->pk64, st));
         nl += 1;
@@ -587,6 +599,8 @@ int psum_batch_create(const psum_plan_t* plans, int B, const int64_t* offsets, p
     std::vector<int> grp_count;
     int64_t pt = 0, chk_pt = 0, f0 = 0, C0 = 0, unit_n = 0, unit_c = 0, tile_n = 0, tile_c = 0;
     int shift0 = 0;
+    int64_t cent0 = 0;                      // first entry of the system's check image table
+    std::vector<int64_t> cent_first(B);
     bt->sys.resize(B);
     bt->near_n.resize(B);
     bt->near_c.resize(B);
@@ -605,7 +619,10 @@ int psum_batch_create(const psum_plan_t* plans, int B, const int64_t* offsets, p
         S.C0 = C0;
         S.pinv = pl.d_pinv;
         S.Rbox = pl.d_Rbox;
-        S.check_pos = pl.d_check_pos;
+        // float32 plans with two-layer tables keep that form in the batch
+        const bool layers = fp32 && pl.lc_tiles > 0;
+        S.layers = layers ? 1 : 0;
+        S.check_pos = layers ? pl.d_lc_pos : pl.d_check_pos;
         S.tab64 = pl.d_shtab64;
         S.tab32 = pl.d_shtab32;
         S.p = pl.opt.p;
@@ -628,11 +645,15 @@ int psum_batch_create(const psum_plan_t* plans, int B, const int64_t* offsets, p
             grp_start.push_back(S.n0 + g * kNearChunk);
             grp_count.push_back((int)std::max<int64_t>(0, std::min<int64_t>(kNearChunk, n - g * kNearChunk)));
         }
-        const int64_t chk_tiles = pl.n_check_tiles;
+        const int64_t chk_tiles = layers ? pl.lc_tiles : pl.n_check_tiles;
+        const int c_img = layers ? pl.lc_img : pl.n_images;
         bt->near_n[b] = NearSys{unit_n, tile_n, n_tiles, n_chunks, pt / kNearChunk, shift0, pl.n_images,
                                 near_chunk_stride(n_chunks)};
-        bt->near_c[b] = NearSys{unit_c, tile_c, chk_tiles, n_chunks, pt / kNearChunk, shift0, pl.n_images,
-                                near_chunk_stride(n_chunks)};
+        // float32: the check sums index their own image tables (cent0); float64: the block's
+        bt->near_c[b] = NearSys{unit_c, tile_c, chk_tiles, n_chunks, pt / kNearChunk,
+                                fp32 ? (int)cent0 : shift0, c_img, near_chunk_stride(n_chunks)};
+        cent_first[b] = cent0;
+        cent0 += layers ? 6 * (int64_t)c_img : c_img;
         SymSys ss{};
         ss.tile0 = tile_n;
         ss.n_tiles = n_tiles;
@@ -654,6 +675,7 @@ int psum_batch_create(const psum_plan_t* plans, int B, const int64_t* offsets, p
     }
     bt->n_pts = pt;
     bt->n_chk_pts = chk_pt;
+    bt->n_centries = fp32 ? (size_t)cent0 : 0;
     bt->n_groups = pt / kNearChunk;
     bt->n_seg = (int)seg_sys.size();
     bt->units = unit_n;
@@ -713,18 +735,41 @@ int psum_batch_create(const psum_plan_t* plans, int B, const int64_t* offsets, p
         st = cuda_st(cudaMemcpy(bt->d_shifts + so, pl.d_shifts, sizeof(double) * 3 * pl.n_images,
                                 cudaMemcpyDeviceToDevice));
         so += 3 * (size_t)pl.n_images;
-        const size_t npts = (size_t)pl.n_check_tiles * tile;
         const BatchDev& S = bt->sys[b];
+        const size_t npts = (size_t)(S.layers ? pl.lc_tiles : pl.n_check_tiles) * tile;
         if (st == PSUM_OK && fp32) {
-            const float4* src = (const float4*)pl.d_check_tgt;
+            const float4* src = (const float4*)(S.layers ? pl.d_lc_tgt : pl.d_check_tgt);
+            const double* corg = S.layers ? pl.d_lc_org : pl.d_check_org;
+            const size_t ngrp = npts / kNearChunk;
             st = cuda_st(cudaMemcpy(bt->d_chk_hi + 2 * S.chk_pt0, src, sizeof(float4) * 2 * npts,
                                     cudaMemcpyDeviceToDevice));
             if (st == PSUM_OK)
                 st = cuda_st(cudaMemcpy(bt->d_chk_lo + 2 * S.chk_pt0, src + 2 * npts, sizeof(float4) * 2 * npts,
                                         cudaMemcpyDeviceToDevice));
             if (st == PSUM_OK)
-                st = cuda_st(cudaMemcpy(bt->d_chk_org + 4 * (S.chk_pt0 / kNearChunk), pl.d_check_org,
-                                        sizeof(double) * 4 * (npts / kNearChunk), cudaMemcpyDeviceToDevice));
+                st = cuda_st(cudaMemcpy(bt->d_chk_org + 4 * (S.chk_pt0 / kNearChunk), corg,
+                                        sizeof(double) * 4 * ngrp, cudaMemcpyDeviceToDevice));
+            // the system's check image table and group classes
+            const size_t ce = (size_t)cent_first[b];
+            if (st == PSUM_OK && S.layers) {
+                const size_t n_e = 6 * (size_t)pl.lc_img;
+                st = cuda_st(cudaMemcpy(bt->d_cshifts + 3 * ce, pl.d_lc_shifts, sizeof(double) * 3 * n_e,
+                                        cudaMemcpyDeviceToDevice));
+                if (st == PSUM_OK)
+                    st = cuda_st(cudaMemcpy(bt->d_cw + ce, pl.d_lc_w, sizeof(float) * n_e, cudaMemcpyDeviceToDevice));
+                if (st == PSUM_OK)
+                    st = cuda_st(cudaMemcpy(bt->d_chk_cls + S.chk_pt0 / kNearChunk, pl.d_lc_cls, sizeof(int) * ngrp,
+                                            cudaMemcpyDeviceToDevice));
+            } else if (st == PSUM_OK) {
+                const std::vector<float> ones((size_t)pl.n_images, 1.f);
+                st = cuda_st(cudaMemcpy(bt->d_cshifts + 3 * ce, pl.d_shifts, sizeof(double) * 3 * pl.n_images,
+                                        cudaMemcpyDeviceToDevice));
+                if (st == PSUM_OK)
+                    st = cuda_st(cudaMemcpy(bt->d_cw + ce, ones.data(), sizeof(float) * ones.size(),
+                                            cudaMemcpyHostToDevice));
+                if (st == PSUM_OK)
+                    st = cuda_st(cudaMemset(bt->d_chk_cls + S.chk_pt0 / kNearChunk, 0, sizeof(int) * ngrp));
+            }
         } else if (st == PSUM_OK) {
             st = cuda_st(cudaMemcpy(bt->d_chk64 + S.chk_pt0, pl.d_check_tgt, sizeof(double4_32a) * npts,
                                     cudaMemcpyDeviceToDevice));

@@ -108,3 +108,33 @@ def test_layers_deterministic_and_graph_replay():
         assert np.array_equal(a, b) and np.array_equal(a, c)
     finally:
         pc.close()
+
+
+@pytest.mark.parametrize("precision", ["fp32c", "ff"])
+def test_batch_with_mixed_check_forms(precision):
+    # systems whose plans take the two-layer form and systems whose plans take the point
+    # form in one batch: each against the oracle and against its single evaluation
+    systems = W.config(4, small=True)
+    forms = ["layers" if b % 2 == 0 else "points" for b in range(len(systems))]
+    pb = B.PeriodicBatch(systems, precision=precision, checks=forms)
+    try:
+        assert [B.psum_check_form(p) for p in pb.plans] == forms
+        x = torch.as_tensor(np.concatenate([s.x for s in systems]), dtype=torch.float64, device="cuda")
+        q = torch.as_tensor(np.concatenate([s.q for s in systems]), dtype=torch.float64, device="cuda")
+        phi, g = pb(x, q)
+        phi, g = phi.cpu().numpy(), g.cpu().numpy()
+        for b, (s, form) in enumerate(zip(systems, forms)):
+            sl = slice(pb.offsets[b], pb.offsets[b + 1])
+            ref = O.periodic_sum(s.x, s.q, s.d, s.p, s.M, K=s.K)
+            e_phi, e_g = O.relative_l2(phi[sl], ref["phi"]), O.relative_l2(g[sl], ref["grad"])
+            assert e_phi < TOL[precision] and e_g < TOL[precision], (b, form, e_phi, e_g)
+            pc = B.PeriodicCoulomb(s.d, s.p, s.M, precision=precision, K=s.K, checks=form)
+            try:
+                p1, g1 = pc(_dev(s.x), _dev(s.q))
+            finally:
+                pc.close()
+            single_tol = 1e-7 if precision == "fp32c" else 1e-12
+            assert O.relative_l2(phi[sl], p1.cpu().numpy()) < single_tol, (b, form)
+            assert O.relative_l2(g[sl], g1.cpu().numpy()) < single_tol, (b, form)
+    finally:
+        pb.close()
