@@ -98,10 +98,11 @@ extern "C" {
  * (the other two image indices over their block ranges): 2 (2K_a+1)(2K_b+1) images at M
  * points instead of (2K_1+1)(2K_2+1)(2K_3+1) images at 2M points (18 x M against 27 x 2M for
  * the 3x3x3 block). */
-#define PSUM_CHECKS_AUTO    0  /* layers where they apply (FP32C and FF plans without ball trimming,
-                                  single systems), points otherwise */
+#define PSUM_CHECKS_AUTO    0  /* layers where they apply (plans without ball trimming, every
+                                  precision, single systems and batches), points otherwise */
 #define PSUM_CHECKS_POINTS  1  /* phi_near at y_l and at y~_l, differenced in float64 */
-#define PSUM_CHECKS_LAYERS  2  /* the two-layer form; PSUM_ERR_ARG for FP64 and ball-trimmed plans */
+#define PSUM_CHECKS_LAYERS  2  /* the two-layer form; PSUM_ERR_ARG for ball-trimmed plans (the ball
+                                  is not a block of images) */
 
 #define PSUM_MEAN_ZERO 0  /* C_1 makes the box mean of phi zero (Eq. pfx3, phi_mean = 0) */
 #define PSUM_MEAN_NONE 1  /* C_1 = 0 (potential defined up to a constant, Sec. 3) */
@@ -296,8 +297,7 @@ typedef struct psum_batch_info {
  * persistent launch (fixed work items, taken dynamically) for all charge pair sums and one for all check-point pair
  * sums.  plans[b] fixes system b's box, degree, check points and near block; all plans
  * must share the precision and the current device (a plan may appear several times).
- * Each system's check sums take its plan's form (psum_check_form): float32 plans in the
- * two-layer form evaluate it in the batch too.
+ * Each system's check sums take its plan's form (psum_check_form).
  * offsets (host, B+1 entries, offsets[0] = 0, increasing) delimit system b's charges in
  * the concatenated arrays: rows offsets[b] .. offsets[b+1]-1.  1 <= B <= 256.  All
  * device memory of the batch is allocated here.  The plans must outlive the batch. */

@@ -161,7 +161,10 @@ size_t layout(Plan& pl, int64_t N, char* base, Layout& L, bool backward = false,
         int64_t gmax = (int64_t)pl.num_sms * near64_occupancy_ctas();
         if (g_cap > 0 && gmax > g_cap) gmax = g_cap;
         L.Ln = near_partition(L.n_tiles, L.n_chunks, n_img, gmax, ipc);
-        L.Lc = near_partition(pl.n_check_tiles, L.n_chunks, n_img, gmax, g_cap > 0 ? 1 : kCheckItemsPerCta);
+        const bool layers = pl.lc_tiles > 0;
+        const int64_t c_tiles = layers ? pl.lc_tiles : pl.n_check_tiles;
+        L.Lc = near_partition(c_tiles, L.n_chunks, layers ? pl.lc_img : n_img, gmax,
+                              g_cap > 0 ? 1 : kCheckItemsPerCta);
         // the symmetric float64 kernel: charges, block image set, a normal (growing) scratch
         L.sym = false;
         const int pk = pl.opt.pair_kernel;
@@ -183,8 +186,8 @@ size_t layout(Plan& pl, int64_t N, char* base, Layout& L, bool backward = false,
         L.pk64 = b.take<double4_32a>((size_t)L.n_src_pts);
         if (sep) L.tpk64 = b.take<double4_32a>((size_t)L.n_pts);
         L.part_n = b.take<double>(L.sym ? L.S.doubles : (size_t)L.n_tiles * L.Ln.max_contrib * 4 * kTile64);
-        L.part_c = b.take<double>((size_t)pl.n_check_tiles * L.Lc.max_contrib * kTile64);
-        L.phi_c = b.take<double>((size_t)pl.n_check_tiles * kTile64);
+        L.part_c = b.take<double>((size_t)c_tiles * L.Lc.max_contrib * kTile64);
+        L.phi_c = b.take<double>((size_t)c_tiles * kTile64);
     }
     L.phi_n = b.take<double>((size_t)L.n_pts);
     L.grad_n = b.take<double>(3 * (size_t)L.n_pts);
@@ -331,8 +334,11 @@ int queue_forward(psum_plan_s* h, int64_t N, const double* x, const double* q, d
         TRY(launch_near64(true, L.pk64, t64, pl.d_shifts, L.part_n, L.Ln, st, pl.Rb));
     }
     if (h->profile) TRY(cudaEventRecord(h->ev[2], st));
-    const bool layers = fp32 && pl.lc_tiles > 0;
-    if (layers) {
+    const bool layers = pl.lc_tiles > 0;
+    if (layers && !fp32) {
+        TRY(launch_near64(false, L.pk64, (const double4_32a*)pl.d_lc_tgt, pl.d_lc_shifts, L.part_c, L.Lc, st, 0.0,
+                          pl.d_lc_cls, pl.d_lc_w));
+    } else if (layers) {
         const float4* ct = (const float4*)pl.d_lc_tgt;
         const size_t half = 2 * (size_t)pl.lc_tiles * kTile32;         // hi parts, then lo parts
         TRY(launch_near32(false, L.pk32, L.pk32lo, L.org, ct, ct + half, pl.d_lc_org, pl.d_lc_shifts, L.part_c,
@@ -352,7 +358,7 @@ int queue_forward(psum_plan_s* h, int64_t N, const double* x, const double* q, d
         TRY(launch_sym_reduce(L.part_n, N, L.S, L.phi_n, L.grad_n, st, !fp32));
     else
         TRY(launch_near_reduce(L.part_n, sep ? T : N, tile, 4, L.Ln, L.phi_n, L.grad_n, st));
-    TRY(launch_near_reduce(L.part_c, layers ? (int64_t)pl.lc_tiles * kTile32 : pl.n_check, tile, 1, L.Lc, L.phi_c,
+    TRY(launch_near_reduce(L.part_c, layers ? (int64_t)pl.lc_tiles * tile : pl.n_check, tile, 1, L.Lc, L.phi_c,
                            nullptr, st));
     h->launches += 4;   // two near-field kernels, two reductions
     const bool zero_mean = o.mean_mode == PSUM_MEAN_ZERO;
@@ -493,7 +499,7 @@ bool valid_opts(const psum_opts* o) {
     if (o->check_form != PSUM_CHECKS_AUTO && o->check_form != PSUM_CHECKS_POINTS &&
         o->check_form != PSUM_CHECKS_LAYERS)
         return false;
-    if (o->check_form == PSUM_CHECKS_LAYERS && (o->precision == PSUM_FP64 || o->lambda > 0.0)) return false;
+    if (o->check_form == PSUM_CHECKS_LAYERS && o->lambda > 0.0) return false;
     if (o->mean_mode != PSUM_MEAN_ZERO && o->mean_mode != PSUM_MEAN_NONE) return false;
     return true;
 }

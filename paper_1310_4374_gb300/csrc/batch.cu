@@ -281,9 +281,9 @@ struct psum_batch_s {
     double* d_shifts = nullptr;
     float4 *d_chk_hi = nullptr, *d_chk_lo = nullptr;
     double* d_chk_org = nullptr;
-    // float32 batches: the check sums' image tables, per system either its block images
-    // (weight 1, every group class 0) or its plan's two-layer tables (6 classes), and the
-    // class of each packed check group
+    // the check sums' image tables, per system either its block images (weight 1, every
+    // group class 0) or its plan's two-layer tables (6 classes), and the class of each packed
+    // check group (a float64 tile is one group)
     int* d_chk_cls = nullptr;
     double* d_cshifts = nullptr;
     float* d_cw = nullptr;
@@ -362,10 +362,10 @@ size_t batch_layout(psum_batch_s* bt, char* base) {
     size_t n_shift = 0;
     for (const psum_plan_t p : bt->plans) n_shift += 3 * (size_t)p->pl.n_images;
     bt->d_shifts = b.take<double>(n_shift);
+    bt->d_chk_cls = b.take<int>((size_t)(bt->n_chk_pts / kNearChunk));
+    bt->d_cshifts = b.take<double>(3 * bt->n_centries);
+    bt->d_cw = b.take<float>(bt->n_centries);
     if (fp32) {
-        bt->d_chk_cls = b.take<int>((size_t)(bt->n_chk_pts / kNearChunk));
-        bt->d_cshifts = b.take<double>(3 * bt->n_centries);
-        bt->d_cw = b.take<float>(bt->n_centries);
         bt->d_chk_hi = b.take<float4>(2 * (size_t)bt->n_chk_pts);
         bt->d_chk_lo = b.take<float4>(2 * (size_t)bt->n_chk_pts);
         bt->d_chk_org = b.take<double>(4 * (size_t)(bt->n_chk_pts / kNearChunk));
@@ -442,7 +442,8 @@ int queue_batch(psum_batch_s* bt, const double* x, const double* q, double* phi,
         BTRY(launch_pack64_groups(x, q, bt->n_pts, bt->d_grp_start, bt->d_grp_count, bt->pk64, st));
         nl += 1;
         BTRY(launch_near64(true, bt->pk64, bt->pk64, bt->d_shifts, bt->part_n, bt->Ln[0], st));
-        BTRY(launch_near64(false, bt->pk64, bt->d_chk64, bt->d_shifts, bt->part_c, bt->Lc, st));
+        BTRY(launch_near64(false, bt->pk64, bt->d_chk64, bt->d_cshifts, bt->part_c, bt->Lc, st, 0.0, bt->d_chk_cls,
+                           bt->d_cw));
     }
     const int tile = fp32 ? kTile32 : kTile64;
     if (variant == kVariantSym)
@@ -619,8 +620,8 @@ int psum_batch_create(const psum_plan_t* plans, int B, const int64_t* offsets, p
         S.C0 = C0;
         S.pinv = pl.d_pinv;
         S.Rbox = pl.d_Rbox;
-        // float32 plans with two-layer tables keep that form in the batch
-        const bool layers = fp32 && pl.lc_tiles > 0;
+        // plans with two-layer tables keep that form in the batch
+        const bool layers = pl.lc_tiles > 0;
         S.layers = layers ? 1 : 0;
         S.check_pos = layers ? pl.d_lc_pos : pl.d_check_pos;
         S.tab64 = pl.d_shtab64;
@@ -649,9 +650,9 @@ int psum_batch_create(const psum_plan_t* plans, int B, const int64_t* offsets, p
         const int c_img = layers ? pl.lc_img : pl.n_images;
         bt->near_n[b] = NearSys{unit_n, tile_n, n_tiles, n_chunks, pt / kNearChunk, shift0, pl.n_images,
                                 near_chunk_stride(n_chunks)};
-        // float32: the check sums index their own image tables (cent0); float64: the block's
-        bt->near_c[b] = NearSys{unit_c, tile_c, chk_tiles, n_chunks, pt / kNearChunk,
-                                fp32 ? (int)cent0 : shift0, c_img, near_chunk_stride(n_chunks)};
+        // the check sums index their own image tables (cent0)
+        bt->near_c[b] = NearSys{unit_c, tile_c, chk_tiles, n_chunks, pt / kNearChunk, (int)cent0, c_img,
+                                near_chunk_stride(n_chunks)};
         cent_first[b] = cent0;
         cent0 += layers ? 6 * (int64_t)c_img : c_img;
         SymSys ss{};
@@ -675,7 +676,7 @@ int psum_batch_create(const psum_plan_t* plans, int B, const int64_t* offsets, p
     }
     bt->n_pts = pt;
     bt->n_chk_pts = chk_pt;
-    bt->n_centries = fp32 ? (size_t)cent0 : 0;
+    bt->n_centries = (size_t)cent0;
     bt->n_groups = pt / kNearChunk;
     bt->n_seg = (int)seg_sys.size();
     bt->units = unit_n;
@@ -737,10 +738,10 @@ int psum_batch_create(const psum_plan_t* plans, int B, const int64_t* offsets, p
         so += 3 * (size_t)pl.n_images;
         const BatchDev& S = bt->sys[b];
         const size_t npts = (size_t)(S.layers ? pl.lc_tiles : pl.n_check_tiles) * tile;
+        const size_t ngrp = npts / kNearChunk;
         if (st == PSUM_OK && fp32) {
             const float4* src = (const float4*)(S.layers ? pl.d_lc_tgt : pl.d_check_tgt);
             const double* corg = S.layers ? pl.d_lc_org : pl.d_check_org;
-            const size_t ngrp = npts / kNearChunk;
             st = cuda_st(cudaMemcpy(bt->d_chk_hi + 2 * S.chk_pt0, src, sizeof(float4) * 2 * npts,
                                     cudaMemcpyDeviceToDevice));
             if (st == PSUM_OK)
@@ -749,30 +750,30 @@ int psum_batch_create(const psum_plan_t* plans, int B, const int64_t* offsets, p
             if (st == PSUM_OK)
                 st = cuda_st(cudaMemcpy(bt->d_chk_org + 4 * (S.chk_pt0 / kNearChunk), corg,
                                         sizeof(double) * 4 * ngrp, cudaMemcpyDeviceToDevice));
-            // the system's check image table and group classes
-            const size_t ce = (size_t)cent_first[b];
-            if (st == PSUM_OK && S.layers) {
-                const size_t n_e = 6 * (size_t)pl.lc_img;
-                st = cuda_st(cudaMemcpy(bt->d_cshifts + 3 * ce, pl.d_lc_shifts, sizeof(double) * 3 * n_e,
-                                        cudaMemcpyDeviceToDevice));
-                if (st == PSUM_OK)
-                    st = cuda_st(cudaMemcpy(bt->d_cw + ce, pl.d_lc_w, sizeof(float) * n_e, cudaMemcpyDeviceToDevice));
-                if (st == PSUM_OK)
-                    st = cuda_st(cudaMemcpy(bt->d_chk_cls + S.chk_pt0 / kNearChunk, pl.d_lc_cls, sizeof(int) * ngrp,
-                                            cudaMemcpyDeviceToDevice));
-            } else if (st == PSUM_OK) {
-                const std::vector<float> ones((size_t)pl.n_images, 1.f);
-                st = cuda_st(cudaMemcpy(bt->d_cshifts + 3 * ce, pl.d_shifts, sizeof(double) * 3 * pl.n_images,
-                                        cudaMemcpyDeviceToDevice));
-                if (st == PSUM_OK)
-                    st = cuda_st(cudaMemcpy(bt->d_cw + ce, ones.data(), sizeof(float) * ones.size(),
-                                            cudaMemcpyHostToDevice));
-                if (st == PSUM_OK)
-                    st = cuda_st(cudaMemset(bt->d_chk_cls + S.chk_pt0 / kNearChunk, 0, sizeof(int) * ngrp));
-            }
         } else if (st == PSUM_OK) {
-            st = cuda_st(cudaMemcpy(bt->d_chk64 + S.chk_pt0, pl.d_check_tgt, sizeof(double4_32a) * npts,
+            st = cuda_st(cudaMemcpy(bt->d_chk64 + S.chk_pt0, S.layers ? pl.d_lc_tgt : pl.d_check_tgt,
+                                    sizeof(double4_32a) * npts, cudaMemcpyDeviceToDevice));
+        }
+        // the system's check image table and group classes
+        const size_t ce = (size_t)cent_first[b];
+        if (st == PSUM_OK && S.layers) {
+            const size_t n_e = 6 * (size_t)pl.lc_img;
+            st = cuda_st(cudaMemcpy(bt->d_cshifts + 3 * ce, pl.d_lc_shifts, sizeof(double) * 3 * n_e,
                                     cudaMemcpyDeviceToDevice));
+            if (st == PSUM_OK)
+                st = cuda_st(cudaMemcpy(bt->d_cw + ce, pl.d_lc_w, sizeof(float) * n_e, cudaMemcpyDeviceToDevice));
+            if (st == PSUM_OK)
+                st = cuda_st(cudaMemcpy(bt->d_chk_cls + S.chk_pt0 / kNearChunk, pl.d_lc_cls, sizeof(int) * ngrp,
+                                        cudaMemcpyDeviceToDevice));
+        } else if (st == PSUM_OK) {
+            const std::vector<float> ones((size_t)pl.n_images, 1.f);
+            st = cuda_st(cudaMemcpy(bt->d_cshifts + 3 * ce, pl.d_shifts, sizeof(double) * 3 * pl.n_images,
+                                    cudaMemcpyDeviceToDevice));
+            if (st == PSUM_OK)
+                st = cuda_st(cudaMemcpy(bt->d_cw + ce, ones.data(), sizeof(float) * ones.size(),
+                                        cudaMemcpyHostToDevice));
+            if (st == PSUM_OK)
+                st = cuda_st(cudaMemset(bt->d_chk_cls + S.chk_pt0 / kNearChunk, 0, sizeof(int) * ngrp));
         }
     }
     if (st == PSUM_OK) st = cuda_st(cudaMallocHost((void**)&bt->h_status, sizeof(int) * B));

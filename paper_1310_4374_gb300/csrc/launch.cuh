@@ -12,7 +12,8 @@ cudaError_t launch_near32(bool grad, const float4* src_hi, const float4* src_lo,
                           const double* src_x = nullptr, double Rb = 0.0, bool ff = false,
                           const int* tgt_cls = nullptr, const float* img_w = nullptr);
 cudaError_t launch_near64(bool grad, const double4_32a* src, const double4_32a* tgt, const double* shifts,
-                          double* partial, const NearPlanLaunch& L, cudaStream_t st, double Rb = 0.0);
+                          double* partial, const NearPlanLaunch& L, cudaStream_t st, double Rb = 0.0,
+                          const int* tgt_cls = nullptr, const float* img_w = nullptr);
 cudaError_t launch_near_reduce(const double* partial, int64_t n_valid, int tile_size, int nq,
                                const NearPlanLaunch& L, double* out_phi, double* out_grad, cudaStream_t st);
 int near32_occupancy_ctas(int n_img, int variant = 0, bool trimmed = false, bool ff = false);

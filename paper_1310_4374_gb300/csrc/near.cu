@@ -407,6 +407,11 @@ struct Near64Args {
     int* counter;                // next work item
     int max_contrib;
     NearSysTable tab;
+    // two-layer check sums (potential only): the class of each target tile, and the image
+    // vector shifts[shift0 + c n_img + j] with weight img_w[shift0 + c n_img + j] of
+    // (class c, image j).  Null: one image list, weight 1.
+    const int* tgt_cls;
+    const float* img_w;
 };
 
 
@@ -467,6 +472,16 @@ __global__ void __launch_bounds__(kThreads64) k_near64(Near64Args a) {
         }
         // y - x_i - p with the shift folded into the target
         const double* sh = a.shifts + 3 * (S.shift0 + img);
+        double w = 1.0;                  // the unit's weight (potential only); exact in the fma
+        if (!kGrad && a.tgt_cls) {
+            const int e = S.shift0 + a.tgt_cls[tile] * S.n_img + img;
+            sh = a.shifts + 3 * e;
+            w = (double)a.img_w[e];
+            if (w == 0.0) {              // a padding image of the tile's class
+                ++u;
+                continue;
+            }
+        }
         const double px = tx - sh[0], py = ty - sh[1], pz = tz - sh[2];
         const double4_32a* src = s_src;
         if (a.Rb > 0.0) {
@@ -483,7 +498,10 @@ __global__ void __launch_bounds__(kThreads64) k_near64(Near64Args a) {
             const double r2 = fma(ez, ez, fma(ey, ey, ex * ex));
             const double ri = rsqrt_f64_k0(r2);           // K(0) = 0
             const double qr = Q.w * ri;
-            acc[0] += qr;
+            if (kGrad)
+                acc[0] += qr;
+            else
+                acc[0] = fma(w, qr, acc[0]);
             if (kGrad) {
                 const double w = qr * ri * ri;
                 acc[1 % NQ] = fma(ex, w, acc[1 % NQ]);
@@ -597,9 +615,12 @@ cudaError_t launch_near32(bool grad, const float4* src_hi, const float4* src_lo,
 }
 
 cudaError_t launch_near64(bool grad, const double4_32a* src, const double4_32a* tgt, const double* shifts,
-                          double* partial, const NearPlanLaunch& L, cudaStream_t st, double Rb) {
+                          double* partial, const NearPlanLaunch& L, cudaStream_t st, double Rb, const int* tgt_cls,
+                          const float* img_w) {
+    if ((tgt_cls != nullptr) != (img_w != nullptr) || (tgt_cls && (grad || Rb > 0.0))) return cudaErrorInvalidValue;
     Near64Args a;
     a.src = src; a.tgt = tgt; a.shifts = shifts; a.partial = partial; a.Rb = Rb;
+    a.tgt_cls = tgt_cls; a.img_w = img_w;
     a.U = L.U; a.W = L.W; a.counter = L.counter; a.max_contrib = L.max_contrib; a.tab = L.tab;
     if (!L.counter) return cudaErrorInvalidValue;
     const cudaError_t e = cudaMemsetAsync(L.counter, 0, sizeof(int), st);

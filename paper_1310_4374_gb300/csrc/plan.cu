@@ -235,15 +235,17 @@ static void pack_groups32(const std::vector<double>& pts, const std::vector<int>
     }
 }
 
-// The two-layer form of the right-hand side (float32 plans without ball trimming).  The
+// The two-layer form of the right-hand side (plans without ball trimming).  The
 // partner of y_l is y~_l = y_l - s d_k e_k, so the near block seen from y~_l is the block
 // seen from y_l shifted by one period along k: phi_near(y~_l) - phi_near(y_l) is the sum
 // over the image layer i_k = s (K_k + 1) minus the sum over the layer i_k = -s K_k (Eq. 3
 // at both points; algorithm "get", step 3).  Class c = 2k + (s < 0) fixes the two layers;
 // images j < Lmax of a class are its upper layer (weight +1), j >= Lmax its lower layer
 // (weight -1), and a class whose layers are smaller than the largest, Lmax, is padded with
-// weight-0 entries.
+// weight-0 entries.  Float32 plans pack the points in groups of kNearChunk (tiles of 4
+// groups), float64 plans in tiles of kTile64 absolute points: either way one class per group.
 static int build_check_layers(Plan& pl, const double d[3]) {
+    const bool fp32 = pl.opt.precision != PSUM_FP64;
     const int M = pl.opt.M;
     const int* K = pl.opt.K;
     int Lsize[3], Lmax = 0;
@@ -303,23 +305,33 @@ static int build_check_layers(Plan& pl, const double d[3]) {
         while (gcls.size() < slot.size() / kNearChunk) gcls.push_back(c);
         i = e;
     }
-    while (slot.size() % kTile32) slot.push_back(-1);
+    static_assert(kTile64 == kNearChunk, "a float64 tile is one class group");
+    while (slot.size() % (fp32 ? kTile32 : kTile64)) slot.push_back(-1);
     while (gcls.size() < slot.size() / kNearChunk) gcls.push_back(0);
     const int ngroups = (int)gcls.size();
-    std::vector<float4> pk;
-    std::vector<double> org;
-    pack_groups32(pl.Y, slot, ngroups, pk, org);
     std::vector<int> pos(M);
     for (size_t i = 0; i < slot.size(); ++i)
         if (slot[i] >= 0) pos[slot[i]] = (int)i;
     int s1;
-    if ((s1 = upload((float4**)&pl.d_lc_tgt, pk.data(), pk.size()))) return s1;
-    if ((s1 = upload(&pl.d_lc_org, org.data(), org.size()))) return s1;
+    if (fp32) {
+        std::vector<float4> pk;
+        std::vector<double> org;
+        pack_groups32(pl.Y, slot, ngroups, pk, org);
+        if ((s1 = upload((float4**)&pl.d_lc_tgt, pk.data(), pk.size()))) return s1;
+        if ((s1 = upload(&pl.d_lc_org, org.data(), org.size()))) return s1;
+    } else {
+        std::vector<double4_32a> pk(slot.size(), make_double4_32a(1e3, 1e3, 1e3, 0.0));
+        for (size_t i = 0; i < slot.size(); ++i)
+            if (slot[i] >= 0)
+                pk[i] = make_double4_32a(pl.Y[3 * (size_t)slot[i]], pl.Y[3 * (size_t)slot[i] + 1],
+                                         pl.Y[3 * (size_t)slot[i] + 2], 0.0);
+        if ((s1 = upload((double4_32a**)&pl.d_lc_tgt, pk.data(), pk.size()))) return s1;
+    }
     if ((s1 = upload(&pl.d_lc_pos, pos.data(), pos.size()))) return s1;
     if ((s1 = upload(&pl.d_lc_cls, gcls.data(), gcls.size()))) return s1;
     if ((s1 = upload(&pl.d_lc_shifts, sh.data(), sh.size()))) return s1;
     if ((s1 = upload(&pl.d_lc_w, w.data(), w.size()))) return s1;
-    pl.lc_tiles = ngroups / kTgt32;
+    pl.lc_tiles = fp32 ? ngroups / kTgt32 : ngroups;
     pl.lc_img = n_img;
     return PSUM_OK;
 }
@@ -471,8 +483,7 @@ int build_plan(const psum_opts& o, Plan& pl) {
     if (s2) return s2;
     pl.lc_tiles = 0;
     pl.lc_img = 0;
-    if (o.precision != PSUM_FP64 && !(pl.Rb > 0.0) && o.check_form != PSUM_CHECKS_POINTS &&
-        (s2 = build_check_layers(pl, d)))
+    if (!(pl.Rb > 0.0) && o.check_form != PSUM_CHECKS_POINTS && (s2 = build_check_layers(pl, d)))
         return s2;
     if ((s2 = upload(&pl.d_pinv, pl.pinv.data(), pl.pinv.size()))) return s2;
     if ((s2 = upload(&pl.d_Rbox, pl.Rbox.data(), pl.Rbox.size()))) return s2;

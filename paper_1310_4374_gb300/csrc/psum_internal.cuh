@@ -232,8 +232,8 @@ struct Plan {
     // image list, so they are packed class by class in whole groups of kGroup points.
     int lc_tiles = 0;               // target tiles (0: the plan evaluates the 2M points)
     int lc_img = 0;                 // images per class: 2 x the largest layer (zero-weight padding)
-    void* d_lc_tgt = nullptr;       // packed points, hi parts then lo parts (FP32C/FF layout)
-    double* d_lc_org = nullptr;     // 4 per group: origin and radius
+    void* d_lc_tgt = nullptr;       // packed points: float32 hi parts then lo parts, or double4_32a
+    double* d_lc_org = nullptr;     // float32 packing: 4 per group, origin and radius
     int* d_lc_pos = nullptr;        // M: packed position of y_l
     int* d_lc_cls = nullptr;        // class of each group
     double* d_lc_shifts = nullptr;  // [6][lc_img][3] image vectors of each class's layers

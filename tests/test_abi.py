@@ -108,9 +108,9 @@ def test_unknown_pair_kernel_is_rejected(pair_kernel):
     assert B.load().psum_plan_create_ex(ctypes.byref(o), ctypes.byref(h)) == B.PSUM_ERR_ARG
 
 
-@pytest.mark.parametrize("check_form,prec,lam", [(-1, "fp32c", 0.0), (3, "fp32c", 0.0),
-                                                 (2, "fp64", 0.0),       # layers: float32 plans only
-                                                 (2, "fp32c", 1.5)])     # and block (untrimmed) near sets
+@pytest.mark.parametrize("check_form,prec,lam", [(-1, "fp32c", 0.0), (3, "fp64", 0.0),
+                                                 (2, "fp32c", 1.5),      # layers: block near sets only,
+                                                 (2, "fp64", 1.7)])      # not the ball
 def test_invalid_check_form_is_rejected(check_form, prec, lam):
     # checked on the host before any device call
     o = B.psum_opts_default()

@@ -1,10 +1,10 @@
-"""The right-hand side of the fit in its two-layer form (float32 plans): the partner
+"""The right-hand side of the fit in its two-layer form: the partner
 y~_l = y_l - s d_k e_k sees the near block shifted by one period along k, so
 phi_near(y~_l) - phi_near(y_l) is the image layer i_k = s(K_k + 1) minus the layer
 i_k = -s K_k, summed at y_l alone (algorithm "get", step 3; Eq. 3).  The GPU path with
 each form against the FP64 oracle, and the two forms against each other.
 
-Tolerances (relative L2 error over all charges): FP32C 1e-6, FF 1e-10.
+Tolerances (relative L2 error over all charges): FP32C 1e-6, FF and FP64 1e-10.
 """
 import numpy as np
 import pytest
@@ -16,10 +16,10 @@ from paper_1310_4374_gb300 import workloads as W
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp32c": 1e-6, "ff": 1e-10}
+TOL = {"fp32c": 1e-6, "ff": 1e-10, "fp64": 1e-10}
 # the two forms round differently; their coefficients agree to the float32 pair sums'
-# accuracy amplified by the pseudo-inverse (FP32C), or to float64 accuracy (FF)
-C_TOL = {"fp32c": 1e-4, "ff": 1e-9}
+# accuracy amplified by the pseudo-inverse (FP32C), or to float64 accuracy (FF, FP64)
+C_TOL = {"fp32c": 1e-4, "ff": 1e-9, "fp64": 1e-9}
 
 
 def _dev(a):
@@ -61,7 +61,7 @@ def _gpu(s, precision, checks, kw):
         pc.close()
 
 
-@pytest.mark.parametrize("precision", ["fp32c", "ff"])
+@pytest.mark.parametrize("precision", ["fp32c", "ff", "fp64"])
 @pytest.mark.parametrize("name,make,kw", CASES, ids=[c[0] for c in CASES])
 def test_layers_against_oracle_and_points(name, make, kw, precision):
     s = make()
@@ -81,8 +81,9 @@ def test_layers_against_oracle_and_points(name, make, kw, precision):
 def test_automatic_check_form():
     s = W.uniform_gauss(N=300, d=(1.0, 1.5, 2.0), p=8, M=200, seed=1)
     expect = [({"precision": "fp32c"}, "layers"), ({"precision": "ff"}, "layers"),
-              ({"precision": "fp64"}, "points"), ({"precision": "fp32c", "checks": "points"}, "points"),
-              ({"precision": "fp32c", "lam": 1.5}, "points")]
+              ({"precision": "fp64"}, "layers"), ({"precision": "fp32c", "checks": "points"}, "points"),
+              ({"precision": "fp64", "checks": "points"}, "points"),
+              ({"precision": "fp32c", "lam": 1.5}, "points"), ({"precision": "fp64", "lam": 1.5}, "points")]
     for kw, form in expect:
         pc = B.PeriodicCoulomb(s.d, s.p, s.M, **kw)
         try:
@@ -110,7 +111,7 @@ def test_layers_deterministic_and_graph_replay():
         pc.close()
 
 
-@pytest.mark.parametrize("precision", ["fp32c", "ff"])
+@pytest.mark.parametrize("precision", ["fp32c", "ff", "fp64"])
 def test_batch_with_mixed_check_forms(precision):
     # systems whose plans take the two-layer form and systems whose plans take the point
     # form in one batch: each against the oracle and against its single evaluation
