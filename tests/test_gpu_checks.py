@@ -116,7 +116,9 @@ def test_batch_with_mixed_check_forms(precision):
     # systems whose plans take the two-layer form and systems whose plans take the point
     # form in one batch: each against the oracle and against its single evaluation
     systems = W.config(4, small=True)
-    forms = ["layers" if b % 2 == 0 else "points" for b in range(len(systems))]
+    forms = ["points" if b % 3 == 1 else "layers" for b in range(len(systems))]
+    # a widened block K = (2, 1, 1) among the layered systems (layers of 15 and 9 images)
+    assert any(tuple(s.K) != (1, 1, 1) and f == "layers" for s, f in zip(systems, forms))
     pb = B.PeriodicBatch(systems, precision=precision, checks=forms)
     try:
         assert [B.psum_check_form(p) for p in pb.plans] == forms
