@@ -151,7 +151,7 @@ __global__ void __launch_bounds__(256) k_bproject(const BatchDev* __restrict__ s
     if (lane == 0) C[S.C0 + 1 + row] = s;
 }
 
-// mean of phi_near per segment (Eq. pfx4 through App. C's face and edge integrals)
+// mean of phi_near per segment (Eq. pfx4; the block potential by its regrouped corner sum)
 
 __global__ void __launch_bounds__(kSeg) k_bbox_mean(const double* __restrict__ x, const double* __restrict__ q,
                                                     const BatchDev* __restrict__ sys,
@@ -164,7 +164,7 @@ __global__ void __launch_bounds__(kSeg) k_bbox_mean(const double* __restrict__ x
     double s = 0.0;
     if (i < S.n0 + S.n && S.zero_mean) {
         const double X[3] = {x[3 * i], x[3 * i + 1], x[3 * i + 2]};
-        s = q[i] * block_potential_corners(X, S.H);
+        s = q[i] * block_potential_inside(X, S.H);
     }
     __shared__ double ws[kSeg / 32];
     for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);

@@ -81,26 +81,26 @@ __global__ void k_validate_finish(const double* __restrict__ partial, int nblk, 
     if (threadIdx.x == 0 && !(fabs(s) <= 1e-12 * sa)) atomicOr(status, kStatNonNeutral);
 }
 
-// One (charge, corner) pair per work item: sum_i q_i U(x_i) with U the corner sum over the
-// block's 8 corners.  Eight items per charge in blocks of 64 threads keep small systems from
-// running a handful of blocks through the float64 pipes of a few SMs (4000 charges: 148 us
-// with one 256-thread block per 256 charges).
+// One (charge, term) pair per work item: sum_i q_i U(x_i) with U the regrouped corner sum
+// over the block (12 terms, each one logarithm and one two-argument arctangent; every charge
+// of the box lies inside the block).  Twelve items per
+// charge in blocks of 64 threads keep small systems from running a handful of blocks through
+// the float64 pipes of a few SMs (4000 charges: 148 us with one 256-thread block per 256
+// charges).
 constexpr int kMeanThreads = 64;
+constexpr int kMeanTerms = 12;
 
 __global__ void __launch_bounds__(kMeanThreads) k_box_mean(const double* __restrict__ x, const double* __restrict__ q,
                                                            int64_t n, double H0, double H1, double H2,
                                                            double* __restrict__ partial) {
+    const double H[3] = {H0, H1, H2};
     double s = 0.0, dummy = 0.0;
-    for (int64_t k = (int64_t)blockIdx.x * kMeanThreads + threadIdx.x; k < 8 * n;
+    for (int64_t k = (int64_t)blockIdx.x * kMeanThreads + threadIdx.x; k < kMeanTerms * n;
          k += (int64_t)gridDim.x * kMeanThreads) {
-        const int64_t i = k >> 3;
-        const int c = (int)(k & 7);
-        const double a = (c & 1) ? H0 - x[3 * i] : -H0 - x[3 * i];
-        const double b = (c & 2) ? H1 - x[3 * i + 1] : -H1 - x[3 * i + 1];
-        const double e = (c & 4) ? H2 - x[3 * i + 2] : -H2 - x[3 * i + 2];
-        const int lower = !(c & 1) + !(c & 2) + !(c & 4);
-        const double f = prism_corner(a, b, e);
-        s += q[i] * ((lower & 1) ? -f : f);
+        const int64_t i = k / kMeanTerms;
+        const int j = (int)(k - i * kMeanTerms);
+        const double X[3] = {x[3 * i], x[3 * i + 1], x[3 * i + 2]};
+        s += q[i] * block_potential_inside_term(X, H, j);
     }
     block_sum2<kMeanThreads>(s, dummy);
     if (threadIdx.x == 0) partial[blockIdx.x] = s;
@@ -351,7 +351,7 @@ cudaError_t launch_validate(const double* x, const double* q, int64_t n, const d
 }
 
 int mean_blocks(int64_t n, int num_sms) {
-    int64_t nb = (8 * n + kMeanThreads - 1) / kMeanThreads;
+    int64_t nb = (kMeanTerms * n + kMeanThreads - 1) / kMeanThreads;
     const int64_t cap = 16LL * num_sms;
     if (nb > cap) nb = cap;
     return nb < 1 ? 1 : (int)nb;

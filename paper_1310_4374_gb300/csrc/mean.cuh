@@ -92,4 +92,64 @@ __host__ __device__ __forceinline__ double block_potential_corners(const double 
     return U;
 }
 
+// The corner sum regrouped for a point inside the block (upper corner offsets positive, lower
+// ones negative or, on a lower face, zero).  Take an axis k and one of
+// the four corners (p, q) of the other two axes ((k+1, k+2) cyclically): the two block corners
+// that differ in k alone carry opposite signs, and F's terms p q ln(k + r) and
+// -p^2/2 atan(q k/(p r)) of the two combine, with (k_u, r_u) and (k_l, r_l) the upper and lower
+// corner's offset along k and distance:
+//   ln(k_u + r_u) - ln(k_l + r_l) = ln((k_u + r_u)(r_l - k_l) / (p^2 + q^2))
+//     (k_l + r_l = (p^2 + q^2)/(r_l - k_l), no cancellation as k_l < 0),
+//   atan(u) - atan(v) = atan2(p q (k_u r_l - k_l r_u), p^2 r_u r_l + q^2 k_u k_l)
+//     (u, v the two arguments: arg((1 + iu)(1 - iv)) with the factor p^2 r_u r_l > 0 taken out;
+//      the difference lies in (-pi, pi), so the principal value is exact).
+// Every log and arctangent of the 8 corners falls in exactly one (axis, corner) pair: 12
+// logarithms and 12 two-argument arctangents instead of 24 and 24.
+__host__ __device__ __forceinline__ double block_pair_term(double p, double q, double ku, double kl, double ru,
+                                                           double rl) {
+    // a vanishing p q drops the logarithm (its limit is 0; a charge on a face of a block with
+    // K_k = 0 can make p, q or k_l zero)
+    const double pq2 = p * p + q * q;
+    const double L = p * q != 0.0 ? p * q * log((ku + ru) * (rl - kl) / pq2) : 0.0;
+    const double A = 0.5 * p * p * atan2(p * q * (ku * rl - kl * ru), p * p * ru * rl + q * q * ku * kl);
+    return L - A;
+}
+
+// Term j (0..11) of the regrouped corner sum: axis k = j / 4, the other two axes' corner from
+// j % 4 (bit 0: p upper, bit 1: q upper), signed +1 when an even number of p, q is lower.
+__host__ __device__ __forceinline__ double block_potential_inside_term(const double X[3], const double H[3], int j) {
+    const int k = j >> 2, k1 = k == 2 ? 0 : k + 1, k2 = k == 0 ? 2 : k - 1;
+    const double p = (j & 1) ? H[k1] - X[k1] : -H[k1] - X[k1];
+    const double q = (j & 2) ? H[k2] - X[k2] : -H[k2] - X[k2];
+    const double ku = H[k] - X[k], kl = -H[k] - X[k];
+    const double pq2 = p * p + q * q;
+    const double t = block_pair_term(p, q, ku, kl, sqrt(pq2 + ku * ku), sqrt(pq2 + kl * kl));
+    const int lower = !(j & 1) + !(j & 2);
+    return (lower & 1) ? -t : t;
+}
+
+// U(x) over the block for x inside it (-H_k <= x_k < H_k): the 12 regrouped terms, the
+// distances of the 8 corners computed once.
+__host__ __device__ __forceinline__ double block_potential_inside(const double X[3], const double H[3]) {
+    const double lo[3] = {-H[0] - X[0], -H[1] - X[1], -H[2] - X[2]};
+    const double up[3] = {H[0] - X[0], H[1] - X[1], H[2] - X[2]};
+    double r[8];                          // corner c: bit k set = upper along axis k
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const double a = (c & 1) ? up[0] : lo[0], b = (c & 2) ? up[1] : lo[1], e = (c & 4) ? up[2] : lo[2];
+        r[c] = sqrt(a * a + b * b + e * e);
+    }
+    double U = 0.0;
+#pragma unroll
+    for (int j = 0; j < 12; ++j) {
+        const int k = j >> 2, k1 = k == 2 ? 0 : k + 1, k2 = k == 0 ? 2 : k - 1;
+        const int cu = (1 << k) | ((j & 1) << k1) | (((j >> 1) & 1) << k2);   // upper along k
+        const double t = block_pair_term((j & 1) ? up[k1] : lo[k1], (j & 2) ? up[k2] : lo[k2], up[k], lo[k], r[cu],
+                                         r[cu & ~(1 << k)]);
+        const int lower = !(j & 1) + !(j & 2);
+        U += (lower & 1) ? -t : t;
+    }
+    return U;
+}
+
 }  // namespace psum
