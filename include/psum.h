@@ -99,7 +99,10 @@ extern "C" {
  * points instead of (2K_1+1)(2K_2+1)(2K_3+1) images at 2M points (18 x M against 27 x 2M for
  * the 3x3x3 block). */
 #define PSUM_CHECKS_AUTO    0  /* layers where they apply (plans without ball trimming, every
-                                  precision, single systems and batches), points otherwise */
+                                  precision, single systems and batches) and take no more (target
+                                  tile, image) units than the points: the points are packed class
+                                  by class in whole groups of 128, so with few points per class
+                                  (FP32C, M = 200) the 2M points are cheaper; points otherwise */
 #define PSUM_CHECKS_POINTS  1  /* phi_near at y_l and at y~_l, differenced in float64 */
 #define PSUM_CHECKS_LAYERS  2  /* the two-layer form; PSUM_ERR_ARG for ball-trimmed plans (the ball
                                   is not a block of images) */

@@ -309,6 +309,12 @@ static int build_check_layers(Plan& pl, const double d[3]) {
     while (slot.size() % (fp32 ? kTile32 : kTile64)) slot.push_back(-1);
     while (gcls.size() < slot.size() / kNearChunk) gcls.push_back(0);
     const int ngroups = (int)gcls.size();
+    const int tiles = fp32 ? ngroups / kTgt32 : ngroups;
+    // the automatic choice takes the layers only where they need no more (target tile, image)
+    // units than the points: with few points per class the classes' part-filled groups can
+    // outweigh the third of the images saved (FP32C, M = 200: 2 tiles x 18 against 1 x 27)
+    if (pl.opt.check_form == PSUM_CHECKS_AUTO && (int64_t)tiles * n_img > (int64_t)pl.n_check_tiles * pl.n_images)
+        return PSUM_OK;
     std::vector<int> pos(M);
     for (size_t i = 0; i < slot.size(); ++i)
         if (slot[i] >= 0) pos[slot[i]] = (int)i;
@@ -331,7 +337,7 @@ static int build_check_layers(Plan& pl, const double d[3]) {
     if ((s1 = upload(&pl.d_lc_cls, gcls.data(), gcls.size()))) return s1;
     if ((s1 = upload(&pl.d_lc_shifts, sh.data(), sh.size()))) return s1;
     if ((s1 = upload(&pl.d_lc_w, w.data(), w.size()))) return s1;
-    pl.lc_tiles = fp32 ? ngroups / kTgt32 : ngroups;
+    pl.lc_tiles = tiles;
     pl.lc_img = n_img;
     return PSUM_OK;
 }

@@ -79,15 +79,22 @@ def test_layers_against_oracle_and_points(name, make, kw, precision):
 
 
 def test_automatic_check_form():
+    # the layers where they apply and need no more (tile, image) units than the 2M points
     s = W.uniform_gauss(N=300, d=(1.0, 1.5, 2.0), p=8, M=200, seed=1)
-    expect = [({"precision": "fp32c"}, "layers"), ({"precision": "ff"}, "layers"),
-              ({"precision": "fp64"}, "layers"), ({"precision": "fp32c", "checks": "points"}, "points"),
-              ({"precision": "fp64", "checks": "points"}, "points"),
-              ({"precision": "fp32c", "lam": 1.5}, "points"), ({"precision": "fp64", "lam": 1.5}, "points")]
+    expect = [({"precision": "fp32c", "M": 200}, "points"),     # 2 tiles x 18 against 1 x 27
+              ({"precision": "fp32c", "M": 400}, "layers"),     # 2 x 18 against 2 x 27
+              ({"precision": "ff", "M": 400}, "layers"),
+              ({"precision": "fp64", "M": 200}, "layers"),      # tiles of 128: 6 x 18 against 4 x 27
+              ({"precision": "fp32c", "M": 200, "checks": "layers"}, "layers"),
+              ({"precision": "fp32c", "M": 400, "checks": "points"}, "points"),
+              ({"precision": "fp64", "M": 200, "checks": "points"}, "points"),
+              ({"precision": "fp32c", "M": 800, "lam": 1.5}, "points"), ({"precision": "fp64", "M": 200, "lam": 1.5}, "points")]
     for kw, form in expect:
-        pc = B.PeriodicCoulomb(s.d, s.p, s.M, **kw)
+        kw = dict(kw)
+        M = kw.pop("M")
+        pc = B.PeriodicCoulomb(s.d, s.p, M, **kw)
         try:
-            assert B.psum_check_form(pc.plan) == form, kw
+            assert B.psum_check_form(pc.plan) == form, (M, kw)
         finally:
             pc.close()
 
