@@ -100,12 +100,12 @@ extern "C" {
  * the 3x3x3 block). */
 #define PSUM_CHECKS_AUTO    0  /* layers where they apply (plans without ball trimming, every
                                   precision, single systems and batches) and take no more (target
-                                  tile, image) units than the points: the points are packed class
-                                  by class in whole groups of 128, so with few points per class
-                                  (FP32C, M = 200) the 2M points are cheaper; points otherwise */
+                                  tile, image) units than the points; points otherwise */
 #define PSUM_CHECKS_POINTS  1  /* phi_near at y_l and at y~_l, differenced in float64 */
 #define PSUM_CHECKS_LAYERS  2  /* the two-layer form; PSUM_ERR_ARG for ball-trimmed plans (the ball
-                                  is not a block of images) */
+                                  is not a block of images).  Float32 plans whose layers exceed the
+                                  pair kernel's shared memory (K = 3 along two axes) keep the
+                                  points; psum_check_form reports the form taken. */
 
 #define PSUM_MEAN_ZERO 0  /* C_1 makes the box mean of phi zero (Eq. pfx3, phi_mean = 0) */
 #define PSUM_MEAN_NONE 1  /* C_1 = 0 (potential defined up to a constant, Sec. 3) */

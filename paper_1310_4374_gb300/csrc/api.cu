@@ -337,12 +337,12 @@ int queue_forward(psum_plan_s* h, int64_t N, const double* x, const double* q, d
     const bool layers = pl.lc_tiles > 0;
     if (layers && !fp32) {
         TRY(launch_near64(false, L.pk64, (const double4_32a*)pl.d_lc_tgt, pl.d_lc_shifts, L.part_c, L.Lc, st, 0.0,
-                          pl.d_lc_cls, pl.d_lc_w));
+                          pl.d_lc_w, kCheckClasses));
     } else if (layers) {
         const float4* ct = (const float4*)pl.d_lc_tgt;
         const size_t half = 2 * (size_t)pl.lc_tiles * kTile32;         // hi parts, then lo parts
         TRY(launch_near32(false, L.pk32, L.pk32lo, L.org, ct, ct + half, pl.d_lc_org, pl.d_lc_shifts, L.part_c,
-                          L.Lc, st, 0, nullptr, 0.0, ff, pl.d_lc_cls, pl.d_lc_w));
+                          L.Lc, st, 0, nullptr, 0.0, ff, pl.d_lc_gmask, pl.d_lc_w, kCheckClasses, pl.d_lc_sub));
     } else if (fp32) {
         const float4* ct = (const float4*)pl.d_check_tgt;
         const size_t half = 2 * (size_t)pl.n_check_tiles * kTile32;    // hi parts, then lo parts

@@ -281,10 +281,13 @@ struct psum_batch_s {
     double* d_shifts = nullptr;
     float4 *d_chk_hi = nullptr, *d_chk_lo = nullptr;
     double* d_chk_org = nullptr;
-    // the check sums' image tables, per system either its block images (weight 1, every
-    // group class 0) or its plan's two-layer tables (6 classes), and the class of each packed
-    // check group (a float64 tile is one group)
+    // the check sums' image tables: per system its block images with weight 1, or, when the
+    // batch runs the two-layer form (c_cls = kCheckClasses), its plan's two-layer tables for
+    // its points' 6 classes (a system in the point form: class 0 its block images, the other
+    // classes the same with weight 0); float32: the classes present in each check group
+    int c_cls = 1;
     int* d_chk_cls = nullptr;
+    double* d_chk_sub = nullptr;        // float32, two-layer form: [group][6][4] class spheres
     double* d_cshifts = nullptr;
     float* d_cw = nullptr;
     size_t n_centries = 0;
@@ -363,6 +366,7 @@ size_t batch_layout(psum_batch_s* bt, char* base) {
     for (const psum_plan_t p : bt->plans) n_shift += 3 * (size_t)p->pl.n_images;
     bt->d_shifts = b.take<double>(n_shift);
     bt->d_chk_cls = b.take<int>((size_t)(bt->n_chk_pts / kNearChunk));
+    bt->d_chk_sub = b.take<double>((size_t)(bt->n_chk_pts / kNearChunk) * kCheckClasses * 4);
     bt->d_cshifts = b.take<double>(3 * bt->n_centries);
     bt->d_cw = b.take<float>(bt->n_centries);
     if (fp32) {
@@ -437,13 +441,14 @@ int queue_batch(psum_batch_s* bt, const double* x, const double* q, double* phi,
             BTRY(launch_near32(true, bt->pk_hi, bt->pk_lo, bt->org, bt->pk_hi, bt->pk_lo, bt->org, bt->d_shifts,
                                bt->part_n, bt->Ln[variant], st, variant, nullptr, 0.0, ff));
         BTRY(launch_near32(false, bt->pk_hi, bt->pk_lo, bt->org, bt->d_chk_hi, bt->d_chk_lo, bt->d_chk_org,
-                           bt->d_cshifts, bt->part_c, bt->Lc, st, 0, nullptr, 0.0, ff, bt->d_chk_cls, bt->d_cw));
+                           bt->d_cshifts, bt->part_c, bt->Lc, st, 0, nullptr, 0.0, ff, bt->d_chk_cls, bt->d_cw,
+                           bt->c_cls, bt->d_chk_sub));
     } else {
         BTRY(launch_pack64_groups(x, q, bt->n_pts, bt->d_grp_start, bt->d_grp_count, bt->pk64, st));
         nl += 1;
         BTRY(launch_near64(true, bt->pk64, bt->pk64, bt->d_shifts, bt->part_n, bt->Ln[0], st));
-        BTRY(launch_near64(false, bt->pk64, bt->d_chk64, bt->d_cshifts, bt->part_c, bt->Lc, st, 0.0, bt->d_chk_cls,
-                           bt->d_cw));
+        BTRY(launch_near64(false, bt->pk64, bt->d_chk64, bt->d_cshifts, bt->part_c, bt->Lc, st, 0.0, bt->d_cw,
+                           bt->c_cls));
     }
     const int tile = fp32 ? kTile32 : kTile64;
     if (variant == kVariantSym)
@@ -602,6 +607,19 @@ int psum_batch_create(const psum_plan_t* plans, int B, const int64_t* offsets, p
     int shift0 = 0;
     int64_t cent0 = 0;                      // first entry of the system's check image table
     std::vector<int64_t> cent_first(B);
+    // the two-layer form when a plan takes it and (float32) the per-class offsets of the
+    // largest image list fit the kernel's shared memory
+    {
+        bool any = false;
+        int max_c = 1;
+        for (int b = 0; b < B; ++b) {
+            const Plan& pl = plans[b]->pl;
+            any = any || pl.lc_tiles > 0;
+            max_c = std::max(max_c, pl.lc_tiles > 0 ? pl.lc_img : pl.n_images);
+        }
+        bt->c_cls = any && (!fp32 || near32_dyn_smem(max_c, false, false, kCheckClasses) <= kNear32DynSmemMax)
+                        ? kCheckClasses : 1;
+    }
     bt->sys.resize(B);
     bt->near_n.resize(B);
     bt->near_c.resize(B);
@@ -621,7 +639,7 @@ int psum_batch_create(const psum_plan_t* plans, int B, const int64_t* offsets, p
         S.pinv = pl.d_pinv;
         S.Rbox = pl.d_Rbox;
         // plans with two-layer tables keep that form in the batch
-        const bool layers = pl.lc_tiles > 0;
+        const bool layers = bt->c_cls > 1 && pl.lc_tiles > 0;
         S.layers = layers ? 1 : 0;
         S.check_pos = layers ? pl.d_lc_pos : pl.d_check_pos;
         S.tab64 = pl.d_shtab64;
@@ -654,7 +672,7 @@ int psum_batch_create(const psum_plan_t* plans, int B, const int64_t* offsets, p
         bt->near_c[b] = NearSys{unit_c, tile_c, chk_tiles, n_chunks, pt / kNearChunk, (int)cent0, c_img,
                                 near_chunk_stride(n_chunks)};
         cent_first[b] = cent0;
-        cent0 += layers ? 6 * (int64_t)c_img : c_img;
+        cent0 += (int64_t)bt->c_cls * c_img;
         SymSys ss{};
         ss.tile0 = tile_n;
         ss.n_tiles = n_tiles;
@@ -757,23 +775,42 @@ int psum_batch_create(const psum_plan_t* plans, int B, const int64_t* offsets, p
         // the system's check image table and group classes
         const size_t ce = (size_t)cent_first[b];
         if (st == PSUM_OK && S.layers) {
-            const size_t n_e = 6 * (size_t)pl.lc_img;
+            const size_t n_e = (size_t)kCheckClasses * pl.lc_img;
             st = cuda_st(cudaMemcpy(bt->d_cshifts + 3 * ce, pl.d_lc_shifts, sizeof(double) * 3 * n_e,
                                     cudaMemcpyDeviceToDevice));
             if (st == PSUM_OK)
                 st = cuda_st(cudaMemcpy(bt->d_cw + ce, pl.d_lc_w, sizeof(float) * n_e, cudaMemcpyDeviceToDevice));
-            if (st == PSUM_OK)
-                st = cuda_st(cudaMemcpy(bt->d_chk_cls + S.chk_pt0 / kNearChunk, pl.d_lc_cls, sizeof(int) * ngrp,
+            if (st == PSUM_OK && fp32)
+                st = cuda_st(cudaMemcpy(bt->d_chk_cls + S.chk_pt0 / kNearChunk, pl.d_lc_gmask, sizeof(int) * ngrp,
                                         cudaMemcpyDeviceToDevice));
+            if (st == PSUM_OK && fp32)
+                st = cuda_st(cudaMemcpy(bt->d_chk_sub + (S.chk_pt0 / kNearChunk) * kCheckClasses * 4, pl.d_lc_sub,
+                                        sizeof(double) * ngrp * kCheckClasses * 4, cudaMemcpyDeviceToDevice));
         } else if (st == PSUM_OK) {
-            const std::vector<float> ones((size_t)pl.n_images, 1.f);
-            st = cuda_st(cudaMemcpy(bt->d_cshifts + 3 * ce, pl.d_shifts, sizeof(double) * 3 * pl.n_images,
-                                    cudaMemcpyDeviceToDevice));
+            // the block images for every class (weight 1 for class 0, which all its points have)
+            std::vector<float> wts((size_t)bt->c_cls * pl.n_images, 0.f);
+            std::fill(wts.begin(), wts.begin() + pl.n_images, 1.f);
+            for (int c = 0; c < bt->c_cls && st == PSUM_OK; ++c)
+                st = cuda_st(cudaMemcpy(bt->d_cshifts + 3 * (ce + (size_t)c * pl.n_images), pl.d_shifts,
+                                        sizeof(double) * 3 * pl.n_images, cudaMemcpyDeviceToDevice));
             if (st == PSUM_OK)
-                st = cuda_st(cudaMemcpy(bt->d_cw + ce, ones.data(), sizeof(float) * ones.size(),
+                st = cuda_st(cudaMemcpy(bt->d_cw + ce, wts.data(), sizeof(float) * wts.size(), cudaMemcpyHostToDevice));
+            if (st == PSUM_OK && fp32) {
+                const std::vector<int> ones(ngrp, 1);
+                st = cuda_st(cudaMemcpy(bt->d_chk_cls + S.chk_pt0 / kNearChunk, ones.data(), sizeof(int) * ngrp,
                                         cudaMemcpyHostToDevice));
-            if (st == PSUM_OK)
-                st = cuda_st(cudaMemset(bt->d_chk_cls + S.chk_pt0 / kNearChunk, 0, sizeof(int) * ngrp));
+                // every class's sphere is the group's own (only class 0 occurs)
+                std::vector<double> org(4 * ngrp), sub(ngrp * kCheckClasses * 4);
+                if (st == PSUM_OK)
+                    st = cuda_st(cudaMemcpy(org.data(), pl.d_check_org, sizeof(double) * org.size(),
+                                            cudaMemcpyDeviceToHost));
+                for (size_t g = 0; g < ngrp; ++g)
+                    for (int c = 0; c < kCheckClasses; ++c)
+                        for (int k = 0; k < 4; ++k) sub[4 * (g * kCheckClasses + c) + k] = org[4 * g + k];
+                if (st == PSUM_OK)
+                    st = cuda_st(cudaMemcpy(bt->d_chk_sub + (S.chk_pt0 / kNearChunk) * kCheckClasses * 4, sub.data(),
+                                            sizeof(double) * sub.size(), cudaMemcpyHostToDevice));
+            }
         }
     }
     if (st == PSUM_OK) st = cuda_st(cudaMallocHost((void**)&bt->h_status, sizeof(int) * B));

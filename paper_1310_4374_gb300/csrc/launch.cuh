@@ -10,10 +10,16 @@ cudaError_t launch_near32(bool grad, const float4* src_hi, const float4* src_lo,
                           const float4* tgt_hi, const float4* tgt_lo, const double* tgt_org, const double* shifts,
                           double* partial, const NearPlanLaunch& L, cudaStream_t st, int variant = 0,
                           const double* src_x = nullptr, double Rb = 0.0, bool ff = false,
-                          const int* tgt_cls = nullptr, const float* img_w = nullptr);
+                          const int* grp_cls = nullptr, const float* img_w = nullptr, int n_cls = 1,
+                          const double* grp_sub = nullptr);
 cudaError_t launch_near64(bool grad, const double4_32a* src, const double4_32a* tgt, const double* shifts,
                           double* partial, const NearPlanLaunch& L, cudaStream_t st, double Rb = 0.0,
-                          const int* tgt_cls = nullptr, const float* img_w = nullptr);
+                          const float* img_w = nullptr, int n_cls = 1);
+constexpr int kCheckClasses = 6;   // two-layer check sums: partner axis and side
+// dynamic shared memory of k_near32 for n_img images and n_cls image lists per target group;
+// the launches stay within the 48 KiB that needs no opt-in
+size_t near32_dyn_smem(int n_img, bool trimmed, bool grad, int n_cls);
+constexpr size_t kNear32DynSmemMax = 48 * 1024;
 cudaError_t launch_near_reduce(const double* partial, int64_t n_valid, int tile_size, int nq,
                                const NearPlanLaunch& L, double* out_phi, double* out_grad, cudaStream_t st);
 int near32_occupancy_ctas(int n_img, int variant = 0, bool trimmed = false, bool ff = false);

@@ -54,11 +54,14 @@ struct Near32Args {
     int inject;              // test hook: expect 16 bytes more than the copies bring
     int max_contrib, max_img;
     NearSysTable tab;
-    // two-layer check sums (potential only): the class of each target group; the image
-    // vector of (class c, image j) is shifts[shift0 + c n_img + j] and its weight
-    // img_w[shift0 + c n_img + j].  Null: one image list, weight 1.
-    const int* tgt_cls;
+    // two-layer check sums (potential only): each target's class c (0..n_cls-1) rides in its
+    // pack's charge slot; the image vector of (class c, image j) is shifts[shift0 + c n_img + j]
+    // and its weight img_w[shift0 + c n_img + j]; grp_cls holds each target group's classes as
+    // a bit mask.  n_cls = 1 and null tables: one image list, weight 1.
+    const int* grp_cls;
+    const double* grp_sub;       // [group][n_cls][4]: centre and radius of each class's points
     const float* img_w;
+    int n_cls;
 };
 
 // Two register budgets of the same kernel: 4 resident CTAs per SM (up to 128 registers) or
@@ -75,12 +78,15 @@ __global__ void __launch_bounds__(kThreads32, kMinB) k_near32(Near32Args a) {
     __shared__ float2 s_th[3][2][kThreads32];             // target hi offsets, [coord][pair]
     __shared__ float2 s_tl[kFF ? 3 : 1][2][kThreads32];   // FF: target lo offsets
     __shared__ float2 s_acc[NQ][2][2][kThreads32];        // [quantity][pair][hi, lo]
-    extern __shared__ float4 s_dyn4[];                    // [max_img][kTgt32][6] deltas, [max_img] flags,
-    float* s_delta = (float*)s_dyn4;                      // potential only: [max_img][kTgt32] weights,
-    int* s_near = (int*)(s_delta + 6 * kTgt32 * a.max_img);   // then (trimmed plans) the compacted
-    float* s_w = (float*)(s_near + a.max_img);            // sources of a straddling unit
+    // classes of the targets' image lists: 1, or (two-layer check sums) one per target
+    const int ncls = kGrad ? 1 : a.n_cls;
+    __shared__ int s_tcls[kGrad ? 1 : kTgt32][kThreads32];   // potential only: the targets' classes
+    extern __shared__ float4 s_dyn4[];                    // [max_img][kTgt32][ncls][6] deltas, [max_img] flags,
+    float* s_delta = (float*)s_dyn4;                      // potential only: [max_img][kTgt32][ncls] weights,
+    int* s_near = (int*)(s_delta + 6 * kTgt32 * ncls * a.max_img);   // then (trimmed plans) the
+    float* s_w = (float*)(s_near + a.max_img);            // compacted sources of a straddling unit
     constexpr int kWts = kGrad ? 0 : kTgt32;
-    float4* s_hm = s_dyn4 + (6 * kTgt32 * a.max_img + a.max_img + kWts * a.max_img + 3) / 4;
+    float4* s_hm = s_dyn4 + (6 * kTgt32 * ncls * a.max_img + a.max_img + kWts * ncls * a.max_img + 3) / 4;
 
     __shared__ int s_item;
     __shared__ int s_fail;
@@ -147,6 +153,13 @@ __global__ void __launch_bounds__(kThreads32, kMinB) k_near32(Near32Args a) {
                 s_th[0][j][tid] = make_float2(A0.x, A1.x);
                 s_th[1][j][tid] = make_float2(A0.z, A1.z);
                 s_th[2][j][tid] = make_float2(B0.x, B1.x);
+                if constexpr (!kGrad) {
+                    // a class outside 0..ncls-1 (the padding of a point-form pack holds 1e3
+                    // there) reads class 0: the index stays inside the tables
+                    const float c0 = B0.z, c1 = B1.z;
+                    s_tcls[2 * j][tid] = ncls > 1 && c0 >= 0.f && c0 < (float)ncls ? (int)c0 : 0;
+                    s_tcls[2 * j + 1][tid] = ncls > 1 && c1 >= 0.f && c1 < (float)ncls ? (int)c1 : 0;
+                }
                 if (kFF) {
                     const float4 C0 = a.tgt_lo[2 * i0], D0 = a.tgt_lo[2 * i0 + 1];
                     const float4 C1 = a.tgt_lo[2 * i1], D1 = a.tgt_lo[2 * i1 + 1];
@@ -175,6 +188,35 @@ __global__ void __launch_bounds__(kThreads32, kMinB) k_near32(Near32Args a) {
             }
             const double* so = a.src_org + 4 * chunk;
             const int shift0 = Sp->shift0;
+            if (!kGrad && ncls > 1) {
+                // per (image, group, class): the offset with the class's layer image, its
+                // weight; a unit is near when a class present in a group is near
+                for (int im = tid; im < n_img; im += kThreads32) s_near[im] = 0;
+                __syncthreads();
+                for (int e = tid; e < n_img * kTgt32 * ncls; e += kThreads32) {
+                    const int im = e / (kTgt32 * ncls), r = e - im * kTgt32 * ncls;
+                    const int k = r / ncls, c = r - k * ncls;
+                    // a class no target of the group has (padding included) is never read
+                    if (!((a.grp_cls[cur_tile * kTgt32 + k] >> c) & 1)) continue;
+                    const int ei = shift0 + c * n_img + im;
+                    const double* sh = a.shifts + 3 * ei;
+                    const double* to = a.tgt_org + 4 * (cur_tile * kTgt32 + k);
+                    const double D0 = (to[0] - so[0]) - sh[0], D1 = (to[1] - so[1]) - sh[1],
+                                 D2 = (to[2] - so[2]) - sh[2];
+                    float* dl = s_delta + 6 * e;
+                    dl[0] = (float)D0; dl[1] = (float)D1; dl[2] = (float)D2;
+                    dl[3] = (float)(D0 - (double)dl[0]); dl[4] = (float)(D1 - (double)dl[1]);
+                    dl[5] = (float)(D2 - (double)dl[2]);
+                    s_w[e] = a.img_w[ei];
+                    // the near test on the class's own points of the group
+                    const double* sb = a.grp_sub + 4 * ((cur_tile * kTgt32 + k) * ncls + c);
+                    const double E0 = (sb[0] - so[0]) - sh[0], E1 = (sb[1] - so[1]) - sh[1],
+                                 E2 = (sb[2] - so[2]) - sh[2];
+                    const double reach = kNearFactor * (sb[3] + so[3]);
+                    if (E0 * E0 + E1 * E1 + E2 * E2 <= reach * reach)
+                        atomicOr(s_near + im, k < 2 ? kUnitNear0 : kUnitNear1);
+                }
+            } else
             for (int im = tid; im < n_img; im += kThreads32) {
                 const double* sh = a.shifts + 3 * (shift0 + im);
                 int nr = 0;
@@ -183,12 +225,7 @@ __global__ void __launch_bounds__(kThreads32, kMinB) k_near32(Near32Args a) {
                     const double* to = a.tgt_org + 4 * (cur_tile * kTgt32 + k);
                     const double* shk = sh;
                     if constexpr (!kGrad) {
-                        float wk = 1.f;
-                        if (a.tgt_cls) {   // the group's own layer image and its weight
-                            const int e = shift0 + a.tgt_cls[cur_tile * kTgt32 + k] * n_img + im;
-                            shk = a.shifts + 3 * e;
-                            wk = a.img_w[e];
-                        }
+                        const float wk = a.img_w ? a.img_w[shift0 + im] : 1.f;
                         s_w[im * kTgt32 + k] = wk;
                         weighted = weighted || wk != 0.f;
                     }
@@ -228,7 +265,9 @@ __global__ void __launch_bounds__(kThreads32, kMinB) k_near32(Near32Args a) {
             }
             cur_chunk = chunk;
         }
-        const float* dl = s_delta + 6 * (img * kTgt32);
+        const float* dl = s_delta + 6 * (img * kTgt32 * ncls);
+        // the offsets of target group g's thread target (its class's entry) and the weights
+        auto dptr = [&](int g) { return dl + 6 * (g * ncls + (kGrad ? 0 : s_tcls[g][tid])); };
         const int cls = s_near[img];
         if ((kTrim || !kGrad) && (cls & kUnitOutside)) {
             ++u;
@@ -237,7 +276,9 @@ __global__ void __launch_bounds__(kThreads32, kMinB) k_near32(Near32Args a) {
         // potential only: the weight of each target group for this image (1, or +-1 and 0
         // for the two-layer check sums); multiplying by it is exact
         auto wpair = [&](int j) {
-            return make_float2(s_w[img * kTgt32 + 2 * j], s_w[img * kTgt32 + 2 * j + 1]);
+            const float* wl = s_w + img * kTgt32 * ncls;
+            return make_float2(wl[2 * j * ncls + (kGrad ? 0 : s_tcls[2 * j][tid])],
+                               wl[(2 * j + 1) * ncls + (kGrad ? 0 : s_tcls[2 * j + 1][tid])]);
         };
         // sources the unit's pair loops run over: the staged chunk, or for a unit that
         // straddles the ball its sources inside the ball, compacted (padded to whole blocks
@@ -283,8 +324,8 @@ __global__ void __launch_bounds__(kThreads32, kMinB) k_near32(Near32Args a) {
             // every unit in float-float: t' = t + delta as hi + lo
 #pragma unroll 1
             for (int j = 0; j < 2; ++j) {
-                const float* d0 = dl + 6 * (2 * j);
-                const float* d1 = dl + 6 * (2 * j + 1);
+                const float* d0 = dptr(2 * j);
+                const float* d1 = dptr(2 * j + 1);
                 float2 nTh[3], nTl[3];
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
@@ -313,8 +354,8 @@ __global__ void __launch_bounds__(kThreads32, kMinB) k_near32(Near32Args a) {
             // both lo parts); a pair whose two groups are both far takes the far loop alone
 #pragma unroll 1
             for (int j = 0; j < 2; ++j) {
-                const float* d0 = dl + 6 * (2 * j);
-                const float* d1 = dl + 6 * (2 * j + 1);
+                const float* d0 = dptr(2 * j);
+                const float* d1 = dptr(2 * j + 1);
                 if (!(cls & (j ? kUnitNear1 : kUnitNear0))) {
                     const float2 tx = s_th[0][j][tid], ty = s_th[1][j][tid], tz = s_th[2][j][tid];
                     const float2 nx[1] = {make_float2(-(tx.x + d0[0]), -(tx.y + d1[0]))};
@@ -367,8 +408,8 @@ __global__ void __launch_bounds__(kThreads32, kMinB) k_near32(Near32Args a) {
             float2 nx[2], ny[2], nz[2];
 #pragma unroll
             for (int j = 0; j < 2; ++j) {
-                const float* d0 = dl + 6 * (2 * j);
-                const float* d1 = dl + 6 * (2 * j + 1);
+                const float* d0 = dptr(2 * j);
+                const float* d1 = dptr(2 * j + 1);
                 const float2 tx = s_th[0][j][tid], ty = s_th[1][j][tid], tz = s_th[2][j][tid];
                 nx[j] = make_float2(-(tx.x + d0[0]), -(tx.y + d1[0]));
                 ny[j] = make_float2(-(ty.x + d0[1]), -(ty.y + d1[1]));
@@ -407,11 +448,12 @@ struct Near64Args {
     int* counter;                // next work item
     int max_contrib;
     NearSysTable tab;
-    // two-layer check sums (potential only): the class of each target tile, and the image
-    // vector shifts[shift0 + c n_img + j] with weight img_w[shift0 + c n_img + j] of
-    // (class c, image j).  Null: one image list, weight 1.
-    const int* tgt_cls;
+    // two-layer check sums (potential only): each target's class c (0..n_cls-1) rides in its
+    // pack's fourth component; the image vector of (class c, image j) is
+    // shifts[shift0 + c n_img + j], its weight img_w[shift0 + c n_img + j].  n_cls = 1 and a
+    // null table: one image list, weight 1.
     const float* img_w;
+    int n_cls;
 };
 
 
@@ -424,6 +466,7 @@ __global__ void __launch_bounds__(kThreads64) k_near64(Near64Args a) {
     const int tid = threadIdx.x;
     int64_t item = 0;
     double tx = 0, ty = 0, tz = 0;
+    int tcls = 0;                        // the target's class (two-layer check sums)
     double acc[NQ];
 
     auto flush = [&](int64_t tile, int64_t first_unit) {
@@ -458,6 +501,8 @@ __global__ void __launch_bounds__(kThreads64) k_near64(Near64Args a) {
             if (cur_tile >= 0) flush(cur_tile, cur_first);
             const double4_32a t = a.tgt[tile * kTile64 + tid];
             tx = t.x; ty = t.y; tz = t.z;
+            // a class outside 0..n_cls-1 reads class 0: the index stays inside the tables
+            tcls = (!kGrad && a.n_cls > 1 && t.w >= 0.0 && t.w < (double)a.n_cls) ? (int)t.w : 0;
 #pragma unroll
             for (int qi = 0; qi < NQ; ++qi) acc[qi] = 0.0;
             cur_tile = tile;
@@ -472,12 +517,12 @@ __global__ void __launch_bounds__(kThreads64) k_near64(Near64Args a) {
         }
         // y - x_i - p with the shift folded into the target
         const double* sh = a.shifts + 3 * (S.shift0 + img);
-        double w = 1.0;                  // the unit's weight (potential only); exact in the fma
-        if (!kGrad && a.tgt_cls) {
-            const int e = S.shift0 + a.tgt_cls[tile] * S.n_img + img;
+        double w = 1.0;                  // the target's weight (potential only); exact in the fma
+        if (!kGrad && a.img_w) {
+            const int e = S.shift0 + tcls * S.n_img + img;
             sh = a.shifts + 3 * e;
             w = (double)a.img_w[e];
-            if (w == 0.0) {              // a padding image of the tile's class
+            if (a.n_cls == 1 && w == 0.0) {   // one image list: the unit's weight, uniform
                 ++u;
                 continue;
             }
@@ -561,16 +606,17 @@ __global__ void __launch_bounds__(32 * kReduceWarps) k_near_reduce(const double*
 // ---------------------------------------------------------------------------
 // Host launchers
 // ---------------------------------------------------------------------------
-size_t near32_dyn_smem(int n_img, bool trimmed, bool grad) {
-    const size_t head = ((6 * kTgt32 * (size_t)n_img + n_img + (grad ? 0 : kTgt32 * (size_t)n_img) + 3) / 4) *
-                        sizeof(float4);
+size_t near32_dyn_smem(int n_img, bool trimmed, bool grad, int n_cls) {
+    const size_t head = ((6 * kTgt32 * (size_t)n_cls * n_img + n_img + (grad ? 0 : kTgt32 * (size_t)n_cls * n_img) +
+                          3) / 4) * sizeof(float4);
     return head + (trimmed ? sizeof(float4) * 4 * kNearChunk : 0);   // compacted sources (hi, lo parts)
 }
 
 cudaError_t launch_near32(bool grad, const float4* src_hi, const float4* src_lo, const double* src_org,
                           const float4* tgt_hi, const float4* tgt_lo, const double* tgt_org, const double* shifts,
                           double* partial, const NearPlanLaunch& L, cudaStream_t st, int variant,
-                          const double* src_x, double Rb, bool ff, const int* tgt_cls, const float* img_w) {
+                          const double* src_x, double Rb, bool ff, const int* grp_cls, const float* img_w,
+                          int n_cls, const double* grp_sub) {
     Near32Args a;
     a.status = L.status;
     a.n_status = L.n_status;
@@ -583,10 +629,13 @@ cudaError_t launch_near32(bool grad, const float4* src_hi, const float4* src_lo,
     a.tab = L.tab;
     a.src_x = src_x;
     a.Rb = Rb;
-    if ((tgt_cls != nullptr) != (img_w != nullptr) || (tgt_cls && (grad || Rb > 0.0))) return cudaErrorInvalidValue;
-    a.tgt_cls = tgt_cls;
+    if (n_cls < 1 || (n_cls > 1 && (!grp_cls || !grp_sub || !img_w || grad || Rb > 0.0)) || (img_w && grad))
+        return cudaErrorInvalidValue;
+    a.grp_cls = grp_cls;
+    a.grp_sub = grp_sub;
     a.img_w = img_w;
-    const size_t smem = near32_dyn_smem(L.max_img, Rb > 0.0, grad);
+    a.n_cls = n_cls;
+    const size_t smem = near32_dyn_smem(L.max_img, Rb > 0.0, grad, n_cls);
     if (!L.counter) return cudaErrorInvalidValue;
     const cudaError_t e = cudaMemsetAsync(L.counter, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
@@ -615,12 +664,12 @@ cudaError_t launch_near32(bool grad, const float4* src_hi, const float4* src_lo,
 }
 
 cudaError_t launch_near64(bool grad, const double4_32a* src, const double4_32a* tgt, const double* shifts,
-                          double* partial, const NearPlanLaunch& L, cudaStream_t st, double Rb, const int* tgt_cls,
-                          const float* img_w) {
-    if ((tgt_cls != nullptr) != (img_w != nullptr) || (tgt_cls && (grad || Rb > 0.0))) return cudaErrorInvalidValue;
+                          double* partial, const NearPlanLaunch& L, cudaStream_t st, double Rb, const float* img_w,
+                          int n_cls) {
+    if (n_cls < 1 || (n_cls > 1 && !img_w) || (img_w && (grad || Rb > 0.0))) return cudaErrorInvalidValue;
     Near64Args a;
     a.src = src; a.tgt = tgt; a.shifts = shifts; a.partial = partial; a.Rb = Rb;
-    a.tgt_cls = tgt_cls; a.img_w = img_w;
+    a.img_w = img_w; a.n_cls = n_cls;
     a.U = L.U; a.W = L.W; a.counter = L.counter; a.max_contrib = L.max_contrib; a.tab = L.tab;
     if (!L.counter) return cudaErrorInvalidValue;
     const cudaError_t e = cudaMemsetAsync(L.counter, 0, sizeof(int), st);
@@ -643,7 +692,7 @@ cudaError_t launch_near_reduce(const double* partial, int64_t n_valid, int tile_
 
 int near32_occupancy_ctas(int n_img, int variant, bool trimmed, bool ff) {
     int nb = 0;
-    const size_t smem = near32_dyn_smem(n_img, trimmed, true);
+    const size_t smem = near32_dyn_smem(n_img, trimmed, true, 1);
     constexpr int B0 = kNear32MinBlocks[0], B1 = kNear32MinBlocks[1];
     if (ff && trimmed)
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_near32<true, B0, true, true>, kThreads32, smem);

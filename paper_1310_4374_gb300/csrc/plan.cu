@@ -16,7 +16,7 @@
 #include <numeric>
 #include <vector>
 
-#include "psum_internal.cuh"
+#include "launch.cuh"
 #include "mean.cuh"
 
 namespace psum {
@@ -242,8 +242,9 @@ static void pack_groups32(const std::vector<double>& pts, const std::vector<int>
 // at both points; algorithm "get", step 3).  Class c = 2k + (s < 0) fixes the two layers;
 // images j < Lmax of a class are its upper layer (weight +1), j >= Lmax its lower layer
 // (weight -1), and a class whose layers are smaller than the largest, Lmax, is padded with
-// weight-0 entries.  Float32 plans pack the points in groups of kNearChunk (tiles of 4
-// groups), float64 plans in tiles of kTile64 absolute points: either way one class per group.
+// weight-0 entries.  The points are packed class by class in Morton order, float32 plans in
+// groups of kNearChunk (tiles of 4 groups), float64 plans in tiles of kTile64 absolute points,
+// each point's class in the pack's charge slot (unused for targets).
 static int build_check_layers(Plan& pl, const double d[3]) {
     const bool fp32 = pl.opt.precision != PSUM_FP64;
     const int M = pl.opt.M;
@@ -295,26 +296,18 @@ static int build_check_layers(Plan& pl, const double d[3]) {
     std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
         return cls[x] != cls[y] ? cls[x] < cls[y] : key[x] < key[y];
     });
-    std::vector<int> slot, gcls;
-    for (size_t i = 0; i < order.size();) {
-        const int c = cls[order[i]];
-        size_t e = i;
-        while (e < order.size() && cls[order[e]] == c) ++e;
-        for (size_t t = i; t < e; ++t) slot.push_back(order[t]);
-        while (slot.size() % kNearChunk) slot.push_back(-1);
-        while (gcls.size() < slot.size() / kNearChunk) gcls.push_back(c);
-        i = e;
-    }
-    static_assert(kTile64 == kNearChunk, "a float64 tile is one class group");
+    // one class per target: the points go class by class without padding (a group at a class
+    // boundary holds two), the class in the pack's unused charge slot
+    std::vector<int> slot(order);
     while (slot.size() % (fp32 ? kTile32 : kTile64)) slot.push_back(-1);
-    while (gcls.size() < slot.size() / kNearChunk) gcls.push_back(0);
-    const int ngroups = (int)gcls.size();
-    const int tiles = fp32 ? ngroups / kTgt32 : ngroups;
+    const int tiles = (int)(slot.size() / (fp32 ? kTile32 : kTile64));
     // the automatic choice takes the layers only where they need no more (target tile, image)
-    // units than the points: with few points per class the classes' part-filled groups can
-    // outweigh the third of the images saved (FP32C, M = 200: 2 tiles x 18 against 1 x 27)
+    // units than the points
     if (pl.opt.check_form == PSUM_CHECKS_AUTO && (int64_t)tiles * n_img > (int64_t)pl.n_check_tiles * pl.n_images)
         return PSUM_OK;
+    // float32: the kernel keeps an offset per (image, group, class) in shared memory; blocks
+    // with K = 3 along two axes would need more than it takes without opt-in
+    if (fp32 && near32_dyn_smem(n_img, false, false, kCheckClasses) > kNear32DynSmemMax) return PSUM_OK;
     std::vector<int> pos(M);
     for (size_t i = 0; i < slot.size(); ++i)
         if (slot[i] >= 0) pos[slot[i]] = (int)i;
@@ -322,19 +315,55 @@ static int build_check_layers(Plan& pl, const double d[3]) {
     if (fp32) {
         std::vector<float4> pk;
         std::vector<double> org;
-        pack_groups32(pl.Y, slot, ngroups, pk, org);
+        pack_groups32(pl.Y, slot, (int)(slot.size() / kNearChunk), pk, org);
+        const size_t ng = slot.size() / kNearChunk;
+        std::vector<int> gmask(ng, 0);   // classes present in each group
+        for (size_t i = 0; i < slot.size(); ++i) {
+            const int c = slot[i] >= 0 ? cls[slot[i]] : 0;
+            pk[2 * i + 1].z = (float)c;
+            pk[2 * i + 1].w = (float)c;
+            gmask[i / kNearChunk] |= 1 << c;     // padding slots read class 0
+        }
+        // per (group, class): centre and radius of the class's points in the group, for the
+        // near-unit test (a group at a class boundary spans two caps of the sphere)
+        std::vector<double> sub(ng * kCheckClasses * 4, 0.0);
+        for (size_t g = 0; g < ng; ++g)
+            for (int c = 0; c < kCheckClasses; ++c) {
+                double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+                for (size_t i = g * kNearChunk; i < (g + 1) * kNearChunk; ++i)
+                    if (slot[i] >= 0 && cls[slot[i]] == c)
+                        for (int k = 0; k < 3; ++k) {
+                            lo[k] = std::min(lo[k], pl.Y[3 * (size_t)slot[i] + k]);
+                            hi[k] = std::max(hi[k], pl.Y[3 * (size_t)slot[i] + k]);
+                        }
+                double* o = &sub[4 * (g * kCheckClasses + c)];
+                if (!(lo[0] <= hi[0])) {      // class absent: the group's own sphere
+                    for (int k = 0; k < 4; ++k) o[k] = org[4 * g + k];
+                    continue;
+                }
+                double r2 = 0.0;
+                for (int k = 0; k < 3; ++k) o[k] = 0.5 * (lo[k] + hi[k]);
+                for (size_t i = g * kNearChunk; i < (g + 1) * kNearChunk; ++i)
+                    if (slot[i] >= 0 && cls[slot[i]] == c) {
+                        const double* y = &pl.Y[3 * (size_t)slot[i]];
+                        r2 = std::max(r2, (y[0] - o[0]) * (y[0] - o[0]) + (y[1] - o[1]) * (y[1] - o[1]) +
+                                              (y[2] - o[2]) * (y[2] - o[2]));
+                    }
+                o[3] = std::sqrt(r2);
+            }
         if ((s1 = upload((float4**)&pl.d_lc_tgt, pk.data(), pk.size()))) return s1;
         if ((s1 = upload(&pl.d_lc_org, org.data(), org.size()))) return s1;
+        if ((s1 = upload(&pl.d_lc_gmask, gmask.data(), gmask.size()))) return s1;
+        if ((s1 = upload(&pl.d_lc_sub, sub.data(), sub.size()))) return s1;
     } else {
         std::vector<double4_32a> pk(slot.size(), make_double4_32a(1e3, 1e3, 1e3, 0.0));
         for (size_t i = 0; i < slot.size(); ++i)
             if (slot[i] >= 0)
                 pk[i] = make_double4_32a(pl.Y[3 * (size_t)slot[i]], pl.Y[3 * (size_t)slot[i] + 1],
-                                         pl.Y[3 * (size_t)slot[i] + 2], 0.0);
+                                         pl.Y[3 * (size_t)slot[i] + 2], (double)cls[slot[i]]);
         if ((s1 = upload((double4_32a**)&pl.d_lc_tgt, pk.data(), pk.size()))) return s1;
     }
     if ((s1 = upload(&pl.d_lc_pos, pos.data(), pos.size()))) return s1;
-    if ((s1 = upload(&pl.d_lc_cls, gcls.data(), gcls.size()))) return s1;
     if ((s1 = upload(&pl.d_lc_shifts, sh.data(), sh.size()))) return s1;
     if ((s1 = upload(&pl.d_lc_w, w.data(), w.size()))) return s1;
     pl.lc_tiles = tiles;
@@ -518,8 +547,9 @@ void free_plan_device(Plan& pl) {
     cudaFree(pl.d_check_org);
     cudaFree(pl.d_lc_tgt);
     cudaFree(pl.d_lc_org);
+    cudaFree(pl.d_lc_gmask);
+    cudaFree(pl.d_lc_sub);
     cudaFree(pl.d_lc_pos);
-    cudaFree(pl.d_lc_cls);
     cudaFree(pl.d_lc_shifts);
     cudaFree(pl.d_lc_w);
     cudaFree(pl.d_pinv);

@@ -229,13 +229,14 @@ struct Plan {
     // the right-hand side as two image layers at the M check points (PSUM_CHECKS_LAYERS):
     // f_l = sum over the layer i_k = s(K_k + 1) minus the layer i_k = -s K_k, where the
     // partner is y~_l = y_l - s d_k e_k.  Points of one class c = 2k + (s < 0) share their
-    // image list, so they are packed class by class in whole groups of kGroup points.
+    // image list; each packed point carries its class in the (unused) charge slot.
     int lc_tiles = 0;               // target tiles (0: the plan evaluates the 2M points)
     int lc_img = 0;                 // images per class: 2 x the largest layer (zero-weight padding)
-    void* d_lc_tgt = nullptr;       // packed points: float32 hi parts then lo parts, or double4_32a
+    void* d_lc_tgt = nullptr;       // packed points (class in the charge slot): float32 hi parts then lo parts, or double4_32a
     double* d_lc_org = nullptr;     // float32 packing: 4 per group, origin and radius
+    int* d_lc_gmask = nullptr;      // float32 packing: the classes present in each group (bit mask)
+    double* d_lc_sub = nullptr;     // float32 packing: [group][6][4] centre and radius of each class's points
     int* d_lc_pos = nullptr;        // M: packed position of y_l
-    int* d_lc_cls = nullptr;        // class of each group
     double* d_lc_shifts = nullptr;  // [6][lc_img][3] image vectors of each class's layers
     float* d_lc_w = nullptr;        // [6][lc_img] weights: +1 (upper layer), -1 (lower), 0 (padding)
 

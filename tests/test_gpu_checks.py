@@ -74,18 +74,24 @@ def test_layers_against_oracle_and_points(name, make, kw, precision):
         e_phi = O.relative_l2(phi, ref["phi"])
         e_g = O.relative_l2(g, ref["grad"])
         assert e_phi < tol and e_g < tol, f"{what}: eps2 phi {e_phi:.3e}, grad {e_g:.3e}"
+    if kw.get("basis") == "rbf":
+        # the equivalent sources of Eq. 5 are an ill-conditioned basis: the fit fixes the field
+        # to the method's accuracy, not each coefficient; compare the two forms' fields instead
+        assert O.relative_l2(phi_l, phi_p) < 2 * tol and O.relative_l2(g_l, g_p) < 2 * tol
+        return
     e_C = np.linalg.norm(C_l - C_p) / np.linalg.norm(C_p)
     assert e_C < C_TOL[precision], f"coefficients of the two forms differ by {e_C:.3e}"
 
 
 def test_automatic_check_form():
-    # the layers where they apply and need no more (tile, image) units than the 2M points
+    # the layers where they apply and need no more (tile, image) units than the 2M points, and
+    # (float32) where the per-class offsets fit the kernel's shared memory
     s = W.uniform_gauss(N=300, d=(1.0, 1.5, 2.0), p=8, M=200, seed=1)
-    expect = [({"precision": "fp32c", "M": 200}, "points"),     # 2 tiles x 18 against 1 x 27
-              ({"precision": "fp32c", "M": 400}, "layers"),     # 2 x 18 against 2 x 27
+    expect = [({"precision": "fp32c", "M": 200}, "layers"),     # 1 tile x 18 against 1 x 27
               ({"precision": "ff", "M": 400}, "layers"),
-              ({"precision": "fp64", "M": 200}, "layers"),      # tiles of 128: 6 x 18 against 4 x 27
-              ({"precision": "fp32c", "M": 200, "checks": "layers"}, "layers"),
+              ({"precision": "fp64", "M": 200}, "layers"),      # tiles of 128: 2 x 18 against 4 x 27
+              ({"precision": "fp32c", "M": 200, "K": (3, 3, 1)}, "points"),   # 98 layer images
+              ({"precision": "fp64", "M": 200, "K": (3, 3, 1)}, "layers"),
               ({"precision": "fp32c", "M": 400, "checks": "points"}, "points"),
               ({"precision": "fp64", "M": 200, "checks": "points"}, "points"),
               ({"precision": "fp32c", "M": 800, "lam": 1.5}, "points"), ({"precision": "fp64", "M": 200, "lam": 1.5}, "points")]
