@@ -4,7 +4,9 @@
 //   grad phi_near(y) = sum_{p} sum_i q_i (x_i + p - y) / |y - x_i - p|^3
 //
 // at the N charges (potential and gradient), at the 2M check points (potential
-// only) or at separate evaluation points.  The kernels share one work decomposition:
+// only), at the M check points as the partner difference of two image layers (potential
+// only; each target's class selects its layer images and their weights +1, -1 or 0), or at
+// separate evaluation points.  The kernels share one work decomposition:
 //
 //   * the work unit is (target tile, source chunk, image); the unit space is cut
 //     into W equal contiguous work items (fixed, so every tile's partial-sum slots
