@@ -223,7 +223,9 @@ int psum_eval_host(psum_plan_t plan, int64_t N, const double *x, const double *q
  * The first call on a device looks up the array's device address (cudaGetSymbolAddress);
  * make that first call before any stream capture.  All calls share the one array:
  * calls whose work overlaps on the GPU (other streams, other plans, other threads)
- * race and corrupt each other's results -- serialise them, e.g. on one stream. */
+ * race and corrupt each other's results -- serialise them, e.g. on one stream.  Like
+ * psum_eval, a call replaces the plan's coefficients (psum_get_coeffs, and the C that
+ * psum_energy_backward uses). */
 int psum_eval_noalloc(psum_plan_t plan, int64_t N, const double *x, const double *q,
                       double *phi, double *grad, void *stream);
 
@@ -240,13 +242,33 @@ int psum_energy(psum_plan_t plan, int64_t N, const double *q, const double *phi,
  *   psi(x)    = sum_l u_l [G(y~_l - x) - G(y_l - x)]   (G: the near-block image kernel),
  *   dEdq[i]   = gE (phi_i - phi_far(x_i)/2 + psi(x_i)/2),
  *   dEdx[3i+k]= gE q_i (grad_i - grad phi_far(x_i)/2 + grad psi(x_i)/2)_k.
- * x, q, phi, grad (device) must be the inputs and outputs of the LAST psum_eval of this
- * plan (its coefficients C are used).  gE is a device scalar multiplying the result (the
+ * x, q, phi, grad (device) must be the inputs and outputs of the LAST evaluation of this
+ * plan -- psum_eval, psum_eval_host, psum_eval_graph or psum_eval_noalloc, each of which
+ * replaces the plan's coefficients C, which are used here (psum_energy_backward_c takes
+ * them as an argument instead).  gE is a device scalar multiplying the result (the
  * upstream gradient), or NULL for 1.  dEdq or dEdx may be NULL (not both).  The 27 N^2
  * pair sum is not repeated: psi is a sum over the 2M check points. */
 int psum_energy_backward(psum_plan_t plan, int64_t N, const double *x, const double *q,
                          const double *phi, const double *grad, const double *gE,
                          double *dEdq, double *dEdx, void *stream);
+
+/* Queue a copy of the P coefficients C_1..C_P of the plan's last evaluation (stacked by
+ * Eq. 1.8) into the DEVICE array C (caller-owned, P doubles, on the plan's device) on
+ * `stream`; no synchronisation.  Made right after an evaluation, it keeps that evaluation's
+ * far-field expansion (Eq. 1.8 with the fitted C of Eq. 10) for psum_energy_backward_c.
+ * PSUM_ERR_ARG for a NULL plan or array. */
+int psum_coeffs_device(psum_plan_t plan, double *C, void *stream);
+
+/* psum_energy_backward with the coefficients of the forward evaluation passed in: C (device,
+ * P doubles, as psum_coeffs_device writes them) replaces the plan's last coefficients in the
+ * moments w_t and in phi_far and grad phi_far at the charges, so the derivatives belong to
+ * the evaluation that produced (x, q, phi, grad, C) however many evaluations of the plan
+ * came after it (as in an autograd graph with several forwards through one plan).  The
+ * same adjoint formulas, arguments and errors as psum_energy_backward, plus PSUM_ERR_ARG for
+ * a NULL C. */
+int psum_energy_backward_c(psum_plan_t plan, int64_t N, const double *x, const double *q,
+                           const double *phi, const double *grad, const double *C, const double *gE,
+                           double *dEdq, double *dEdx, void *stream);
 
 /* Copy the P coefficients C_1..C_P of the last evaluation to host memory
  * (stacked by Eq. 1.8; C[0] is the constant C_1).  Waits for `stream`. */

@@ -109,6 +109,8 @@ def load(build_if_needed: bool = True):
     lib.psum_launch_count.argtypes = [_vp, ctypes.POINTER(ctypes.c_int64)]
     lib.psum_energy.argtypes = [_vp, ctypes.c_int64, _vp, _vp, _vp, _vp]
     lib.psum_energy_backward.argtypes = [_vp, ctypes.c_int64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
+    lib.psum_energy_backward_c.argtypes = [_vp, ctypes.c_int64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
+    lib.psum_coeffs_device.argtypes = [_vp, _vp, _vp]
     lib.psum_batch_create.argtypes = [ctypes.POINTER(_vp), ctypes.c_int, ctypes.POINTER(ctypes.c_int64),
                                       ctypes.POINTER(_vp)]
     lib.psum_batch_eval.argtypes = [_vp, _vp, _vp, _vp, _vp, ctypes.c_int, _vp]
@@ -124,7 +126,8 @@ def load(build_if_needed: bool = True):
     for name in ("psum_plan_create", "psum_plan_create_ex", "psum_eval", "psum_eval_host", "psum_eval_noalloc",
                  "psum_sync",
                  "psum_get_coeffs", "psum_plan_info", "psum_pair_kernel", "psum_check_form", "psum_profile", "psum_last_timings", "psum_launch_count",
-                 "psum_energy", "psum_energy_backward", "psum_eval_points", "psum_debug_inject_timeout", "psum_eval_graph", "psum_batch_create", "psum_batch_eval",
+                 "psum_energy", "psum_energy_backward", "psum_energy_backward_c", "psum_coeffs_device",
+                 "psum_eval_points", "psum_debug_inject_timeout", "psum_eval_graph", "psum_batch_create", "psum_batch_eval",
                  "psum_batch_sync", "psum_batch_get_coeffs", "psum_batch_get_info"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
@@ -320,6 +323,22 @@ def psum_energy_backward(plan, x, q, phi, grad, gE=None, dEdq=None, dEdx=None, s
     _check(load().psum_energy_backward(plan, int(q.numel()), x.data_ptr(), q.data_ptr(), phi.data_ptr(),
                                        grad.data_ptr(), ptr(gE), ptr(dEdq), ptr(dEdx), _stream_ptr(stream)),
            "psum_energy_backward")
+
+
+def psum_coeffs_device(plan, C, stream=None):
+    """Queue a copy of the last evaluation's P coefficients into the device tensor C."""
+    if not (C.is_cuda and C.is_contiguous() and C.dtype.itemsize == 8):
+        raise ValueError("psum_coeffs_device takes a contiguous float64 CUDA tensor")
+    _check(load().psum_coeffs_device(plan, C.data_ptr(), _stream_ptr(stream)), "psum_coeffs_device")
+
+
+def psum_energy_backward_c(plan, x, q, phi, grad, C, gE=None, dEdq=None, dEdx=None, stream=None):
+    """psum_energy_backward with the forward evaluation's coefficients C (device tensor)."""
+    def ptr(t):
+        return t.data_ptr() if t is not None else None
+    _check(load().psum_energy_backward_c(plan, int(q.numel()), x.data_ptr(), q.data_ptr(), phi.data_ptr(),
+                                         grad.data_ptr(), C.data_ptr(), ptr(gE), ptr(dEdq), ptr(dEdx),
+                                         _stream_ptr(stream)), "psum_energy_backward_c")
 
 
 def psum_launch_count(plan) -> int:

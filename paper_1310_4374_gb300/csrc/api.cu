@@ -413,8 +413,12 @@ int eval_points_device(psum_plan_s* h, int64_t N, const double* x, const double*
     return queue_forward(h, N, x, q, phi, grad, L, st, T, y);
 }
 
+// The energy derivatives (the exact adjoint of the discrete method: moments w = sum q R^(x/R0),
+// u = (A^+)^T w, psi from the check points carrying -u and u) with the far-field coefficients C
+// of the evaluation that produced phi and grad.
 int backward_device(psum_plan_s* h, int64_t N, const double* x, const double* q, const double* phi,
-                    const double* grad, const double* gE, double* dEdq, double* dEdx, cudaStream_t st) {
+                    const double* grad, const double* C, const double* gE, double* dEdq, double* dEdx,
+                    cudaStream_t st) {
     Plan& pl = h->pl;
     const psum_opts& o = pl.opt;
     Layout L;
@@ -437,7 +441,7 @@ int backward_device(psum_plan_s* h, int64_t N, const double* x, const double* q,
         h->launches += 1;
     }
     // moments w and the far field at the charges; u = (A^+)^T w
-    TRY(launch_moments(x, q, N, pl.d_C, o.p, 1.0 / pl.R0, pl.d_shtab64, L.far_phi, L.far_grad, L.w_part,
+    TRY(launch_moments(x, q, N, C, o.p, 1.0 / pl.R0, pl.d_shtab64, L.far_phi, L.far_grad, L.w_part,
                        L.nblk_mom, L.w, st));
     TRY(launch_adjoint(pl.d_pinv, P - 1, M, L.w, L.u, st));
     h->launches += 3;
@@ -684,7 +688,25 @@ int psum_energy_backward(psum_plan_t h, int64_t N, const double* x, const double
     if (h->pl.Rb > 0.0) return PSUM_ERR_ARG;   // the adjoint assumes the untrimmed near block
     if (h->pl.opt.basis != PSUM_BASIS_SPHERICAL) return PSUM_ERR_ARG;   // and the solid-harmonic moments
     DeviceGuard g(h->pl.device);
-    return backward_device(h, N, x, q, phi, grad, gE, dEdq, dEdx, (cudaStream_t)stream);
+    return backward_device(h, N, x, q, phi, grad, h->pl.d_C, gE, dEdq, dEdx, (cudaStream_t)stream);
+}
+
+int psum_coeffs_device(psum_plan_t h, double* C, void* stream) {
+    if (!h || !C) return PSUM_ERR_ARG;
+    DeviceGuard g(h->pl.device);
+    TRY(cudaMemcpyAsync(C, h->pl.d_C, sizeof(double) * h->pl.P, cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+    return PSUM_OK;
+}
+
+int psum_energy_backward_c(psum_plan_t h, int64_t N, const double* x, const double* q, const double* phi,
+                           const double* grad, const double* C, const double* gE, double* dEdq, double* dEdx,
+                           void* stream) {
+    if (!h || N < 1 || N > (int64_t)1 << 30 || !x || !q || !phi || !grad || !C || (!dEdq && !dEdx))
+        return PSUM_ERR_ARG;
+    if (h->pl.Rb > 0.0) return PSUM_ERR_ARG;
+    if (h->pl.opt.basis != PSUM_BASIS_SPHERICAL) return PSUM_ERR_ARG;
+    DeviceGuard g(h->pl.device);
+    return backward_device(h, N, x, q, phi, grad, C, gE, dEdq, dEdx, (cudaStream_t)stream);
 }
 
 int psum_get_coeffs(psum_plan_t h, double* C, void* stream) {

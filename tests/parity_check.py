@@ -1,0 +1,50 @@
+"""Agreement of a GPU result with its reference, norm-wise and element by element.
+
+eps2 is the error metric of Eq. st2 (Sec. 4.1): the RMS of the difference over the RMS
+of the reference.  Beside it every comparison bounds the largest single difference,
+max_i |a_i - ref_i| / rms(ref), so that a few wrong targets cannot hide in the norm (at
+N targets a norm dilutes one wrong value by 1/sqrt(N)).  The element-wise bound is
+MAX_FACTOR times the eps2 tolerance: for errors that are sums of many independent
+roundings the largest of N values sits about sqrt(2 ln N) (under 5 for N <= 3e5) rms
+widths out, so at an eps2 right at its tolerance the largest value still has a margin of
+two.
+"""
+import numpy as np
+
+MAX_FACTOR = 10.0
+
+
+def errors(a, ref, scale=None):
+    """(eps2, max |a - ref| / rms(ref)); `scale` replaces rms(ref) where given."""
+    a = np.asarray(a, dtype=np.float64).reshape(-1)
+    ref = np.asarray(ref, dtype=np.float64).reshape(-1)
+    rms = float(np.sqrt(np.mean(ref ** 2))) if scale is None else float(scale)
+    d = a - ref
+    return float(np.sqrt(np.mean(d ** 2)) / rms), float(np.max(np.abs(d)) / rms)
+
+
+def assert_close(a, ref, tol, what="", max_tol=None, scale=None):
+    e2, emax = errors(a, ref, scale)
+    mt = MAX_FACTOR * tol if max_tol is None else max_tol
+    assert e2 < tol and emax < mt, (f"{what}: eps2 {e2:.3e} (tol {tol:.1e}), "
+                                    f"max/rms {emax:.3e} (tol {mt:.1e})")
+    return e2, emax
+
+
+def full_size_sample(x, d, n=4096, cluster=1100, seed=0):
+    """Sorted indices of n charges for a sampled full-size comparison: every charge of three
+    compact clusters -- the `cluster` charges nearest (in box-normalised max norm) to the
+    lower corner and to the upper corner of the box, where the spatial (Morton) order of the
+    charges starts and ends, and to its centre -- so that whole target tiles at both ends of
+    the order and in the middle are compared, plus charges drawn at random up to n."""
+    x = np.asarray(x, dtype=np.float64)
+    u = x / np.asarray(d, dtype=np.float64)              # in [-1/2, 1/2)
+    picks = set()
+    for c in (-0.5, 0.5, 0.0):
+        dist = np.max(np.abs(u - c), axis=1)
+        picks.update(np.argsort(dist, kind="stable")[:cluster].tolist())
+    rng = np.random.default_rng(seed)
+    rest = np.setdiff1d(np.arange(len(x)), np.fromiter(picks, dtype=np.int64))
+    need = max(0, min(n, len(x)) - len(picks))
+    picks.update(rng.choice(rest, size=need, replace=False).tolist())
+    return np.sort(np.fromiter(picks, dtype=np.int64))

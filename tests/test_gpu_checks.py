@@ -10,6 +10,7 @@ import numpy as np
 import pytest
 
 from oracle import psum_oracle as O
+from parity_check import assert_close
 from paper_1310_4374_gb300 import binding as B
 from paper_1310_4374_gb300 import workloads as W
 
@@ -71,13 +72,13 @@ def test_layers_against_oracle_and_points(name, make, kw, precision):
     assert (form_l, form_p) == ("layers", "points")
     tol = TOL[precision]
     for phi, g, what in ((phi_l, g_l, "layers"), (phi_p, g_p, "points")):
-        e_phi = O.relative_l2(phi, ref["phi"])
-        e_g = O.relative_l2(g, ref["grad"])
-        assert e_phi < tol and e_g < tol, f"{what}: eps2 phi {e_phi:.3e}, grad {e_g:.3e}"
+        assert_close(phi, ref["phi"], tol, f"{what} phi")
+        assert_close(g, ref["grad"], tol, f"{what} grad")
     if kw.get("basis") == "rbf":
         # the equivalent sources of Eq. 5 are an ill-conditioned basis: the fit fixes the field
         # to the method's accuracy, not each coefficient; compare the two forms' fields instead
-        assert O.relative_l2(phi_l, phi_p) < 2 * tol and O.relative_l2(g_l, g_p) < 2 * tol
+        assert_close(phi_l, phi_p, 2 * tol, "phi layers vs points")
+        assert_close(g_l, g_p, 2 * tol, "grad layers vs points")
         return
     e_C = np.linalg.norm(C_l - C_p) / np.linalg.norm(C_p)
     assert e_C < C_TOL[precision], f"coefficients of the two forms differ by {e_C:.3e}"
@@ -142,15 +143,15 @@ def test_batch_with_mixed_check_forms(precision):
         for b, (s, form) in enumerate(zip(systems, forms)):
             sl = slice(pb.offsets[b], pb.offsets[b + 1])
             ref = O.periodic_sum(s.x, s.q, s.d, s.p, s.M, K=s.K)
-            e_phi, e_g = O.relative_l2(phi[sl], ref["phi"]), O.relative_l2(g[sl], ref["grad"])
-            assert e_phi < TOL[precision] and e_g < TOL[precision], (b, form, e_phi, e_g)
+            assert_close(phi[sl], ref["phi"], TOL[precision], (b, form, "phi"))
+            assert_close(g[sl], ref["grad"], TOL[precision], (b, form, "grad"))
             pc = B.PeriodicCoulomb(s.d, s.p, s.M, precision=precision, K=s.K, checks=form)
             try:
                 p1, g1 = pc(_dev(s.x), _dev(s.q))
             finally:
                 pc.close()
             single_tol = 1e-7 if precision == "fp32c" else 1e-12
-            assert O.relative_l2(phi[sl], p1.cpu().numpy()) < single_tol, (b, form)
-            assert O.relative_l2(g[sl], g1.cpu().numpy()) < single_tol, (b, form)
+            assert_close(phi[sl], p1.cpu().numpy(), single_tol, (b, form))
+            assert_close(g[sl], g1.cpu().numpy(), single_tol, (b, form))
     finally:
         pb.close()

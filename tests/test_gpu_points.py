@@ -4,6 +4,7 @@ import numpy as np
 import pytest
 
 from oracle import psum_oracle as O
+from parity_check import assert_close
 from paper_1310_4374_gb300 import binding as B
 from paper_1310_4374_gb300 import workloads as W
 
@@ -40,13 +41,13 @@ def test_points_match_oracle(name, make, T, precision):
     y = _points(T, s.d, 17)
     phi, g = _at(s, y, precision)
     ref = O.Plan(s.d, s.p, s.M).evaluate(s.x, s.q, targets=y, parts=True)
-    assert O.relative_l2(phi, ref["phi"]) < TOL[precision]
+    assert_close(phi, ref["phi"], TOL[precision])
     # Float-float offsets keep about 2^-48 of the group-relative coordinates (groups of 128
     # points span ~0.4 of the box at 3000 charges), not of the offset: random points that
     # fall very close to a charge see field terms with a relative error near 1e-12, which
     # leaves the field's epsilon_2 at about 1.1e-10 (measured) where float64 keeps 1e-12.
     gtol = 3e-10 if precision == "ff" else TOL[precision]
-    assert O.relative_l2(g, ref["grad"]) < gtol
+    assert_close(g, ref["grad"], gtol)
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32c"])
@@ -60,8 +61,8 @@ def test_points_at_the_charges_equal_psum_eval(precision):
     finally:
         pc.close()
     tol = 1e-13 if precision == "fp64" else 1e-7
-    assert O.relative_l2(phi2.cpu().numpy(), phi.cpu().numpy()) < tol
-    assert O.relative_l2(g2.cpu().numpy(), g.cpu().numpy()) < tol
+    assert_close(phi2.cpu().numpy(), phi.cpu().numpy(), tol)
+    assert_close(g2.cpu().numpy(), g.cpu().numpy(), tol)
 
 
 def test_points_with_trimming_rbf_and_gauss_grid():
@@ -76,8 +77,8 @@ def test_points_with_trimming_rbf_and_gauss_grid():
         finally:
             pc.close()
         ref = O.Plan(s.d, s.p, M, **okw).evaluate(s.x, s.q, targets=y, parts=True)
-        assert O.relative_l2(phi.cpu().numpy(), ref["phi"]) < 1e-10, kw
-        assert O.relative_l2(g.cpu().numpy(), ref["grad"]) < 1e-10, kw
+        assert_close(phi.cpu().numpy(), ref["phi"], 1e-10, kw)
+        assert_close(g.cpu().numpy(), ref["grad"], 1e-10, kw)
 
 
 @pytest.mark.parametrize("d", [(1.0, 1.0, 1.0), (1.0, 1.0, 2.0)])

@@ -7,11 +7,11 @@ psum_eval's within the parity tolerances, call after call on the shared array.
 This file is collected last so that a run stopping at the first failure has run every
 other test before it.
 """
-import numpy as np
 import pytest
 
 from paper_1310_4374_gb300 import binding as B
 from paper_1310_4374_gb300 import workloads as W
+from parity_check import assert_close
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -19,10 +19,8 @@ pytestmark = pytest.mark.gpu
 TOL = {"fp64": 1e-10, "fp32c": 1e-6}
 
 
-def _rel(a, b):
-    a = a.detach().cpu().numpy().reshape(-1)
-    b = b.detach().cpu().numpy().reshape(-1)
-    return float(np.sqrt(np.mean((a - b) ** 2)) / np.sqrt(np.mean(b ** 2)))
+def _np(t):
+    return t.detach().cpu().numpy()
 
 
 @pytest.mark.parametrize("precision", ["fp32c", "fp64"])
@@ -39,8 +37,28 @@ def test_noalloc_matches_psum_eval_on_two_calls(precision):
             g = torch.full_like(ref_g, float("nan"))
             B.psum_eval_noalloc(pc.plan, x, q, phi, g, check=True)
             assert torch.isfinite(phi).all() and torch.isfinite(g).all()
-            assert _rel(phi, ref_phi) < TOL[precision]
-            assert _rel(g, ref_g) < TOL[precision]
+            assert_close(_np(phi), _np(ref_phi), TOL[precision], (s.N, "phi"))
+            assert_close(_np(g), _np(ref_g), TOL[precision], (s.N, "grad"))
+    finally:
+        pc.close()
+
+
+@pytest.mark.parametrize("precision", ["fp32c", "fp64"])
+def test_noalloc_holds_its_stated_limit(precision):
+    # the header promises N = 32768 charges for p = 16 and M = 800 in either precision: the
+    # scratch of that evaluation fits the fixed array (else PSUM_ERR_ARG) and the results
+    # match psum_eval
+    s = W.uniform_gauss(N=32768, d=(1.0, 1.5, 2.0), p=16, M=800, seed=11)
+    pc = B.PeriodicCoulomb(s.d, s.p, s.M, precision=precision)
+    try:
+        x = torch.as_tensor(s.x, dtype=torch.float64, device="cuda")
+        q = torch.as_tensor(s.q, dtype=torch.float64, device="cuda")
+        ref_phi, ref_g = pc(x, q)
+        phi = torch.full_like(ref_phi, float("nan"))
+        g = torch.full_like(ref_g, float("nan"))
+        B.psum_eval_noalloc(pc.plan, x, q, phi, g, check=True)
+        assert_close(_np(phi), _np(ref_phi), TOL[precision], "phi")
+        assert_close(_np(g), _np(ref_g), TOL[precision], "grad")
     finally:
         pc.close()
 
