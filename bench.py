@@ -67,6 +67,9 @@ def parse():
     ap.add_argument("--n", type=int, default=N_MAIN, help="charges (smaller cases are for profiling only)")
     ap.add_argument("--pairs", default="auto", choices=["auto", "one-sided", "symmetric"],
                     help="pair kernel of the charge sums (auto: symmetric from 12 tiles of 512 charges)")
+    ap.add_argument("--terms", default="fast", choices=["fast", "refined"],
+                    help="float32 pair terms of the main workload (refined: float-float offsets and 1/r fused "
+                         "into the sums, for strongly cancelling systems)")
     ap.add_argument("--checks", default="auto", choices=["auto", "points", "layers"],
                     help="form of the check-point sums (auto: the two image layers at the M points)")
     return ap.parse_args()
@@ -167,7 +170,7 @@ def near_code_hash():
     return hashlib.sha256(" ".join(src.split()).encode()).hexdigest()[:16]
 
 
-def near_kernel_traffic(n_points, kernel, image_groups):
+def near_kernel_traffic(n_points, kernel, image_groups, terms="fast"):
     """DRAM bytes per launch of the charge near-field kernel from the committed ncu
     summary of a smaller case: the read of the packed sources (which stay in L2) scales
     with the number of points; the write of the partial sums scales with the number of
@@ -178,7 +181,8 @@ def near_kernel_traffic(n_points, kernel, image_groups):
     try:
         with open(path) as f:
             rec = json.load(f)
-        if rec.get("near_code_sha256_16") != near_code_hash() or rec.get("pair_kernel") != kernel:
+        if (rec.get("near_code_sha256_16") != near_code_hash() or rec.get("pair_kernel") != kernel
+                or rec.get("terms", "fast") != terms):
             return None
         read = rec["dram_read_bytes"] * n_points / rec["n_points"]
         if kernel == "symmetric":
@@ -215,7 +219,8 @@ def run_psum(args):
     # every rank evaluates its own replica of the system (weak scaling, no exchange)
     s = W.uniform_gauss(N=args.n, d=D_MAIN, p=P_MAIN, M=M_MAIN, seed=SEED_MAIN + rank)
     pairs_step = 27 * s.N * (s.N + 2 * s.M)
-    pc = B.PeriodicCoulomb(s.d, s.p, s.M, precision="fp32c", pairs=args.pairs, checks=args.checks)
+    pc = B.PeriodicCoulomb(s.d, s.p, s.M, precision="fp32c", pairs=args.pairs, checks=args.checks,
+                           terms=args.terms)
     pair_kernel, image_groups = B.psum_pair_kernel(pc.plan, s.N)
     check_form = B.psum_check_form(pc.plan)
     # interactions the kernels evaluate: the charge sums, and the check sums as 27 images at
@@ -276,7 +281,7 @@ def run_psum(args):
     pair_rate = near_pairs / (near_ms * 1e-3)
     # achieved = algorithmic operations (14 per pair) x pairs of one launch / its duration
     achieved = FP32_OPS_PAIR_ALG * pair_rate
-    traffic = near_kernel_traffic(s.N, pair_kernel, image_groups)
+    traffic = near_kernel_traffic(s.N, pair_kernel, image_groups, args.terms)
     roofline = {"bound": "alu", "kernel": "k_near32s (symmetric pairs)" if sym else "k_near32<grad>",
                 "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
                 "unit": "T FP32-pipe ops/s", "frac": achieved / peak_ops, "traffic": traffic,
@@ -309,6 +314,7 @@ def run_psum(args):
                                                   "the partner's face minus the opposite layer, 18 images at "
                                                   "the M points)" if check_form == "layers" else ""),
                       "pairs_evaluated_per_step": pairs_evaluated,
+                      "terms": args.terms,
                       "precision": "fp32c: f32 pair arithmetic on group-relative coordinates, two-sum "
                                    "compensated accumulation; f64 sort keys, fit, mean and far field",
                       "l2": "flushed before every timed step (256 MiB write, outside the events)",
@@ -492,49 +498,57 @@ def batch_leg(args):
 
 def backward_leg(args):
     """Energy, forces and dE/dq of 100k tight dipoles (200k charges) in the (1, 1, 2) box,
-    p = 16, M = 800, fp32c: forward psum_eval + psum_energy + psum_energy_backward."""
+    p = 16, M = 800, fp32c: forward psum_eval + psum_energy + psum_energy_backward.  The
+    potential of this system cancels strongly (about 20x below the root-sum-square of its
+    terms), so it runs the refined float32 terms that meet the 1e-6 bound; the fast terms'
+    forward is timed beside it."""
     import torch
 
     from paper_1310_4374_gb300 import binding as B
     from paper_1310_4374_gb300 import workloads as W
 
     s = W.config(5)
-    pc = B.PeriodicCoulomb(s.d, s.p, s.M, precision="fp32c")
-    try:
-        x = torch.as_tensor(s.x, dtype=torch.float64, device="cuda")
-        q = torch.as_tensor(s.q, dtype=torch.float64, device="cuda")
-        phi = torch.empty_like(q)
-        grad = torch.empty_like(x)
-        E = torch.empty(1, dtype=torch.float64, device="cuda")
-        dEdq = torch.empty_like(q)
-        dEdx = torch.empty_like(x)
+    x = torch.as_tensor(s.x, dtype=torch.float64, device="cuda")
+    q = torch.as_tensor(s.q, dtype=torch.float64, device="cuda")
+    phi = torch.empty_like(q)
+    grad = torch.empty_like(x)
+    E = torch.empty(1, dtype=torch.float64, device="cuda")
+    dEdq = torch.empty_like(q)
+    dEdx = torch.empty_like(x)
+    res = {}
+    for terms in ("refined", "fast"):
+        pc = B.PeriodicCoulomb(s.d, s.p, s.M, precision="fp32c", terms=terms)
+        try:
+            def step():
+                B.psum_eval(pc.plan, x, q, phi, grad)
+                B.psum_energy(pc.plan, q, phi, E)
+                B.psum_energy_backward(pc.plan, x, q, phi, grad, None, dEdq, dEdx)
 
-        def step():
+            step()
+            torch.cuda.synchronize()
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            ev[0].record()
             B.psum_eval(pc.plan, x, q, phi, grad)
             B.psum_energy(pc.plan, q, phi, E)
+            ev[1].record()
             B.psum_energy_backward(pc.plan, x, q, phi, grad, None, dEdq, dEdx)
-
-        step()
-        torch.cuda.synchronize()
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
-        ev[0].record()
-        B.psum_eval(pc.plan, x, q, phi, grad)
-        B.psum_energy(pc.plan, q, phi, E)
-        ev[1].record()
-        B.psum_energy_backward(pc.plan, x, q, phi, grad, None, dEdq, dEdx)
-        ev[2].record()
-        torch.cuda.synchronize()
-        st = B.psum_sync(pc.plan)
-        if st != B.PSUM_OK:
-            raise B.PsumError(st, "backward leg")
-        fwd, bwd = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
-    finally:
-        pc.close()
+            ev[2].record()
+            torch.cuda.synchronize()
+            st = B.psum_sync(pc.plan)
+            if st != B.PSUM_OK:
+                raise B.PsumError(st, "backward leg")
+            res[terms] = (ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2]), B.psum_scratch_bytes(pc.plan, s.N))
+        finally:
+            pc.close()
+    fwd, bwd, (nbytes, bands) = res["refined"]
     pairs_f = 27 * s.N * (s.N + 2 * s.M)
     pairs_b = 27 * s.N * 2 * s.M
-    return {"workload": "100k dipole pairs (200k charges, +-0.8, separation 0.01), d = (1,1,2), p = 16, M = 800, fp32c",
+    return {"workload": "100k dipole pairs (200k charges, +-0.8, separation 0.01), d = (1,1,2), p = 16, M = 800, "
+                        "fp32c with refined terms",
             "forward_ms": fwd, "backward_ms": bwd, "pairs_per_s": (pairs_f + pairs_b) / ((fwd + bwd) * 1e-3),
-            "pairs_forward": pairs_f, "pairs_backward": pairs_b}
+            "pairs_forward": pairs_f, "pairs_backward": pairs_b, "scratch_bytes": nbytes, "bands": bands,
+            "fast_terms": {"forward_ms": res["fast"][0], "backward_ms": res["fast"][1],
+                           "note": "eps2(phi) 1.65e-6 on this system, above the 1e-6 bound"}}
 
 
 def variants_leg(args):

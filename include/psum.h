@@ -64,6 +64,7 @@ extern "C" {
 #define PSUM_ERR_TIMEOUT     6  /* a bounded device-side wait gave up */
 #define PSUM_ERR_NOMEM       7  /* host or device allocation failed */
 #define PSUM_ERR_NONFINITE   8  /* a result is not finite (e.g. two charges closer than FP32 resolves) */
+#define PSUM_ERR_INTERNAL    9  /* a debug build's bounds check refused an access (psum_debug_checks) */
 
 /* ---- options ------------------------------------------------------------ */
 #define PSUM_FP64   0  /* near-field pair sum in float64 */
@@ -107,6 +108,21 @@ extern "C" {
                                   pair kernel's shared memory (K = 3 along two axes) keep the
                                   points; psum_check_form reports the form taken. */
 
+/* float32 pair terms of PSUM_FP32C plans (psum_opts.fp32_terms).  The float32 term q/r carries
+ * the rounding of its offsets, of r^2, of the rsqrt estimate and of the product, about one
+ * float32 unit in the last place (rms) of the term; the potential's error is that times
+ * kappa = sqrt(sum of squared terms) / rms(phi), the cancellation of the near sum.  Random
+ * charges have kappa of a few (about 4.7e-7 at 1e5 charges); tight dipoles of 2e5 charges about
+ * 20 (1.6e-6). */
+#define PSUM_TERMS_FAST     0  /* plain float32 terms */
+#define PSUM_TERMS_REFINED  1  /* the charge sums' far terms with 1/r as a float pair (the rsqrt
+                                  estimate plus its Newton correction) fused into the sums
+                                  unrounded, the targets' offsets rounded once, and the potential's
+                                  running sums cut every 8 steps: about 0.6 of the fast terms' error
+                                  for about 1.25x the symmetric charge kernel's time.  Applies to
+                                  the symmetric charge kernel (psum_pair_kernel); the one-sided
+                                  kernels and batches keep the fast terms. */
+
 #define PSUM_MEAN_ZERO 0  /* C_1 makes the box mean of phi zero (Eq. pfx3, phi_mean = 0) */
 #define PSUM_MEAN_NONE 1  /* C_1 = 0 (potential defined up to a constant, Sec. 3) */
 
@@ -137,6 +153,7 @@ typedef struct psum_opts {
     double rbf_radius;  /* centres at rbf_radius R0, > 1 (0: on S_b, i.e. at lambda_eff R0) */
     int pair_kernel;    /* PSUM_PAIRS_AUTO, PSUM_PAIRS_ONE_SIDED or PSUM_PAIRS_SYMMETRIC */
     int check_form;     /* PSUM_CHECKS_AUTO, PSUM_CHECKS_POINTS or PSUM_CHECKS_LAYERS */
+    int fp32_terms;     /* PSUM_TERMS_FAST or PSUM_TERMS_REFINED (PSUM_FP32C plans; ignored otherwise) */
 } psum_opts;
 
 typedef struct psum_info {
@@ -153,7 +170,7 @@ typedef struct psum_info {
 
 /* Fill `o` with the defaults: unit cube, p = 8, M = 200, PSUM_FP64,
    PSUM_MEAN_ZERO, K = (1,1,1), PSUM_POINTS_FIBONACCI, lambda = 0, PSUM_BASIS_SPHERICAL,
-   n_rbf = 256, rbf_radius = 0, PSUM_PAIRS_AUTO, PSUM_CHECKS_AUTO. */
+   n_rbf = 256, rbf_radius = 0, PSUM_PAIRS_AUTO, PSUM_CHECKS_AUTO, PSUM_TERMS_FAST. */
 void psum_opts_default(psum_opts *o);
 
 /* Algorithm "set" (Sec. 2.3.1): circumradius R0 (step 1), M check points on the
@@ -282,6 +299,12 @@ int psum_plan_info(psum_plan_t plan, psum_info *info);
  * Host only; PSUM_ERR_ARG for a null plan or kernel pointer or N < 0. */
 int psum_pair_kernel(psum_plan_t plan, int64_t N, int *kernel, int *image_groups);
 
+/* Device scratch psum_eval takes for N charges on this plan (*bytes: the plan's buffer grows to
+ * this size), and *bands (may be NULL): the number of bands of row tiles the symmetric charge
+ * kernel runs in turn, each reduced before the next, so that its partial sums stay within 1.5 GiB
+ * (0 with the one-sided kernel).  Host only; PSUM_ERR_ARG for a null plan or bytes, or N < 1. */
+int psum_scratch_bytes(psum_plan_t plan, int64_t N, int64_t *bytes, int *bands);
+
 /* The form of the check-point sums psum_eval runs on this plan, after the automatic choice:
  * *form = PSUM_CHECKS_POINTS or PSUM_CHECKS_LAYERS.  Host only; PSUM_ERR_ARG for a null plan
  * or form pointer. */
@@ -324,7 +347,7 @@ typedef struct psum_batch_info {
  * must share the precision and the current device (a plan may appear several times).
  * Each system's check sums take its plan's form (psum_check_form).
  * offsets (host, B+1 entries, offsets[0] = 0, increasing) delimit system b's charges in
- * the concatenated arrays: rows offsets[b] .. offsets[b+1]-1.  1 <= B <= 256.  All
+ * the concatenated arrays: rows offsets[b] .. offsets[b+1]-1.  1 <= B <= 65535.  All
  * device memory of the batch is allocated here.  The plans must outlive the batch. */
 int psum_batch_create(const psum_plan_t *plans, int B, const int64_t *offsets, psum_batch_t *out);
 
@@ -355,6 +378,30 @@ void psum_batch_destroy(psum_batch_t batch);
    psum_sync and writes NaN, and the CUDA context stays usable.  Off by default; returns
    PSUM_ERR_ARG for a NULL plan. */
 int psum_debug_inject_timeout(psum_plan_t plan, int enable);
+
+/* Debug builds (the paper has no counterpart).  A library compiled with -DPSUM_DEBUG_CHECKS=1
+   range-checks every write and read of the pair kernels' partial sums against the buffer's size:
+   an access outside it is skipped and flagged, psum_sync returns PSUM_ERR_INTERNAL and the outputs
+   are NaN, and the CUDA context stays usable (no trap).  psum_debug_checks() returns 1 in such a
+   build, 0 otherwise.  psum_debug_bounds_limit is its test hook: the checks see the partial
+   buffers as `doubles` long (0: their real size), so that a smaller value makes them fire without
+   any access leaving the real buffer; it has no effect on other builds.  PSUM_ERR_ARG for a NULL
+   plan or doubles < 0. */
+int psum_debug_checks(void);
+int psum_debug_bounds_limit(psum_plan_t plan, int64_t doubles);
+
+/* Test hook of the failure path (the paper has no counterpart): the next `count` growths of
+   this plan's scratch buffer fail as an out-of-memory cudaMalloc would -- the call that needed
+   it returns PSUM_ERR_NOMEM, queues nothing and leaves the plan without scratch, so a later call
+   grows it again.  No allocation is attempted for a failed growth.  PSUM_ERR_ARG for a NULL plan
+   or count < 0. */
+int psum_debug_fail_allocs(psum_plan_t plan, int count);
+
+/* Test hook of the banded partial sums (the paper has no counterpart): caps the symmetric charge
+   kernel's partial slots per band at `bytes` (0 restores 1.5 GiB), so that small systems run
+   several bands.  Results agree with the single band to rounding (the same slots, reduced in
+   another grouping).  PSUM_ERR_ARG for a NULL plan or bytes < 0. */
+int psum_debug_band_bytes(psum_plan_t plan, int64_t bytes);
 
 /* Release the plan and its device memory (waits for the device). NULL is a no-op. */
 void psum_destroy(psum_plan_t plan);

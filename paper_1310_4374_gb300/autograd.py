@@ -52,9 +52,9 @@ class PeriodicCoulombEnergy(torch.nn.Module):
     """
 
     def __init__(self, d, p: int, M: int, precision: str = "fp32c", mean: str = "zero", K=(1, 1, 1),
-                 check: bool = True):
+                 check: bool = True, terms: str = "fast"):
         super().__init__()
-        self.plan = B.psum_plan_create_ex(d, p, M, precision, mean, K)
+        self.plan = B.psum_plan_create_ex(d, p, M, precision, mean, K, terms=terms)
         self.P = B.psum_plan_info(self.plan)["P"]
         self.check = check
 

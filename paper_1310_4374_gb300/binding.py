@@ -22,6 +22,7 @@ PSUM_ERR_CUDA = 5
 PSUM_ERR_TIMEOUT = 6
 PSUM_ERR_NOMEM = 7
 PSUM_ERR_NONFINITE = 8
+PSUM_ERR_INTERNAL = 9
 
 PSUM_FP64 = 0
 PSUM_FP32C = 1
@@ -36,6 +37,7 @@ POINTS = {"fibonacci": 0, "gauss": 1}
 BASES = {"spherical": 0, "rbf": 1}
 PAIR_KERNELS = {"auto": 0, "one-sided": 1, "symmetric": 2}
 CHECK_FORMS = {"auto": 0, "points": 1, "layers": 2}
+FP32_TERMS = {"fast": 0, "refined": 1}
 MEAN_MODES = {"zero": PSUM_MEAN_ZERO, "none": PSUM_MEAN_NONE}
 
 
@@ -44,7 +46,7 @@ class psum_opts(ctypes.Structure):
                 ("precision", ctypes.c_int), ("mean_mode", ctypes.c_int), ("K", ctypes.c_int * 3),
                 ("points", ctypes.c_int), ("lambda_", ctypes.c_double), ("basis", ctypes.c_int),
                 ("n_rbf", ctypes.c_int), ("rbf_radius", ctypes.c_double), ("pair_kernel", ctypes.c_int),
-                ("check_form", ctypes.c_int)]
+                ("check_form", ctypes.c_int), ("fp32_terms", ctypes.c_int)]
 
 
 class psum_info(ctypes.Structure):
@@ -104,6 +106,12 @@ def load(build_if_needed: bool = True):
     lib.psum_plan_info.argtypes = [_vp, ctypes.POINTER(psum_info)]
     lib.psum_pair_kernel.argtypes = [_vp, ctypes.c_int64, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
     lib.psum_check_form.argtypes = [_vp, ctypes.POINTER(ctypes.c_int)]
+    lib.psum_scratch_bytes.argtypes = [_vp, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64),
+                                       ctypes.POINTER(ctypes.c_int)]
+    lib.psum_debug_band_bytes.argtypes = [_vp, ctypes.c_int64]
+    lib.psum_debug_fail_allocs.argtypes = [_vp, ctypes.c_int]
+    lib.psum_debug_bounds_limit.argtypes = [_vp, ctypes.c_int64]
+    lib.psum_debug_checks.argtypes = []
     lib.psum_profile.argtypes = [_vp, ctypes.c_int]
     lib.psum_last_timings.argtypes = [_vp, _dp, _vp]
     lib.psum_launch_count.argtypes = [_vp, ctypes.POINTER(ctypes.c_int64)]
@@ -125,7 +133,9 @@ def load(build_if_needed: bool = True):
     lib.psum_strerror.restype = ctypes.c_char_p
     for name in ("psum_plan_create", "psum_plan_create_ex", "psum_eval", "psum_eval_host", "psum_eval_noalloc",
                  "psum_sync",
-                 "psum_get_coeffs", "psum_plan_info", "psum_pair_kernel", "psum_check_form", "psum_profile", "psum_last_timings", "psum_launch_count",
+                 "psum_get_coeffs", "psum_plan_info", "psum_pair_kernel", "psum_check_form",
+                 "psum_scratch_bytes", "psum_debug_band_bytes", "psum_debug_fail_allocs",
+                 "psum_debug_bounds_limit", "psum_debug_checks", "psum_profile", "psum_last_timings", "psum_launch_count",
                  "psum_energy", "psum_energy_backward", "psum_energy_backward_c", "psum_coeffs_device",
                  "psum_eval_points", "psum_debug_inject_timeout", "psum_eval_graph", "psum_batch_create", "psum_batch_eval",
                  "psum_batch_sync", "psum_batch_get_coeffs", "psum_batch_get_info"):
@@ -176,8 +186,9 @@ def psum_plan_create(d1: float, d2: float, d3: float, p: int, M: int):
 
 def psum_plan_create_ex(d, p: int, M: int, precision="fp64", mean="zero", K=(1, 1, 1), points="fibonacci",
                         lam: float = 0.0, basis="spherical", n_rbf: int = 256, rbf_radius: float = 0.0,
-                        pairs="auto", checks="auto"):
+                        pairs="auto", checks="auto", terms="fast"):
     o = psum_opts_default()
+    o.fp32_terms = FP32_TERMS[terms] if isinstance(terms, str) else int(terms)
     o.pair_kernel = PAIR_KERNELS[pairs] if isinstance(pairs, str) else int(pairs)
     o.check_form = CHECK_FORMS[checks] if isinstance(checks, str) else int(checks)
     o.lambda_ = float(lam)
@@ -291,6 +302,29 @@ def psum_pair_kernel(plan, N: int):
     k, g = ctypes.c_int(0), ctypes.c_int(0)
     _check(load().psum_pair_kernel(plan, int(N), ctypes.byref(k), ctypes.byref(g)), "psum_pair_kernel")
     return ("symmetric" if k.value == 2 else "one-sided"), g.value
+
+
+def psum_scratch_bytes(plan, N: int):
+    """(scratch bytes of psum_eval for N charges, bands of the symmetric charge kernel)."""
+    nb, bands = ctypes.c_int64(0), ctypes.c_int(0)
+    _check(load().psum_scratch_bytes(plan, int(N), ctypes.byref(nb), ctypes.byref(bands)), "psum_scratch_bytes")
+    return int(nb.value), int(bands.value)
+
+
+def psum_debug_band_bytes(plan, nbytes: int) -> None:
+    _check(load().psum_debug_band_bytes(plan, int(nbytes)), "psum_debug_band_bytes")
+
+
+def psum_debug_bounds_limit(plan, doubles: int) -> None:
+    _check(load().psum_debug_bounds_limit(plan, int(doubles)), "psum_debug_bounds_limit")
+
+
+def psum_debug_checks() -> bool:
+    return bool(load().psum_debug_checks())
+
+
+def psum_debug_fail_allocs(plan, count: int) -> None:
+    _check(load().psum_debug_fail_allocs(plan, int(count)), "psum_debug_fail_allocs")
 
 
 def psum_check_form(plan) -> str:
@@ -446,9 +480,9 @@ class PeriodicCoulomb:
 
     def __init__(self, d, p: int, M: int, precision="fp64", mean="zero", K=(1, 1, 1), points="fibonacci",
                  lam: float = 0.0, basis="spherical", n_rbf: int = 256, rbf_radius: float = 0.0, pairs="auto",
-                 checks="auto"):
+                 checks="auto", terms="fast"):
         self.plan = psum_plan_create_ex(d, p, M, precision, mean, K, points, lam, basis, n_rbf, rbf_radius,
-                                        pairs, checks)
+                                        pairs, checks, terms)
         self.info = psum_plan_info(self.plan)
 
     def at(self, x, q, y, grad: bool = True, stream=None, check: bool = True):

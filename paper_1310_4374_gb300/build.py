@@ -2,6 +2,8 @@
 
 Each ``csrc/*.cu`` translation unit is compiled in parallel and the objects are
 linked into ``paper_1310_4374_gb300/_build/libpsum.so`` (static CUDA runtime).
+``build(debug=True)`` makes the debug library ``_build_debug/libpsum.so``, whose pair
+kernels range-check their partial sums (-DPSUM_DEBUG_CHECKS=1).
 """
 from __future__ import annotations
 
@@ -19,6 +21,9 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB_PATH = os.path.join(BUILD_DIR, "libpsum.so")
+DEBUG_BUILD_DIR = os.path.join(HERE, "_build_debug")
+DEBUG_LIB_PATH = os.path.join(DEBUG_BUILD_DIR, "libpsum.so")
+DEBUG_FLAGS = ["-DPSUM_DEBUG_CHECKS=1"]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # host code without floating-point contraction: the plan's float64 arithmetic (R0, the ball
@@ -39,31 +44,35 @@ def _sources():
     return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
 
 
-def _digest() -> str:
+def _digest(extra=()) -> str:
     h = hashlib.sha256()
     for f in _sources() + sorted(glob.glob(os.path.join(CSRC, "*.cuh"))) + [os.path.join(INCLUDE, "psum.h")]:
         with open(f, "rb") as fh:
             h.update(os.path.basename(f).encode())
             h.update(fh.read())
-    h.update(" ".join(ARCH + NVCC_FLAGS).encode())
+    h.update(" ".join(ARCH + NVCC_FLAGS + list(extra)).encode())
     return h.hexdigest()[:16]
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile the library if its sources changed; return the path of libpsum.so."""
-    os.makedirs(BUILD_DIR, exist_ok=True)
-    stamp = os.path.join(BUILD_DIR, "libpsum.stamp")
-    dig = _digest()
-    if not force and os.path.exists(LIB_PATH) and os.path.exists(stamp):
+def build(force: bool = False, verbose: bool = False, debug: bool = False) -> str:
+    """Compile the library if its sources changed; return the path of libpsum.so (of the
+    debug library with ``debug``)."""
+    build_dir = DEBUG_BUILD_DIR if debug else BUILD_DIR
+    lib_path = DEBUG_LIB_PATH if debug else LIB_PATH
+    extra = DEBUG_FLAGS if debug else []
+    os.makedirs(build_dir, exist_ok=True)
+    stamp = os.path.join(build_dir, "libpsum.stamp")
+    dig = _digest(extra)
+    if not force and os.path.exists(lib_path) and os.path.exists(stamp):
         with open(stamp) as f:
             if f.read().strip() == dig:
-                return LIB_PATH
+                return lib_path
     nvcc = _nvcc()
     objs = []
 
     def compile_one(src):
-        obj = os.path.join(BUILD_DIR, os.path.basename(src)[:-3] + ".o")
-        cmd = [nvcc, *ARCH, *NVCC_FLAGS, "-c", src, "-o", obj]
+        obj = os.path.join(build_dir, os.path.basename(src)[:-3] + ".o")
+        cmd = [nvcc, *ARCH, *NVCC_FLAGS, *extra, "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")
@@ -73,16 +82,16 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 1)) as ex:
         objs = list(ex.map(compile_one, _sources()))
-    tmp = LIB_PATH + f".tmp{os.getpid()}"
+    tmp = lib_path + f".tmp{os.getpid()}"
     cmd = [nvcc, *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB_PATH)
+    os.replace(tmp, lib_path)
     with open(stamp, "w") as f:
         f.write(dig)
-    return LIB_PATH
+    return lib_path
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose=True))
+    print(build(force="--force" in sys.argv, verbose=True, debug="--debug" in sys.argv))

@@ -33,7 +33,13 @@ int cuda_status(cudaError_t e) {
     return PSUM_ERR_CUDA;
 }
 
+// refined float32 pair terms (PSUM_TERMS_REFINED) in the symmetric charge kernel of FP32C plans
+bool refined_terms(const Plan& pl) {
+    return pl.opt.precision == PSUM_FP32C && pl.opt.fp32_terms == PSUM_TERMS_REFINED;
+}
+
 int map_device_status(int s) {
+    if (s & kStatBounds) return PSUM_ERR_INTERNAL;
     if (s & kStatNonNeutral) return PSUM_ERR_NONNEUTRAL;
     if (s & kStatOutOfBox) return PSUM_ERR_OUT_OF_BOX;
     if (s & kStatNonFinite) return PSUM_ERR_NONFINITE;
@@ -65,7 +71,8 @@ struct Layout {
     int nblk_mom;
     NearPlanLaunch Ln, Lc;
     bool sym;              // the charge pair sums by the symmetric kernel (partition S)
-    NearSymLaunch S;
+    NearSymLaunch S;       // its first band (row tiles 0 .. sym_bw - 1)
+    int64_t sym_bw = 0, sym_bands = 0;   // band width (row tiles) and number of bands
     int64_t n_tiles, n_chunks, n_pts;   // target tiles, source chunks, packed target points
     int64_t n_src_groups, n_src_pts;    // the charges' pack (groups of 128, FP32C/FF; points, FP64)
     int nblk_val, nblk_mean;
@@ -75,6 +82,34 @@ struct Layout {
     double* torg;
     double4_32a* tpk64;
 };
+
+// Split the single system of L.S (one full band) into bands of row tiles whose partial slots
+// fit `cap` bytes (kSymBandBytes unless a test lowers it); L.S becomes the first band.
+void sym_bands(Layout& L, int tile, size_t cap) {
+    SymSys& s = L.S.tab.one;
+    const int64_t G = L.S.G;
+    L.sym_bw = sym_band_width(s.n_tiles, (size_t)s.n_g * 4 * tile * sizeof(double), cap ? cap : kSymBandBytes);
+    L.sym_bands = (s.n_tiles + L.sym_bw - 1) / L.sym_bw;
+    s.a0 = 0;
+    s.a1 = L.sym_bw;
+    s.item0 = 0;
+    L.S.W = sym_sys_items(s);
+    L.S.doubles = sym_sys_doubles(s, tile);
+    L.S.G = G < L.S.W ? G : L.S.W;
+}
+
+// The launch of band k of the symmetric partition (row tiles k bw .. (k + 1) bw - 1).
+NearSymLaunch sym_band_launch(const Layout& L, int64_t k, bool inject, int64_t debug_limit = 0) {
+    NearSymLaunch S = L.S;
+    S.debug_limit = debug_limit;
+    SymSys& b = S.tab.one;
+    b.a0 = k * L.sym_bw;
+    b.a1 = std::min(b.n_tiles, b.a0 + L.sym_bw);
+    S.W = sym_sys_items(b);
+    S.G = std::min(L.S.G, S.W);
+    S.inject = inject ? 1 : 0;
+    return S;
+}
 
 // Lay out the scratch buffer for N charges; with base == nullptr only the size is computed.
 // `backward` adds the buffers of the energy derivatives; T >= 0 adds T separate evaluation
@@ -124,10 +159,11 @@ size_t layout(Plan& pl, int64_t N, char* base, Layout& L, bool backward = false,
             one[0].n_chunks = L.n_chunks;
             one[0].shift0 = 0;
             one[0].n_img = n_img;
-            L.S = sym_partition(one, (int64_t)pl.num_sms * near32s_occupancy_ctas(n_img, ffp));
-            L.S.G = (int64_t)pl.num_sms * near32s_occupancy_ctas(L.S.max_ipg, ffp);
-            if (L.S.G > L.S.W) L.S.G = L.S.W;
-            L.sym = L.S.doubles * sizeof(double) <= kSymMaxPartialBytes;
+            const bool rf = refined_terms(pl);
+            L.S = sym_partition(one, (int64_t)pl.num_sms * near32s_occupancy_ctas(n_img, ffp, rf));
+            L.S.G = (int64_t)pl.num_sms * near32s_occupancy_ctas(L.S.max_ipg, ffp, rf);
+            sym_bands(L, kTile32, pl.sym_band_bytes);
+            L.sym = true;
         }
         L.xs = trimmed ? b.take<double>(3 * (size_t)L.n_src_pts) : nullptr;
         L.ka = b.take<uint32_t>(N);
@@ -177,7 +213,8 @@ size_t layout(Plan& pl, int64_t N, char* base, Layout& L, bool backward = false,
             one[0].shift0 = 0;
             one[0].n_img = n_img;
             L.S = sym_partition(one, (int64_t)pl.num_sms * near64s_occupancy_ctas(), kTile64);
-            L.sym = L.S.doubles * sizeof(double) <= kSymMaxPartialBytes;
+            sym_bands(L, kTile64, pl.sym_band_bytes);
+            L.sym = true;
         }
         L.ka = L.va = L.kb = L.vb = L.hist = nullptr;
         L.pk32 = L.pk32lo = nullptr;
@@ -263,11 +300,15 @@ class DeviceGuard {
         if (e_ != cudaSuccess) return cuda_status(e_); \
     } while (0)
 
-int ensure_scratch(Plan& pl, size_t need) {
+int ensure_scratch(Plan& pl, size_t need, int* fail_allocs = nullptr) {
     if (need <= pl.scratch.bytes) return PSUM_OK;
     cudaFree(pl.scratch.ptr);              // synchronises: no queued kernel still uses the old buffer
     pl.scratch.ptr = nullptr;
     pl.scratch.bytes = 0;
+    if (fail_allocs && *fail_allocs > 0) {   // test hook: this growth fails as cudaMalloc would
+        --*fail_allocs;
+        return PSUM_ERR_NOMEM;
+    }
     TRY(cudaMalloc(&pl.scratch.ptr, need));
     pl.scratch.bytes = need;
     return PSUM_OK;
@@ -319,15 +360,23 @@ int queue_forward(psum_plan_s* h, int64_t N, const double* x, const double* q, d
     const double* tor = sep ? L.torg : L.org;
     const double4_32a* t64 = sep ? L.tpk64 : L.pk64;
     if (h->profile) TRY(cudaEventRecord(h->ev[1], st));
-    if (L.sym && fp32) {
-        NearSymLaunch S = L.S;
-        S.inject = h->inject_timeout ? 1 : 0;
-        TRY(launch_near32s(L.pk32, L.pk32lo, L.org, pl.d_shifts, L.part_n, S, st, ff));
-    } else if (L.sym) {
-        TRY(launch_near64s(L.pk64, pl.d_shifts, L.part_n, L.S, st));
+    if (L.sym) {
+        // band by band: the pair kernel writes the band's slots, the reduction adds them to the
+        // near-field sums in a fixed order (the first band sets them) before the next band
+        // reuses the slots; the last band's reduction runs with the others after the check sums
+        for (int64_t k = 0; k < L.sym_bands; ++k) {
+            const NearSymLaunch S = sym_band_launch(L, k, h->inject_timeout, h->debug_limit);
+            if (fp32)
+                TRY(launch_near32s(L.pk32, L.pk32lo, L.org, pl.d_shifts, L.part_n, S, st, ff, refined_terms(pl)));
+            else
+                TRY(launch_near64s(L.pk64, pl.d_shifts, L.part_n, S, st));
+            if (k + 1 < L.sym_bands) TRY(launch_sym_reduce(L.part_n, N, S, L.phi_n, L.grad_n, st, !fp32, k > 0));
+        }
+        h->launches += 2 * L.sym_bands - 2;   // beyond the one kernel and one reduction counted below
     } else if (fp32) {
         NearPlanLaunch Ln = L.Ln;
         Ln.inject = h->inject_timeout ? 1 : 0;
+        Ln.debug_limit = h->debug_limit;
         TRY(launch_near32(true, L.pk32, L.pk32lo, L.org, thi, tlo, tor, pl.d_shifts, L.part_n, Ln, st, 0, L.xs,
                           pl.Rb, ff));
     } else {
@@ -355,7 +404,9 @@ int queue_forward(psum_plan_s* h, int64_t N, const double* x, const double* q, d
     if (h->profile) TRY(cudaEventRecord(h->ev[3], st));
     const int tile = fp32 ? kTile32 : kTile64;
     if (L.sym)
-        TRY(launch_sym_reduce(L.part_n, N, L.S, L.phi_n, L.grad_n, st, !fp32));
+        TRY(launch_sym_reduce(L.part_n, N, sym_band_launch(L, L.sym_bands - 1, false, h->debug_limit), L.phi_n,
+                              L.grad_n, st, !fp32,
+                              L.sym_bands > 1));
     else
         TRY(launch_near_reduce(L.part_n, sep ? T : N, tile, 4, L.Ln, L.phi_n, L.grad_n, st));
     TRY(launch_near_reduce(L.part_c, layers ? (int64_t)pl.lc_tiles * tile : pl.n_check, tile, 1, L.Lc, L.phi_c,
@@ -397,7 +448,7 @@ int eval_device(psum_plan_s* h, int64_t N, const double* x, const double* q, dou
                 cudaStream_t st) {
     Plan& pl = h->pl;
     Layout L;
-    int rs = ensure_scratch(pl, layout(pl, N, nullptr, L));
+    int rs = ensure_scratch(pl, layout(pl, N, nullptr, L), &h->fail_allocs);
     if (rs != PSUM_OK) return rs;
     layout(pl, N, (char*)pl.scratch.ptr, L);
     return queue_forward(h, N, x, q, phi, grad, L, st);
@@ -407,7 +458,7 @@ int eval_points_device(psum_plan_s* h, int64_t N, const double* x, const double*
                        double* phi, double* grad, cudaStream_t st) {
     Plan& pl = h->pl;
     Layout L;
-    int rs = ensure_scratch(pl, layout(pl, N, nullptr, L, false, 0, T));
+    int rs = ensure_scratch(pl, layout(pl, N, nullptr, L, false, 0, T), &h->fail_allocs);
     if (rs != PSUM_OK) return rs;
     layout(pl, N, (char*)pl.scratch.ptr, L, false, 0, T);
     return queue_forward(h, N, x, q, phi, grad, L, st, T, y);
@@ -422,7 +473,7 @@ int backward_device(psum_plan_s* h, int64_t N, const double* x, const double* q,
     Plan& pl = h->pl;
     const psum_opts& o = pl.opt;
     Layout L;
-    int rs = ensure_scratch(pl, layout(pl, N, nullptr, L, true));
+    int rs = ensure_scratch(pl, layout(pl, N, nullptr, L, true), &h->fail_allocs);
     if (rs != PSUM_OK) return rs;
     layout(pl, N, (char*)pl.scratch.ptr, L, true);
     const bool fp32 = o.precision != PSUM_FP64;       // float32 packing (FP32C and FF)
@@ -504,6 +555,7 @@ bool valid_opts(const psum_opts* o) {
         o->check_form != PSUM_CHECKS_LAYERS)
         return false;
     if (o->check_form == PSUM_CHECKS_LAYERS && o->lambda > 0.0) return false;
+    if (o->fp32_terms != PSUM_TERMS_FAST && o->fp32_terms != PSUM_TERMS_REFINED) return false;
     if (o->mean_mode != PSUM_MEAN_ZERO && o->mean_mode != PSUM_MEAN_NONE) return false;
     return true;
 }
@@ -528,6 +580,7 @@ void psum_opts_default(psum_opts* o) {
     o->rbf_radius = 0.0;
     o->pair_kernel = PSUM_PAIRS_AUTO;
     o->check_form = PSUM_CHECKS_AUTO;
+    o->fp32_terms = PSUM_TERMS_FAST;
 }
 
 int psum_plan_create_ex(const psum_opts* o, psum_plan_t* out) {
@@ -581,7 +634,7 @@ int psum_eval_graph(psum_plan_t h, int64_t N, const double* x, const double* q, 
     Plan& pl = h->pl;
     cudaStream_t st = (cudaStream_t)stream;
     Layout L;
-    int rs = ensure_scratch(pl, layout(pl, N, nullptr, L));     // outside any capture
+    int rs = ensure_scratch(pl, layout(pl, N, nullptr, L), &h->fail_allocs);     // outside any capture
     if (rs != PSUM_OK) return rs;
     const void* key[6] = {x, q, phi, grad, pl.scratch.ptr, (const void*)(intptr_t)h->inject_timeout};
     bool same = h->gexec != nullptr && h->gN == N;
@@ -674,7 +727,7 @@ int psum_energy(psum_plan_t h, int64_t N, const double* q, const double* phi, do
     if (!h || N < 1 || N > (int64_t)1 << 30 || !q || !phi || !E) return PSUM_ERR_ARG;
     DeviceGuard g(h->pl.device);
     Layout L;
-    int rs = ensure_scratch(h->pl, layout(h->pl, N, nullptr, L));
+    int rs = ensure_scratch(h->pl, layout(h->pl, N, nullptr, L), &h->fail_allocs);
     if (rs != PSUM_OK) return rs;
     layout(h->pl, N, (char*)h->pl.scratch.ptr, L);
     TRY(launch_energy(q, phi, N, L.val_part, L.nblk_val, E, (cudaStream_t)stream));
@@ -746,6 +799,35 @@ int psum_pair_kernel(psum_plan_t h, int64_t N, int* kernel, int* image_groups) {
     layout(h->pl, N, nullptr, L);
     *kernel = L.sym ? PSUM_PAIRS_SYMMETRIC : PSUM_PAIRS_ONE_SIDED;
     if (image_groups) *image_groups = L.sym ? L.S.tab.one.n_g : 0;
+    return PSUM_OK;
+}
+
+int psum_scratch_bytes(psum_plan_t h, int64_t N, int64_t* bytes, int* bands) {
+    if (!h || !bytes || N < 1) return PSUM_ERR_ARG;
+    DeviceGuard g(h->pl.device);
+    Layout L{};
+    *bytes = (int64_t)layout(h->pl, N, nullptr, L);
+    if (bands) *bands = L.sym ? (int)L.sym_bands : 0;
+    return PSUM_OK;
+}
+
+int psum_debug_bounds_limit(psum_plan_t h, int64_t doubles) {
+    if (!h || doubles < 0) return PSUM_ERR_ARG;
+    h->debug_limit = doubles;
+    return PSUM_OK;
+}
+
+int psum_debug_checks(void) { return PSUM_DEBUG_CHECKS; }
+
+int psum_debug_fail_allocs(psum_plan_t h, int count) {
+    if (!h || count < 0) return PSUM_ERR_ARG;
+    h->fail_allocs = count;
+    return PSUM_OK;
+}
+
+int psum_debug_band_bytes(psum_plan_t h, int64_t bytes) {
+    if (!h || bytes < 0) return PSUM_ERR_ARG;
+    h->pl.sym_band_bytes = (size_t)bytes;
     return PSUM_OK;
 }
 
@@ -872,6 +954,7 @@ const char* psum_strerror(int s) {
         case PSUM_ERR_TIMEOUT: return "a device-side wait timed out";
         case PSUM_ERR_NOMEM: return "out of memory";
         case PSUM_ERR_NONFINITE: return "a result or charge is not finite";
+        case PSUM_ERR_INTERNAL: return "an internal bounds check refused an access (debug build)";
         default: return "unknown status";
     }
 }

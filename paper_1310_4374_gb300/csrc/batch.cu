@@ -21,7 +21,11 @@
 namespace psum {
 
 constexpr int kSeg = 128;        // charges per segment (validation, mean, far field)
-constexpr int kMaxBatch = 256;   // 8-bit system prefix of the sort key
+// systems of one batch: up to 256 sort with an 8-bit system prefix on the 24-bit Morton key
+// (4 radix passes); more sort by the Morton key, then stably by the system (16 bits, 2 passes);
+// per-system launches put the system in grid.y (at most 65535)
+constexpr int kMaxBatch = 65535;
+constexpr int kPrefixBatch = 256;
 
 struct BatchDev {
     int64_t n0, n;            // the system's charges: rows n0 .. n0+n-1 (caller order = sorted order range)
@@ -104,11 +108,12 @@ __global__ void k_bvalidate_finish(const BatchDev* __restrict__ sys, const doubl
     if (threadIdx.x == 0 && !(fabs(s) <= 1e-12 * sa)) atomicOr(status + blockIdx.x, kStatNonNeutral);
 }
 
-// sort keys: system in the top 8 bits, the 24-bit Morton code of the system's box below
+// sort keys: the 24-bit Morton code of the system's box, with the system in the top 8 bits
+// when `prefix` (batches of up to 256 systems)
 __global__ void __launch_bounds__(kSeg) k_bmorton(const double* __restrict__ x, const BatchDev* __restrict__ sys,
                                                   const int* __restrict__ seg_sys,
                                                   const int64_t* __restrict__ seg_start, uint32_t* __restrict__ keys,
-                                                  uint32_t* __restrict__ vals) {
+                                                  uint32_t* __restrict__ vals, int prefix) {
     const int seg = blockIdx.x;
     const int b = seg_sys[seg];
     const BatchDev& S = sys[b];
@@ -121,8 +126,24 @@ __global__ void __launch_bounds__(kSeg) k_bmorton(const double* __restrict__ x, 
         v = v < 0 ? 0 : (v > 255 ? 255 : v);
         c[k] = (uint32_t)v;
     }
-    keys[i] = ((uint32_t)b << 24) | spread8(c[0]) | (spread8(c[1]) << 1) | (spread8(c[2]) << 2);
+    keys[i] = (prefix ? (uint32_t)b << 24 : 0u) | spread8(c[0]) | (spread8(c[1]) << 1) | (spread8(c[2]) << 2);
     vals[i] = (uint32_t)i;
+}
+
+// after the Morton passes of a large batch: the system of each sorted charge as the key of the
+// remaining (stable) passes, found from its row by binary search over the systems' first rows
+__global__ void k_bsys_keys(const uint32_t* __restrict__ vin, int64_t n, const BatchDev* __restrict__ sys, int B,
+                            uint32_t* __restrict__ kout, uint32_t* __restrict__ vout) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const uint32_t v = vin[j];
+    int lo = 0, hi = B - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (sys[mid].n0 <= (int64_t)v) lo = mid; else hi = mid - 1;
+    }
+    kout[j] = (uint32_t)lo;
+    vout[j] = v;
 }
 
 // step 4: f_l = phi_near(y~_l) - phi_near(y_l), for every system (grid.y = system); a
@@ -217,7 +238,7 @@ __global__ void __launch_bounds__(kSeg) k_bfar(const double* __restrict__ x, con
     if (s >= S.n0 + S.n) return;
     const int64_t i = perm ? (int64_t)perm[s] : s;
     const int64_t pk = S.pt0 + (s - S.n0);
-    if (status[b] & (kStatNonNeutral | kStatOutOfBox | kStatNonFinite | kStatTimeout)) {
+    if (status[b] & (kStatNonNeutral | kStatOutOfBox | kStatNonFinite | kStatTimeout | kStatBounds)) {
         phi[i] = __longlong_as_double(0x7ff8000000000000ll);
         if (grad) grad[3 * i] = grad[3 * i + 1] = grad[3 * i + 2] = __longlong_as_double(0x7ff8000000000000ll);
         return;
@@ -428,8 +449,18 @@ int queue_batch(psum_batch_s* bt, const double* x, const double* q, double* phi,
     nl += 2;
     const uint32_t* perm = nullptr;
     if (fp32) {
-        k_bmorton<<<bt->n_seg, kSeg, 0, st>>>(x, bt->d_sys, bt->d_seg_sys, bt->d_seg_start, bt->ka, bt->va);
-        BTRY(launch_radix_sort(bt->ka, bt->va, bt->kb, bt->vb, bt->hist, bt->N, 4, st));
+        const bool prefix = B <= kPrefixBatch;
+        k_bmorton<<<bt->n_seg, kSeg, 0, st>>>(x, bt->d_sys, bt->d_seg_sys, bt->d_seg_start, bt->ka, bt->va,
+                                              prefix ? 1 : 0);
+        if (prefix) {
+            BTRY(launch_radix_sort(bt->ka, bt->va, bt->kb, bt->vb, bt->hist, bt->N, 4, st));
+        } else {
+            // Morton passes (result in kb, vb), the systems as keys, two stable passes on them
+            BTRY(launch_radix_sort(bt->ka, bt->va, bt->kb, bt->vb, bt->hist, bt->N, 3, st));
+            k_bsys_keys<<<(unsigned)((bt->N + 255) / 256), 256, 0, st>>>(bt->vb, bt->N, bt->d_sys, B, bt->ka, bt->va);
+            BTRY(launch_radix_sort(bt->ka, bt->va, bt->kb, bt->vb, bt->hist, bt->N, 2, st));
+            nl += 1 + 6 - 3;
+        }
         perm = bt->va;
         BTRY(launch_pack32_groups(x, q, perm, bt->n_groups, bt->d_grp_start, bt->d_grp_count, bt->pk_hi, bt->pk_lo,
                                   bt->org, st));
@@ -880,7 +911,8 @@ int psum_batch_sync(psum_batch_t bt, int* status, void* stream) {
     for (int b = 0; b < bt->B; ++b) {
         const int s = bt->h_status[b];
         int code = PSUM_OK;
-        if (s & kStatNonNeutral) code = PSUM_ERR_NONNEUTRAL;
+        if (s & kStatBounds) code = PSUM_ERR_INTERNAL;
+        else if (s & kStatNonNeutral) code = PSUM_ERR_NONNEUTRAL;
         else if (s & kStatOutOfBox) code = PSUM_ERR_OUT_OF_BOX;
         else if (s & kStatNonFinite) code = PSUM_ERR_NONFINITE;
         else if (s & kStatTimeout) code = PSUM_ERR_TIMEOUT;

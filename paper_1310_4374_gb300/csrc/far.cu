@@ -210,7 +210,7 @@ __global__ void __launch_bounds__(kFarThreads) k_far_combine(const double* __res
     const int64_t s = (int64_t)blockIdx.x * kFarThreads + threadIdx.x;
     if (s >= n) return;
     const int64_t i = perm ? (int64_t)perm[s] : s;
-    const bool failed = (*status & (kStatNonNeutral | kStatOutOfBox | kStatNonFinite | kStatTimeout)) != 0;
+    const bool failed = (*status & (kStatNonNeutral | kStatOutOfBox | kStatNonFinite | kStatTimeout | kStatBounds)) != 0;
     if (failed) {
         phi[i] = __longlong_as_double(0x7ff8000000000000ll);
         if (grad) grad[3 * i] = grad[3 * i + 1] = grad[3 * i + 2] = __longlong_as_double(0x7ff8000000000000ll);
@@ -294,7 +294,7 @@ __global__ void __launch_bounds__(kFarThreads) k_far_rbf(const double* __restric
         }
     }
     if (!live) return;
-    const bool failed = (*status & (kStatNonNeutral | kStatOutOfBox | kStatNonFinite | kStatTimeout)) != 0;
+    const bool failed = (*status & (kStatNonNeutral | kStatOutOfBox | kStatNonFinite | kStatTimeout | kStatBounds)) != 0;
     if (failed) {
         phi[i] = __longlong_as_double(0x7ff8000000000000ll);
         if (grad) grad[3 * i] = grad[3 * i + 1] = grad[3 * i + 2] = __longlong_as_double(0x7ff8000000000000ll);

@@ -24,13 +24,14 @@ cudaError_t launch_near_reduce(const double* partial, int64_t n_valid, int tile_
                                const NearPlanLaunch& L, double* out_phi, double* out_grad, cudaStream_t st);
 int near32_occupancy_ctas(int n_img, int variant = 0, bool trimmed = false, bool ff = false);
 cudaError_t launch_near32s(const float4* pk_hi, const float4* pk_lo, const double* org, const double* shifts,
-                           double* partial, const NearSymLaunch& S, cudaStream_t st, bool ff = false);
+                           double* partial, const NearSymLaunch& S, cudaStream_t st, bool ff = false,
+                           bool refine = false);
 cudaError_t launch_sym_reduce(const double* partial, int64_t n_valid, const NearSymLaunch& S, double* out_phi,
-                              double* out_grad, cudaStream_t st, bool fp64 = false);
+                              double* out_grad, cudaStream_t st, bool fp64 = false, bool accumulate = false);
 cudaError_t launch_near64s(const double4_32a* pk, const double* shifts, double* partial, const NearSymLaunch& S,
                            cudaStream_t st);
 int near64s_occupancy_ctas();
-int near32s_occupancy_ctas(int img_per_g, bool ff = false);
+int near32s_occupancy_ctas(int img_per_g, bool ff = false, bool refine = false);
 constexpr int kNear32Variants = 2;
 int near64_occupancy_ctas();
 // sort.cu

@@ -54,6 +54,7 @@ struct Near32Args {
     int* status;             // error words (kStatTimeout when a chunk copy never lands)
     int n_status;
     int inject;              // test hook: expect 16 bytes more than the copies bring
+    int64_t limit;           // doubles of the partial buffer (debug bounds checks)
     int max_contrib, max_img;
     NearSysTable tab;
     // two-layer check sums (potential only): each target's class c (0..n_cls-1) rides in its
@@ -107,11 +108,13 @@ __global__ void __launch_bounds__(kThreads32, kMinB) k_near32(Near32Args a) {
 
     auto flush = [&](int64_t tile, int64_t first_unit) {
         const int64_t slot = item - sk_owner(first_unit, a.U, a.W);
-        double* dst = a.partial + ((tile * a.max_contrib + slot) * NQ) * kTile32;
+        const int64_t off = ((tile * a.max_contrib + slot) * NQ) * kTile32;
+        double* dst = a.partial + off;
+        const bool ok = debug_in_range(off, NQ * kTile32, a.limit, a.status, a.n_status);
 #pragma unroll
         for (int qi = 0; qi < NQ; ++qi)
 #pragma unroll
-            for (int j = 0; j < 2; ++j) {
+            for (int j = 0; j < 2 && ok; ++j) {
                 const float2 h = s_acc[qi][j][0][tid], l = s_acc[qi][j][1][tid];
                 dst[qi * kTile32 + (2 * j) * kThreads32 + tid] = (double)h.x + (double)l.x;
                 dst[qi * kTile32 + (2 * j + 1) * kThreads32 + tid] = (double)h.y + (double)l.y;
@@ -210,6 +213,7 @@ __global__ void __launch_bounds__(kThreads32, kMinB) k_near32(Near32Args a) {
                     dl[3] = (float)(D0 - (double)dl[0]); dl[4] = (float)(D1 - (double)dl[1]);
                     dl[5] = (float)(D2 - (double)dl[2]);
                     s_w[e] = a.img_w[ei];
+                    if (s_w[e] != 0.f) atomicOr(s_near + im, kUnitWeighted);
                     // the near test on the class's own points of the group
                     const double* sb = a.grp_sub + 4 * ((cur_tile * kTgt32 + k) * ncls + c);
                     const double E0 = (sb[0] - so[0]) - sh[0], E1 = (sb[1] - so[1]) - sh[1],
@@ -218,6 +222,11 @@ __global__ void __launch_bounds__(kThreads32, kMinB) k_near32(Near32Args a) {
                     if (E0 * E0 + E1 * E1 + E2 * E2 <= reach * reach)
                         atomicOr(s_near + im, k < 2 ? kUnitNear0 : kUnitNear1);
                 }
+                __syncthreads();
+                // an image whose weight is zero for every class present (a padding layer image
+                // of an anisotropic block) adds nothing to any target: skip its unit
+                for (int im = tid; im < n_img; im += kThreads32)
+                    s_near[im] = (s_near[im] & kUnitWeighted) ? (s_near[im] & ~kUnitWeighted) : kUnitOutside;
             } else
             for (int im = tid; im < n_img; im += kThreads32) {
                 const double* sh = a.shifts + 3 * (shift0 + im);
@@ -629,6 +638,11 @@ cudaError_t launch_near32(bool grad, const float4* src_hi, const float4* src_lo,
     a.partial = partial; a.U = L.U; a.W = L.W; a.counter = L.counter; a.max_contrib = L.max_contrib;
     a.max_img = L.max_img;
     a.tab = L.tab;
+    {
+        // the partial buffer as the debug bounds checks see it (a test may shrink it)
+        const int64_t real = L.n_tiles * L.max_contrib * (grad ? 4 : 1) * kTile32;
+        a.limit = L.debug_limit > 0 && L.debug_limit < real ? L.debug_limit : real;
+    }
     a.src_x = src_x;
     a.Rb = Rb;
     if (n_cls < 1 || (n_cls > 1 && (!grp_cls || !grp_sub || !img_w || grad || Rb > 0.0)) || (img_w && grad))

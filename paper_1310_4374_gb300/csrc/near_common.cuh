@@ -87,6 +87,7 @@ constexpr int kUnitOutside = 2;    // every source image outside the ball: nothi
 constexpr int kUnitStraddle = 4;   // per-source test against the ball
 constexpr int kUnitNear1 = 8;      // the same for target pair 1 (groups 2, 3)
 constexpr int kUnitNear = kUnitNear0 | kUnitNear1;
+constexpr int kUnitWeighted = 16;  // while staging two-layer check sums: an image with a nonzero weight
 
 // |x + p|^2 <= Rb^2 with the rounding of a plain left-to-right evaluation (no contraction),
 // the same decision for a source at the boundary as a straightforward float64 evaluation
@@ -342,6 +343,19 @@ __device__ __forceinline__ double rsqrt_f64_k0(double r2) {
     const double e = fma(-r2, y * y, 1.0);
     const double ri = fma(y * e, fma(0.375, e, 0.5), y);
     return r2f > 0.f ? ri : 0.0;
+}
+
+// Debug builds (-DPSUM_DEBUG_CHECKS=1) check every write and read of the pair kernels'
+// partial sums against the buffer's size: an access outside it is skipped and flagged in the
+// launch's status words (kStatBounds, PSUM_ERR_INTERNAL at psum_sync) instead of faulting.
+__device__ __forceinline__ bool debug_in_range(int64_t off, int64_t n, int64_t limit, int* status, int n_status) {
+#if PSUM_DEBUG_CHECKS
+    if (off < 0 || off + n > limit) {
+        for (int k = 0; k < n_status; ++k) atomicOr(status + k, kStatBounds);
+        return false;
+    }
+#endif
+    return true;
 }
 
 // warps of the reduction kernels (fixed-order combination of the partial slots)

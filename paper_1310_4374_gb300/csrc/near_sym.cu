@@ -50,6 +50,7 @@ struct Near32SymArgs {
     int* status;
     int n_status;
     int inject;              // test hook: expect 16 bytes more than the copies bring
+    int64_t limit;           // doubles of the partial buffer (debug bounds checks)
 };
 
 // compensated float32 (hi, lo) += v
@@ -94,6 +95,72 @@ __device__ __forceinline__ void sym_far_step_pair(float4 A, float4 B, const floa
         ry = __ffma2_rn(ey, wb, ry);
         rz = __ffma2_rn(ez, wb, rz);
     }
+    rp = __fadd2_rn(rp, bp);
+}
+
+// The same far step with refined potential terms (PSUM_TERMS_REFINED).  The float32 term q/r
+// carries the rounding of its offsets, of r^2, of the MUFU estimate z (0.58 ulp rms, measured)
+// and of the product q z -- about one ulp of the term in all; on systems whose potential
+// cancels strongly (tight dipoles: a potential of rms ~100 from terms whose root-sum-square is
+// ~20x larger) these errors, not the sums, set the potential's accuracy.  Here:
+//   * the offset e = s + n' is carried as eh + el: el = (s - (eh - n')) is the exact rounding
+//     error of the sum wherever |n'| >= |s| component by component (Fast2Sum; where not, both
+//     are small and so is the error left), and the target offset's own rounding enters r^2
+//     through the per-target constant c0 = n' . n'_lo (n'_lo = -(t + D) - n', float64 unit
+//     offset D), so r^2 = rh + 2 c with c = c0 + eh . el;
+//   * 1/r is the pair z + k, with k the Newton correction -z (r^2 z^2 - 1) / 2 computed from that
+//     r^2, and both products go into fused multiply-adds unrounded: the action adds q_s z to its
+//     running sum and q_s k to a separate correction sum; the reaction forms the 4 targets'
+//     corrections first and adds their q_t z on top.
+// The field keeps the unrefined weight q z^3 (a few ulps of terms that cancel far less).  Per
+// term about 0.41 ulp rms instead of 0.99 (float32 emulation of this arithmetic); per target
+// and source pair 31 packed operations instead of 19.
+__device__ __forceinline__ void sym_far_step_pair_refined(float4 A, float4 B, const float2 (&nx)[4],
+                                                          const float2 (&ny)[4], const float2 (&nz)[4],
+                                                          const float2 (&c0)[4], const float2 (&tq)[4],
+                                                          float2 (&aphi)[4], float2 (&acor)[4], float2 (&agx)[4],
+                                                          float2 (&agy)[4], float2 (&agz)[4], float2& rp, float2& rx,
+                                                          float2& ry, float2& rz) {
+    const float2 sx = make_float2(A.x, A.y), sy = make_float2(A.z, A.w), sz = make_float2(B.x, B.y);
+    const float2 sq = make_float2(B.z, B.w);
+    const float2 m1 = make_float2(-1.f, -1.f);
+    float2 z[4], k[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float2 ex = __fadd2_rn(sx, nx[i]);
+        const float2 ey = __fadd2_rn(sy, ny[i]);
+        const float2 ez = __fadd2_rn(sz, nz[i]);
+        const float2 lx = __ffma2_rn(m1, __ffma2_rn(m1, nx[i], ex), sx);    // s - (e - n')
+        const float2 ly = __ffma2_rn(m1, __ffma2_rn(m1, ny[i], ey), sy);
+        const float2 lz = __ffma2_rn(m1, __ffma2_rn(m1, nz[i], ez), sz);
+        float2 r2 = __fmul2_rn(ex, ex);
+        r2 = __ffma2_rn(ey, ey, r2);
+        r2 = __ffma2_rn(ez, ez, r2);
+        float2 c = __ffma2_rn(ex, lx, c0[i]);
+        c = __ffma2_rn(ey, ly, c);
+        c = __ffma2_rn(ez, lz, c);
+        z[i] = make_float2(rsqrt_mufu(r2.x), rsqrt_mufu(r2.y));
+        const float2 zz = __fmul2_rn(z[i], z[i]);
+        const float2 rt = __ffma2_rn(make_float2(2.f, 2.f), c, r2);           // r^2 with its low part
+        const float2 g = __ffma2_rn(rt, zz, m1);                               // r^2 z^2 - 1
+        k[i] = __fmul2_rn(__fmul2_rn(make_float2(-0.5f, -0.5f), z[i]), g);
+        const float2 ri3 = __fmul2_rn(z[i], zz);
+        aphi[i] = __ffma2_rn(sq, z[i], aphi[i]);
+        acor[i] = __ffma2_rn(sq, k[i], acor[i]);
+        const float2 wa = __fmul2_rn(sq, ri3);
+        agx[i] = __ffma2_rn(ex, wa, agx[i]);
+        agy[i] = __ffma2_rn(ey, wa, agy[i]);
+        agz[i] = __ffma2_rn(ez, wa, agz[i]);
+        const float2 wb = __fmul2_rn(tq[i], ri3);
+        rx = __ffma2_rn(ex, wb, rx);
+        ry = __ffma2_rn(ey, wb, ry);
+        rz = __ffma2_rn(ez, wb, rz);
+    }
+    float2 bp = __fmul2_rn(tq[0], k[0]);
+#pragma unroll
+    for (int i = 1; i < 4; ++i) bp = __ffma2_rn(tq[i], k[i], bp);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) bp = __ffma2_rn(tq[i], z[i], bp);
     rp = __fadd2_rn(rp, bp);
 }
 
@@ -223,8 +290,9 @@ __device__ __forceinline__ void sym_ff_step(const float4* __restrict__ s_hi, con
     }
 }
 
-template <int kMinB, bool kFF>
+template <int kMinB, bool kFF, bool kRefine = false>
 __global__ void __launch_bounds__(kThreads32, kMinB) k_near32s(Near32SymArgs a) {
+    static_assert(!(kFF && kRefine), "float-float pairs need no refinement");
     constexpr int kWarps = kThreads32 / 32;
     __shared__ float4 s_hi[2 * kNearChunk];
     __shared__ float4 s_lo[2 * kNearChunk];
@@ -264,14 +332,10 @@ __global__ void __launch_bounds__(kThreads32, kMinB) k_near32s(Near32SymArgs a) 
     const int64_t local = item - S.item0;
     const int64_t pair = local / S.n_g;
     const int gi = (int)(local - pair * S.n_g);
-    // pair = tb (tb + 1) / 2 + ta, ta <= tb (tiles of the system)
-    int64_t tb = (int64_t)((sqrt(8.0 * (double)pair + 1.0) - 1.0) * 0.5);
-    while (tb > 0 && tb * (tb + 1) / 2 > pair) --tb;
-    while ((tb + 1) * (tb + 2) / 2 <= pair) ++tb;
-    const int64_t ta = pair - tb * (tb + 1) / 2;
+    int64_t ta, tb;                      // the band's pair: ta <= tb (tiles of the system)
+    sym_band_pair(S, pair, ta, tb);
     const bool diag = ta == tb;
     const int64_t TA = S.tile0 + ta;     // global tiles
-    const int64_t n_slots = S.n_tiles * S.n_g;
     const int im0 = gi * S.img_per_g;
     const int nimg = min(S.img_per_g, S.n_img - im0);
     // targets of tile ta; zero the action sums
@@ -450,6 +514,105 @@ __global__ void __launch_bounds__(kThreads32, kMinB) k_near32s(Near32SymArgs a) 
             float2 agx[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)}, agy[2] = {agx[0], agx[0]},
                    agz[2] = {agx[0], agx[0]};
             float2 aphi[2] = {agx[0], agx[0]}, aphi2[2] = {agx[0], agx[0]};   // far: two interleaved sums; near: hi, lo
+            if (kRefine && !(cls & kUnitNear)) {
+                // refined potential terms (sym_far_step_pair_refined).  The targets' negated
+                // offsets -(t + D) are rounded once from the float64 unit offset D = hi + lo; the
+                // potential's running sums are cut every 8 steps: the action's two halves go into
+                // the compensated sums, and each source's reaction is kept as four 8-step
+                // segments (parked in registers while the sums rotate through the warp, then
+                // fetched back by the lane that owns the source and added as a tree).
+                float2 nx[4], ny[4], nz[4], c0[4], tq4[4];
+                float2 ph[4], pc[4], gx[4], gy[4], gz[4];
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    const float* d0 = dl + 6 * (2 * j);
+                    const float* d1 = dl + 6 * (2 * j + 1);
+                    float o0[3], o1[3], w0 = 0.f, w1 = 0.f;
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        // n' = -(t + D) rounded once, and its remainder n'_lo
+                        const float2 th = s_th[c][j][tid];
+                        float e0, e1;
+                        const float h0 = two_sum(th.x, d0[c], e0);
+                        const float h1 = two_sum(th.y, d1[c], e1);
+                        const float l0 = e0 + d0[3 + c], l1 = e1 + d1[3 + c];
+                        float f0, f1;
+                        o0[c] = -two_sum(h0, l0, f0);
+                        o1[c] = -two_sum(h1, l1, f1);
+                        w0 = fmaf(o0[c], -f0, w0);                    // n' . n'_lo
+                        w1 = fmaf(o1[c], -f1, w1);
+                    }
+                    nx[2 * j] = make_float2(o0[0], o0[0]); nx[2 * j + 1] = make_float2(o1[0], o1[0]);
+                    ny[2 * j] = make_float2(o0[1], o0[1]); ny[2 * j + 1] = make_float2(o1[1], o1[1]);
+                    nz[2 * j] = make_float2(o0[2], o0[2]); nz[2 * j + 1] = make_float2(o1[2], o1[2]);
+                    c0[2 * j] = make_float2(w0, w0); c0[2 * j + 1] = make_float2(w1, w1);
+                    tq4[2 * j] = make_float2(tq[j].x, tq[j].x);
+                    tq4[2 * j + 1] = make_float2(tq[j].y, tq[j].y);
+                }
+#pragma unroll
+                for (int i2 = 0; i2 < 4; ++i2) ph[i2] = pc[i2] = gx[i2] = gy[i2] = gz[i2] = make_float2(0.f, 0.f);
+#pragma unroll 1
+                for (int g = 0; g < kNearChunk / 64; ++g) {
+                    float2 rp = make_float2(0.f, 0.f), rx = rp, ry = rp, rz = rp, st0 = rp, st1 = rp, st2 = rp;
+#pragma unroll 1
+                    for (int k = 0; k < 32; ++k) {
+                        const int P = 32 * g + ((lane + k) & 31);
+                        sym_far_step_pair_refined(s_sp[2 * P], s_sp[2 * P + 1], nx, ny, nz, c0, tq4, ph, pc, gx, gy,
+                                                  gz, rp, rx, ry, rz);
+                        rp.x = __shfl_sync(0xffffffffu, rp.x, up);
+                        rp.y = __shfl_sync(0xffffffffu, rp.y, up);
+                        rx.x = __shfl_sync(0xffffffffu, rx.x, up);
+                        rx.y = __shfl_sync(0xffffffffu, rx.y, up);
+                        ry.x = __shfl_sync(0xffffffffu, ry.x, up);
+                        ry.y = __shfl_sync(0xffffffffu, ry.y, up);
+                        rz.x = __shfl_sync(0xffffffffu, rz.x, up);
+                        rz.y = __shfl_sync(0xffffffffu, rz.y, up);
+                        if ((k & 7) == 7) {
+#pragma unroll
+                            for (int j = 0; j < 2; ++j)
+                                two_sum_acc2(s_acc[0][j][0][tid], s_acc[0][j][1][tid],
+                                             make_float2(ph[2 * j].x + ph[2 * j].y, ph[2 * j + 1].x + ph[2 * j + 1].y));
+#pragma unroll
+                            for (int i2 = 0; i2 < 4; ++i2) ph[i2] = make_float2(0.f, 0.f);
+                            // after step k the lane holds pair (lane + k + 1) mod 32's partial sum
+                            if (k == 7) st0 = rp;
+                            if (k == 15) st1 = rp;
+                            if (k == 23) st2 = rp;
+                            if (k != 31) rp = make_float2(0.f, 0.f);
+                        }
+                    }
+                    // pair lane's segments of steps 0-7, 8-15 and 16-23 sit 8, 16 and 24 lanes down
+                    const float2 s1 = make_float2(__shfl_sync(0xffffffffu, st0.x, (lane + 24) & 31),
+                                                  __shfl_sync(0xffffffffu, st0.y, (lane + 24) & 31));
+                    const float2 s2 = make_float2(__shfl_sync(0xffffffffu, st1.x, (lane + 16) & 31),
+                                                  __shfl_sync(0xffffffffu, st1.y, (lane + 16) & 31));
+                    const float2 s3 = make_float2(__shfl_sync(0xffffffffu, st2.x, (lane + 8) & 31),
+                                                  __shfl_sync(0xffffffffu, st2.y, (lane + 8) & 31));
+                    const float2 tot = __fadd2_rn(__fadd2_rn(s1, s2), __fadd2_rn(s3, rp));
+                    const int s = 2 * (32 * g + lane);
+                    two_sum_acc(s_re[warp][0][0][s], s_re[warp][0][1][s], tot.x);
+                    two_sum_acc(s_re[warp][0][0][s + 1], s_re[warp][0][1][s + 1], tot.y);
+                    two_sum_acc(s_re[warp][1][0][s], s_re[warp][1][1][s], rx.x);
+                    two_sum_acc(s_re[warp][1][0][s + 1], s_re[warp][1][1][s + 1], rx.y);
+                    two_sum_acc(s_re[warp][2][0][s], s_re[warp][2][1][s], ry.x);
+                    two_sum_acc(s_re[warp][2][0][s + 1], s_re[warp][2][1][s + 1], ry.y);
+                    two_sum_acc(s_re[warp][3][0][s], s_re[warp][3][1][s], rz.x);
+                    two_sum_acc(s_re[warp][3][0][s + 1], s_re[warp][3][1][s + 1], rz.y);
+                }
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    // the corrections (tiny against the terms) into the low parts; the field as usual
+                    s_acc[0][j][1][tid] = __fadd2_rn(s_acc[0][j][1][tid],
+                                                     make_float2(pc[2 * j].x + pc[2 * j].y, pc[2 * j + 1].x + pc[2 * j + 1].y));
+                    two_sum_acc2(s_acc[1][j][0][tid], s_acc[1][j][1][tid],
+                                 make_float2(gx[2 * j].x + gx[2 * j].y, gx[2 * j + 1].x + gx[2 * j + 1].y));
+                    two_sum_acc2(s_acc[2][j][0][tid], s_acc[2][j][1][tid],
+                                 make_float2(gy[2 * j].x + gy[2 * j].y, gy[2 * j + 1].x + gy[2 * j + 1].y));
+                    two_sum_acc2(s_acc[3][j][0][tid], s_acc[3][j][1][tid],
+                                 make_float2(gz[2 * j].x + gz[2 * j].y, gz[2 * j + 1].x + gz[2 * j + 1].y));
+                }
+                continue;
+            }
             if (!(cls & kUnitNear)) {
                 // targets as 4 scalars (duplicated into both halves), sources two at a time
                 float2 nx[4], ny[4], nz[4], tq4[4];
@@ -572,9 +735,10 @@ __global__ void __launch_bounds__(kThreads32, kMinB) k_near32s(Near32SymArgs a) 
             // the chunk's reaction: the warps' sums in a fixed order, into slot (tb, ta, gi) at
             // the chunk's positions in tile tb (the field with the reaction's sign)
             __syncthreads();
-            double* dst = a.partial + S.part0 + ((tb * n_slots + ta * S.n_g + gi) * 4) * kTile32 +
-                          (chunk - c0) * kNearChunk;
-            for (int s = tid; s < kNearChunk; s += kThreads32) {
+            const int64_t off = S.part0 + ((sym_slot(S, tb, ta) * S.n_g + gi) * 4) * kTile32;
+            double* dst = a.partial + off + (chunk - c0) * kNearChunk;
+            const bool ok = debug_in_range(off, 4 * kTile32, a.limit, a.status, a.n_status);
+            for (int s = tid; s < kNearChunk && ok; s += kThreads32) {
 #pragma unroll
                 for (int qi = 0; qi < 4; ++qi) {
                     double v = 0.0;
@@ -589,18 +753,22 @@ __global__ void __launch_bounds__(kThreads32, kMinB) k_near32s(Near32SymArgs a) 
     // slot is defined
     if (!diag)
         for (int64_t c = c1; c < c0 + kTgt32; ++c) {
-            double* dst = a.partial + S.part0 + ((tb * n_slots + ta * S.n_g + gi) * 4) * kTile32 + (c - c0) * kNearChunk;
-            for (int s = tid; s < kNearChunk; s += kThreads32)
+            const int64_t off = S.part0 + ((sym_slot(S, tb, ta) * S.n_g + gi) * 4) * kTile32;
+            double* dst = a.partial + off + (c - c0) * kNearChunk;
+            const bool ok = debug_in_range(off, 4 * kTile32, a.limit, a.status, a.n_status);
+            for (int s = tid; s < kNearChunk && ok; s += kThreads32)
 #pragma unroll
                 for (int qi = 0; qi < 4; ++qi) dst[qi * kTile32 + s] = 0.0;
         }
     // the action on tile ta: slot (ta, tb, gi)
     {
-        double* dst = a.partial + S.part0 + ((ta * n_slots + tb * S.n_g + gi) * 4) * kTile32;
+        const int64_t off = S.part0 + ((sym_slot(S, ta, tb) * S.n_g + gi) * 4) * kTile32;
+        double* dst = a.partial + off;
+        const bool ok = debug_in_range(off, 4 * kTile32, a.limit, a.status, a.n_status);
 #pragma unroll
         for (int qi = 0; qi < 4; ++qi)
 #pragma unroll
-            for (int j = 0; j < 2; ++j) {
+            for (int j = 0; j < 2 && ok; ++j) {
                 const float2 h = s_acc[qi][j][0][tid], l = s_acc[qi][j][1][tid];
                 dst[qi * kTile32 + (2 * j) * kThreads32 + tid] = (double)h.x + (double)l.x;
                 dst[qi * kTile32 + (2 * j + 1) * kThreads32 + tid] = (double)h.y + (double)l.y;
@@ -624,6 +792,9 @@ struct Near64SymArgs {
     SymSysTable tab;
     int64_t W;
     int* counter;
+    int* status;             // error words (debug bounds checks)
+    int n_status;
+    int64_t limit;           // doubles of the partial buffer (debug bounds checks)
 };
 
 template <int kMinB>
@@ -644,12 +815,9 @@ __global__ void __launch_bounds__(kThreads64, kMinB) k_near64s(Near64SymArgs a) 
     const int64_t local = item - S.item0;
     const int64_t pair = local / S.n_g;
     const int gi = (int)(local - pair * S.n_g);
-    int64_t tb = (int64_t)((sqrt(8.0 * (double)pair + 1.0) - 1.0) * 0.5);
-    while (tb > 0 && tb * (tb + 1) / 2 > pair) --tb;
-    while ((tb + 1) * (tb + 2) / 2 <= pair) ++tb;
-    const int64_t ta = pair - tb * (tb + 1) / 2;
+    int64_t ta, tb;
+    sym_band_pair(S, pair, ta, tb);
     const bool diag = ta == tb;
-    const int64_t n_slots = S.n_tiles * S.n_g;
     const int im0 = gi * S.img_per_g;
     const int nimg = min(S.img_per_g, S.n_img - im0);
     const double4_32a t = a.pk[(S.tile0 + ta) * kTile64 + tid];
@@ -715,15 +883,19 @@ __global__ void __launch_bounds__(kThreads64, kMinB) k_near64s(Near64SymArgs a) 
         }
     }
     {
-        double* dst = a.partial + S.part0 + ((ta * n_slots + tb * S.n_g + gi) * 4) * kTile64 + tid;
+        const int64_t off = S.part0 + ((sym_slot(S, ta, tb) * S.n_g + gi) * 4) * kTile64;
+        double* dst = a.partial + off + tid;
+        if (debug_in_range(off, 4 * kTile64, a.limit, a.status, a.n_status))
 #pragma unroll
-        for (int qi = 0; qi < 4; ++qi) dst[qi * kTile64] = acc[qi];
+            for (int qi = 0; qi < 4; ++qi) dst[qi * kTile64] = acc[qi];
     }
     if (!diag) {
         __syncthreads();
-        double* dst = a.partial + S.part0 + ((tb * n_slots + ta * S.n_g + gi) * 4) * kTile64 + tid;
+        const int64_t off = S.part0 + ((sym_slot(S, tb, ta) * S.n_g + gi) * 4) * kTile64;
+        double* dst = a.partial + off + tid;
+        const bool ok = debug_in_range(off, 4 * kTile64, a.limit, a.status, a.n_status);
 #pragma unroll
-        for (int qi = 0; qi < 4; ++qi) {
+        for (int qi = 0; qi < 4 && ok; ++qi) {
             double v = 0.0;
 #pragma unroll
             for (int w = 0; w < kWarps; ++w) v += s_re[w][qi][tid];
@@ -733,47 +905,74 @@ __global__ void __launch_bounds__(kThreads64, kMinB) k_near64s(Near64SymArgs a) 
     }
 }
 
-// Reduction of the symmetric kernel's slots: target i (packed order, i < n_valid) in tile t
-// of its system adds that system's slots 0 .. n_tiles n_g - 1 of row t; a block takes 32
-// consecutive targets (one tile) and one quantity, its 8 warps every 8th slot, combined in a
-// fixed order.
+// Reduction of the symmetric kernel's slots after one band: target i (packed order, i <
+// n_valid) in tile t of its system adds the slots of row t that the band wrote -- for a band
+// tile its block row and its actions on the tiles after the band, for a later tile its
+// reactions from the band's tiles; tiles before the band have none -- each over the image
+// groups.  A block takes 32 consecutive targets (one tile) and one quantity, its 8 warps every
+// 8th slot, combined in a fixed order; `accumulate` adds to the output of the earlier bands.
 template <int kTile>
 __global__ void __launch_bounds__(32 * kReduceWarps) k_sym_reduce(const double* __restrict__ partial, int64_t n_valid,
                                                                  SymSysTable tab, double* __restrict__ out_phi,
-                                                                 double* __restrict__ out_grad) {
+                                                                 double* __restrict__ out_grad, int accumulate,
+                                                                 int64_t limit, int* status, int n_status) {
     __shared__ double s_part[kReduceWarps][32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int qi = blockIdx.y;
     const int64_t i0 = (int64_t)blockIdx.x * 32;
     const int64_t i = i0 + lane;
     const int64_t T = i0 / kTile;
-    int64_t tile0 = tab.one.tile0, n_slots = tab.one.n_tiles * tab.one.n_g, part0 = tab.one.part0;
-    if (tab.many) {
-        const SymSys& S = tab.many[sym_sys_by_tile(tab, T)];
-        tile0 = S.tile0;
-        n_slots = S.n_tiles * S.n_g;
-        part0 = S.part0;
+    const SymSys S = tab.many ? tab.many[sym_sys_by_tile(tab, T)] : tab.one;
+    const int64_t t = T - S.tile0;
+    if (t < S.a0) return;                   // uniform over the block: no slot of this band
+    const int64_t bw = S.a1 - S.a0, n_out = S.n_tiles - S.a1;
+    // the row's slots as one or two contiguous runs of (slot, image group) entries
+    int64_t r1, n1, r2 = 0, n2 = 0;
+    if (t < S.a1) {
+        r1 = sym_slot(S, t, S.a0);
+        n1 = bw;
+        r2 = n_out > 0 ? sym_slot(S, t, S.a1) : 0;
+        n2 = n_out;
+    } else {
+        r1 = sym_slot(S, t, S.a0);
+        n1 = bw;
     }
-    const int64_t tile = T - tile0;
+    const int64_t e1 = n1 * S.n_g, e_all = e1 + n2 * S.n_g;
     const int loc = (int)(i - T * kTile);
-    const double* base = partial + part0 + (tile * n_slots * 4 + qi) * kTile + loc;
+    const double* base = partial + S.part0 + qi * kTile + loc;
     double acc = 0.0;
     if (i < n_valid)
-        for (int64_t s = warp; s < n_slots; s += kReduceWarps) acc += base[s * 4 * kTile];
+        for (int64_t k = warp; k < e_all; k += kReduceWarps) {
+            const int64_t e = k < e1 ? r1 * S.n_g + k : r2 * S.n_g + (k - e1);
+            if (debug_in_range(S.part0 + e * 4 * kTile, 4 * kTile, limit, status, n_status)) acc += base[e * 4 * kTile];
+        }
     s_part[warp][lane] = acc;
     __syncthreads();
     if (warp == 0 && i < n_valid) {
         double v = s_part[0][lane];
 #pragma unroll
         for (int w = 1; w < kReduceWarps; ++w) v += s_part[w][lane];
-        if (qi == 0)
-            out_phi[i] = v;
-        else if (out_grad)
-            out_grad[3 * i + qi - 1] = v;
+        if (qi == 0) {
+            out_phi[i] = accumulate ? out_phi[i] + v : v;
+        } else if (out_grad) {
+            double& o = out_grad[3 * i + qi - 1];
+            o = accumulate ? o + v : v;
+        }
     }
 }
 
+// size of the partial buffer as the debug bounds checks see it (a test may shrink it)
+int64_t sym_limit(const NearSymLaunch& S) {
+    const int64_t real = (int64_t)S.doubles;
+    return S.debug_limit > 0 && S.debug_limit < real ? S.debug_limit : real;
+}
+
 constexpr int kNear32sMinBlocks = 4;
+// the refined instance holds the offsets' low parts and the correction sums too
+#ifndef PSUM_REFINED_MIN_BLOCKS
+#define PSUM_REFINED_MIN_BLOCKS 4
+#endif
+constexpr int kNear32sRefMinBlocks = PSUM_REFINED_MIN_BLOCKS;
 
 size_t near32s_dyn_smem(int img_per_g) {
     const size_t reaction = (size_t)(kThreads32 / 32) * 4 * 2 * kNearChunk * sizeof(float);
@@ -783,16 +982,19 @@ size_t near32s_dyn_smem(int img_per_g) {
 // the kernel's static and dynamic shared memory together pass the 48 KiB default: allow the
 // largest dynamic size any image group needs
 cudaError_t near32s_allow_smem() {
-    const cudaError_t e = cudaFuncSetAttribute(k_near32s<kNear32sMinBlocks, false>,
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)near32s_dyn_smem(kMaxImages));
+    const int bytes = (int)near32s_dyn_smem(kMaxImages);
+    cudaError_t e = cudaFuncSetAttribute(k_near32s<kNear32sMinBlocks, false, false>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_near32s<kNear32sMinBlocks, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)near32s_dyn_smem(kMaxImages));
+    e = cudaFuncSetAttribute(k_near32s<kNear32sRefMinBlocks, false, true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_near32s<kNear32sMinBlocks, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                bytes);
 }
 
 cudaError_t launch_near32s(const float4* pk_hi, const float4* pk_lo, const double* org, const double* shifts,
-                           double* partial, const NearSymLaunch& S, cudaStream_t st, bool ff) {
+                           double* partial, const NearSymLaunch& S, cudaStream_t st, bool ff, bool refine) {
     if (!S.counter || !S.status || S.n_status < 1 || S.max_ipg < 1) return cudaErrorInvalidValue;
     if (S.W <= 0) return cudaSuccess;
     const cudaError_t ea = near32s_allow_smem();
@@ -801,35 +1003,47 @@ cudaError_t launch_near32s(const float4* pk_hi, const float4* pk_lo, const doubl
     a.pk_hi = pk_hi; a.pk_lo = pk_lo; a.org = org; a.shifts = shifts; a.partial = partial;
     a.tab = S.tab; a.W = S.W; a.max_ipg = S.max_ipg;
     a.counter = S.counter; a.status = S.status; a.n_status = S.n_status; a.inject = S.inject;
+    a.limit = sym_limit(S);
     const cudaError_t e = cudaMemsetAsync(S.counter, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
+    const size_t smem = near32s_dyn_smem(S.max_ipg);
     if (ff)
-        k_near32s<kNear32sMinBlocks, true><<<(unsigned)S.G, kThreads32, near32s_dyn_smem(S.max_ipg), st>>>(a);
+        k_near32s<kNear32sMinBlocks, true, false><<<(unsigned)S.G, kThreads32, smem, st>>>(a);
+    else if (refine)
+        k_near32s<kNear32sRefMinBlocks, false, true><<<(unsigned)S.G, kThreads32, smem, st>>>(a);
     else
-        k_near32s<kNear32sMinBlocks, false><<<(unsigned)S.G, kThreads32, near32s_dyn_smem(S.max_ipg), st>>>(a);
+        k_near32s<kNear32sMinBlocks, false, false><<<(unsigned)S.G, kThreads32, smem, st>>>(a);
     return cudaGetLastError();
 }
 
-int near32s_occupancy_ctas(int img_per_g, bool ff) {
+int near32s_occupancy_ctas(int img_per_g, bool ff, bool refine) {
     int nb = 0;
     near32s_allow_smem();
+    const size_t smem = near32s_dyn_smem(img_per_g);
     if (ff)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_near32s<kNear32sMinBlocks, true>, kThreads32,
-                                                      near32s_dyn_smem(img_per_g));
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_near32s<kNear32sMinBlocks, true, false>, kThreads32,
+                                                      smem);
+    else if (refine)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_near32s<kNear32sRefMinBlocks, false, true>, kThreads32,
+                                                      smem);
     else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_near32s<kNear32sMinBlocks, false>, kThreads32,
-                                                      near32s_dyn_smem(img_per_g));
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_near32s<kNear32sMinBlocks, false, false>, kThreads32,
+                                                      smem);
     return nb < 1 ? 1 : nb;
 }
 
 cudaError_t launch_sym_reduce(const double* partial, int64_t n_valid, const NearSymLaunch& S, double* out_phi,
-                              double* out_grad, cudaStream_t st, bool fp64) {
+                              double* out_grad, cudaStream_t st, bool fp64, bool accumulate) {
     if (n_valid <= 0) return cudaSuccess;
     const dim3 grid((unsigned)((n_valid + 31) / 32), 4u);
+    const int acc = accumulate ? 1 : 0;
+    const int64_t lim = sym_limit(S);
     if (fp64)
-        k_sym_reduce<kTile64><<<grid, 32 * kReduceWarps, 0, st>>>(partial, n_valid, S.tab, out_phi, out_grad);
+        k_sym_reduce<kTile64><<<grid, 32 * kReduceWarps, 0, st>>>(partial, n_valid, S.tab, out_phi, out_grad, acc, lim,
+                                                                S.status, S.n_status);
     else
-        k_sym_reduce<kTile32><<<grid, 32 * kReduceWarps, 0, st>>>(partial, n_valid, S.tab, out_phi, out_grad);
+        k_sym_reduce<kTile32><<<grid, 32 * kReduceWarps, 0, st>>>(partial, n_valid, S.tab, out_phi, out_grad, acc, lim,
+                                                                S.status, S.n_status);
     return cudaGetLastError();
 }
 
@@ -841,6 +1055,7 @@ cudaError_t launch_near64s(const double4_32a* pk, const double* shifts, double* 
     if (S.W <= 0) return cudaSuccess;
     Near64SymArgs a;
     a.pk = pk; a.shifts = shifts; a.partial = partial; a.tab = S.tab; a.W = S.W; a.counter = S.counter;
+    a.status = S.status; a.n_status = S.n_status; a.limit = sym_limit(S);
     const cudaError_t e = cudaMemsetAsync(S.counter, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
     k_near64s<kNear64sMinBlocks><<<(unsigned)S.G, kThreads64, 0, st>>>(a);

@@ -318,11 +318,15 @@ static int build_check_layers(Plan& pl, const double d[3]) {
         pack_groups32(pl.Y, slot, (int)(slot.size() / kNearChunk), pk, org);
         const size_t ng = slot.size() / kNearChunk;
         std::vector<int> gmask(ng, 0);   // classes present in each group
+        int last = cls[slot[0]];         // slot 0 holds a point: M >= 1
         for (size_t i = 0; i < slot.size(); ++i) {
-            const int c = slot[i] >= 0 ? cls[slot[i]] : 0;
+            // a padding slot takes the class of the last point before it, which its group
+            // holds unless the whole group is padding (it then holds that class alone)
+            const int c = slot[i] >= 0 ? cls[slot[i]] : last;
+            last = c;
             pk[2 * i + 1].z = (float)c;
             pk[2 * i + 1].w = (float)c;
-            gmask[i / kNearChunk] |= 1 << c;     // padding slots read class 0
+            gmask[i / kNearChunk] |= 1 << c;
         }
         // per (group, class): centre and radius of the class's points in the group, for the
         // near-unit test (a group at a class boundary spans two caps of the sphere)

@@ -33,6 +33,10 @@ constexpr int kStatNonNeutral = 1;
 constexpr int kStatOutOfBox = 2;
 constexpr int kStatNonFinite = 4;
 constexpr int kStatTimeout = 8;
+constexpr int kStatBounds = 16;    // a debug-build bounds check refused an access (PSUM_DEBUG_CHECKS)
+#ifndef PSUM_DEBUG_CHECKS
+#define PSUM_DEBUG_CHECKS 0        // 1: range checks on the pair kernels' partial sums
+#endif
 
 // 0-based stacking of Eq. 1.8: t = n(n+1) + m
 __host__ __device__ __forceinline__ int sh_index(int n, int m) { return n * (n + 1) + m; }
@@ -250,6 +254,9 @@ struct Plan {
     int* d_status = nullptr;
     int* h_status = nullptr;        // pinned
 
+    // test hook: bytes of symmetric-kernel partial slots per band (0: kSymBandBytes)
+    size_t sym_band_bytes = 0;
+
     // scratch, grown on demand
     DevBuf scratch;
     // pinned host staging and device staging for psum_eval_host
@@ -375,6 +382,7 @@ struct NearPlanLaunch {
     int* status = nullptr;        // device error words the pair kernel may flag (kStatTimeout)
     int n_status = 0;
     int inject = 0;               // test hook: arm the chunk-copy barrier for bytes that never come
+    int64_t debug_limit = 0;      // test hook of the debug bounds checks: a smaller partial buffer (doubles)
     int max_contrib;              // partial slots per tile
     int max_img;                  // largest image count of any system (shared-memory sizing)
     int64_t n_tiles;              // rows of the partial buffer
@@ -382,14 +390,26 @@ struct NearPlanLaunch {
 };
 
 // The symmetric charge kernel (FP32C, block image sets): work items are (system, tile pair
-// (a <= b), group of images); a system's partial block holds n_tiles x (n_tiles n_g) slots of
-// 4 x kTile32 doubles.  The targets are the system's charges, packed in whole tiles from
+// (a <= b), group of images).  The targets are the system's charges, packed in whole tiles from
 // global tile tile0 (groups 4 tile0 ..); its source chunks are the first n_chunks groups.
+//
+// Partial sums: the action of pair (a, b) on tile a and its reaction on tile b each go to a slot
+// of 4 x tile doubles per image group, one writer per slot.  A launch covers the BAND of row
+// tiles a0 <= a < a1 (pairs (a, b), a <= b < n_tiles); with slot (t, u) meaning "tile t's
+// targets, from tile u":
+//   * the square block t, u in [a0, a1): the action of (a, b) at (a, b) and its reaction at
+//     (b, a), complementary triangles;
+//   * actions of a band tile on the tiles b >= a1 after it, (a - a0) x (n_tiles - a1);
+//   * reactions on those tiles, (b - a1) x (a - a0).
+// One band covering every tile is the full square (n_tiles^2 slots).  Larger systems run several
+// bands in turn, each reduced into float64 accumulators before the next, so the partial buffer
+// is bounded by its first (largest) band while every sum keeps a fixed order.
 struct SymSys {
     int64_t item0;            // first work item
     int64_t tile0;            // first (global) tile
     int64_t n_tiles, n_chunks;
     int64_t part0;            // first double of the system's partial block
+    int64_t a0, a1;           // band of row tiles
     int shift0, n_img;        // image vectors shift0 .. shift0 + n_img - 1
     int n_g, img_per_g;       // image groups per tile pair and images per group
 };
@@ -399,11 +419,41 @@ struct SymSysTable {
     int n;
 };
 
+// tile pairs of the band: sum over a0 <= a < a1 of (n_tiles - a)
+__host__ __device__ __forceinline__ int64_t sym_band_pairs(const SymSys& s) {
+    const int64_t bw = s.a1 - s.a0;
+    return bw * s.n_tiles - (s.a0 + s.a1 - 1) * bw / 2;
+}
 __host__ __device__ __forceinline__ int64_t sym_sys_items(const SymSys& s) {
-    return s.n_tiles * (s.n_tiles + 1) / 2 * s.n_g;
+    return sym_band_pairs(s) * s.n_g;
+}
+__host__ __device__ __forceinline__ int64_t sym_band_slots(const SymSys& s) {
+    const int64_t bw = s.a1 - s.a0, n_out = s.n_tiles - s.a1;
+    return bw * bw + 2 * bw * n_out;
 }
 __host__ __device__ __forceinline__ size_t sym_sys_doubles(const SymSys& s, int tile) {
-    return (size_t)s.n_tiles * (size_t)s.n_tiles * (size_t)s.n_g * 4 * (size_t)tile;
+    return (size_t)sym_band_slots(s) * (size_t)s.n_g * 4 * (size_t)tile;
+}
+// slot of tile t's targets for the contribution from tile u (see above)
+__host__ __device__ __forceinline__ int64_t sym_slot(const SymSys& s, int64_t t, int64_t u) {
+    const int64_t bw = s.a1 - s.a0, n_out = s.n_tiles - s.a1;
+    if (t < s.a1) return u < s.a1 ? (t - s.a0) * bw + (u - s.a0) : bw * bw + (t - s.a0) * n_out + (u - s.a1);
+    return bw * bw + bw * n_out + (t - s.a1) * bw + (u - s.a0);
+}
+// rows of the band's pairs before row a: sum over a0 <= a' < a of (n_tiles - a')
+__host__ __device__ __forceinline__ int64_t sym_band_row_start(const SymSys& s, int64_t a) {
+    const int64_t k = a - s.a0;
+    return k * s.n_tiles - (s.a0 + a - 1) * k / 2;
+}
+// the band's pair with index p: row a (largest with row start <= p) and column b >= a
+__host__ __device__ __forceinline__ void sym_band_pair(const SymSys& s, int64_t p, int64_t& a, int64_t& b) {
+    int64_t lo = s.a0, hi = s.a1 - 1;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) >> 1;
+        if (sym_band_row_start(s, mid) <= p) lo = mid; else hi = mid - 1;
+    }
+    a = lo;
+    b = a + (p - sym_band_row_start(s, a));
 }
 
 struct NearSymLaunch {
@@ -415,6 +465,7 @@ struct NearSymLaunch {
     int* status = nullptr;
     int n_status = 0;
     int inject = 0;
+    int64_t debug_limit = 0;       // test hook of the debug bounds checks: a smaller partial buffer (doubles)
 };
 
 // Image groups: the fewest (1, 3, 9, ... up to one image per group) that give at least
@@ -430,7 +481,26 @@ constexpr int kSymItemsPerCta = PSUM_SYM_ITEMS_PER_CTA;
 constexpr int64_t kSymMinTiles = 12;
 constexpr int64_t kSymMinTilesFF = 6;
 constexpr int64_t kSymMinTiles64 = 1;
-constexpr size_t kSymMaxPartialBytes = (size_t)8 << 30;       // and a partial buffer of at most 8 GiB
+constexpr size_t kSymMaxPartialBytes = (size_t)8 << 30;       // batches: a partial buffer of at most 8 GiB
+// single systems: bands of row tiles whose partial slots fit this many bytes (one band up to
+// 1.5 GiB: about 300 tiles of 512 charges in float32, 600 of 128 in float64)
+#ifndef PSUM_SYM_BAND_BYTES
+#define PSUM_SYM_BAND_BYTES ((size_t)3 << 29)
+#endif
+constexpr size_t kSymBandBytes = PSUM_SYM_BAND_BYTES;
+
+// The widest equal band width whose first (largest) band -- bw^2 + 2 bw (n_tiles - bw) slots --
+// fits `cap` bytes of slots of `slot_bytes` each; n_tiles when the whole square fits.
+inline int64_t sym_band_width(int64_t n_tiles, size_t slot_bytes, size_t cap) {
+    const int64_t cap_slots = (int64_t)(cap / (slot_bytes ? slot_bytes : 1));
+    if (n_tiles * n_tiles <= cap_slots) return n_tiles;
+    const double n = (double)n_tiles, c = (double)cap_slots;
+    int64_t bw = (int64_t)(n - std::sqrt(n * n - c));
+    if (bw < 1) bw = 1;
+    while (bw > 1 && 2 * bw * n_tiles - bw * bw > cap_slots) --bw;
+    while (bw + 1 < n_tiles && 2 * (bw + 1) * n_tiles - (bw + 1) * (bw + 1) <= cap_slots) ++bw;
+    return bw;
+}
 
 // `sys` holds tile0, n_tiles, n_chunks, shift0 and n_img of every system; the rest is filled
 // here.  G is the number of resident CTAs.
@@ -447,6 +517,8 @@ inline NearSymLaunch sym_partition(std::vector<SymSys>& sys, int64_t G, int tile
     int64_t item = 0;
     size_t part = 0;
     for (SymSys& s : sys) {
+        s.a0 = 0;
+        s.a1 = s.n_tiles;
         const int g = ng < s.n_img ? ng : s.n_img;
         s.img_per_g = (s.n_img + g - 1) / g;
         s.n_g = (s.n_img + s.img_per_g - 1) / s.img_per_g;
@@ -541,6 +613,8 @@ struct psum_plan_s {
     int64_t launches = 0;       // kernels queued so far
     bool profile = false;
     bool inject_timeout = false;  // test hook: the charge pair kernel's copy waits run out
+    int64_t debug_limit = 0;      // test hook: the partial buffers' size as the debug bounds checks see it
+    int fail_allocs = 0;          // test hook: the next scratch allocations fail as if out of memory
     cudaEvent_t ev[6] = {};
     // psum_eval_graph: one evaluation captured into a CUDA graph, replayed while the
     // arguments and the scratch buffer stay the same

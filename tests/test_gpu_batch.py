@@ -112,3 +112,49 @@ def test_batch_reports_status_per_system():
         assert torch.isnan(phi[sl]).all() and torch.isfinite(phi[:pb.offsets[2]]).all()
     finally:
         pb.close()
+
+
+def _many(B, seed):
+    """B small neutral +-1 systems (p = 8, M = 200), boxes (1, U[1,2], U[1,2]) with the batch
+    workload's near-block rule."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for b in range(B):
+        N = 2 * int(rng.integers(30, 400))
+        d = (1.0, float(rng.uniform(1.0, 2.0)), float(rng.uniform(1.0, 2.0)))
+        x = rng.uniform(-0.5, 0.5, size=(N, 3)) * np.asarray(d)
+        q = np.concatenate([np.ones(N // 2), -np.ones(N // 2)])
+        rng.shuffle(q)
+        out.append(W.System(x, q, d, 8, 200, name=f"many{seed}_{b}_N{N}", K=W.batch_near_block(d)))
+    return out
+
+
+@pytest.mark.parametrize("precision,nsys", [("fp32c", 1024), ("ff", 300)])
+def test_batches_beyond_256_systems(precision, nsys):
+    # more than 256 systems sort by the Morton key, then stably by the system: every system's
+    # result equals its own evaluation on the same plan (to the kernels' rounding) and, on a
+    # sample of systems, the oracle
+    systems = _many(nsys, seed=nsys)
+    pb = B.PeriodicBatch(systems, precision=precision)
+    try:
+        x, q = _cat(systems)
+        phi, g = pb(x, q, use_graph=True)
+        phi, g = phi.cpu().numpy(), g.cpu().numpy()
+        tol = TOL["fp64"] if precision == "ff" else TOL["fp32c"]
+        for b, s in enumerate(systems):
+            p1 = torch.empty(s.N, dtype=torch.float64, device="cuda")
+            g1 = torch.empty((s.N, 3), dtype=torch.float64, device="cuda")
+            B.psum_eval(pb.plans[b], torch.as_tensor(s.x, device="cuda"), torch.as_tensor(s.q, device="cuda"), p1, g1,
+                        check=True)
+            sl = slice(pb.offsets[b], pb.offsets[b + 1])
+            assert_close(phi[sl], p1.cpu().numpy(), tol, (b, s.name, "phi"))
+            assert_close(g[sl], g1.cpu().numpy(), tol, (b, s.name, "grad"))
+        rng = np.random.default_rng(nsys + 1)
+        for b in list(rng.choice(nsys, size=6, replace=False)) + [0, nsys - 1]:
+            s = systems[b]
+            ref = _oracle(s)
+            sl = slice(pb.offsets[b], pb.offsets[b + 1])
+            assert_close(phi[sl], ref["phi"], tol, (b, s.name, "phi vs oracle"))
+            assert_close(g[sl], ref["grad"], tol, (b, s.name, "grad vs oracle"))
+    finally:
+        pb.close()

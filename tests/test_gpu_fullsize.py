@@ -19,20 +19,27 @@ def _dev(a):
     return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
 
 
-# The float32 path's error grows with the number of terms a target sums: each of the
-# 27 x 200k terms carries a rounding of a few float32 ulps of its own size, so the error of
-# the sum is about eps sqrt(sum of squared terms), here ~2e-4 against a potential of rms ~100
-# (dominated by each charge's partner at 0.01).  Measured against the float-float path:
-# epsilon_2(phi) 6.8e-7, 1.1e-6 and 1.9e-6 for 2e4, 6e4 and 2e5 charges, while the field
-# stays at 2.1-2.6e-7.  The float-float path holds the float64 tolerance at full size.
-TOL = {"fp32c": {"phi": 3e-6, "grad": 1e-6, "adj": 3e-6}, "ff": {"phi": 1e-10, "grad": 1e-10, "adj": 1e-9}}
+# The float32 path's error grows with the cancellation of the near sum: each of the
+# 27 x 200k terms a charge sums carries about one float32 ulp of its own size (offsets, r^2,
+# rsqrt, product), so the potential's error is about u sqrt(sum of squared terms), here
+# ~20 times the potential's rms (~100, dominated by each charge's partner at 0.01).  Measured
+# against the float-float path: epsilon_2(phi) 5.9e-7, 1.0e-6 and 1.65e-6 for 2e4, 6e4 and 2e5
+# charges with the fast terms, 3.5e-7, 5.6e-7 and 8.7e-7 with the refined ones
+# (PSUM_TERMS_REFINED: float-float offsets and 1/r fused into the sums), while the field stays
+# at 2.1-2.6e-7.  The float-float path holds the float64 tolerance at full size.
+TOL = {"fp32c": {"phi": 1e-6, "grad": 1e-6, "adj": 1e-6}, "ff": {"phi": 1e-10, "grad": 1e-10, "adj": 1e-9}}
+
+DIPOLE_CASES = [("fp32c", "refined"), ("ff", "fast"),
+                pytest.param("fp32c", "fast", marks=pytest.mark.xfail(
+                    strict=False, reason="fast float32 terms: eps2(phi) 1.65e-6 at 2e5 dipole charges, "
+                                         "the per-term rounding floor; PSUM_TERMS_REFINED meets 1e-6"))]
 
 
-@pytest.mark.parametrize("precision", ["fp32c", "ff"])
-def test_dipole_system_forward_and_adjoint_on_sampled_charges(precision):
+@pytest.mark.parametrize("precision,terms", DIPOLE_CASES)
+def test_dipole_system_forward_and_adjoint_on_sampled_charges(precision, terms):
     s = W.config(5)                                   # 100k tight dipoles, 200k charges
     tol = TOL[precision]
-    pc = B.PeriodicCoulomb(s.d, s.p, s.M, precision=precision)
+    pc = B.PeriodicCoulomb(s.d, s.p, s.M, precision=precision, terms=terms)
     try:
         x, q = _dev(s.x), _dev(s.q)
         phi, g = pc(x, q)
@@ -115,8 +122,8 @@ def test_symmetric_float64_class_kernels_at_50k_charges_on_sampled_targets(preci
 
 
 def test_symmetric_kernel_at_300k_charges_on_sampled_targets():
-    # 586 tiles: 5.6 GB of tile-pair partial sums, 172 000 work items (the largest FP32C
-    # systems below the 8 GiB cap); 1024 sampled charges against the oracle
+    # 586 tiles, 172 000 work items: 5.6 GB of tile-pair partial sums in one band, run as bands
+    # of 1.5 GiB; 1024 sampled charges against the oracle
     s = W.uniform_gauss(N=300_000, d=(1.0, 1.5, 2.0), p=8, M=200, seed=22)
     pc = B.PeriodicCoulomb(s.d, s.p, s.M, precision="fp32c")
     try:
