@@ -65,6 +65,7 @@ extern "C" {
 #define PSUM_ERR_NOMEM       7  /* host or device allocation failed */
 #define PSUM_ERR_NONFINITE   8  /* a result is not finite (e.g. two charges closer than FP32 resolves) */
 #define PSUM_ERR_INTERNAL    9  /* a debug build's bounds check refused an access (psum_debug_checks) */
+#define PSUM_ERR_IO         10  /* a plan file cannot be read or written, or does not match (psum_plan_load) */
 
 /* ---- options ------------------------------------------------------------ */
 #define PSUM_FP64   0  /* near-field pair sum in float64 */
@@ -184,6 +185,20 @@ void psum_opts_default(psum_opts *o);
  * *out is set only on success.  psum_plan_create uses FP64 and the defaults. */
 int psum_plan_create(double d1, double d2, double d3, int p, int M, psum_plan_t *out);
 int psum_plan_create_ex(const psum_opts *o, psum_plan_t *out);
+
+/* Keep algorithm "set"'s factorisation (Sec. 2.1 recommends storing the decomposition, and the
+ * set time is the cost of a new plan, Sec. 4.2): psum_plan_save writes the plan's options, the
+ * fingerprint of its check points and partners, the rank, the condition estimate and the
+ * (P-1) x M pseudo-inverse to `path`, with a checksum; psum_plan_load reads such a file and builds
+ * the plan without factoring A again (check points, box integrals and tables are recomputed: they
+ * are cheap and deterministic).  The loaded plan evaluates exactly as the saved one.  Errors:
+ * PSUM_ERR_ARG for NULL arguments; PSUM_ERR_IO when the file cannot be written or read, is
+ * truncated, fails its checksum or magic word, was written by a library with another psum_opts
+ * layout, or its check points do not hash to the ones this library computes for its options;
+ * otherwise those of psum_plan_create_ex.  *out is set only on success.  Host files are
+ * little-endian IEEE doubles. */
+int psum_plan_save(psum_plan_t plan, const char *path);
+int psum_plan_load(const char *path, psum_plan_t *out);
 
 /* Algorithm "get" (Sec. 2.3.2) with Y0 = X0 (Remark 1): phi[i] and grad[3i..3i+2]
  * at every charge.  x (N x 3), q (N), phi (N) and grad (N x 3, may be NULL) are

@@ -23,6 +23,7 @@ PSUM_ERR_TIMEOUT = 6
 PSUM_ERR_NOMEM = 7
 PSUM_ERR_NONFINITE = 8
 PSUM_ERR_INTERNAL = 9
+PSUM_ERR_IO = 10
 
 PSUM_FP64 = 0
 PSUM_FP32C = 1
@@ -95,6 +96,8 @@ def load(build_if_needed: bool = True):
     lib.psum_plan_create.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int,
                                      ctypes.POINTER(_vp)]
     lib.psum_plan_create_ex.argtypes = [ctypes.POINTER(psum_opts), ctypes.POINTER(_vp)]
+    lib.psum_plan_save.argtypes = [_vp, ctypes.c_char_p]
+    lib.psum_plan_load.argtypes = [ctypes.c_char_p, ctypes.POINTER(_vp)]
     lib.psum_eval.argtypes = [_vp, ctypes.c_int64, _vp, _vp, _vp, _vp, _vp]
     lib.psum_debug_inject_timeout.argtypes = [_vp, ctypes.c_int]
     lib.psum_eval_graph.argtypes = [_vp, ctypes.c_int64, _vp, _vp, _vp, _vp, _vp]
@@ -131,7 +134,7 @@ def load(build_if_needed: bool = True):
     lib.psum_destroy.restype = None
     lib.psum_strerror.argtypes = [ctypes.c_int]
     lib.psum_strerror.restype = ctypes.c_char_p
-    for name in ("psum_plan_create", "psum_plan_create_ex", "psum_eval", "psum_eval_host", "psum_eval_noalloc",
+    for name in ("psum_plan_create", "psum_plan_create_ex", "psum_plan_save", "psum_plan_load", "psum_eval", "psum_eval_host", "psum_eval_noalloc",
                  "psum_sync",
                  "psum_get_coeffs", "psum_plan_info", "psum_pair_kernel", "psum_check_form",
                  "psum_scratch_bytes", "psum_debug_band_bytes", "psum_debug_fail_allocs",
@@ -204,6 +207,18 @@ def psum_plan_create_ex(d, p: int, M: int, precision="fp64", mean="zero", K=(1, 
     o.mean_mode = MEAN_MODES[mean] if isinstance(mean, str) else int(mean)
     h = _vp()
     _check(load().psum_plan_create_ex(ctypes.byref(o), ctypes.byref(h)), "psum_plan_create_ex")
+    return h
+
+
+def psum_plan_save(plan, path) -> None:
+    """Write the plan's options and factorisation to a file (algorithm "set" kept, Sec. 2.1)."""
+    _check(load().psum_plan_save(plan, os.fsencode(path)), "psum_plan_save")
+
+
+def psum_plan_load(path):
+    """A plan from a file of psum_plan_save, without factoring the fitting matrix again."""
+    h = _vp()
+    _check(load().psum_plan_load(os.fsencode(path), ctypes.byref(h)), "psum_plan_load")
     return h
 
 

@@ -583,13 +583,24 @@ void psum_opts_default(psum_opts* o) {
     o->fp32_terms = PSUM_TERMS_FAST;
 }
 
-int psum_plan_create_ex(const psum_opts* o, psum_plan_t* out) {
+}  // extern "C"
+
+namespace {
+
+// Plan creation; `stored` (may be null) carries a factorisation read by psum_plan_load.
+int create_plan(const psum_opts* o, psum_plan_t* out, const Plan* stored) {
     if (!out || !valid_opts(o)) return PSUM_ERR_ARG;
     psum_opts oo = *o;
     if (oo.points == PSUM_POINTS_GAUSS) oo.M = (oo.p + 1) * (2 * oo.p + 1);
     if (oo.basis == PSUM_BASIS_RBF && oo.n_rbf == 0) oo.n_rbf = 256;
     psum_plan_s* h = new (std::nothrow) psum_plan_s();
     if (!h) return PSUM_ERR_NOMEM;
+    if (stored) {
+        h->pl.preset_pinv = stored->preset_pinv;
+        h->pl.preset_rank = stored->preset_rank;
+        h->pl.preset_cond = stored->preset_cond;
+        h->pl.preset_geom = stored->preset_geom;
+    }
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) {
         delete h;
@@ -604,9 +615,96 @@ int psum_plan_create_ex(const psum_opts* o, psum_plan_t* out) {
         delete h;
         return st;
     }
+    h->pl.preset_pinv.clear();
+    h->pl.preset_pinv.shrink_to_fit();
     for (auto& e : h->ev) cudaEventCreate(&e);
     *out = h;
     return PSUM_OK;
+}
+
+// Plan files: a magic word, the size of psum_opts, the plan's options, the fingerprint of its
+// check points, the rank and condition estimate, the (P-1) x M pseudo-inverse, and an FNV-1a
+// checksum of all that.  Little-endian IEEE doubles as the host writes them.
+constexpr char kPlanMagic[8] = {'P', 'S', 'U', 'M', 'P', 'L', 'N', '1'};
+
+uint64_t fnv1a(const unsigned char* p, size_t n, uint64_t h = 1469598103934665603ull) {
+    for (size_t i = 0; i < n; ++i) {
+        h ^= p[i];
+        h *= 1099511628211ull;
+    }
+    return h;
+}
+
+}  // namespace
+
+extern "C" {
+
+int psum_plan_create_ex(const psum_opts* o, psum_plan_t* out) { return create_plan(o, out, nullptr); }
+
+int psum_plan_save(psum_plan_t h, const char* path) {
+    if (!h || !path) return PSUM_ERR_ARG;
+    const Plan& pl = h->pl;
+    std::vector<unsigned char> buf;
+    auto put = [&buf](const void* p, size_t n) {
+        const unsigned char* c = (const unsigned char*)p;
+        buf.insert(buf.end(), c, c + n);
+    };
+    const uint32_t ob = (uint32_t)sizeof(psum_opts);
+    const int32_t rank = pl.rank;
+    const uint64_t npinv = pl.pinv.size();
+    put(kPlanMagic, sizeof kPlanMagic);
+    put(&ob, sizeof ob);
+    put(&pl.opt, sizeof pl.opt);
+    put(&pl.geom_hash, sizeof pl.geom_hash);
+    put(&rank, sizeof rank);
+    put(&pl.cond_est, sizeof pl.cond_est);
+    put(&npinv, sizeof npinv);
+    put(pl.pinv.data(), sizeof(double) * npinv);
+    const uint64_t sum = fnv1a(buf.data(), buf.size());
+    put(&sum, sizeof sum);
+    FILE* f = std::fopen(path, "wb");
+    if (!f) return PSUM_ERR_IO;
+    const size_t wrote = std::fwrite(buf.data(), 1, buf.size(), f);
+    const int closed = std::fclose(f);
+    return wrote == buf.size() && closed == 0 ? PSUM_OK : PSUM_ERR_IO;
+}
+
+int psum_plan_load(const char* path, psum_plan_t* out) {
+    if (!path || !out) return PSUM_ERR_ARG;
+    FILE* f = std::fopen(path, "rb");
+    if (!f) return PSUM_ERR_IO;
+    std::vector<unsigned char> buf;
+    unsigned char chunk[1 << 16];
+    size_t n;
+    while ((n = std::fread(chunk, 1, sizeof chunk, f)) > 0) buf.insert(buf.end(), chunk, chunk + n);
+    std::fclose(f);
+    size_t off = 0;
+    auto get = [&](void* p, size_t k) {
+        if (off + k > buf.size()) return false;
+        std::memcpy(p, buf.data() + off, k);
+        off += k;
+        return true;
+    };
+    char magic[8];
+    uint32_t ob = 0;
+    psum_opts o;
+    Plan stored;
+    int32_t rank = 0;
+    uint64_t npinv = 0, sum = 0;
+    if (!get(magic, sizeof magic) || std::memcmp(magic, kPlanMagic, sizeof magic) != 0) return PSUM_ERR_IO;
+    if (!get(&ob, sizeof ob) || ob != sizeof(psum_opts) || !get(&o, sizeof o)) return PSUM_ERR_IO;
+    if (!get(&stored.preset_geom, sizeof stored.preset_geom) || !get(&rank, sizeof rank) ||
+        !get(&stored.preset_cond, sizeof stored.preset_cond) || !get(&npinv, sizeof npinv))
+        return PSUM_ERR_IO;
+    if (npinv == 0 || npinv > (uint64_t)1 << 32 || off + sizeof(double) * npinv + sizeof sum != buf.size())
+        return PSUM_ERR_IO;
+    stored.preset_pinv.resize(npinv);
+    get(stored.preset_pinv.data(), sizeof(double) * npinv);
+    const uint64_t expect = fnv1a(buf.data(), off);
+    if (!get(&sum, sizeof sum) || sum != expect) return PSUM_ERR_IO;
+    if (!valid_opts(&o)) return PSUM_ERR_IO;
+    stored.preset_rank = rank;
+    return create_plan(&o, out, &stored);
 }
 
 int psum_plan_create(double d1, double d2, double d3, int p, int M, psum_plan_t* out) {
@@ -955,6 +1053,7 @@ const char* psum_strerror(int s) {
         case PSUM_ERR_NOMEM: return "out of memory";
         case PSUM_ERR_NONFINITE: return "a result or charge is not finite";
         case PSUM_ERR_INTERNAL: return "an internal bounds check refused an access (debug build)";
+        case PSUM_ERR_IO: return "a plan file cannot be read or written, or does not match this library";
         default: return "unknown status";
     }
 }

@@ -451,7 +451,32 @@ int build_plan(const psum_opts& o, Plan& pl) {
             for (int t = 1; t < pl.P; ++t) A[(size_t)(t - 1) * M + l] = b1[t] - b2[t];
         }
     }
-    int st = qr_pseudo_inverse(A, M, n, pl.pinv, pl.rank, pl.cond_est);               // step 5
+    // the geometry's fingerprint: a stored factorisation is only taken for the same A
+    uint64_t h = 1469598103934665603ull;
+    auto mix = [&h](const std::vector<double>& v) {
+        for (double x : v) {
+            uint64_t b;
+            std::memcpy(&b, &x, sizeof b);
+            for (int k = 0; k < 8; ++k) {
+                h ^= (b >> (8 * k)) & 0xffu;
+                h *= 1099511628211ull;
+            }
+        }
+    };
+    mix(pl.Y);
+    mix(pl.Yt);
+    mix(pl.Xs);
+    pl.geom_hash = h;
+    int st = PSUM_OK;
+    if (!pl.preset_pinv.empty()) {                                                    // step 5, stored
+        if (pl.preset_geom != pl.geom_hash || pl.preset_pinv.size() != (size_t)n * M) return PSUM_ERR_IO;
+        pl.pinv = pl.preset_pinv;
+        pl.rank = pl.preset_rank;
+        pl.cond_est = pl.preset_cond;
+        if (pl.rank < n) return PSUM_ERR_RANK;
+    } else {
+        st = qr_pseudo_inverse(A, M, n, pl.pinv, pl.rank, pl.cond_est);               // step 5
+    }
     if (st != PSUM_OK) return st;
     if (rbf) {                                                                        // step 6
         // the box mean of 1/|y - x_t| is the single box's Newtonian potential at x_t over V0

@@ -219,6 +219,13 @@ struct Plan {
     std::vector<double> pinv;       // (P-1) x M pseudo-inverse of A (row-major)
     std::vector<double> Rbox;       // P box integrals R_t^(0)
     std::vector<double> Xs;         // RBF basis: n_rbf centres x 3
+    // a stored factorisation (psum_plan_load): when preset_pinv is not empty, algorithm "set"
+    // takes it instead of factoring A, after checking that the geometry hashes the same
+    std::vector<double> preset_pinv;
+    int preset_rank = 0;
+    double preset_cond = 0.0;
+    uint64_t preset_geom = 0;
+    uint64_t geom_hash = 0;         // FNV-1a of the check points and their partners (bit patterns)
     int self_image = 0;             // index of the zero image vector in `shifts`
 
     // check targets (2M points) as the near kernels consume them

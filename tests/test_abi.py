@@ -30,7 +30,7 @@ def test_library_exports_every_declared_symbol():
 
 def test_strerror_and_defaults_without_gpu():
     assert B.psum_strerror(B.PSUM_OK) == "ok"
-    for s in range(1, 9):
+    for s in range(1, 11):
         assert B.psum_strerror(s) and B.psum_strerror(s) != "unknown status"
     assert B.psum_strerror(99) == "unknown status"
     o = B.psum_opts_default()
@@ -120,3 +120,28 @@ def test_invalid_check_form_is_rejected(check_form, prec, lam):
     o.check_form = check_form
     h = ctypes.c_void_p()
     assert B.load().psum_plan_create_ex(ctypes.byref(o), ctypes.byref(h)) == B.PSUM_ERR_ARG
+
+
+def test_plan_files_that_do_not_match_are_refused_on_the_host(tmp_path):
+    # psum_plan_load checks the file before any device call: a missing file, a wrong magic word,
+    # a truncated file and a bad checksum are PSUM_ERR_IO
+    with pytest.raises(B.PsumError) as e:
+        B.psum_plan_load(tmp_path / "missing.plan")
+    assert e.value.status == B.PSUM_ERR_IO
+    bad = tmp_path / "bad.plan"
+    bad.write_bytes(b"NOTAPLAN" + bytes(200))
+    with pytest.raises(B.PsumError) as e:
+        B.psum_plan_load(bad)
+    assert e.value.status == B.PSUM_ERR_IO
+    # a well-formed header with a pseudo-inverse of 4 doubles but a wrong checksum
+    o = B.psum_opts_default()
+    body = (b"PSUMPLN1" + ctypes.sizeof(o).to_bytes(4, "little") + bytes(o) + bytes(8) + (7).to_bytes(4, "little")
+            + bytes(8) + (4).to_bytes(8, "little") + bytes(32))
+    for blob in (body + (12345).to_bytes(8, "little"), body[:-5]):
+        bad.write_bytes(blob)
+        with pytest.raises(B.PsumError) as e:
+            B.psum_plan_load(bad)
+        assert e.value.status == B.PSUM_ERR_IO
+    with pytest.raises(B.PsumError) as e:
+        B.psum_plan_save(None, tmp_path / "x.plan")
+    assert e.value.status == B.PSUM_ERR_ARG
