@@ -30,7 +30,9 @@
  *
  * Memory and streams
  *   Every device pointer is owned by the caller and must stay valid until the
- *   work queued on `stream` has finished.  `stream` is a cudaStream_t passed
+ *   work queued on `stream` has finished.  An evaluation forks part of its work onto an
+ *   internal stream of the plan and joins it again before it returns to `stream`, so
+ *   completion of `stream` covers all of it (also inside a graph capture of `stream`).  `stream` is a cudaStream_t passed
  *   as void* (NULL = the legacy default stream).  A plan owns its check
  *   points, its factorisation, the image list and its scratch memory; the
  *   scratch grows on demand inside psum_eval (a cudaMalloc, which synchronises
@@ -330,8 +332,10 @@ int psum_check_form(psum_plan_t plan, int *form);
  * PSUM_NUM_STAGES durations (milliseconds) of the last evaluation:
  *   [0] validation, spatial sort and packing
  *   [1] near-field sum at the charges (potential and gradient)
- *   [2] near-field sum at the check points (potential, or its two-layer difference)
- *   [3] reductions, right-hand side, least squares, mean and C_1
+ *   [2] the charges' reduction, and what is left of the check-point sums and the box mean:
+ *       those run on an internal stream of the lowest priority from the end of [0], beside
+ *       the charge sum, and fill the SMs it releases as it finishes
+ *   [3] right-hand side, least squares and C_1
  *   [4] far field, combination and write-back
  * Returns PSUM_ERR_ARG if profiling is off. */
 #define PSUM_NUM_STAGES 5

@@ -33,6 +33,11 @@ int cuda_status(cudaError_t e) {
     return PSUM_ERR_CUDA;
 }
 
+// register budget of the check sums (the 6-CTA instance exists for untrimmed FP32C plans only)
+int check_variant(const Plan& pl) {
+    return pl.opt.precision == PSUM_FP32C && !(pl.Rb > 0.0) ? kCheckVariant : 0;
+}
+
 // refined float32 pair terms (PSUM_TERMS_REFINED) in the symmetric charge kernel of FP32C plans
 bool refined_terms(const Plan& pl) {
     return pl.opt.precision == PSUM_FP32C && pl.opt.fp32_terms == PSUM_TERMS_REFINED;
@@ -136,14 +141,20 @@ size_t layout(Plan& pl, int64_t N, char* base, Layout& L, bool backward = false,
         L.n_src_groups = sep ? L.n_chunks : n_groups;
         L.n_src_pts = L.n_src_groups * kNearChunk;
         const bool trimmed = pl.Rb > 0.0;
-        int64_t gmax = (int64_t)pl.num_sms * near32_occupancy_ctas(n_img, 0, trimmed, pl.opt.precision == PSUM_FF);
+        const bool ffp0 = pl.opt.precision == PSUM_FF;
+        int64_t gmax = (int64_t)pl.num_sms * near32_occupancy_ctas(n_img, 0, trimmed, ffp0);
         if (g_cap > 0 && gmax > g_cap) gmax = g_cap;
         L.Ln = near_partition(L.n_tiles, L.n_chunks, n_img, gmax, ipc);
         // check sums: the 2M points with the block's images, or the M points with their
         // class's two image layers
         const bool layers = pl.lc_tiles > 0;
         const int64_t c_tiles = layers ? pl.lc_tiles : pl.n_check_tiles;
-        L.Lc = near_partition(c_tiles, L.n_chunks, layers ? pl.lc_img : n_img, gmax,
+        // the check sums' own instance (potential only) sets their width
+        const int cv = check_variant(pl);
+        int64_t gmax_c = (int64_t)pl.num_sms * near32_occupancy_ctas(layers ? pl.lc_img : n_img, cv, trimmed, ffp0, false,
+                                                                      layers ? kCheckClasses : 1);
+        if (g_cap > 0 && gmax_c > g_cap) gmax_c = g_cap;
+        L.Lc = near_partition(c_tiles, L.n_chunks, layers ? pl.lc_img : n_img, gmax_c,
                               g_cap > 0 ? 1 : kCheckItemsPerCta);
         // the symmetric kernel: FP32C charges, block image set, a normal (growing) scratch
         L.sym = false;
@@ -360,10 +371,13 @@ int queue_forward(psum_plan_s* h, int64_t N, const double* x, const double* q, d
     const double* tor = sep ? L.torg : L.org;
     const double4_32a* t64 = sep ? L.tpk64 : L.pk64;
     if (h->profile) TRY(cudaEventRecord(h->ev[1], st));
+    // fork: the side stream (least urgent priority) waits for the packing, then takes the
+    // check-point sums, their reduction and the box mean while the charge kernel runs first
+    TRY(cudaEventRecord(h->fork, st));
     if (L.sym) {
         // band by band: the pair kernel writes the band's slots, the reduction adds them to the
         // near-field sums in a fixed order (the first band sets them) before the next band
-        // reuses the slots; the last band's reduction runs with the others after the check sums
+        // reuses the slots; the last band's reduction runs after the kernel's timing event
         for (int64_t k = 0; k < L.sym_bands; ++k) {
             const NearSymLaunch S = sym_band_launch(L, k, h->inject_timeout, h->debug_limit);
             if (fp32)
@@ -383,47 +397,52 @@ int queue_forward(psum_plan_s* h, int64_t N, const double* x, const double* q, d
         TRY(launch_near64(true, L.pk64, t64, pl.d_shifts, L.part_n, L.Ln, st, pl.Rb));
     }
     if (h->profile) TRY(cudaEventRecord(h->ev[2], st));
+    cudaStream_t sd = h->side;
+    TRY(cudaStreamWaitEvent(sd, h->fork, 0));
     const bool layers = pl.lc_tiles > 0;
     if (layers && !fp32) {
-        TRY(launch_near64(false, L.pk64, (const double4_32a*)pl.d_lc_tgt, pl.d_lc_shifts, L.part_c, L.Lc, st, 0.0,
+        TRY(launch_near64(false, L.pk64, (const double4_32a*)pl.d_lc_tgt, pl.d_lc_shifts, L.part_c, L.Lc, sd, 0.0,
                           pl.d_lc_w, kCheckClasses));
     } else if (layers) {
         const float4* ct = (const float4*)pl.d_lc_tgt;
         const size_t half = 2 * (size_t)pl.lc_tiles * kTile32;         // hi parts, then lo parts
         TRY(launch_near32(false, L.pk32, L.pk32lo, L.org, ct, ct + half, pl.d_lc_org, pl.d_lc_shifts, L.part_c,
-                          L.Lc, st, 0, nullptr, 0.0, ff, pl.d_lc_gmask, pl.d_lc_w, kCheckClasses, pl.d_lc_sub));
+                          L.Lc, sd, check_variant(pl), nullptr, 0.0, ff, pl.d_lc_gmask, pl.d_lc_w, kCheckClasses,
+                          pl.d_lc_sub));
     } else if (fp32) {
         const float4* ct = (const float4*)pl.d_check_tgt;
         const size_t half = 2 * (size_t)pl.n_check_tiles * kTile32;    // hi parts, then lo parts
         TRY(launch_near32(false, L.pk32, L.pk32lo, L.org, ct, ct + half, pl.d_check_org, pl.d_shifts, L.part_c,
-                          L.Lc, st, 0, L.xs, pl.Rb, ff));
+                          L.Lc, sd, check_variant(pl), L.xs, pl.Rb, ff));
     } else {
-        TRY(launch_near64(false, L.pk64, (const double4_32a*)pl.d_check_tgt, pl.d_shifts, L.part_c, L.Lc, st,
+        TRY(launch_near64(false, L.pk64, (const double4_32a*)pl.d_check_tgt, pl.d_shifts, L.part_c, L.Lc, sd,
                           pl.Rb));
     }
-    if (h->profile) TRY(cudaEventRecord(h->ev[3], st));
     const int tile = fp32 ? kTile32 : kTile64;
-    if (L.sym)
-        TRY(launch_sym_reduce(L.part_n, N, sym_band_launch(L, L.sym_bands - 1, false, h->debug_limit), L.phi_n,
-                              L.grad_n, st, !fp32,
-                              L.sym_bands > 1));
-    else
-        TRY(launch_near_reduce(L.part_n, sep ? T : N, tile, 4, L.Ln, L.phi_n, L.grad_n, st));
     TRY(launch_near_reduce(L.part_c, layers ? (int64_t)pl.lc_tiles * tile : pl.n_check, tile, 1, L.Lc, L.phi_c,
-                           nullptr, st));
-    h->launches += 4;   // two near-field kernels, two reductions
+                           nullptr, sd));
     const bool zero_mean = o.mean_mode == PSUM_MEAN_ZERO;
     if (zero_mean) {
         if (pl.Rb > 0.0) {
             TRY(launch_box_mean_ball(x, q, fp32 ? L.va : nullptr, N, o.d, pl.d_shifts, pl.n_images, pl.Rb,
-                                     L.mean_part, L.nblk_mean, st));
+                                     L.mean_part, L.nblk_mean, sd));
         } else {
             const double H[3] = {0.5 * (2 * o.K[0] + 1) * o.d[0], 0.5 * (2 * o.K[1] + 1) * o.d[1],
                                  0.5 * (2 * o.K[2] + 1) * o.d[2]};
-            TRY(launch_box_mean(x, q, N, H, L.mean_part, L.nblk_mean, st));
+            TRY(launch_box_mean(x, q, N, H, L.mean_part, L.nblk_mean, sd));
         }
         h->launches += 1;
     }
+    TRY(cudaEventRecord(h->join, sd));
+    if (L.sym)
+        TRY(launch_sym_reduce(L.part_n, N, sym_band_launch(L, L.sym_bands - 1, false, h->debug_limit), L.phi_n,
+                              L.grad_n, st, !fp32, L.sym_bands > 1));
+    else
+        TRY(launch_near_reduce(L.part_n, sep ? T : N, tile, 4, L.Ln, L.phi_n, L.grad_n, st));
+    h->launches += 4;   // two near-field kernels, two reductions
+    // join: the fit needs the check sums and the mean
+    TRY(cudaStreamWaitEvent(st, h->join, 0));
+    if (h->profile) TRY(cudaEventRecord(h->ev[3], st));
     TRY(launch_project(pl.d_pinv, P - 1, M, L.phi_c, layers ? pl.d_lc_pos : pl.d_check_pos, L.f, pl.d_C, st,
                        layers));
     TRY(launch_constant(pl.d_C, pl.d_Rbox, P, L.mean_part, L.nblk_mean, 1.0 / (o.d[0] * o.d[1] * o.d[2]),
@@ -618,6 +637,14 @@ int create_plan(const psum_opts* o, psum_plan_t* out, const Plan* stored) {
     h->pl.preset_pinv.clear();
     h->pl.preset_pinv.shrink_to_fit();
     for (auto& e : h->ev) cudaEventCreate(&e);
+    int lo = 0, hi = 0;
+    cudaDeviceGetStreamPriorityRange(&lo, &hi);   // lo: the least urgent priority
+    if (cudaStreamCreateWithPriority(&h->side, cudaStreamNonBlocking, lo) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->join, cudaEventDisableTiming) != cudaSuccess) {
+        psum_destroy(h);
+        return PSUM_ERR_CUDA;
+    }
     *out = h;
     return PSUM_OK;
 }
@@ -975,6 +1002,9 @@ void psum_destroy(psum_plan_t h) {
             if (e) cudaEventDestroy(e);
         if (h->gexec) cudaGraphExecDestroy(h->gexec);
         if (h->cap) cudaStreamDestroy(h->cap);
+        if (h->side) cudaStreamDestroy(h->side);
+        if (h->fork) cudaEventDestroy(h->fork);
+        if (h->join) cudaEventDestroy(h->join);
         free_plan_device(h->pl);
     }
     delete h;

@@ -334,6 +334,11 @@ struct psum_batch_s {
     int64_t units = 0, pairs = 0;
     // graph
     cudaStream_t cap = nullptr;
+    // the check-point sums, fits and means on a side stream of the lowest priority (forked after
+    // the packing, joined before the constants): they fill the SMs the persistent charge kernel
+    // releases during its last work items
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
     cudaGraphExec_t exec = nullptr;
     const void* g_args[5] = {};
     int64_t launches = 0;
@@ -466,34 +471,42 @@ int queue_batch(psum_batch_s* bt, const double* x, const double* q, double* phi,
                                   bt->org, st));
         nl += 1 + 12 + 1;
         const bool ff = bt->precision == PSUM_FF;
+        BTRY(cudaEventRecord(bt->fork, st));
         if (variant == kVariantSym)
             BTRY(launch_near32s(bt->pk_hi, bt->pk_lo, bt->org, bt->d_shifts, bt->part_s, bt->Ls, st));
         else
             BTRY(launch_near32(true, bt->pk_hi, bt->pk_lo, bt->org, bt->pk_hi, bt->pk_lo, bt->org, bt->d_shifts,
                                bt->part_n, bt->Ln[variant], st, variant, nullptr, 0.0, ff));
+        BTRY(cudaStreamWaitEvent(bt->side, bt->fork, 0));
         BTRY(launch_near32(false, bt->pk_hi, bt->pk_lo, bt->org, bt->d_chk_hi, bt->d_chk_lo, bt->d_chk_org,
-                           bt->d_cshifts, bt->part_c, bt->Lc, st, 0, nullptr, 0.0, ff, bt->d_chk_cls, bt->d_cw,
+                           bt->d_cshifts, bt->part_c, bt->Lc, bt->side, 0, nullptr, 0.0, ff, bt->d_chk_cls, bt->d_cw,
                            bt->c_cls, bt->d_chk_sub));
     } else {
         BTRY(launch_pack64_groups(x, q, bt->n_pts, bt->d_grp_start, bt->d_grp_count, bt->pk64, st));
         nl += 1;
+        BTRY(cudaEventRecord(bt->fork, st));
         BTRY(launch_near64(true, bt->pk64, bt->pk64, bt->d_shifts, bt->part_n, bt->Ln[0], st));
-        BTRY(launch_near64(false, bt->pk64, bt->d_chk64, bt->d_cshifts, bt->part_c, bt->Lc, st, 0.0, bt->d_cw,
+        BTRY(cudaStreamWaitEvent(bt->side, bt->fork, 0));
+        BTRY(launch_near64(false, bt->pk64, bt->d_chk64, bt->d_cshifts, bt->part_c, bt->Lc, bt->side, 0.0, bt->d_cw,
                            bt->c_cls));
     }
+    // side stream: the check sums' reduction, the right-hand sides, the fits and the box means
     const int tile = fp32 ? kTile32 : kTile64;
+    cudaStream_t sd = bt->side;
+    BTRY(launch_near_reduce(bt->part_c, bt->n_chk_pts, tile, 1, bt->Lc, bt->phi_c, nullptr, sd));
+    int maxM = 1, maxP = 1;
+    for (const BatchDev& s : bt->sys) { maxM = std::max(maxM, s.M); maxP = std::max(maxP, s.P); }
+    k_brhs<<<dim3((maxM + 255) / 256, B), 256, 0, sd>>>(bt->d_sys, bt->phi_c, bt->f);
+    k_bproject<<<dim3((maxP - 1 + 7) / 8, B), 256, 0, sd>>>(bt->d_sys, bt->f, bt->C);
+    k_bbox_mean<<<bt->n_seg, kSeg, 0, sd>>>(x, q, bt->d_sys, bt->d_seg_sys, bt->d_seg_start, bt->mean_part);
+    BTRY(cudaEventRecord(bt->join, sd));
     if (variant == kVariantSym)
         BTRY(launch_sym_reduce(bt->part_s, bt->n_pts, bt->Ls, bt->phi_n, bt->grad_n, st));
     else
         BTRY(launch_near_reduce(bt->part_n, bt->n_pts, tile, 4, bt->Ln[fp32 ? variant : 0], bt->phi_n, bt->grad_n,
                                 st));
-    BTRY(launch_near_reduce(bt->part_c, bt->n_chk_pts, tile, 1, bt->Lc, bt->phi_c, nullptr, st));
     nl += 4;
-    int maxM = 1, maxP = 1;
-    for (const BatchDev& s : bt->sys) { maxM = std::max(maxM, s.M); maxP = std::max(maxP, s.P); }
-    k_brhs<<<dim3((maxM + 255) / 256, B), 256, 0, st>>>(bt->d_sys, bt->phi_c, bt->f);
-    k_bproject<<<dim3((maxP - 1 + 7) / 8, B), 256, 0, st>>>(bt->d_sys, bt->f, bt->C);
-    k_bbox_mean<<<bt->n_seg, kSeg, 0, st>>>(x, q, bt->d_sys, bt->d_seg_sys, bt->d_seg_start, bt->mean_part);
+    BTRY(cudaStreamWaitEvent(st, bt->join, 0));
     k_bconstant<<<B, 32, 0, st>>>(bt->d_sys, bt->mean_part, bt->C);
     int max_tab = 1;
     for (const psum_plan_t p : bt->plans) max_tab = std::max(max_tab, sh_tab_size(p->pl.opt.p));
@@ -598,6 +611,9 @@ class DevGuard {
 void release(psum_batch_s* bt) {
     if (bt->exec) cudaGraphExecDestroy(bt->exec);
     if (bt->cap) cudaStreamDestroy(bt->cap);
+    if (bt->side) cudaStreamDestroy(bt->side);
+    if (bt->fork) cudaEventDestroy(bt->fork);
+    if (bt->join) cudaEventDestroy(bt->join);
     cudaFree(bt->mem);
     if (bt->h_status) cudaFreeHost(bt->h_status);
 }
@@ -847,6 +863,13 @@ int psum_batch_create(const psum_plan_t* plans, int B, const int64_t* offsets, p
     if (st == PSUM_OK) st = cuda_st(cudaMallocHost((void**)&bt->h_status, sizeof(int) * B));
     if (st == PSUM_OK) st = cuda_st(cudaMemset(bt->d_status, 0, sizeof(int) * B));
     if (st == PSUM_OK) st = cuda_st(cudaStreamCreateWithFlags(&bt->cap, cudaStreamNonBlocking));
+    if (st == PSUM_OK) {
+        int lo = 0, hi = 0;
+        cudaDeviceGetStreamPriorityRange(&lo, &hi);
+        st = cuda_st(cudaStreamCreateWithPriority(&bt->side, cudaStreamNonBlocking, lo));
+    }
+    if (st == PSUM_OK) st = cuda_st(cudaEventCreateWithFlags(&bt->fork, cudaEventDisableTiming));
+    if (st == PSUM_OK) st = cuda_st(cudaEventCreateWithFlags(&bt->join, cudaEventDisableTiming));
     if (st != PSUM_OK) {
         release(bt);
         delete bt;

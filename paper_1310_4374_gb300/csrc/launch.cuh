@@ -22,7 +22,13 @@ size_t near32_dyn_smem(int n_img, bool trimmed, bool grad, int n_cls);
 constexpr size_t kNear32DynSmemMax = 48 * 1024;
 cudaError_t launch_near_reduce(const double* partial, int64_t n_valid, int tile_size, int nq,
                                const NearPlanLaunch& L, double* out_phi, double* out_grad, cudaStream_t st);
-int near32_occupancy_ctas(int n_img, int variant = 0, bool trimmed = false, bool ff = false);
+int near32_occupancy_ctas(int n_img, int variant = 0, bool trimmed = false, bool ff = false, bool grad = true,
+                          int n_cls = 1);
+// register budget of the check-point (potential-only) launch of block plans: 0 = 4 CTAs/SM, 1 = 6
+#ifndef PSUM_CHECK_VARIANT
+#define PSUM_CHECK_VARIANT 0
+#endif
+constexpr int kCheckVariant = PSUM_CHECK_VARIANT;
 cudaError_t launch_near32s(const float4* pk_hi, const float4* pk_lo, const double* org, const double* shifts,
                            double* partial, const NearSymLaunch& S, cudaStream_t st, bool ff = false,
                            bool refine = false);

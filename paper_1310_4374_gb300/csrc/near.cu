@@ -617,6 +617,30 @@ __global__ void __launch_bounds__(32 * kReduceWarps) k_near_reduce(const double*
 // ---------------------------------------------------------------------------
 // Host launchers
 // ---------------------------------------------------------------------------
+// The instance of k_near32 a launch runs: trimmed near sets and float-float take the larger
+// register budget, the others the variant's.
+using Near32Kernel = void (*)(Near32Args);
+Near32Kernel near32_instance(bool grad, int variant, bool trimmed, bool ff) {
+    constexpr int B0 = kNear32MinBlocks[0], B1 = kNear32MinBlocks[1];
+    if (ff) {
+        if (trimmed) return grad ? k_near32<true, B0, true, true> : k_near32<false, B0, true, true>;
+        return grad ? k_near32<true, B0, false, true> : k_near32<false, B0, false, true>;
+    }
+    if (trimmed) return grad ? k_near32<true, B0, true, false> : k_near32<false, B0, true, false>;
+    if (variant == 1) return grad ? k_near32<true, B1, false, false> : k_near32<false, B1, false, false>;
+    return grad ? k_near32<true, B0, false, false> : k_near32<false, B0, false, false>;
+}
+
+// Dynamic shared memory beyond what needs no opt-in (a ball that keeps many images, with
+// their offsets per target group): raise the instance's limit to what the launch asks for.
+cudaError_t near32_allow_smem(Near32Kernel kernel, size_t smem) {
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
+    if (e != cudaSuccess) return e;
+    if (fa.sharedSizeBytes + smem <= (size_t)48 * 1024) return cudaSuccess;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
 size_t near32_dyn_smem(int n_img, bool trimmed, bool grad, int n_cls) {
     const size_t head = ((6 * kTgt32 * (size_t)n_cls * n_img + n_img + (grad ? 0 : kTgt32 * (size_t)n_cls * n_img) +
                           3) / 4) * sizeof(float4);
@@ -655,27 +679,11 @@ cudaError_t launch_near32(bool grad, const float4* src_hi, const float4* src_lo,
     if (!L.counter) return cudaErrorInvalidValue;
     const cudaError_t e = cudaMemsetAsync(L.counter, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
-    constexpr int B0 = kNear32MinBlocks[0], B1 = kNear32MinBlocks[1];
     const unsigned G = (unsigned)L.G;
-    if (ff) {
-        if (Rb > 0.0) {
-            if (grad) k_near32<true, B0, true, true><<<G, kThreads32, smem, st>>>(a);
-            else k_near32<false, B0, true, true><<<G, kThreads32, smem, st>>>(a);
-        } else {
-            if (grad) k_near32<true, B0, false, true><<<G, kThreads32, smem, st>>>(a);
-            else k_near32<false, B0, false, true><<<G, kThreads32, smem, st>>>(a);
-        }
-    } else if (Rb > 0.0) {
-        // trimmed near sets take the larger register budget: the ball tests add live state
-        if (grad) k_near32<true, B0, true, false><<<G, kThreads32, smem, st>>>(a);
-        else k_near32<false, B0, true, false><<<G, kThreads32, smem, st>>>(a);
-    } else if (variant == 1) {
-        if (grad) k_near32<true, B1, false, false><<<G, kThreads32, smem, st>>>(a);
-        else k_near32<false, B1, false, false><<<G, kThreads32, smem, st>>>(a);
-    } else {
-        if (grad) k_near32<true, B0, false, false><<<G, kThreads32, smem, st>>>(a);
-        else k_near32<false, B0, false, false><<<G, kThreads32, smem, st>>>(a);
-    }
+    const auto kernel = near32_instance(grad, variant, Rb > 0.0, ff);
+    const cudaError_t ea = near32_allow_smem(kernel, smem);
+    if (ea != cudaSuccess) return ea;
+    kernel<<<G, kThreads32, smem, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -706,20 +714,12 @@ cudaError_t launch_near_reduce(const double* partial, int64_t n_valid, int tile_
     return cudaGetLastError();
 }
 
-int near32_occupancy_ctas(int n_img, int variant, bool trimmed, bool ff) {
+int near32_occupancy_ctas(int n_img, int variant, bool trimmed, bool ff, bool grad, int n_cls) {
     int nb = 0;
-    const size_t smem = near32_dyn_smem(n_img, trimmed, true, 1);
-    constexpr int B0 = kNear32MinBlocks[0], B1 = kNear32MinBlocks[1];
-    if (ff && trimmed)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_near32<true, B0, true, true>, kThreads32, smem);
-    else if (ff)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_near32<true, B0, false, true>, kThreads32, smem);
-    else if (trimmed)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_near32<true, B0, true, false>, kThreads32, smem);
-    else if (variant == 1)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_near32<true, B1, false, false>, kThreads32, smem);
-    else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_near32<true, B0, false, false>, kThreads32, smem);
+    const size_t smem = near32_dyn_smem(n_img, trimmed, grad, n_cls);
+    const Near32Kernel kernel = near32_instance(grad, variant, trimmed, ff);
+    if (near32_allow_smem(kernel, smem) == cudaSuccess)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, kThreads32, smem);
     return nb < 1 ? 1 : nb;
 }
 

@@ -623,6 +623,11 @@ struct psum_plan_s {
     int64_t debug_limit = 0;      // test hook: the partial buffers' size as the debug bounds checks see it
     int fail_allocs = 0;          // test hook: the next scratch allocations fail as if out of memory
     cudaEvent_t ev[6] = {};
+    // the check-point sums and the box mean run on a side stream of the lowest priority, forked
+    // after the packing and joined before the fit, so that they fill the SMs the persistent
+    // charge kernel releases during its last work items
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
     // psum_eval_graph: one evaluation captured into a CUDA graph, replayed while the
     // arguments and the scratch buffer stay the same
     cudaStream_t cap = nullptr;
