@@ -421,19 +421,23 @@ int queue_forward(psum_plan_s* h, int64_t N, const double* x, const double* q, d
     const int tile = fp32 ? kTile32 : kTile64;
     TRY(launch_near_reduce(L.part_c, layers ? (int64_t)pl.lc_tiles * tile : pl.n_check, tile, 1, L.Lc, L.phi_c,
                            nullptr, sd));
+    TRY(cudaEventRecord(h->join, sd));
+    // the box mean on a second side stream, beside the check sums
     const bool zero_mean = o.mean_mode == PSUM_MEAN_ZERO;
     if (zero_mean) {
+        cudaStream_t s2 = h->side2;
+        TRY(cudaStreamWaitEvent(s2, h->fork, 0));
         if (pl.Rb > 0.0) {
             TRY(launch_box_mean_ball(x, q, fp32 ? L.va : nullptr, N, o.d, pl.d_shifts, pl.n_images, pl.Rb,
-                                     L.mean_part, L.nblk_mean, sd));
+                                     L.mean_part, L.nblk_mean, s2));
         } else {
             const double H[3] = {0.5 * (2 * o.K[0] + 1) * o.d[0], 0.5 * (2 * o.K[1] + 1) * o.d[1],
                                  0.5 * (2 * o.K[2] + 1) * o.d[2]};
-            TRY(launch_box_mean(x, q, N, H, L.mean_part, L.nblk_mean, sd));
+            TRY(launch_box_mean(x, q, N, H, L.mean_part, L.nblk_mean, s2));
         }
+        TRY(cudaEventRecord(h->join2, s2));
         h->launches += 1;
     }
-    TRY(cudaEventRecord(h->join, sd));
     if (L.sym)
         TRY(launch_sym_reduce(L.part_n, N, sym_band_launch(L, L.sym_bands - 1, false, h->debug_limit), L.phi_n,
                               L.grad_n, st, !fp32, L.sym_bands > 1));
@@ -442,6 +446,7 @@ int queue_forward(psum_plan_s* h, int64_t N, const double* x, const double* q, d
     h->launches += 4;   // two near-field kernels, two reductions
     // join: the fit needs the check sums and the mean
     TRY(cudaStreamWaitEvent(st, h->join, 0));
+    if (zero_mean) TRY(cudaStreamWaitEvent(st, h->join2, 0));
     if (h->profile) TRY(cudaEventRecord(h->ev[3], st));
     TRY(launch_project(pl.d_pinv, P - 1, M, L.phi_c, layers ? pl.d_lc_pos : pl.d_check_pos, L.f, pl.d_C, st,
                        layers));
@@ -640,8 +645,10 @@ int create_plan(const psum_opts* o, psum_plan_t* out, const Plan* stored) {
     int lo = 0, hi = 0;
     cudaDeviceGetStreamPriorityRange(&lo, &hi);   // lo: the least urgent priority
     if (cudaStreamCreateWithPriority(&h->side, cudaStreamNonBlocking, lo) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&h->side2, cudaStreamNonBlocking, lo) != cudaSuccess ||
         cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&h->join, cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreateWithFlags(&h->join, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->join2, cudaEventDisableTiming) != cudaSuccess) {
         psum_destroy(h);
         return PSUM_ERR_CUDA;
     }
@@ -1003,8 +1010,10 @@ void psum_destroy(psum_plan_t h) {
         if (h->gexec) cudaGraphExecDestroy(h->gexec);
         if (h->cap) cudaStreamDestroy(h->cap);
         if (h->side) cudaStreamDestroy(h->side);
+        if (h->side2) cudaStreamDestroy(h->side2);
         if (h->fork) cudaEventDestroy(h->fork);
         if (h->join) cudaEventDestroy(h->join);
+        if (h->join2) cudaEventDestroy(h->join2);
         free_plan_device(h->pl);
     }
     delete h;

@@ -337,8 +337,8 @@ struct psum_batch_s {
     // the check-point sums, fits and means on a side stream of the lowest priority (forked after
     // the packing, joined before the constants): they fill the SMs the persistent charge kernel
     // releases during its last work items
-    cudaStream_t side = nullptr;
-    cudaEvent_t fork = nullptr, join = nullptr;
+    cudaStream_t side = nullptr, side2 = nullptr;   // check sums and fits; box means
+    cudaEvent_t fork = nullptr, join = nullptr, join2 = nullptr;
     cudaGraphExec_t exec = nullptr;
     const void* g_args[5] = {};
     int64_t launches = 0;
@@ -498,8 +498,10 @@ int queue_batch(psum_batch_s* bt, const double* x, const double* q, double* phi,
     for (const BatchDev& s : bt->sys) { maxM = std::max(maxM, s.M); maxP = std::max(maxP, s.P); }
     k_brhs<<<dim3((maxM + 255) / 256, B), 256, 0, sd>>>(bt->d_sys, bt->phi_c, bt->f);
     k_bproject<<<dim3((maxP - 1 + 7) / 8, B), 256, 0, sd>>>(bt->d_sys, bt->f, bt->C);
-    k_bbox_mean<<<bt->n_seg, kSeg, 0, sd>>>(x, q, bt->d_sys, bt->d_seg_sys, bt->d_seg_start, bt->mean_part);
     BTRY(cudaEventRecord(bt->join, sd));
+    BTRY(cudaStreamWaitEvent(bt->side2, bt->fork, 0));
+    k_bbox_mean<<<bt->n_seg, kSeg, 0, bt->side2>>>(x, q, bt->d_sys, bt->d_seg_sys, bt->d_seg_start, bt->mean_part);
+    BTRY(cudaEventRecord(bt->join2, bt->side2));
     if (variant == kVariantSym)
         BTRY(launch_sym_reduce(bt->part_s, bt->n_pts, bt->Ls, bt->phi_n, bt->grad_n, st));
     else
@@ -507,6 +509,7 @@ int queue_batch(psum_batch_s* bt, const double* x, const double* q, double* phi,
                                 st));
     nl += 4;
     BTRY(cudaStreamWaitEvent(st, bt->join, 0));
+    BTRY(cudaStreamWaitEvent(st, bt->join2, 0));
     k_bconstant<<<B, 32, 0, st>>>(bt->d_sys, bt->mean_part, bt->C);
     int max_tab = 1;
     for (const psum_plan_t p : bt->plans) max_tab = std::max(max_tab, sh_tab_size(p->pl.opt.p));
@@ -612,6 +615,8 @@ void release(psum_batch_s* bt) {
     if (bt->exec) cudaGraphExecDestroy(bt->exec);
     if (bt->cap) cudaStreamDestroy(bt->cap);
     if (bt->side) cudaStreamDestroy(bt->side);
+    if (bt->side2) cudaStreamDestroy(bt->side2);
+    if (bt->join2) cudaEventDestroy(bt->join2);
     if (bt->fork) cudaEventDestroy(bt->fork);
     if (bt->join) cudaEventDestroy(bt->join);
     cudaFree(bt->mem);
@@ -867,7 +872,9 @@ int psum_batch_create(const psum_plan_t* plans, int B, const int64_t* offsets, p
         int lo = 0, hi = 0;
         cudaDeviceGetStreamPriorityRange(&lo, &hi);
         st = cuda_st(cudaStreamCreateWithPriority(&bt->side, cudaStreamNonBlocking, lo));
+        if (st == PSUM_OK) st = cuda_st(cudaStreamCreateWithPriority(&bt->side2, cudaStreamNonBlocking, lo));
     }
+    if (st == PSUM_OK) st = cuda_st(cudaEventCreateWithFlags(&bt->join2, cudaEventDisableTiming));
     if (st == PSUM_OK) st = cuda_st(cudaEventCreateWithFlags(&bt->fork, cudaEventDisableTiming));
     if (st == PSUM_OK) st = cuda_st(cudaEventCreateWithFlags(&bt->join, cudaEventDisableTiming));
     if (st != PSUM_OK) {

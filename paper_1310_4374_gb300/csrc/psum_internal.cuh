@@ -626,8 +626,8 @@ struct psum_plan_s {
     // the check-point sums and the box mean run on a side stream of the lowest priority, forked
     // after the packing and joined before the fit, so that they fill the SMs the persistent
     // charge kernel releases during its last work items
-    cudaStream_t side = nullptr;
-    cudaEvent_t fork = nullptr, join = nullptr;
+    cudaStream_t side = nullptr, side2 = nullptr;   // check sums; box mean
+    cudaEvent_t fork = nullptr, join = nullptr, join2 = nullptr;
     // psum_eval_graph: one evaluation captured into a CUDA graph, replayed while the
     // arguments and the scratch buffer stay the same
     cudaStream_t cap = nullptr;
