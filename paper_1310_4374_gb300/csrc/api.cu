@@ -260,8 +260,11 @@ size_t layout(Plan& pl, int64_t N, char* base, Layout& L, bool backward = false,
     L.chk_src64 = nullptr;
     L.nblk_mom = 0;
     if (backward) {
-        const int n_img = pl.n_images;
-        const int64_t n_chk_chunks = fp32 ? (int64_t)pl.n_check_tiles * kTgt32 : (int64_t)pl.n_check_tiles;
+        // the check points as sources: the two-layer sets (float32 packing with layers) or the 2M points
+        const bool bk_layers = fp32 && pl.bk_chunks > 0;
+        const int n_img = bk_layers ? pl.bk_lmax : pl.n_images;
+        const int64_t n_chk_chunks = bk_layers ? (int64_t)pl.bk_chunks
+                                               : fp32 ? (int64_t)pl.n_check_tiles * kTgt32 : (int64_t)pl.n_check_tiles;
         const int64_t gmax = (int64_t)pl.num_sms *
                              (fp32 ? near32_occupancy_ctas(n_img, 0, false, pl.opt.precision == PSUM_FF)
                                    : near64_occupancy_ctas());
@@ -522,7 +525,16 @@ int backward_device(psum_plan_s* h, int64_t N, const double* x, const double* q,
     h->launches += 3;
     // psi and grad psi at the charges: the check points as sources
     const int tile = fp32 ? kTile32 : kTile64;
-    if (fp32) {
+    if (fp32 && pl.bk_chunks > 0) {
+        // two-layer check sources: each chunk with its (class, side) image list
+        const size_t n_bk = (size_t)pl.bk_chunks * kNearChunk;
+        const float4* bk = (const float4*)pl.d_bk_pk;
+        TRY(launch_check_sources32(bk, bk + 2 * n_bk, pl.d_bk_slot, (int64_t)n_bk, M, L.u, L.chk_src32, L.chk_src32lo,
+                                   st, true));
+        TRY(launch_near32(true, L.chk_src32, ff ? L.chk_src32lo : bk + 2 * n_bk, pl.d_bk_org, L.pk32, L.pk32lo, L.org,
+                          pl.d_bk_shifts, L.part_b, L.Lb, st, 0, nullptr, 0.0, ff, nullptr, nullptr, 1, nullptr,
+                          pl.d_bk_img0, pl.d_bk_nimg));
+    } else if (fp32) {
         const size_t n_chk_pts = (size_t)pl.n_check_tiles * kTile32;
         const float4* chk = (const float4*)pl.d_check_tgt;
         TRY(launch_check_sources32(chk, chk + 2 * n_chk_pts, pl.d_check_inv, (int64_t)n_chk_pts, M, L.u,

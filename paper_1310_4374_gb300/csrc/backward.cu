@@ -6,8 +6,10 @@
 //   psi(x)   = sum_l u_l [G(y~_l - x) - G(y_l - x)]   (G: the near-block image kernel),
 //   dE/dq_k  = phi(x_k) - phi_far(x_k)/2 + psi(x_k)/2,
 //   dE/dx_k  = q_k [grad phi - grad phi_far/2 + grad psi/2](x_k).
-// psi is a near-field sum of 2M check-point charges (+u at y~, -u at y) at the charges,
-// done by the same pair kernels as the forward sum.
+// psi is a near-field sum of check-point charges at the charges, done by the same pair kernels
+// as the forward sum: 2M charges (+u at y~, -u at y) with the near block's images, or, as the
+// right-hand side's two image layers, M points twice (+u_l with the upper layer's images, -u_l
+// with the lower's; float32 packing with plans that take the layers).
 #include "psum_internal.cuh"
 
 namespace psum {
@@ -83,17 +85,24 @@ __global__ void k_adjoint(const double* __restrict__ pinv, int rows, int M, cons
     u[l] = s;
 }
 
-// Check points as sources: charge -u_l at y_l and +u_l at y~_l (packed positions from the plan).
-// The check points as sources of psi, charges -u_l at y_l and u_l at y~_l.  With out_lo
-// (float-float plans) the lo parts are copied too, with the charges' float32 remainders.
+// The check points as sources of psi with charges from u (packed positions from the plan).
+// Point form (layers == 0): slot s holds point j = inv[s] (j < M: y_j, charge -u_j; else
+// y~_{j-M}, charge +u_{j-M}).  Two-layer form: inv[s] = 2 l + side, charge +u_l with the upper
+// layer's images (side 0), -u_l with the lower layer's (side 1).  -1: padding, charge 0.  With
+// out_lo (float-float plans) the lo parts are copied too, with the charges' float32 remainders.
 __global__ void k_check_sources32(const float4* __restrict__ chk_hi, const float4* __restrict__ chk_lo,
                                   const int* __restrict__ inv, int64_t n_pts, int M, const double* __restrict__ u,
-                                  float4* __restrict__ out_hi, float4* __restrict__ out_lo) {
+                                  float4* __restrict__ out_hi, float4* __restrict__ out_lo, int layers) {
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n_pts) return;
     const int j = inv[s];
     double cd = 0.0;
-    if (j >= 0) cd = j < M ? -u[j] : u[j - M];
+    if (j >= 0) {
+        if (layers)
+            cd = (j & 1) ? -u[j >> 1] : u[j >> 1];
+        else
+            cd = j < M ? -u[j] : u[j - M];
+    }
     const float c = (float)cd;
     const float4 A = chk_hi[2 * s], B = chk_hi[2 * s + 1];
     out_hi[2 * s] = A;
@@ -190,9 +199,9 @@ cudaError_t launch_adjoint(const double* pinv, int rows, int M, const double* w,
 }
 
 cudaError_t launch_check_sources32(const float4* chk_hi, const float4* chk_lo, const int* inv, int64_t n_pts, int M,
-                                   const double* u, float4* out_hi, float4* out_lo, cudaStream_t st) {
+                                   const double* u, float4* out_hi, float4* out_lo, cudaStream_t st, bool layers) {
     k_check_sources32<<<(unsigned)((n_pts + 255) / 256), 256, 0, st>>>(chk_hi, chk_lo, inv, n_pts, M, u, out_hi,
-                                                                         out_lo);
+                                                                         out_lo, layers ? 1 : 0);
     return cudaGetLastError();
 }
 

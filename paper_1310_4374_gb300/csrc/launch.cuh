@@ -11,7 +11,8 @@ cudaError_t launch_near32(bool grad, const float4* src_hi, const float4* src_lo,
                           double* partial, const NearPlanLaunch& L, cudaStream_t st, int variant = 0,
                           const double* src_x = nullptr, double Rb = 0.0, bool ff = false,
                           const int* grp_cls = nullptr, const float* img_w = nullptr, int n_cls = 1,
-                          const double* grp_sub = nullptr);
+                          const double* grp_sub = nullptr, const int* chunk_img0 = nullptr,
+                          const int* chunk_nimg = nullptr);
 cudaError_t launch_near64(bool grad, const double4_32a* src, const double4_32a* tgt, const double* shifts,
                           double* partial, const NearPlanLaunch& L, cudaStream_t st, double Rb = 0.0,
                           const float* img_w = nullptr, int n_cls = 1);
@@ -89,7 +90,8 @@ int moments_blocks(int64_t n);
 size_t moments_smem(int p);
 cudaError_t launch_adjoint(const double* pinv, int rows, int M, const double* w, double* u, cudaStream_t st);
 cudaError_t launch_check_sources32(const float4* chk_hi, const float4* chk_lo, const int* inv, int64_t n_pts, int M,
-                                   const double* u, float4* out_hi, float4* out_lo, cudaStream_t st);
+                                   const double* u, float4* out_hi, float4* out_lo, cudaStream_t st,
+                                   bool layers = false);
 cudaError_t launch_check_sources64(const double4_32a* chk, int64_t n_pts, int M, const double* u,
                                    double4_32a* out, cudaStream_t st);
 cudaError_t launch_backward_combine(int64_t n, const int* perm, const double* q, const double* phi,

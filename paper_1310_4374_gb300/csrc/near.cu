@@ -65,6 +65,10 @@ struct Near32Args {
     const double* grp_sub;       // [group][n_cls][4]: centre and radius of each class's points
     const float* img_w;
     int n_cls;
+    // per source chunk (may be null): the first entry of its image list in `shifts` and its count
+    // (units past the count add nothing); the backward's two-layer check sources
+    const int* chunk_img0;
+    const int* chunk_nimg;
 };
 
 // Two register budgets of the same kernel: 4 resident CTAs per SM (up to 128 registers) or
@@ -229,7 +233,8 @@ __global__ void __launch_bounds__(kThreads32, kMinB) k_near32(Near32Args a) {
                     s_near[im] = (s_near[im] & kUnitWeighted) ? (s_near[im] & ~kUnitWeighted) : kUnitOutside;
             } else
             for (int im = tid; im < n_img; im += kThreads32) {
-                const double* sh = a.shifts + 3 * (shift0 + im);
+                const int img0 = a.chunk_img0 ? a.chunk_img0[chunk] : shift0;
+                const double* sh = a.shifts + 3 * (img0 + im);
                 int nr = 0;
                 bool weighted = false;
                 for (int k = 0; k < kTgt32; ++k) {
@@ -260,6 +265,7 @@ __global__ void __launch_bounds__(kThreads32, kMinB) k_near32(Near32Args a) {
                     else if (ri < 0.0 || c2s > ri * ri) nr |= kUnitStraddle;
                 }
                 if (!kGrad && !weighted) nr = kUnitOutside;   // padding image of every group: skip
+                if (a.chunk_nimg && im >= a.chunk_nimg[chunk]) nr = kUnitOutside;   // past the chunk's list
                 s_near[im] = nr;
             }
             const long long limit = a.inject ? (1LL << 12) : kCopySpinLimit;
@@ -280,7 +286,7 @@ __global__ void __launch_bounds__(kThreads32, kMinB) k_near32(Near32Args a) {
         // the offsets of target group g's thread target (its class's entry) and the weights
         auto dptr = [&](int g) { return dl + 6 * (g * ncls + (kGrad ? 0 : s_tcls[g][tid])); };
         const int cls = s_near[img];
-        if ((kTrim || !kGrad) && (cls & kUnitOutside)) {
+        if ((kTrim || !kGrad || a.chunk_nimg) && (cls & kUnitOutside)) {
             ++u;
             continue;
         }
@@ -651,8 +657,12 @@ cudaError_t launch_near32(bool grad, const float4* src_hi, const float4* src_lo,
                           const float4* tgt_hi, const float4* tgt_lo, const double* tgt_org, const double* shifts,
                           double* partial, const NearPlanLaunch& L, cudaStream_t st, int variant,
                           const double* src_x, double Rb, bool ff, const int* grp_cls, const float* img_w,
-                          int n_cls, const double* grp_sub) {
+                          int n_cls, const double* grp_sub, const int* chunk_img0, const int* chunk_nimg) {
     Near32Args a;
+    a.chunk_img0 = chunk_img0;
+    a.chunk_nimg = chunk_nimg;
+    if ((chunk_img0 != nullptr) != (chunk_nimg != nullptr) || (chunk_img0 && (n_cls > 1 || Rb > 0.0)))
+        return cudaErrorInvalidValue;
     a.status = L.status;
     a.n_status = L.n_status;
     a.inject = L.inject;

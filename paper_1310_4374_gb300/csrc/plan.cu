@@ -372,6 +372,47 @@ static int build_check_layers(Plan& pl, const double d[3]) {
     if ((s1 = upload(&pl.d_lc_w, w.data(), w.size()))) return s1;
     pl.lc_tiles = tiles;
     pl.lc_img = n_img;
+    if (!fp32) return PSUM_OK;
+    // the backward's check sources as the two layers (float32 packing): set (c, side) holds the
+    // points of class c, side 0 with the upper layer (weight +1), side 1 with the lower (-1);
+    // the source sees the target through the negated image vector
+    std::vector<int> bk_slot, bk_img0, bk_nimg;
+    std::vector<int> slot_pt;
+    for (int c = 0; c < 6; ++c)
+        for (int side = 0; side < 2; ++side) {
+            std::vector<int> pts;   // Morton order within the class: compact chunks
+            for (int l : order)
+                if (cls[l] == c) pts.push_back(l);
+            if (pts.empty()) continue;
+            const int chunks = (int)((pts.size() + kNearChunk - 1) / kNearChunk);
+            for (int ch = 0; ch < chunks; ++ch) {
+                bk_img0.push_back((2 * c + side) * Lmax);
+                bk_nimg.push_back(Lsize[c / 2]);
+                for (int k = 0; k < kNearChunk; ++k) {
+                    const size_t i = (size_t)ch * kNearChunk + k;
+                    bk_slot.push_back(i < pts.size() ? 2 * pts[i] + side : -1);
+                    slot_pt.push_back(i < pts.size() ? pts[i] : -1);
+                }
+            }
+        }
+    std::vector<double> bsh(12 * (size_t)Lmax * 3, 0.0);
+    for (int c = 0; c < 6; ++c)
+        for (int side = 0; side < 2; ++side)
+            for (int j = 0; j < Lmax; ++j)
+                for (int k = 0; k < 3; ++k)
+                    bsh[3 * ((size_t)(2 * c + side) * Lmax + j) + k] = -sh[3 * ((size_t)c * n_img + side * Lmax + j) + k];
+    const int bk_chunks = (int)bk_img0.size();
+    std::vector<float4> bpk;
+    std::vector<double> borg;
+    pack_groups32(pl.Y, slot_pt, bk_chunks, bpk, borg);
+    if ((s1 = upload((float4**)&pl.d_bk_pk, bpk.data(), bpk.size()))) return s1;
+    if ((s1 = upload(&pl.d_bk_org, borg.data(), borg.size()))) return s1;
+    if ((s1 = upload(&pl.d_bk_slot, bk_slot.data(), bk_slot.size()))) return s1;
+    if ((s1 = upload(&pl.d_bk_img0, bk_img0.data(), bk_img0.size()))) return s1;
+    if ((s1 = upload(&pl.d_bk_nimg, bk_nimg.data(), bk_nimg.size()))) return s1;
+    if ((s1 = upload(&pl.d_bk_shifts, bsh.data(), bsh.size()))) return s1;
+    pl.bk_chunks = bk_chunks;
+    pl.bk_lmax = Lmax;
     return PSUM_OK;
 }
 
@@ -581,6 +622,12 @@ void free_plan_device(Plan& pl) {
     cudaFree(pl.d_lc_pos);
     cudaFree(pl.d_lc_shifts);
     cudaFree(pl.d_lc_w);
+    cudaFree(pl.d_bk_pk);
+    cudaFree(pl.d_bk_org);
+    cudaFree(pl.d_bk_slot);
+    cudaFree(pl.d_bk_img0);
+    cudaFree(pl.d_bk_nimg);
+    cudaFree(pl.d_bk_shifts);
     cudaFree(pl.d_pinv);
     cudaFree(pl.d_Rbox);
     cudaFree(pl.d_shifts);

@@ -251,6 +251,21 @@ struct Plan {
     double* d_lc_shifts = nullptr;  // [6][lc_img][3] image vectors of each class's layers
     float* d_lc_w = nullptr;        // [6][lc_img] weights: +1 (upper layer), -1 (lower), 0 (padding)
 
+    // the backward's check sources as two image layers (float32 packing, plans with layers):
+    // psi(x) = sum_l u_l [G(y~_l - x) - G(y_l - x)] is, as f_l, the sum over the two layers of
+    // class c(l) with signs +-1, so each check point is a source of charge +u_l with the upper
+    // layer's images and one of -u_l with the lower layer's (negated: the point is the source).
+    // The 12 (class, side) sets are packed set by set in whole chunks of 128; each chunk has its
+    // image list (bk_img0: first entry of d_bk_shifts) and count (bk_nimg).
+    int bk_chunks = 0;              // 0: the backward keeps the 2M check points as sources
+    int bk_lmax = 0;                // images per (class, side) list
+    void* d_bk_pk = nullptr;        // float4 hi parts (2 per slot) then lo parts; charges set per backward
+    double* d_bk_org = nullptr;     // 4 per chunk: origin and radius
+    int* d_bk_slot = nullptr;       // per slot: 2 l + (lower side), or -1 for padding
+    int* d_bk_img0 = nullptr;       // per chunk
+    int* d_bk_nimg = nullptr;       // per chunk
+    double* d_bk_shifts = nullptr;  // [12][bk_lmax][3]
+
     double* d_pinv = nullptr;
     double* d_Rbox = nullptr;
     double* d_shtab64 = nullptr;    // recurrence coefficients (sh_visit_tab), double
