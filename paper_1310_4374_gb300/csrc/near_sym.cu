@@ -114,10 +114,12 @@ __device__ __forceinline__ void sym_far_step_pair(float4 A, float4 B, const floa
 //     corrections first and adds their q_t z on top.
 // The field keeps the unrefined weight q z^3 (a few ulps of terms that cancel far less).  Per
 // term about 0.41 ulp rms instead of 0.99 (float32 emulation of this arithmetic); per target
-// and source pair 31 packed operations instead of 19.
+// and source pair 30 packed operations instead of 19 (the correction's -1/2 rides on the
+// targets' charges for the reaction and on the action's correction sum).
 __device__ __forceinline__ void sym_far_step_pair_refined(float4 A, float4 B, const float2 (&nx)[4],
                                                           const float2 (&ny)[4], const float2 (&nz)[4],
                                                           const float2 (&c0)[4], const float2 (&tq)[4],
+                                                          const float2 (&tqh)[4],
                                                           float2 (&aphi)[4], float2 (&acor)[4], float2 (&agx)[4],
                                                           float2 (&agy)[4], float2 (&agz)[4], float2& rp, float2& rx,
                                                           float2& ry, float2& rz) {
@@ -143,7 +145,7 @@ __device__ __forceinline__ void sym_far_step_pair_refined(float4 A, float4 B, co
         const float2 zz = __fmul2_rn(z[i], z[i]);
         const float2 rt = __ffma2_rn(make_float2(2.f, 2.f), c, r2);           // r^2 with its low part
         const float2 g = __ffma2_rn(rt, zz, m1);                               // r^2 z^2 - 1
-        k[i] = __fmul2_rn(__fmul2_rn(make_float2(-0.5f, -0.5f), z[i]), g);
+        k[i] = __fmul2_rn(z[i], g);            // -2x the correction: the -1/2 goes into acor's scale and tqh
         const float2 ri3 = __fmul2_rn(z[i], zz);
         aphi[i] = __ffma2_rn(sq, z[i], aphi[i]);
         acor[i] = __ffma2_rn(sq, k[i], acor[i]);
@@ -156,9 +158,9 @@ __device__ __forceinline__ void sym_far_step_pair_refined(float4 A, float4 B, co
         ry = __ffma2_rn(ey, wb, ry);
         rz = __ffma2_rn(ez, wb, rz);
     }
-    float2 bp = __fmul2_rn(tq[0], k[0]);
+    float2 bp = __fmul2_rn(tqh[0], k[0]);
 #pragma unroll
-    for (int i = 1; i < 4; ++i) bp = __ffma2_rn(tq[i], k[i], bp);
+    for (int i = 1; i < 4; ++i) bp = __ffma2_rn(tqh[i], k[i], bp);
 #pragma unroll
     for (int i = 0; i < 4; ++i) bp = __ffma2_rn(tq[i], z[i], bp);
     rp = __fadd2_rn(rp, bp);
@@ -521,7 +523,7 @@ __global__ void __launch_bounds__(kThreads32, kMinB) k_near32s(Near32SymArgs a) 
                 // the compensated sums, and each source's reaction is kept as four 8-step
                 // segments (parked in registers while the sums rotate through the warp, then
                 // fetched back by the lane that owns the source and added as a tree).
-                float2 nx[4], ny[4], nz[4], c0[4], tq4[4];
+                float2 nx[4], ny[4], nz[4], c0[4], tq4[4], tqh4[4];
                 float2 ph[4], pc[4], gx[4], gy[4], gz[4];
 #pragma unroll
                 for (int j = 0; j < 2; ++j) {
@@ -548,6 +550,8 @@ __global__ void __launch_bounds__(kThreads32, kMinB) k_near32s(Near32SymArgs a) 
                     c0[2 * j] = make_float2(w0, w0); c0[2 * j + 1] = make_float2(w1, w1);
                     tq4[2 * j] = make_float2(tq[j].x, tq[j].x);
                     tq4[2 * j + 1] = make_float2(tq[j].y, tq[j].y);
+                    tqh4[2 * j] = make_float2(-0.5f * tq[j].x, -0.5f * tq[j].x);      // exact
+                    tqh4[2 * j + 1] = make_float2(-0.5f * tq[j].y, -0.5f * tq[j].y);
                 }
 #pragma unroll
                 for (int i2 = 0; i2 < 4; ++i2) ph[i2] = pc[i2] = gx[i2] = gy[i2] = gz[i2] = make_float2(0.f, 0.f);
@@ -557,8 +561,8 @@ __global__ void __launch_bounds__(kThreads32, kMinB) k_near32s(Near32SymArgs a) 
 #pragma unroll 1
                     for (int k = 0; k < 32; ++k) {
                         const int P = 32 * g + ((lane + k) & 31);
-                        sym_far_step_pair_refined(s_sp[2 * P], s_sp[2 * P + 1], nx, ny, nz, c0, tq4, ph, pc, gx, gy,
-                                                  gz, rp, rx, ry, rz);
+                        sym_far_step_pair_refined(s_sp[2 * P], s_sp[2 * P + 1], nx, ny, nz, c0, tq4, tqh4, ph, pc, gx,
+                                                  gy, gz, rp, rx, ry, rz);
                         rp.x = __shfl_sync(0xffffffffu, rp.x, up);
                         rp.y = __shfl_sync(0xffffffffu, rp.y, up);
                         rx.x = __shfl_sync(0xffffffffu, rx.x, up);
@@ -601,9 +605,11 @@ __global__ void __launch_bounds__(kThreads32, kMinB) k_near32s(Near32SymArgs a) 
                 }
 #pragma unroll
                 for (int j = 0; j < 2; ++j) {
-                    // the corrections (tiny against the terms) into the low parts; the field as usual
+                    // the corrections (tiny against the terms, summed as -2x: scaled by -1/2, exact)
+                    // into the low parts; the field as usual
                     s_acc[0][j][1][tid] = __fadd2_rn(s_acc[0][j][1][tid],
-                                                     make_float2(pc[2 * j].x + pc[2 * j].y, pc[2 * j + 1].x + pc[2 * j + 1].y));
+                                                     make_float2(-0.5f * (pc[2 * j].x + pc[2 * j].y),
+                                                                 -0.5f * (pc[2 * j + 1].x + pc[2 * j + 1].y)));
                     two_sum_acc2(s_acc[1][j][0][tid], s_acc[1][j][1][tid],
                                  make_float2(gx[2 * j].x + gx[2 * j].y, gx[2 * j + 1].x + gx[2 * j + 1].y));
                     two_sum_acc2(s_acc[2][j][0][tid], s_acc[2][j][1][tid],
