@@ -88,6 +88,17 @@ constexpr int kUnitStraddle = 4;   // per-source test against the ball
 constexpr int kUnitNear1 = 8;      // the same for target pair 1 (groups 2, 3)
 constexpr int kUnitNear = kUnitNear0 | kUnitNear1;
 constexpr int kUnitWeighted = 16;  // while staging two-layer check sums: an image with a nonzero weight
+// symmetric charge kernels, a tile against itself: the pairs of image -p come as the reactions
+// of image p's, so of each mirror pair of nonzero images only the one whose first nonzero
+// shift coordinate is positive runs (the other is skipped), and the zero image runs one-sided
+constexpr int kUnitMirrored = 32;
+constexpr int kUnitSelf = 64;
+
+// +1, -1 or 0: the sign of the first nonzero coordinate of a shift (which of p and -p runs)
+__device__ __forceinline__ int shift_sign(const double* sh) {
+    return sh[0] != 0.0 ? (sh[0] > 0.0 ? 1 : -1)
+                        : sh[1] != 0.0 ? (sh[1] > 0.0 ? 1 : -1) : sh[2] != 0.0 ? (sh[2] > 0.0 ? 1 : -1) : 0;
+}
 
 // |x + p|^2 <= Rb^2 with the rounding of a plain left-to-right evaluation (no contraction),
 // the same decision for a source at the boundary as a straightforward float64 evaluation

@@ -14,8 +14,10 @@ namespace psum {
 // (j, i, -p) are one distance apart: one offset, one rsqrt and one 1/r^2 serve the
 // target's sum (the action, q_j / r) and the source's (the reaction, q_i / r, field
 // with the opposite sign).  The image set {p} of a block is symmetric, so the pairs
-// of tiles (a, b), a < b, each taken once with every image, cover the whole sum; a
-// tile against itself (a = b) runs the one-sided pair loops (near_common.cuh).
+// of tiles (a, b), a < b, each taken once with every image, cover the whole sum.  A tile
+// against itself (a = b) takes one image of each mirror pair {p, -p}, p != 0 (the one whose
+// first nonzero coordinate is positive), with reactions onto its own charges, and the zero
+// image by the one-sided pair loops (near_common.cuh), K(0) = 0.
 //
 //   * the work item is (tile pair (a, b), group of images); items are taken from a
 //     device counter; the action on tile a goes to partial slot (a, b, g), the reaction
@@ -383,6 +385,14 @@ __global__ void __launch_bounds__(kThreads32, kMinB) k_near32s(Near32SymArgs a) 
         for (int im = tid; im < nimg; im += kThreads32) {
             const double* sh = a.shifts + 3 * (S.shift0 + im0 + im);
             int nr = 0;
+            if (diag) {
+                const int sg = shift_sign(sh);
+                if (sg < 0) {
+                    s_near[im] = kUnitMirrored;
+                    continue;
+                }
+                if (sg == 0) nr = kUnitSelf;
+            }
             for (int k = 0; k < kTgt32; ++k) {
                 const double* to = a.org + 4 * (TA * kTgt32 + k);
                 const double D0 = (to[0] - so[0]) - sh[0], D1 = (to[1] - so[1]) - sh[1], D2 = (to[2] - so[2]) - sh[2];
@@ -406,7 +416,7 @@ __global__ void __launch_bounds__(kThreads32, kMinB) k_near32s(Near32SymArgs a) 
             }
             return;
         }
-        if (!kFF && !diag) {
+        if (!kFF) {
             // the chunk again as source pairs for the far rotation
             const int P = tid >> 1, h = tid & 1;
             const float4 U = s_hi[2 * (2 * P) + h], V = s_hi[2 * (2 * P + 1) + h];
@@ -416,6 +426,7 @@ __global__ void __launch_bounds__(kThreads32, kMinB) k_near32s(Near32SymArgs a) 
         for (int im = 0; im < nimg; ++im) {
             const float* dl = s_delta + 6 * (im * kTgt32);
             const int cls = s_near[im];
+            if (cls & kUnitMirrored) continue;
             if constexpr (kFF) {
                 // every unit in float-float: t' = t + delta as hi + lo, one packed pair at a time
 #pragma unroll 1
@@ -434,7 +445,7 @@ __global__ void __launch_bounds__(kThreads32, kMinB) k_near32s(Near32SymArgs a) 
                     float2 acc[4][2];
 #pragma unroll
                     for (int qi = 0; qi < 4; ++qi) acc[qi][0] = acc[qi][1] = make_float2(0.f, 0.f);
-                    if (diag) {
+                    if (cls & kUnitSelf) {
                         pair_loop_ff<true>(s_hi, s_lo, nTh, nTl, acc);
                     } else {
                         const float2 tqh = s_tq[j][tid], tql = s_tql[kFF ? j : 0][tid];
@@ -466,8 +477,8 @@ __global__ void __launch_bounds__(kThreads32, kMinB) k_near32s(Near32SymArgs a) 
                 }
                 continue;
             }
-            if (diag) {
-                // a tile against its own chunks: the one-sided units
+            if (cls & kUnitSelf) {
+                // a tile against its own chunks in the zero image: the one-sided units
 #pragma unroll 1
                 for (int j = 0; j < 2; ++j) {
                     const float* d0 = dl + 6 * (2 * j);
@@ -753,6 +764,29 @@ __global__ void __launch_bounds__(kThreads32, kMinB) k_near32s(Near32SymArgs a) 
                     dst[qi * kTile32 + s] = qi == 0 ? v : -v;
                 }
             }
+        } else {
+            // a tile against itself: the chunk is the tile's group k, and source s of it is this
+            // thread's target in that group (pair k / 2, half k % 2); its reaction joins the
+            // action sums, as hi + lo of the warps' sums in the same fixed order
+            __syncthreads();
+            const int k = (int)(chunk - c0), j = k >> 1;
+#pragma unroll
+            for (int qi = 0; qi < 4; ++qi) {
+                double v = 0.0;
+#pragma unroll
+                for (int w = 0; w < kWarps; ++w) v += (double)s_re[w][qi][0][tid] + (double)s_re[w][qi][1][tid];
+                if (qi) v = -v;
+                const float vh = (float)v, vl = (float)(v - (double)vh);
+                float2& h = s_acc[qi][j][0][tid];
+                float2& l = s_acc[qi][j][1][tid];
+                if (k & 1) {
+                    two_sum_acc(h.y, l.y, vh);
+                    l.y += vl;
+                } else {
+                    two_sum_acc(h.x, l.x, vh);
+                    l.x += vl;
+                }
+            }
         }
     }
     // positions of tile tb past its last chunk (padding) get zero reactions, so that every
@@ -789,7 +823,8 @@ __global__ void __launch_bounds__(kThreads32, kMinB) k_near32s(Near32SymArgs a) 
 // group); per image a warp visits the 128 sources of tile b in 4 rotations of 32, adding
 // the action q_s / r to its targets and passing each source's reaction sums one lane down
 // per step (float64 shuffles); every warp keeps its own float64 reaction sums per source,
-// added in a fixed order when the item is done.  A tile against itself runs one-sided.
+// added in a fixed order when the item is done.  A tile against itself takes one image of
+// each mirror pair with reactions onto its own charges, and the zero image one-sided.
 // ---------------------------------------------------------------------------
 struct Near64SymArgs {
     const double4_32a* pk;   // charges (x, y, z, q), absolute, padded with far-away zero charges
@@ -837,8 +872,10 @@ __global__ void __launch_bounds__(kThreads64, kMinB) k_near64s(Near64SymArgs a) 
     for (int im = 0; im < nimg; ++im) {
         // y - x_i - p with the shift folded into the target
         const double* sh = a.shifts + 3 * (S.shift0 + im0 + im);
+        const int sg = diag ? shift_sign(sh) : 1;
+        if (sg < 0) continue;                    // a tile against itself: image -p by reaction
         const double px = t.x - sh[0], py = t.y - sh[1], pz = t.z - sh[2];
-        if (diag) {
+        if (sg == 0) {                           // ... and its zero image one-sided
 #pragma unroll 4
             for (int s = 0; s < kNearChunk; ++s) {
                 const double4_32a Q = s_src[s];
@@ -886,6 +923,17 @@ __global__ void __launch_bounds__(kThreads64, kMinB) k_near64s(Near64SymArgs a) 
             s_re[warp][1][s] += rx;
             s_re[warp][2][s] += ry;
             s_re[warp][3][s] += rz;
+        }
+    }
+    if (diag) {
+        // a tile against itself: source tid is this thread's target, its reaction joins the action
+        __syncthreads();
+#pragma unroll
+        for (int qi = 0; qi < 4; ++qi) {
+            double v = 0.0;
+#pragma unroll
+            for (int w = 0; w < kWarps; ++w) v += s_re[w][qi][tid];
+            acc[qi] += qi == 0 ? v : -v;
         }
     }
     {
