@@ -168,6 +168,7 @@ size_t layout(Plan& pl, int64_t N, char* base, Layout& L, bool backward = false,
             one[0].tile0 = 0;
             one[0].n_tiles = L.n_tiles;
             one[0].n_chunks = L.n_chunks;
+            one[0].last_n = (int)(N - (L.n_chunks - 1) * kNearChunk);
             one[0].shift0 = 0;
             one[0].n_img = n_img;
             const bool rf = refined_terms(pl);
@@ -221,6 +222,7 @@ size_t layout(Plan& pl, int64_t N, char* base, Layout& L, bool backward = false,
             one[0].tile0 = 0;
             one[0].n_tiles = L.n_tiles;
             one[0].n_chunks = L.n_chunks;
+            one[0].last_n = (int)(N - (L.n_chunks - 1) * kTile64);
             one[0].shift0 = 0;
             one[0].n_img = n_img;
             L.S = sym_partition(one, (int64_t)pl.num_sms * near64s_occupancy_ctas(), kTile64);
@@ -339,6 +341,21 @@ int queue_forward(psum_plan_s* h, int64_t N, const double* x, const double* q, d
     const bool ff = o.precision == PSUM_FF;
     const int M = o.M, P = pl.P;
     if (h->profile) TRY(cudaEventRecord(h->ev[0], st));
+    // the block's box mean needs only the caller's charges: on the second side stream (least
+    // urgent priority) from the start, beside validation, sort and packing; the ball's mean
+    // reads the sorted order and forks with the check sums below
+    const bool zero_mean = o.mean_mode == PSUM_MEAN_ZERO;
+    const bool early_mean = zero_mean && !(pl.Rb > 0.0);
+    if (early_mean) {
+        cudaStream_t s2 = h->side2;
+        TRY(cudaEventRecord(h->fork0, st));
+        TRY(cudaStreamWaitEvent(s2, h->fork0, 0));
+        const double H[3] = {0.5 * (2 * o.K[0] + 1) * o.d[0], 0.5 * (2 * o.K[1] + 1) * o.d[1],
+                             0.5 * (2 * o.K[2] + 1) * o.d[2]};
+        TRY(launch_box_mean(x, q, N, H, L.mean_part, L.nblk_mean, s2));
+        TRY(cudaEventRecord(h->join2, s2));
+        h->launches += 1;
+    }
     // the status word must start at zero; every other buffer is written before it is read
     TRY(cudaMemsetAsync(L.eval_status, 0, sizeof(int), st));
     TRY(launch_validate(x, q, N, o.d, L.val_part, L.nblk_val, L.eval_status, st));
@@ -425,19 +442,12 @@ int queue_forward(psum_plan_s* h, int64_t N, const double* x, const double* q, d
     TRY(launch_near_reduce(L.part_c, layers ? (int64_t)pl.lc_tiles * tile : pl.n_check, tile, 1, L.Lc, L.phi_c,
                            nullptr, sd));
     TRY(cudaEventRecord(h->join, sd));
-    // the box mean on a second side stream, beside the check sums
-    const bool zero_mean = o.mean_mode == PSUM_MEAN_ZERO;
-    if (zero_mean) {
+    // the ball's box mean on the second side stream, beside the check sums
+    if (zero_mean && !early_mean) {
         cudaStream_t s2 = h->side2;
         TRY(cudaStreamWaitEvent(s2, h->fork, 0));
-        if (pl.Rb > 0.0) {
-            TRY(launch_box_mean_ball(x, q, fp32 ? L.va : nullptr, N, o.d, pl.d_shifts, pl.n_images, pl.Rb,
-                                     L.mean_part, L.nblk_mean, s2));
-        } else {
-            const double H[3] = {0.5 * (2 * o.K[0] + 1) * o.d[0], 0.5 * (2 * o.K[1] + 1) * o.d[1],
-                                 0.5 * (2 * o.K[2] + 1) * o.d[2]};
-            TRY(launch_box_mean(x, q, N, H, L.mean_part, L.nblk_mean, s2));
-        }
+        TRY(launch_box_mean_ball(x, q, fp32 ? L.va : nullptr, N, o.d, pl.d_shifts, pl.n_images, pl.Rb,
+                                 L.mean_part, L.nblk_mean, s2));
         TRY(cudaEventRecord(h->join2, s2));
         h->launches += 1;
     }
@@ -658,6 +668,7 @@ int create_plan(const psum_opts* o, psum_plan_t* out, const Plan* stored) {
     cudaDeviceGetStreamPriorityRange(&lo, &hi);   // lo: the least urgent priority
     if (cudaStreamCreateWithPriority(&h->side, cudaStreamNonBlocking, lo) != cudaSuccess ||
         cudaStreamCreateWithPriority(&h->side2, cudaStreamNonBlocking, lo) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->fork0, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&h->join, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&h->join2, cudaEventDisableTiming) != cudaSuccess) {
@@ -1023,6 +1034,7 @@ void psum_destroy(psum_plan_t h) {
         if (h->cap) cudaStreamDestroy(h->cap);
         if (h->side) cudaStreamDestroy(h->side);
         if (h->side2) cudaStreamDestroy(h->side2);
+        if (h->fork0) cudaEventDestroy(h->fork0);
         if (h->fork) cudaEventDestroy(h->fork);
         if (h->join) cudaEventDestroy(h->join);
         if (h->join2) cudaEventDestroy(h->join2);

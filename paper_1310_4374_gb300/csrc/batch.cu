@@ -338,7 +338,7 @@ struct psum_batch_s {
     // the packing, joined before the constants): they fill the SMs the persistent charge kernel
     // releases during its last work items
     cudaStream_t side = nullptr, side2 = nullptr;   // check sums and fits; box means
-    cudaEvent_t fork = nullptr, join = nullptr, join2 = nullptr;
+    cudaEvent_t fork0 = nullptr, fork = nullptr, join = nullptr, join2 = nullptr;
     cudaGraphExec_t exec = nullptr;
     const void* g_args[5] = {};
     int64_t launches = 0;
@@ -447,6 +447,13 @@ int queue_batch(psum_batch_s* bt, const double* x, const double* q, double* phi,
     const bool fp32 = bt->precision != PSUM_FP64;   // float32 packing (FP32C and FF)
     const int B = bt->B;
     int64_t nl = 0;
+    // the box means need only the caller's charges: on the second side stream (least urgent
+    // priority) from the start, where they fill the SMs that validation, sort and packing leave
+    // idle, and the tail of the charge kernel
+    BTRY(cudaEventRecord(bt->fork0, st));
+    BTRY(cudaStreamWaitEvent(bt->side2, bt->fork0, 0));
+    k_bbox_mean<<<bt->n_seg, kSeg, 0, bt->side2>>>(x, q, bt->d_sys, bt->d_seg_sys, bt->d_seg_start, bt->mean_part);
+    BTRY(cudaEventRecord(bt->join2, bt->side2));
     BTRY(cudaMemsetAsync(bt->d_status, 0, sizeof(int) * B, st));
     k_bvalidate<<<bt->n_seg, kSeg, 0, st>>>(x, q, bt->d_sys, bt->d_seg_sys, bt->d_seg_start, bt->val_part,
                                             bt->d_status);
@@ -490,7 +497,7 @@ int queue_batch(psum_batch_s* bt, const double* x, const double* q, double* phi,
         BTRY(launch_near64(false, bt->pk64, bt->d_chk64, bt->d_cshifts, bt->part_c, bt->Lc, bt->side, 0.0, bt->d_cw,
                            bt->c_cls));
     }
-    // side stream: the check sums' reduction, the right-hand sides, the fits and the box means
+    // side stream: the check sums' reduction, the right-hand sides and the fits
     const int tile = fp32 ? kTile32 : kTile64;
     cudaStream_t sd = bt->side;
     BTRY(launch_near_reduce(bt->part_c, bt->n_chk_pts, tile, 1, bt->Lc, bt->phi_c, nullptr, sd));
@@ -499,9 +506,6 @@ int queue_batch(psum_batch_s* bt, const double* x, const double* q, double* phi,
     k_brhs<<<dim3((maxM + 255) / 256, B), 256, 0, sd>>>(bt->d_sys, bt->phi_c, bt->f);
     k_bproject<<<dim3((maxP - 1 + 7) / 8, B), 256, 0, sd>>>(bt->d_sys, bt->f, bt->C);
     BTRY(cudaEventRecord(bt->join, sd));
-    BTRY(cudaStreamWaitEvent(bt->side2, bt->fork, 0));
-    k_bbox_mean<<<bt->n_seg, kSeg, 0, bt->side2>>>(x, q, bt->d_sys, bt->d_seg_sys, bt->d_seg_start, bt->mean_part);
-    BTRY(cudaEventRecord(bt->join2, bt->side2));
     if (variant == kVariantSym)
         BTRY(launch_sym_reduce(bt->part_s, bt->n_pts, bt->Ls, bt->phi_n, bt->grad_n, st));
     else
@@ -618,6 +622,7 @@ void release(psum_batch_s* bt) {
     if (bt->side2) cudaStreamDestroy(bt->side2);
     if (bt->join2) cudaEventDestroy(bt->join2);
     if (bt->fork) cudaEventDestroy(bt->fork);
+    if (bt->fork0) cudaEventDestroy(bt->fork0);
     if (bt->join) cudaEventDestroy(bt->join);
     cudaFree(bt->mem);
     if (bt->h_status) cudaFreeHost(bt->h_status);
@@ -729,6 +734,7 @@ int psum_batch_create(const psum_plan_t* plans, int B, const int64_t* offsets, p
         ss.tile0 = tile_n;
         ss.n_tiles = n_tiles;
         ss.n_chunks = n_chunks;
+        ss.last_n = n_chunks > 0 ? (int)(n - (n_chunks - 1) * kNearChunk) : 0;
         ss.shift0 = shift0;
         ss.n_img = pl.n_images;
         bt->sym_sys[b] = ss;
@@ -876,6 +882,7 @@ int psum_batch_create(const psum_plan_t* plans, int B, const int64_t* offsets, p
     }
     if (st == PSUM_OK) st = cuda_st(cudaEventCreateWithFlags(&bt->join2, cudaEventDisableTiming));
     if (st == PSUM_OK) st = cuda_st(cudaEventCreateWithFlags(&bt->fork, cudaEventDisableTiming));
+    if (st == PSUM_OK) st = cuda_st(cudaEventCreateWithFlags(&bt->fork0, cudaEventDisableTiming));
     if (st == PSUM_OK) st = cuda_st(cudaEventCreateWithFlags(&bt->join, cudaEventDisableTiming));
     if (st != PSUM_OK) {
         release(bt);

@@ -381,6 +381,10 @@ __global__ void __launch_bounds__(kThreads32, kMinB) k_near32s(Near32SymArgs a) 
             bulk_g2s(s_hi, a.pk_hi + chunk * (2 * kNearChunk), kChunkBytes, &s_bar);
             bulk_g2s(s_lo, a.pk_lo + chunk * (2 * kNearChunk), kChunkBytes, &s_bar);
         }
+        // the system's last chunk holds last_n charges and padding: source blocks of padding
+        // alone are skipped (their reactions stay zero)
+        const int nv = chunk == S.tile0 * kTgt32 + S.n_chunks - 1 && S.last_n > 0 ? S.last_n : kNearChunk;
+        const int nb32 = (nv + 31) >> 5, nb64 = (nv + 63) >> 6;
         const double* so = a.org + 4 * chunk;
         for (int im = tid; im < nimg; im += kThreads32) {
             const double* sh = a.shifts + 3 * (S.shift0 + im0 + im);
@@ -450,7 +454,7 @@ __global__ void __launch_bounds__(kThreads32, kMinB) k_near32s(Near32SymArgs a) 
                     } else {
                         const float2 tqh = s_tq[j][tid], tql = s_tql[kFF ? j : 0][tid];
 #pragma unroll 1
-                        for (int g = 0; g < kNearChunk / 32; ++g) {
+                        for (int g = 0; g < nb32; ++g) {
                             float r[4][2] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
 #pragma unroll 1
                             for (int k = 0; k < 32; ++k) {
@@ -567,7 +571,7 @@ __global__ void __launch_bounds__(kThreads32, kMinB) k_near32s(Near32SymArgs a) 
 #pragma unroll
                 for (int i2 = 0; i2 < 4; ++i2) ph[i2] = pc[i2] = gx[i2] = gy[i2] = gz[i2] = make_float2(0.f, 0.f);
 #pragma unroll 1
-                for (int g = 0; g < kNearChunk / 64; ++g) {
+                for (int g = 0; g < nb64; ++g) {
                     float2 rp = make_float2(0.f, 0.f), rx = rp, ry = rp, rz = rp, st0 = rp, st1 = rp, st2 = rp;
 #pragma unroll 1
                     for (int k = 0; k < 32; ++k) {
@@ -651,7 +655,7 @@ __global__ void __launch_bounds__(kThreads32, kMinB) k_near32s(Near32SymArgs a) 
 #pragma unroll
                 for (int i2 = 0; i2 < 4; ++i2) ph[i2] = gx[i2] = gy[i2] = gz[i2] = make_float2(0.f, 0.f);
 #pragma unroll 1
-                for (int g = 0; g < kNearChunk / 64; ++g) {
+                for (int g = 0; g < nb64; ++g) {
                     float2 rp = make_float2(0.f, 0.f), rx = rp, ry = rp, rz = rp;
 #pragma unroll 1
                     for (int k = 0; k < 32; ++k) {
@@ -713,7 +717,7 @@ __global__ void __launch_bounds__(kThreads32, kMinB) k_near32s(Near32SymArgs a) 
                     }
                 }
 #pragma unroll 1
-                for (int g = 0; g < kNearChunk / 32; ++g) {
+                for (int g = 0; g < nb32; ++g) {
                     float rp = 0.f, rpl = 0.f, rx = 0.f, ry = 0.f, rz = 0.f;
 #pragma unroll 1
                     for (int k0 = 0; k0 < 32; k0 += kNearFold) {
@@ -869,6 +873,8 @@ __global__ void __launch_bounds__(kThreads64, kMinB) k_near64s(Near64SymArgs a) 
         for (int k = 0; k < kNearChunk / 32; ++k) s_re[warp][qi][32 * k + lane] = 0.0;
     __syncthreads();
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    // the system's last tile holds last_n charges: source blocks of padding alone are skipped
+    const int nb32 = tb == S.n_tiles - 1 && S.last_n > 0 ? (S.last_n + 31) >> 5 : kNearChunk / 32;
     for (int im = 0; im < nimg; ++im) {
         // y - x_i - p with the shift folded into the target
         const double* sh = a.shifts + 3 * (S.shift0 + im0 + im);
@@ -892,7 +898,7 @@ __global__ void __launch_bounds__(kThreads64, kMinB) k_near64s(Near64SymArgs a) 
             continue;
         }
 #pragma unroll 1
-        for (int g = 0; g < kNearChunk / 32; ++g) {
+        for (int g = 0; g < nb32; ++g) {
             double rp = 0.0, rx = 0.0, ry = 0.0, rz = 0.0;
 #pragma unroll 2
             for (int k = 0; k < 32; ++k) {

@@ -434,6 +434,7 @@ struct SymSys {
     int64_t a0, a1;           // band of row tiles
     int shift0, n_img;        // image vectors shift0 .. shift0 + n_img - 1
     int n_g, img_per_g;       // image groups per tile pair and images per group
+    int last_n;               // charges in the system's last chunk (1..kNearChunk; 0 = a full chunk)
 };
 struct SymSysTable {
     SymSys one;
@@ -642,7 +643,7 @@ struct psum_plan_s {
     // after the packing and joined before the fit, so that they fill the SMs the persistent
     // charge kernel releases during its last work items
     cudaStream_t side = nullptr, side2 = nullptr;   // check sums; box mean
-    cudaEvent_t fork = nullptr, join = nullptr, join2 = nullptr;
+    cudaEvent_t fork0 = nullptr, fork = nullptr, join = nullptr, join2 = nullptr;
     // psum_eval_graph: one evaluation captured into a CUDA graph, replayed while the
     // arguments and the scratch buffer stay the same
     cudaStream_t cap = nullptr;
