@@ -61,6 +61,7 @@ struct Layout {
     uint32_t *ka, *va, *kb, *vb, *hist;
     float4 *pk32, *pk32lo;
     double* org;
+    float4* ext;         // per charge group: bounding-box half extents (the symmetric kernel's near test)
     double* xs;          // float64 packed source positions (trimmed plans)
     // FP64
     double4_32a* pk64;
@@ -186,6 +187,7 @@ size_t layout(Plan& pl, int64_t N, char* base, Layout& L, bool backward = false,
         L.pk32 = b.take<float4>(2 * (size_t)L.n_src_pts);
         L.pk32lo = b.take<float4>(2 * (size_t)L.n_src_pts);
         L.org = b.take<double>(4 * (size_t)L.n_src_groups);
+        L.ext = L.sym ? b.take<float4>(L.n_src_groups) : nullptr;
         L.pk64 = nullptr;
         if (sep) {
             L.tka = b.take<uint32_t>(T);
@@ -232,6 +234,7 @@ size_t layout(Plan& pl, int64_t N, char* base, Layout& L, bool backward = false,
         L.ka = L.va = L.kb = L.vb = L.hist = nullptr;
         L.pk32 = L.pk32lo = nullptr;
         L.org = nullptr;
+        L.ext = nullptr;
         L.xs = nullptr;
         L.pk64 = b.take<double4_32a>((size_t)L.n_src_pts);
         if (sep) L.tpk64 = b.take<double4_32a>((size_t)L.n_pts);
@@ -364,7 +367,7 @@ int queue_forward(psum_plan_s* h, int64_t N, const double* x, const double* q, d
     if (fp32) {
         TRY(launch_morton_sort(x, N, o.d, L.ka, L.va, L.kb, L.vb, L.hist, st));
         perm = (const int*)L.va;
-        TRY(launch_pack32(x, q, L.va, N, L.n_src_groups, L.pk32, L.pk32lo, L.org, st, L.xs));
+        TRY(launch_pack32(x, q, L.va, N, L.n_src_groups, L.pk32, L.pk32lo, L.org, st, L.xs, L.ext));
         h->launches += morton_sort_launches(N) + 1;
     } else {
         TRY(launch_pack64(x, q, N, L.n_src_pts, L.pk64, st));
@@ -401,7 +404,8 @@ int queue_forward(psum_plan_s* h, int64_t N, const double* x, const double* q, d
         for (int64_t k = 0; k < L.sym_bands; ++k) {
             const NearSymLaunch S = sym_band_launch(L, k, h->inject_timeout, h->debug_limit);
             if (fp32)
-                TRY(launch_near32s(L.pk32, L.pk32lo, L.org, pl.d_shifts, L.part_n, S, st, ff, refined_terms(pl)));
+                TRY(launch_near32s(L.pk32, L.pk32lo, L.org, L.ext, pl.d_shifts, L.part_n, S, st, ff,
+                                   refined_terms(pl)));
             else
                 TRY(launch_near64s(L.pk64, pl.d_shifts, L.part_n, S, st));
             if (k + 1 < L.sym_bands) TRY(launch_sym_reduce(L.part_n, N, S, L.phi_n, L.grad_n, st, !fp32, k > 0));

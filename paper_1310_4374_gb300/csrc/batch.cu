@@ -316,6 +316,7 @@ struct psum_batch_s {
     uint32_t *ka = nullptr, *va = nullptr, *kb = nullptr, *vb = nullptr, *hist = nullptr;
     float4 *pk_hi = nullptr, *pk_lo = nullptr;
     double* org = nullptr;
+    float4* ext = nullptr;   // per group: bounding-box half extents (the symmetric kernel's near test)
     double4_32a* pk64 = nullptr;
     double *part_n = nullptr, *part_c = nullptr, *phi_n = nullptr, *grad_n = nullptr, *phi_c = nullptr;
     double *f = nullptr, *C = nullptr, *val_part = nullptr, *mean_part = nullptr;
@@ -407,6 +408,7 @@ size_t batch_layout(psum_batch_s* bt, char* base) {
         bt->pk_hi = b.take<float4>(2 * (size_t)bt->n_pts);
         bt->pk_lo = b.take<float4>(2 * (size_t)bt->n_pts);
         bt->org = b.take<double>(4 * (size_t)bt->n_groups);
+        bt->ext = b.take<float4>(bt->n_groups);
     } else {
         bt->d_chk64 = b.take<double4_32a>(bt->n_chk_pts);
         bt->pk64 = b.take<double4_32a>(bt->n_pts);
@@ -475,12 +477,12 @@ int queue_batch(psum_batch_s* bt, const double* x, const double* q, double* phi,
         }
         perm = bt->va;
         BTRY(launch_pack32_groups(x, q, perm, bt->n_groups, bt->d_grp_start, bt->d_grp_count, bt->pk_hi, bt->pk_lo,
-                                  bt->org, st));
+                                  bt->org, st, bt->ext));
         nl += 1 + 12 + 1;
         const bool ff = bt->precision == PSUM_FF;
         BTRY(cudaEventRecord(bt->fork, st));
         if (variant == kVariantSym)
-            BTRY(launch_near32s(bt->pk_hi, bt->pk_lo, bt->org, bt->d_shifts, bt->part_s, bt->Ls, st));
+            BTRY(launch_near32s(bt->pk_hi, bt->pk_lo, bt->org, bt->ext, bt->d_shifts, bt->part_s, bt->Ls, st));
         else
             BTRY(launch_near32(true, bt->pk_hi, bt->pk_lo, bt->org, bt->pk_hi, bt->pk_lo, bt->org, bt->d_shifts,
                                bt->part_n, bt->Ln[variant], st, variant, nullptr, 0.0, ff));
@@ -572,7 +574,7 @@ int autotune(psum_batch_s* bt, cudaStream_t st) {
         for (int rep = 0; rep < 3; ++rep) {
             BTRY(cudaEventRecord(e0, st));
             if (v == kVariantSym) {
-                BTRY(launch_near32s(bt->pk_hi, bt->pk_lo, bt->org, bt->d_shifts, bt->part_s, bt->Ls, st));
+                BTRY(launch_near32s(bt->pk_hi, bt->pk_lo, bt->org, bt->ext, bt->d_shifts, bt->part_s, bt->Ls, st));
                 BTRY(launch_sym_reduce(bt->part_s, bt->n_pts, bt->Ls, bt->phi_n, bt->grad_n, st));
             } else {
                 BTRY(launch_near32(true, bt->pk_hi, bt->pk_lo, bt->org, bt->pk_hi, bt->pk_lo, bt->org, bt->d_shifts,

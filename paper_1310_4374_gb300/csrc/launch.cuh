@@ -30,9 +30,9 @@ int near32_occupancy_ctas(int n_img, int variant = 0, bool trimmed = false, bool
 #define PSUM_CHECK_VARIANT 0
 #endif
 constexpr int kCheckVariant = PSUM_CHECK_VARIANT;
-cudaError_t launch_near32s(const float4* pk_hi, const float4* pk_lo, const double* org, const double* shifts,
-                           double* partial, const NearSymLaunch& S, cudaStream_t st, bool ff = false,
-                           bool refine = false);
+cudaError_t launch_near32s(const float4* pk_hi, const float4* pk_lo, const double* org, const float4* ext,
+                           const double* shifts, double* partial, const NearSymLaunch& S, cudaStream_t st,
+                           bool ff = false, bool refine = false);
 cudaError_t launch_sym_reduce(const double* partial, int64_t n_valid, const NearSymLaunch& S, double* out_phi,
                               double* out_grad, cudaStream_t st, bool fp64 = false, bool accumulate = false);
 cudaError_t launch_near64s(const double4_32a* pk, const double* shifts, double* partial, const NearSymLaunch& S,
@@ -47,13 +47,14 @@ int morton_sort_launches(int64_t n);   // kernels launch_morton_sort queues for 
 cudaError_t launch_morton_sort(const double* x, int64_t n, const double d[3], uint32_t* ka, uint32_t* va,
                                uint32_t* kb, uint32_t* vb, uint32_t* hist, cudaStream_t st);
 cudaError_t launch_pack32(const double* x, const double* q, const uint32_t* perm, int64_t n, int64_t n_groups,
-                          float4* pk_hi, float4* pk_lo, double* org, cudaStream_t st, double* xs = nullptr);
+                          float4* pk_hi, float4* pk_lo, double* org, cudaStream_t st, double* xs = nullptr,
+                          float4* ext = nullptr);
 cudaError_t launch_pack64(const double* x, const double* q, int64_t n, int64_t n_pad, double4_32a* pk, cudaStream_t st);
 cudaError_t launch_radix_sort(uint32_t* ka, uint32_t* va, uint32_t* kb, uint32_t* vb, uint32_t* hist, int64_t n,
                               int passes, cudaStream_t st);
 cudaError_t launch_pack32_groups(const double* x, const double* q, const uint32_t* perm, int64_t n_groups,
                                  const int64_t* grp_start, const int* grp_count, float4* pk_hi, float4* pk_lo,
-                                 double* org, cudaStream_t st);
+                                 double* org, cudaStream_t st, float4* ext = nullptr);
 cudaError_t launch_pack64_groups(const double* x, const double* q, int64_t n_pts, const int64_t* grp_start,
                                  const int* grp_count, double4_32a* pk, cudaStream_t st);
 // far.cu

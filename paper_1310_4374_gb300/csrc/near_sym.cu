@@ -43,6 +43,8 @@ struct Near32SymArgs {
     const float4* pk_hi;     // the charges' pack: 2 float4 per point, (x,x,y,y),(z,z,q,q) offsets
     const float4* pk_lo;     // their float32 rounding remainders
     const double* org;       // 4 per group of 128 points: origin x, y, z and radius
+    const float4* ext;       // per group: bounding-box half extents about the origin (nullptr: the
+                             // near test compares origin distances with the radii alone)
     const double* shifts;    // image vectors, 3 per image, systems one after another
     double* partial;         // per system [n_tiles][n_tiles * n_g][4][kTile32] from part0
     SymSysTable tab;
@@ -404,8 +406,20 @@ __global__ void __launch_bounds__(kThreads32, kMinB) k_near32s(Near32SymArgs a) 
                 dl[0] = (float)D0; dl[1] = (float)D1; dl[2] = (float)D2;
                 dl[3] = (float)(D0 - (double)dl[0]); dl[4] = (float)(D1 - (double)dl[1]);
                 dl[5] = (float)(D2 - (double)dl[2]);
-                const double reach = kNearFactor * (to[3] + so[3]);
-                if (D0 * D0 + D1 * D1 + D2 * D2 <= reach * reach) nr |= k < 2 ? kUnitNear0 : kUnitNear1;
+                bool near;
+                if (a.ext) {
+                    // the gap between the two bounding boxes bounds every pair distance from below
+                    const float4 ht = a.ext[TA * kTgt32 + k], hs = a.ext[chunk];
+                    const double g0 = fmax(0.0, fabs(D0) - ((double)ht.x + (double)hs.x));
+                    const double g1 = fmax(0.0, fabs(D1) - ((double)ht.y + (double)hs.y));
+                    const double g2 = fmax(0.0, fabs(D2) - ((double)ht.z + (double)hs.z));
+                    const double gap = (kNearFactor - 1.0) * (to[3] + so[3]);
+                    near = g0 * g0 + g1 * g1 + g2 * g2 <= gap * gap;
+                } else {
+                    const double reach = kNearFactor * (to[3] + so[3]);
+                    near = D0 * D0 + D1 * D1 + D2 * D2 <= reach * reach;
+                }
+                if (near) nr |= k < 2 ? kUnitNear0 : kUnitNear1;
             }
             s_near[im] = nr;
         }
@@ -1053,14 +1067,15 @@ cudaError_t near32s_allow_smem() {
                                 bytes);
 }
 
-cudaError_t launch_near32s(const float4* pk_hi, const float4* pk_lo, const double* org, const double* shifts,
-                           double* partial, const NearSymLaunch& S, cudaStream_t st, bool ff, bool refine) {
+cudaError_t launch_near32s(const float4* pk_hi, const float4* pk_lo, const double* org, const float4* ext,
+                           const double* shifts, double* partial, const NearSymLaunch& S, cudaStream_t st, bool ff,
+                           bool refine) {
     if (!S.counter || !S.status || S.n_status < 1 || S.max_ipg < 1) return cudaErrorInvalidValue;
     if (S.W <= 0) return cudaSuccess;
     const cudaError_t ea = near32s_allow_smem();
     if (ea != cudaSuccess) return ea;
     Near32SymArgs a;
-    a.pk_hi = pk_hi; a.pk_lo = pk_lo; a.org = org; a.shifts = shifts; a.partial = partial;
+    a.pk_hi = pk_hi; a.pk_lo = pk_lo; a.org = org; a.ext = ext; a.shifts = shifts; a.partial = partial;
     a.tab = S.tab; a.W = S.W; a.max_ipg = S.max_ipg;
     a.counter = S.counter; a.status = S.status; a.n_status = S.n_status; a.inject = S.inject;
     a.limit = sym_limit(S);

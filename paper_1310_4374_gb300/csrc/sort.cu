@@ -129,7 +129,8 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(const uint32_t* _
 // each point's offset from the origin is split into a float32 hi part and the float32
 // rounding remainder lo, packed two float4 each: (x,x,y,y),(z,z,q,q) and (xl,xl,yl,yl),(zl,zl,ql,ql)
 // (ql = q - float(q), read only by the float-float kernels).
-// Padding points (s >= n) get q = 0 and a far-away position.
+// Padding points (s >= n) get q = 0 and a far-away position.  `ext` (optional) receives each
+// group's bounding-box half extents about its origin.
 // With a group table (batches) group g covers the sorted positions
 // [grp_start[g], grp_start[g] + grp_count[g]); without one, [128 g, min(128 (g+1), n)).
 constexpr int kPackWarps = 4;   // warps (groups) per block of k_pack32
@@ -138,7 +139,7 @@ __global__ void __launch_bounds__(32 * kPackWarps) k_pack32(const double* __rest
                          const uint32_t* __restrict__ perm, int64_t n, int64_t n_groups,
                          const int64_t* __restrict__ grp_start, const int* __restrict__ grp_count,
                          float4* __restrict__ pk_hi, float4* __restrict__ pk_lo, double* __restrict__ org,
-                         double* __restrict__ xs) {
+                         double* __restrict__ xs, float4* __restrict__ ext) {
     const int64_t grp = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (grp >= n_groups) return;
@@ -223,6 +224,12 @@ __global__ void __launch_bounds__(32 * kPackWarps) k_pack32(const double* __rest
     if (lane == 0) {
         org[4 * grp] = o[0]; org[4 * grp + 1] = o[1]; org[4 * grp + 2] = o[2];
         org[4 * grp + 3] = sqrt(r2max);
+        if (ext) {
+            // half extents of the bounding box about the origin, rounded up (never smaller)
+            float h[3];
+            for (int c = 0; c < 3; ++c) h[c] = lo[c] <= hi[c] ? __double2float_ru(fmax(hi[c] - o[c], o[c] - lo[c])) : 0.f;
+            ext[grp] = make_float4(h[0], h[1], h[2], 0.f);
+        }
     }
 }
 
@@ -333,20 +340,20 @@ cudaError_t launch_morton_sort(const double* x, int64_t n, const double d[3], ui
 }
 
 cudaError_t launch_pack32(const double* x, const double* q, const uint32_t* perm, int64_t n, int64_t n_groups,
-                          float4* pk_hi, float4* pk_lo, double* org, cudaStream_t st, double* xs) {
+                          float4* pk_hi, float4* pk_lo, double* org, cudaStream_t st, double* xs, float4* ext) {
     const int warps = kPackWarps;
     k_pack32<<<(unsigned)((n_groups + warps - 1) / warps), 32 * warps, 0, st>>>(x, q, perm, n, n_groups, nullptr,
-                                                                                  nullptr, pk_hi, pk_lo, org, xs);
+                                                                                  nullptr, pk_hi, pk_lo, org, xs, ext);
     return cudaGetLastError();
 }
 
 cudaError_t launch_pack32_groups(const double* x, const double* q, const uint32_t* perm, int64_t n_groups,
                                  const int64_t* grp_start, const int* grp_count, float4* pk_hi, float4* pk_lo,
-                                 double* org, cudaStream_t st) {
+                                 double* org, cudaStream_t st, float4* ext) {
     const int warps = kPackWarps;
     k_pack32<<<(unsigned)((n_groups + warps - 1) / warps), 32 * warps, 0, st>>>(x, q, perm, 0, n_groups, grp_start,
                                                                                   grp_count, pk_hi, pk_lo, org,
-                                                                                  nullptr);
+                                                                                  nullptr, ext);
     return cudaGetLastError();
 }
 
