@@ -197,12 +197,16 @@ __global__ void __launch_bounds__(kThreads32, kMinB) k_near32(Near32Args a) {
             }
             const double* so = a.src_org + 4 * chunk;
             const int shift0 = Sp->shift0;
+            // the item's units of this chunk are its images img .. im_hi - 1 (images innermost):
+            // only those get offsets and classes
+            const int im_lo = img;
+            const int im_hi = (int)(u_end - u < (int64_t)(n_img - img) ? img + (u_end - u) : n_img);
             if (!kGrad && ncls > 1) {
                 // per (image, group, class): the offset with the class's layer image, its
                 // weight; a unit is near when a class present in a group is near
-                for (int im = tid; im < n_img; im += kThreads32) s_near[im] = 0;
+                for (int im = im_lo + tid; im < im_hi; im += kThreads32) s_near[im] = 0;
                 __syncthreads();
-                for (int e = tid; e < n_img * kTgt32 * ncls; e += kThreads32) {
+                for (int e = im_lo * kTgt32 * ncls + tid; e < im_hi * kTgt32 * ncls; e += kThreads32) {
                     const int im = e / (kTgt32 * ncls), r = e - im * kTgt32 * ncls;
                     const int k = r / ncls, c = r - k * ncls;
                     // a class no target of the group has (padding included) is never read
@@ -229,10 +233,10 @@ __global__ void __launch_bounds__(kThreads32, kMinB) k_near32(Near32Args a) {
                 __syncthreads();
                 // an image whose weight is zero for every class present (a padding layer image
                 // of an anisotropic block) adds nothing to any target: skip its unit
-                for (int im = tid; im < n_img; im += kThreads32)
+                for (int im = im_lo + tid; im < im_hi; im += kThreads32)
                     s_near[im] = (s_near[im] & kUnitWeighted) ? (s_near[im] & ~kUnitWeighted) : kUnitOutside;
             } else
-            for (int im = tid; im < n_img; im += kThreads32) {
+            for (int im = im_lo + tid; im < im_hi; im += kThreads32) {
                 const int img0 = a.chunk_img0 ? a.chunk_img0[chunk] : shift0;
                 const double* sh = a.shifts + 3 * (img0 + im);
                 int nr = 0;

@@ -152,6 +152,33 @@ __device__ __forceinline__ void pair_loop_far(const float4* __restrict__ s_hi, c
     float2 bphi[NP];
 #pragma unroll
     for (int j = 0; j < NP; ++j) bphi[j] = make_float2(0.f, 0.f);
+    if constexpr (!kGrad) {
+        // potential only: each term q / r enters its sum by one fused multiply-add
+#pragma unroll kFarUnroll
+        for (int s = 0; s < n; s += 2) {
+            const float4 A0 = s_hi[2 * s], B0 = s_hi[2 * s + 1];
+            const float4 A1 = s_hi[2 * s + 2], B1 = s_hi[2 * s + 3];
+#pragma unroll
+            for (int j = 0; j < NP; ++j) {
+                const float2 ex0 = __fadd2_rn(make_float2(A0.x, A0.y), nx[j]);
+                const float2 ey0 = __fadd2_rn(make_float2(A0.z, A0.w), ny[j]);
+                const float2 ez0 = __fadd2_rn(make_float2(B0.x, B0.y), nz[j]);
+                const float2 ex1 = __fadd2_rn(make_float2(A1.x, A1.y), nx[j]);
+                const float2 ey1 = __fadd2_rn(make_float2(A1.z, A1.w), ny[j]);
+                const float2 ez1 = __fadd2_rn(make_float2(B1.x, B1.y), nz[j]);
+                float2 r0 = __fmul2_rn(ex0, ex0), r1 = __fmul2_rn(ex1, ex1);
+                r0 = __ffma2_rn(ey0, ey0, r0);
+                r1 = __ffma2_rn(ey1, ey1, r1);
+                r0 = __ffma2_rn(ez0, ez0, r0);
+                r1 = __ffma2_rn(ez1, ez1, r1);
+                aphi[j] = __ffma2_rn(make_float2(B0.z, B0.w), make_float2(rsqrt_mufu(r0.x), rsqrt_mufu(r0.y)), aphi[j]);
+                bphi[j] = __ffma2_rn(make_float2(B1.z, B1.w), make_float2(rsqrt_mufu(r1.x), rsqrt_mufu(r1.y)), bphi[j]);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < NP; ++j) aphi[j] = __fadd2_rn(aphi[j], bphi[j]);
+        return;
+    }
 #pragma unroll kFarUnroll
     for (int s = 0; s < n; s += 2) {
         float2 q0[NP], q1[NP];
