@@ -450,8 +450,7 @@ int queue_forward(psum_plan_s* h, int64_t N, const double* x, const double* q, d
     if (zero_mean && !early_mean) {
         cudaStream_t s2 = h->side2;
         TRY(cudaStreamWaitEvent(s2, h->fork, 0));
-        TRY(launch_box_mean_ball(x, q, fp32 ? L.va : nullptr, N, o.d, pl.d_shifts, pl.n_images, pl.Rb,
-                                 L.mean_part, L.nblk_mean, s2));
+        TRY(launch_box_mean_ball(x, q, fp32 ? L.va : nullptr, N, o.d, o.K, pl.Rb, L.mean_part, L.nblk_mean, s2));
         TRY(cudaEventRecord(h->join2, s2));
         h->launches += 1;
     }

@@ -185,7 +185,7 @@ __global__ void __launch_bounds__(kSeg) k_bbox_mean(const double* __restrict__ x
     double s = 0.0;
     if (i < S.n0 + S.n && S.zero_mean) {
         const double X[3] = {x[3 * i], x[3 * i + 1], x[3 * i + 2]};
-        s = q[i] * block_potential_inside(X, S.H);
+        s = q[i] * box_potential_paired(X, S.H);
     }
     __shared__ double ws[kSeg / 32];
     for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);

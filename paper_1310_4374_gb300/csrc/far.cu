@@ -100,37 +100,56 @@ __global__ void __launch_bounds__(kMeanThreads) k_box_mean(const double* __restr
         const int64_t i = k / kMeanTerms;
         const int j = (int)(k - i * kMeanTerms);
         const double X[3] = {x[3 * i], x[3 * i + 1], x[3 * i + 2]};
-        s += q[i] * block_potential_inside_term(X, H, j);
+        s += q[i] * box_potential_paired_term(X, H, j);
     }
     block_sum2<kMeanThreads>(s, dummy);
     if (threadIdx.x == 0) partial[blockIdx.x] = s;
 }
 
 // With the near set trimmed to the ball S_b (get step 2) every kept source image x + p
-// (|x + p| <= Rb, the same float64 test as the pair kernels) contributes the potential of
-// the single box at x + p (by the corner sum, the cheaper closed form for one box).  Which
-// images are kept depends on the charge, so the threads of
-// a warp take charges in Morton order when a permutation is given: neighbours keep nearly
-// the same images and the warp evaluates few potentials that only some of its lanes need.
+// (|x + p| <= Rb, the same float64 test as the pair kernels) contributes the potential of the
+// box at x + p.  Along a line of images (fixed offsets on axes 0 and 1) the kept ones come in
+// runs, and a run of boxes is one rod-shaped box: its potential is one regrouped corner sum
+// (12 logarithms, 12 arctangents) instead of one per box.  The covering block's lattice is
+// walked directly (i d_k is the image table's float64 value), so every kept test matches the
+// pair kernels'.  Which images are kept depends on the charge, so the threads of a warp take
+// charges in Morton order when a permutation is given: neighbours see nearly the same runs.
 __global__ void __launch_bounds__(kRedThreads) k_box_mean_ball(const double* __restrict__ x,
                                                                const double* __restrict__ q,
                                                                const uint32_t* __restrict__ perm, int64_t n,
-                                                               double H0, double H1, double H2,
-                                                               const double* __restrict__ shifts, int n_img,
-                                                               double Rb, double* __restrict__ partial) {
-    const double H[3] = {H0, H1, H2};
+                                                               double d0, double d1, double d2, int K0, int K1,
+                                                               int K2, double Rb, double* __restrict__ partial) {
+    const double Rb2 = __dmul_rn(Rb, Rb);
     double s = 0.0, dummy = 0.0;
     for (int64_t k = (int64_t)blockIdx.x * kRedThreads + threadIdx.x; k < n; k += (int64_t)gridDim.x * kRedThreads) {
         const int64_t i = perm ? (int64_t)perm[k] : k;
+        const double x0 = x[3 * i], x1 = x[3 * i + 1], x2 = x[3 * i + 2];
         double u = 0.0;
-        for (int im = 0; im < n_img; ++im) {
-            const double* p = shifts + 3 * im;
-            const double a = __dadd_rn(x[3 * i], p[0]), b = __dadd_rn(x[3 * i + 1], p[1]),
-                         c = __dadd_rn(x[3 * i + 2], p[2]);
-            const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(a, a), __dmul_rn(b, b)), __dmul_rn(c, c));
-            if (r2 <= __dmul_rn(Rb, Rb)) {
-                const double X[3] = {a, b, c};
-                u += block_potential_corners(X, H);
+        for (int i1 = -K0; i1 <= K0; ++i1) {
+            const double a = __dadd_rn(x0, i1 * d0);
+            for (int i2 = -K1; i2 <= K1; ++i2) {
+                const double b = __dadd_rn(x1, i2 * d1);
+                const double ab = __dadd_rn(__dmul_rn(a, a), __dmul_rn(b, b));
+                if (ab > Rb2) continue;            // c^2 >= 0: no image of this line is kept
+                int lo = 0;
+                bool run = false;
+                for (int i3 = -K2; i3 <= K2 + 1; ++i3) {
+                    bool kept = false;
+                    if (i3 <= K2) {
+                        const double c = __dadd_rn(x2, i3 * d2);
+                        kept = __dadd_rn(ab, __dmul_rn(c, c)) <= Rb2;
+                    }
+                    if (kept && !run) {
+                        lo = i3;
+                        run = true;
+                    } else if (!kept && run) {
+                        // the run lo .. i3 - 1: one box of i3 - lo images along axis 2
+                        const double X[3] = {a, b, x2 + 0.5 * (double)(lo + i3 - 1) * d2};
+                        const double H[3] = {0.5 * d0, 0.5 * d1, 0.5 * (double)(i3 - lo) * d2};
+                        u += box_potential_paired(X, H);
+                        run = false;
+                    }
+                }
             }
         }
         s += q[i] * u;
@@ -364,10 +383,9 @@ cudaError_t launch_box_mean(const double* x, const double* q, int64_t n, const d
 }
 
 cudaError_t launch_box_mean_ball(const double* x, const double* q, const uint32_t* perm, int64_t n,
-                                 const double d[3], const double* shifts, int n_img, double Rb, double* partial,
-                                 int nblk, cudaStream_t st) {
-    k_box_mean_ball<<<nblk, kRedThreads, 0, st>>>(x, q, perm, n, 0.5 * d[0], 0.5 * d[1], 0.5 * d[2], shifts, n_img,
-                                                 Rb, partial);
+                                 const double d[3], const int K[3], double Rb, double* partial, int nblk,
+                                 cudaStream_t st) {
+    k_box_mean_ball<<<nblk, kRedThreads, 0, st>>>(x, q, perm, n, d[0], d[1], d[2], K[0], K[1], K[2], Rb, partial);
     return cudaGetLastError();
 }
 

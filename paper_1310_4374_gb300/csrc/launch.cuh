@@ -72,8 +72,8 @@ cudaError_t launch_far_rbf(const double* x, int64_t n, const int* perm, const do
                            double* phi, double* grad, int* status_out, cudaStream_t st);
 // trimmed near set: sum over the kept images x + p (|x + p| <= Rb) of the single box's potential
 cudaError_t launch_box_mean_ball(const double* x, const double* q, const uint32_t* perm, int64_t n,
-                                 const double d[3], const double* shifts, int n_img, double Rb, double* partial,
-                                 int nblk, cudaStream_t st);
+                                 const double d[3], const int K[3], double Rb, double* partial, int nblk,
+                                 cudaStream_t st);
 cudaError_t launch_project(const double* pinv, int rows, int M, const double* phi_check, const int* check_pos,
                            double* f, double* C, cudaStream_t st, bool layers = false);
 cudaError_t launch_constant(double* C, const double* Rbox, int P, const double* mean_partial, int nblk,

@@ -55,51 +55,21 @@ __host__ __device__ __forceinline__ double block_potential(const double X[3], co
 // of coordinates of c take the lower bound, with
 //   F(a, b, c) = ab ln(c + r) + bc ln(a + r) + ca ln(b + r)
 //                - a^2/2 atan(bc/(ar)) - b^2/2 atan(ca/(br)) - c^2/2 atan(ab/(cr)),
-// r = |(a, b, c)|.  It needs 24 logarithms and 24 arctangents where the face/edge route
-// takes 48 and 96, so the device means use it (the block mean: 1.27 ms for 1e5 charges
-// by the face/edge route); the plan's RBF box means on the host keep the face/edge route.
-// The two agree to 1.2e-13 on 2e5 random points.  Vanishing products drop their term
-// (their limit is 0).
-__host__ __device__ __forceinline__ double log_plus_r(double a, double r, double rest2) {
-    // ln(a + r) with r^2 = a^2 + rest2, without cancellation for a < 0
-    return a >= 0.0 ? log(a + r) : log(rest2 / (r - a));
-}
+// r = |(a, b, c)|: 24 logarithms and 24 arctangents where the face/edge route takes 48 and
+// 96.  The device means evaluate it regrouped (below, 12 and 12); the plan's RBF box means on
+// the host keep the face/edge route.  On 2e5 random boxes and points, inside and outside, the
+// regrouped sum is within 2.9e-13 (relative) of a long-double corner sum, the plain float64
+// corner sum within 1.1e-12.  Vanishing products drop their term (their limit is 0).
 
-__host__ __device__ __forceinline__ double prism_corner(double a, double b, double c) {
-    const double a2 = a * a, b2 = b * b, c2 = c * c;
-    const double r = sqrt(a2 + b2 + c2);
-    double f = 0.0;
-    if (a * b != 0.0) f += a * b * log_plus_r(c, r, a2 + b2);
-    if (b * c != 0.0) f += b * c * log_plus_r(a, r, b2 + c2);
-    if (c * a != 0.0) f += c * a * log_plus_r(b, r, c2 + a2);
-    if (a != 0.0 && b * c != 0.0) f -= 0.5 * a2 * atan(b * c / (a * r));
-    if (b != 0.0 && c * a != 0.0) f -= 0.5 * b2 * atan(c * a / (b * r));
-    if (c != 0.0 && a * b != 0.0) f -= 0.5 * c2 * atan(a * b / (c * r));
-    return f;
-}
-
-__host__ __device__ __forceinline__ double block_potential_corners(const double X[3], const double H[3]) {
-    double U = 0.0;
-#pragma unroll 1
-    for (int k = 0; k < 8; ++k) {
-        const double a = (k & 1) ? H[0] - X[0] : -H[0] - X[0];
-        const double b = (k & 2) ? H[1] - X[1] : -H[1] - X[1];
-        const double c = (k & 4) ? H[2] - X[2] : -H[2] - X[2];
-        const int lower = !(k & 1) + !(k & 2) + !(k & 4);
-        const double f = prism_corner(a, b, c);
-        U += (lower & 1) ? -f : f;
-    }
-    return U;
-}
-
-// The corner sum regrouped for a point inside the block (upper corner offsets positive, lower
-// ones negative or, on a lower face, zero).  Take an axis k and one of
+// The corner sum regrouped (any point; the block's own means have it inside, the ball's mean
+// also outside).  Take an axis k and one of
 // the four corners (p, q) of the other two axes ((k+1, k+2) cyclically): the two block corners
 // that differ in k alone carry opposite signs, and F's terms p q ln(k + r) and
 // -p^2/2 atan(q k/(p r)) of the two combine, with (k_u, r_u) and (k_l, r_l) the upper and lower
 // corner's offset along k and distance:
 //   ln(k_u + r_u) - ln(k_l + r_l) = ln((k_u + r_u)(r_l - k_l) / (p^2 + q^2))
-//     (k_l + r_l = (p^2 + q^2)/(r_l - k_l), no cancellation as k_l < 0),
+//     (k_l + r_l = (p^2 + q^2)/(r_l - k_l), no cancellation where k_l < 0 < k_u; with both
+//      offsets positive the plain ratio, with both at most zero the ratio of the r - k forms),
 //   atan(u) - atan(v) = atan2(p q (k_u r_l - k_l r_u), p^2 r_u r_l + q^2 k_u k_l)
 //     (u, v the two arguments: arg((1 + iu)(1 - iv)) with the factor p^2 r_u r_l > 0 taken out;
 //      the difference lies in (-pi, pi), so the principal value is exact).
@@ -108,16 +78,22 @@ __host__ __device__ __forceinline__ double block_potential_corners(const double 
 __host__ __device__ __forceinline__ double block_pair_term(double p, double q, double ku, double kl, double ru,
                                                            double rl) {
     // a vanishing p q drops the logarithm (its limit is 0; a charge on a face of a block with
-    // K_k = 0 can make p, q or k_l zero)
+    // K_k = 0 can make p, q or k_l zero).  The log's argument is formed without cancellation
+    // wherever the point lies along the axis: below the box (k_l > 0) as (k_u + r_u)/(k_l + r_l),
+    // above it (k_u <= 0) as (r_l - k_l)/(r_u - k_u), level with it as above.
     const double pq2 = p * p + q * q;
-    const double L = p * q != 0.0 ? p * q * log((ku + ru) * (rl - kl) / pq2) : 0.0;
+    double L = 0.0;
+    if (p * q != 0.0) {
+        const double arg = kl > 0.0 ? (ku + ru) / (kl + rl) : ku <= 0.0 ? (rl - kl) / (ru - ku) : (ku + ru) * (rl - kl) / pq2;
+        L = p * q * log(arg);
+    }
     const double A = 0.5 * p * p * atan2(p * q * (ku * rl - kl * ru), p * p * ru * rl + q * q * ku * kl);
     return L - A;
 }
 
 // Term j (0..11) of the regrouped corner sum: axis k = j / 4, the other two axes' corner from
 // j % 4 (bit 0: p upper, bit 1: q upper), signed +1 when an even number of p, q is lower.
-__host__ __device__ __forceinline__ double block_potential_inside_term(const double X[3], const double H[3], int j) {
+__host__ __device__ __forceinline__ double box_potential_paired_term(const double X[3], const double H[3], int j) {
     const int k = j >> 2, k1 = k == 2 ? 0 : k + 1, k2 = k == 0 ? 2 : k - 1;
     const double p = (j & 1) ? H[k1] - X[k1] : -H[k1] - X[k1];
     const double q = (j & 2) ? H[k2] - X[k2] : -H[k2] - X[k2];
@@ -128,9 +104,9 @@ __host__ __device__ __forceinline__ double block_potential_inside_term(const dou
     return (lower & 1) ? -t : t;
 }
 
-// U(x) over the block for x inside it (-H_k <= x_k < H_k): the 12 regrouped terms, the
-// distances of the 8 corners computed once.
-__host__ __device__ __forceinline__ double block_potential_inside(const double X[3], const double H[3]) {
+// U(x) of the box [-H, H] at any point x: the 12 regrouped terms, the distances of the 8
+// corners computed once.
+__host__ __device__ __forceinline__ double box_potential_paired(const double X[3], const double H[3]) {
     const double lo[3] = {-H[0] - X[0], -H[1] - X[1], -H[2] - X[2]};
     const double up[3] = {H[0] - X[0], H[1] - X[1], H[2] - X[2]};
     double r[8];                          // corner c: bit k set = upper along axis k
