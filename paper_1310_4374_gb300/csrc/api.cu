@@ -365,10 +365,10 @@ int queue_forward(psum_plan_s* h, int64_t N, const double* x, const double* q, d
     h->launches += 2;
     const int* perm = nullptr;
     if (fp32) {
-        TRY(launch_morton_sort(x, N, o.d, L.ka, L.va, L.kb, L.vb, L.hist, st));
+        TRY(launch_curve_sort(x, N, o.d, L.ka, L.va, L.kb, L.vb, L.hist, st));
         perm = (const int*)L.va;
         TRY(launch_pack32(x, q, L.va, N, L.n_src_groups, L.pk32, L.pk32lo, L.org, st, L.xs, L.ext));
-        h->launches += morton_sort_launches(N) + 1;
+        h->launches += curve_sort_launches(N) + 1;
     } else {
         TRY(launch_pack64(x, q, N, L.n_src_pts, L.pk64, st));
         h->launches += 1;
@@ -380,10 +380,10 @@ int queue_forward(psum_plan_s* h, int64_t N, const double* x, const double* q, d
         TRY(launch_validate_points(y, T, o.d, L.nblk_val, L.eval_status, st));
         h->launches += 1;
         if (fp32) {
-            TRY(launch_morton_sort(y, T, o.d, L.tka, L.tva, L.tkb, L.tvb, L.thist, st));
+            TRY(launch_curve_sort(y, T, o.d, L.tka, L.tva, L.tkb, L.tvb, L.thist, st));
             eperm = (const int*)L.tva;
             TRY(launch_pack32(y, nullptr, L.tva, T, L.n_tiles * kTgt32, L.tpk32, L.tpk32lo, L.torg, st));
-            h->launches += morton_sort_launches(T) + 1;
+            h->launches += curve_sort_launches(T) + 1;
         } else {
             TRY(launch_pack64(y, nullptr, T, L.n_pts, L.tpk64, st));
             h->launches += 1;
@@ -523,10 +523,10 @@ int backward_device(psum_plan_s* h, int64_t N, const double* x, const double* q,
     TRY(cudaMemsetAsync(L.eval_status, 0, sizeof(int), st));
     const int* perm = nullptr;
     if (fp32) {
-        TRY(launch_morton_sort(x, N, o.d, L.ka, L.va, L.kb, L.vb, L.hist, st));
+        TRY(launch_curve_sort(x, N, o.d, L.ka, L.va, L.kb, L.vb, L.hist, st));
         perm = (const int*)L.va;
         TRY(launch_pack32(x, q, L.va, N, L.n_src_groups, L.pk32, L.pk32lo, L.org, st));
-        h->launches += morton_sort_launches(N) + 1;
+        h->launches += curve_sort_launches(N) + 1;
     } else {
         TRY(launch_pack64(x, q, N, L.n_src_pts, L.pk64, st));
         h->launches += 1;

@@ -21,8 +21,8 @@
 namespace psum {
 
 constexpr int kSeg = 128;        // charges per segment (validation, mean, far field)
-// systems of one batch: up to 256 sort with an 8-bit system prefix on the 24-bit Morton key
-// (4 radix passes); more sort by the Morton key, then stably by the system (16 bits, 2 passes);
+// systems of one batch: up to 256 sort with an 8-bit system prefix on the 24-bit Hilbert key
+// (4 radix passes); more sort by the Hilbert key, then stably by the system (16 bits, 2 passes);
 // per-system launches put the system in grid.y (at most 65535)
 constexpr int kMaxBatch = 65535;
 constexpr int kPrefixBatch = 256;
@@ -48,14 +48,6 @@ struct BatchDev {
 // ---------------------------------------------------------------------------
 // kernels
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t spread8(uint32_t v) {
-    v &= 0xffu;
-    v = (v | (v << 8)) & 0x00f00fu;
-    v = (v | (v << 4)) & 0x0c30c3u;
-    v = (v | (v << 2)) & 0x249249u;
-    return v;
-}
-
 // validation (Eq. 1), one block per segment of one system
 __global__ void __launch_bounds__(kSeg) k_bvalidate(const double* __restrict__ x, const double* __restrict__ q,
                                                     const BatchDev* __restrict__ sys,
@@ -108,9 +100,9 @@ __global__ void k_bvalidate_finish(const BatchDev* __restrict__ sys, const doubl
     if (threadIdx.x == 0 && !(fabs(s) <= 1e-12 * sa)) atomicOr(status + blockIdx.x, kStatNonNeutral);
 }
 
-// sort keys: the 24-bit Morton code of the system's box, with the system in the top 8 bits
+// sort keys: the 24-bit Hilbert index in the system's box, with the system in the top 8 bits
 // when `prefix` (batches of up to 256 systems)
-__global__ void __launch_bounds__(kSeg) k_bmorton(const double* __restrict__ x, const BatchDev* __restrict__ sys,
+__global__ void __launch_bounds__(kSeg) k_bcurve_keys(const double* __restrict__ x, const BatchDev* __restrict__ sys,
                                                   const int* __restrict__ seg_sys,
                                                   const int64_t* __restrict__ seg_start, uint32_t* __restrict__ keys,
                                                   uint32_t* __restrict__ vals, int prefix) {
@@ -126,11 +118,11 @@ __global__ void __launch_bounds__(kSeg) k_bmorton(const double* __restrict__ x, 
         v = v < 0 ? 0 : (v > 255 ? 255 : v);
         c[k] = (uint32_t)v;
     }
-    keys[i] = (prefix ? (uint32_t)b << 24 : 0u) | spread8(c[0]) | (spread8(c[1]) << 1) | (spread8(c[2]) << 2);
+    keys[i] = (prefix ? (uint32_t)b << 24 : 0u) | hilbert_key24(c[0], c[1], c[2]);
     vals[i] = (uint32_t)i;
 }
 
-// after the Morton passes of a large batch: the system of each sorted charge as the key of the
+// after the curve-key passes of a large batch: the system of each sorted charge as the key of the
 // remaining (stable) passes, found from its row by binary search over the systems' first rows
 __global__ void k_bsys_keys(const uint32_t* __restrict__ vin, int64_t n, const BatchDev* __restrict__ sys, int B,
                             uint32_t* __restrict__ kout, uint32_t* __restrict__ vout) {
@@ -464,12 +456,12 @@ int queue_batch(psum_batch_s* bt, const double* x, const double* q, double* phi,
     const uint32_t* perm = nullptr;
     if (fp32) {
         const bool prefix = B <= kPrefixBatch;
-        k_bmorton<<<bt->n_seg, kSeg, 0, st>>>(x, bt->d_sys, bt->d_seg_sys, bt->d_seg_start, bt->ka, bt->va,
+        k_bcurve_keys<<<bt->n_seg, kSeg, 0, st>>>(x, bt->d_sys, bt->d_seg_sys, bt->d_seg_start, bt->ka, bt->va,
                                               prefix ? 1 : 0);
         if (prefix) {
             BTRY(launch_radix_sort(bt->ka, bt->va, bt->kb, bt->vb, bt->hist, bt->N, 4, st));
         } else {
-            // Morton passes (result in kb, vb), the systems as keys, two stable passes on them
+            // curve-key passes (result in kb, vb), the systems as keys, two stable passes on them
             BTRY(launch_radix_sort(bt->ka, bt->va, bt->kb, bt->vb, bt->hist, bt->N, 3, st));
             k_bsys_keys<<<(unsigned)((bt->N + 255) / 256), 256, 0, st>>>(bt->vb, bt->N, bt->d_sys, B, bt->ka, bt->va);
             BTRY(launch_radix_sort(bt->ka, bt->va, bt->kb, bt->vb, bt->hist, bt->N, 2, st));

@@ -113,7 +113,7 @@ __global__ void __launch_bounds__(kMeanThreads) k_box_mean(const double* __restr
 // (12 logarithms, 12 arctangents) instead of one per box.  The covering block's lattice is
 // walked directly (i d_k is the image table's float64 value), so every kept test matches the
 // pair kernels'.  Which images are kept depends on the charge, so the threads of a warp take
-// charges in Morton order when a permutation is given: neighbours see nearly the same runs.
+// charges in Hilbert order when a permutation is given: neighbours see nearly the same runs.
 __global__ void __launch_bounds__(kRedThreads) k_box_mean_ball(const double* __restrict__ x,
                                                                const double* __restrict__ q,
                                                                const uint32_t* __restrict__ perm, int64_t n,

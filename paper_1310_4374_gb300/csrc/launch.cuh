@@ -43,8 +43,8 @@ constexpr int kNear32Variants = 2;
 int near64_occupancy_ctas();
 // sort.cu
 int sort_blocks(int64_t n);
-int morton_sort_launches(int64_t n);   // kernels launch_morton_sort queues for n points
-cudaError_t launch_morton_sort(const double* x, int64_t n, const double d[3], uint32_t* ka, uint32_t* va,
+int curve_sort_launches(int64_t n);   // kernels launch_curve_sort queues for n points
+cudaError_t launch_curve_sort(const double* x, int64_t n, const double d[3], uint32_t* ka, uint32_t* va,
                                uint32_t* kb, uint32_t* vb, uint32_t* hist, cudaStream_t st);
 cudaError_t launch_pack32(const double* x, const double* q, const uint32_t* perm, int64_t n, int64_t n_groups,
                           float4* pk_hi, float4* pk_lo, double* org, cudaStream_t st, double* xs = nullptr,

@@ -19,7 +19,7 @@
 //     partial buffer, and a reduction kernel adds the slots in a fixed order.
 //
 // FP32C: coordinates are float32 offsets from a float64 origin per group of
-// 128 consecutive (Morton-sorted) points; the offset between a target group and
+// 128 consecutive (Hilbert-sorted) points; the offset between a target group and
 // a source chunk, minus the image vector, is formed in float64 and rounded once,
 // so close pairs keep their relative precision.  Pair arithmetic uses packed
 // f32x2 instructions on two targets at a time and MUFU rsqrt; per-unit float32

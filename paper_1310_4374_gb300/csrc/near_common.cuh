@@ -148,16 +148,19 @@ __device__ __forceinline__ void pair_loop_far(const float4* __restrict__ s_hi, c
                                               const float2 (&ny)[NP], const float2 (&nz)[NP], float2 (&aphi)[NP],
                                               float2 (&agx)[NP], float2 (&agy)[NP], float2 (&agz)[NP],
                                               int n = kNearChunk) {
-    // the potential, whose terms cancel most, goes into two interleaved partial sums
+    // the potential, whose terms cancel most, goes into two partial sums, one over each half
+    // of the sources: each runs over consecutive sources of the spatial order, whose signs
+    // alternate in a lattice or in dipoles (even and odd sources apart would each sum one sign)
     float2 bphi[NP];
 #pragma unroll
     for (int j = 0; j < NP; ++j) bphi[j] = make_float2(0.f, 0.f);
+    const int hn = n >> 1;        // n is even (a chunk, or compacted sources in blocks of 4)
     if constexpr (!kGrad) {
         // potential only: each term q / r enters its sum by one fused multiply-add
 #pragma unroll kFarUnroll
-        for (int s = 0; s < n; s += 2) {
+        for (int s = 0; s < hn; ++s) {
             const float4 A0 = s_hi[2 * s], B0 = s_hi[2 * s + 1];
-            const float4 A1 = s_hi[2 * s + 2], B1 = s_hi[2 * s + 3];
+            const float4 A1 = s_hi[2 * (s + hn)], B1 = s_hi[2 * (s + hn) + 1];
 #pragma unroll
             for (int j = 0; j < NP; ++j) {
                 const float2 ex0 = __fadd2_rn(make_float2(A0.x, A0.y), nx[j]);
@@ -180,10 +183,10 @@ __device__ __forceinline__ void pair_loop_far(const float4* __restrict__ s_hi, c
         return;
     }
 #pragma unroll kFarUnroll
-    for (int s = 0; s < n; s += 2) {
+    for (int s = 0; s < hn; ++s) {
         float2 q0[NP], q1[NP];
         pair_term<kGrad, NP>(s_hi, s, nx, ny, nz, q0, agx, agy, agz);
-        pair_term<kGrad, NP>(s_hi, s + 1, nx, ny, nz, q1, agx, agy, agz);
+        pair_term<kGrad, NP>(s_hi, s + hn, nx, ny, nz, q1, agx, agy, agz);
 #pragma unroll
         for (int j = 0; j < NP; ++j) {
             aphi[j] = __fadd2_rn(aphi[j], q0[j]);

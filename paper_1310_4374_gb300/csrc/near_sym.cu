@@ -26,7 +26,9 @@ namespace psum {
 //   * per source chunk of tile b and image, a warp's 32 lanes (4 targets each) visit the
 //     chunk in 2 rounds of 32 source pairs (the chunk re-laid in shared memory as pairs,
 //     (x0,x1,y0,y1),(z0,z1,q0,q1), so that one packed operation serves both sources of
-//     a pair for one target): at step k lane l takes pair (l + k) mod 32 of the round and
+//     a pair for one target; round g pairs source 64 g + l with 64 g + l + 32, so each
+//     half of a packed sum takes a run of consecutive sources of the spatial order): at
+//     step k lane l takes pair (l + k) mod 32 of the round and
 //     adds its targets' terms to the pair's reaction sums, which then move one lane down
 //     (shuffles), so after 32 steps lane l holds the reactions of pair l over the warp's
 //     128 targets; the 4 warps keep private compensated (hi, lo) sums per source,
@@ -435,9 +437,13 @@ __global__ void __launch_bounds__(kThreads32, kMinB) k_near32s(Near32SymArgs a) 
             return;
         }
         if (!kFF) {
-            // the chunk again as source pairs for the far rotation
+            // the chunk again as source pairs for the far rotation: pair P = 32 g + l holds
+            // sources 64 g + l and 64 g + l + 32, so that each half of a packed sum runs over
+            // 32 consecutive sources of the spatial order (consecutive points of a lattice or
+            // of dipoles alternate in sign: even and odd ones apart would each sum one sign)
             const int P = tid >> 1, h = tid & 1;
-            const float4 U = s_hi[2 * (2 * P) + h], V = s_hi[2 * (2 * P + 1) + h];
+            const int sa = 64 * (P >> 5) + (P & 31);
+            const float4 U = s_hi[2 * sa + h], V = s_hi[2 * (sa + 32) + h];
             s_sp[tid] = make_float4(U.x, V.x, U.z, V.z);
             __syncthreads();
         }
@@ -622,15 +628,15 @@ __global__ void __launch_bounds__(kThreads32, kMinB) k_near32s(Near32SymArgs a) 
                     const float2 s3 = make_float2(__shfl_sync(0xffffffffu, st2.x, (lane + 8) & 31),
                                                   __shfl_sync(0xffffffffu, st2.y, (lane + 8) & 31));
                     const float2 tot = __fadd2_rn(__fadd2_rn(s1, s2), __fadd2_rn(s3, rp));
-                    const int s = 2 * (32 * g + lane);
+                    const int s = 64 * g + lane, sb = s + 32;    // the lane's pair: sources s, s + 32
                     two_sum_acc(s_re[warp][0][0][s], s_re[warp][0][1][s], tot.x);
-                    two_sum_acc(s_re[warp][0][0][s + 1], s_re[warp][0][1][s + 1], tot.y);
+                    two_sum_acc(s_re[warp][0][0][sb], s_re[warp][0][1][sb], tot.y);
                     two_sum_acc(s_re[warp][1][0][s], s_re[warp][1][1][s], rx.x);
-                    two_sum_acc(s_re[warp][1][0][s + 1], s_re[warp][1][1][s + 1], rx.y);
+                    two_sum_acc(s_re[warp][1][0][sb], s_re[warp][1][1][sb], rx.y);
                     two_sum_acc(s_re[warp][2][0][s], s_re[warp][2][1][s], ry.x);
-                    two_sum_acc(s_re[warp][2][0][s + 1], s_re[warp][2][1][s + 1], ry.y);
+                    two_sum_acc(s_re[warp][2][0][sb], s_re[warp][2][1][sb], ry.y);
                     two_sum_acc(s_re[warp][3][0][s], s_re[warp][3][1][s], rz.x);
-                    two_sum_acc(s_re[warp][3][0][s + 1], s_re[warp][3][1][s + 1], rz.y);
+                    two_sum_acc(s_re[warp][3][0][sb], s_re[warp][3][1][sb], rz.y);
                 }
 #pragma unroll
                 for (int j = 0; j < 2; ++j) {
@@ -685,16 +691,16 @@ __global__ void __launch_bounds__(kThreads32, kMinB) k_near32s(Near32SymArgs a) 
                         rz.x = __shfl_sync(0xffffffffu, rz.x, up);
                         rz.y = __shfl_sync(0xffffffffu, rz.y, up);
                     }
-                    // the lane holds the reactions of sources 2 P and 2 P + 1, P = 32 g + lane
-                    const int s = 2 * (32 * g + lane);
+                    // the lane holds the reactions of pair 32 g + lane: sources s and s + 32
+                    const int s = 64 * g + lane, s1 = s + 32;
                     two_sum_acc(s_re[warp][0][0][s], s_re[warp][0][1][s], rp.x);
-                    two_sum_acc(s_re[warp][0][0][s + 1], s_re[warp][0][1][s + 1], rp.y);
+                    two_sum_acc(s_re[warp][0][0][s1], s_re[warp][0][1][s1], rp.y);
                     two_sum_acc(s_re[warp][1][0][s], s_re[warp][1][1][s], rx.x);
-                    two_sum_acc(s_re[warp][1][0][s + 1], s_re[warp][1][1][s + 1], rx.y);
+                    two_sum_acc(s_re[warp][1][0][s1], s_re[warp][1][1][s1], rx.y);
                     two_sum_acc(s_re[warp][2][0][s], s_re[warp][2][1][s], ry.x);
-                    two_sum_acc(s_re[warp][2][0][s + 1], s_re[warp][2][1][s + 1], ry.y);
+                    two_sum_acc(s_re[warp][2][0][s1], s_re[warp][2][1][s1], ry.y);
                     two_sum_acc(s_re[warp][3][0][s], s_re[warp][3][1][s], rz.x);
-                    two_sum_acc(s_re[warp][3][0][s + 1], s_re[warp][3][1][s + 1], rz.y);
+                    two_sum_acc(s_re[warp][3][0][s1], s_re[warp][3][1][s1], rz.y);
                 }
 #pragma unroll
                 for (int j = 0; j < 2; ++j) {

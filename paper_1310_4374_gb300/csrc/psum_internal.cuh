@@ -13,7 +13,7 @@ namespace psum {
 
 // ---------------------------------------------------------------------------
 // Tiling of the near-field pair sum.
-//   * a source CHUNK is kNearChunk consecutive (Morton-ordered) sources staged
+//   * a source CHUNK is kNearChunk consecutive (Hilbert-ordered) sources staged
 //     in shared memory, with one float64 origin;
 //   * a target TILE is kThreads threads x kTgt targets, with one float64 origin;
 //   * a work UNIT is (tile, chunk, image): every target of the tile against
@@ -27,6 +27,47 @@ constexpr int kThreads64 = 128;           // threads per CTA, FP64 kernel
 constexpr int kTile64 = kThreads64;       // one target per thread
 constexpr int kMaxImages = 343;           // K <= 3 per axis; trimmed plans: images kept
 constexpr int kMaxDegree = 40;
+
+// Spatial order of the charges: the index of a point's cell of a 256^3 grid over the box along
+// the 3-D Hilbert curve (24 bits), computed by Skilling's method ("Programming the Hilbert
+// curve", AIP Conf. Proc. 707, 2004): the cell's coordinates are turned in place into the
+// curve's "transposed" index (undoing the excess rotations level by level, then a Gray code),
+// whose bits interleaved level by level, axis 0 first, give the index.  Consecutive cells of
+// the curve share a face, so groups of consecutive points are compact (a Z-order curve jumps
+// between distant cells; its groups' bounding boxes are larger and more pairs of groups are
+// near one another).
+__host__ __device__ __forceinline__ uint32_t spread3_8(uint32_t v) {
+    // 8 bits -> every third bit of 24
+    v &= 0xffu;
+    v = (v | (v << 8)) & 0x00f00fu;
+    v = (v | (v << 4)) & 0x0c30c3u;
+    v = (v | (v << 2)) & 0x249249u;
+    return v;
+}
+__host__ __device__ __forceinline__ uint32_t hilbert_key24(uint32_t c0, uint32_t c1, uint32_t c2) {
+    uint32_t X[3] = {c0 & 0xffu, c1 & 0xffu, c2 & 0xffu};
+    for (uint32_t Q = 1u << 7; Q > 1; Q >>= 1) {
+        const uint32_t P = Q - 1;
+        for (int i = 0; i < 3; ++i) {
+            if (X[i] & Q) {
+                X[0] ^= P;                                 // invert the low bits of axis 0
+            } else {
+                const uint32_t t = (X[0] ^ X[i]) & P;      // exchange the low bits of axes 0 and i
+                X[0] ^= t;
+                X[i] ^= t;
+            }
+        }
+    }
+    X[1] ^= X[0];
+    X[2] ^= X[1];
+    uint32_t t = 0;
+    for (uint32_t Q = 1u << 7; Q > 1; Q >>= 1)
+        if (X[2] & Q) t ^= Q - 1;
+    X[0] ^= t;
+    X[1] ^= t;
+    X[2] ^= t;
+    return (spread3_8(X[0]) << 2) | (spread3_8(X[1]) << 1) | spread3_8(X[2]);
+}
 
 // device status bits (OR-ed by kernels, mapped to PSUM_ERR_* on the host)
 constexpr int kStatNonNeutral = 1;
@@ -322,7 +363,7 @@ struct NearSys {
 };
 
 // A stride near n / golden ratio, coprime to n: consecutive steps land far apart in the
-// (Morton-ordered) chunk sequence, so the chunks next to a tile -- the costly float-float
+// (Hilbert-ordered) chunk sequence, so the chunks next to a tile -- the costly float-float
 // "near" units -- spread evenly over the work items instead of
 // piling up in the few whose unit ranges hold the tile's spatial neighbours.
 inline int64_t near_chunk_stride(int64_t n) {

@@ -2,7 +2,7 @@
 //
 // FP32C needs sources grouped into compact chunks so that float32 offsets from a
 // per-chunk float64 origin keep the precision of close pairs.  The charges are
-// ordered along a Morton (Z-order) curve of a 256^3 grid over the box by a
+// ordered along the Hilbert curve of a 256^3 grid over the box (hilbert_key24) by a
 // stable least-significant-digit radix sort (8-bit digits), then packed 128 at
 // a time with the midpoint of each chunk's bounding box as its origin.
 #include "psum_internal.cuh"
@@ -15,16 +15,7 @@ constexpr int kSortPerThread = 8;
 constexpr int kSortTile = kSortThreads * kSortPerThread;   // 2048 keys per block
 constexpr int kRadix = 256;
 
-__device__ __forceinline__ uint32_t spread_bits8(uint32_t v) {
-    // 8 bits -> every third bit of 24
-    v &= 0xffu;
-    v = (v | (v << 8)) & 0x00f00fu;
-    v = (v | (v << 4)) & 0x0c30c3u;
-    v = (v | (v << 2)) & 0x249249u;
-    return v;
-}
-
-__global__ void k_morton(const double* __restrict__ x, int64_t n, double d0, double d1, double d2,
+__global__ void k_curve_keys(const double* __restrict__ x, int64_t n, double d0, double d1, double d2,
                          uint32_t* __restrict__ keys, uint32_t* __restrict__ vals) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -36,7 +27,7 @@ __global__ void k_morton(const double* __restrict__ x, int64_t n, double d0, dou
         v = v < 0 ? 0 : (v > 255 ? 255 : v);      // also maps NaN (validated elsewhere) into range
         c[k] = (uint32_t)v;
     }
-    keys[i] = spread_bits8(c[0]) | (spread_bits8(c[1]) << 1) | (spread_bits8(c[2]) << 2);
+    keys[i] = hilbert_key24(c[0], c[1], c[2]);
     vals[i] = (uint32_t)i;
 }
 
@@ -324,14 +315,14 @@ __global__ void __launch_bounds__(kSmallSortThreads) k_sort_small(const uint32_t
     }
 }
 
-int morton_sort_launches(int64_t n) { return n <= kSmallSort ? 2 : 1 + 3 * 3; }
+int curve_sort_launches(int64_t n) { return n <= kSmallSort ? 2 : 1 + 3 * 3; }
 
-// Morton order of the points: 24-bit keys, written to (kb, vb) and sorted (3 radix passes,
+// Hilbert order of the points: 24-bit keys, written to (kb, vb) and sorted (3 radix passes,
 // or one block for small inputs) so that the sorted keys and the permutation end in (ka, va).
-cudaError_t launch_morton_sort(const double* x, int64_t n, const double d[3], uint32_t* ka, uint32_t* va,
+cudaError_t launch_curve_sort(const double* x, int64_t n, const double d[3], uint32_t* ka, uint32_t* va,
                                uint32_t* kb, uint32_t* vb, uint32_t* hist, cudaStream_t st) {
     const int bs = 256;
-    k_morton<<<(unsigned)((n + bs - 1) / bs), bs, 0, st>>>(x, n, d[0], d[1], d[2], kb, vb);
+    k_curve_keys<<<(unsigned)((n + bs - 1) / bs), bs, 0, st>>>(x, n, d[0], d[1], d[2], kb, vb);
     if (n <= kSmallSort) {
         k_sort_small<<<1, kSmallSortThreads, 0, st>>>(kb, vb, (int)n, ka, va);
         return cudaGetLastError();

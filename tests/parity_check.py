@@ -36,14 +36,14 @@ def assert_close(a, ref, tol, what="", max_tol=None, scale=None):
 def full_size_sample(x, d, n=4096, cluster=1100, seed=0):
     """Sorted indices of n charges for a sampled full-size comparison: every charge of three
     compact clusters -- the `cluster` charges nearest (in box-normalised max norm) to the
-    lower corner and to the upper corner of the box, where the spatial (Morton) order of the
-    charges starts and ends, and to its centre -- so that whole target tiles at both ends of
-    the order and in the middle are compared, plus charges drawn at random up to n."""
+    corners of the box where the spatial (Hilbert) order of the charges starts, (-1/2, -1/2,
+    -1/2), and ends, (1/2, -1/2, -1/2), and to its centre -- so that whole target tiles at both
+    ends of the order and in the middle are compared, plus charges drawn at random up to n."""
     x = np.asarray(x, dtype=np.float64)
     u = x / np.asarray(d, dtype=np.float64)              # in [-1/2, 1/2)
     picks = set()
-    for c in (-0.5, 0.5, 0.0):
-        dist = np.max(np.abs(u - c), axis=1)
+    for c in ((-0.5, -0.5, -0.5), (0.5, -0.5, -0.5), (0.0, 0.0, 0.0)):
+        dist = np.max(np.abs(u - np.asarray(c)), axis=1)
         picks.update(np.argsort(dist, kind="stable")[:cluster].tolist())
     rng = np.random.default_rng(seed)
     rest = np.setdiff1d(np.arange(len(x)), np.fromiter(picks, dtype=np.int64))

@@ -131,7 +131,7 @@ def _many(B, seed):
 
 @pytest.mark.parametrize("precision,nsys", [("fp32c", 1024), ("ff", 300)])
 def test_batches_beyond_256_systems(precision, nsys):
-    # more than 256 systems sort by the Morton key, then stably by the system: every system's
+    # more than 256 systems sort by the Hilbert key, then stably by the system: every system's
     # result equals its own evaluation on the same plan (to the kernels' rounding) and, on a
     # sample of systems, the oracle
     systems = _many(nsys, seed=nsys)
