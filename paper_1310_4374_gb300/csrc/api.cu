@@ -146,6 +146,7 @@ size_t layout(Plan& pl, int64_t N, char* base, Layout& L, bool backward = false,
         int64_t gmax = (int64_t)pl.num_sms * near32_occupancy_ctas(n_img, 0, trimmed, ffp0);
         if (g_cap > 0 && gmax > g_cap) gmax = g_cap;
         L.Ln = near_partition(L.n_tiles, L.n_chunks, n_img, gmax, ipc);
+        L.Ln.tab.one.tau2 = coincident_r2(pl.opt.d);
         // check sums: the 2M points with the block's images, or the M points with their
         // class's two image layers
         const bool layers = pl.lc_tiles > 0;
@@ -157,6 +158,7 @@ size_t layout(Plan& pl, int64_t N, char* base, Layout& L, bool backward = false,
         if (g_cap > 0 && gmax_c > g_cap) gmax_c = g_cap;
         L.Lc = near_partition(c_tiles, L.n_chunks, layers ? pl.lc_img : n_img, gmax_c,
                               g_cap > 0 ? 1 : kCheckItemsPerCta);
+        L.Lc.tab.one.tau2 = coincident_r2(pl.opt.d);
         // the symmetric kernel: FP32C charges, block image set, a normal (growing) scratch
         L.sym = false;
         const int pk = pl.opt.pair_kernel;
@@ -172,6 +174,7 @@ size_t layout(Plan& pl, int64_t N, char* base, Layout& L, bool backward = false,
             one[0].last_n = (int)(N - (L.n_chunks - 1) * kNearChunk);
             one[0].shift0 = 0;
             one[0].n_img = n_img;
+            one[0].tau2 = coincident_r2(pl.opt.d);
             const bool rf = refined_terms(pl);
             L.S = sym_partition(one, (int64_t)pl.num_sms * near32s_occupancy_ctas(n_img, ffp, rf));
             L.S.G = (int64_t)pl.num_sms * near32s_occupancy_ctas(L.S.max_ipg, ffp, rf);
@@ -274,6 +277,7 @@ size_t layout(Plan& pl, int64_t N, char* base, Layout& L, bool backward = false,
                              (fp32 ? near32_occupancy_ctas(n_img, 0, false, pl.opt.precision == PSUM_FF)
                                    : near64_occupancy_ctas());
         L.Lb = near_partition(L.n_tiles, n_chk_chunks, n_img, gmax);
+        L.Lb.tab.one.tau2 = coincident_r2(pl.opt.d);
         L.Lb.counter = flags + 3;
         L.Lb.status = flags;
         L.Lb.n_status = 1;

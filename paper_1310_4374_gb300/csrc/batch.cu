@@ -718,10 +718,10 @@ int psum_batch_create(const psum_plan_t* plans, int B, const int64_t* offsets, p
         const int64_t chk_tiles = layers ? pl.lc_tiles : pl.n_check_tiles;
         const int c_img = layers ? pl.lc_img : pl.n_images;
         bt->near_n[b] = NearSys{unit_n, tile_n, n_tiles, n_chunks, pt / kNearChunk, shift0, pl.n_images,
-                                near_chunk_stride(n_chunks)};
+                                near_chunk_stride(n_chunks), coincident_r2(pl.opt.d)};
         // the check sums index their own image tables (cent0)
         bt->near_c[b] = NearSys{unit_c, tile_c, chk_tiles, n_chunks, pt / kNearChunk, (int)cent0, c_img,
-                                near_chunk_stride(n_chunks)};
+                                near_chunk_stride(n_chunks), coincident_r2(pl.opt.d)};
         cent_first[b] = cent0;
         cent0 += (int64_t)bt->c_cls * c_img;
         SymSys ss{};
@@ -729,6 +729,7 @@ int psum_batch_create(const psum_plan_t* plans, int B, const int64_t* offsets, p
         ss.n_tiles = n_tiles;
         ss.n_chunks = n_chunks;
         ss.last_n = n_chunks > 0 ? (int)(n - (n_chunks - 1) * kNearChunk) : 0;
+        ss.tau2 = coincident_r2(pl.opt.d);
         ss.shift0 = shift0;
         ss.n_img = pl.n_images;
         bt->sym_sys[b] = ss;

@@ -359,7 +359,11 @@ __global__ void __launch_bounds__(kThreads32, kMinB) k_near32(Near32Args a) {
                 float2 acc[4][2];
 #pragma unroll
                 for (int qi = 0; qi < 4; ++qi) acc[qi][0] = acc[qi][1] = make_float2(0.f, 0.f);
-                pair_loop_ff<kGrad>(uhi, ulo, nTh, nTl, acc, un);
+                const float tau2 = Sp->tau2;
+                if (cls & (j ? kUnitNear1 : kUnitNear0))
+                    pair_loop_ff<kGrad, true>(uhi, ulo, nTh, nTl, acc, tau2, un);
+                else
+                    pair_loop_ff<kGrad, false>(uhi, ulo, nTh, nTl, acc, tau2, un);
                 if constexpr (!kGrad) {
                     acc[0][0] = __fmul2_rn(acc[0][0], wpair(j));
                     acc[0][1] = __fmul2_rn(acc[0][1], wpair(j));
@@ -411,8 +415,9 @@ __global__ void __launch_bounds__(kThreads32, kMinB) k_near32(Near32Args a) {
                     nl[c] = make_float2(-(e0 + (tl.x + d0[3 + c])), -(e1 + (tl.y + d1[3 + c])));
                 }
                 float2 aphi = make_float2(0.f, 0.f), aphi_lo = aphi, agx = aphi, agy = aphi, agz = aphi;
+                const float tau2 = Sp->tau2;
                 pair_loop_near<kGrad>(uhi, ulo, nh[0], nh[1], nh[2], nl[0], nl[1], nl[2], aphi, aphi_lo, agx, agy,
-                                      agz, un);
+                                      agz, tau2, un);
                 if constexpr (!kGrad) {
                     aphi = __fmul2_rn(aphi, wpair(j));
                     aphi_lo = __fmul2_rn(aphi_lo, wpair(j));

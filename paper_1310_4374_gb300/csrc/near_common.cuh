@@ -222,7 +222,7 @@ template <bool kGrad>
 __device__ __forceinline__ void pair_loop_near(const float4* __restrict__ s_hi, const float4* __restrict__ s_lo,
                                                float2 nhx, float2 nhy, float2 nhz, float2 nlx, float2 nly,
                                                float2 nlz, float2& aphi, float2& aphi_lo, float2& agx, float2& agy,
-                                               float2& agz, int n = kNearChunk) {
+                                               float2& agz, float tau2, int n = kNearChunk) {
 #pragma unroll 1
     for (int s0 = 0; s0 < n; s0 += kNearFold) {
         float2 blk = make_float2(0.f, 0.f);
@@ -240,8 +240,8 @@ __device__ __forceinline__ void pair_loop_near(const float4* __restrict__ s_hi, 
             r2 = __ffma2_rn(ey, ey, r2);
             r2 = __ffma2_rn(ez, ez, r2);
             float2 ri = make_float2(rsqrt_mufu(r2.x), rsqrt_mufu(r2.y));
-            ri.x = r2.x > 0.f ? ri.x : 0.f;                   // K(0) = 0 (Eq. 1)
-            ri.y = r2.y > 0.f ? ri.y : 0.f;
+            ri.x = r2.x > tau2 ? ri.x : 0.f;                  // K(0) = 0 (Eq. 1), coincident_r2 (psum_internal.cuh)
+            ri.y = r2.y > tau2 ? ri.y : 0.f;
             const float2 qr = __fmul2_rn(make_float2(B.z, B.w), ri);
             blk = k == 0 ? qr : __fadd2_rn(blk, qr);
             if (kGrad) {
@@ -296,12 +296,30 @@ __device__ __forceinline__ float2 ff_mul2(float2 ah, float2 al, float2 bh, float
 // s - t' come out of a two-sum of the hi parts plus the lo parts; r^2 is summed with
 // the product errors; 1/r is the MUFU estimate y refined by one Newton step taken in
 // float-float, ri = y - y (r^2 y^2 - 1)/2, which leaves a relative error near
-// (3/2)(2^-22.9)^2 + 2^-46; K(0) = 0 where r^2 is exactly zero.  acc[q] = (hi, lo) of
+// (3/2)(2^-22.9)^2 + 2^-46; K(0) = 0 where r^2 is zero or below tau2
+// (coincident_r2 in psum_internal.cuh).  acc[q] = (hi, lo) of
 // phi and (kGrad) the three field sums.
-template <bool kGrad>
+// The offset's hi part comes from the rounded target offset, so a pair closer than about one
+// float32 ulp of the offsets (a few 1e-8 of the group size) has hi and lo parts of equal size
+// and opposite sign, and r^2 formed from hi^2 + 2 hi lo is wrong; near units (kRenorm) first
+// renormalise each component by a fast two-sum (3 more packed operations), far units cannot hold
+// such a pair.
+template <bool kRenorm>
+__device__ __forceinline__ void ff_renorm(float2 (&eh)[3], float2 (&el)[3]) {
+    if constexpr (kRenorm) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float2 sm = __fadd2_rn(eh[c], el[c]);
+            el[c] = __fadd2_rn(el[c], neg2(__fadd2_rn(sm, neg2(eh[c]))));
+            eh[c] = sm;
+        }
+    }
+}
+
+template <bool kGrad, bool kRenorm>
 __device__ __forceinline__ void pair_loop_ff(const float4* __restrict__ s_hi, const float4* __restrict__ s_lo,
                                              const float2 (&nTh)[3], const float2 (&nTl)[3], float2 (&acc)[4][2],
-                                             int n = kNearChunk) {
+                                             float tau2, int n = kNearChunk) {
 #pragma unroll 1
     for (int s = 0; s < n; ++s) {
         const float4 A = s_hi[2 * s], B = s_hi[2 * s + 1], C = s_lo[2 * s], D = s_lo[2 * s + 1];
@@ -315,6 +333,7 @@ __device__ __forceinline__ void pair_loop_ff(const float4* __restrict__ s_hi, co
             eh[c] = two_sum2(sh[c], nTh[c], err);
             el[c] = __fadd2_rn(__fadd2_rn(sl[c], nTl[c]), err);
         }
+        ff_renorm<kRenorm>(eh, el);
         // r^2 = sum (eh + el)^2 as r2h + r2l
         const float2 p0 = __fmul2_rn(eh[0], eh[0]), p1 = __fmul2_rn(eh[1], eh[1]), p2 = __fmul2_rn(eh[2], eh[2]);
         float2 lo = __ffma2_rn(eh[0], eh[0], neg2(p0));
@@ -340,8 +359,8 @@ __device__ __forceinline__ void pair_loop_ff(const float4* __restrict__ s_hi, co
         h = __ffma2_rn(__fmul2_rn(r2l, y), y, h);             // h = r^2 y^2 - 1
         float2 rih = y;
         float2 ril = __fmul2_rn(__fmul2_rn(make_float2(-0.5f, -0.5f), y), h);
-        if (r2h.x == 0.f) rih.x = ril.x = 0.f;                // K(0) = 0 (Eq. 1)
-        if (r2h.y == 0.f) rih.y = ril.y = 0.f;
+        if (!(r2h.x > tau2)) rih.x = ril.x = 0.f;             // K(0) = 0 (Eq. 1), coincident_r2 (psum_internal.cuh)
+        if (!(r2h.y > tau2)) rih.y = ril.y = 0.f;
         // q / r
         float2 Pl;
         const float2 Ph = ff_mul2(qh, ql, rih, ril, Pl);

@@ -177,7 +177,7 @@ __device__ __forceinline__ void sym_far_step_pair_refined(float4 A, float4 B, co
 // the 4 targets' terms) into the compensated (rp, rpl).
 __device__ __forceinline__ void sym_near_step(const float4* __restrict__ s_hi, const float4* __restrict__ s_lo,
                                               int si, const float2 (&nh)[2][3], const float2 (&nl)[2][3],
-                                              const float2 (&tq)[2], float2 (&blk)[2], bool first,
+                                              const float2 (&tq)[2], float tau2, float2 (&blk)[2], bool first,
                                               float2 (&agx)[2], float2 (&agy)[2], float2 (&agz)[2], float& rp,
                                               float& rpl, float& rx, float& ry, float& rz) {
     const float4 A = s_hi[2 * si], B = s_hi[2 * si + 1];
@@ -193,8 +193,8 @@ __device__ __forceinline__ void sym_near_step(const float4* __restrict__ s_hi, c
         r2 = __ffma2_rn(ey, ey, r2);
         r2 = __ffma2_rn(ez, ez, r2);
         float2 ri = make_float2(rsqrt_mufu(r2.x), rsqrt_mufu(r2.y));
-        ri.x = r2.x > 0.f ? ri.x : 0.f;                   // K(0) = 0 (Eq. 1)
-        ri.y = r2.y > 0.f ? ri.y : 0.f;
+        ri.x = r2.x > tau2 ? ri.x : 0.f;                  // K(0) = 0 (Eq. 1), coincident_r2
+        ri.y = r2.y > tau2 ? ri.y : 0.f;
         const float2 ri2 = __fmul2_rn(ri, ri);
         const float2 qa = __fmul2_rn(sq, ri);
         blk[j] = first ? qa : __fadd2_rn(blk[j], qa);
@@ -226,10 +226,11 @@ __device__ __forceinline__ void sym_near_step(const float4* __restrict__ s_hi, c
 // tqh + tql) against source si, both directions in float-float arithmetic (the one-sided
 // loop's offsets, r^2 and Newton-refined 1/r, computed once).  The action goes to acc
 // (hi, lo per quantity); the reaction, summed over the 2 targets, to the compensated scalar
-// sums r[q] = (hi, lo).
+// sums r[q] = (hi, lo).  kRenorm: near units (ff_renorm).
+template <bool kRenorm>
 __device__ __forceinline__ void sym_ff_step(const float4* __restrict__ s_hi, const float4* __restrict__ s_lo,
                                             int si, const float2 (&nTh)[3], const float2 (&nTl)[3], float2 tqh,
-                                            float2 tql, float2 (&acc)[4][2], float (&r)[4][2]) {
+                                            float2 tql, float tau2, float2 (&acc)[4][2], float (&r)[4][2]) {
     const float4 A = s_hi[2 * si], B = s_hi[2 * si + 1], C = s_lo[2 * si], D = s_lo[2 * si + 1];
     const float2 sh[3] = {make_float2(A.x, A.y), make_float2(A.z, A.w), make_float2(B.x, B.y)};
     const float2 sl[3] = {make_float2(C.x, C.y), make_float2(C.z, C.w), make_float2(D.x, D.y)};
@@ -241,6 +242,7 @@ __device__ __forceinline__ void sym_ff_step(const float4* __restrict__ s_hi, con
         eh[c] = two_sum2(sh[c], nTh[c], err);
         el[c] = __fadd2_rn(__fadd2_rn(sl[c], nTl[c]), err);
     }
+    ff_renorm<kRenorm>(eh, el);
     const float2 p0 = __fmul2_rn(eh[0], eh[0]), p1 = __fmul2_rn(eh[1], eh[1]), p2 = __fmul2_rn(eh[2], eh[2]);
     float2 lo = __ffma2_rn(eh[0], eh[0], neg2(p0));
     lo = __fadd2_rn(lo, __ffma2_rn(eh[1], eh[1], neg2(p1)));
@@ -264,8 +266,8 @@ __device__ __forceinline__ void sym_ff_step(const float4* __restrict__ s_hi, con
     h = __ffma2_rn(__fmul2_rn(r2l, y), y, h);
     float2 rih = y;
     float2 ril = __fmul2_rn(__fmul2_rn(make_float2(-0.5f, -0.5f), y), h);
-    if (r2h.x == 0.f) rih.x = ril.x = 0.f;                // K(0) = 0 (Eq. 1)
-    if (r2h.y == 0.f) rih.y = ril.y = 0.f;
+    if (!(r2h.x > tau2)) rih.x = ril.x = 0.f;             // K(0) = 0 (Eq. 1), coincident_r2
+    if (!(r2h.y > tau2)) rih.y = ril.y = 0.f;
     float2 r2il;
     const float2 r2ih = ff_mul2(rih, ril, rih, ril, r2il);
     // action: q_s / r and q_s (s - t') / r^3
@@ -469,8 +471,13 @@ __global__ void __launch_bounds__(kThreads32, kMinB) k_near32s(Near32SymArgs a) 
                     float2 acc[4][2];
 #pragma unroll
                     for (int qi = 0; qi < 4; ++qi) acc[qi][0] = acc[qi][1] = make_float2(0.f, 0.f);
+                    const float tau2 = S.tau2;
+                    const bool nearj = cls & (j ? kUnitNear1 : kUnitNear0);
                     if (cls & kUnitSelf) {
-                        pair_loop_ff<true>(s_hi, s_lo, nTh, nTl, acc);
+                        if (nearj)
+                            pair_loop_ff<true, true>(s_hi, s_lo, nTh, nTl, acc, tau2);
+                        else
+                            pair_loop_ff<true, false>(s_hi, s_lo, nTh, nTl, acc, tau2);
                     } else {
                         const float2 tqh = s_tq[j][tid], tql = s_tql[kFF ? j : 0][tid];
 #pragma unroll 1
@@ -478,7 +485,11 @@ __global__ void __launch_bounds__(kThreads32, kMinB) k_near32s(Near32SymArgs a) 
                             float r[4][2] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
 #pragma unroll 1
                             for (int k = 0; k < 32; ++k) {
-                                sym_ff_step(s_hi, s_lo, 32 * g + ((lane + k) & 31), nTh, nTl, tqh, tql, acc, r);
+                                const int si = 32 * g + ((lane + k) & 31);
+                                if (nearj)
+                                    sym_ff_step<true>(s_hi, s_lo, si, nTh, nTl, tqh, tql, tau2, acc, r);
+                                else
+                                    sym_ff_step<false>(s_hi, s_lo, si, nTh, nTl, tqh, tql, tau2, acc, r);
 #pragma unroll
                                 for (int qi = 0; qi < 4; ++qi) {
                                     r[qi][0] = __shfl_sync(0xffffffffu, r[qi][0], up);
@@ -537,8 +548,9 @@ __global__ void __launch_bounds__(kThreads32, kMinB) k_near32s(Near32SymArgs a) 
                         nl[c] = make_float2(-(e0 + (tls[c].x + d0[3 + c])), -(e1 + (tls[c].y + d1[3 + c])));
                     }
                     float2 aphi = make_float2(0.f, 0.f), aphi_lo = aphi, agx = aphi, agy = aphi, agz = aphi;
+                    const float tau2 = S.tau2;
                     pair_loop_near<true>(s_hi, s_lo, nh[0], nh[1], nh[2], nl[0], nl[1], nl[2], aphi, aphi_lo, agx,
-                                         agy, agz);
+                                         agy, agz, tau2);
                     two_sum_acc2(s_acc[0][j][0][tid], s_acc[0][j][1][tid], aphi);
                     s_acc[0][j][1][tid] = __fadd2_rn(s_acc[0][j][1][tid], aphi_lo);
                     two_sum_acc2(s_acc[1][j][0][tid], s_acc[1][j][1][tid], agx);
@@ -721,7 +733,7 @@ __global__ void __launch_bounds__(kThreads32, kMinB) k_near32s(Near32SymArgs a) 
                 for (int j = 0; j < 2; ++j) {
                     const float* d0 = dl + 6 * (2 * j);
                     const float* d1 = dl + 6 * (2 * j + 1);
-                    const int64_t i0 = (TA * kTgt32 + 2 * j) * kGroup + tid;
+                                        const int64_t i0 = (TA * kTgt32 + 2 * j) * kGroup + tid;
                     const int64_t i1 = i0 + kGroup;
                     const float4 C0 = a.pk_lo[2 * i0], D0 = a.pk_lo[2 * i0 + 1];
                     const float4 C1 = a.pk_lo[2 * i1], D1 = a.pk_lo[2 * i1 + 1];
@@ -744,8 +756,8 @@ __global__ void __launch_bounds__(kThreads32, kMinB) k_near32s(Near32SymArgs a) 
                         float2 blk[2];
 #pragma unroll
                         for (int k = 0; k < kNearFold; ++k) {
-                            sym_near_step(s_hi, s_lo, 32 * g + ((lane + k0 + k) & 31), nh, nl, tq, blk, k == 0, agx,
-                                          agy, agz, rp, rpl, rx, ry, rz);
+                            sym_near_step(s_hi, s_lo, 32 * g + ((lane + k0 + k) & 31), nh, nl, tq, S.tau2, blk, k == 0,
+                                          agx, agy, agz, rp, rpl, rx, ry, rz);
                             rp = __shfl_sync(0xffffffffu, rp, up);
                             rpl = __shfl_sync(0xffffffffu, rpl, up);
                             rx = __shfl_sync(0xffffffffu, rx, up);

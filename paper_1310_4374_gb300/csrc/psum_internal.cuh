@@ -351,6 +351,17 @@ __host__ __device__ __forceinline__ int64_t sk_owner(int64_t u, int64_t U, int64
 
 // One system of a near-field launch.  Its work units are the global indices
 // [unit0, unit0 + n_tiles * n_chunks * n_img), ordered (tile, chunk, image).
+// Two charges at one position but in different groups: their float32 and float-float offsets
+// come from two different group origins and carry a few 2^-48 of the group scale in rounding,
+// so the pair comes out a tiny, nonzero distance apart and its 1/r is meaningless.  The near
+// units (and every float-float unit) take a pair closer than 2^-37 R0 (R0 the half diagonal of
+// the box, which bounds the group radii) as coincident, K(0) = 0 as for an exact zero (Eq. 1);
+// float32 offsets resolve no distance that small anyway.  The squared threshold, per system.
+inline float coincident_r2(const double d[3]) {
+    const double t = std::ldexp(0.5 * std::sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]), -37);
+    return (float)(t * t);
+}
+
 struct NearSys {
     int64_t unit0;       // first unit
     int64_t tile0;       // first tile of the system in the target pack (= its first partial-buffer row)
@@ -360,6 +371,7 @@ struct NearSys {
     int shift0;          // first image vector of the system in the shift table
     int n_img;
     int64_t chunk_stride;  // a tile visits its chunks in the order (k * chunk_stride) mod n_chunks
+    float tau2;          // coincident_r2 of the system's box (float32 kernels)
 };
 
 // A stride near n / golden ratio, coprime to n: consecutive steps land far apart in the
@@ -476,6 +488,7 @@ struct SymSys {
     int shift0, n_img;        // image vectors shift0 .. shift0 + n_img - 1
     int n_g, img_per_g;       // image groups per tile pair and images per group
     int last_n;               // charges in the system's last chunk (1..kNearChunk; 0 = a full chunk)
+    float tau2;               // coincident_r2 of the system's box (float32 kernels)
 };
 struct SymSysTable {
     SymSys one;
