@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(const uint32_t* _
 // group's bounding-box half extents about its origin.
 // With a group table (batches) group g covers the sorted positions
 // [grp_start[g], grp_start[g] + grp_count[g]); without one, [128 g, min(128 (g+1), n)).
-constexpr int kPackWarps = 4;   // warps (groups) per block of k_pack32
+constexpr int kPackWarps = 16;  // warps (groups) per block of k_pack32
 
 __global__ void __launch_bounds__(32 * kPackWarps) k_pack32(const double* __restrict__ x, const double* __restrict__ q,
                          const uint32_t* __restrict__ perm, int64_t n, int64_t n_groups,
@@ -133,9 +133,9 @@ __global__ void __launch_bounds__(32 * kPackWarps) k_pack32(const double* __rest
                          double* __restrict__ xs, float4* __restrict__ ext) {
     const int64_t grp = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
-    if (grp >= n_groups) return;
-    const int64_t s0 = grp_start ? grp_start[grp] : grp * kNearChunk;
-    const int64_t s1 = grp_start ? s0 + grp_count[grp] : (grp + 1) * kNearChunk < n ? (grp + 1) * kNearChunk : n;
+    const bool live = grp < n_groups;      // a warp past the last group takes part in the barriers only
+    const int64_t s0 = !live ? 0 : grp_start ? grp_start[grp] : grp * kNearChunk;
+    const int64_t s1 = !live ? 0 : grp_start ? s0 + grp_count[grp] : (grp + 1) * kNearChunk < n ? (grp + 1) * kNearChunk : n;
     constexpr int per = kNearChunk / 32;
     double px[per][3], pq[per];
     bool ok[per];
@@ -166,25 +166,32 @@ __global__ void __launch_bounds__(32 * kPackWarps) k_pack32(const double* __rest
     // each charge absorbs the error carried so far, so the group's float32 charges sum to
     // its float64 total up to one rounding; a non-neutral rounding residue would add the
     // potential of a net charge over all images to every target.
-    // The recurrence is sequential: one lane runs it over the group's charges, staged in
-    // shared memory (a chain of float64 operations, no shuffles).
-    __shared__ double s_q[kPackWarps][kNearChunk];
-    __shared__ float s_f[kPackWarps][kNearChunk];
+    // The recurrence is sequential, a chain of float64 operations over the group's charges
+    // staged in shared memory.  The block's groups run theirs side by side, one lane each of
+    // its first warp: a float64 warp instruction occupies the SM's narrow float64 pipe the same
+    // time however few lanes it has, so one lane per warp would cost kPackWarps times as much.
+    // (Rows padded by one element: the lanes' rows fall in different banks.)
+    __shared__ double s_q[kPackWarps][kNearChunk + 1];
+    __shared__ float s_f[kPackWarps][kNearChunk + 1];
+    __shared__ int s_cnt[kPackWarps];
     const int w = threadIdx.x >> 5;
 #pragma unroll
     for (int k = 0; k < per; ++k) s_q[w][k * 32 + lane] = ok[k] ? pq[k] : 0.0;
-    __syncwarp();
-    if (lane == 0) {
-        const int cnt = (int)(s1 - s0);
+    if (lane == 0) s_cnt[w] = (int)(s1 - s0);
+    __syncthreads();
+    if (threadIdx.x < kPackWarps) {
+        const int wg = threadIdx.x;
+        const int cnt = s_cnt[wg];
         double carry = 0.0;
         for (int m = 0; m < cnt; ++m) {
-            const double qm = s_q[w][m];
+            const double qm = s_q[wg][m];
             const float v = (float)(qm - carry);
             carry += (double)v - qm;
-            s_f[w][m] = v;
+            s_f[wg][m] = v;
         }
     }
-    __syncwarp();
+    __syncthreads();
+    if (!live) return;
     float fqk[per];
 #pragma unroll
     for (int k = 0; k < per; ++k) fqk[k] = s_f[w][k * 32 + lane];
