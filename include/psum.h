@@ -30,8 +30,8 @@
  *
  * Memory and streams
  *   Every device pointer is owned by the caller and must stay valid until the
- *   work queued on `stream` has finished.  An evaluation forks part of its work onto an
- *   internal stream of the plan and joins it again before it returns to `stream`, so
+ *   work queued on `stream` has finished.  An evaluation forks part of its work onto two
+ *   internal streams of the plan and joins them again before it returns to `stream`, so
  *   completion of `stream` covers all of it (also inside a graph capture of `stream`).  `stream` is a cudaStream_t passed
  *   as void* (NULL = the legacy default stream).  A plan owns its check
  *   points, its factorisation, the image list and its scratch memory; the
