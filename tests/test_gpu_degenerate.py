@@ -108,3 +108,25 @@ def test_degenerate_inputs_match_the_oracle(name, precision, pairs):
     assert np.all(np.isfinite(phi)) and np.all(np.isfinite(g))
     assert_close(phi, ref["phi"], tol, f"{name}/{precision}/{pairs} phi")
     assert_close(g, ref["grad"], tol, f"{name}/{precision}/{pairs} grad")
+
+
+@pytest.mark.parametrize("precision,pairs", [("fp32c", "one-sided"), ("fp32c", "symmetric"), ("ff", "auto")])
+def test_degenerate_systems_in_one_batch(precision, pairs):
+    """The batch tables carry each system's coincidence threshold (charge and check-point
+    launches, both charge kernels): coincident triples, clumps and a plane in one batch."""
+    systems = [CASES[n]() for n in ("triples", "clumps", "plane")]
+    pb = B.PeriodicBatch(systems, precision=precision, pairs=pairs)
+    try:
+        x = torch.as_tensor(np.concatenate([s.x for s in systems]), device="cuda")
+        q = torch.as_tensor(np.concatenate([s.q for s in systems]), device="cuda")
+        phi, g = pb(x, q)
+        phi, g = phi.cpu().numpy(), g.cpu().numpy()
+        for b, s in enumerate(systems):
+            if s.name not in _REF:
+                _REF[s.name] = O.Plan(s.d, s.p, s.M).evaluate(s.x, s.q, mean="zero", parts=True)
+            sl = slice(pb.offsets[b], pb.offsets[b + 1])
+            assert np.all(np.isfinite(phi[sl])) and np.all(np.isfinite(g[sl]))
+            assert_close(phi[sl], _REF[s.name]["phi"], TOL[precision], f"batch {s.name}/{precision}/{pairs} phi")
+            assert_close(g[sl], _REF[s.name]["grad"], TOL[precision], f"batch {s.name}/{precision}/{pairs} grad")
+    finally:
+        pb.close()
