@@ -75,7 +75,12 @@ extern "C" {
                           compensated (two-sum) accumulation, float64 elsewhere */
 #define PSUM_FF     2  /* pair arithmetic in float-float (a float32 pair carrying about 44 bits)
                           on the float32 pipe: float64-class results (the float64 tolerance)
-                          without float64 pair arithmetic; float64 elsewhere. */
+                          without float64 pair arithmetic; float64 elsewhere.  Offsets are
+                          relative to 128-point groups, so where charges sit far closer than
+                          their groups' size (a cluster of 1e-6 inside a box of 1) the relative
+                          accuracy falls toward 2^-48 times that ratio. */
+/* Both float32 precisions take two charges closer than 2^-37 R0 (R0 the half diagonal of the
+   box) as coincident (K(0) = 0); PSUM_FP64 drops exact zeros only. */
 
 #define PSUM_POINTS_FIBONACCI 0  /* M check points on a spherical Fibonacci lattice */
 #define PSUM_POINTS_GAUSS     1  /* the Gauss spherical grid of Sec. 2.2: polar angles at the zeros of
@@ -116,13 +121,13 @@ extern "C" {
  * float32 unit in the last place (rms) of the term; the potential's error is that times
  * kappa = sqrt(sum of squared terms) / rms(phi), the cancellation of the near sum.  Random
  * charges have kappa of a few (about 4.7e-7 at 1e5 charges); tight dipoles of 2e5 charges about
- * 20 (1.6e-6). */
+ * 20 (1.3e-6). */
 #define PSUM_TERMS_FAST     0  /* plain float32 terms */
 #define PSUM_TERMS_REFINED  1  /* the charge sums' far terms with 1/r as a float pair (the rsqrt
                                   estimate plus its Newton correction) fused into the sums
                                   unrounded, the targets' offsets rounded once, and the potential's
                                   running sums cut every 8 steps: about 0.6 of the fast terms' error
-                                  for about 1.25x the symmetric charge kernel's time.  Applies to
+                                  for about 1.7x the symmetric charge kernel's time.  Applies to
                                   the symmetric charge kernel (psum_pair_kernel); the one-sided
                                   kernels and batches keep the fast terms. */
 
