@@ -135,6 +135,9 @@ __global__ void __launch_bounds__(kThreads32, kMinB) k_near32(Near32Args a) {
     const int64_t u_end = sk_bound(item + 1, a.U, a.W);
     int sb = near_sys_by_unit(a.tab, u);
     int64_t cur_tile = -1, cur_chunk = -1, cur_first = 0;
+    // two-layer check sums: a tile whose groups 2 and 3 hold no point (both marked
+    // kGroupEmpty, the padding after the last points) runs its second packed target pair not at all
+    bool pair1_live = true;
     while (u < u_end) {
         // the system descriptor is re-read (parameter or L1) rather than held in registers
         const NearSys* Sp = a.tab.many ? a.tab.many + sb : &a.tab.one;
@@ -184,6 +187,8 @@ __global__ void __launch_bounds__(kThreads32, kMinB) k_near32(Near32Args a) {
             }
             cur_tile = tile;
             cur_first = Sp->unit0 + tile_l * upt;
+            pair1_live = kGrad || ncls <= 1 || !a.grp_cls ||
+                         !(a.grp_cls[tile * kTgt32 + 2] & a.grp_cls[tile * kTgt32 + 3] & kGroupEmpty);
             cur_chunk = -1;
         }
         if (chunk != cur_chunk) {
@@ -341,10 +346,11 @@ __global__ void __launch_bounds__(kThreads32, kMinB) k_near32(Near32Args a) {
             ulo = s_hm + 2 * kNearChunk;
             un = padded;
         }
+        const int n_pairs = pair1_live ? 2 : 1;
         if constexpr (kFF) {
             // every unit in float-float: t' = t + delta as hi + lo
 #pragma unroll 1
-            for (int j = 0; j < 2; ++j) {
+            for (int j = 0; j < n_pairs; ++j) {
                 const float* d0 = dptr(2 * j);
                 const float* d1 = dptr(2 * j + 1);
                 float2 nTh[3], nTl[3];
@@ -378,7 +384,7 @@ __global__ void __launch_bounds__(kThreads32, kMinB) k_near32(Near32Args a) {
             // near pairs: t' = t + delta in float-float (hi by rounding, lo = exact remainder +
             // both lo parts); a pair whose two groups are both far takes the far loop alone
 #pragma unroll 1
-            for (int j = 0; j < 2; ++j) {
+            for (int j = 0; j < n_pairs; ++j) {
                 const float* d0 = dptr(2 * j);
                 const float* d1 = dptr(2 * j + 1);
                 if (!(cls & (j ? kUnitNear1 : kUnitNear0))) {
@@ -429,6 +435,23 @@ __global__ void __launch_bounds__(kThreads32, kMinB) k_near32(Near32Args a) {
                     two_sum_acc2(s_acc[2 % NQ][j][0][tid], s_acc[2 % NQ][j][1][tid], agy);
                     two_sum_acc2(s_acc[3 % NQ][j][0][tid], s_acc[3 % NQ][j][1][tid], agz);
                 }
+            }
+        } else if (!pair1_live) {
+            // the first packed target pair alone
+            const float* d0 = dptr(0);
+            const float* d1 = dptr(1);
+            const float2 tx = s_th[0][0][tid], ty = s_th[1][0][tid], tz = s_th[2][0][tid];
+            const float2 nx[1] = {make_float2(-(tx.x + d0[0]), -(tx.y + d1[0]))};
+            const float2 ny[1] = {make_float2(-(ty.x + d0[1]), -(ty.y + d1[1]))};
+            const float2 nz[1] = {make_float2(-(tz.x + d0[2]), -(tz.y + d1[2]))};
+            float2 aphi[1] = {make_float2(0.f, 0.f)}, agx[1] = {aphi[0]}, agy[1] = {aphi[0]}, agz[1] = {aphi[0]};
+            pair_loop_far<kGrad, 1>(uhi, nx, ny, nz, aphi, agx, agy, agz, un);
+            if constexpr (!kGrad) aphi[0] = __fmul2_rn(aphi[0], wpair(0));
+            two_sum_acc2(s_acc[0][0][0][tid], s_acc[0][0][1][tid], aphi[0]);
+            if (kGrad) {
+                two_sum_acc2(s_acc[1 % NQ][0][0][tid], s_acc[1 % NQ][0][1][tid], agx[0]);
+                two_sum_acc2(s_acc[2 % NQ][0][0][tid], s_acc[2 % NQ][0][1][tid], agy[0]);
+                two_sum_acc2(s_acc[3 % NQ][0][0][tid], s_acc[3 % NQ][0][1][tid], agz[0]);
             }
         } else {
             float2 nx[2], ny[2], nz[2];

@@ -318,6 +318,7 @@ static int build_check_layers(Plan& pl, const double d[3]) {
         pack_groups32(pl.Y, slot, (int)(slot.size() / kNearChunk), pk, org);
         const size_t ng = slot.size() / kNearChunk;
         std::vector<int> gmask(ng, 0);   // classes present in each group
+        std::vector<int> npts(ng, 0);
         int last = cls[slot[0]];         // slot 0 holds a point: M >= 1
         for (size_t i = 0; i < slot.size(); ++i) {
             // a padding slot takes the class of the last point before it, which its group
@@ -327,7 +328,12 @@ static int build_check_layers(Plan& pl, const double d[3]) {
             pk[2 * i + 1].z = (float)c;
             pk[2 * i + 1].w = (float)c;
             gmask[i / kNearChunk] |= 1 << c;
+            if (slot[i] >= 0) ++npts[i / kNearChunk];
         }
+        // a group of padding alone is marked (kGroupEmpty): the kernel skips a packed target
+        // pair of two such groups
+        for (size_t g = 0; g < ng; ++g)
+            if (!npts[g]) gmask[g] |= kGroupEmpty;
         // per (group, class): centre and radius of the class's points in the group, for the
         // near-unit test (a group at a class boundary spans two caps of the sphere)
         std::vector<double> sub(ng * kCheckClasses * 4, 0.0);

@@ -69,6 +69,9 @@ __host__ __device__ __forceinline__ uint32_t hilbert_key24(uint32_t c0, uint32_t
     return (spread3_8(X[0]) << 2) | (spread3_8(X[1]) << 1) | spread3_8(X[2]);
 }
 
+// two-layer check points: flag in a group's class mask for a group of padding alone
+constexpr int kGroupEmpty = 1 << 30;
+
 // device status bits (OR-ed by kernels, mapped to PSUM_ERR_* on the host)
 constexpr int kStatNonNeutral = 1;
 constexpr int kStatOutOfBox = 2;
