@@ -130,3 +130,25 @@ def test_degenerate_systems_in_one_batch(precision, pairs):
             assert_close(g[sl], _REF[s.name]["grad"], TOL[precision], f"batch {s.name}/{precision}/{pairs} grad")
     finally:
         pb.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32c", "ff"])
+def test_evaluation_points_on_charges_in_other_groups(precision):
+    """Evaluation points at a subset of the charge positions (plus points between them): sorted
+    and grouped on their own, so a point and the charge it sits on lie in different groups; the
+    pair is dropped (K(0) = 0) as in the oracle, which skips exact zeros."""
+    s = _triples()
+    rng = np.random.default_rng(9)
+    y = np.concatenate([s.x[rng.choice(len(s.x), 700, replace=False)],
+                        rng.uniform(-0.5, 0.5, (300, 3)) * np.asarray(D)])
+    ref = O.Plan(s.d, s.p, s.M).evaluate(s.x, s.q, targets=y, parts=True)
+    pc = B.PeriodicCoulomb(s.d, s.p, s.M, precision=precision)
+    try:
+        phi, g = pc.at(torch.as_tensor(s.x, device="cuda"), torch.as_tensor(s.q, device="cuda"),
+                       torch.as_tensor(y, device="cuda"))
+        phi, g = phi.cpu().numpy(), g.cpu().numpy()
+    finally:
+        pc.close()
+    assert np.all(np.isfinite(phi)) and np.all(np.isfinite(g))
+    assert_close(phi, ref["phi"], TOL[precision], f"points/{precision} phi")
+    assert_close(g, ref["grad"], TOL[precision], f"points/{precision} grad")
